@@ -1,0 +1,141 @@
+"""Pins of the oracle's assembled operators on closed surfaces (identities,
+closed forms on the sphere, O(h^2) convergence)."""
+import functools
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import closed_forms as cf
+from synth import icosphere
+
+A_RAD = 2.0
+KAPPA = 0.125
+
+
+@functools.lru_cache(maxsize=None)
+def _ops(level, radius=A_RAD, kappa=KAPPA):
+    v, t = icosphere(level, radius)
+    return v, t, oracle.assemble(v, t, kappa)
+
+
+def test_mass_matrix_closed_form():
+    v, t, o = _ops(1)
+    area = sum(0.5 * np.linalg.norm(np.cross(v[b] - v[a], v[c] - v[a])) for a, b, c in t)
+    assert abs(o.M.sum() - area) < 1e-13 * area
+    assert np.abs(o.M - o.M.T).max() == 0.0
+    # one triangle by hand: |tau|/12 [[2,1,1],[1,2,1],[1,1,2]]
+    v1 = np.array([[0, 0, 0], [2, 0, 0], [0, 1, 0], [0, 0, 3]], float)
+    t1 = np.array([[0, 2, 1], [0, 1, 3], [1, 2, 3], [0, 3, 2]], dtype=np.int32)
+    M = oracle.assemble(v1, t1, 0.1).M
+    ar = [0.5 * np.linalg.norm(np.cross(v1[b] - v1[a], v1[c] - v1[a])) for a, b, c in t1]
+    ref = np.zeros((4, 4))
+    for (a, b, c), s in zip(t1, ar):
+        for i in (a, b, c):
+            for j in (a, b, c):
+                ref[i, j] += s / 12.0 * (2.0 if i == j else 1.0)
+    assert np.allclose(M, ref, rtol=1e-14, atol=0)
+
+
+@pytest.mark.parametrize("level", [1, 2])
+def test_laplace_double_layer_gauss_identity(level):
+    """K_L 1 = -1/2 M 1 on a closed surface (solid-angle identity; the jump
+    relation gives -1/2 for the interior trace of the double layer of 1)."""
+    v, t, o = _ops(level)
+    one = np.ones(len(v))
+    err = np.linalg.norm(o.KL @ one + 0.5 * o.M @ one) / np.linalg.norm(0.5 * o.M @ one)
+    assert err < 1e-5
+
+
+def test_laplace_hypersingular_kills_constants():
+    v, t, o = _ops(2)
+    assert np.abs(o.DL @ np.ones(len(v))).max() < 1e-13 * np.abs(o.DL).max()
+
+
+def _errs(fn, levels=(1, 2, 3)):
+    return [fn(*_ops(L)) for L in levels]
+
+
+def _check_h2(errs, lo=3.0):
+    r1, r2 = errs[0] / errs[1], errs[1] / errs[2]
+    assert lo < r1 < 5.5 and lo < r2 < 5.5, errs
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("op", ["VL", "VY", "KY", "TY", "DY"])
+def test_sphere_constants_converge_at_h2(op):
+    """A 1 ~ lambda M 1 with lambda from the closed forms on the sphere
+    (derived with the chord-length integral); the error falls ~4x per level."""
+    V1, K1, D1 = cf.sphere_constant_eigs(A_RAD, KAPPA)
+    lam = {"VL": A_RAD, "VY": V1, "KY": K1, "TY": K1, "DY": D1}[op]
+
+    def err(v, t, o):
+        one = np.ones(len(v))
+        m1 = o.M @ one
+        return np.linalg.norm(getattr(o, op) @ one - lam * m1) / np.linalg.norm(lam * m1)
+    # T 1 = K^T 1 sums the double-layer kernel over its first argument, which
+    # the flat faces of the polyhedron approximate more slowly (ratio ~2.5 per
+    # level on levels 1-4, the same for the Laplace kernel); K 1 is O(h^2).
+    _check_h2(_errs(err), lo=2.2 if op == "TY" else 3.0)
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("deg", [1, 2])
+def test_laplace_sphere_harmonics(deg):
+    """Rayleigh quotients of the P1 interpolant of a degree-n harmonic tend to
+    V: a/(2n+1), K: -1/(2(2n+1)), D: n(n+1)/(a(2n+1)) at O(h^2)."""
+    lamV, lamK, lamD = cf.laplace_sphere_eigs(A_RAD, deg)
+
+    def err(v, t, o):
+        z = v[:, 2] / np.linalg.norm(v, axis=1)
+        y = z if deg == 1 else 1.5 * z * z - 0.5
+        mm = y @ o.M @ y
+        e = [abs(y @ o.VL @ y / mm - lamV) / lamV, abs(y @ o.KL @ y / mm - lamK) / abs(lamK),
+             abs(y @ o.DL @ y / mm - lamD) / lamD]
+        return max(e)
+    errs = _errs(err)
+    assert errs[-1] < 2e-2
+    assert errs[0] / errs[2] > 10.0, errs
+
+
+def test_symmetry_of_V_and_D():
+    v, t, o = _ops(2)
+    for name in ("VL", "VY", "DL", "DY"):
+        A = getattr(o, name)
+        assert np.abs(A - A.T).max() < 1e-6 * np.abs(A).max(), name
+
+
+@pytest.mark.slow
+def test_calderon_identity_strong_form():
+    """[-K V; D T]^2 = 1/4 I (paper eq. prec:calderon) for the strong-form
+    discrete Laplace operators M^-1 A: eigenvalues cluster at 1/4."""
+    v, t, o = _ops(3)
+    Minv = np.linalg.inv(o.M)
+    n = len(v)
+    C = np.block([[-Minv @ o.KL, Minv @ o.VL], [Minv @ o.DL, Minv @ o.TL]])
+    ev = np.linalg.eigvals(C @ C).real
+    assert abs(np.median(ev) - 0.25) < 0.025
+    assert np.mean(np.abs(ev - 0.25) < 0.05) > 0.9
+
+
+def test_row_sample_equals_dense_rows():
+    v, t, o = _ops(1)
+    rows = np.array([0, 7, 41])
+    R = oracle.assemble_rows(v, t, rows, KAPPA)
+    for name in ("VL", "KL", "DL", "VY", "KY", "DY", "M"):
+        ref = getattr(o, name)[rows]  # same terms, summed in another order
+        assert np.abs(R[name] - ref).max() <= 1e-14 * np.abs(ref).max(), name
+
+
+def test_source_projections_partition_and_gauss_law():
+    """sum_i b_D,i = int phi_D (P1 partition of unity, compared with the
+    closed form for a centred charge on the sphere's polyhedron up to the
+    quadrature) and sum_i b_N,i = -sum q / eps_int (Gauss's law)."""
+    v, t = icosphere(3, A_RAD)
+    xq = np.array([[0.1, -0.2, 0.3], [-0.4, 0.2, 0.0]])
+    q = np.array([0.7, -0.25])
+    bD, bN = oracle.source_projections(v, t, xq, q, 4.0)
+    assert abs(bN.sum() + q.sum() / 4.0) < 1e-3 * abs(q.sum() / 4.0)
+    # centred unit charge: phi_D = 1/(4 pi eps r) and int over the sphere = a/eps
+    bD0, _ = oracle.source_projections(v, t, np.zeros((1, 3)), np.ones(1), 4.0)
+    assert abs(bD0.sum() - A_RAD / 4.0) < 1e-2 * A_RAD / 4.0
