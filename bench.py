@@ -1,0 +1,356 @@
+"""Benchmark: boundary-element Poisson-Boltzmann solves on the multi-charge
+sphere (icosphere level 5, radius 10 A, 20 charges uniform in the ball of
+radius 8 A with values uniform in [-1, 1] e; eps 4/80, kappa 0.125), plus the
+far-field matvec rate.
+
+One step = one complete solve through the C ABI on device-resident inputs:
+mesh ingest, FP64 near-field build, charge right-hand side, preconditioned
+GMRES (FP32 inner solves inside FP64 iterative refinement) and the
+solvation-energy reduction, with Delta G read back to the host.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Multi-GPU (torchrun, one process per GPU): independent replicas of the same
+solve on every GPU (the solve does not shard); only timing scalars cross
+ranks. Prints one JSON line on rank 0.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from synth import multi_charge_sphere  # noqa: E402
+
+METRIC = "PB solves/s and p50/p99 latency at dG rel err <=1e-5; BEM matvec Gpairs/s"
+UNIT = "solves/s"
+SM_COUNT_GB300 = 152
+FP32_LANES_PER_SM = 128  # FP32 pipe operations per SM per clock
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--case", type=int, default=10)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "f64"])
+    ap.add_argument("--level", type=int, default=5)
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def workload(level):
+    v, t, xq, q = multi_charge_sphere(level=level, radius=10.0, n_charges=20, charge_radius=8.0, seed=2)
+    return v, t, xq, q
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi samples every 200 ms while the timed region runs."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, ValueError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                smax.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- oracle
+def oracle_sample(v, t, xq, q, case, rows=48):
+    """The FP64 oracle on a bounded sample of one solve: a row sample of the
+    dense assembly (extrapolated to all rows), the dense LU of the 2N_v
+    system timed on an n = 2048 matrix and scaled by n^3, and the exact
+    right-hand side and energy loops. Returns (seconds per solve, cores, text)."""
+    import oracle
+    import scipy.linalg
+    phys = oracle.Physics(4.0, 80.0, 0.125)
+    nv = v.shape[0]
+    cores = os.cpu_count() or 1
+    rng = np.random.default_rng(0)
+    sel = np.sort(rng.choice(nv, size=min(rows, nv), replace=False))
+    t0 = time.perf_counter()
+    oracle.assemble_rows(v, t, sel, phys.kappa, nthreads=cores)
+    t_rows = time.perf_counter() - t0
+    t_asm = t_rows * nv / len(sel)
+    t0 = time.perf_counter()
+    oracle.source_projections(v, t, xq, q, phys.eps_int)
+    t_rhs = time.perf_counter() - t0
+    n_small = 2048
+    a = rng.standard_normal((n_small, n_small)) + n_small * np.eye(n_small)
+    t0 = time.perf_counter()
+    scipy.linalg.lu_factor(a, overwrite_a=True)
+    t_lu = (time.perf_counter() - t0) * (2.0 * nv / n_small) ** 3
+    t0 = time.perf_counter()
+    oracle.reaction_potential(v, t, np.zeros(nv), np.zeros(nv), xq)
+    t_en = time.perf_counter() - t0
+    total = t_asm + t_rhs + t_lu + t_en
+    text = (f"{len(sel)} of {nv} assembly rows timed and scaled to all rows ({t_asm:.1f} s); dense LU timed at "
+            f"n={n_small} and scaled by n^3 to n={2 * nv} ({t_lu:.1f} s); right-hand side and energy timed in "
+            f"full ({t_rhs + t_en:.2f} s); case {case}")
+    return total, cores, text
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    v, t, xq, q = workload(args.level)
+    times = []
+    for i in range(args.warmup + args.steps):
+        total, cores, text = oracle_sample(v, t, xq, q, args.case, rows=16 if i < args.warmup else 48)
+        if i >= args.warmup:
+            times.append(total)
+    sec = float(np.mean(times))
+    val = 1.0 / sec
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "multi-charge sphere: icosphere level 5 (10242 verts, 20480 tris), 20 charges, "
+                                   f"case {args.case}, FP64 CPU oracle", "case": args.case},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": text},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------- ours
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2108_10481_gb300 as pb
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    v, t, xq, q = workload(args.level)
+    form, prec = pb.CASES[args.case]
+    P = pb.Params(4.0, 80.0, 0.125)
+    precision = pb.PB_MIXED if args.precision == "mixed" else pb.PB_F64
+    opts = pb.solve_opts(tol=args.tol, max_it=400, precision=precision, inner_tol=1e-4)
+    ctx = pb.pb_init(local_rank)
+    dv = torch.as_tensor(v, device=dev)
+    dt = torch.as_tensor(t, device=dev)
+    dxq = torch.as_tensor(xq, device=dev)
+    dq = torch.as_tensor(q, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    def step():
+        m = pb.pb_mesh_load(ctx, dv, dt)
+        nf = pb.pb_near_build(ctx, m, P.kappa)
+        rhs = pb.pb_rhs_charges(ctx, m, dxq, dq, P, form)
+        x, info = pb.pb_solve(ctx, m, nf, P, form, prec, rhs, opts=opts)
+        dG, dGk = pb.pb_energy(ctx, m, x, form, dxq, dq, P)
+        nf.free()
+        m.free()
+        return dGk, info
+
+    # warm-up (untimed)
+    for _ in range(args.warmup):
+        dGk, info = step()
+    torch.cuda.synchronize()
+
+    # accuracy of the measured path: FP64 GPU solve of the same case (outside the timed region)
+    m = pb.pb_mesh_load(ctx, dv, dt)
+    nf = pb.pb_near_build(ctx, m, P.kappa)
+    rhs = pb.pb_rhs_charges(ctx, m, dxq, dq, P, form)
+    x64, info64 = pb.pb_solve(ctx, m, nf, P, form, prec, rhs, opts=pb.solve_opts(tol=1e-8, max_it=600))
+    _, dG64 = pb.pb_energy(ctx, m, x64, form, dxq, dq, P)
+    # far-field matvec rate (FP32 system application of this formulation)
+    xs = torch.randn(2 * v.shape[0], dtype=torch.float64, device=dev)
+    ys = torch.empty_like(xs)
+    for _ in range(3):
+        pb.pb_system_apply(ctx, m, nf, P, form, xs, pb.PB_F32, y=ys)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    nmv = 10
+    flush.zero_()
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(nmv):
+        pb.pb_system_apply(ctx, m, nf, P, form, xs, pb.PB_F32, y=ys)
+    e1.record()
+    torch.cuda.synchronize()
+    mv_ms = e0.elapsed_time(e1) / nmv
+    npts = m.info()["n_points"]
+    nf.free()
+    m.free()
+
+    # timed region
+    sampler = ClockSampler(local_rank)
+    torch.cuda.synchronize()
+    barrier()
+    sampler.start()
+    pb.pb_profile(ctx, True)
+    launches0 = pb.pb_launch_count()
+    step_ms, dGs, iters, outer = [], [], [], []
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()  # L2 flush between timed steps, outside the events
+        ev[k][0].record()
+        dGk, info = step()
+        ev[k][1].record()
+        dGs.append(dGk)
+        iters.append(info["iters"])
+        outer.append(info["outer_iters"])
+    torch.cuda.synchronize()
+    barrier()
+    wall = time.perf_counter() - wall0
+    launches = pb.pb_launch_count() - launches0
+    clocks = sampler.stop()
+    for a, b in ev:
+        step_ms.append(a.elapsed_time(b))
+    fam = {k: pb.pb_profile_read(ctx, k) for k in (pb.PB_KERNEL_PAIR32, pb.PB_KERNEL_PAIR32_ACCURATE,
+                                                   pb.PB_KERNEL_PAIR64)}
+    pb.pb_profile(ctx, False)
+    total_ms = float(np.sum(step_ms))
+    if world > 1:
+        tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        total_ms = float(tt.item())
+
+    # e2e: the host-buffer entry point, pinned inputs, dG read back each step
+    e2e = None
+    if not args.no_e2e:
+        import torch as _t
+        hv = _t.from_numpy(v).pin_memory().numpy()
+        ht = _t.from_numpy(t).pin_memory().numpy()
+        hxq = _t.from_numpy(np.ascontiguousarray(xq)).pin_memory().numpy()
+        hq = _t.from_numpy(q).pin_memory().numpy()
+        pb.pb_solvation_energy(ctx, hv, ht, hxq, hq, P, form, prec, opts=opts)
+        torch.cuda.synchronize()
+        barrier()
+        k_e2e = max(3, args.steps // 2)
+        w0 = time.perf_counter()
+        for _ in range(k_e2e):
+            pb.pb_solvation_energy(ctx, hv, ht, hxq, hq, P, form, prec, opts=opts)
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - w0
+        if world > 1:
+            tt = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            e2e_s = float(tt.item())
+        e2e = {"value": world * k_e2e / e2e_s, "unit": UNIT,
+               "h2d_bytes_per_step": int(v.nbytes + t.nbytes + xq.nbytes + q.nbytes), "d2h_bytes_per_step": 8}
+
+    if rank != 0:
+        return
+    # roofline of the dominant kernel family (largest device time in the timed region)
+    kid = max(fam, key=lambda k: fam[k]["ms"])
+    st = fam[kid]
+    names = {pb.PB_KERNEL_PAIR32: "k_pair32 (FP32 far field)", pb.PB_KERNEL_PAIR32_ACCURATE:
+             "k_pair32 split-coordinate (FP32 far field, FP64 tile sums)", pb.PB_KERNEL_PAIR64: "k_pair64 (FP64)"}
+    avg_ms = st["ms"] / max(1, st["launches"])
+    ops_per_launch = st["ops"] / max(1, st["launches"])
+    achieved = ops_per_launch / (avg_ms * 1e-3) / 1e12 if avg_ms > 0 else 0.0
+    sm_max = clocks.get("sm_max_mhz") or 2070.0
+    peak = SM_COUNT_GB300 * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12
+    lat = np.array(step_ms)
+    dG_err = abs(float(np.mean(dGs)) / dG64 - 1.0)
+    value = world * args.steps / (total_ms * 1e-3)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+        "config": {"workload": "multi-charge sphere: icosphere level %d (%d verts, %d tris), radius 10 A, 20 charges "
+                               "uniform in r<=8 A, q~U[-1,1] e, eps 4/80, kappa 0.125" % (args.level, v.shape[0],
+                                                                                         t.shape[0]),
+                   "case": args.case, "formulation": form, "preconditioner": prec, "precision": args.precision,
+                   "gmres_tol": args.tol, "quadrature": "far 6-point degree-4 rule, singular 4^4 Gauss per region",
+                   "points": npts, "l2": "flushed (256 MB write) before every timed step",
+                   "parallelism": "replicas" if world > 1 else "1 GPU"},
+        "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                       "min": float(lat.min()), "max": float(lat.max())},
+        "dG_kcal": float(np.mean(dGs)), "dG_rel_err_vs_f64_gpu": dG_err, "gmres_iters": int(np.median(iters)),
+        "refinement_sweeps": int(np.median(outer)),
+        "matvec": {"gpairs_per_s": npts * npts / (mv_ms * 1e-3) / 1e9, "ms": mv_ms, "points": npts,
+                   "tri_pairs_per_s": t.shape[0] ** 2 / (mv_ms * 1e-3), "precision": "f32"},
+        "roofline": {"bound": "alu", "kernel": names[kid], "achieved": achieved, "peak": peak, "unit": "Tops/s",
+                     "frac": achieved / peak if peak > 0 else None, "traffic": None,
+                     "launches": st["launches"], "avg_launch_ms": avg_ms,
+                     "ops_per_pair": st["ops"] / max(1.0, st["pairs"]),
+                     "peak_basis": "%d SMs x %d FP32 ops/clk x %.0f MHz" % (SM_COUNT_GB300, FP32_LANES_PER_SM, sm_max)},
+        "clocks": clocks, "gpu_launches": int(launches), "wall_s": wall,
+    }
+    if e2e:
+        line["e2e"] = e2e
+    if not args.no_baseline:
+        sec, cores, text = oracle_sample(v, t, xq, q, args.case)
+        line["cpu_baseline"] = {"value": 1.0 / sec, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": text}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if os.environ.get("PB_BENCH_BACKEND", "nccl") == "nccl" else "gloo")
+    run_ours(args, rank, world, local_rank)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,256 @@
+/*
+ * pbbem.h - C ABI of the GB300 boundary-element Poisson-Boltzmann library.
+ *
+ * Problem (arxiv 2108.10481, eq. poissonboltzmann): a closed molecular
+ * surface Gamma separates an interior region (permittivity eps_int, point
+ * charges q_j at x_j) from a solvent (permittivity eps_ext, inverse Debye
+ * length kappa). The library discretises the interior Laplace and exterior
+ * Yukawa boundary operators (paper eq. layer_potentials: single layer V,
+ * double layer K, adjoint double layer T, hypersingular D) with continuous
+ * piecewise-linear (P1) Galerkin elements on a triangle mesh (paper,
+ * "Numerical discretization": one unknown per vertex and trace), solves one
+ * of the paper's boundary integral formulations with preconditioned GMRES and
+ * returns the polar solvation energy (paper eq. dG).
+ *
+ * Conventions
+ *   - Every function returns an int status: PB_OK (0) or a negative PB_E*
+ *     code. On error a message is stored per thread and pb_last_error()
+ *     returns it. No function aborts, traps or exits the process.
+ *   - "device" pointers are CUDA device addresses on the context's device,
+ *     owned by the caller (e.g. torch tensors); "host" pointers are ordinary
+ *     CPU memory. Arrays are dense, row-major, 64-bit floats unless stated.
+ *   - Unknown vectors have 2*N_v entries: x = [u; v] with u the Dirichlet and
+ *     v the Neumann trace coefficients (P1, one per vertex) on the side the
+ *     formulation solves for (interior or exterior, paper eqs.
+ *     bie:dirichlet:int ... bie:lu:ext).
+ *   - stream: a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream). Compute calls enqueue work on it; calls that return host
+ *     scalars (pb_energy, pb_solve's info) synchronise it.
+ *   - Handles (pb_ctx, pb_mesh, pb_near) are owned by the library and freed
+ *     with their pb_free_* call. A handle may be used from one host thread at
+ *     a time.
+ *   - Units: lengths in Angstrom, charges in e; potentials in "paper units"
+ *     (G = 1/(4 pi r), sources q/eps_int); energies additionally in kcal/mol.
+ */
+#ifndef PBBEM_H
+#define PBBEM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define PB_OK 0
+#define PB_EINVAL (-1)   /* bad argument (NULL handle, size, enum, pointer kind) */
+#define PB_EMESH (-2)    /* mesh is not a closed, oriented, 2-manifold surface */
+#define PB_ENOMEM (-3)   /* device or host allocation failed */
+#define PB_ENOCONV (-4)  /* GMRES reached max_it before tol (best x returned) */
+#define PB_ENUMERIC (-5) /* NaN or Inf met in a residual */
+#define PB_ECUDA (-6)    /* a CUDA runtime call failed */
+#define PB_ETIMEOUT (-7) /* a bounded device-side wait gave up */
+
+/* ---- enumerations ------------------------------------------------------ */
+/* operators of paper eq. layer_potentials, plus the mass matrix */
+#define PB_OP_V 0
+#define PB_OP_K 1
+#define PB_OP_T 2
+#define PB_OP_D 3
+#define PB_OP_M 4
+/* Green's functions (paper, "Boundary integral formulations"):
+ * G_int = 1/(4 pi r), G_ext = exp(-kappa r)/(4 pi r) */
+#define PB_LAPLACE 0
+#define PB_YUKAWA 1
+/* arithmetic of a far-field application */
+#define PB_F64 0          /* FP64 everywhere */
+#define PB_F32 1          /* FP32 pair sums and FP32 near field (inner solves) */
+#define PB_F32_ACCURATE 2 /* FP32 pair arithmetic on split (hi+lo) coordinates with
+                             FP64 accumulation per source tile, FP64 near field */
+#define PB_MIXED 3        /* (pb_solve_opts.precision) FP32 inner GMRES inside FP64
+                             iterative refinement */
+
+/* formulations (paper, "Boundary integral formulations") */
+#define PB_DIRECT_INT 0      /* eq. bie:dirichlet:int, unknowns interior */
+#define PB_DIRECT_EXT 1      /* eq. bie:dirichlet:ext, unknowns exterior */
+#define PB_DIRECT_INT_PERM 2 /* the same two rows swapped */
+#define PB_DIRECT_EXT_PERM 3
+#define PB_CFIE_INT 4        /* eq. bie:combined:int, alpha and beta from the opts */
+#define PB_CFIE_EXT 5        /* eq. bie:combined:ext */
+#define PB_PMCHWT_INT 6      /* eq. bie:pmchwt:int (alpha = beta = -1, as printed) */
+#define PB_PMCHWT_EXT 7      /* eq. bie:pmchwt:ext */
+#define PB_MULLER_INT 8      /* eq. bie:muller:int (alpha = beta = 1) */
+#define PB_MULLER_EXT 9      /* eq. bie:muller:ext */
+#define PB_JUFFER 10         /* eq. bie:juffer:int (alpha = eps_ext/eps_int, beta = 1/alpha) */
+#define PB_LU 11             /* eq. bie:lu:ext (second row scaled by eps_int/eps_ext) */
+
+/* preconditioners (paper, "Preconditioning") */
+#define PB_PC_NONE 0
+#define PB_PC_BLOCK_DIAG 1          /* per-DOF inverse of the diagonals of the four blocks */
+#define PB_PC_MASS 2                /* eq. prec:mass */
+#define PB_PC_SCALED_MASS 3         /* eq. prec:mass:scaled, (a, b) from the opts or the
+                                       Juffer default a = 1+eps_ext/eps_int, b = 1+eps_int/eps_ext */
+#define PB_PC_CALDERON_FULL 4       /* eqs. prec:calderon:int:full / ext:full (PMCHWT only) */
+#define PB_PC_CALDERON_INT 5        /* interior half Calderon */
+#define PB_PC_CALDERON_EXT 6        /* exterior half Calderon */
+#define PB_PC_SCALED_CALDERON_INT 7 /* scaled mass on top of the interior half Calderon */
+#define PB_PC_SCALED_CALDERON_EXT 8 /* ... of the exterior half Calderon */
+
+typedef struct pb_ctx pb_ctx;
+typedef struct pb_mesh pb_mesh;
+typedef struct pb_near pb_near;
+
+/* physical parameters (paper eq. poissonboltzmann) */
+typedef struct {
+    double eps_int; /* interior permittivity (> 0) */
+    double eps_ext; /* solvent permittivity (> 0) */
+    double kappa;   /* inverse Debye length, 1/Angstrom (>= 0) */
+} pb_params;
+
+/* quadrature plan: the discrete definition of every operator entry */
+typedef struct {
+    int far_q; /* points of the symmetric triangle rule used on both triangles of
+                  pairs that share no vertex: 1, 3 (degree 2) or 6 (degree 4) */
+    int n_ss;  /* Gauss-Legendre points per dimension of the regularised [0,1]^4
+                  rule for coincident, edge- and vertex-adjacent pairs (1..12) */
+} pb_quad_plan;
+
+/* memory kind of pb_mesh_load's inputs */
+#define PB_MEM_HOST 0
+#define PB_MEM_DEVICE 1
+
+typedef struct {
+    double tol;        /* relative left-preconditioned residual target */
+    int max_it;        /* GMRES iterations (per refinement sweep for PB_MIXED) */
+    int restart;       /* 0 = unrestarted (basis of max_it vectors) */
+    int precision;     /* PB_F64 or PB_MIXED */
+    double inner_tol;  /* PB_MIXED: relative tolerance of each inner solve */
+    int max_outer;     /* PB_MIXED: refinement sweeps */
+    double alpha;      /* PB_CFIE_INT / PB_CFIE_EXT coefficients */
+    double beta;
+    double pc_a;       /* scaled-mass constants; 0 = the paper's choice */
+    double pc_b;
+} pb_solve_opts;
+
+typedef struct {
+    int status;          /* same as the return code */
+    int iters;           /* total GMRES iterations (all sweeps) */
+    int outer_iters;     /* refinement sweeps (1 for PB_F64) */
+    int system_applies;  /* far-field system applications */
+    double rel_residual; /* final ||P^-1 (b - A x)|| / ||P^-1 b|| (FP64 outer estimate) */
+    double time_ms;      /* device time of the solve */
+} pb_solve_info;
+
+/* ---- context ------------------------------------------------------------ */
+/* Create a context on CUDA device `device`. Returns PB_ECUDA if the device
+ * cannot be used, PB_EINVAL if out is NULL. */
+int pb_init(int device, pb_ctx** out);
+/* Free a context (NULL is allowed). Meshes and near fields must be freed first. */
+int pb_free_ctx(pb_ctx* ctx);
+/* Message of the last error on this thread ("" if none). Never NULL. */
+const char* pb_last_error(void);
+/* Library version string, e.g. "pbbem 0.1 sm_103a". */
+const char* pb_version(void);
+
+/* ---- a1: mesh ingest ---------------------------------------------------- */
+/* Copy in and validate a triangle mesh (paper, "Numerical discretization":
+ * P1 elements on a triangular surface mesh; eq. poissonboltzmann: the
+ * interface Gamma with outward normal n).
+ *   verts: n_verts x 3 doubles; tris: n_tris x 3 int32 vertex indices listed
+ *   counter-clockwise seen from outside; mem: PB_MEM_HOST or PB_MEM_DEVICE.
+ * Checks: indices in range, no zero-area triangle, every edge shared by
+ * exactly two triangles with opposite orientations (closed, oriented
+ * 2-manifold), positive enclosed volume; else PB_EMESH. Builds the
+ * quadrature points of `plan` (NULL = {6, 4}), the vertex->triangle map, the
+ * adjacent triangle pairs and the vertex-pair pattern of the near field.
+ * The library owns *out; free with pb_free_mesh. */
+int pb_mesh_load(pb_ctx* ctx, const double* verts, int64_t n_verts, const int32_t* tris,
+                 int64_t n_tris, const pb_quad_plan* plan, int mem, pb_mesh** out);
+int pb_free_mesh(pb_mesh* mesh);
+/* Sizes of a loaded mesh: out[0..5] = N_v, N_t, quadrature points, near
+ * nonzeros per operator, adjacent triangle pairs, device bytes held. */
+int pb_mesh_info(const pb_mesh* mesh, int64_t out[6]);
+
+/* ---- a2: near field ----------------------------------------------------- */
+/* FP64 device build of the singular near field for Yukawa parameter kappa:
+ * for every pair of triangles sharing a vertex, the regularised-quadrature
+ * local blocks of V, K, D (Laplace and Yukawa) minus the same blocks by the
+ * far rule, summed into a vertex-pair CSR (T by transposition, M exact), and
+ * the full operator diagonals. Reusable for any charges with the same kappa.
+ * The library owns *out; free with pb_free_near. */
+int pb_near_build(pb_ctx* ctx, const pb_mesh* mesh, double kappa, pb_near** out, void* stream);
+int pb_free_near(pb_near* near);
+
+/* ---- a3 + a4 + a5: operator application --------------------------------- */
+/* y = A x for one Galerkin operator (N_v -> N_v): op in PB_OP_V..PB_OP_M,
+ * kernel PB_LAPLACE or PB_YUKAWA (ignored for PB_OP_M), prec PB_F64, PB_F32
+ * or PB_F32_ACCURATE. x and y are device arrays of N_v doubles and must not
+ * overlap. The near field must have been built for the kappa wanted. */
+int pb_op_apply(pb_ctx* ctx, const pb_mesh* mesh, const pb_near* near, int op, int kernel,
+                int prec, const double* x, double* y, void* stream);
+/* y = A x for the 2x2 weak-form system of a formulation (PB_DIRECT_INT ...
+ * PB_LU; alpha/beta used by the CFIE forms only). x, y: device, 2*N_v. */
+int pb_system_apply(pb_ctx* ctx, const pb_mesh* mesh, const pb_near* near, const pb_params* prm,
+                    int form, double alpha, double beta, int prec, const double* x, double* y,
+                    void* stream);
+
+/* ---- a6: right-hand side ------------------------------------------------ */
+/* rhs = the formulation's right-hand side built from the source projections
+ * (paper eq. sources: phi_D = sum_j q_j/(4 pi eps_int |x - x_j|), phi_N its
+ * normal derivative), tested against the P1 basis with the far rule.
+ * xq (n_q x 3) and q (n_q) are device arrays; rhs is device, 2*N_v. */
+int pb_rhs_charges(pb_ctx* ctx, const pb_mesh* mesh, const double* xq, const double* q, int64_t n_q,
+                   const pb_params* prm, int form, double alpha, double beta, double* rhs,
+                   void* stream);
+
+/* ---- a7 + a8 + a9: preconditioned GMRES --------------------------------- */
+/* Solve P^-1 A x = P^-1 rhs (paper, "Preconditioning": left preconditioning,
+ * GMRES) from x = 0. opts NULL = {tol 1e-6, max_it 500, unrestarted, PB_F64}.
+ * rhs and x are device arrays of 2*N_v. On PB_ENOCONV x holds the best
+ * iterate and info (optional) is filled. */
+int pb_solve(pb_ctx* ctx, const pb_mesh* mesh, const pb_near* near, const pb_params* prm, int form,
+             int precond, const pb_solve_opts* opts, const double* rhs, double* x,
+             pb_solve_info* info, void* stream);
+
+/* ---- a10: reaction potential and solvation energy ------------------------ */
+/* phi_reac(x_j) = V_int[v_int](x_j) - K_int[u_int](x_j) (paper eq.
+ * phireac_bie) from the solution x of formulation `form` (exterior forms are
+ * converted by u_int = u_ext, v_int = (eps_ext/eps_int) v_ext), and
+ * Delta G = 1/2 sum_j q_j phi_reac(x_j) (paper eq. dG), reduced in FP64.
+ * xq, q device; dG_paper and dG_kcal host (either may be NULL); phi (device,
+ * n_q, may be NULL) receives phi_reac. */
+int pb_energy(pb_ctx* ctx, const pb_mesh* mesh, const double* x, int form, const double* xq,
+              const double* q, int64_t n_q, const pb_params* prm, double* phi, double* dG_paper,
+              double* dG_kcal, void* stream);
+
+/* ---- whole path from host buffers --------------------------------------- */
+/* One solve from host arrays: mesh load, near build, right-hand side, solve
+ * and energy, freeing everything it made. verts/tris/xq/q are host arrays;
+ * dG_kcal (host) receives the energy in kcal/mol. */
+int pb_solvation_energy(pb_ctx* ctx, const double* verts, int64_t n_verts, const int32_t* tris,
+                        int64_t n_tris, const double* xq, const double* q, int64_t n_q,
+                        const pb_params* prm, const pb_quad_plan* plan, int form, int precond,
+                        const pb_solve_opts* opts, double* dG_kcal, pb_solve_info* info,
+                        void* stream);
+
+/* ---- measurement ---------------------------------------------------------- */
+/* kernel families timed by pb_profile */
+#define PB_KERNEL_PAIR32 0          /* FP32 far-field pair kernel (inner solves) */
+#define PB_KERNEL_PAIR32_ACCURATE 1 /* split-coordinate FP32 pair kernel (outer residuals) */
+#define PB_KERNEL_PAIR64 2          /* FP64 pair kernel */
+/* enable (1) or disable (0) per-launch CUDA-event timing of the pair kernels
+ * on their launching stream; either call resets the statistics. No effect on
+ * results. */
+int pb_profile(pb_ctx* ctx, int enable);
+/* Statistics of one kernel family since pb_profile(ctx, 1): launches, summed
+ * device time in ms, target-source point pairs, and FP32/FP64 pipe operations
+ * by the kernel's formula count (operations per pair x pairs). Waits for the
+ * recorded events. Any output pointer may be NULL. */
+int pb_profile_read(pb_ctx* ctx, int kernel, int64_t* launches, double* total_ms, double* pairs, double* ops);
+/* Number of kernels this library has launched in this process (all kinds). */
+int64_t pb_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PBBEM_H */

@@ -1,0 +1,253 @@
+"""Python binding of the C ABI: the same names as include/pbbem.h, taking
+torch tensors (device memory and streams) and doing argument marshalling only.
+Every step of the computation runs in libpbbem's CUDA kernels."""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import native as N
+
+# status codes, enumerations (mirror include/pbbem.h)
+PB_OK, PB_EINVAL, PB_EMESH, PB_ENOMEM, PB_ENOCONV, PB_ENUMERIC, PB_ECUDA, PB_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6, -7
+PB_OP_V, PB_OP_K, PB_OP_T, PB_OP_D, PB_OP_M = 0, 1, 2, 3, 4
+PB_LAPLACE, PB_YUKAWA = 0, 1
+PB_F64, PB_F32, PB_F32_ACCURATE, PB_MIXED = 0, 1, 2, 3
+FORMS = {"direct_int": 0, "direct_ext": 1, "direct_int_perm": 2, "direct_ext_perm": 3, "cfie_int": 4,
+         "cfie_ext": 5, "pmchwt_int": 6, "pmchwt_ext": 7, "muller_int": 8, "muller_ext": 9, "juffer": 10,
+         "lu": 11}
+PRECONDS = {"none": 0, "block_diag": 1, "mass": 2, "scaled_mass": 3, "calderon_full": 4, "calderon_int": 5,
+            "calderon_ext": 6, "scaled_calderon_int": 7, "scaled_calderon_ext": 8}
+# Table 1 of the paper: case -> (formulation, preconditioner)
+CASES = {
+    1: ("direct_int", "none"), 2: ("direct_int", "block_diag"), 3: ("direct_ext", "none"),
+    4: ("direct_ext", "block_diag"), 5: ("direct_int_perm", "none"), 6: ("direct_int_perm", "block_diag"),
+    7: ("direct_ext_perm", "none"), 8: ("direct_ext_perm", "block_diag"), 9: ("juffer", "mass"),
+    10: ("juffer", "scaled_mass"), 11: ("lu", "none"), 12: ("lu", "mass"), 13: ("muller_int", "mass"),
+    14: ("muller_ext", "mass"), 15: ("pmchwt_int", "mass"), 16: ("pmchwt_int", "calderon_full"),
+    17: ("pmchwt_int", "calderon_int"), 18: ("pmchwt_int", "calderon_ext"), 19: ("pmchwt_ext", "mass"),
+    20: ("pmchwt_ext", "calderon_full"), 21: ("pmchwt_ext", "calderon_ext"), 22: ("pmchwt_ext", "calderon_int"),
+    23: ("pmchwt_int", "scaled_calderon_int"), 24: ("pmchwt_int", "scaled_calderon_ext"),
+    25: ("pmchwt_ext", "scaled_calderon_ext"), 26: ("pmchwt_ext", "scaled_calderon_int"),
+}
+
+
+class PBError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"pbbem error {code}: {msg}")
+        self.code = code
+
+
+def _check(rc: int):
+    if rc != PB_OK:
+        raise PBError(rc, N.load().pb_last_error().decode())
+    return rc
+
+
+def _stream(stream):
+    if stream is None:
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, torch.cuda.Stream):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+def _dptr(t: torch.Tensor, name: str):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous float64 CUDA tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _form(form):
+    return FORMS[form] if isinstance(form, str) else int(form)
+
+
+def _prec(pc):
+    return PRECONDS[pc] if isinstance(pc, str) else int(pc)
+
+
+@dataclass
+class Params:
+    eps_int: float = 4.0
+    eps_ext: float = 80.0
+    kappa: float = 0.125
+
+    def c(self):
+        return N.pb_params(self.eps_int, self.eps_ext, self.kappa)
+
+
+class _Handle:
+    _free = None
+
+    def __init__(self, ptr, owner=None):
+        self.ptr = ptr
+        self.owner = owner  # keeps the parent alive
+
+    def free(self):
+        if self.ptr:
+            getattr(N.load(), self._free)(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+class Ctx(_Handle):
+    _free = "pb_free_ctx"
+
+
+class Mesh(_Handle):
+    _free = "pb_free_mesh"
+
+    def info(self):
+        out = (ctypes.c_int64 * 6)()
+        _check(N.load().pb_mesh_info(self.ptr, out))
+        return dict(zip(["n_verts", "n_tris", "n_points", "nnz", "n_pairs", "device_bytes"], list(out)))
+
+
+class Near(_Handle):
+    _free = "pb_free_near"
+
+
+PB_KERNEL_PAIR32, PB_KERNEL_PAIR32_ACCURATE, PB_KERNEL_PAIR64 = 0, 1, 2
+
+
+def pb_profile(ctx: Ctx, enable: bool = True):
+    _check(N.load().pb_profile(ctx.ptr, 1 if enable else 0))
+
+
+def pb_profile_read(ctx: Ctx, kernel: int):
+    """dict(launches, ms, pairs, ops) of one pair-kernel family since pb_profile(ctx, True)."""
+    n = ctypes.c_int64()
+    ms, pairs, ops = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(N.load().pb_profile_read(ctx.ptr, kernel, ctypes.byref(n), ctypes.byref(ms), ctypes.byref(pairs),
+                                    ctypes.byref(ops)))
+    return {"launches": n.value, "ms": ms.value, "pairs": pairs.value, "ops": ops.value}
+
+
+def pb_launch_count() -> int:
+    return int(N.load().pb_launch_count())
+
+
+def pb_version() -> str:
+    return N.load().pb_version().decode()
+
+
+def pb_init(device: int = 0) -> Ctx:
+    h = ctypes.c_void_p()
+    _check(N.load().pb_init(int(device), ctypes.byref(h)))
+    return Ctx(h.value)
+
+
+def pb_mesh_load(ctx: Ctx, verts, tris, far_q: int = 6, n_ss: int = 4) -> Mesh:
+    """verts [N_v,3] float64 and tris [N_t,3] int32, numpy (host) or CUDA tensors."""
+    plan = N.pb_quad_plan(far_q, n_ss)
+    if isinstance(verts, torch.Tensor) and verts.is_cuda:
+        v = verts.contiguous()
+        t = tris.to(torch.int32).contiguous()
+        mem, vp, tp, nv, nt = 1, v.data_ptr(), t.data_ptr(), v.shape[0], t.shape[0]
+        keep = (v, t)
+    else:
+        v = np.ascontiguousarray(verts, dtype=np.float64)
+        t = np.ascontiguousarray(tris, dtype=np.int32)
+        mem, vp, tp, nv, nt = 0, v.ctypes.data, t.ctypes.data, v.shape[0], t.shape[0]
+        keep = (v, t)
+    h = ctypes.c_void_p()
+    _check(N.load().pb_mesh_load(ctx.ptr, ctypes.c_void_p(vp), nv, ctypes.c_void_p(tp), nt, ctypes.byref(plan),
+                                 mem, ctypes.byref(h)))
+    del keep
+    return Mesh(h.value, ctx)
+
+
+def pb_near_build(ctx: Ctx, mesh: Mesh, kappa: float, stream=None) -> Near:
+    h = ctypes.c_void_p()
+    _check(N.load().pb_near_build(ctx.ptr, mesh.ptr, float(kappa), ctypes.byref(h), _stream(stream)))
+    return Near(h.value, mesh)
+
+
+def pb_op_apply(ctx: Ctx, mesh: Mesh, near: Near, op: int, kernel: int, prec: int, x: torch.Tensor,
+                y: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    if y is None:
+        y = torch.empty_like(x)
+    _check(N.load().pb_op_apply(ctx.ptr, mesh.ptr, near.ptr, op, kernel, prec, _dptr(x, "x"), _dptr(y, "y"),
+                                _stream(stream)))
+    return y
+
+
+def pb_system_apply(ctx: Ctx, mesh: Mesh, near: Near, params: Params, form, x: torch.Tensor, prec: int = PB_F64,
+                    alpha: float = 0.0, beta: float = 0.0, y: torch.Tensor | None = None, stream=None):
+    if y is None:
+        y = torch.empty_like(x)
+    p = params.c()
+    _check(N.load().pb_system_apply(ctx.ptr, mesh.ptr, near.ptr, ctypes.byref(p), _form(form), alpha, beta, prec,
+                                    _dptr(x, "x"), _dptr(y, "y"), _stream(stream)))
+    return y
+
+
+def pb_rhs_charges(ctx: Ctx, mesh: Mesh, xq: torch.Tensor, q: torch.Tensor, params: Params, form,
+                   alpha: float = 0.0, beta: float = 0.0, rhs: torch.Tensor | None = None, stream=None):
+    nv = mesh.info()["n_verts"]
+    if rhs is None:
+        rhs = torch.empty(2 * nv, dtype=torch.float64, device=xq.device)
+    p = params.c()
+    _check(N.load().pb_rhs_charges(ctx.ptr, mesh.ptr, _dptr(xq, "xq"), _dptr(q, "q"), q.numel(), ctypes.byref(p),
+                                   _form(form), alpha, beta, _dptr(rhs, "rhs"), _stream(stream)))
+    return rhs
+
+
+def solve_opts(tol=1e-6, max_it=500, restart=0, precision=PB_F64, inner_tol=1e-4, max_outer=20, alpha=0.0,
+               beta=0.0, pc_a=0.0, pc_b=0.0):
+    return N.pb_solve_opts(tol, max_it, restart, precision, inner_tol, max_outer, alpha, beta, pc_a, pc_b)
+
+
+def pb_solve(ctx: Ctx, mesh: Mesh, near: Near, params: Params, form, precond, rhs: torch.Tensor,
+             x: torch.Tensor | None = None, opts=None, stream=None, raise_on_noconv: bool = True):
+    """Returns (x, info dict)."""
+    if x is None:
+        x = torch.empty_like(rhs)
+    p = params.c()
+    o = opts if opts is not None else solve_opts()
+    info = N.pb_solve_info()
+    rc = N.load().pb_solve(ctx.ptr, mesh.ptr, near.ptr, ctypes.byref(p), _form(form), _prec(precond),
+                           ctypes.byref(o), _dptr(rhs, "rhs"), _dptr(x, "x"), ctypes.byref(info), _stream(stream))
+    d = {k: getattr(info, k) for k, _ in N.pb_solve_info._fields_}
+    if rc != PB_OK and (raise_on_noconv or rc != PB_ENOCONV):
+        _check(rc)
+    return x, d
+
+
+def pb_energy(ctx: Ctx, mesh: Mesh, x: torch.Tensor, form, xq: torch.Tensor, q: torch.Tensor, params: Params,
+              phi: torch.Tensor | None = None, stream=None):
+    """Returns (dG in paper units, dG in kcal/mol); phi (optional, n_q) receives phi_reac."""
+    p = params.c()
+    a, b = ctypes.c_double(), ctypes.c_double()
+    _check(N.load().pb_energy(ctx.ptr, mesh.ptr, _dptr(x, "x"), _form(form), _dptr(xq, "xq"), _dptr(q, "q"),
+                              q.numel(), ctypes.byref(p), _dptr(phi, "phi") if phi is not None else None,
+                              ctypes.byref(a), ctypes.byref(b), _stream(stream)))
+    return a.value, b.value
+
+
+def pb_solvation_energy(ctx: Ctx, verts: np.ndarray, tris: np.ndarray, xq: np.ndarray, q: np.ndarray,
+                        params: Params, form, precond, far_q: int = 6, n_ss: int = 4, opts=None, stream=None):
+    """Whole path from host arrays; returns (dG kcal/mol, info dict)."""
+    v = np.ascontiguousarray(verts, dtype=np.float64)
+    t = np.ascontiguousarray(tris, dtype=np.int32)
+    x = np.ascontiguousarray(xq, dtype=np.float64).reshape(-1, 3)
+    qq = np.ascontiguousarray(q, dtype=np.float64).reshape(-1)
+    p = params.c()
+    plan = N.pb_quad_plan(far_q, n_ss)
+    o = opts if opts is not None else solve_opts()
+    info = N.pb_solve_info()
+    out = ctypes.c_double()
+    _check(N.load().pb_solvation_energy(ctx.ptr, ctypes.c_void_p(v.ctypes.data), v.shape[0],
+                                        ctypes.c_void_p(t.ctypes.data), t.shape[0], ctypes.c_void_p(x.ctypes.data),
+                                        ctypes.c_void_p(qq.ctypes.data), qq.shape[0], ctypes.byref(p),
+                                        ctypes.byref(plan), _form(form), _prec(precond), ctypes.byref(o),
+                                        ctypes.byref(out), ctypes.byref(info), _stream(stream)))
+    return out.value, {k: getattr(info, k) for k, _ in N.pb_solve_info._fields_}

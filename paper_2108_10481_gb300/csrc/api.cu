@@ -1,0 +1,133 @@
+// Context, error reporting and device allocation helpers of the C ABI.
+#include <cudaTypedefs.h>
+#include <stdarg.h>
+#include <stdio.h>
+
+#include <atomic>
+
+#include "internal.h"
+
+namespace pb {
+
+static thread_local char g_err[1024] = "";
+static std::atomic<int64_t> g_launches{0};
+
+void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+int set_error(int code, const char* fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+
+int dev_alloc(void** p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) return PB_OK;
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        *p = nullptr;
+        cudaGetLastError();
+        return set_error(e == cudaErrorMemoryAllocation ? PB_ENOMEM : PB_ECUDA,
+                         "cudaMalloc(%zu bytes) failed: %s", bytes, cudaGetErrorString(e));
+    }
+    return PB_OK;
+}
+
+int ws_reserve(Workspace& w, size_t bytes) {
+    if (bytes <= w.bytes) return PB_OK;
+    ws_free(w);
+    PB_TRY(dev_alloc(&w.ptr, bytes));
+    w.bytes = bytes;
+    return PB_OK;
+}
+
+void ws_free(Workspace& w) {
+    if (w.ptr) cudaFree(w.ptr);
+    w.ptr = nullptr;
+    w.bytes = 0;
+}
+
+}  // namespace pb
+
+using namespace pb;
+
+extern "C" const char* pb_last_error(void) { return g_err; }
+
+extern "C" const char* pb_version(void) { return "pbbem 0.1 sm_103a"; }
+
+extern "C" int pb_init(int device, pb_ctx** out) {
+    if (!out) return set_error(PB_EINVAL, "pb_init: out is NULL");
+    *out = nullptr;
+    int n = 0;
+    PB_CUDA(cudaGetDeviceCount(&n));
+    if (device < 0 || device >= n) return set_error(PB_EINVAL, "pb_init: device %d of %d", device, n);
+    PB_CUDA(cudaSetDevice(device));
+    pb_ctx* c = new pb_ctx();
+    c->device = device;
+    cudaDeviceProp prop;
+    cudaError_t e = cudaGetDeviceProperties(&prop, device);
+    if (e != cudaSuccess) {
+        delete c;
+        return set_error(PB_ECUDA, "cudaGetDeviceProperties: %s", cudaGetErrorString(e));
+    }
+    c->num_sms = prop.multiProcessorCount;
+    c->cc_major = prop.major;
+    c->cc_minor = prop.minor;
+    cudaDriverEntryPointQueryResult q;
+    void* fn = nullptr;
+    e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !fn) {
+        delete c;
+        return set_error(PB_ECUDA, "cuTensorMapEncodeTiled entry point unavailable");
+    }
+    c->encode_tiled = fn;
+    *out = c;
+    return PB_OK;
+}
+
+static void reset_stats(pb_ctx* ctx) {
+    for (auto& st : ctx->stats) {
+        for (auto& e : st.events) {
+            cudaEventDestroy(e.first);
+            cudaEventDestroy(e.second);
+        }
+        st = KernelStats();
+    }
+}
+
+extern "C" int pb_free_ctx(pb_ctx* ctx) {
+    if (ctx) reset_stats(ctx);
+    delete ctx;
+    return PB_OK;
+}
+
+extern "C" int pb_profile(pb_ctx* ctx, int enable) {
+    if (!ctx) return set_error(PB_EINVAL, "pb_profile: NULL context");
+    reset_stats(ctx);
+    ctx->profile = enable ? 1 : 0;
+    return PB_OK;
+}
+
+extern "C" int pb_profile_read(pb_ctx* ctx, int kernel, int64_t* launches, double* total_ms, double* pairs,
+                               double* ops) {
+    if (!ctx || kernel < 0 || kernel > 2) return set_error(PB_EINVAL, "pb_profile_read: bad argument");
+    KernelStats& st = ctx->stats[kernel];
+    for (auto& e : st.events) {
+        float ms = 0.0f;
+        PB_CUDA(cudaEventSynchronize(e.second));
+        PB_CUDA(cudaEventElapsedTime(&ms, e.first, e.second));
+        st.ms += ms;
+        cudaEventDestroy(e.first);
+        cudaEventDestroy(e.second);
+    }
+    st.events.clear();
+    if (launches) *launches = st.launches;
+    if (total_ms) *total_ms = st.ms;
+    if (pairs) *pairs = st.pairs;
+    if (ops) *ops = st.ops;
+    return PB_OK;
+}
+
+extern "C" int64_t pb_launch_count(void) { return g_launches.load(); }

@@ -1,0 +1,643 @@
+// a3 + a4 + a5: application of a 2x2 block operator y = B x.
+//
+//   far field  : every target quadrature point x_p against every source point
+//                y_q (identical points skipped), Laplace and Yukawa fused:
+//                G_L = 1/(4 pi r), G_Y = e^{-kappa r}/(4 pi r),
+//                dG/dn_y = (x - y).n_y (1 + kappa r) e^{-kappa r}/(4 pi r^3)
+//                (paper eq. layer_potentials with its Green's functions);
+//   P1 maps    : coefficients -> source densities (a4 i), point sums -> test
+//                functions by a gather over each vertex's triangles (a4 ii);
+//   near field : the FP64 correction of pairs that share a vertex, as a
+//                vertex-pair CSR SpMV fused with the gather (a5).
+//
+// Source record (12 slots): y(3), s = w v/(4 pi), p = w u n_y/(4 pi) (3),
+// c = w curl u/(4 pi) (3), with w the point's rule weight times the area and
+// curl u = sum_a u_a (-e_a / (2|tau|)) on the source triangle. The FP32
+// record has 16 slots: the same 12 plus the low parts of y (split coordinates).
+//
+// Target accumulators of one kernel row:
+//   phi-row (V, K):  sum rinv (cVL + cVY e) s + rinv^3 (cKL + cKY e (1+kappa r)) (d.p)
+//   DT-row (D, T):   Tv = sum rinv^3 (cTL + cTY e(1+kappa r)) s d,   (T = -n_x.Tv)
+//                    Cv = sum rinv (cDL + cDY e) c,                   (D curl part)
+//                    Bv = sum rinv e p                               (D normal part x kappa^2 cDY)
+// with d = x - y, e = exp(-kappa r).
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "internal.h"
+
+namespace pb {
+
+constexpr int REC64 = 12;  // doubles per FP64 source record
+constexpr int REC32 = 16;  // floats per FP32 source record
+constexpr double INV4PI = 0.07957747154594767;  // 1 / (4 pi)
+
+// ------------------------------------------------------------ sources (a4 i)
+template <typename T, int REC>
+__global__ void k_sources(int64_t nt, int Q, Rule rule, const int32_t* __restrict__ tris,
+                          const double* __restrict__ tgeo, const double* __restrict__ pts64,
+                          const float* __restrict__ pts32, const float* __restrict__ pts32lo,
+                          const double* __restrict__ u, const double* __restrict__ v, int need_u,
+                          int need_v, T* __restrict__ rec) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    const double* g = tgeo + 16 * t;
+    int32_t i0 = tris[3 * t], i1 = tris[3 * t + 1], i2 = tris[3 * t + 2];
+    double ua[3] = {0, 0, 0}, va[3] = {0, 0, 0};
+    if (need_u) { ua[0] = u[i0]; ua[1] = u[i1]; ua[2] = u[i2]; }
+    if (need_v) { va[0] = v[i0]; va[1] = v[i1]; va[2] = v[i2]; }
+    double inv2a = -1.0 / (2.0 * g[3]);
+    double cu[3];
+    for (int k = 0; k < 3; ++k) cu[k] = inv2a * (ua[0] * g[4 + k] + ua[1] * g[7 + k] + ua[2] * g[10 + k]);
+    for (int q = 0; q < Q; ++q) {
+        int64_t i = t * Q + q;
+        double w = pts64[4 * i + 3] * INV4PI;
+        double uq = rule.l[q][0] * ua[0] + rule.l[q][1] * ua[1] + rule.l[q][2] * ua[2];
+        double vq = rule.l[q][0] * va[0] + rule.l[q][1] * va[1] + rule.l[q][2] * va[2];
+        T* r = rec + REC * i;
+        if (REC == REC64) {
+            for (int k = 0; k < 3; ++k) r[k] = (T)pts64[4 * i + k];
+        } else {
+            for (int k = 0; k < 3; ++k) {
+                r[k] = (T)pts32[4 * i + k];
+                r[12 + k] = (T)pts32lo[4 * i + k];
+            }
+            r[15] = (T)0;
+        }
+        r[3] = (T)(w * vq);
+        for (int k = 0; k < 3; ++k) {
+            r[4 + k] = (T)(w * uq * g[k]);
+            r[7 + k] = (T)(w * cu[k]);
+        }
+        if (REC == REC64) { r[10] = (T)0; r[11] = (T)0; }
+        else { r[10] = (T)0; r[11] = (T)0; }
+    }
+}
+
+// ------------------------------------------------------- FP64 pair kernel (a3)
+constexpr int TPB64 = 128;  // threads (= targets) per CTA
+constexpr int TS64 = 64;    // sources per shared-memory tile
+
+struct Coef {
+    double k[2][4];
+    double kappa;
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(TPB64) k_pair64(int64_t np, const double* __restrict__ pts64,
+                                                  const double* __restrict__ rec, Coef cf,
+                                                  int64_t chunk, double* __restrict__ part) {
+    constexpr int NACC = MODE == 0 ? 2 : 10;
+    __shared__ double sh[TS64 * REC64];
+    int64_t tgt = blockIdx.x * (int64_t)TPB64 + threadIdx.x;
+    int split = blockIdx.y;
+    int64_t j0 = split * chunk, j1 = min(np, j0 + chunk);
+    bool live = tgt < np;
+    double x0 = 0, x1 = 0, x2 = 0;
+    if (live) { x0 = pts64[4 * tgt]; x1 = pts64[4 * tgt + 1]; x2 = pts64[4 * tgt + 2]; }
+    double acc[NACC];
+    for (int a = 0; a < NACC; ++a) acc[a] = 0.0;
+    const double kap = cf.kappa;
+    for (int64_t jt = j0; jt < j1; jt += TS64) {
+        int nload = (int)min((int64_t)TS64, j1 - jt);
+        for (int k = threadIdx.x; k < TS64 * REC64; k += TPB64)
+            sh[k] = (k < nload * REC64) ? rec[jt * REC64 + k] : 0.0;
+        __syncthreads();
+        for (int j = 0; j < nload; ++j) {
+            const double* s = sh + REC64 * j;
+            double d0 = x0 - s[0], d1 = x1 - s[1], d2 = x2 - s[2];
+            double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+            if (!(r2 > 0.0)) continue;  // identical point (coincident triangle)
+            double rinv = 1.0 / sqrt(r2);
+            double r = r2 * rinv;
+            double e = exp(-kap * r);
+            double ek = e * (1.0 + kap * r);
+            double rinv3 = rinv * rinv * rinv;
+            double dp = d0 * s[4] + d1 * s[5] + d2 * s[6];
+            double rs = rinv * s[3], r3dp = rinv3 * dp;
+            acc[0] += (cf.k[0][0] + cf.k[0][1] * e) * rs + (cf.k[0][2] + cf.k[0][3] * ek) * r3dp;
+            if (MODE == 0) {
+                acc[1] += (cf.k[1][0] + cf.k[1][1] * e) * rs + (cf.k[1][2] + cf.k[1][3] * ek) * r3dp;
+            } else {
+                double ts = (cf.k[1][2] + cf.k[1][3] * ek) * rinv3 * s[3];
+                acc[1] += ts * d0; acc[2] += ts * d1; acc[3] += ts * d2;
+                double gc = (cf.k[1][0] + cf.k[1][1] * e) * rinv;
+                acc[4] += gc * s[7]; acc[5] += gc * s[8]; acc[6] += gc * s[9];
+                double gb = e * rinv;
+                acc[7] += gb * s[4]; acc[8] += gb * s[5]; acc[9] += gb * s[6];
+            }
+        }
+        __syncthreads();
+    }
+    if (live)
+        for (int a = 0; a < NACC; ++a) part[((int64_t)split * NACC + a) * np + tgt] = acc[a];
+}
+
+// ------------------------------------------------ FP32 pair kernel, TMA-fed (a3)
+constexpr int TPB32 = 256;  // threads per CTA
+constexpr int TGT32 = 2;    // targets per thread
+constexpr int TS32 = 128;   // sources per TMA tile (box rows)
+constexpr int ST32 = 3;     // pipeline stages
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t phase) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait: gives up after ~2^22 polls and records the failure
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase, int* status) {
+    for (int i = 0; i < (1 << 22); ++i)
+        if (mbar_try_wait(bar, phase)) return true;
+    atomicExch(status, PB_ETIMEOUT);
+    return false;
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int c0, int c1, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+        "[%4];" ::"r"(smem_u32(dst)),
+        "l"((uint64_t)map), "r"(c0), "r"(c1), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float ex2_approx(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+struct Coef32 {
+    float k[2][4];
+    float kappa;
+    float mk2;  // -kappa * log2(e)
+};
+
+template <int MODE, bool ACC>
+__global__ void __launch_bounds__(TPB32) k_pair32(const __grid_constant__ CUtensorMap tmap, int64_t np,
+                                                  const float* __restrict__ pts32,
+                                                  const float* __restrict__ pts32lo, Coef32 cf,
+                                                  int64_t chunk, void* __restrict__ part_out,
+                                                  int* __restrict__ status) {
+    constexpr int NACC = MODE == 0 ? 2 : 10;
+    __shared__ __align__(128) float sh[ST32][TS32 * REC32];
+    __shared__ __align__(8) uint64_t bar[ST32];
+    const int split = blockIdx.y;
+    const int64_t j0 = split * chunk;
+    const int64_t j1 = min(np, j0 + chunk);
+    const int ntiles = (int)((j1 - j0 + TS32 - 1) / TS32);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < ST32; ++s) mbar_init(&bar[s], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < ST32 && s < ntiles; ++s) {
+            mbar_expect_tx(&bar[s], TS32 * REC32 * sizeof(float));
+            tma_load_2d(sh[s], &tmap, 0, (int)(j0 + (int64_t)s * TS32), &bar[s]);
+        }
+    }
+
+    float x[TGT32][3], xl[TGT32][3];
+    int64_t tg[TGT32];
+    for (int t = 0; t < TGT32; ++t) {
+        tg[t] = blockIdx.x * (int64_t)(TPB32 * TGT32) + t * TPB32 + threadIdx.x;
+        int64_t i = tg[t] < np ? tg[t] : np - 1;
+        for (int k = 0; k < 3; ++k) {
+            x[t][k] = pts32[4 * i + k];
+            xl[t][k] = ACC ? pts32lo[4 * i + k] : 0.0f;
+        }
+    }
+    float acc[TGT32][NACC];
+    double accd[TGT32][ACC ? NACC : 1];
+    for (int t = 0; t < TGT32; ++t) {
+        for (int a = 0; a < NACC; ++a) acc[t][a] = 0.0f;
+        for (int a = 0; a < (ACC ? NACC : 1); ++a) accd[t][a] = 0.0;
+    }
+    const float kap = cf.kappa, mk2 = cf.mk2;
+    bool ok = true;
+    for (int it = 0; it < ntiles; ++it) {
+        const int st = it % ST32;
+        const uint32_t phase = (uint32_t)((it / ST32) & 1);
+        if (!mbar_wait(&bar[st], phase, status)) { ok = false; break; }
+        const float* tile = sh[st];
+#pragma unroll 2
+        for (int j = 0; j < TS32; ++j) {
+            const float4 s0 = *reinterpret_cast<const float4*>(tile + REC32 * j);
+            const float4 s1 = *reinterpret_cast<const float4*>(tile + REC32 * j + 4);
+            float4 s2 = make_float4(0.f, 0.f, 0.f, 0.f), s3 = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (MODE == 1) s2 = *reinterpret_cast<const float4*>(tile + REC32 * j + 8);
+            if (ACC) s3 = *reinterpret_cast<const float4*>(tile + REC32 * j + 12);
+#pragma unroll
+            for (int t = 0; t < TGT32; ++t) {
+                float d0 = x[t][0] - s0.x, d1 = x[t][1] - s0.y, d2 = x[t][2] - s0.z;
+                if (ACC) { d0 += xl[t][0] - s3.x; d1 += xl[t][1] - s3.y; d2 += xl[t][2] - s3.z; }
+                float r2 = fmaf(d0, d0, fmaf(d1, d1, d2 * d2));
+                float rinv = r2 > 0.0f ? rsqrt_approx(r2) : 0.0f;
+                float r = r2 * rinv;
+                float e = ex2_approx(r * mk2);
+                float ek = fmaf(e, kap * r, e);
+                float rinv3 = rinv * rinv * rinv;
+                float dp = fmaf(d0, s1.x, fmaf(d1, s1.y, d2 * s1.z));
+                float rs = rinv * s0.w, r3dp = rinv3 * dp;
+                acc[t][0] = fmaf(fmaf(cf.k[0][1], e, cf.k[0][0]), rs, acc[t][0]);
+                acc[t][0] = fmaf(fmaf(cf.k[0][3], ek, cf.k[0][2]), r3dp, acc[t][0]);
+                if (MODE == 0) {
+                    acc[t][1] = fmaf(fmaf(cf.k[1][1], e, cf.k[1][0]), rs, acc[t][1]);
+                    acc[t][1] = fmaf(fmaf(cf.k[1][3], ek, cf.k[1][2]), r3dp, acc[t][1]);
+                } else {
+                    float ts = fmaf(cf.k[1][3], ek, cf.k[1][2]) * (rinv3 * s0.w);
+                    acc[t][1] = fmaf(ts, d0, acc[t][1]);
+                    acc[t][2] = fmaf(ts, d1, acc[t][2]);
+                    acc[t][3] = fmaf(ts, d2, acc[t][3]);
+                    float gc = fmaf(cf.k[1][1], e, cf.k[1][0]) * rinv;
+                    acc[t][4] = fmaf(gc, s1.w, acc[t][4]);
+                    acc[t][5] = fmaf(gc, s2.x, acc[t][5]);
+                    acc[t][6] = fmaf(gc, s2.y, acc[t][6]);
+                    float gb = e * rinv;
+                    acc[t][7] = fmaf(gb, s1.x, acc[t][7]);
+                    acc[t][8] = fmaf(gb, s1.y, acc[t][8]);
+                    acc[t][9] = fmaf(gb, s1.z, acc[t][9]);
+                }
+            }
+        }
+        if (ACC) {
+            for (int t = 0; t < TGT32; ++t)
+                for (int a = 0; a < NACC; ++a) {
+                    accd[t][a] += (double)acc[t][a];
+                    acc[t][a] = 0.0f;
+                }
+        }
+        __syncthreads();  // every thread is done with this stage
+        if (threadIdx.x == 0 && it + ST32 < ntiles) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_expect_tx(&bar[st], TS32 * REC32 * sizeof(float));
+            tma_load_2d(sh[st], &tmap, 0, (int)(j0 + (int64_t)(it + ST32) * TS32), &bar[st]);
+        }
+    }
+    if (!ok) {
+        // drain: wait (bounded) for the copies this CTA issued, then leave
+        if (threadIdx.x == 0)
+            for (int s = 0; s < ST32; ++s) {
+                for (int i = 0; i < (1 << 20); ++i)
+                    if (mbar_try_wait(&bar[s], 0) || mbar_try_wait(&bar[s], 1)) break;
+            }
+        __syncthreads();
+        return;
+    }
+    for (int t = 0; t < TGT32; ++t) {
+        if (tg[t] >= np) continue;
+        for (int a = 0; a < NACC; ++a) {
+            int64_t o = ((int64_t)split * NACC + a) * np + tg[t];
+            if (ACC) static_cast<double*>(part_out)[o] = accd[t][a];
+            else static_cast<float*>(part_out)[o] = acc[t][a];
+        }
+    }
+}
+
+// --------------------------------------------- point sums -> test functions (a4 ii)
+template <typename P>
+__global__ void k_tri_reduce(int64_t nt, int64_t np, Rule rule, int nsplit, int mode, FarPlan fp,
+                             const double* __restrict__ tgeo, const double* __restrict__ pts64,
+                             const P* __restrict__ part, double* __restrict__ tri_out) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    const int Q = rule.Q;
+    const int NACC = mode == 0 ? 2 : 10;
+    const double* g = tgeo + 16 * t;
+    double out[2][3] = {{0, 0, 0}, {0, 0, 0}};
+    double ctot[3] = {0, 0, 0};
+    for (int q = 0; q < Q; ++q) {
+        int64_t i = t * Q + q;
+        double w = pts64[4 * i + 3];
+        double a[10];
+        for (int k = 0; k < NACC; ++k) {
+            double s = 0.0;
+            for (int sp = 0; sp < nsplit; ++sp) s += (double)part[((int64_t)sp * NACC + k) * np + i];
+            a[k] = s;
+        }
+        // kernel row 0: phi-row
+        for (int b = 0; b < 3; ++b) out[0][b] += w * rule.l[q][b] * a[0];
+        if (mode == 0) {
+            for (int b = 0; b < 3; ++b) out[1][b] += w * rule.l[q][b] * a[1];
+        } else {
+            double nT = g[0] * a[1] + g[1] * a[2] + g[2] * a[3];
+            double nB = g[0] * a[7] + g[1] * a[8] + g[2] * a[9];
+            double sc = -nT + fp.kappa * fp.kappa * fp.k[1][1] * nB;
+            for (int b = 0; b < 3; ++b) out[1][b] += w * rule.l[q][b] * sc;
+            for (int k = 0; k < 3; ++k) ctot[k] += w * a[4 + k];
+        }
+    }
+    if (mode == 1) {
+        double inv2a = -1.0 / (2.0 * g[3]);
+        for (int b = 0; b < 3; ++b) {
+            const double* e = g + 4 + 3 * b;
+            out[1][b] += inv2a * (e[0] * ctot[0] + e[1] * ctot[1] + e[2] * ctot[2]);
+        }
+    }
+    double* o = tri_out + 6 * t;
+    for (int r = 0; r < 2; ++r)
+        for (int b = 0; b < 3; ++b) o[3 * fp.out_row[r] + b] = out[r][b];
+}
+
+// ------------------------------------- gather + near-field SpMV (a4 ii + a5)
+// 8 lanes per vertex; lane-strided sums reduced by shuffles in a fixed order.
+template <typename V>
+__global__ void k_gather_spmv(int64_t nv, const int32_t* __restrict__ v2t_ptr, const int32_t* __restrict__ v2t,
+                              const double* __restrict__ tri, int use_far, const int32_t* __restrict__ row_ptr,
+                              const int32_t* __restrict__ col, const V* __restrict__ comb, int64_t nnz,
+                              const double* __restrict__ x, double* __restrict__ y) {
+    int64_t gid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t i = gid >> 3;
+    int lane = threadIdx.x & 7;
+    double y0 = 0.0, y1 = 0.0;
+    if (i < nv) {
+        if (use_far)
+            for (int32_t k = v2t_ptr[i] + lane; k < v2t_ptr[i + 1]; k += 8) {
+                int32_t ta = v2t[k];
+                int64_t t = ta / 3;
+                int a = ta - 3 * (int)t;
+                y0 += tri[6 * t + a];
+                y1 += tri[6 * t + 3 + a];
+            }
+        const double* u = x;
+        const double* v = x + nv;
+        for (int32_t k = row_ptr[i] + lane; k < row_ptr[i + 1]; k += 8) {
+            double uc = u[col[k]], vc = v[col[k]];
+            y0 += (double)comb[k] * uc + (double)comb[nnz + k] * vc;
+            y1 += (double)comb[2 * nnz + k] * uc + (double)comb[3 * nnz + k] * vc;
+        }
+    }
+    for (int o = 4; o > 0; o >>= 1) {
+        y0 += __shfl_xor_sync(0xffffffffu, y0, o, 8);
+        y1 += __shfl_xor_sync(0xffffffffu, y1, o, 8);
+    }
+    if (i < nv && lane == 0) {
+        y[i] = y0;
+        y[nv + i] = y1;
+    }
+}
+
+// ------------------------------------------------------------ near combine
+__global__ void k_combine(int64_t nnz, const double* __restrict__ val, const int32_t* __restrict__ tpos,
+                          BlockOp B, double* __restrict__ c64, float* __restrict__ c32) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= nnz) return;
+    int64_t et = tpos[e];
+    double vals[O_N];
+    vals[O_M] = val[N_M * nnz + e];
+    vals[O_VL] = val[N_VL * nnz + e];
+    vals[O_KL] = val[N_KL * nnz + e];
+    vals[O_TL] = val[N_KL * nnz + et];
+    vals[O_DL] = val[N_DL * nnz + e];
+    vals[O_VY] = val[N_VY * nnz + e];
+    vals[O_KY] = val[N_KY * nnz + e];
+    vals[O_TY] = val[N_KY * nnz + et];
+    vals[O_DY] = val[N_DY * nnz + e];
+    for (int r = 0; r < 2; ++r)
+        for (int c = 0; c < 2; ++c) {
+            double s = 0.0;
+            for (int o = 0; o < O_N; ++o) s += B.c[r][c][o] * vals[o];
+            c64[(2 * r + c) * nnz + e] = s;
+            c32[(2 * r + c) * nnz + e] = (float)s;
+        }
+}
+
+int combine_near(const pb_mesh* m, const pb_near* nf, const BlockOp& B, double* c64, float* c32,
+                 cudaStream_t s) {
+    k_combine<<<(unsigned)((m->nnz + 255) / 256), 256, 0, s>>>(m->nnz, nf->val, m->tpos, B, c64, c32); ::pb::count_launch();
+    PB_CUDA(cudaGetLastError());
+    return PB_OK;
+}
+
+// ------------------------------------------------------------- far plan
+int make_far_plan(const BlockOp& B, double kappa, FarPlan* fp) {
+    int kind[2];  // 0: phi-row, 1: DT-row
+    double k[2][4];
+    for (int R = 0; R < 2; ++R) {
+        const double* cu = B.c[R][0];
+        const double* cv = B.c[R][1];
+        if (cu[O_VL] != 0 || cu[O_VY] != 0 || cu[O_TL] != 0 || cu[O_TY] != 0 || cv[O_KL] != 0 ||
+            cv[O_KY] != 0 || cv[O_DL] != 0 || cv[O_DY] != 0)
+            return set_error(PB_EINVAL, "block operator acts with V/T on u or K/D on v");
+        bool phi = cv[O_VL] != 0 || cv[O_VY] != 0 || cu[O_KL] != 0 || cu[O_KY] != 0;
+        bool dt = cu[O_DL] != 0 || cu[O_DY] != 0 || cv[O_TL] != 0 || cv[O_TY] != 0;
+        if (phi && dt) return set_error(PB_EINVAL, "a block row mixes V/K with D/T terms");
+        kind[R] = dt ? 1 : 0;
+        if (dt) { k[R][0] = cu[O_DL]; k[R][1] = cu[O_DY]; k[R][2] = cv[O_TL]; k[R][3] = cv[O_TY]; }
+        else { k[R][0] = cv[O_VL]; k[R][1] = cv[O_VY]; k[R][2] = cu[O_KL]; k[R][3] = cu[O_KY]; }
+    }
+    if (kind[0] == 1 && kind[1] == 1) return set_error(PB_EINVAL, "two D/T rows are not supported");
+    fp->kappa = kappa;
+    fp->any = false;
+    for (int R = 0; R < 2; ++R)
+        for (int j = 0; j < 4; ++j) fp->any = fp->any || k[R][j] != 0.0;
+    if (kind[0] == 0 && kind[1] == 0) {
+        fp->mode = 0;
+        fp->out_row[0] = 0;
+        fp->out_row[1] = 1;
+        for (int j = 0; j < 4; ++j) { fp->k[0][j] = k[0][j]; fp->k[1][j] = k[1][j]; }
+    } else {
+        int rphi = kind[0] == 0 ? 0 : 1, rdt = 1 - rphi;
+        fp->mode = 1;
+        fp->out_row[0] = rphi;
+        fp->out_row[1] = rdt;
+        for (int j = 0; j < 4; ++j) { fp->k[0][j] = k[rphi][j]; fp->k[1][j] = k[rdt][j]; }
+    }
+    return PB_OK;
+}
+
+// split count: fill the GPU in whole waves (see the layout notes in the design)
+static int choose_splits(int64_t np, int tpc, int tile, int slots) {
+    int64_t nb = (np + tpc - 1) / tpc;
+    int64_t ntiles = (np + tile - 1) / tile;
+    int best = 1;
+    double best_cost = 1e300;
+    for (int S = 1; S <= 32; ++S) {
+        if (S > ntiles) break;
+        int64_t ctas = nb * S;
+        int64_t waves = (ctas + slots - 1) / slots;
+        int64_t per = (ntiles + S - 1) / S;
+        double cost = (double)waves * (double)per * (1.0 + 0.01 * S);
+        if (cost < best_cost) { best_cost = cost; best = S; }
+    }
+    return best;
+}
+
+static int occupancy_slots(const pb_mesh* m, const void* kern, int threads) {
+    int per_sm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0) != cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    cudaGetLastError();
+    return per_sm * m->ctx->num_sms;
+}
+
+static int make_tmap(const pb_mesh* m, const float* rec, CUtensorMap* map) {
+    auto enc = (PFN_cuTensorMapEncodeTiled_v12000)m->ctx->encode_tiled;
+    cuuint64_t dims[2] = {(cuuint64_t)REC32, (cuuint64_t)m->np};
+    cuuint64_t strides[1] = {(cuuint64_t)REC32 * sizeof(float)};
+    cuuint32_t box[2] = {(cuuint32_t)REC32, (cuuint32_t)TS32};
+    cuuint32_t es[2] = {1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)rec, dims, strides, box, es,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return set_error(PB_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return PB_OK;
+}
+
+// FP32-pipe operations per point pair by the formula count of the kernels
+// above (FADD, FMUL and FFMA each one; the two MUFU operations not counted):
+// shared geometry 17, a phi-row 4, a DT-row 15, split coordinates +6.
+constexpr double OPS_VK2 = 25.0, OPS_VKDT = 36.0, OPS_SPLIT = 6.0;
+
+// CUDA events around one launch on its stream, when the context profiles.
+struct Timer {
+    pb_ctx* ctx;
+    int id;
+    cudaStream_t s;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    double pairs, ops;
+    Timer(pb_ctx* c, int k, cudaStream_t st, double p, double o) : ctx(c), id(k), s(st), pairs(p), ops(o) {
+        if (ctx->profile && cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess)
+            cudaEventRecord(e0, s);
+    }
+    void stop() {
+        if (!e1) return;
+        cudaEventRecord(e1, s);
+        KernelStats& st = ctx->stats[id];
+        st.events.push_back({e0, e1});
+        st.launches += 1;
+        st.pairs += pairs;
+        st.ops += pairs * ops;
+        e0 = e1 = nullptr;
+    }
+};
+
+// workspace layout helpers
+static size_t part_bytes(const pb_mesh* m) { return sizeof(double) * 32 * 10 * (size_t)m->np; }
+
+int apply_blockop(const pb_mesh* m, const pb_near* nf, const BlockOp& B, int prec, const double* x, double* y,
+                  cudaStream_t s) {
+    if (prec != PB_F64 && prec != PB_F32 && prec != PB_F32_ACCURATE)
+        return set_error(PB_EINVAL, "unknown precision %d", prec);
+    FarPlan fp;
+    PB_TRY(make_far_plan(B, nf->kappa, &fp));
+    const int64_t nv = m->nv, nt = m->nt, np = m->np;
+    PB_TRY(ws_reserve(const_cast<pb_mesh*>(m)->ws_src, sizeof(double) * REC64 * np + 256));
+    PB_TRY(ws_reserve(const_cast<pb_mesh*>(m)->ws_part, part_bytes(m) + 256));
+    PB_TRY(ws_reserve(const_cast<pb_mesh*>(m)->ws_tri, sizeof(double) * 6 * nt));
+    PB_TRY(ws_reserve(const_cast<pb_mesh*>(m)->ws_comb, (sizeof(double) + sizeof(float)) * 4 * m->nnz));
+    double* tri = (double*)m->ws_tri.ptr;
+    int* status = m->status;
+    double* c64 = (double*)m->ws_comb.ptr;
+    float* c32 = (float*)(c64 + 4 * m->nnz);
+    PB_TRY(combine_near(m, nf, B, c64, c32, s));
+
+    if (fp.any) {
+        bool need_u = false, need_v = false;
+        for (int R = 0; R < 2; ++R)
+            for (int o = 1; o < O_N; ++o) {
+                need_u = need_u || B.c[R][0][o] != 0.0;
+                need_v = need_v || B.c[R][1][o] != 0.0;
+            }
+        const int nacc = fp.mode == 0 ? 2 : 10;
+        Rule rule = mesh_rule(m);
+        unsigned tb = (unsigned)((nt + 127) / 128);
+        if (prec == PB_F64) {
+            double* rec = (double*)m->ws_src.ptr;
+            k_sources<double, REC64><<<tb, 128, 0, s>>>(nt, m->Q, rule, m->tris, m->tgeo, m->pts64, m->pts32,
+                                                        m->pts32lo, x, x + nv, need_u, need_v, rec); ::pb::count_launch();
+            const void* kern = fp.mode == 0 ? (const void*)k_pair64<0> : (const void*)k_pair64<1>;
+            int S = choose_splits(np, TPB64, TS64, occupancy_slots(m, kern, TPB64));
+            int64_t chunk = ((np + S - 1) / S + TS64 - 1) / TS64 * TS64;
+            S = (int)((np + chunk - 1) / chunk);
+            Coef cf;
+            for (int R = 0; R < 2; ++R)
+                for (int j = 0; j < 4; ++j) cf.k[R][j] = fp.k[R][j];
+            cf.kappa = fp.kappa;
+            dim3 grid((unsigned)((np + TPB64 - 1) / TPB64), (unsigned)S);
+            double* part = (double*)m->ws_part.ptr;
+            Timer tm(m->ctx, PB_KERNEL_PAIR64, s, (double)np * (double)np, fp.mode == 0 ? OPS_VK2 : OPS_VKDT);
+            if (fp.mode == 0) k_pair64<0><<<grid, TPB64, 0, s>>>(np, m->pts64, rec, cf, chunk, part);
+            else k_pair64<1><<<grid, TPB64, 0, s>>>(np, m->pts64, rec, cf, chunk, part);
+            ::pb::count_launch();
+            tm.stop();
+            k_tri_reduce<double><<<tb, 128, 0, s>>>(nt, np, rule, S, fp.mode, fp, m->tgeo, m->pts64, part, tri);
+            ::pb::count_launch();
+        } else {
+            float* rec = (float*)m->ws_src.ptr;
+            k_sources<float, REC32><<<tb, 128, 0, s>>>(nt, m->Q, rule, m->tris, m->tgeo, m->pts64, m->pts32,
+                                                       m->pts32lo, x, x + nv, need_u, need_v, rec);
+            ::pb::count_launch();
+            CUtensorMap map;
+            PB_TRY(make_tmap(m, rec, &map));
+            bool acc = prec == PB_F32_ACCURATE;
+            const void* kern = fp.mode == 0 ? (acc ? (const void*)k_pair32<0, true> : (const void*)k_pair32<0, false>)
+                                            : (acc ? (const void*)k_pair32<1, true> : (const void*)k_pair32<1, false>);
+            int S = choose_splits(np, TPB32 * TGT32, TS32, occupancy_slots(m, kern, TPB32));
+            int64_t chunk = ((np + S - 1) / S + TS32 - 1) / TS32 * TS32;
+            S = (int)((np + chunk - 1) / chunk);
+            Coef32 cf;
+            for (int R = 0; R < 2; ++R)
+                for (int j = 0; j < 4; ++j) cf.k[R][j] = (float)fp.k[R][j];
+            cf.kappa = (float)fp.kappa;
+            cf.mk2 = (float)(-fp.kappa * 1.4426950408889634);
+            dim3 grid((unsigned)((np + TPB32 * TGT32 - 1) / (TPB32 * TGT32)), (unsigned)S);
+            void* part = m->ws_part.ptr;
+            double ops = (fp.mode == 0 ? OPS_VK2 : OPS_VKDT) + (acc ? OPS_SPLIT : 0.0);
+            Timer tm(m->ctx, acc ? PB_KERNEL_PAIR32_ACCURATE : PB_KERNEL_PAIR32, s, (double)np * (double)np, ops);
+            if (fp.mode == 0) {
+                if (acc) k_pair32<0, true><<<grid, TPB32, 0, s>>>(map, np, m->pts32, m->pts32lo, cf, chunk, part, status);
+                else k_pair32<0, false><<<grid, TPB32, 0, s>>>(map, np, m->pts32, m->pts32lo, cf, chunk, part, status);
+            } else {
+                if (acc) k_pair32<1, true><<<grid, TPB32, 0, s>>>(map, np, m->pts32, m->pts32lo, cf, chunk, part, status);
+                else k_pair32<1, false><<<grid, TPB32, 0, s>>>(map, np, m->pts32, m->pts32lo, cf, chunk, part, status);
+            }
+            ::pb::count_launch();
+            tm.stop();
+            if (acc)
+                k_tri_reduce<double><<<tb, 128, 0, s>>>(nt, np, rule, S, fp.mode, fp, m->tgeo, m->pts64,
+                                                        (const double*)part, tri);
+            else
+                k_tri_reduce<float><<<tb, 128, 0, s>>>(nt, np, rule, S, fp.mode, fp, m->tgeo, m->pts64,
+                                                       (const float*)part, tri);
+            ::pb::count_launch();
+        }
+        (void)nacc;
+    }
+    unsigned gb = (unsigned)((nv * 8 + 255) / 256);
+    if (prec == PB_F32)
+        k_gather_spmv<float><<<gb, 256, 0, s>>>(nv, m->v2t_ptr, m->v2t, tri, fp.any ? 1 : 0, m->row_ptr, m->col,
+                                                c32, m->nnz, x, y);
+    else
+        k_gather_spmv<double><<<gb, 256, 0, s>>>(nv, m->v2t_ptr, m->v2t, tri, fp.any ? 1 : 0, m->row_ptr, m->col,
+                                                 c64, m->nnz, x, y);
+    ::pb::count_launch();
+    PB_CUDA(cudaGetLastError());
+    return PB_OK;
+}
+
+int far_splits(const pb_mesh* m, int tpc, int ctas_per_sm) {
+    return choose_splits(m->np, tpc, TS32, ctas_per_sm * m->ctx->num_sms);
+}
+
+}  // namespace pb

@@ -1,0 +1,165 @@
+// Internal declarations of the pbbem library (not part of the C ABI).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "pbbem.h"
+
+namespace pb {
+
+// ---------------------------------------------------------------- errors
+int set_error(int code, const char* fmt, ...);
+#define PB_CUDA(call)                                                                        \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return ::pb::set_error(PB_ECUDA, "%s failed: %s (%s:%d)", #call,                 \
+                                   cudaGetErrorString(e_), __FILE__, __LINE__);              \
+    } while (0)
+#define PB_TRY(expr)            \
+    do {                        \
+        int rc_ = (expr);       \
+        if (rc_ != PB_OK) return rc_; \
+    } while (0)
+
+// ------------------------------------------------------- operator indices
+// Operators stored by the near field, in this order (T is K transposed).
+enum Op { O_M = 0, O_VL, O_KL, O_TL, O_DL, O_VY, O_KY, O_TY, O_DY, O_N };
+// Near-field value arrays as stored (T is read through the transpose map).
+enum NearVal { N_VL = 0, N_KL, N_DL, N_VY, N_KY, N_DY, N_M, N_VALS };
+
+// A 2x2 block operator: block (r, c) = sum_o coef[r][c][o] * A_o, acting on
+// x = [u; v] (c = 0: u, the Dirichlet trace; c = 1: v, the Neumann trace).
+struct BlockOp {
+    double c[2][2][O_N];
+};
+
+// Far-field work of one block operator, split into the two kernel row kinds:
+//   phi-row: V (on v) and K (on u) terms, tested with lambda_a;
+//   DT-row:  D (on u) and T (on v) terms (hypersingular and adjoint double layer).
+struct FarPlan {
+    int mode;          // 0: both rows phi-rows (VK2); 1: one phi-row + one DT-row (VKDT)
+    int out_row[2];    // output block of kernel row 0 and row 1
+    // kernel row 0 (phi-row): cVL, cVY, cKL, cKY
+    // kernel row 1: phi-row (cVL, cVY, cKL, cKY) or DT-row (cDL, cDY, cTL, cTY)
+    double k[2][4];
+    double kappa;
+    bool any;          // any far-field term at all
+};
+
+// The regular triangle rule, passed to kernels by value.
+struct Rule {
+    double l[6][3];
+    double w[6];
+    int Q;
+};
+
+// ------------------------------------------------------------- handles
+struct Workspace {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace pb
+
+namespace pb {
+struct KernelStats {
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> events;  // unresolved launches
+    int64_t launches = 0;
+    double ms = 0.0, pairs = 0.0, ops = 0.0;
+};
+void count_launch(int n = 1);
+}  // namespace pb
+
+struct pb_ctx {
+    int profile = 0;
+    pb::KernelStats stats[3];
+    int device = 0;
+    int num_sms = 0;
+    int cc_major = 0, cc_minor = 0;
+    void* encode_tiled = nullptr;  // cuTensorMapEncodeTiled entry point
+};
+
+struct pb_mesh {
+    pb_ctx* ctx = nullptr;
+    int64_t nv = 0, nt = 0, np = 0;
+    int Q = 0, n_ss = 0;
+    double rule_l[6][3];
+    double rule_w[6];
+    // device arrays
+    double* verts = nullptr;    // nv x 3
+    int32_t* tris = nullptr;    // nt x 3
+    double* tgeo = nullptr;     // nt x 16: n(3), area, e0(3), e1(3), e2(3), pad(3)
+    double* pts64 = nullptr;    // np x 4: x, y, z, w (rule weight x area)
+    float* pts32 = nullptr;     // np x 4: x, y, z, w rounded to float
+    float* pts32lo = nullptr;   // np x 4: x - float(x), ..., 0
+    int32_t* v2t_ptr = nullptr; // nv + 1
+    int32_t* v2t = nullptr;     // 3 nt entries: tri * 3 + local vertex
+    // adjacent triangle pairs
+    int64_t npairs = 0;
+    int4* pairs = nullptr;      // (ti, tj, kind, perms): kind 0 coincident, 1 edge, 2 vertex
+    // vertex-pair pattern of the near field (symmetric)
+    int64_t nnz = 0;
+    int32_t* row_ptr = nullptr; // nv + 1
+    int32_t* col = nullptr;     // nnz
+    int32_t* tpos = nullptr;    // nnz: index of the transposed entry
+    int32_t* diag_pos = nullptr;// nv
+    int32_t* contrib_ptr = nullptr; // nnz + 1
+    int32_t* contrib = nullptr;     // pair * 9 + a * 3 + b
+    int64_t ncontrib = 0;
+    int* status = nullptr;          // device status word of bounded waits (0 = fine)
+    // workspaces (grown on demand)
+    pb::Workspace ws_src, ws_part, ws_tri, ws_vec, ws_comb;
+    size_t device_bytes = 0;
+};
+
+struct pb_near {
+    const pb_mesh* mesh = nullptr;
+    double kappa = 0.0;
+    double* val = nullptr;   // N_VALS x nnz (near part = regularised - far rule; M exact)
+    double* diag = nullptr;  // N_VALS x nv: full operator diagonals
+};
+
+namespace pb {
+
+inline Rule mesh_rule(const pb_mesh* m) {
+    Rule r;
+    for (int q = 0; q < 6; ++q) {
+        for (int c = 0; c < 3; ++c) r.l[q][c] = m->rule_l[q][c];
+        r.w[q] = m->rule_w[q];
+    }
+    r.Q = m->Q;
+    return r;
+}
+
+// device allocation helpers (track bytes on the mesh)
+int dev_alloc(void** p, size_t bytes);
+int ws_reserve(Workspace& w, size_t bytes);
+void ws_free(Workspace& w);
+
+// formulation -> block operators (system, Calderon operators, RHS scaling)
+int system_blockop(const pb_params* prm, int form, double alpha, double beta, BlockOp* out);
+int calderon_blockop(const pb_params* prm, int form, int which /*0 int, 1 ext*/, BlockOp* out);
+bool form_is_exterior(int form);
+int make_far_plan(const BlockOp& B, double kappa, FarPlan* out);
+
+// a3 + a4 + a5: y = B x (x, y device, 2 nv doubles)
+int apply_blockop(const pb_mesh* m, const pb_near* nf, const BlockOp& B, int prec, const double* x,
+                  double* y, cudaStream_t s);
+// near values combined for a block operator (FP64 and FP32 copies) and diagonals
+int combine_near(const pb_mesh* m, const pb_near* nf, const BlockOp& B, double* comb64, float* comb32,
+                 cudaStream_t s);
+
+// far-field split count for the pair kernels
+int far_splits(const pb_mesh* m, int targets_per_cta, int ctas_per_sm);
+
+// Chebyshev solve with the mass matrix: y = M^-1 x on both halves of a 2 nv vector
+int mass_solve(const pb_mesh* m, const pb_near* nf, const double* x, double* y, double* work,
+               int iters, cudaStream_t s);
+
+}  // namespace pb

@@ -1,0 +1,338 @@
+// a2: FP64 near field. For every ordered pair of triangles sharing a vertex,
+// the local 3x3 Galerkin blocks of V, K, D (Laplace and Yukawa) by a
+// regularised [0,1]^4 rule (maps in the manner of Sauter and Schwab, with a
+// Gauss-Legendre product rule), minus the same blocks by the far rule that the
+// pair kernel applies to every pair, summed into the vertex-pair CSR. The full
+// (regularised) diagonals are kept for the block-diagonal preconditioner.
+//
+// Operators (paper eq. layer_potentials, weak forms on P1):
+//   V_ab = int int l_a(x) G(x,y) l_b(y)       K_ab = int int l_a(x) dG/dn_y l_b(y)
+//   D_ab = int int G [curl l_a . curl l_b + kappa^2 n_x.n_y l_a l_b]  (hypersingular,
+//          integrated by parts; curl l_a = -e_a / (2|tau|), e_a the edge opposite a)
+// with G_int = 1/(4 pi r), G_ext = exp(-kappa r)/(4 pi r).
+#include <cmath>
+
+#include "internal.h"
+
+namespace pb {
+
+struct Gauss {
+    double x[12];
+    double w[12];
+    int n;
+};
+
+// Gauss-Legendre nodes on [0,1] by Newton's method on P_n (three-term
+// recurrence for P_n, derivative from P_n and P_{n-1}).
+static Gauss gauss01(int n) {
+    Gauss g;
+    g.n = n;
+    for (int i = 0; i < n; ++i) {
+        double x = cos(M_PI * (i + 0.75) / (n + 0.5));
+        double dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = x;
+            for (int k = 2; k <= n; ++k) {
+                double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+                p0 = p1;
+                p1 = p2;
+            }
+            if (n == 1) { p1 = x; p0 = 1.0; }
+            dp = n * (x * p1 - p0) / (x * x - 1.0);
+            double dx = p1 / dp;
+            x -= dx;
+            if (fabs(dx) < 1e-16) break;
+        }
+        // recompute the derivative at the converged node for the weight
+        double p0 = 1.0, p1 = x;
+        for (int k = 2; k <= n; ++k) {
+            double p2 = ((2.0 * k - 1.0) * x * p1 - (k - 1.0) * p0) / k;
+            p0 = p1;
+            p1 = p2;
+        }
+        if (n == 1) { p1 = x; p0 = 1.0; }
+        dp = n * (x * p1 - p0) / (x * x - 1.0);
+        double w = 2.0 / ((1.0 - x * x) * dp * dp);
+        g.x[i] = 0.5 * (1.0 - x);  // ascending on [0,1]
+        g.w[i] = 0.5 * w;
+    }
+    return g;
+}
+
+// One regularised cube point -> reference points (sx,tx) in tau and (sy,ty)
+// in sigma on {0 <= t <= s <= 1}, returning the region Jacobian.
+// kind 0: coincident (6 regions), 1: common edge t = 0 (6), 2: common vertex (0,0) (2).
+__device__ __forceinline__ double ss_map(int kind, int reg, double xi, double e1, double e2, double e3,
+                                         double& sx, double& tx, double& sy, double& ty) {
+    double a0, a1, b0, b1, jac;
+    int base = reg;
+    bool swap = false;
+    if (kind == 2) {
+        swap = reg == 1;
+        a0 = xi; a1 = xi * e1;
+        b0 = xi * e2; b1 = xi * e2 * e3;
+        jac = xi * xi * xi * e2;
+    } else {
+        if (reg >= 3) { base = reg - 3; swap = true; }
+        if (kind == 0) {
+            jac = xi * xi * xi * e1 * e1 * e2;
+            if (base == 0) {
+                a0 = xi; a1 = xi * (1.0 - e1 + e1 * e2);
+                b0 = xi * (1.0 - e1 * e2 * e3); b1 = xi * (1.0 - e1);
+            } else if (base == 1) {
+                a0 = xi; a1 = xi * e1 * (1.0 - e2 + e2 * e3);
+                b0 = xi * (1.0 - e1 * e2); b1 = xi * e1 * (1.0 - e2);
+            } else {
+                a0 = xi * (1.0 - e1 * e2 * e3); a1 = xi * e1 * (1.0 - e2 * e3);
+                b0 = xi; b1 = xi * e1 * (1.0 - e2);
+            }
+        } else {
+            // x^ = (s1, s1 w1), y^ = (s2, s2 w2), s1 = xi, s2 = xi (1 - h); the
+            // largest of (h, w1, w2) is e1 and the other two are e1 times (e2, e3)
+            double h, w1, w2;
+            if (base == 0) { h = e1; w1 = e1 * e2; w2 = e1 * e3; }
+            else if (base == 1) { w1 = e1; h = e1 * e2; w2 = e1 * e3; }
+            else { w2 = e1; h = e1 * e2; w1 = e1 * e3; }
+            double s2 = xi * (1.0 - h);
+            a0 = xi; a1 = xi * w1;
+            b0 = s2; b1 = s2 * w2;
+            jac = xi * xi * xi * (1.0 - h) * e1 * e1;
+        }
+    }
+    if (swap) { sx = b0; tx = b1; sy = a0; ty = a1; }
+    else { sx = a0; tx = a1; sy = b0; ty = b1; }
+    return jac;
+}
+
+struct PairGeom {
+    double p[3][3];  // original vertex order
+    double n[3];
+    double area;
+};
+
+__device__ __forceinline__ void load_tri(const double* verts, const int32_t* tris, const double* tgeo,
+                                         int t, PairGeom& g) {
+    for (int a = 0; a < 3; ++a)
+        for (int k = 0; k < 3; ++k) g.p[a][k] = verts[3 * (int64_t)tris[3 * (int64_t)t + a] + k];
+    for (int k = 0; k < 3; ++k) g.n[k] = tgeo[16 * (int64_t)t + k];
+    g.area = tgeo[16 * (int64_t)t + 3];
+}
+
+// reference (s,t) on the reordered triangle -> point and original barycentrics
+__device__ __forceinline__ void ref_to_phys(const PairGeom& g, int perm, double s, double t, double* x,
+                                            double* lam) {
+    double mu[3] = {1.0 - s, s - t, t};
+    lam[perm & 3] = mu[0];
+    lam[(perm >> 2) & 3] = mu[1];
+    lam[(perm >> 4) & 3] = mu[2];
+    for (int k = 0; k < 3; ++k) x[k] = lam[0] * g.p[0][k] + lam[1] * g.p[1][k] + lam[2] * g.p[2][k];
+}
+
+// 38 accumulators: SL[9], SY[9], KL[9], KY[9], sum w G_L, sum w G_Y
+#define NACC_NEAR 38
+
+__device__ __forceinline__ void accum_point(double* acc, double w, const double* x, const double* y,
+                                            const double* ny, const double* lx, const double* ly,
+                                            double kappa) {
+    double d0 = x[0] - y[0], d1 = x[1] - y[1], d2 = x[2] - y[2];
+    double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+    double r = sqrt(r2);
+    double gl = 1.0 / (4.0 * M_PI * r);
+    double ek = exp(-kappa * r);
+    double gy = ek * gl;
+    double dn = d0 * ny[0] + d1 * ny[1] + d2 * ny[2];
+    double kl = gl * dn / r2;
+    double ky = kl * ek * (1.0 + kappa * r);
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            double ll = w * lx[a] * ly[b];
+            acc[3 * a + b] += gl * ll;
+            acc[9 + 3 * a + b] += gy * ll;
+            acc[18 + 3 * a + b] += kl * ll;
+            acc[27 + 3 * a + b] += ky * ll;
+        }
+    acc[36] += w * gl;
+    acc[37] += w * gy;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Expand 38 reduced accumulators into six 3x3 blocks (V_L, K_L, D_L, V_Y, K_Y, D_Y).
+__device__ void expand_blocks(const double* acc, const PairGeom& A, const PairGeom& B,
+                              const double* tgeoA, const double* tgeoB, double kappa, double* out) {
+    double nn = A.n[0] * B.n[0] + A.n[1] * B.n[1] + A.n[2] * B.n[2];
+    double f = 1.0 / (4.0 * A.area * B.area);
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            const double* ea = tgeoA + 4 + 3 * a;
+            const double* eb = tgeoB + 4 + 3 * b;
+            double cc = f * (ea[0] * eb[0] + ea[1] * eb[1] + ea[2] * eb[2]);
+            int ab = 3 * a + b;
+            out[0 * 9 + ab] = acc[ab];
+            out[1 * 9 + ab] = acc[18 + ab];
+            out[2 * 9 + ab] = cc * acc[36];
+            out[3 * 9 + ab] = acc[9 + ab];
+            out[4 * 9 + ab] = acc[27 + ab];
+            out[5 * 9 + ab] = cc * acc[37] + kappa * kappa * nn * acc[9 + ab];
+        }
+}
+
+// One warp per adjacent pair. Writes ss[p][54] (regularised) and far[p][54]
+// (far rule, identical points excluded).
+__global__ void k_near_pairs(const double* __restrict__ verts, const int32_t* __restrict__ tris,
+                             const double* __restrict__ tgeo, const int4* __restrict__ pairs,
+                             int64_t npairs, Gauss gq, Rule rule, double kappa,
+                             double* __restrict__ ss_out, double* __restrict__ far_out) {
+    int lane = threadIdx.x & 31;
+    int64_t p = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (p >= npairs) return;
+    int4 pr = pairs[p];
+    PairGeom A, B;
+    load_tri(verts, tris, tgeo, pr.x, A);
+    load_tri(verts, tris, tgeo, pr.y, B);
+    int kind = pr.z;
+    int permA = pr.w & 63, permB = (pr.w >> 6) & 63;
+    int nreg = kind == 2 ? 2 : 6;
+    int n = gq.n;
+    int n2 = n * n, n4 = n2 * n2;
+    double jac_ab = (2.0 * A.area) * (2.0 * B.area);
+    double acc[NACC_NEAR];
+    for (int k = 0; k < NACC_NEAR; ++k) acc[k] = 0.0;
+    for (int idx = lane; idx < nreg * n4; idx += 32) {
+        int reg = idx / n4;
+        int r = idx - reg * n4;
+        int i0 = r / (n2 * n), i1 = (r / n2) % n, i2 = (r / n) % n, i3 = r % n;
+        double sx, tx, sy, ty;
+        double jac = ss_map(kind, reg, gq.x[i0], gq.x[i1], gq.x[i2], gq.x[i3], sx, tx, sy, ty);
+        double w = gq.w[i0] * gq.w[i1] * gq.w[i2] * gq.w[i3] * jac * jac_ab;
+        double x[3], y[3], lx[3], ly[3];
+        ref_to_phys(A, permA, sx, tx, x, lx);
+        ref_to_phys(B, permB, sy, ty, y, ly);
+        accum_point(acc, w, x, y, B.n, lx, ly, kappa);
+    }
+    for (int k = 0; k < NACC_NEAR; ++k) acc[k] = warp_sum(acc[k]);
+    if (lane == 0)
+        expand_blocks(acc, A, B, tgeo + 16 * (int64_t)pr.x, tgeo + 16 * (int64_t)pr.y, kappa, ss_out + 54 * p);
+    // far rule on the same pair (what the pair kernel adds for it)
+    for (int k = 0; k < NACC_NEAR; ++k) acc[k] = 0.0;
+    int Q = rule.Q;
+    for (int idx = lane; idx < Q * Q; idx += 32) {
+        int i = idx / Q, j = idx % Q;
+        if (kind == 0 && i == j) continue;  // identical points are skipped by the pair kernel
+        double x[3], y[3];
+        for (int k = 0; k < 3; ++k) {
+            x[k] = rule.l[i][0] * A.p[0][k] + rule.l[i][1] * A.p[1][k] + rule.l[i][2] * A.p[2][k];
+            y[k] = rule.l[j][0] * B.p[0][k] + rule.l[j][1] * B.p[1][k] + rule.l[j][2] * B.p[2][k];
+        }
+        double w = rule.w[i] * A.area * rule.w[j] * B.area;
+        accum_point(acc, w, x, y, B.n, rule.l[i], rule.l[j], kappa);
+    }
+    for (int k = 0; k < NACC_NEAR; ++k) acc[k] = warp_sum(acc[k]);
+    if (lane == 0)
+        expand_blocks(acc, A, B, tgeo + 16 * (int64_t)pr.x, tgeo + 16 * (int64_t)pr.y, kappa, far_out + 54 * p);
+}
+
+// One thread per nonzero: sum the contributions in their fixed (pair) order.
+__global__ void k_near_entries(int64_t nnz, int64_t nv, const int32_t* __restrict__ row_of,
+                               const int32_t* __restrict__ col, const int32_t* __restrict__ cptr,
+                               const int32_t* __restrict__ contrib, const int4* __restrict__ pairs,
+                               const double* __restrict__ tgeo, const double* __restrict__ ss,
+                               const double* __restrict__ far, double* __restrict__ val,
+                               double* __restrict__ diag) {
+    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e >= nnz) return;
+    double nearv[6] = {0, 0, 0, 0, 0, 0}, full[6] = {0, 0, 0, 0, 0, 0}, mass = 0.0;
+    for (int32_t c = cptr[e]; c < cptr[e + 1]; ++c) {
+        int32_t code = contrib[c];
+        int64_t p = code / 9;
+        int ab = code - 9 * (int)p;
+        for (int o = 0; o < 6; ++o) {
+            double s = ss[54 * p + 9 * o + ab];
+            nearv[o] += s - far[54 * p + 9 * o + ab];
+            full[o] += s;
+        }
+        int4 pr = pairs[p];
+        if (pr.z == 0) mass += tgeo[16 * (int64_t)pr.x + 3] / 12.0 * ((ab % 4 == 0) ? 2.0 : 1.0);
+    }
+    const int map[6] = {N_VL, N_KL, N_DL, N_VY, N_KY, N_DY};
+    for (int o = 0; o < 6; ++o) val[map[o] * nnz + e] = nearv[o];
+    val[N_M * nnz + e] = mass;
+    int32_t i = row_of[e];
+    if (col[e] == i) {
+        for (int o = 0; o < 6; ++o) diag[map[o] * nv + i] = full[o];
+        diag[N_M * nv + i] = mass;
+    }
+}
+
+__global__ void k_row_of(int64_t nv, const int32_t* __restrict__ row_ptr, int32_t* __restrict__ row_of) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nv) return;
+    for (int32_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) row_of[k] = (int32_t)i;
+}
+
+static void free_near(pb_near* nf) {
+    if (nf->val) cudaFree(nf->val);
+    if (nf->diag) cudaFree(nf->diag);
+    nf->val = nf->diag = nullptr;
+}
+
+static int build(pb_ctx* ctx, const pb_mesh* m, double kappa, pb_near* nf, cudaStream_t s) {
+    nf->mesh = m;
+    nf->kappa = kappa;
+    PB_TRY(dev_alloc((void**)&nf->val, sizeof(double) * N_VALS * m->nnz));
+    PB_TRY(dev_alloc((void**)&nf->diag, sizeof(double) * N_VALS * m->nv));
+    double *ss = nullptr, *far = nullptr;
+    int32_t* row_of = nullptr;
+    int rc = dev_alloc((void**)&ss, sizeof(double) * 54 * m->npairs);
+    if (rc == PB_OK) rc = dev_alloc((void**)&far, sizeof(double) * 54 * m->npairs);
+    if (rc == PB_OK) rc = dev_alloc((void**)&row_of, sizeof(int32_t) * m->nnz);
+    if (rc == PB_OK) {
+        Gauss gq = gauss01(m->n_ss);
+        int threads = 128;  // 4 pairs per block
+        int64_t blocks = (m->npairs * 32 + threads - 1) / threads;
+        k_near_pairs<<<(unsigned)blocks, threads, 0, s>>>(m->verts, m->tris, m->tgeo, m->pairs, m->npairs,
+                                                         gq, mesh_rule(m), kappa, ss, far); ::pb::count_launch();
+        k_row_of<<<(unsigned)((m->nv + 255) / 256), 256, 0, s>>>(m->nv, m->row_ptr, row_of); ::pb::count_launch();
+        cudaMemsetAsync(nf->diag, 0, sizeof(double) * N_VALS * m->nv, s);
+        k_near_entries<<<(unsigned)((m->nnz + 255) / 256), 256, 0, s>>>(
+            m->nnz, m->nv, row_of, m->col, m->contrib_ptr, m->contrib, m->pairs, m->tgeo, ss, far, nf->val,
+            nf->diag); ::pb::count_launch();
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) rc = set_error(PB_ECUDA, "near build: %s", cudaGetErrorString(e));
+    }
+    if (ss) cudaFree(ss);
+    if (far) cudaFree(far);
+    if (row_of) cudaFree(row_of);
+    return rc;
+}
+
+}  // namespace pb
+
+using namespace pb;
+
+extern "C" int pb_near_build(pb_ctx* ctx, const pb_mesh* mesh, double kappa, pb_near** out, void* stream) {
+    if (!ctx || !mesh || !out) return set_error(PB_EINVAL, "pb_near_build: NULL argument");
+    if (!(kappa >= 0.0) || !std::isfinite(kappa)) return set_error(PB_EINVAL, "kappa must be >= 0");
+    *out = nullptr;
+    PB_CUDA(cudaSetDevice(ctx->device));
+    pb_near* nf = new pb_near();
+    int rc = build(ctx, mesh, kappa, nf, (cudaStream_t)stream);
+    if (rc != PB_OK) {
+        free_near(nf);
+        delete nf;
+        return rc;
+    }
+    *out = nf;
+    return PB_OK;
+}
+
+extern "C" int pb_free_near(pb_near* nf) {
+    if (!nf) return PB_OK;
+    free_near(nf);
+    delete nf;
+    return PB_OK;
+}

@@ -1,0 +1,214 @@
+// a6 + a10: charges -> surface (right-hand side) and surface -> charges
+// (reaction potential, solvation energy), FP64.
+//
+// Paper eq. sources: phi_D(x) = sum_j q_j / (4 pi eps_int |x - x_j|) and
+// phi_N = d phi_D / dn_x, tested against the P1 basis with the far rule.
+// Paper eqs. phireac_bie and dG: phi_reac(x_j) = V_int[v_int](x_j) - K_int[u_int](x_j),
+// Delta G = 1/2 sum_j q_j phi_reac(x_j).
+#include <math.h>
+
+#include "internal.h"
+
+namespace pb {
+
+int rhs_coefs(const pb_params* prm, int form, double alpha, double beta, double d[2], double n[2]);
+
+constexpr int QTILE = 256;
+
+// per point: phi_D and phi_N of all charges, then per triangle the tested sums
+__global__ void k_rhs_points(int64_t nt, Rule rule, const double* __restrict__ pts64, const double* __restrict__ tgeo,
+                             const double* __restrict__ xq, const double* __restrict__ q, int64_t nq, double eps_int,
+                             double* __restrict__ tri_out) {
+    __shared__ double sq[QTILE * 4];
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    bool live = t < nt;
+    const int Q = rule.Q;
+    double pd[6] = {0, 0, 0, 0, 0, 0}, pn[6] = {0, 0, 0, 0, 0, 0};
+    double nx = 0, ny = 0, nz = 0;
+    if (live) { nx = tgeo[16 * t]; ny = tgeo[16 * t + 1]; nz = tgeo[16 * t + 2]; }
+    for (int64_t j0 = 0; j0 < nq; j0 += QTILE) {
+        int cnt = (int)min((int64_t)QTILE, nq - j0);
+        for (int k = threadIdx.x; k < cnt; k += blockDim.x) {
+            sq[4 * k] = xq[3 * (j0 + k)];
+            sq[4 * k + 1] = xq[3 * (j0 + k) + 1];
+            sq[4 * k + 2] = xq[3 * (j0 + k) + 2];
+            sq[4 * k + 3] = q[j0 + k];
+        }
+        __syncthreads();
+        if (live)
+            for (int k = 0; k < Q; ++k) {
+                const double* x = pts64 + 4 * (t * Q + k);
+                for (int j = 0; j < cnt; ++j) {
+                    double d0 = x[0] - sq[4 * j], d1 = x[1] - sq[4 * j + 1], d2 = x[2] - sq[4 * j + 2];
+                    double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+                    double rinv = 1.0 / sqrt(r2);
+                    double c = sq[4 * j + 3] * rinv;
+                    pd[k] += c;
+                    pn[k] -= c * rinv * rinv * (d0 * nx + d1 * ny + d2 * nz);
+                }
+            }
+        __syncthreads();
+    }
+    if (!live) return;
+    const double f = 1.0 / (4.0 * M_PI * eps_int);
+    double out[6] = {0, 0, 0, 0, 0, 0};
+    for (int k = 0; k < Q; ++k) {
+        double w = pts64[4 * (t * Q + k) + 3] * f;
+        for (int a = 0; a < 3; ++a) {
+            out[a] += w * rule.l[k][a] * pd[k];
+            out[3 + a] += w * rule.l[k][a] * pn[k];
+        }
+    }
+    for (int k = 0; k < 6; ++k) tri_out[6 * t + k] = out[k];
+}
+
+__global__ void k_rhs_gather(int64_t nv, const int32_t* __restrict__ v2t_ptr, const int32_t* __restrict__ v2t,
+                             const double* __restrict__ tri, double d0, double d1, double n0, double n1,
+                             double* __restrict__ rhs) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nv) return;
+    double bd = 0.0, bn = 0.0;
+    for (int32_t k = v2t_ptr[i]; k < v2t_ptr[i + 1]; ++k) {
+        int32_t ta = v2t[k];
+        int64_t t = ta / 3;
+        int a = ta - 3 * (int)t;
+        bd += tri[6 * t + a];
+        bn += tri[6 * t + 3 + a];
+    }
+    rhs[i] = d0 * bd + n0 * bn;
+    rhs[nv + i] = d1 * bd + n1 * bn;
+}
+
+// phi_reac partial sums: grid (chunks, charges)
+constexpr int EN_THREADS = 256;
+constexpr int EN_CHUNK = 8192;
+
+__global__ void k_energy_part(int64_t nt, Rule rule, const int32_t* __restrict__ tris, const double* __restrict__ tgeo,
+                              const double* __restrict__ pts64, const double* __restrict__ x, int64_t nv,
+                              double vscale, const double* __restrict__ xq, double* __restrict__ part, int nchunk) {
+    __shared__ double red[EN_THREADS / 32];
+    const int Q = rule.Q;
+    const int64_t np = nt * Q;
+    int c = blockIdx.x;
+    int64_t j = blockIdx.y;
+    double qx = xq[3 * j], qy = xq[3 * j + 1], qz = xq[3 * j + 2];
+    int64_t i0 = (int64_t)c * EN_CHUNK, i1 = min(np, i0 + EN_CHUNK);
+    double s = 0.0;
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += EN_THREADS) {
+        int64_t t = i / Q;
+        int k = (int)(i - t * Q);
+        const int32_t* f = tris + 3 * t;
+        double u = rule.l[k][0] * x[f[0]] + rule.l[k][1] * x[f[1]] + rule.l[k][2] * x[f[2]];
+        double v = vscale * (rule.l[k][0] * x[nv + f[0]] + rule.l[k][1] * x[nv + f[1]] + rule.l[k][2] * x[nv + f[2]]);
+        const double* y = pts64 + 4 * i;
+        double d0 = qx - y[0], d1 = qy - y[1], d2 = qz - y[2];
+        double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+        double rinv = 1.0 / sqrt(r2);
+        const double* g = tgeo + 16 * t;
+        double dn = d0 * g[0] + d1 * g[1] + d2 * g[2];
+        // G_L v - dG_L/dn_y u, with 1/(4 pi) applied at the end
+        s += y[3] * (rinv * v - rinv * rinv * rinv * dn * u);
+    }
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double tsum = 0.0;
+        for (int w = 0; w < EN_THREADS / 32; ++w) tsum += red[w];
+        part[j * nchunk + c] = tsum;
+    }
+}
+
+__global__ void k_energy_final(int64_t nq, int nchunk, const double* __restrict__ part, const double* __restrict__ q,
+                               double* __restrict__ phi, double* __restrict__ dG) {
+    // one thread: fixed summation order
+    double e = 0.0;
+    for (int64_t j = 0; j < nq; ++j) {
+        double p = 0.0;
+        for (int c = 0; c < nchunk; ++c) p += part[j * nchunk + c];
+        p *= 1.0 / (4.0 * M_PI);
+        if (phi) phi[j] = p;
+        e += q[j] * p;
+    }
+    dG[0] = 0.5 * e;
+}
+
+}  // namespace pb
+
+using namespace pb;
+
+extern "C" int pb_rhs_charges(pb_ctx* ctx, const pb_mesh* m, const double* xq, const double* q, int64_t n_q,
+                              const pb_params* prm, int form, double alpha, double beta, double* rhs, void* stream) {
+    if (!ctx || !m || !xq || !q || !rhs || !prm) return set_error(PB_EINVAL, "pb_rhs_charges: NULL argument");
+    if (n_q < 1) return set_error(PB_EINVAL, "need at least one charge");
+    double d[2], n[2];
+    PB_TRY(rhs_coefs(prm, form, alpha, beta, d, n));
+    cudaStream_t s = (cudaStream_t)stream;
+    PB_TRY(ws_reserve(const_cast<pb_mesh*>(m)->ws_tri, sizeof(double) * 6 * m->nt));
+    double* tri = (double*)m->ws_tri.ptr;
+    k_rhs_points<<<(unsigned)((m->nt + 127) / 128), 128, 0, s>>>(m->nt, mesh_rule(m), m->pts64, m->tgeo, xq, q, n_q,
+                                                                prm->eps_int, tri); ::pb::count_launch();
+    k_rhs_gather<<<(unsigned)((m->nv + 255) / 256), 256, 0, s>>>(m->nv, m->v2t_ptr, m->v2t, tri, d[0], d[1], n[0],
+                                                                n[1], rhs); ::pb::count_launch();
+    PB_CUDA(cudaGetLastError());
+    return PB_OK;
+}
+
+extern "C" int pb_energy(pb_ctx* ctx, const pb_mesh* m, const double* x, int form, const double* xq, const double* q,
+                         int64_t n_q, const pb_params* prm, double* phi, double* dG_paper, double* dG_kcal,
+                         void* stream) {
+    if (!ctx || !m || !x || !xq || !q || !prm) return set_error(PB_EINVAL, "pb_energy: NULL argument");
+    if (n_q < 1) return set_error(PB_EINVAL, "need at least one charge");
+    if (form < PB_DIRECT_INT || form > PB_LU) return set_error(PB_EINVAL, "unknown formulation %d", form);
+    cudaStream_t s = (cudaStream_t)stream;
+    // exterior unknowns -> interior traces: u_int = u_ext, v_int = (eps_ext/eps_int) v_ext
+    double vscale = form_is_exterior(form) ? prm->eps_ext / prm->eps_int : 1.0;
+    int nchunk = (int)((m->np + EN_CHUNK - 1) / EN_CHUNK);
+    double* part = nullptr;
+    PB_TRY(dev_alloc((void**)&part, sizeof(double) * (n_q * nchunk + 1)));
+    double* dG = part + n_q * nchunk;
+    dim3 grid(nchunk, (unsigned)n_q);
+    k_energy_part<<<grid, EN_THREADS, 0, s>>>(m->nt, mesh_rule(m), m->tris, m->tgeo, m->pts64, x, m->nv, vscale, xq, part,
+                                            nchunk); ::pb::count_launch();
+    k_energy_final<<<1, 1, 0, s>>>(n_q, nchunk, part, q, phi, dG); ::pb::count_launch();
+    double h = 0.0;
+    cudaError_t e = cudaMemcpyAsync(&h, dG, sizeof(double), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(part);
+    if (e != cudaSuccess) return set_error(PB_ECUDA, "pb_energy: %s", cudaGetErrorString(e));
+    if (dG_paper) *dG_paper = h;
+    if (dG_kcal) *dG_kcal = h * 4.0 * M_PI * 332.0636;
+    return PB_OK;
+}
+
+extern "C" int pb_solvation_energy(pb_ctx* ctx, const double* verts, int64_t n_verts, const int32_t* tris,
+                                   int64_t n_tris, const double* xq, const double* q, int64_t n_q,
+                                   const pb_params* prm, const pb_quad_plan* plan, int form, int precond,
+                                   const pb_solve_opts* opts, double* dG_kcal, pb_solve_info* info, void* stream) {
+    if (!ctx || !verts || !tris || !xq || !q || !prm || !dG_kcal)
+        return set_error(PB_EINVAL, "pb_solvation_energy: NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    pb_mesh* m = nullptr;
+    pb_near* nf = nullptr;
+    double* buf = nullptr;
+    int rc = pb_mesh_load(ctx, verts, n_verts, tris, n_tris, plan, PB_MEM_HOST, &m);
+    if (rc == PB_OK) rc = pb_near_build(ctx, m, prm->kappa, &nf, stream);
+    if (rc == PB_OK) rc = dev_alloc((void**)&buf, sizeof(double) * (4 * n_q + 4 * m->nv));
+    if (rc == PB_OK) {
+        double* dxq = buf;
+        double* dq = buf + 3 * n_q;
+        double* rhs = dq + n_q;
+        double* x = rhs + 2 * m->nv;
+        cudaError_t e = cudaMemcpyAsync(dxq, xq, sizeof(double) * 3 * n_q, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(dq, q, sizeof(double) * n_q, cudaMemcpyHostToDevice, s);
+        if (e != cudaSuccess) rc = set_error(PB_ECUDA, "copy of charges: %s", cudaGetErrorString(e));
+        double a = opts ? opts->alpha : 0.0, b = opts ? opts->beta : 0.0;
+        if (rc == PB_OK) rc = pb_rhs_charges(ctx, m, dxq, dq, n_q, prm, form, a, b, rhs, stream);
+        if (rc == PB_OK) rc = pb_solve(ctx, m, nf, prm, form, precond, opts, rhs, x, info, stream);
+        if (rc == PB_OK) rc = pb_energy(ctx, m, x, form, dxq, dq, n_q, prm, nullptr, nullptr, dG_kcal, stream);
+    }
+    if (buf) cudaFree(buf);
+    pb_free_near(nf);
+    pb_free_mesh(m);
+    return rc;
+}

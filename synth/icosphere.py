@@ -64,3 +64,41 @@ def icosphere(level: int, radius: float = 1.0, center=(0.0, 0.0, 0.0)):
         f = np.array(nf, dtype=np.int64)
     v = v * float(radius) + np.asarray(center, dtype=np.float64)
     return np.ascontiguousarray(v, dtype=np.float64), np.ascontiguousarray(f, dtype=np.int32)
+
+
+def uv_ellipsoid(n_lon: int, n_lat: int, axes=(1.0, 1.0, 1.0), center=(0.0, 0.0, 0.0), twist: float = 0.0):
+    """Latitude-longitude ellipsoid with two pole vertices.
+
+    n_lat - 1 rings of n_lon vertices; 2 n_lon (n_lat - 1) triangles, so the
+    triangle count is not a power-of-two multiple (useful for ragged tails).
+    ``twist`` rotates each ring by twist * ring index (radians) to make the
+    triangles non-symmetric. Counter-clockwise seen from outside."""
+    if n_lon < 3 or n_lat < 2:
+        raise ValueError("need n_lon >= 3 and n_lat >= 2")
+    a = np.asarray(axes, dtype=np.float64)
+    verts = [[0.0, 0.0, 1.0]]
+    for i in range(1, n_lat):
+        th = np.pi * i / n_lat
+        for j in range(n_lon):
+            ph = 2.0 * np.pi * j / n_lon + twist * i
+            verts.append([np.sin(th) * np.cos(ph), np.sin(th) * np.sin(ph), np.cos(th)])
+    verts.append([0.0, 0.0, -1.0])
+    v = np.array(verts) * a + np.asarray(center, dtype=np.float64)
+    south = len(verts) - 1
+
+    def ring(i, j):
+        return 1 + (i - 1) * n_lon + (j % n_lon)
+
+    f = []
+    for j in range(n_lon):
+        f.append([0, ring(1, j), ring(1, j + 1)])
+    for i in range(1, n_lat - 1):
+        for j in range(n_lon):
+            p, q, r, s = ring(i, j), ring(i, j + 1), ring(i + 1, j), ring(i + 1, j + 1)
+            f.append([p, r, s])
+            f.append([p, s, q])
+    for j in range(n_lon):
+        f.append([south, ring(n_lat - 1, j + 1), ring(n_lat - 1, j)])
+    f = np.array(f, dtype=np.int64)
+    f = _orient_outward(v - np.asarray(center, dtype=np.float64), f)
+    return np.ascontiguousarray(v, dtype=np.float64), np.ascontiguousarray(f, dtype=np.int32)
