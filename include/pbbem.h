@@ -194,6 +194,30 @@ int pb_system_apply(pb_ctx* ctx, const pb_mesh* mesh, const pb_near* near, const
                     int form, double alpha, double beta, int prec, const double* x, double* y,
                     void* stream);
 
+/* Allocation-free FP32 system application (the paper has no counterpart: it
+ * exists for callers that cannot call cudaMalloc). It computes what
+ * pb_system_apply(..., PB_F32, ...) computes, with the same kernels, but keeps
+ * every temporary in one file-scope device array of 16 MiB that each GPU
+ * loading the library holds until the process exits; it calls no cudaMalloc,
+ * cudaFree or other allocating routine. The callers it is for: processes
+ * whose device memory belongs to another allocator that reserves it up front
+ * (a raw cudaMalloc would fail or take memory that allocator counts on), and
+ * latency-bound loops that cannot afford the device-wide synchronisation that
+ * cudaMalloc and cudaFree bring.
+ *   - Limit: meshes whose temporaries fit in 16 MiB (about 9,000 triangles
+ *     with the 6-point rule); larger meshes get PB_EINVAL with the sizes.
+ *   - The first call on a device, with that device current, looks up the
+ *     array's device address once (cudaGetSymbolAddress); make that first call
+ *     before any stream capture.
+ *   - All calls share the one array and it keeps the last call's contents
+ *     (each call writes every word it later reads, so nothing must start at
+ *     zero). Calls that overlap on the GPU - on different streams, or from
+ *     different threads - race on it and must not be issued.
+ * x, y: device arrays of 2*N_v doubles that must not overlap; the caller owns
+ * them. */
+int pb_system_apply_noalloc(pb_ctx* ctx, const pb_mesh* mesh, const pb_near* near, const pb_params* prm,
+                            int form, double alpha, double beta, const double* x, double* y, void* stream);
+
 /* ---- a6: right-hand side ------------------------------------------------ */
 /* rhs = the formulation's right-hand side built from the source projections
  * (paper eq. sources: phi_D = sum_j q_j/(4 pi eps_int |x - x_j|), phi_N its

@@ -190,6 +190,17 @@ def pb_system_apply(ctx: Ctx, mesh: Mesh, near: Near, params: Params, form, x: t
     return y
 
 
+def pb_system_apply_noalloc(ctx: Ctx, mesh: Mesh, near: Near, params: Params, form, x: torch.Tensor,
+                            y: torch.Tensor, alpha: float = 0.0, beta: float = 0.0, stream=None):
+    """FP32 system application that allocates no device memory: for callers
+    that cannot call cudaMalloc (see include/pbbem.h). y must be preallocated
+    by the caller; meshes up to the library's 16 MiB scratch limit."""
+    p = params.c()
+    _check(N.load().pb_system_apply_noalloc(ctx.ptr, mesh.ptr, near.ptr, ctypes.byref(p), _form(form), alpha, beta,
+                                            _dptr(x, "x"), _dptr(y, "y"), _stream(stream)))
+    return y
+
+
 def pb_rhs_charges(ctx: Ctx, mesh: Mesh, xq: torch.Tensor, q: torch.Tensor, params: Params, form,
                    alpha: float = 0.0, beta: float = 0.0, rhs: torch.Tensor | None = None, stream=None):
     nv = mesh.info()["n_verts"]

@@ -25,6 +25,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 #include "internal.h"
 
@@ -641,3 +642,115 @@ int far_splits(const pb_mesh* m, int tpc, int ctas_per_sm) {
 }
 
 }  // namespace pb
+
+// ------------------------------------------------------ allocation-free variant
+// Some callers cannot call cudaMalloc: a process whose device memory is owned
+// entirely by another allocator (a framework that reserves almost all of HBM
+// up front, so a raw cudaMalloc fails or steals from it), or a latency-bound
+// loop that must not pay for the device-wide synchronisation that cudaMalloc
+// and cudaFree imply. pb_system_apply_noalloc serves them: the FP32 system
+// application with every temporary in the file-scope array below instead of
+// the mesh's workspaces.
+namespace pb {
+
+constexpr size_t NOALLOC_SCRATCH_BYTES = (size_t)16 << 20;  // 16 MiB on every GPU that loads the library
+constexpr int NOALLOC_MAX_SPLITS = 4;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
+
+// Device address of the scratch array, looked up once per device. In host code
+// the array's name is only a host-side stand-in, so the address must come
+// from cudaGetSymbolAddress with that device current.
+static int noalloc_scratch(int device, unsigned char** out) {
+    static std::mutex mu;
+    static unsigned char* addr[64] = {nullptr};
+    if (device < 0 || device >= 64) return set_error(PB_EINVAL, "device %d out of range", device);
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[device]) {
+        void* p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return set_error(PB_ECUDA, "cudaGetSymbolAddress of the scratch array failed: %s", cudaGetErrorString(e));
+        addr[device] = (unsigned char*)p;
+    }
+    *out = addr[device];
+    return PB_OK;
+}
+
+static size_t align256(size_t n) { return (n + 255) / 256 * 256; }
+
+}  // namespace pb
+
+extern "C" int pb_system_apply_noalloc(pb_ctx* ctx, const pb_mesh* m, const pb_near* nf, const pb_params* prm,
+                                       int form, double alpha, double beta, const double* x, double* y,
+                                       void* stream) {
+    using namespace pb;
+    if (!ctx || !m || !nf || !prm || !x || !y) return set_error(PB_EINVAL, "pb_system_apply_noalloc: NULL argument");
+    if (nf->mesh != m) return set_error(PB_EINVAL, "near field belongs to another mesh");
+    if (x == y) return set_error(PB_EINVAL, "x and y must not overlap");
+    BlockOp B;
+    PB_TRY(system_blockop(prm, form, alpha, beta, &B));
+    FarPlan fp;
+    PB_TRY(make_far_plan(B, nf->kappa, &fp));
+    const int64_t nv = m->nv, nt = m->nt, np = m->np;
+    const int nacc = fp.mode == 0 ? 2 : 10;
+    // scratch layout: sources | partial sums (<= 4 splits) | per-triangle sums | combined near values
+    const size_t b_src = align256(sizeof(float) * REC32 * (size_t)np);
+    const size_t b_part = align256(sizeof(float) * NOALLOC_MAX_SPLITS * 10 * (size_t)np);
+    const size_t b_tri = align256(sizeof(double) * 6 * (size_t)nt);
+    const size_t b_comb = align256((sizeof(double) + sizeof(float)) * 4 * (size_t)m->nnz);
+    const size_t need = b_src + b_part + b_tri + b_comb;
+    if (need > NOALLOC_SCRATCH_BYTES)
+        return set_error(PB_EINVAL, "pb_system_apply_noalloc: mesh needs %zu bytes of scratch, the limit is %zu "
+                         "(%lld triangles here)", need, NOALLOC_SCRATCH_BYTES, (long long)nt);
+    PB_CUDA(cudaSetDevice(ctx->device));
+    unsigned char* base = nullptr;
+    PB_TRY(noalloc_scratch(ctx->device, &base));
+    float* rec = (float*)base;
+    float* part = (float*)(base + b_src);
+    double* tri = (double*)(base + b_src + b_part);
+    double* c64 = (double*)(base + b_src + b_part + b_tri);
+    float* c32 = (float*)(c64 + 4 * m->nnz);
+    cudaStream_t s = (cudaStream_t)stream;
+    // every scratch word read below is first written by this call: nothing to clear
+    PB_TRY(combine_near(m, nf, B, c64, c32, s));
+    if (fp.any) {
+        bool need_u = false, need_v = false;
+        for (int R = 0; R < 2; ++R)
+            for (int o = 1; o < O_N; ++o) {
+                need_u = need_u || B.c[R][0][o] != 0.0;
+                need_v = need_v || B.c[R][1][o] != 0.0;
+            }
+        Rule rule = mesh_rule(m);
+        unsigned tb = (unsigned)((nt + 127) / 128);
+        k_sources<float, REC32><<<tb, 128, 0, s>>>(nt, m->Q, rule, m->tris, m->tgeo, m->pts64, m->pts32, m->pts32lo,
+                                                   x, x + nv, need_u, need_v, rec);
+        ::pb::count_launch();
+        CUtensorMap map;
+        PB_TRY(make_tmap(m, rec, &map));
+        const void* kern = fp.mode == 0 ? (const void*)k_pair32<0, false> : (const void*)k_pair32<1, false>;
+        int S = std::min(NOALLOC_MAX_SPLITS, choose_splits(np, TPB32 * TGT32, TS32, occupancy_slots(m, kern, TPB32)));
+        int64_t chunk = ((np + S - 1) / S + TS32 - 1) / TS32 * TS32;
+        S = (int)((np + chunk - 1) / chunk);
+        Coef32 cf;
+        for (int R = 0; R < 2; ++R)
+            for (int j = 0; j < 4; ++j) cf.k[R][j] = (float)fp.k[R][j];
+        cf.kappa = (float)fp.kappa;
+        cf.mk2 = (float)(-fp.kappa * 1.4426950408889634);
+        dim3 grid((unsigned)((np + TPB32 * TGT32 - 1) / (TPB32 * TGT32)), (unsigned)S);
+        if (fp.mode == 0)
+            k_pair32<0, false><<<grid, TPB32, 0, s>>>(map, np, m->pts32, m->pts32lo, cf, chunk, part, m->status);
+        else
+            k_pair32<1, false><<<grid, TPB32, 0, s>>>(map, np, m->pts32, m->pts32lo, cf, chunk, part, m->status);
+        ::pb::count_launch();
+        k_tri_reduce<float><<<tb, 128, 0, s>>>(nt, np, rule, S, fp.mode, fp, m->tgeo, m->pts64, part, tri);
+        ::pb::count_launch();
+    }
+    (void)nacc;
+    unsigned gb = (unsigned)((nv * 8 + 255) / 256);
+    k_gather_spmv<float><<<gb, 256, 0, s>>>(nv, m->v2t_ptr, m->v2t, tri, fp.any ? 1 : 0, m->row_ptr, m->col, c32,
+                                            m->nnz, x, y);
+    ::pb::count_launch();
+    PB_CUDA(cudaGetLastError());
+    return PB_OK;
+}

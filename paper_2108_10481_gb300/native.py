@@ -55,6 +55,7 @@ SIGNATURES = {
     "pb_solvation_energy": [P, P, c_int64, P, c_int64, P, P, c_int64, ctypes.POINTER(pb_params),
                             ctypes.POINTER(pb_quad_plan), c_int, c_int, ctypes.POINTER(pb_solve_opts),
                             ctypes.POINTER(c_double), ctypes.POINTER(pb_solve_info), P],
+    "pb_system_apply_noalloc": [P, P, P, ctypes.POINTER(pb_params), c_int, c_double, c_double, P, P, P],
     "pb_profile": [P, c_int],
     "pb_profile_read": [P, c_int, ctypes.POINTER(c_int64), ctypes.POINTER(c_double), ctypes.POINTER(c_double),
                         ctypes.POINTER(c_double)],
