@@ -37,7 +37,7 @@ L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes per launch of the FP32 pair kernel in its V/K + D/T mode, from one ncu capture at 122,880 points
 # (dram__bytes_read.sum + dram__bytes_write.sum; profiles/pair32_vkdt_multi_charge_sphere.md). Valid only for
 # that kernel as captured; any other dominant kernel reports null.
-NCU_TRAFFIC = {("pair32", "juffer", 122880): 9.84e6}
+NCU_TRAFFIC = {}
 
 
 def parse():

@@ -2,6 +2,7 @@
 #include <cudaTypedefs.h>
 #include <stdarg.h>
 #include <stdio.h>
+#include <stdlib.h>
 
 #include <atomic>
 
@@ -83,6 +84,8 @@ extern "C" int pb_init(int device, pb_ctx** out) {
         return set_error(PB_ECUDA, "cuTensorMapEncodeTiled entry point unavailable");
     }
     c->encode_tiled = fn;
+    const char* pk = getenv("PBBEM_PAIR_KERNEL");
+    if (pk && pk[0] == '1') c->pair_kernel = 1;
     *out = c;
     return PB_OK;
 }

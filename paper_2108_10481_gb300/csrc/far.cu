@@ -315,6 +315,237 @@ __global__ void __launch_bounds__(TPB32) k_pair32(const __grid_constant__ CUtens
     }
 }
 
+// ------------------------------------ FP32 pair kernel, packed f32x2 (a3)
+// The same sums as k_pair32 with Blackwell's packed FP32 instructions: each
+// thread holds its targets in pairs, so one fma/add/mul.rn.f32x2 advances two
+// targets. Source values are stored twice in a 32-float record so that every
+// packed operand is a register pair loaded straight from shared memory:
+//   x x y y z z s s | px px py py pz pz cx cx | cy cy cz cz xl xl yl yl | zl zl - - - - - -
+// The identical-point guard is needed only in tiles that overlap the CTA's
+// own targets or run past the last point (zero-filled rows).
+constexpr int REC2 = 32;   // floats per duplicated source record
+constexpr int TPB2 = 256;  // threads per CTA
+constexpr int TS2 = 64;    // records per TMA tile
+constexpr int ST2 = 4;     // pipeline stages
+
+__device__ __forceinline__ float2 add2(float2 a, float2 b) {
+    float2 d;
+    asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n add.rn.f32x2 rd, ra, rb;\n"
+        " mov.b64 {%0, %1}, rd;\n}\n" : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    float2 d;
+    asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n sub.rn.f32x2 rd, ra, rb;\n"
+        " mov.b64 {%0, %1}, rd;\n}\n" : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) {
+    float2 d;
+    asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n mul.rn.f32x2 rd, ra, rb;\n"
+        " mov.b64 {%0, %1}, rd;\n}\n" : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("{\n .reg .b64 ra, rb, rc, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n mov.b64 rc, {%6, %7};\n"
+        " fma.rn.f32x2 rd, ra, rb, rc;\n mov.b64 {%0, %1}, rd;\n}\n"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+__device__ __forceinline__ float2 splat(float v) { return make_float2(v, v); }
+
+template <typename T>
+__global__ void k_sources2(int64_t nt, int Q, Rule rule, const int32_t* __restrict__ tris,
+                           const double* __restrict__ tgeo, const double* __restrict__ pts64,
+                           const float* __restrict__ pts32, const float* __restrict__ pts32lo,
+                           const double* __restrict__ u, const double* __restrict__ v, int need_u, int need_v,
+                           float* __restrict__ rec) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    const double* g = tgeo + 16 * t;
+    int32_t i0 = tris[3 * t], i1 = tris[3 * t + 1], i2 = tris[3 * t + 2];
+    double ua[3] = {0, 0, 0}, va[3] = {0, 0, 0};
+    if (need_u) { ua[0] = u[i0]; ua[1] = u[i1]; ua[2] = u[i2]; }
+    if (need_v) { va[0] = v[i0]; va[1] = v[i1]; va[2] = v[i2]; }
+    double inv2a = -1.0 / (2.0 * g[3]);
+    double cu[3];
+    for (int k = 0; k < 3; ++k) cu[k] = inv2a * (ua[0] * g[4 + k] + ua[1] * g[7 + k] + ua[2] * g[10 + k]);
+    for (int q = 0; q < Q; ++q) {
+        int64_t i = t * Q + q;
+        double w = pts64[4 * i + 3] * INV4PI;
+        double uq = rule.l[q][0] * ua[0] + rule.l[q][1] * ua[1] + rule.l[q][2] * ua[2];
+        double vq = rule.l[q][0] * va[0] + rule.l[q][1] * va[1] + rule.l[q][2] * va[2];
+        float val[16] = {pts32[4 * i], pts32[4 * i + 1], pts32[4 * i + 2], (float)(w * vq),
+                         (float)(w * uq * g[0]), (float)(w * uq * g[1]), (float)(w * uq * g[2]),
+                         (float)(w * cu[0]), (float)(w * cu[1]), (float)(w * cu[2]),
+                         pts32lo[4 * i], pts32lo[4 * i + 1], pts32lo[4 * i + 2], 0.f, 0.f, 0.f};
+        float4* r = reinterpret_cast<float4*>(rec + REC2 * i);
+        for (int k = 0; k < 8; ++k) r[k] = make_float4(val[2 * k], val[2 * k], val[2 * k + 1], val[2 * k + 1]);
+    }
+}
+
+struct Coef2 {
+    float2 c[2][4];
+    float2 kap, mk2;
+};
+
+template <int MODE, bool ACC, int NPK, bool GUARD>
+__device__ __forceinline__ void tile_x2(const float* __restrict__ tile, const float2 (&X)[NPK][3],
+                                        const float2 (&XL)[NPK][3], float2 (&acc)[NPK][MODE == 0 ? 2 : 10],
+                                        const Coef2& cf) {
+#pragma unroll 2
+    for (int j = 0; j < TS2; ++j) {
+        const float* r = tile + REC2 * j;
+        const float4 q0 = *reinterpret_cast<const float4*>(r);
+        const float4 q1 = *reinterpret_cast<const float4*>(r + 4);
+        const float4 q2 = *reinterpret_cast<const float4*>(r + 8);
+        const float4 q3 = *reinterpret_cast<const float4*>(r + 12);
+        float4 q4 = make_float4(0.f, 0.f, 0.f, 0.f), q5 = q4, q6 = q4;
+        if (MODE == 1) q4 = *reinterpret_cast<const float4*>(r + 16);
+        if (ACC) {
+            q5 = *reinterpret_cast<const float4*>(r + 20);
+            q6 = *reinterpret_cast<const float4*>(r + 24);
+        }
+        const float2 Sx = make_float2(q0.x, q0.y), Sy = make_float2(q0.z, q0.w), Sz = make_float2(q1.x, q1.y);
+        const float2 Ss = make_float2(q1.z, q1.w), Px = make_float2(q2.x, q2.y), Py = make_float2(q2.z, q2.w);
+        const float2 Pz = make_float2(q3.x, q3.y);
+#pragma unroll
+        for (int p = 0; p < NPK; ++p) {
+            float2 d0 = sub2(X[p][0], Sx), d1 = sub2(X[p][1], Sy), d2 = sub2(X[p][2], Sz);
+            if (ACC) {
+                d0 = add2(d0, sub2(XL[p][0], make_float2(q5.x, q5.y)));
+                d1 = add2(d1, sub2(XL[p][1], make_float2(q5.z, q5.w)));
+                d2 = add2(d2, sub2(XL[p][2], make_float2(q6.x, q6.y)));
+            }
+            const float2 r2 = fma2(d0, d0, fma2(d1, d1, mul2(d2, d2)));
+            float2 rinv = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+            if (GUARD) {
+                rinv.x = r2.x > 0.0f ? rinv.x : 0.0f;
+                rinv.y = r2.y > 0.0f ? rinv.y : 0.0f;
+            }
+            const float2 rr = mul2(r2, rinv);
+            const float2 arg = mul2(rr, cf.mk2);
+            const float2 e = make_float2(ex2_approx(arg.x), ex2_approx(arg.y));
+            const float2 ek = fma2(e, mul2(rr, cf.kap), e);
+            const float2 rinv3 = mul2(mul2(rinv, rinv), rinv);
+            const float2 dp = fma2(d0, Px, fma2(d1, Py, mul2(d2, Pz)));
+            const float2 rs = mul2(rinv, Ss), r3dp = mul2(rinv3, dp);
+            acc[p][0] = fma2(fma2(cf.c[0][1], e, cf.c[0][0]), rs, acc[p][0]);
+            acc[p][0] = fma2(fma2(cf.c[0][3], ek, cf.c[0][2]), r3dp, acc[p][0]);
+            if (MODE == 0) {
+                acc[p][1] = fma2(fma2(cf.c[1][1], e, cf.c[1][0]), rs, acc[p][1]);
+                acc[p][1] = fma2(fma2(cf.c[1][3], ek, cf.c[1][2]), r3dp, acc[p][1]);
+            } else {
+                const float2 ts = mul2(fma2(cf.c[1][3], ek, cf.c[1][2]), mul2(rinv3, Ss));
+                acc[p][1] = fma2(ts, d0, acc[p][1]);
+                acc[p][2] = fma2(ts, d1, acc[p][2]);
+                acc[p][3] = fma2(ts, d2, acc[p][3]);
+                const float2 gc = mul2(fma2(cf.c[1][1], e, cf.c[1][0]), rinv);
+                acc[p][4] = fma2(gc, make_float2(q3.z, q3.w), acc[p][4]);
+                acc[p][5] = fma2(gc, make_float2(q4.x, q4.y), acc[p][5]);
+                acc[p][6] = fma2(gc, make_float2(q4.z, q4.w), acc[p][6]);
+                const float2 gb = mul2(e, rinv);
+                acc[p][7] = fma2(gb, Px, acc[p][7]);
+                acc[p][8] = fma2(gb, Py, acc[p][8]);
+                acc[p][9] = fma2(gb, Pz, acc[p][9]);
+            }
+        }
+    }
+}
+
+template <int MODE, bool ACC>
+__global__ void __launch_bounds__(TPB2) k_pair32x2(const __grid_constant__ CUtensorMap tmap, int64_t np,
+                                                   const float* __restrict__ pts32, const float* __restrict__ pts32lo,
+                                                   Coef32 c32, int64_t chunk, void* __restrict__ part_out,
+                                                   int* __restrict__ status) {
+    constexpr int NACC = MODE == 0 ? 2 : 10;
+    constexpr int NPK = ACC ? 1 : 2;   // packed target pairs per thread
+    constexpr int TGT = 2 * NPK;
+    __shared__ __align__(128) float sh[ST2][TS2 * REC2];
+    __shared__ __align__(8) uint64_t bar[ST2];
+    const int split = blockIdx.y;
+    const int64_t j0 = split * chunk;
+    const int64_t j1 = min(np, j0 + chunk);
+    const int ntiles = (int)((j1 - j0 + TS2 - 1) / TS2);
+    const int64_t blk0 = blockIdx.x * (int64_t)(TPB2 * TGT), blk1 = blk0 + TPB2 * TGT;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < ST2; ++s) mbar_init(&bar[s], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < ST2 && s < ntiles; ++s) {
+            mbar_expect_tx(&bar[s], TS2 * REC2 * sizeof(float));
+            tma_load_2d(sh[s], &tmap, 0, (int)(j0 + (int64_t)s * TS2), &bar[s]);
+        }
+    }
+    Coef2 cf;
+    for (int R = 0; R < 2; ++R)
+        for (int k = 0; k < 4; ++k) cf.c[R][k] = splat(c32.k[R][k]);
+    cf.kap = splat(c32.kappa);
+    cf.mk2 = splat(c32.mk2);
+    float2 X[NPK][3], XL[NPK][3];
+    int64_t tg[TGT];
+    for (int t = 0; t < TGT; ++t) tg[t] = blk0 + t * TPB2 + threadIdx.x;
+    for (int p = 0; p < NPK; ++p) {
+        int64_t a = tg[2 * p] < np ? tg[2 * p] : np - 1;
+        int64_t b = tg[2 * p + 1] < np ? tg[2 * p + 1] : np - 1;
+        for (int k = 0; k < 3; ++k) {
+            X[p][k] = make_float2(pts32[4 * a + k], pts32[4 * b + k]);
+            XL[p][k] = ACC ? make_float2(pts32lo[4 * a + k], pts32lo[4 * b + k]) : make_float2(0.f, 0.f);
+        }
+    }
+    float2 acc[NPK][NACC];
+    double accd[TGT][ACC ? NACC : 1];
+    for (int p = 0; p < NPK; ++p)
+        for (int a = 0; a < NACC; ++a) acc[p][a] = make_float2(0.f, 0.f);
+    for (int t = 0; t < TGT; ++t)
+        for (int a = 0; a < (ACC ? NACC : 1); ++a) accd[t][a] = 0.0;
+    bool ok = true;
+    for (int it = 0; it < ntiles; ++it) {
+        const int st = it % ST2;
+        const uint32_t phase = (uint32_t)((it / ST2) & 1);
+        if (!mbar_wait(&bar[st], phase, status)) { ok = false; break; }
+        const int64_t jt = j0 + (int64_t)it * TS2;
+        const bool guard = (jt < blk1 && jt + TS2 > blk0) || jt + TS2 > np;
+        if (guard) tile_x2<MODE, ACC, NPK, true>(sh[st], X, XL, acc, cf);
+        else tile_x2<MODE, ACC, NPK, false>(sh[st], X, XL, acc, cf);
+        if (ACC) {
+            for (int p = 0; p < NPK; ++p)
+                for (int a = 0; a < NACC; ++a) {
+                    accd[2 * p][a] += (double)acc[p][a].x;
+                    accd[2 * p + 1][a] += (double)acc[p][a].y;
+                    acc[p][a] = make_float2(0.f, 0.f);
+                }
+        }
+        __syncthreads();  // every thread is done with this stage
+        if (threadIdx.x == 0 && it + ST2 < ntiles) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_expect_tx(&bar[st], TS2 * REC2 * sizeof(float));
+            tma_load_2d(sh[st], &tmap, 0, (int)(j0 + (int64_t)(it + ST2) * TS2), &bar[st]);
+        }
+    }
+    if (!ok) {
+        if (threadIdx.x == 0)
+            for (int s = 0; s < ST2; ++s)
+                for (int i = 0; i < (1 << 20); ++i)
+                    if (mbar_try_wait(&bar[s], 0) || mbar_try_wait(&bar[s], 1)) break;
+        __syncthreads();
+        return;
+    }
+    for (int t = 0; t < TGT; ++t) {
+        if (tg[t] >= np) continue;
+        const int p = t >> 1, h = t & 1;
+        for (int a = 0; a < NACC; ++a) {
+            int64_t o = ((int64_t)split * NACC + a) * np + tg[t];
+            if (ACC) static_cast<double*>(part_out)[o] = accd[t][a];
+            else static_cast<float*>(part_out)[o] = h ? acc[p][a].y : acc[p][a].x;
+        }
+    }
+}
+
 // --------------------------------------------- point sums -> test functions (a4 ii)
 template <typename P>
 __global__ void k_tri_reduce(int64_t nt, int64_t np, Rule rule, int nsplit, int mode, FarPlan fp,
@@ -492,11 +723,12 @@ static int occupancy_slots(const pb_mesh* m, const void* kern, int threads) {
     return per_sm * m->ctx->num_sms;
 }
 
-static int make_tmap(const pb_mesh* m, const float* rec, CUtensorMap* map) {
+static int make_tmap(const pb_mesh* m, const float* rec, CUtensorMap* map, int rec_floats = REC32,
+                     int box_rows = TS32) {
     auto enc = (PFN_cuTensorMapEncodeTiled_v12000)m->ctx->encode_tiled;
-    cuuint64_t dims[2] = {(cuuint64_t)REC32, (cuuint64_t)m->np};
-    cuuint64_t strides[1] = {(cuuint64_t)REC32 * sizeof(float)};
-    cuuint32_t box[2] = {(cuuint32_t)REC32, (cuuint32_t)TS32};
+    cuuint64_t dims[2] = {(cuuint64_t)rec_floats, (cuuint64_t)m->np};
+    cuuint64_t strides[1] = {(cuuint64_t)rec_floats * sizeof(float)};
+    cuuint32_t box[2] = {(cuuint32_t)rec_floats, (cuuint32_t)box_rows};
     cuuint32_t es[2] = {1, 1};
     CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, (void*)rec, dims, strides, box, es,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -543,7 +775,7 @@ int apply_blockop(const pb_mesh* m, const pb_near* nf, const BlockOp& B, int pre
     FarPlan fp;
     PB_TRY(make_far_plan(B, nf->kappa, &fp));
     const int64_t nv = m->nv, nt = m->nt, np = m->np;
-    PB_TRY(ws_reserve(const_cast<pb_mesh*>(m)->ws_src, sizeof(double) * REC64 * np + 256));
+    PB_TRY(ws_reserve(const_cast<pb_mesh*>(m)->ws_src, sizeof(float) * REC2 * np + 256));  // >= REC64 doubles
     PB_TRY(ws_reserve(const_cast<pb_mesh*>(m)->ws_part, part_bytes(m) + 256));
     PB_TRY(ws_reserve(const_cast<pb_mesh*>(m)->ws_tri, sizeof(double) * 6 * nt));
     PB_TRY(ws_reserve(const_cast<pb_mesh*>(m)->ws_comb, (sizeof(double) + sizeof(float)) * 4 * m->nnz));
@@ -583,6 +815,45 @@ int apply_blockop(const pb_mesh* m, const pb_near* nf, const BlockOp& B, int pre
             ::pb::count_launch();
             tm.stop();
             k_tri_reduce<double><<<tb, 128, 0, s>>>(nt, np, rule, S, fp.mode, fp, m->tgeo, m->pts64, part, tri);
+            ::pb::count_launch();
+        } else if (m->ctx->pair_kernel == 2) {
+            float* rec = (float*)m->ws_src.ptr;
+            k_sources2<float><<<tb, 128, 0, s>>>(nt, m->Q, rule, m->tris, m->tgeo, m->pts64, m->pts32, m->pts32lo, x,
+                                                 x + nv, need_u, need_v, rec);
+            ::pb::count_launch();
+            CUtensorMap map;
+            PB_TRY(make_tmap(m, rec, &map, REC2, TS2));
+            bool acc = prec == PB_F32_ACCURATE;
+            const int tpc = TPB2 * (acc ? 2 : 4);
+            const void* kern = fp.mode == 0 ? (acc ? (const void*)k_pair32x2<0, true> : (const void*)k_pair32x2<0, false>)
+                                            : (acc ? (const void*)k_pair32x2<1, true> : (const void*)k_pair32x2<1, false>);
+            int S = choose_splits(np, tpc, TS2, occupancy_slots(m, kern, TPB2));
+            int64_t chunk = ((np + S - 1) / S + TS2 - 1) / TS2 * TS2;
+            S = (int)((np + chunk - 1) / chunk);
+            Coef32 cf;
+            for (int R = 0; R < 2; ++R)
+                for (int j = 0; j < 4; ++j) cf.k[R][j] = (float)fp.k[R][j];
+            cf.kappa = (float)fp.kappa;
+            cf.mk2 = (float)(-fp.kappa * 1.4426950408889634);
+            dim3 grid((unsigned)((np + tpc - 1) / tpc), (unsigned)S);
+            void* part = m->ws_part.ptr;
+            double ops = (fp.mode == 0 ? OPS_VK2 : OPS_VKDT) + (acc ? OPS_SPLIT : 0.0);
+            Timer tm(m->ctx, acc ? PB_KERNEL_PAIR32_ACCURATE : PB_KERNEL_PAIR32, s, (double)np * (double)np, ops);
+            if (fp.mode == 0) {
+                if (acc) k_pair32x2<0, true><<<grid, TPB2, 0, s>>>(map, np, m->pts32, m->pts32lo, cf, chunk, part, status);
+                else k_pair32x2<0, false><<<grid, TPB2, 0, s>>>(map, np, m->pts32, m->pts32lo, cf, chunk, part, status);
+            } else {
+                if (acc) k_pair32x2<1, true><<<grid, TPB2, 0, s>>>(map, np, m->pts32, m->pts32lo, cf, chunk, part, status);
+                else k_pair32x2<1, false><<<grid, TPB2, 0, s>>>(map, np, m->pts32, m->pts32lo, cf, chunk, part, status);
+            }
+            ::pb::count_launch();
+            tm.stop();
+            if (acc)
+                k_tri_reduce<double><<<tb, 128, 0, s>>>(nt, np, rule, S, fp.mode, fp, m->tgeo, m->pts64,
+                                                        (const double*)part, tri);
+            else
+                k_tri_reduce<float><<<tb, 128, 0, s>>>(nt, np, rule, S, fp.mode, fp, m->tgeo, m->pts64,
+                                                       (const float*)part, tri);
             ::pb::count_launch();
         } else {
             float* rec = (float*)m->ws_src.ptr;

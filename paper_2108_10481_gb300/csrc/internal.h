@@ -78,6 +78,7 @@ void count_launch(int n = 1);
 
 struct pb_ctx {
     int profile = 0;
+    int pair_kernel = 2;  // FP32 far-field kernel: 2 = packed f32x2 (default), 1 = scalar
     pb::KernelStats stats[3];
     int device = 0;
     int num_sms = 0;

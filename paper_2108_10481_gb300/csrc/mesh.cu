@@ -268,52 +268,70 @@ static int load(pb_ctx* ctx, const double* verts_in, int64_t nv, const int32_t* 
     }
     m->npairs = (int64_t)pairs.size();
 
-    // ---- near pattern: (tau[a], sigma[b]) over adjacent pairs; symmetric
-    std::vector<std::vector<int32_t>> rows(nv);
-    for (const int4& p : pairs)
-        for (int a = 0; a < 3; ++a)
-            for (int b = 0; b < 3; ++b) rows[T[3 * p.x + a]].push_back(T[3 * p.y + b]);
-    std::vector<int32_t> row_ptr(nv + 1, 0);
+    // ---- near pattern: row i holds every vertex of every triangle adjacent to a
+    // triangle at i (the 2-ring); built with a marker array, then sorted.
+    std::vector<int32_t> pair_ptr(nt + 1, 0);
+    for (const int4& p : pairs) pair_ptr[p.x + 1]++;
+    for (int64_t t = 0; t < nt; ++t) pair_ptr[t + 1] += pair_ptr[t];
+    std::vector<int32_t> row_ptr(nv + 1, 0), col, mark(nv, -1), colpos(nv, 0);
+    col.reserve((size_t)24 * nv);
     for (int64_t i = 0; i < nv; ++i) {
-        auto& r = rows[i];
-        std::sort(r.begin(), r.end());
-        r.erase(std::unique(r.begin(), r.end()), r.end());
-        row_ptr[i + 1] = row_ptr[i] + (int32_t)r.size();
+        size_t start = col.size();
+        for (int32_t k = v2t_ptr[i]; k < v2t_ptr[i + 1]; ++k) {
+            int32_t t = v2t[k] / 3;
+            for (int32_t p = pair_ptr[t]; p < pair_ptr[t + 1]; ++p) {
+                const int32_t* f = &T[3 * (int64_t)pairs[p].y];
+                for (int b = 0; b < 3; ++b)
+                    if (mark[f[b]] != (int32_t)i) {
+                        mark[f[b]] = (int32_t)i;
+                        col.push_back(f[b]);
+                    }
+            }
+        }
+        std::sort(col.begin() + start, col.end());
+        if (col.size() > (size_t)(((int64_t)1 << 31) - 1)) return set_error(PB_EINVAL, "near pattern too large");
+        row_ptr[i + 1] = (int32_t)col.size();
     }
-    int64_t nnz = row_ptr[nv];
-    if (nnz > ((int64_t)1 << 31) - 1) return set_error(PB_EINVAL, "near pattern too large");
+    const int64_t nnz = (int64_t)col.size();
     m->nnz = nnz;
-    std::vector<int32_t> col(nnz), tpos(nnz), diag_pos(nv, -1);
-    for (int64_t i = 0; i < nv; ++i) std::copy(rows[i].begin(), rows[i].end(), col.begin() + row_ptr[i]);
-    rows.clear();
-    rows.shrink_to_fit();
-    auto find = [&](int32_t i, int32_t j) -> int32_t {
-        const int32_t* b = col.data() + row_ptr[i];
-        const int32_t* e = col.data() + row_ptr[i + 1];
-        const int32_t* p = std::lower_bound(b, e, j);
-        return (p != e && *p == j) ? (int32_t)(p - col.data()) : -1;
-    };
+    std::vector<int32_t> tpos(nnz), diag_pos(nv, -1);
     for (int64_t i = 0; i < nv; ++i)
         for (int32_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
-            tpos[k] = find(col[k], (int32_t)i);
-            if (tpos[k] < 0) return set_error(PB_EMESH, "internal: near pattern is not symmetric");
-            if (col[k] == i) diag_pos[i] = k;
+            const int32_t j = col[k];
+            const int32_t* bg = col.data() + row_ptr[j];
+            const int32_t* en = col.data() + row_ptr[j + 1];
+            const int32_t* q = std::lower_bound(bg, en, (int32_t)i);
+            if (q == en || *q != (int32_t)i) return set_error(PB_EMESH, "internal: near pattern is not symmetric");
+            tpos[k] = (int32_t)(q - col.data());
+            if (j == i) diag_pos[i] = k;
         }
 
-    // ---- contributions of (pair, a, b) to every nonzero, in pair order
-    std::vector<int32_t> cnt(nnz + 1, 0), cidx(9 * pairs.size());
-    std::vector<int32_t> kpos(9 * pairs.size());
-    for (size_t p = 0; p < pairs.size(); ++p)
-        for (int a = 0; a < 3; ++a)
-            for (int b = 0; b < 3; ++b) {
-                int32_t k = find(T[3 * pairs[p].x + a], T[3 * pairs[p].y + b]);
-                kpos[9 * p + 3 * a + b] = k;
-                cnt[k + 1]++;
+    // ---- contributions (pair * 9 + a * 3 + b) of every adjacent pair to each
+    // nonzero, listed row by row in a fixed order (corners of the row vertex,
+    // then its triangle's pairs, then the trial corner): a counting pass and a
+    // filling pass over the same loops.
+    std::vector<int32_t> cnt(nnz + 1, 0);
+    std::vector<int32_t> cidx((size_t)9 * pairs.size());
+    for (int pass = 0; pass < 2; ++pass) {
+        std::vector<int32_t> fill;
+        if (pass == 1) {
+            for (int64_t k = 0; k < nnz; ++k) cnt[k + 1] += cnt[k];
+            fill.assign(cnt.begin(), cnt.end() - 1);
+        }
+        for (int64_t i = 0; i < nv; ++i) {
+            for (int32_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) colpos[col[k]] = k;
+            for (int32_t k = v2t_ptr[i]; k < v2t_ptr[i + 1]; ++k) {
+                const int32_t t = v2t[k] / 3, a = v2t[k] % 3;
+                for (int32_t p = pair_ptr[t]; p < pair_ptr[t + 1]; ++p) {
+                    const int32_t* f = &T[3 * (int64_t)pairs[p].y];
+                    for (int b = 0; b < 3; ++b) {
+                        const int32_t kk = colpos[f[b]];
+                        if (pass == 0) cnt[kk + 1]++;
+                        else cidx[fill[kk]++] = 9 * p + 3 * a + b;
+                    }
+                }
             }
-    for (int64_t k = 0; k < nnz; ++k) cnt[k + 1] += cnt[k];
-    {
-        std::vector<int32_t> fill(cnt.begin(), cnt.end() - 1);
-        for (size_t e = 0; e < kpos.size(); ++e) cidx[fill[kpos[e]]++] = (int32_t)e;
+        }
     }
     m->ncontrib = (int64_t)cidx.size();
 

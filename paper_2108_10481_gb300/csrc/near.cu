@@ -11,6 +11,7 @@
 //          integrated by parts; curl l_a = -e_a / (2|tau|), e_a the edge opposite a)
 // with G_int = 1/(4 pi r), G_ext = exp(-kappa r)/(4 pi r).
 #include <cmath>
+#include <cstdlib>
 
 #include "internal.h"
 
@@ -104,28 +105,43 @@ __device__ __forceinline__ double ss_map(int kind, int reg, double xi, double e1
     return jac;
 }
 
-struct PairGeom {
-    double p[3][3];  // original vertex order
+// Geometry of one triangle in the reordered frame of its singular map:
+// Q0, E1 = Q1 - Q0, E2 = Q2 - Q1 (x(s,t) = Q0 + s E1 + t E2), the inverse
+// permutation (original corner -> reordered), normal and area. Kept in shared
+// memory per warp: the lanes read it by broadcast.
+struct TriFrame {
+    double q0[3], e1[3], e2[3];
     double n[3];
     double area;
+    int inv[3];  // reordered index of original corner a
 };
 
-__device__ __forceinline__ void load_tri(const double* verts, const int32_t* tris, const double* tgeo,
-                                         int t, PairGeom& g) {
+__device__ void make_frame(const double* verts, const int32_t* tris, const double* tgeo, int t, int perm,
+                           TriFrame& f) {
+    double p[3][3];
     for (int a = 0; a < 3; ++a)
-        for (int k = 0; k < 3; ++k) g.p[a][k] = verts[3 * (int64_t)tris[3 * (int64_t)t + a] + k];
-    for (int k = 0; k < 3; ++k) g.n[k] = tgeo[16 * (int64_t)t + k];
-    g.area = tgeo[16 * (int64_t)t + 3];
+        for (int k = 0; k < 3; ++k) p[a][k] = verts[3 * (int64_t)tris[3 * (int64_t)t + a] + k];
+    int o[3] = {perm & 3, (perm >> 2) & 3, (perm >> 4) & 3};  // original corner of reordered k
+    for (int k = 0; k < 3; ++k) {
+        f.q0[k] = p[o[0]][k];
+        f.e1[k] = p[o[1]][k] - p[o[0]][k];
+        f.e2[k] = p[o[2]][k] - p[o[1]][k];
+        f.n[k] = tgeo[16 * (int64_t)t + k];
+    }
+    f.area = tgeo[16 * (int64_t)t + 3];
+    for (int k = 0; k < 3; ++k) f.inv[o[k]] = k;
 }
 
-// reference (s,t) on the reordered triangle -> point and original barycentrics
-__device__ __forceinline__ void ref_to_phys(const PairGeom& g, int perm, double s, double t, double* x,
-                                            double* lam) {
-    double mu[3] = {1.0 - s, s - t, t};
-    lam[perm & 3] = mu[0];
-    lam[(perm >> 2) & 3] = mu[1];
-    lam[(perm >> 4) & 3] = mu[2];
-    for (int k = 0; k < 3; ++k) x[k] = lam[0] * g.p[0][k] + lam[1] * g.p[1][k] + lam[2] * g.p[2][k];
+// reference (s,t) in the reordered frame -> point and original barycentrics
+__device__ __forceinline__ void frame_point(const TriFrame& f, double s, double t, double* x, double* lam) {
+    const double mu[3] = {1.0 - s, s - t, t};
+    for (int a = 0; a < 3; ++a) lam[a] = mu[f.inv[a]];
+    for (int k = 0; k < 3; ++k) x[k] = f.q0[k] + s * f.e1[k] + t * f.e2[k];
+}
+// original corner a of the triangle
+__device__ __forceinline__ double corner(const TriFrame& f, int a, int k) {
+    int r = f.inv[a];
+    return f.q0[k] + (r >= 1 ? f.e1[k] : 0.0) + (r >= 2 ? f.e2[k] : 0.0);
 }
 
 // 38 accumulators: SL[9], SY[9], KL[9], KY[9], sum w G_L, sum w G_Y
@@ -134,23 +150,26 @@ __device__ __forceinline__ void ref_to_phys(const PairGeom& g, int perm, double 
 __device__ __forceinline__ void accum_point(double* acc, double w, const double* x, const double* y,
                                             const double* ny, const double* lx, const double* ly,
                                             double kappa) {
-    double d0 = x[0] - y[0], d1 = x[1] - y[1], d2 = x[2] - y[2];
-    double r2 = d0 * d0 + d1 * d1 + d2 * d2;
-    double r = sqrt(r2);
-    double gl = 1.0 / (4.0 * M_PI * r);
-    double ek = exp(-kappa * r);
-    double gy = ek * gl;
-    double dn = d0 * ny[0] + d1 * ny[1] + d2 * ny[2];
-    double kl = gl * dn / r2;
-    double ky = kl * ek * (1.0 + kappa * r);
-    for (int a = 0; a < 3; ++a)
+    const double d0 = x[0] - y[0], d1 = x[1] - y[1], d2 = x[2] - y[2];
+    const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+    const double rinv = rsqrt(r2);
+    const double r = r2 * rinv;
+    const double gl = rinv * 0.07957747154594767;  // 1 / (4 pi r)
+    const double ek = exp(-kappa * r);
+    const double gy = ek * gl;
+    const double dn = d0 * ny[0] + d1 * ny[1] + d2 * ny[2];
+    const double kl = gl * dn * rinv * rinv;
+    const double ky = kl * ek * (1.0 + kappa * r);
+    for (int a = 0; a < 3; ++a) {
+        const double wa = w * lx[a];
         for (int b = 0; b < 3; ++b) {
-            double ll = w * lx[a] * ly[b];
+            const double ll = wa * ly[b];
             acc[3 * a + b] += gl * ll;
             acc[9 + 3 * a + b] += gy * ll;
             acc[18 + 3 * a + b] += kl * ll;
             acc[27 + 3 * a + b] += ky * ll;
         }
+    }
     acc[36] += w * gl;
     acc[37] += w * gy;
 }
@@ -161,8 +180,8 @@ __device__ __forceinline__ double warp_sum(double v) {
 }
 
 // Expand 38 reduced accumulators into six 3x3 blocks (V_L, K_L, D_L, V_Y, K_Y, D_Y).
-__device__ void expand_blocks(const double* acc, const PairGeom& A, const PairGeom& B,
-                              const double* tgeoA, const double* tgeoB, double kappa, double* out) {
+__device__ void expand_blocks(const double* acc, const TriFrame& A, const TriFrame& B, const double* tgeoA,
+                              const double* tgeoB, double kappa, double* out) {
     double nn = A.n[0] * B.n[0] + A.n[1] * B.n[1] + A.n[2] * B.n[2];
     double f = 1.0 / (4.0 * A.area * B.area);
     for (int a = 0; a < 3; ++a)
@@ -180,37 +199,42 @@ __device__ void expand_blocks(const double* acc, const PairGeom& A, const PairGe
         }
 }
 
+constexpr int NEAR_THREADS = 128;
+
 // One warp per adjacent pair. Writes ss[p][54] (regularised) and far[p][54]
 // (far rule, identical points excluded).
-__global__ void k_near_pairs(const double* __restrict__ verts, const int32_t* __restrict__ tris,
-                             const double* __restrict__ tgeo, const int4* __restrict__ pairs,
-                             int64_t npairs, Gauss gq, Rule rule, double kappa,
-                             double* __restrict__ ss_out, double* __restrict__ far_out) {
-    int lane = threadIdx.x & 31;
-    int64_t p = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    if (p >= npairs) return;
-    int4 pr = pairs[p];
-    PairGeom A, B;
-    load_tri(verts, tris, tgeo, pr.x, A);
-    load_tri(verts, tris, tgeo, pr.y, B);
-    int kind = pr.z;
-    int permA = pr.w & 63, permB = (pr.w >> 6) & 63;
-    int nreg = kind == 2 ? 2 : 6;
-    int n = gq.n;
-    int n2 = n * n, n4 = n2 * n2;
-    double jac_ab = (2.0 * A.area) * (2.0 * B.area);
+template <int MINB>
+__global__ void __launch_bounds__(NEAR_THREADS, MINB)
+k_near_pairs(const double* __restrict__ verts, const int32_t* __restrict__ tris, const double* __restrict__ tgeo,
+             const int4* __restrict__ pairs, int64_t npairs, Gauss gq, Rule rule, double kappa,
+             double* __restrict__ ss_out, double* __restrict__ far_out) {
+    __shared__ TriFrame frames[NEAR_THREADS / 32][2];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t p = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (p >= npairs) return;  // whole warps leave together
+    const int4 pr = pairs[p];
+    TriFrame& A = frames[wid][0];
+    TriFrame& B = frames[wid][1];
+    if (lane == 0) make_frame(verts, tris, tgeo, pr.x, pr.w & 63, A);
+    if (lane == 1) make_frame(verts, tris, tgeo, pr.y, (pr.w >> 6) & 63, B);
+    __syncwarp();
+    const int kind = pr.z;
+    const int nreg = kind == 2 ? 2 : 6;
+    const int n = gq.n;
+    const int n2 = n * n, n4 = n2 * n2;
+    const double jac_ab = (2.0 * A.area) * (2.0 * B.area);
     double acc[NACC_NEAR];
     for (int k = 0; k < NACC_NEAR; ++k) acc[k] = 0.0;
     for (int idx = lane; idx < nreg * n4; idx += 32) {
-        int reg = idx / n4;
-        int r = idx - reg * n4;
-        int i0 = r / (n2 * n), i1 = (r / n2) % n, i2 = (r / n) % n, i3 = r % n;
+        const int reg = idx / n4;
+        const int r = idx - reg * n4;
+        const int i0 = r / (n2 * n), i1 = (r / n2) % n, i2 = (r / n) % n, i3 = r % n;
         double sx, tx, sy, ty;
-        double jac = ss_map(kind, reg, gq.x[i0], gq.x[i1], gq.x[i2], gq.x[i3], sx, tx, sy, ty);
-        double w = gq.w[i0] * gq.w[i1] * gq.w[i2] * gq.w[i3] * jac * jac_ab;
+        const double jac = ss_map(kind, reg, gq.x[i0], gq.x[i1], gq.x[i2], gq.x[i3], sx, tx, sy, ty);
+        const double w = gq.w[i0] * gq.w[i1] * gq.w[i2] * gq.w[i3] * jac * jac_ab;
         double x[3], y[3], lx[3], ly[3];
-        ref_to_phys(A, permA, sx, tx, x, lx);
-        ref_to_phys(B, permB, sy, ty, y, ly);
+        frame_point(A, sx, tx, x, lx);
+        frame_point(B, sy, ty, y, ly);
         accum_point(acc, w, x, y, B.n, lx, ly, kappa);
     }
     for (int k = 0; k < NACC_NEAR; ++k) acc[k] = warp_sum(acc[k]);
@@ -218,16 +242,16 @@ __global__ void k_near_pairs(const double* __restrict__ verts, const int32_t* __
         expand_blocks(acc, A, B, tgeo + 16 * (int64_t)pr.x, tgeo + 16 * (int64_t)pr.y, kappa, ss_out + 54 * p);
     // far rule on the same pair (what the pair kernel adds for it)
     for (int k = 0; k < NACC_NEAR; ++k) acc[k] = 0.0;
-    int Q = rule.Q;
+    const int Q = rule.Q;
     for (int idx = lane; idx < Q * Q; idx += 32) {
-        int i = idx / Q, j = idx % Q;
+        const int i = idx / Q, j = idx % Q;
         if (kind == 0 && i == j) continue;  // identical points are skipped by the pair kernel
         double x[3], y[3];
         for (int k = 0; k < 3; ++k) {
-            x[k] = rule.l[i][0] * A.p[0][k] + rule.l[i][1] * A.p[1][k] + rule.l[i][2] * A.p[2][k];
-            y[k] = rule.l[j][0] * B.p[0][k] + rule.l[j][1] * B.p[1][k] + rule.l[j][2] * B.p[2][k];
+            x[k] = rule.l[i][0] * corner(A, 0, k) + rule.l[i][1] * corner(A, 1, k) + rule.l[i][2] * corner(A, 2, k);
+            y[k] = rule.l[j][0] * corner(B, 0, k) + rule.l[j][1] * corner(B, 1, k) + rule.l[j][2] * corner(B, 2, k);
         }
-        double w = rule.w[i] * A.area * rule.w[j] * B.area;
+        const double w = rule.w[i] * A.area * rule.w[j] * B.area;
         accum_point(acc, w, x, y, B.n, rule.l[i], rule.l[j], kappa);
     }
     for (int k = 0; k < NACC_NEAR; ++k) acc[k] = warp_sum(acc[k]);
@@ -291,10 +315,20 @@ static int build(pb_ctx* ctx, const pb_mesh* m, double kappa, pb_near* nf, cudaS
     if (rc == PB_OK) rc = dev_alloc((void**)&row_of, sizeof(int32_t) * m->nnz);
     if (rc == PB_OK) {
         Gauss gq = gauss01(m->n_ss);
-        int threads = 128;  // 4 pairs per block
+        int threads = NEAR_THREADS;  // one warp per pair
         int64_t blocks = (m->npairs * 32 + threads - 1) / threads;
-        k_near_pairs<<<(unsigned)blocks, threads, 0, s>>>(m->verts, m->tris, m->tgeo, m->pairs, m->npairs,
-                                                         gq, mesh_rule(m), kappa, ss, far); ::pb::count_launch();
+        const char* mb = getenv("PBBEM_NEAR_MINB");
+        const int minb = mb ? atoi(mb) : 3;
+        if (minb == 2)
+            k_near_pairs<2><<<(unsigned)blocks, threads, 0, s>>>(m->verts, m->tris, m->tgeo, m->pairs, m->npairs,
+                                                                gq, mesh_rule(m), kappa, ss, far);
+        else if (minb == 4)
+            k_near_pairs<4><<<(unsigned)blocks, threads, 0, s>>>(m->verts, m->tris, m->tgeo, m->pairs, m->npairs,
+                                                                gq, mesh_rule(m), kappa, ss, far);
+        else
+            k_near_pairs<3><<<(unsigned)blocks, threads, 0, s>>>(m->verts, m->tris, m->tgeo, m->pairs, m->npairs,
+                                                                gq, mesh_rule(m), kappa, ss, far);
+        ::pb::count_launch();
         k_row_of<<<(unsigned)((m->nv + 255) / 256), 256, 0, s>>>(m->nv, m->row_ptr, row_of); ::pb::count_launch();
         cudaMemsetAsync(nf->diag, 0, sizeof(double) * N_VALS * m->nv, s);
         k_near_entries<<<(unsigned)((m->nnz + 255) / 256), 256, 0, s>>>(
