@@ -14,7 +14,9 @@ Workloads (all seeded, all synthetic):
     (see ``synth.molecule``), standing in for the PDB molecules with
     solvent-excluded surfaces used in the paper's scaling study.
 """
-from .icosphere import icosphere
+from .icosphere import icosphere, uv_ellipsoid
 from .charges import ball_charges, kirkwood_sphere, multi_charge_sphere
+from .molecule import protein_like_500, protein_like_5000, serving_stream, synthetic_molecule
 
-__all__ = ["icosphere", "ball_charges", "kirkwood_sphere", "multi_charge_sphere"]
+__all__ = ["icosphere", "uv_ellipsoid", "ball_charges", "kirkwood_sphere", "multi_charge_sphere",
+           "protein_like_500", "protein_like_5000", "serving_stream", "synthetic_molecule"]
