@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--case", type=int, default=10)
     ap.add_argument("--precision", default="mixed", choices=["mixed", "f64"])
     ap.add_argument("--level", type=int, default=5)
+    ap.add_argument("--workload", default="sphere", choices=["sphere", "protein500", "protein5000"],
+                    help="sphere: the multi-charge sphere (default); proteinN: synthetic N-atom molecule")
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-baseline", action="store_true")
@@ -56,9 +58,25 @@ def parse():
     return ap.parse_args()
 
 
-def workload(level):
+def workload(level, name="sphere"):
+    if name == "protein500":
+        from synth import protein_like_500
+        v, t, xq, q, _ = protein_like_500()
+        return v, t, xq, q
+    if name == "protein5000":
+        from synth import protein_like_5000
+        v, t, xq, q, _ = protein_like_5000()
+        return v, t, xq, q
     v, t, xq, q = multi_charge_sphere(level=level, radius=10.0, n_charges=20, charge_radius=8.0, seed=2)
     return v, t, xq, q
+
+
+def workload_text(args, v, t, xq):
+    if args.workload == "sphere":
+        return ("multi-charge sphere: icosphere level %d (%d verts, %d tris), radius 10 A, 20 charges uniform in "
+                "r<=8 A, q~U[-1,1] e, eps 4/80, kappa 0.125" % (args.level, v.shape[0], t.shape[0]))
+    return ("synthetic protein-like molecule: %d atoms on a seeded random walk, Gaussian surface at ~4 verts/A^2 "
+            "(%d verts, %d tris), eps 4/80, kappa 0.125" % (xq.shape[0], v.shape[0], t.shape[0]))
 
 
 # ------------------------------------------------------------------ clocks
@@ -152,7 +170,7 @@ def oracle_sample(v, t, xq, q, case, rows=48):
 def run_reference(args, rank):
     if rank != 0:
         return
-    v, t, xq, q = workload(args.level)
+    v, t, xq, q = workload(args.level, args.workload)
     times = []
     for i in range(args.warmup + args.steps):
         total, cores, text = oracle_sample(v, t, xq, q, args.case, rows=16 if i < args.warmup else 48)
@@ -163,8 +181,8 @@ def run_reference(args, rank):
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "multi-charge sphere: icosphere level 5 (10242 verts, 20480 tris), 20 charges, "
-                                   f"case {args.case}, FP64 CPU oracle", "case": args.case},
+            "config": {"workload": workload_text(args, v, t, xq) + f"; case {args.case}; FP64 CPU oracle",
+                       "case": args.case},
             "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": text},
             "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -179,7 +197,7 @@ def run_ours(args, rank, world, local_rank):
 
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
-    v, t, xq, q = workload(args.level)
+    v, t, xq, q = workload(args.level, args.workload)
     form, prec = pb.CASES[args.case]
     P = pb.Params(4.0, 80.0, 0.125)
     precision = pb.PB_MIXED if args.precision == "mixed" else pb.PB_F64
@@ -317,9 +335,7 @@ def run_ours(args, rank, world, local_rank):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
-        "config": {"workload": "multi-charge sphere: icosphere level %d (%d verts, %d tris), radius 10 A, 20 charges "
-                               "uniform in r<=8 A, q~U[-1,1] e, eps 4/80, kappa 0.125" % (args.level, v.shape[0],
-                                                                                         t.shape[0]),
+        "config": {"workload": workload_text(args, v, t, xq),
                    "case": args.case, "formulation": form, "preconditioner": prec, "precision": args.precision,
                    "gmres_tol": args.tol, "quadrature": "far 6-point degree-4 rule, singular 4^4 Gauss per region",
                    "points": npts, "l2": "flushed (256 MB write) before every timed step",
