@@ -257,6 +257,59 @@ int pb_solvation_energy(pb_ctx* ctx, const double* verts, int64_t n_verts, const
                         const pb_solve_opts* opts, double* dG_kcal, pb_solve_info* info,
                         void* stream);
 
+/* ---- a11: request server (continuous batching) --------------------------- */
+/* Serving many molecules on one GPU. Not in the paper: its solves run one at
+ * a time; this is the batched form of the same path (pb_mesh_load ...
+ * pb_energy per request) with results equal to solving each request alone. */
+typedef struct pb_server pb_server;
+
+typedef struct {
+    const double* verts;   /* host, n_verts x 3 (copied at submit) */
+    int64_t n_verts;
+    const int32_t* tris;   /* host, n_tris x 3, counter-clockwise seen from outside */
+    int64_t n_tris;
+    const double* xq;      /* host, n_q x 3 charge positions */
+    const double* q;       /* host, n_q charges */
+    int64_t n_q;
+    pb_params params;
+    int form;              /* PB_DIRECT_INT ... PB_LU */
+    int precond;           /* PB_PC_* */
+    pb_solve_opts opts;    /* tol, max_it, restart (Krylov basis size; 0 = max_it), precision, ... */
+    pb_quad_plan plan;     /* {0, 0} = the default {6, 4} */
+    uint64_t tag;          /* the caller's identifier, returned in the result */
+} pb_request;
+
+typedef struct {
+    uint64_t tag;
+    int status;            /* PB_OK, PB_ENOCONV (best iterate used), or the error of its setup */
+    int iters;             /* GMRES iterations */
+    int outer_iters;       /* refinement sweeps (1 for FP64) */
+    double dG_kcal;        /* polar solvation energy */
+    double dG_paper;
+    double rel_residual;   /* final relative preconditioned residual */
+    double latency_ms;     /* submit -> result */
+    double queue_ms;       /* submit -> set up and ready to iterate */
+} pb_result;
+
+/* Create a server on ctx's device that keeps at most max_active requests
+ * resident and admits a request only while the sum of the admitted requests'
+ * device footprints (estimated from their sizes, Krylov basis included) stays
+ * within hbm_budget_bytes. Starts one host thread for admission. */
+int pb_server_create(pb_ctx* ctx, int64_t hbm_budget_bytes, int max_active, pb_server** out);
+/* Stop the admission thread and free every resident request. */
+int pb_server_destroy(pb_server* srv);
+/* Queue a request (its arrays are copied). PB_ENOMEM if it alone exceeds the
+ * budget, PB_EINVAL for a malformed request. Thread-safe. */
+int pb_submit(pb_server* srv, const pb_request* req);
+/* One scheduling step: move newly set-up requests into the active set and
+ * advance every active request by one GMRES step, all their operator
+ * applications in one batched pair-kernel launch per row mode; finished
+ * requests compute their energy and release their memory. Returns at once
+ * when nothing is active. Call from one thread. */
+int pb_server_step(pb_server* srv, int* n_active, int* n_pending);
+/* Move up to max finished results into out; *n_out = how many. Thread-safe. */
+int pb_poll(pb_server* srv, pb_result* out, int max, int* n_out);
+
 /* ---- measurement ---------------------------------------------------------- */
 /* kernel families timed by pb_profile */
 #define PB_KERNEL_PAIR32 0          /* FP32 far-field pair kernel (inner solves) */

@@ -244,6 +244,51 @@ def pb_energy(ctx: Ctx, mesh: Mesh, x: torch.Tensor, form, xq: torch.Tensor, q: 
     return a.value, b.value
 
 
+class Server(_Handle):
+    """Continuous-batching request server (see pb_server_create in include/pbbem.h)."""
+    _free = "pb_server_destroy"
+
+
+def pb_server_create(ctx: Ctx, hbm_budget_bytes: int, max_active: int = 64) -> Server:
+    h = ctypes.c_void_p()
+    _check(N.load().pb_server_create(ctx.ptr, int(hbm_budget_bytes), int(max_active), ctypes.byref(h)))
+    return Server(h.value, ctx)
+
+
+def pb_submit(srv: Server, verts, tris, xq, q, params: Params, form, precond, opts=None, tag: int = 0,
+              far_q: int = 6, n_ss: int = 4):
+    """Queue one molecule (host arrays, copied by the library)."""
+    v = np.ascontiguousarray(verts, dtype=np.float64)
+    t = np.ascontiguousarray(tris, dtype=np.int32)
+    x = np.ascontiguousarray(xq, dtype=np.float64).reshape(-1, 3)
+    qq = np.ascontiguousarray(q, dtype=np.float64).reshape(-1)
+    r = N.pb_request()
+    r.verts, r.n_verts = v.ctypes.data, v.shape[0]
+    r.tris, r.n_tris = t.ctypes.data, t.shape[0]
+    r.xq, r.q, r.n_q = x.ctypes.data, qq.ctypes.data, qq.shape[0]
+    r.params = params.c()
+    r.form, r.precond = _form(form), _prec(precond)
+    r.opts = opts if opts is not None else solve_opts()
+    r.plan = N.pb_quad_plan(far_q, n_ss)
+    r.tag = int(tag)
+    _check(N.load().pb_submit(srv.ptr, ctypes.byref(r)))
+
+
+def pb_server_step(srv: Server):
+    """One scheduling step; returns (n_active, n_pending)."""
+    a, p = ctypes.c_int(), ctypes.c_int()
+    _check(N.load().pb_server_step(srv.ptr, ctypes.byref(a), ctypes.byref(p)))
+    return a.value, p.value
+
+
+def pb_poll(srv: Server, max_results: int = 1024):
+    """Finished results as a list of dicts."""
+    buf = (N.pb_result * max_results)()
+    n = ctypes.c_int()
+    _check(N.load().pb_poll(srv.ptr, buf, max_results, ctypes.byref(n)))
+    return [{k: getattr(buf[i], k) for k, _ in N.pb_result._fields_} for i in range(n.value)]
+
+
 def pb_solvation_energy(ctx: Ctx, verts: np.ndarray, tris: np.ndarray, xq: np.ndarray, q: np.ndarray,
                         params: Params, form, precond, far_q: int = 6, n_ss: int = 4, opts=None, stream=None):
     """Whole path from host arrays; returns (dG kcal/mol, info dict)."""

@@ -14,7 +14,7 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpbbem.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INC, "-I" + SRC]
-SOURCES = ["api.cu", "mesh.cu", "near.cu", "far.cu", "form.cu", "solve.cu", "rhs.cu"]
+SOURCES = ["api.cu", "mesh.cu", "near.cu", "far.cu", "form.cu", "solve.cu", "rhs.cu", "serve.cu"]
 
 
 def nvcc() -> str:

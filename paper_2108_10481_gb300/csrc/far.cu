@@ -546,6 +546,131 @@ __global__ void __launch_bounds__(TPB2) k_pair32x2(const __grid_constant__ CUten
     }
 }
 
+// ------------------------- batched FP32 pair kernel: many meshes in one launch
+// Work item = (job, target block, source split); the per-job split count and
+// chunk are the ones the single-mesh path chooses, so every job's partial sums
+// are bit-identical to a launch for that mesh alone. Source tiles are staged
+// with plain bulk copies (no tensor map per job); every job's record array is
+// padded with zero records to whole tiles.
+struct PairJob {
+    const float* rec;
+    const float* pts32;
+    const float* pts32lo;
+    void* part;
+    int64_t np;
+    int64_t chunk;
+    Coef32 cf;
+    int nsplit;
+    int pad;
+};
+struct PairItem {
+    int job;
+    int tb;
+    int split;
+    int pad;
+};
+
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"((uint64_t)src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+template <int MODE, bool ACC>
+__global__ void __launch_bounds__(TPB2) k_pair32x2_multi(const PairJob* __restrict__ jobs,
+                                                         const PairItem* __restrict__ items,
+                                                         int* __restrict__ status) {
+    constexpr int NACC = MODE == 0 ? 2 : 10;
+    constexpr int NPK = ACC ? 1 : 2;
+    constexpr int TGT = 2 * NPK;
+    __shared__ __align__(128) float sh[ST2][TS2 * REC2];
+    __shared__ __align__(8) uint64_t bar[ST2];
+    const PairItem it0 = items[blockIdx.x];
+    const PairJob& J = jobs[it0.job];
+    const int64_t np = J.np;
+    const int split = it0.split;
+    const int64_t j0 = split * J.chunk;
+    const int64_t j1 = min(np, j0 + J.chunk);
+    const int ntiles = (int)((j1 - j0 + TS2 - 1) / TS2);
+    const int64_t blk0 = (int64_t)it0.tb * (TPB2 * TGT), blk1 = blk0 + TPB2 * TGT;
+    const uint32_t tile_bytes = TS2 * REC2 * sizeof(float);
+
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < ST2; ++st) mbar_init(&bar[st], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int st = 0; st < ST2 && st < ntiles; ++st) {
+            mbar_expect_tx(&bar[st], tile_bytes);
+            bulk_load(sh[st], J.rec + (j0 + (int64_t)st * TS2) * REC2, tile_bytes, &bar[st]);
+        }
+    }
+    Coef2 cf;
+    for (int R = 0; R < 2; ++R)
+        for (int k = 0; k < 4; ++k) cf.c[R][k] = splat(J.cf.k[R][k]);
+    cf.kap = splat(J.cf.kappa);
+    cf.mk2 = splat(J.cf.mk2);
+    float2 X[NPK][3], XL[NPK][3];
+    int64_t tg[TGT];
+    for (int t = 0; t < TGT; ++t) tg[t] = blk0 + t * TPB2 + threadIdx.x;
+    for (int p = 0; p < NPK; ++p) {
+        int64_t a = tg[2 * p] < np ? tg[2 * p] : np - 1;
+        int64_t b = tg[2 * p + 1] < np ? tg[2 * p + 1] : np - 1;
+        for (int k = 0; k < 3; ++k) {
+            X[p][k] = make_float2(J.pts32[4 * a + k], J.pts32[4 * b + k]);
+            XL[p][k] = ACC ? make_float2(J.pts32lo[4 * a + k], J.pts32lo[4 * b + k]) : make_float2(0.f, 0.f);
+        }
+    }
+    float2 acc[NPK][NACC];
+    double accd[TGT][ACC ? NACC : 1];
+    for (int p = 0; p < NPK; ++p)
+        for (int a = 0; a < NACC; ++a) acc[p][a] = make_float2(0.f, 0.f);
+    for (int t = 0; t < TGT; ++t)
+        for (int a = 0; a < (ACC ? NACC : 1); ++a) accd[t][a] = 0.0;
+    bool ok = true;
+    for (int it = 0; it < ntiles; ++it) {
+        const int st = it % ST2;
+        const uint32_t phase = (uint32_t)((it / ST2) & 1);
+        if (!mbar_wait(&bar[st], phase, status)) { ok = false; break; }
+        const int64_t jt = j0 + (int64_t)it * TS2;
+        const bool guard = (jt < blk1 && jt + TS2 > blk0) || jt + TS2 > np;
+        if (guard) tile_x2<MODE, ACC, NPK, true>(sh[st], X, XL, acc, cf);
+        else tile_x2<MODE, ACC, NPK, false>(sh[st], X, XL, acc, cf);
+        if (ACC) {
+            for (int p = 0; p < NPK; ++p)
+                for (int a = 0; a < NACC; ++a) {
+                    accd[2 * p][a] += (double)acc[p][a].x;
+                    accd[2 * p + 1][a] += (double)acc[p][a].y;
+                    acc[p][a] = make_float2(0.f, 0.f);
+                }
+        }
+        __syncthreads();
+        if (threadIdx.x == 0 && it + ST2 < ntiles) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_expect_tx(&bar[st], tile_bytes);
+            bulk_load(sh[st], J.rec + (j0 + (int64_t)(it + ST2) * TS2) * REC2, tile_bytes, &bar[st]);
+        }
+    }
+    if (!ok) {
+        if (threadIdx.x == 0)
+            for (int st = 0; st < ST2; ++st)
+                for (int i = 0; i < (1 << 20); ++i)
+                    if (mbar_try_wait(&bar[st], 0) || mbar_try_wait(&bar[st], 1)) break;
+        __syncthreads();
+        return;
+    }
+    for (int t = 0; t < TGT; ++t) {
+        if (tg[t] >= np) continue;
+        const int p = t >> 1, h = t & 1;
+        for (int a = 0; a < NACC; ++a) {
+            int64_t o = ((int64_t)split * NACC + a) * np + tg[t];
+            if (ACC) static_cast<double*>(J.part)[o] = accd[t][a];
+            else static_cast<float*>(J.part)[o] = h ? acc[p][a].y : acc[p][a].x;
+        }
+    }
+}
+
 // --------------------------------------------- point sums -> test functions (a4 ii)
 template <typename P>
 __global__ void k_tri_reduce(int64_t nt, int64_t np, Rule rule, int nsplit, int mode, FarPlan fp,
@@ -765,8 +890,6 @@ struct Timer {
     }
 };
 
-// workspace layout helpers
-static size_t part_bytes(const pb_mesh* m) { return sizeof(double) * 32 * 10 * (size_t)m->np; }
 
 int apply_blockop(const pb_mesh* m, const pb_near* nf, const BlockOp& B, int prec, const double* x, double* y,
                   cudaStream_t s) {
@@ -776,7 +899,6 @@ int apply_blockop(const pb_mesh* m, const pb_near* nf, const BlockOp& B, int pre
     PB_TRY(make_far_plan(B, nf->kappa, &fp));
     const int64_t nv = m->nv, nt = m->nt, np = m->np;
     PB_TRY(ws_reserve(const_cast<pb_mesh*>(m)->ws_src, sizeof(float) * REC2 * np + 256));  // >= REC64 doubles
-    PB_TRY(ws_reserve(const_cast<pb_mesh*>(m)->ws_part, part_bytes(m) + 256));
     PB_TRY(ws_reserve(const_cast<pb_mesh*>(m)->ws_tri, sizeof(double) * 6 * nt));
     PB_TRY(ws_reserve(const_cast<pb_mesh*>(m)->ws_comb, (sizeof(double) + sizeof(float)) * 4 * m->nnz));
     double* tri = (double*)m->ws_tri.ptr;
@@ -808,6 +930,7 @@ int apply_blockop(const pb_mesh* m, const pb_near* nf, const BlockOp& B, int pre
                 for (int j = 0; j < 4; ++j) cf.k[R][j] = fp.k[R][j];
             cf.kappa = fp.kappa;
             dim3 grid((unsigned)((np + TPB64 - 1) / TPB64), (unsigned)S);
+            PB_TRY(ws_reserve(const_cast<pb_mesh*>(m)->ws_part, sizeof(double) * (size_t)S * nacc * np));
             double* part = (double*)m->ws_part.ptr;
             Timer tm(m->ctx, PB_KERNEL_PAIR64, s, (double)np * (double)np, fp.mode == 0 ? OPS_VK2 : OPS_VKDT);
             if (fp.mode == 0) k_pair64<0><<<grid, TPB64, 0, s>>>(np, m->pts64, rec, cf, chunk, part);
@@ -836,6 +959,7 @@ int apply_blockop(const pb_mesh* m, const pb_near* nf, const BlockOp& B, int pre
             cf.kappa = (float)fp.kappa;
             cf.mk2 = (float)(-fp.kappa * 1.4426950408889634);
             dim3 grid((unsigned)((np + tpc - 1) / tpc), (unsigned)S);
+            PB_TRY(ws_reserve(const_cast<pb_mesh*>(m)->ws_part, (acc ? sizeof(double) : sizeof(float)) * (size_t)S * nacc * np));
             void* part = m->ws_part.ptr;
             double ops = (fp.mode == 0 ? OPS_VK2 : OPS_VKDT) + (acc ? OPS_SPLIT : 0.0);
             Timer tm(m->ctx, acc ? PB_KERNEL_PAIR32_ACCURATE : PB_KERNEL_PAIR32, s, (double)np * (double)np, ops);
@@ -874,6 +998,7 @@ int apply_blockop(const pb_mesh* m, const pb_near* nf, const BlockOp& B, int pre
             cf.kappa = (float)fp.kappa;
             cf.mk2 = (float)(-fp.kappa * 1.4426950408889634);
             dim3 grid((unsigned)((np + TPB32 * TGT32 - 1) / (TPB32 * TGT32)), (unsigned)S);
+            PB_TRY(ws_reserve(const_cast<pb_mesh*>(m)->ws_part, (acc ? sizeof(double) : sizeof(float)) * (size_t)S * nacc * np));
             void* part = m->ws_part.ptr;
             double ops = (fp.mode == 0 ? OPS_VK2 : OPS_VKDT) + (acc ? OPS_SPLIT : 0.0);
             Timer tm(m->ctx, acc ? PB_KERNEL_PAIR32_ACCURATE : PB_KERNEL_PAIR32, s, (double)np * (double)np, ops);
@@ -894,7 +1019,6 @@ int apply_blockop(const pb_mesh* m, const pb_near* nf, const BlockOp& B, int pre
                                                        (const float*)part, tri);
             ::pb::count_launch();
         }
-        (void)nacc;
     }
     unsigned gb = (unsigned)((nv * 8 + 255) / 256);
     if (prec == PB_F32)
@@ -906,6 +1030,154 @@ int apply_blockop(const pb_mesh* m, const pb_near* nf, const BlockOp& B, int pre
     ::pb::count_launch();
     PB_CUDA(cudaGetLastError());
     return PB_OK;
+}
+
+// y_j = B_j x_j for many meshes: sources per job, one packed pair-kernel
+// launch per row mode over all jobs' work items, then each job's reduction
+// and gather. prec: PB_F32 or PB_F32_ACCURATE (PB_F64 runs the jobs one by one).
+int apply_blockops_batched(const std::vector<FarJob>& jobs, int prec, BatchScratch& bs, cudaStream_t s) {
+    if (jobs.empty()) return PB_OK;
+    if (prec == PB_F64) {
+        for (const FarJob& j : jobs) PB_TRY(apply_blockop(j.m, j.nf, j.B, PB_F64, j.x, j.y, s));
+        return PB_OK;
+    }
+    if (prec != PB_F32 && prec != PB_F32_ACCURATE) return set_error(PB_EINVAL, "unknown precision %d", prec);
+    const bool acc = prec == PB_F32_ACCURATE;
+    const int tpc = TPB2 * (acc ? 2 : 4);
+    struct Prep {
+        FarPlan fp;
+        int S;
+        int64_t chunk;
+        double* tri;
+        double* c64;
+        float* c32;
+    };
+    std::vector<Prep> prep(jobs.size());
+    std::vector<PairJob> hjobs[2];
+    std::vector<int> hjob_of[2];
+    for (size_t k = 0; k < jobs.size(); ++k) {
+        const FarJob& J = jobs[k];
+        pb_mesh* m = const_cast<pb_mesh*>(J.m);
+        Prep& P = prep[k];
+        PB_TRY(make_far_plan(J.B, J.nf->kappa, &P.fp));
+        const int64_t nt = m->nt, np = m->np;
+        const int64_t np_pad = (np + TS2 - 1) / TS2 * TS2;
+        PB_TRY(ws_reserve(m->ws_src, sizeof(float) * REC2 * np_pad + 256));
+        PB_TRY(ws_reserve(m->ws_tri, sizeof(double) * 6 * nt));
+        PB_TRY(ws_reserve(m->ws_comb, (sizeof(double) + sizeof(float)) * 4 * m->nnz));
+        P.tri = (double*)m->ws_tri.ptr;
+        P.c64 = (double*)m->ws_comb.ptr;
+        P.c32 = (float*)(P.c64 + 4 * m->nnz);
+        PB_TRY(combine_near(m, J.nf, J.B, P.c64, P.c32, s));
+        if (!P.fp.any) continue;
+        bool need_u = false, need_v = false;
+        for (int R = 0; R < 2; ++R)
+            for (int o = 1; o < O_N; ++o) {
+                need_u = need_u || J.B.c[R][0][o] != 0.0;
+                need_v = need_v || J.B.c[R][1][o] != 0.0;
+            }
+        float* rec = (float*)m->ws_src.ptr;
+        unsigned tb = (unsigned)((nt + 127) / 128);
+        k_sources2<float><<<tb, 128, 0, s>>>(nt, m->Q, mesh_rule(m), m->tris, m->tgeo, m->pts64, m->pts32,
+                                             m->pts32lo, J.x, J.x + m->nv, need_u, need_v, rec);
+        ::pb::count_launch();
+        if (np_pad > np) PB_CUDA(cudaMemsetAsync(rec + REC2 * np, 0, sizeof(float) * REC2 * (np_pad - np), s));
+        // the single-mesh decomposition (same kernel occupancy as that path)
+        const void* kern = P.fp.mode == 0 ? (acc ? (const void*)k_pair32x2<0, true> : (const void*)k_pair32x2<0, false>)
+                                          : (acc ? (const void*)k_pair32x2<1, true> : (const void*)k_pair32x2<1, false>);
+        int S = choose_splits(np, tpc, TS2, occupancy_slots(m, kern, TPB2));
+        P.chunk = ((np + S - 1) / S + TS2 - 1) / TS2 * TS2;
+        P.S = (int)((np + P.chunk - 1) / P.chunk);
+        const int nacc = P.fp.mode == 0 ? 2 : 10;
+        PB_TRY(ws_reserve(m->ws_part, (acc ? sizeof(double) : sizeof(float)) * (size_t)P.S * nacc * np));
+        PairJob pj;
+        pj.rec = rec;
+        pj.pts32 = m->pts32;
+        pj.pts32lo = m->pts32lo;
+        pj.part = m->ws_part.ptr;
+        pj.np = np;
+        pj.chunk = P.chunk;
+        for (int R = 0; R < 2; ++R)
+            for (int j = 0; j < 4; ++j) pj.cf.k[R][j] = (float)P.fp.k[R][j];
+        pj.cf.kappa = (float)P.fp.kappa;
+        pj.cf.mk2 = (float)(-P.fp.kappa * 1.4426950408889634);
+        pj.nsplit = P.S;
+        pj.pad = 0;
+        hjobs[P.fp.mode].push_back(pj);
+        hjob_of[P.fp.mode].push_back((int)k);
+    }
+    for (int mode = 0; mode < 2; ++mode) {
+        if (hjobs[mode].empty()) continue;
+        std::vector<PairItem> items;
+        for (size_t q = 0; q < hjobs[mode].size(); ++q) {
+            const PairJob& pj = hjobs[mode][q];
+            const int ntb = (int)((pj.np + tpc - 1) / tpc);
+            for (int tb = 0; tb < ntb; ++tb)
+                for (int sp = 0; sp < pj.nsplit; ++sp) items.push_back({(int)q, tb, sp, 0});
+        }
+        const size_t jb = sizeof(PairJob) * hjobs[mode].size(), ib = sizeof(PairItem) * items.size();
+        PB_TRY(ws_reserve(bs.table, jb + ib + 256));
+        char* base = (char*)bs.table.ptr;
+        PairJob* djobs = (PairJob*)base;
+        PairItem* ditems = (PairItem*)(base + (jb + 255) / 256 * 256);
+        if ((jb + 255) / 256 * 256 + ib > bs.table.bytes) {
+            PB_TRY(ws_reserve(bs.table, (jb + 255) / 256 * 256 + ib + 256));
+            base = (char*)bs.table.ptr;
+            djobs = (PairJob*)base;
+            ditems = (PairItem*)(base + (jb + 255) / 256 * 256);
+        }
+        PB_CUDA(cudaMemcpyAsync(djobs, hjobs[mode].data(), jb, cudaMemcpyHostToDevice, s));
+        PB_CUDA(cudaMemcpyAsync(ditems, items.data(), ib, cudaMemcpyHostToDevice, s));
+        int* status = jobs[hjob_of[mode][0]].m->status;
+        const unsigned n_items = (unsigned)items.size();
+        if (mode == 0) {
+            if (acc) k_pair32x2_multi<0, true><<<n_items, TPB2, 0, s>>>(djobs, ditems, status);
+            else k_pair32x2_multi<0, false><<<n_items, TPB2, 0, s>>>(djobs, ditems, status);
+        } else {
+            if (acc) k_pair32x2_multi<1, true><<<n_items, TPB2, 0, s>>>(djobs, ditems, status);
+            else k_pair32x2_multi<1, false><<<n_items, TPB2, 0, s>>>(djobs, ditems, status);
+        }
+        ::pb::count_launch();
+    }
+    for (size_t k = 0; k < jobs.size(); ++k) {
+        const FarJob& J = jobs[k];
+        const pb_mesh* m = J.m;
+        const Prep& P = prep[k];
+        if (P.fp.any) {
+            unsigned tb = (unsigned)((m->nt + 127) / 128);
+            if (acc)
+                k_tri_reduce<double><<<tb, 128, 0, s>>>(m->nt, m->np, mesh_rule(m), P.S, P.fp.mode, P.fp, m->tgeo,
+                                                        m->pts64, (const double*)m->ws_part.ptr, P.tri);
+            else
+                k_tri_reduce<float><<<tb, 128, 0, s>>>(m->nt, m->np, mesh_rule(m), P.S, P.fp.mode, P.fp, m->tgeo,
+                                                       m->pts64, (const float*)m->ws_part.ptr, P.tri);
+            ::pb::count_launch();
+        }
+        unsigned gb = (unsigned)((m->nv * 8 + 255) / 256);
+        if (prec == PB_F32)
+            k_gather_spmv<float><<<gb, 256, 0, s>>>(m->nv, m->v2t_ptr, m->v2t, P.tri, P.fp.any ? 1 : 0, m->row_ptr,
+                                                    m->col, P.c32, m->nnz, J.x, J.y);
+        else
+            k_gather_spmv<double><<<gb, 256, 0, s>>>(m->nv, m->v2t_ptr, m->v2t, P.tri, P.fp.any ? 1 : 0, m->row_ptr,
+                                                     m->col, P.c64, m->nnz, J.x, J.y);
+        ::pb::count_launch();
+    }
+    PB_CUDA(cudaGetLastError());
+    return PB_OK;
+}
+
+int far_splits_estimate(pb_ctx* ctx, int64_t np) {
+    int best = 1;
+    const void* kerns[2] = {(const void*)k_pair32x2<1, true>, (const void*)k_pair32x2<1, false>};
+    const int tpcs[2] = {TPB2 * 2, TPB2 * 4};
+    for (int k = 0; k < 2; ++k) {
+        int per_sm = 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kerns[k], TPB2, 0) != cudaSuccess || per_sm < 1)
+            per_sm = 1;
+        cudaGetLastError();
+        best = std::max(best, choose_splits(np, tpcs[k], TS2, per_sm * ctx->num_sms));
+    }
+    return best;
 }
 
 int far_splits(const pb_mesh* m, int tpc, int ctas_per_sm) {

@@ -156,8 +156,23 @@ int apply_blockop(const pb_mesh* m, const pb_near* nf, const BlockOp& B, int pre
 int combine_near(const pb_mesh* m, const pb_near* nf, const BlockOp& B, double* comb64, float* comb32,
                  cudaStream_t s);
 
+// batched application over several meshes (one pair-kernel launch per row mode)
+struct FarJob {
+    const pb_mesh* m;
+    const pb_near* nf;
+    BlockOp B;
+    const double* x;
+    double* y;
+};
+struct BatchScratch {
+    Workspace table;  // job and work-item tables on the device
+};
+int apply_blockops_batched(const std::vector<FarJob>& jobs, int prec, BatchScratch& bs, cudaStream_t s);
+
 // far-field split count for the pair kernels
 int far_splits(const pb_mesh* m, int targets_per_cta, int ctas_per_sm);
+// largest split count the packed kernels use for np points (workspace estimates)
+int far_splits_estimate(pb_ctx* ctx, int64_t np);
 
 // Chebyshev solve with the mass matrix: y = M^-1 x on both halves of a 2 nv vector
 int mass_solve(const pb_mesh* m, const pb_near* nf, const double* x, double* y, double* work,

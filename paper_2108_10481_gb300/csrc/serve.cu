@@ -1,0 +1,444 @@
+// a11: request server - continuous batching of boundary-element solves.
+//
+// Molecules (mesh, charges, eps_int, eps_ext, kappa, formulation,
+// preconditioner) arrive with pb_submit. An admission thread takes them in
+// arrival order whenever the HBM budget and the slot count allow, loads the
+// mesh, builds the FP64 near field and the right-hand side on its own
+// non-blocking stream (so near-field builds overlap the other requests'
+// iterations), and hands them to the active set. Every pb_server_step then
+// advances each active request by one GMRES step: all their operator
+// applications go into one batched pair-kernel launch per row mode over a
+// table of (request, target block, source split) work items, followed by each
+// request's own preconditioner, Gram-Schmidt and Givens kernels, and one
+// read-back of all residual estimates. A request that converges computes its
+// energy, reports its result and frees its memory, making room for the next.
+//
+// Each request keeps the split decomposition it has alone, and all its
+// reductions run in a fixed order, so its result does not depend on what
+// else is in the batch.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <condition_variable>
+#include <deque>
+#include <mutex>
+#include <thread>
+
+#include "solver.h"
+
+namespace pb {
+
+enum Phase { PH_START = 0, PH_ITER, PH_ENERGY };
+
+static double now_ms() {
+    using namespace std::chrono;
+    return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+struct ServeReq {
+    uint64_t tag = 0;
+    std::vector<double> V, xq, q;
+    std::vector<int32_t> T;
+    pb_params prm;
+    int form = 0, pc = 0;
+    pb_solve_opts opts;
+    pb_quad_plan plan;
+    size_t footprint = 0;
+    double t_submit = 0, t_ready = 0;
+    // device state
+    pb_mesh* m = nullptr;
+    pb_near* nf = nullptr;
+    double* buf = nullptr;
+    double *dxq = nullptr, *dq = nullptr, *rhs = nullptr, *x = nullptr, *rr = nullptr, *dd = nullptr, *w = nullptr;
+    Solver S;
+    GmresWork G;
+    bool mixed = false;
+    int mmax = 0;
+    // iteration state
+    int phase = PH_START;
+    int j = 0, outer = 0, total_it = 0;
+    double bnorm = 0, rel = 1, prev_rel = 1, inner_tol = 0;
+    int status = PB_OK;
+};
+
+}  // namespace pb
+
+struct pb_server {
+    pb_ctx* ctx = nullptr;
+    size_t budget = 0;
+    int max_active = 1;
+    std::mutex mu;
+    std::condition_variable cv;
+    std::deque<pb::ServeReq*> waiting;  // submitted, not admitted
+    std::deque<pb::ServeReq*> ready;    // set up, not yet in the active set
+    std::vector<pb::ServeReq*> active;  // owned by the stepping thread
+    std::vector<pb_result> done;
+    size_t used = 0;
+    int admitted = 0;  // admitted and not finished
+    bool stop = false;
+    std::thread admit_thread;
+    cudaStream_t s_main = nullptr, s_setup = nullptr;
+    pb::BatchScratch bs;
+    double* res_dev = nullptr;
+    double* res_host = nullptr;
+    int res_cap = 0;
+};
+
+namespace pb {
+
+static int free_req(ServeReq* r) {
+    if (r->buf) cudaFree(r->buf);
+    r->buf = nullptr;
+    gmres_free(r->G);
+    pb_free_near(r->nf);
+    pb_free_mesh(r->m);
+    r->nf = nullptr;
+    r->m = nullptr;
+    return PB_OK;
+}
+
+// Device bytes a request holds while resident (upper estimates of the
+// adjacency sizes: 16 adjacent pairs per triangle, 25 near nonzeros per vertex).
+static size_t footprint(pb_ctx* ctx, int64_t nv, int64_t nt, int Q, int mmax, int64_t nq) {
+    const double np = (double)Q * nt, npairs = 16.0 * nt, nnz = 25.0 * nv;
+    double mesh = 24 * nv + 12 * nt + 128 * nt + 64 * np + 8 * (nv + 1) + 12 * nt + 16 * npairs + 12 * nnz +
+                  4 * nv + 4 * (nnz + 1) + 36 * npairs;
+    double nearb = 56 * nnz + 56 * nv;
+    double near_tmp = 864 * npairs + 4 * nnz;
+    double src = 128 * (np + 64);
+    int S = far_splits_estimate(ctx, (int64_t)np);
+    double part = (double)S * 10 * np * 8;
+    double work = src + part + 48 * nt + 48 * nnz + 128 * nv;
+    double n2 = 2.0 * nv;
+    double nchunk = std::ceil(n2 / 2048.0);
+    double gm = 8 * ((mmax + 1) * n2 + n2 + (double)(mmax + 1) * mmax + 4 * mmax + 2 + (mmax + 2) * nchunk + 16);
+    double bufb = 8 * (4.0 * nq + 10 * nv);
+    return (size_t)(mesh + nearb + std::max(near_tmp, work) + gm + bufb);
+}
+
+// load, near field, right-hand side and solver state, on the setup stream
+static int setup_req(pb_server* srv, ServeReq* r) {
+    pb_ctx* ctx = srv->ctx;
+    cudaStream_t s = srv->s_setup;
+    PB_TRY(pb_mesh_load(ctx, r->V.data(), (int64_t)r->V.size() / 3, r->T.data(), (int64_t)r->T.size() / 3,
+                        &r->plan, PB_MEM_HOST, &r->m));
+    PB_TRY(pb_near_build(ctx, r->m, r->prm.kappa, &r->nf, s));
+    const int64_t nv = r->m->nv, nq = (int64_t)r->q.size();
+    PB_TRY(dev_alloc((void**)&r->buf, sizeof(double) * (4 * nq + 10 * nv)));
+    r->dxq = r->buf;
+    r->dq = r->dxq + 3 * nq;
+    r->rhs = r->dq + nq;
+    r->x = r->rhs + 2 * nv;
+    r->rr = r->x + 2 * nv;
+    r->dd = r->rr + 2 * nv;
+    r->w = r->dd + 2 * nv;
+    PB_CUDA(cudaMemcpyAsync(r->dxq, r->xq.data(), sizeof(double) * 3 * nq, cudaMemcpyHostToDevice, s));
+    PB_CUDA(cudaMemcpyAsync(r->dq, r->q.data(), sizeof(double) * nq, cudaMemcpyHostToDevice, s));
+    PB_TRY(pb_rhs_charges(ctx, r->m, r->dxq, r->dq, nq, &r->prm, r->form, r->opts.alpha, r->opts.beta, r->rhs, s));
+    PB_CUDA(cudaMemsetAsync(r->x, 0, sizeof(double) * 2 * nv, s));
+    PB_TRY(setup_solver(r->S, r->m, r->nf, &r->prm, r->form, r->pc, &r->opts, s));
+    PB_TRY(gmres_alloc(r->G, 2 * nv, r->mmax));
+    PB_CUDA(cudaStreamSynchronize(s));
+    r->S.s = srv->s_main;
+    r->mixed = r->opts.precision == PB_MIXED;
+    r->phase = PH_START;
+    return PB_OK;
+}
+
+static void finish(pb_server* srv, ServeReq* r, double dGp, double dGk) {
+    pb_result res;
+    res.tag = r->tag;
+    res.status = r->status;
+    res.iters = r->total_it;
+    res.outer_iters = r->mixed ? r->outer : 1;
+    res.dG_paper = dGp;
+    res.dG_kcal = dGk;
+    res.rel_residual = r->rel;
+    double t = now_ms();
+    res.latency_ms = t - r->t_submit;
+    res.queue_ms = r->t_ready - r->t_submit;
+    free_req(r);
+    std::lock_guard<std::mutex> lock(srv->mu);
+    srv->used -= r->footprint;
+    srv->admitted -= 1;
+    srv->done.push_back(res);
+    srv->cv.notify_all();
+}
+
+static void admission_loop(pb_server* srv) {
+    cudaSetDevice(srv->ctx->device);
+    for (;;) {
+        ServeReq* r = nullptr;
+        {
+            std::unique_lock<std::mutex> lock(srv->mu);
+            srv->cv.wait(lock, [&] {
+                return srv->stop || (!srv->waiting.empty() && srv->admitted < srv->max_active &&
+                                     srv->used + srv->waiting.front()->footprint <= srv->budget);
+            });
+            if (srv->stop) return;
+            r = srv->waiting.front();
+            srv->waiting.pop_front();
+            srv->used += r->footprint;
+            srv->admitted += 1;
+        }
+        int rc = setup_req(srv, r);
+        r->t_ready = now_ms();
+        if (rc != PB_OK) {
+            r->status = rc;
+            r->rel = 0.0;
+            finish(srv, r, 0.0, 0.0);
+            delete r;
+            continue;
+        }
+        std::lock_guard<std::mutex> lock(srv->mu);
+        srv->ready.push_back(r);
+        srv->cv.notify_all();
+    }
+}
+
+static int tick(pb_server* srv) {
+    {
+        std::lock_guard<std::mutex> lock(srv->mu);
+        while (!srv->ready.empty()) {
+            srv->active.push_back(srv->ready.front());
+            srv->ready.pop_front();
+        }
+    }
+    std::vector<ServeReq*>& act = srv->active;
+    if (act.empty()) return PB_OK;
+    cudaStream_t s = srv->s_main;
+    const int n = (int)act.size();
+    if (n > srv->res_cap) {
+        if (srv->res_dev) cudaFree(srv->res_dev);
+        if (srv->res_host) cudaFreeHost(srv->res_host);
+        srv->res_dev = nullptr;
+        srv->res_host = nullptr;
+        int cap = std::max(64, 2 * n);
+        PB_TRY(dev_alloc((void**)&srv->res_dev, sizeof(double) * 4 * cap));
+        PB_CUDA(cudaMallocHost((void**)&srv->res_host, sizeof(double) * 4 * cap));
+        srv->res_cap = cap;
+    }
+    auto it_prec = [](const ServeReq* r) { return r->mixed ? PB_F32 : PB_F64; };
+    auto res_prec = [](const ServeReq* r) { return r->mixed ? PB_F32_ACCURATE : PB_F64; };
+
+    // round A: the system operator for every request that needs one
+    std::vector<FarJob> jobs[4];  // by precision
+    for (ServeReq* r : act) {
+        if (r->phase == PH_ITER)
+            jobs[it_prec(r)].push_back({r->m, r->nf, r->S.A, r->G.V + (int64_t)r->j * r->G.n, r->S.t3});
+        else if (r->phase == PH_START && r->mixed && r->outer > 0)
+            jobs[res_prec(r)].push_back({r->m, r->nf, r->S.A, r->x, r->S.t3});
+    }
+    for (int p = 0; p < 4; ++p) PB_TRY(apply_blockops_batched(jobs[p], p, srv->bs, s));
+    for (auto& v : jobs) v.clear();
+    // preconditioner input; Calderon requests queue their second operator
+    std::vector<const double*> pin(n, nullptr);
+    for (int k = 0; k < n; ++k) {
+        ServeReq* r = act[k];
+        const int64_t n2 = 2 * r->m->nv;
+        if (r->phase == PH_ITER) {
+            pin[k] = r->S.t3;
+        } else if (r->phase == PH_START) {
+            if (r->mixed && r->outer > 0) {
+                vec_sub(n2, r->rhs, r->S.t3, r->rr, s);
+                pin[k] = r->rr;
+            } else {
+                pin[k] = r->rhs;
+            }
+        }
+        if (!pin[k]) continue;
+        const int prec = r->phase == PH_ITER ? it_prec(r) : res_prec(r);
+        if (r->pc >= PB_PC_CALDERON_FULL) {
+            PB_TRY(calderon_pre(r->S, pin[k]));
+            jobs[prec].push_back({r->m, r->nf, r->S.C, r->S.t1, r->S.t2});
+        } else {
+            PB_TRY(apply_prec(r->S, prec, pin[k], r->w));
+        }
+    }
+    for (int p = 0; p < 4; ++p) PB_TRY(apply_blockops_batched(jobs[p], p, srv->bs, s));
+    for (int k = 0; k < n; ++k) {
+        ServeReq* r = act[k];
+        if (!pin[k]) continue;
+        if (r->pc >= PB_PC_CALDERON_FULL) PB_TRY(calderon_post(r->S, r->w));
+        double* slot = srv->res_dev + 4 * k;
+        if (r->phase == PH_ITER) PB_TRY(gm_step(r->G, r->j, r->w, slot, s));
+        else gm_norm2(r->G, r->w, slot, s);
+    }
+    PB_CUDA(cudaMemcpyAsync(srv->res_host, srv->res_dev, sizeof(double) * 4 * n, cudaMemcpyDeviceToHost, s));
+    PB_CUDA(cudaStreamSynchronize(s));
+
+    // host decisions
+    for (int k = 0; k < n; ++k) {
+        ServeReq* r = act[k];
+        const double* h = srv->res_host + 4 * k;
+        const double tol = r->opts.tol;
+        if (r->phase == PH_START) {
+            const double beta = std::sqrt(h[0]);
+            if (!std::isfinite(beta)) {
+                r->status = set_error(PB_ENUMERIC, "residual is not finite");
+                r->phase = PH_ENERGY;
+                continue;
+            }
+            if (r->outer == 0) r->bnorm = beta;
+            r->prev_rel = r->rel;
+            r->rel = r->bnorm > 0.0 ? beta / r->bnorm : 0.0;
+            bool stall = r->mixed && r->outer >= 2 && r->rel > 0.5 * r->prev_rel;
+            if (beta == 0.0 || (r->mixed && (r->rel <= tol || stall)) || (!r->mixed && r->outer > 0)) {
+                if (r->rel > tol) r->status = PB_ENOCONV;
+                r->phase = PH_ENERGY;
+                continue;
+            }
+            r->inner_tol = r->mixed ? std::min(0.5, std::max(r->opts.inner_tol, 0.5 * tol / r->rel)) : tol;
+            PB_TRY(gm_begin(r->G, r->w, srv->res_dev + 4 * k, s));
+            if (r->mixed) PB_CUDA(cudaMemsetAsync(r->dd, 0, sizeof(double) * 2 * r->m->nv, s));
+            r->j = 0;
+            r->phase = PH_ITER;
+        } else if (r->phase == PH_ITER) {
+            const double res = h[0];
+            r->total_it += 1;
+            r->j += 1;
+            if (!std::isfinite(res)) {
+                r->status = set_error(PB_ENUMERIC, "residual is not finite");
+                r->phase = PH_ENERGY;
+                continue;
+            }
+            const bool conv = res <= r->inner_tol;
+            if (conv || h[1] == 0.0 || r->j >= r->mmax || r->total_it >= r->opts.max_it) {
+                PB_TRY(gm_finish(r->G, r->j, r->mixed ? r->dd : r->x, s));
+                if (r->mixed) {
+                    vec_add(2 * r->m->nv, r->dd, r->x, s);
+                    r->outer += 1;
+                    r->phase = r->total_it >= r->opts.max_it || r->outer >= std::max(1, r->opts.max_outer)
+                                   ? PH_ENERGY : PH_START;
+                    if (r->phase == PH_ENERGY) r->status = PB_ENOCONV;
+                } else {
+                    r->rel = res;
+                    r->outer = 1;
+                    if (!conv) r->status = PB_ENOCONV;
+                    r->phase = PH_ENERGY;
+                }
+            }
+        }
+    }
+    // finished requests: energy, result, memory back to the budget
+    std::vector<ServeReq*> keep;
+    for (ServeReq* r : act) {
+        if (r->phase != PH_ENERGY) {
+            keep.push_back(r);
+            continue;
+        }
+        double dGp = 0.0, dGk = 0.0;
+        int rc = pb_energy(srv->ctx, r->m, r->x, r->form, r->dxq, r->dq, (int64_t)r->q.size(), &r->prm, nullptr, &dGp,
+                           &dGk, s);
+        if (rc != PB_OK && r->status == PB_OK) r->status = rc;
+        if (r->status == PB_OK) r->status = check_status(r->m, s);
+        finish(srv, r, dGp, dGk);
+        delete r;
+    }
+    act.swap(keep);
+    return PB_OK;
+}
+
+}  // namespace pb
+
+using namespace pb;
+
+extern "C" int pb_server_create(pb_ctx* ctx, int64_t hbm_budget_bytes, int max_active, pb_server** out) {
+    if (!ctx || !out || hbm_budget_bytes <= 0 || max_active < 1)
+        return set_error(PB_EINVAL, "pb_server_create: bad argument");
+    *out = nullptr;
+    PB_CUDA(cudaSetDevice(ctx->device));
+    pb_server* srv = new pb_server();
+    srv->ctx = ctx;
+    srv->budget = (size_t)hbm_budget_bytes;
+    srv->max_active = max_active;
+    if (cudaStreamCreateWithFlags(&srv->s_main, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&srv->s_setup, cudaStreamNonBlocking) != cudaSuccess) {
+        delete srv;
+        return set_error(PB_ECUDA, "stream creation failed");
+    }
+    srv->admit_thread = std::thread(admission_loop, srv);
+    *out = srv;
+    return PB_OK;
+}
+
+extern "C" int pb_server_destroy(pb_server* srv) {
+    if (!srv) return PB_OK;
+    {
+        std::lock_guard<std::mutex> lock(srv->mu);
+        srv->stop = true;
+        srv->cv.notify_all();
+    }
+    if (srv->admit_thread.joinable()) srv->admit_thread.join();
+    cudaSetDevice(srv->ctx->device);
+    cudaDeviceSynchronize();
+    for (ServeReq* r : srv->active) { free_req(r); delete r; }
+    for (ServeReq* r : srv->ready) { free_req(r); delete r; }
+    for (ServeReq* r : srv->waiting) delete r;
+    ws_free(srv->bs.table);
+    if (srv->res_dev) cudaFree(srv->res_dev);
+    if (srv->res_host) cudaFreeHost(srv->res_host);
+    cudaStreamDestroy(srv->s_main);
+    cudaStreamDestroy(srv->s_setup);
+    delete srv;
+    return PB_OK;
+}
+
+extern "C" int pb_submit(pb_server* srv, const pb_request* req) {
+    if (!srv || !req || !req->verts || !req->tris || !req->xq || !req->q || req->n_q < 1 || req->n_verts < 4 ||
+        req->n_tris < 4)
+        return set_error(PB_EINVAL, "pb_submit: bad request");
+    if (req->precond < PB_PC_NONE || req->precond > PB_PC_SCALED_CALDERON_EXT || req->form < PB_DIRECT_INT ||
+        req->form > PB_LU)
+        return set_error(PB_EINVAL, "pb_submit: unknown formulation or preconditioner");
+    ServeReq* r = new ServeReq();
+    r->tag = req->tag;
+    r->V.assign(req->verts, req->verts + 3 * req->n_verts);
+    r->T.assign(req->tris, req->tris + 3 * req->n_tris);
+    r->xq.assign(req->xq, req->xq + 3 * req->n_q);
+    r->q.assign(req->q, req->q + req->n_q);
+    r->prm = req->params;
+    r->form = req->form;
+    r->pc = req->precond;
+    r->opts = req->opts;
+    r->plan = req->plan;
+    if (r->plan.far_q == 0) r->plan = {6, 4};
+    if (!(r->opts.tol > 0.0) || r->opts.max_it < 1) {
+        delete r;
+        return set_error(PB_EINVAL, "pb_submit: need tol > 0 and max_it >= 1");
+    }
+    r->mmax = r->opts.restart > 0 ? std::min(r->opts.restart, r->opts.max_it) : r->opts.max_it;
+    r->footprint = footprint(srv->ctx, req->n_verts, req->n_tris, r->plan.far_q, r->mmax, req->n_q);
+    if (r->footprint > srv->budget) {
+        size_t fp = r->footprint;
+        delete r;
+        return set_error(PB_ENOMEM, "request needs about %zu bytes, more than the server's budget of %zu", fp,
+                         srv->budget);
+    }
+    r->t_submit = now_ms();
+    std::lock_guard<std::mutex> lock(srv->mu);
+    srv->waiting.push_back(r);
+    srv->cv.notify_all();
+    return PB_OK;
+}
+
+extern "C" int pb_server_step(pb_server* srv, int* n_active, int* n_pending) {
+    if (!srv) return set_error(PB_EINVAL, "pb_server_step: NULL server");
+    PB_CUDA(cudaSetDevice(srv->ctx->device));
+    int rc = tick(srv);
+    std::lock_guard<std::mutex> lock(srv->mu);
+    if (n_active) *n_active = (int)srv->active.size();
+    // waiting + being set up + set up but not yet stepping
+    if (n_pending) *n_pending = (int)srv->waiting.size() + srv->admitted - (int)srv->active.size();
+    return rc;
+}
+
+extern "C" int pb_poll(pb_server* srv, pb_result* out, int max, int* n_out) {
+    if (!srv || !n_out || (max > 0 && !out)) return set_error(PB_EINVAL, "pb_poll: bad argument");
+    std::lock_guard<std::mutex> lock(srv->mu);
+    int n = std::min(max, (int)srv->done.size());
+    for (int i = 0; i < n; ++i) out[i] = srv->done[i];
+    srv->done.erase(srv->done.begin(), srv->done.begin() + n);
+    *n_out = n;
+    return PB_OK;
+}

@@ -12,7 +12,7 @@
 #include <chrono>
 #include <vector>
 
-#include "internal.h"
+#include "solver.h"
 
 namespace pb {
 
@@ -176,7 +176,7 @@ __global__ void k_vh(int64_t n, int nk, const double* __restrict__ V, int64_t ld
     w[i] += sign * s;
 }
 // normalise w into V[j+1] with its norm^2 in h[j+1]; zero vector on breakdown
-__global__ void k_normalize(int64_t n, const double* __restrict__ w, double* __restrict__ hcol, int j,
+__global__ void k_normalize(int64_t n, const double* __restrict__ w, const double* __restrict__ hcol, int j,
                             double* __restrict__ vout) {
     int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     double nrm = sqrt(hcol[j + 1]);
@@ -218,27 +218,10 @@ __global__ void k_backsolve(int k, const double* __restrict__ H, int ldh, const 
 }
 
 // ------------------------------------------------------------------- solver
-struct Solver {
-    const pb_mesh* m;
-    const pb_near* nf;
-    pb_params prm;
-    int form, pc;
-    BlockOp A, C;
-    double sa = 1.0, sb = 1.0;  // scaling of the two halves after the preconditioner
-    double* bdiag = nullptr;    // 4 nv
-    double* t1 = nullptr;       // 2 nv each
-    double* t2 = nullptr;
-    double* t3 = nullptr;
-    double* cheb = nullptr;     // 3 x 2 nv
-    int cheb_iters = 34;
-    int applies = 0;
-    cudaStream_t s;
-};
-
 static unsigned nb(int64_t n) { return (unsigned)((n + 255) / 256); }
 
 // y = P^-1 x
-static int apply_prec(Solver& S, int prec, const double* x, double* y) {
+int apply_prec(Solver& S, int prec, const double* x, double* y) {
     const pb_mesh* m = S.m;
     const int64_t nv = m->nv, n2 = 2 * nv;
     switch (S.pc) {
@@ -274,22 +257,7 @@ static int apply_op(Solver& S, int prec, const double* x, double* y) {
     return apply_prec(S, prec, S.t3, y);
 }
 
-struct GmresWork {
-    double* V = nullptr;     // (m+1) x n
-    double* w = nullptr;     // n
-    double* H = nullptr;     // (m+1) x m, column-major
-    double* cs = nullptr;
-    double* sn = nullptr;
-    double* g = nullptr;     // m + 1
-    double* y = nullptr;     // m
-    double* part = nullptr;  // (m+1) x nchunk
-    double* res = nullptr;   // 2 (device)
-    int mmax = 0;
-    int64_t n = 0;
-    void* block = nullptr;
-};
-
-static int gmres_alloc(GmresWork& G, int64_t n, int mmax) {
+int gmres_alloc(GmresWork& G, int64_t n, int mmax) {
     const size_t nchunk = (size_t)((n + DOT_CHUNK - 1) / DOT_CHUNK);
     const size_t m = (size_t)mmax;
     // offsets (in doubles) of every array, then one allocation of the total
@@ -311,13 +279,13 @@ static int gmres_alloc(GmresWork& G, int64_t n, int mmax) {
     G.n = n;
     return PB_OK;
 }
-static void gmres_free(GmresWork& G) {
+void gmres_free(GmresWork& G) {
     if (G.block) cudaFree(G.block);
     G.block = nullptr;
 }
 
 // out[0..nk) = V[0..nk) . w   (accumulate: out += ...)
-static void dots(GmresWork& G, const double* V, int nk, const double* w, double* out, int accumulate, cudaStream_t s) {
+void dots(GmresWork& G, const double* V, int nk, const double* w, double* out, int accumulate, cudaStream_t s) {
     int nchunk = (int)((G.n + DOT_CHUNK - 1) / DOT_CHUNK);
     dim3 grid(nchunk, nk);
     k_dots<<<grid, DOT_THREADS, 0, s>>>(G.n, V, G.n, w, G.part, nchunk); ::pb::count_launch();
@@ -395,7 +363,7 @@ static int gmres(Solver& S, GmresWork& G, int prec, const double* b, double* x, 
     return PB_OK;
 }
 
-static int setup_solver(Solver& S, const pb_mesh* m, const pb_near* nf, const pb_params* prm, int form, int pc,
+int setup_solver(Solver& S, const pb_mesh* m, const pb_near* nf, const pb_params* prm, int form, int pc,
                         const pb_solve_opts* o, cudaStream_t s) {
     S.m = m;
     S.nf = nf;
@@ -443,7 +411,7 @@ static int setup_solver(Solver& S, const pb_mesh* m, const pb_near* nf, const pb
     return PB_OK;
 }
 
-static int check_status(const pb_mesh* m, cudaStream_t s) {
+int check_status(const pb_mesh* m, cudaStream_t s) {
     int* status = m->status;
     int h = 0;
     PB_CUDA(cudaMemcpyAsync(&h, status, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -453,6 +421,103 @@ static int check_status(const pb_mesh* m, cudaStream_t s) {
         return set_error(PB_ETIMEOUT, "a bounded device wait gave up (status %d)", h);
     }
     return PB_OK;
+}
+
+// ---------------------------------------------- step-wise GMRES (the server)
+// The same arithmetic as gmres() above, split at the points where the host
+// needs a scalar, with every scalar kept on the device.
+__global__ void k_gm_begin(const double* __restrict__ n2, double* __restrict__ g, double* __restrict__ beta) {
+    const double b = sqrt(n2[0]);
+    g[0] = b;
+    beta[0] = b;
+}
+__global__ void k_givens_dev(int j, double* __restrict__ H, int ldh, double* __restrict__ cs, double* __restrict__ sn,
+                             double* __restrict__ g, const double* __restrict__ beta, double* __restrict__ res) {
+    double* h = H + (int64_t)j * ldh;
+    for (int i = 0; i < j; ++i) {
+        double t = cs[i] * h[i] + sn[i] * h[i + 1];
+        h[i + 1] = -sn[i] * h[i] + cs[i] * h[i + 1];
+        h[i] = t;
+    }
+    double a = h[j], b = h[j + 1];
+    double den = hypot(a, b);
+    double c = den > 0.0 ? a / den : 1.0, s = den > 0.0 ? b / den : 0.0;
+    cs[j] = c;
+    sn[j] = s;
+    h[j] = den;
+    h[j + 1] = 0.0;
+    g[j + 1] = -s * g[j];
+    g[j] = c * g[j];
+    res[0] = fabs(g[j + 1]) / beta[0];
+    res[1] = den;
+}
+
+void gm_norm2(GmresWork& G, const double* w, double* dst, cudaStream_t s) { dots(G, w, 1, w, dst, 0, s); }
+
+int gm_begin(GmresWork& G, const double* w, const double* n2, cudaStream_t s) {
+    const int ldh = G.mmax + 1;
+    PB_CUDA(cudaMemsetAsync(G.H, 0, sizeof(double) * (size_t)ldh * G.mmax, s));
+    PB_CUDA(cudaMemsetAsync(G.g, 0, sizeof(double) * (G.mmax + 2), s));
+    k_gm_begin<<<1, 1, 0, s>>>(n2, G.g, G.res + 4);
+    ::pb::count_launch();
+    k_normalize<<<nb(G.n), 256, 0, s>>>(G.n, w, n2 - 1, 0, G.V);  // reads n2[0] as hcol[1]
+    ::pb::count_launch();
+    PB_CUDA(cudaGetLastError());
+    return PB_OK;
+}
+
+int gm_step(GmresWork& G, int j, double* w, double* res_out, cudaStream_t s) {
+    const int64_t n = G.n;
+    const int ldh = G.mmax + 1;
+    double* hcol = G.H + (int64_t)j * ldh;
+    dots(G, G.V, j + 1, w, hcol, 0, s);
+    k_vh<<<nb(n), 256, 0, s>>>(n, j + 1, G.V, n, hcol, -1.0, w);
+    ::pb::count_launch();
+    dots(G, G.V, j + 1, w, G.y, 0, s);
+    k_vh<<<nb(n), 256, 0, s>>>(n, j + 1, G.V, n, G.y, -1.0, w);
+    ::pb::count_launch();
+    k_add_inplace<<<nb(j + 1), 256, 0, s>>>(j + 1, G.y, hcol);
+    ::pb::count_launch();
+    dots(G, w, 1, w, hcol + j + 1, 0, s);
+    k_normalize<<<nb(n), 256, 0, s>>>(n, w, hcol, j, G.V + (int64_t)(j + 1) * n);
+    ::pb::count_launch();
+    k_sqrt_entry<<<1, 1, 0, s>>>(hcol, j + 1);
+    ::pb::count_launch();
+    k_givens_dev<<<1, 1, 0, s>>>(j, G.H, ldh, G.cs, G.sn, G.g, G.res + 4, res_out);
+    ::pb::count_launch();
+    PB_CUDA(cudaGetLastError());
+    return PB_OK;
+}
+
+int gm_finish(GmresWork& G, int k, double* x, cudaStream_t s) {
+    if (k <= 0) return PB_OK;
+    k_backsolve<<<1, 1, 0, s>>>(k, G.H, G.mmax + 1, G.g, G.y);
+    ::pb::count_launch();
+    k_vh<<<nb(G.n), 256, 0, s>>>(G.n, k, G.V, G.n, G.y, 1.0, x);
+    ::pb::count_launch();
+    PB_CUDA(cudaGetLastError());
+    return PB_OK;
+}
+
+int calderon_pre(Solver& S, const double* x) { return mass_solve(S.m, S.nf, x, S.t1, S.cheb, S.cheb_iters, S.s); }
+
+int calderon_post(Solver& S, double* y) {
+    PB_TRY(mass_solve(S.m, S.nf, S.t2, y, S.cheb, S.cheb_iters, S.s));
+    if (S.sa != 1.0 || S.sb != 1.0) {
+        k_scale_halves<<<nb(2 * S.m->nv), 256, 0, S.s>>>(S.m->nv, 1.0 / S.sa, 1.0 / S.sb, y);
+        ::pb::count_launch();
+    }
+    PB_CUDA(cudaGetLastError());
+    return PB_OK;
+}
+
+void vec_sub(int64_t n, const double* a, const double* b, double* y, cudaStream_t s) {
+    k_sub<<<nb(n), 256, 0, s>>>(n, a, b, y);
+    ::pb::count_launch();
+}
+void vec_add(int64_t n, const double* a, double* y, cudaStream_t s) {
+    k_add_inplace<<<nb(n), 256, 0, s>>>(n, a, y);
+    ::pb::count_launch();
 }
 
 static int solve_impl(pb_ctx* ctx, const pb_mesh* m, const pb_near* nf, const pb_params* prm, int form, int pc,

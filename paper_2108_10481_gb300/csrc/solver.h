@@ -1,0 +1,60 @@
+// Solver pieces shared by pb_solve (solve.cu) and the request server (serve.cu).
+#pragma once
+
+#include "internal.h"
+
+namespace pb {
+
+struct Solver {
+    const pb_mesh* m;
+    const pb_near* nf;
+    pb_params prm;
+    int form, pc;
+    BlockOp A, C;
+    double sa = 1.0, sb = 1.0;  // scaling of the two halves after the preconditioner
+    double* bdiag = nullptr;    // 4 nv
+    double* t1 = nullptr;       // 2 nv each
+    double* t2 = nullptr;
+    double* t3 = nullptr;
+    double* cheb = nullptr;     // 3 x 2 nv
+    int cheb_iters = 34;
+    int applies = 0;
+    cudaStream_t s;
+};
+
+struct GmresWork {
+    double* V = nullptr;     // (m+1) x n
+    double* w = nullptr;     // n
+    double* H = nullptr;     // (m+1) x m, column-major
+    double* cs = nullptr;
+    double* sn = nullptr;
+    double* g = nullptr;     // m + 1
+    double* y = nullptr;     // m
+    double* part = nullptr;  // (m+1) x nchunk
+    double* res = nullptr;   // 2 (device)
+    int mmax = 0;
+    int64_t n = 0;
+    void* block = nullptr;
+};
+
+
+int setup_solver(Solver& S, const pb_mesh* m, const pb_near* nf, const pb_params* prm, int form, int pc,
+                 const pb_solve_opts* o, cudaStream_t s);
+int apply_prec(Solver& S, int prec, const double* x, double* y);
+int gmres_alloc(GmresWork& G, int64_t n, int mmax);
+void gmres_free(GmresWork& G);
+void dots(GmresWork& G, const double* V, int nk, const double* w, double* out, int accumulate, cudaStream_t s);
+int check_status(const pb_mesh* m, cudaStream_t s);
+
+// step-wise GMRES: scalars stay on the device
+void gm_norm2(GmresWork& G, const double* w, double* dst, cudaStream_t s);
+int gm_begin(GmresWork& G, const double* w, const double* n2, cudaStream_t s);
+int gm_step(GmresWork& G, int j, double* w, double* res_out, cudaStream_t s);
+int gm_finish(GmresWork& G, int k, double* x, cudaStream_t s);
+// Calderon preconditioner split around its operator application (t1 -> t2)
+int calderon_pre(Solver& S, const double* x);
+int calderon_post(Solver& S, double* y);
+void vec_sub(int64_t n, const double* a, const double* b, double* y, cudaStream_t s);
+void vec_add(int64_t n, const double* a, double* y, cudaStream_t s);
+
+}  // namespace pb

@@ -33,6 +33,18 @@ class pb_solve_info(ctypes.Structure):
                 ("rel_residual", c_double), ("time_ms", c_double)]
 
 
+class pb_request(ctypes.Structure):
+    _fields_ = [("verts", c_void_p), ("n_verts", c_int64), ("tris", c_void_p), ("n_tris", c_int64),
+                ("xq", c_void_p), ("q", c_void_p), ("n_q", c_int64), ("params", pb_params), ("form", c_int),
+                ("precond", c_int), ("opts", pb_solve_opts), ("plan", pb_quad_plan), ("tag", ctypes.c_uint64)]
+
+
+class pb_result(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_uint64), ("status", c_int), ("iters", c_int), ("outer_iters", c_int),
+                ("dG_kcal", c_double), ("dG_paper", c_double), ("rel_residual", c_double),
+                ("latency_ms", c_double), ("queue_ms", c_double)]
+
+
 P = c_void_p
 # name -> argtypes (all return int unless listed in _RESTYPE)
 SIGNATURES = {
@@ -56,6 +68,11 @@ SIGNATURES = {
                             ctypes.POINTER(pb_quad_plan), c_int, c_int, ctypes.POINTER(pb_solve_opts),
                             ctypes.POINTER(c_double), ctypes.POINTER(pb_solve_info), P],
     "pb_system_apply_noalloc": [P, P, P, ctypes.POINTER(pb_params), c_int, c_double, c_double, P, P, P],
+    "pb_server_create": [P, c_int64, c_int, ctypes.POINTER(c_void_p)],
+    "pb_server_destroy": [P],
+    "pb_submit": [P, ctypes.POINTER(pb_request)],
+    "pb_server_step": [P, ctypes.POINTER(c_int), ctypes.POINTER(c_int)],
+    "pb_poll": [P, ctypes.POINTER(pb_result), c_int, ctypes.POINTER(c_int)],
     "pb_profile": [P, c_int],
     "pb_profile_read": [P, c_int, ctypes.POINTER(c_int64), ctypes.POINTER(c_double), ctypes.POINTER(c_double),
                         ctypes.POINTER(c_double)],
