@@ -55,6 +55,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-baseline", action="store_true")
     ap.add_argument("--no-check", action="store_true", help="skip the FP64 accuracy solve (profiling runs)")
+    ap.add_argument("--serve", type=int, default=0,
+                    help="serving benchmark on the first N requests of the seeded request stream instead")
+    ap.add_argument("--rate-scale", type=float, default=0.7,
+                    help="serving: Poisson arrival rate as a fraction of the closed-batch solve rate")
     return ap.parse_args()
 
 
@@ -361,6 +365,90 @@ def run_ours(args, rank, world, local_rank):
     print(json.dumps(line), flush=True)
 
 
+def _build_request(spec):
+    """(spec, verts, tris, xq, q) of one request of the serving stream (runs in a worker process)."""
+    from synth import synthetic_molecule
+    v, t, xq, q, _ = synthetic_molecule(spec["n_atoms"], spec["mol_seed"])
+    return spec, v, t, xq, q
+
+
+def run_serving(args, rank, local_rank):
+    """Continuous batching through the request server on the first N requests
+    of the seeded stream (atom counts log-uniform in 50-3000, cases 2/10/12/23):
+    a closed batch gives the sustainable rate R; then Poisson arrivals at
+    rate_scale * R give the latency distribution; the same requests solved one
+    at a time (pb_solve, same precision) are the sequential comparison."""
+    import multiprocessing as mp
+
+    from synth import serving_stream
+    specs = serving_stream(512, 5)[:args.serve]
+    with mp.get_context("spawn").Pool(max(1, min(16, (os.cpu_count() or 2)))) as pool:
+        reqs = pool.map(_build_request, specs)
+    import torch
+
+    import paper_2108_10481_gb300 as pb
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    ctx = pb.pb_init(local_rank)
+    P = pb.Params(4.0, 80.0, 0.125)
+    opts = pb.solve_opts(tol=1e-6, max_it=300, precision=pb.PB_MIXED, inner_tol=1e-4)
+    free, total = torch.cuda.mem_get_info()
+    budget = int(0.8 * free)
+
+    def serve(arrivals):
+        srv = pb.pb_server_create(ctx, budget, 64)
+        order = np.argsort(arrivals)
+        out, k = {}, 0
+        t0 = time.perf_counter()
+        while len(out) < len(reqs):
+            now = time.perf_counter() - t0
+            while k < len(order) and arrivals[order[k]] <= now:
+                spec, v, t, xq, q = reqs[order[k]]
+                form, prec = pb.CASES[spec["case"]]
+                pb.pb_submit(srv, v, t, xq, q, P, form, prec, opts=opts, tag=int(order[k]))
+                k += 1
+            a, p_ = pb.pb_server_step(srv)
+            for r in pb.pb_poll(srv):
+                out[r["tag"]] = r
+            if a == 0 and p_ == 0 and k < len(order):
+                time.sleep(min(0.002, max(0.0, arrivals[order[k]] - (time.perf_counter() - t0))))
+        span = time.perf_counter() - t0
+        srv.free()
+        return out, span
+
+    closed, span_c = serve(np.zeros(len(reqs)))            # all at once
+    rate = len(reqs) / span_c
+    rng = np.random.default_rng(55)
+    arr = np.cumsum(rng.exponential(1.0 / (args.rate_scale * rate), size=len(reqs)))
+    arr -= arr[0]
+    opened, span_o = serve(arr)
+    lat = np.array([opened[i]["latency_ms"] for i in range(len(reqs))])
+    # sequential: one request at a time through the one-call path
+    t0 = time.perf_counter()
+    for spec, v, t, xq, q in reqs:
+        form, prec = pb.CASES[spec["case"]]
+        pb.pb_solvation_energy(ctx, v, t, xq, q, P, form, prec, opts=opts)
+    torch.cuda.synchronize()
+    span_s = time.perf_counter() - t0
+    if rank != 0:
+        return
+    tris = np.array([r[2].shape[0] for r in reqs])
+    ok = all(opened[i]["status"] == 0 for i in range(len(reqs)))
+    same = all(opened[i]["dG_kcal"] == closed[i]["dG_kcal"] for i in range(len(reqs)))
+    line = {"metric": "PB solves/s and p50/p99 latency (serving stream)", "value": len(reqs) / span_o,
+            "unit": "solves/s", "n_gpus": 1, "steps": len(reqs), "warmup": 0, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+            "config": {"workload": "serving stream: first %d of 512 seeded requests, atoms log-uniform in 50-3000 "
+                                   "(%d-%d tris), cases 2/10/12/23, Poisson arrivals at %.2f x the closed-batch rate"
+                                   % (len(reqs), tris.min(), tris.max(), args.rate_scale),
+                       "hbm_budget_bytes": budget, "max_active": 64, "gmres_tol": 1e-6, "precision": "mixed"},
+            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                           "max": float(lat.max())},
+            "closed_batch_solves_per_s": rate, "sequential_solves_per_s": len(reqs) / span_s,
+            "all_converged": ok, "identical_open_vs_closed": same}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank = int(os.environ.get("RANK", "0"))
@@ -368,6 +456,9 @@ def main():
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         run_reference(args, rank)
+        return
+    if args.serve > 0:
+        run_serving(args, rank, local_rank)
         return
     if world > 1:
         import torch.distributed as dist
