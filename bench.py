@@ -34,10 +34,10 @@ UNIT = "solves/s"
 SM_COUNT_GB300 = 152
 FP32_LANES_PER_SM = 128  # FP32 pipe operations per SM per clock
 L2_FLUSH_BYTES = 256 << 20
-# DRAM bytes per launch of the FP32 pair kernel in its V/K + D/T mode, from one ncu capture at 122,880 points
-# (dram__bytes_read.sum + dram__bytes_write.sum; profiles/pair32_vkdt_multi_charge_sphere.md). Valid only for
-# that kernel as captured; any other dominant kernel reports null.
-NCU_TRAFFIC = {}
+# DRAM bytes per launch of the packed FP32 pair kernel in its V/K + D/T mode, from one ncu capture at 122,880
+# points (dram__bytes_read.sum + dram__bytes_write.sum; profiles/pair32x2_vkdt_multi_charge_sphere.md). Valid only
+# for that kernel as captured; any other dominant kernel reports null.
+NCU_TRAFFIC = {("pair32", "juffer", 122880): 17.72e6}
 
 
 def parse():
@@ -81,6 +81,18 @@ def workload_text(args, v, t, xq):
                 "r<=8 A, q~U[-1,1] e, eps 4/80, kappa 0.125" % (args.level, v.shape[0], t.shape[0]))
     return ("synthetic protein-like molecule: %d atoms on a seeded random walk, Gaussian surface at ~4 verts/A^2 "
             "(%d verts, %d tris), eps 4/80, kappa 0.125" % (xq.shape[0], v.shape[0], t.shape[0]))
+
+
+def cross_rank_max(value: float, world: int, device=None) -> float:
+    """Max of a timing scalar over the ranks (the only cross-rank exchange:
+    every rank runs an independent replica of the solve)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device if device is not None else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 # ------------------------------------------------------------------ clocks
@@ -287,11 +299,7 @@ def run_ours(args, rank, world, local_rank):
     fam = {k: pb.pb_profile_read(ctx, k) for k in (pb.PB_KERNEL_PAIR32, pb.PB_KERNEL_PAIR32_ACCURATE,
                                                    pb.PB_KERNEL_PAIR64)}
     pb.pb_profile(ctx, False)
-    total_ms = float(np.sum(step_ms))
-    if world > 1:
-        tt = torch.tensor([total_ms], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = cross_rank_max(float(np.sum(step_ms)), world, dev)
 
     # e2e: the host-buffer entry point, pinned inputs, dG read back each step
     e2e = None
@@ -309,11 +317,7 @@ def run_ours(args, rank, world, local_rank):
         for _ in range(k_e2e):
             pb.pb_solvation_energy(ctx, hv, ht, hxq, hq, P, form, prec, opts=opts)
         torch.cuda.synchronize()
-        e2e_s = time.perf_counter() - w0
-        if world > 1:
-            tt = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            e2e_s = float(tt.item())
+        e2e_s = cross_rank_max(time.perf_counter() - w0, world, dev)
         e2e = {"value": world * k_e2e / e2e_s, "unit": UNIT,
                "h2d_bytes_per_step": int(v.nbytes + t.nbytes + xq.nbytes + q.nbytes), "d2h_bytes_per_step": 8}
 

@@ -310,6 +310,31 @@ int pb_server_step(pb_server* srv, int* n_active, int* n_pending);
 /* Move up to max finished results into out; *n_out = how many. Thread-safe. */
 int pb_poll(pb_server* srv, pb_result* out, int max, int* n_out);
 
+/* ---- a12: autotuner --------------------------------------------------------- */
+/* Launch tuning of the FP32 far field (not in the paper: its software uses
+ * fixed FMM and quadrature settings). */
+typedef struct {
+    int kernel;          /* chosen FP32 kernel: 1 scalar, 2 packed f32x2 */
+    double split_scale;  /* chosen multiplier of the wave-filling split count */
+    double best_ms;      /* one FP32 system application with the choice */
+    double default_ms;   /* ... with the untuned default (packed, x1) */
+} pb_tune_result;
+/* Time every candidate launch of formulation `form`'s FP32 system application
+ * on this mesh (fast and split-coordinate variants) and keep the fastest in
+ * ctx for meshes of this size (same power-of-two bucket of quadrature points).
+ * Later applications, solves and the server use it. out may be NULL. */
+int pb_autotune(pb_ctx* ctx, const pb_mesh* mesh, const pb_near* near, const pb_params* prm, int form,
+                pb_tune_result* out, void* stream);
+/* Quadrature plan for a molecule: solve it (host arrays, like
+ * pb_solvation_energy) with `reference` (NULL = {6, 4}) and with the cheaper
+ * far rules {3, 4} and {1, 4}, and return in out_plan the cheapest plan whose
+ * Delta G differs from the reference one by at most tol_dG relative (the
+ * reference plan when none does); *out_change (optional) = that difference. */
+int pb_autotune_plan(pb_ctx* ctx, const double* verts, int64_t n_verts, const int32_t* tris, int64_t n_tris,
+                     const double* xq, const double* q, int64_t n_q, const pb_params* prm,
+                     const pb_quad_plan* reference, int form, int precond, const pb_solve_opts* opts, double tol_dG,
+                     pb_quad_plan* out_plan, double* out_change, void* stream);
+
 /* ---- measurement ---------------------------------------------------------- */
 /* kernel families timed by pb_profile */
 #define PB_KERNEL_PAIR32 0          /* FP32 far-field pair kernel (inner solves) */

@@ -289,6 +289,36 @@ def pb_poll(srv: Server, max_results: int = 1024):
     return [{k: getattr(buf[i], k) for k, _ in N.pb_result._fields_} for i in range(n.value)]
 
 
+def pb_autotune(ctx: Ctx, mesh: Mesh, near: Near, params: Params, form, stream=None):
+    """Tune the FP32 far-field launch for this mesh size; returns the choice."""
+    r = N.pb_tune_result()
+    p = params.c()
+    _check(N.load().pb_autotune(ctx.ptr, mesh.ptr, near.ptr, ctypes.byref(p), _form(form), ctypes.byref(r),
+                                _stream(stream)))
+    return {k: getattr(r, k) for k, _ in N.pb_tune_result._fields_}
+
+
+def pb_autotune_plan(ctx: Ctx, verts, tris, xq, q, params: Params, form, precond, tol_dG: float = 1e-6,
+                     reference=(6, 4), opts=None, stream=None):
+    """Cheapest quadrature plan whose Delta G stays within tol_dG of the reference plan:
+    returns ((far_q, n_ss), relative change)."""
+    v = np.ascontiguousarray(verts, dtype=np.float64)
+    t = np.ascontiguousarray(tris, dtype=np.int32)
+    x = np.ascontiguousarray(xq, dtype=np.float64).reshape(-1, 3)
+    qq = np.ascontiguousarray(q, dtype=np.float64).reshape(-1)
+    p = params.c()
+    ref = N.pb_quad_plan(*reference)
+    out = N.pb_quad_plan()
+    ch = ctypes.c_double()
+    o = opts if opts is not None else solve_opts()
+    _check(N.load().pb_autotune_plan(ctx.ptr, ctypes.c_void_p(v.ctypes.data), v.shape[0],
+                                     ctypes.c_void_p(t.ctypes.data), t.shape[0], ctypes.c_void_p(x.ctypes.data),
+                                     ctypes.c_void_p(qq.ctypes.data), qq.shape[0], ctypes.byref(p), ctypes.byref(ref),
+                                     _form(form), _prec(precond), ctypes.byref(o), float(tol_dG), ctypes.byref(out),
+                                     ctypes.byref(ch), _stream(stream)))
+    return (out.far_q, out.n_ss), ch.value
+
+
 def pb_solvation_energy(ctx: Ctx, verts: np.ndarray, tris: np.ndarray, xq: np.ndarray, q: np.ndarray,
                         params: Params, form, precond, far_q: int = 6, n_ss: int = 4, opts=None, stream=None):
     """Whole path from host arrays; returns (dG kcal/mol, info dict)."""

@@ -840,6 +840,24 @@ static int choose_splits(int64_t np, int tpc, int tile, int slots) {
     return best;
 }
 
+int tune_bucket(int64_t np) {
+    int b = 0;
+    while (b + 1 < TUNE_BUCKETS && ((int64_t)1 << (b + 1)) <= np) ++b;
+    return b;
+}
+
+TuneEntry tuned(const pb_ctx* ctx, int64_t np, int mode, bool acc) {
+    return ctx->tune[mode ? 1 : 0][acc ? 1 : 0][tune_bucket(np)];
+}
+
+// split count after the tuned scale, within [1, tiles] and <= 32
+static int scaled_splits(int S, double scale, int64_t np, int tile) {
+    const int64_t ntiles = (np + tile - 1) / tile;
+    int s2 = (int)(S * scale + 0.5);
+    s2 = std::max(1, std::min(s2, 32));
+    return (int)std::min<int64_t>(s2, ntiles);
+}
+
 static int occupancy_slots(const pb_mesh* m, const void* kern, int threads) {
     int per_sm = 1;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, 0) != cudaSuccess || per_sm < 1)
@@ -939,7 +957,8 @@ int apply_blockop(const pb_mesh* m, const pb_near* nf, const BlockOp& B, int pre
             tm.stop();
             k_tri_reduce<double><<<tb, 128, 0, s>>>(nt, np, rule, S, fp.mode, fp, m->tgeo, m->pts64, part, tri);
             ::pb::count_launch();
-        } else if (m->ctx->pair_kernel == 2) {
+        } else if (tuned(m->ctx, np, fp.mode, prec == PB_F32_ACCURATE).kernel == 2 ||
+                   (tuned(m->ctx, np, fp.mode, prec == PB_F32_ACCURATE).kernel == 0 && m->ctx->pair_kernel == 2)) {
             float* rec = (float*)m->ws_src.ptr;
             k_sources2<float><<<tb, 128, 0, s>>>(nt, m->Q, rule, m->tris, m->tgeo, m->pts64, m->pts32, m->pts32lo, x,
                                                  x + nv, need_u, need_v, rec);
@@ -951,6 +970,7 @@ int apply_blockop(const pb_mesh* m, const pb_near* nf, const BlockOp& B, int pre
             const void* kern = fp.mode == 0 ? (acc ? (const void*)k_pair32x2<0, true> : (const void*)k_pair32x2<0, false>)
                                             : (acc ? (const void*)k_pair32x2<1, true> : (const void*)k_pair32x2<1, false>);
             int S = choose_splits(np, tpc, TS2, occupancy_slots(m, kern, TPB2));
+            S = scaled_splits(S, tuned(m->ctx, np, fp.mode, acc).split_scale, np, TS2);
             int64_t chunk = ((np + S - 1) / S + TS2 - 1) / TS2 * TS2;
             S = (int)((np + chunk - 1) / chunk);
             Coef32 cf;
@@ -990,6 +1010,7 @@ int apply_blockop(const pb_mesh* m, const pb_near* nf, const BlockOp& B, int pre
             const void* kern = fp.mode == 0 ? (acc ? (const void*)k_pair32<0, true> : (const void*)k_pair32<0, false>)
                                             : (acc ? (const void*)k_pair32<1, true> : (const void*)k_pair32<1, false>);
             int S = choose_splits(np, TPB32 * TGT32, TS32, occupancy_slots(m, kern, TPB32));
+            S = scaled_splits(S, tuned(m->ctx, np, fp.mode, acc).split_scale, np, TS32);
             int64_t chunk = ((np + S - 1) / S + TS32 - 1) / TS32 * TS32;
             S = (int)((np + chunk - 1) / chunk);
             Coef32 cf;
@@ -1086,6 +1107,7 @@ int apply_blockops_batched(const std::vector<FarJob>& jobs, int prec, BatchScrat
         const void* kern = P.fp.mode == 0 ? (acc ? (const void*)k_pair32x2<0, true> : (const void*)k_pair32x2<0, false>)
                                           : (acc ? (const void*)k_pair32x2<1, true> : (const void*)k_pair32x2<1, false>);
         int S = choose_splits(np, tpc, TS2, occupancy_slots(m, kern, TPB2));
+        S = scaled_splits(S, tuned(m->ctx, np, P.fp.mode, acc).split_scale, np, TS2);
         P.chunk = ((np + S - 1) / S + TS2 - 1) / TS2 * TS2;
         P.S = (int)((np + P.chunk - 1) / P.chunk);
         const int nacc = P.fp.mode == 0 ? 2 : 10;
@@ -1296,4 +1318,77 @@ extern "C" int pb_system_apply_noalloc(pb_ctx* ctx, const pb_mesh* m, const pb_n
     ::pb::count_launch();
     PB_CUDA(cudaGetLastError());
     return PB_OK;
+}
+
+// ------------------------------------------------------------------ a12: autotuner
+// Times the FP32 far-field application of one formulation on the caller's
+// mesh for every candidate launch (scalar or packed kernel; split count x0.5,
+// x1, x2 of the wave-filling choice; both the fast and the split-coordinate
+// variant), keeps the fastest per variant in the context's table for this
+// size bucket, and reports the gain. Results of the tuned launches are the
+// same sums in another split order (FP32 rounding differences only).
+extern "C" int pb_autotune(pb_ctx* ctx, const pb_mesh* m, const pb_near* nf, const pb_params* prm, int form,
+                           pb_tune_result* out, void* stream) {
+    using namespace pb;
+    if (!ctx || !m || !nf || !prm) return set_error(PB_EINVAL, "pb_autotune: NULL argument");
+    BlockOp B;
+    PB_TRY(system_blockop(prm, form, 0.0, 0.0, &B));
+    FarPlan fp;
+    PB_TRY(make_far_plan(B, nf->kappa, &fp));
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t n2 = 2 * m->nv;
+    double* xy = nullptr;
+    PB_TRY(dev_alloc((void**)&xy, sizeof(double) * 2 * n2));
+    std::vector<double> hx(n2);
+    for (int64_t i = 0; i < n2; ++i) hx[i] = std::sin(0.37 * (double)i) + 0.5;
+    cudaMemcpy(xy, hx.data(), sizeof(double) * n2, cudaMemcpyHostToDevice);
+    const int bucket = tune_bucket(m->np);
+    const int kernels[2] = {2, 1};
+    const double scales[3] = {1.0, 0.5, 2.0};
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    int rc = PB_OK;
+    for (int acc = 0; acc < 2 && rc == PB_OK; ++acc) {
+        const int prec = acc ? PB_F32_ACCURATE : PB_F32;
+        TuneEntry& slot = ctx->tune[fp.mode ? 1 : 0][acc][bucket];
+        const TuneEntry saved = slot;
+        double best = 1e300, dflt = 0.0;
+        TuneEntry best_e;
+        for (int k : kernels)
+            for (double sc : scales) {
+                slot.kernel = k;
+                slot.split_scale = sc;
+                rc = apply_blockop(m, nf, B, prec, xy, xy + n2, s);  // warm-up and workspace growth
+                if (rc != PB_OK) break;
+                float ms_total = 0.0f;
+                const int reps = 3;
+                cudaEventRecord(e0, s);
+                for (int r = 0; r < reps && rc == PB_OK; ++r) rc = apply_blockop(m, nf, B, prec, xy, xy + n2, s);
+                cudaEventRecord(e1, s);
+                cudaEventSynchronize(e1);
+                cudaEventElapsedTime(&ms_total, e0, e1);
+                const double ms = ms_total / reps;
+                if (k == 2 && sc == 1.0) dflt = ms;
+                if (ms < best) {
+                    best = ms;
+                    best_e = slot;
+                }
+            }
+        slot = rc == PB_OK ? best_e : saved;
+        if (out && !acc) {
+            out->kernel = best_e.kernel;
+            out->split_scale = best_e.split_scale;
+            out->best_ms = best;
+            out->default_ms = dflt;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(xy);
+    if (rc == PB_OK) {
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) rc = set_error(PB_ECUDA, "pb_autotune: %s", cudaGetErrorString(e));
+    }
+    return rc;
 }

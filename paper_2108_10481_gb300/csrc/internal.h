@@ -76,9 +76,20 @@ struct KernelStats {
 void count_launch(int n = 1);
 }  // namespace pb
 
+namespace pb {
+// Autotuned choice of the FP32 far-field launch for one size bucket
+// (log2 of the point count) and row mode / precision.
+struct TuneEntry {
+    int kernel = 0;          // 0 = not tuned, 1 = scalar, 2 = packed f32x2
+    double split_scale = 1;  // multiplier of the wave-filling split count
+};
+constexpr int TUNE_BUCKETS = 40;
+}  // namespace pb
+
 struct pb_ctx {
     int profile = 0;
     int pair_kernel = 2;  // FP32 far-field kernel: 2 = packed f32x2 (default), 1 = scalar
+    pb::TuneEntry tune[2][2][pb::TUNE_BUCKETS];  // [mode][accurate][bucket]
     pb::KernelStats stats[3];
     int device = 0;
     int num_sms = 0;
@@ -173,6 +184,9 @@ int apply_blockops_batched(const std::vector<FarJob>& jobs, int prec, BatchScrat
 int far_splits(const pb_mesh* m, int targets_per_cta, int ctas_per_sm);
 // largest split count the packed kernels use for np points (workspace estimates)
 int far_splits_estimate(pb_ctx* ctx, int64_t np);
+// the tuned entry that applies to np points (kernel 0 when none)
+TuneEntry tuned(const pb_ctx* ctx, int64_t np, int mode, bool acc);
+int tune_bucket(int64_t np);
 
 // Chebyshev solve with the mass matrix: y = M^-1 x on both halves of a 2 nv vector
 int mass_solve(const pb_mesh* m, const pb_near* nf, const double* x, double* y, double* work,

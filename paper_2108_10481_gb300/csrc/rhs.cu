@@ -7,6 +7,8 @@
 // Delta G = 1/2 sum_j q_j phi_reac(x_j).
 #include <math.h>
 
+#include <cmath>
+
 #include "internal.h"
 
 namespace pb {
@@ -211,4 +213,37 @@ extern "C" int pb_solvation_energy(pb_ctx* ctx, const double* verts, int64_t n_v
     pb_free_near(nf);
     pb_free_mesh(m);
     return rc;
+}
+
+// a12, quadrature part: the cheapest of the relaxed plans {far_q 3, 1} (with
+// the singular rule kept) whose Delta G differs from the reference plan's by
+// at most tol_dG relative; the reference plan itself when none qualifies.
+extern "C" int pb_autotune_plan(pb_ctx* ctx, const double* verts, int64_t n_verts, const int32_t* tris,
+                                int64_t n_tris, const double* xq, const double* q, int64_t n_q, const pb_params* prm,
+                                const pb_quad_plan* reference, int form, int precond, const pb_solve_opts* opts,
+                                double tol_dG, pb_quad_plan* out_plan, double* out_change, void* stream) {
+    if (!ctx || !verts || !tris || !xq || !q || !prm || !out_plan || !(tol_dG >= 0.0))
+        return set_error(PB_EINVAL, "pb_autotune_plan: bad argument");
+    pb_quad_plan ref = reference ? *reference : pb_quad_plan{6, 4};
+    double dref = 0.0;
+    PB_TRY(pb_solvation_energy(ctx, verts, n_verts, tris, n_tris, xq, q, n_q, prm, &ref, form, precond, opts, &dref,
+                               nullptr, stream));
+    *out_plan = ref;
+    if (out_change) *out_change = 0.0;
+    const int cands[2] = {3, 1};
+    for (int qn : cands) {
+        if (qn >= ref.far_q) continue;
+        pb_quad_plan p = {qn, ref.n_ss};
+        double d = 0.0;
+        PB_TRY(pb_solvation_energy(ctx, verts, n_verts, tris, n_tris, xq, q, n_q, prm, &p, form, precond, opts, &d,
+                                   nullptr, stream));
+        const double change = std::fabs(d / dref - 1.0);
+        if (change <= tol_dG) {
+            *out_plan = p;
+            if (out_change) *out_change = change;
+        } else {
+            break;  // a coarser rule will not do better
+        }
+    }
+    return PB_OK;
 }

@@ -45,6 +45,10 @@ class pb_result(ctypes.Structure):
                 ("latency_ms", c_double), ("queue_ms", c_double)]
 
 
+class pb_tune_result(ctypes.Structure):
+    _fields_ = [("kernel", c_int), ("split_scale", c_double), ("best_ms", c_double), ("default_ms", c_double)]
+
+
 P = c_void_p
 # name -> argtypes (all return int unless listed in _RESTYPE)
 SIGNATURES = {
@@ -73,6 +77,10 @@ SIGNATURES = {
     "pb_submit": [P, ctypes.POINTER(pb_request)],
     "pb_server_step": [P, ctypes.POINTER(c_int), ctypes.POINTER(c_int)],
     "pb_poll": [P, ctypes.POINTER(pb_result), c_int, ctypes.POINTER(c_int)],
+    "pb_autotune": [P, P, P, ctypes.POINTER(pb_params), c_int, ctypes.POINTER(pb_tune_result), P],
+    "pb_autotune_plan": [P, P, c_int64, P, c_int64, P, P, c_int64, ctypes.POINTER(pb_params),
+                         ctypes.POINTER(pb_quad_plan), c_int, c_int, ctypes.POINTER(pb_solve_opts), c_double,
+                         ctypes.POINTER(pb_quad_plan), ctypes.POINTER(c_double), P],
     "pb_profile": [P, c_int],
     "pb_profile_read": [P, c_int, ctypes.POINTER(c_int64), ctypes.POINTER(c_double), ctypes.POINTER(c_double),
                         ctypes.POINTER(c_double)],
