@@ -349,6 +349,11 @@ int pb_profile(pb_ctx* ctx, int enable);
  * by the kernel's formula count (operations per pair x pairs). Waits for the
  * recorded events. Any output pointer may be NULL. */
 int pb_profile_read(pb_ctx* ctx, int kernel, int64_t* launches, double* total_ms, double* pairs, double* ops);
+/* Failure detection self-test: run the pair kernels' bounded mbarrier wait on a
+ * barrier that nothing completes, giving up after `polls` polls (1..2^24);
+ * *status_out receives the status word the kernel wrote (PB_ETIMEOUT when the
+ * wait ran out). The kernel returns normally and the context stays usable. */
+int pb_selftest_wait(pb_ctx* ctx, int64_t polls, int* status_out);
 /* Number of kernels this library has launched in this process (all kinds). */
 int64_t pb_launch_count(void);
 

@@ -131,6 +131,13 @@ def pb_profile_read(ctx: Ctx, kernel: int):
     return {"launches": n.value, "ms": ms.value, "pairs": pairs.value, "ops": ops.value}
 
 
+def pb_selftest_wait(ctx: Ctx, polls: int = 4096) -> int:
+    """Status word left by a bounded wait on a barrier nothing completes."""
+    st = ctypes.c_int()
+    _check(N.load().pb_selftest_wait(ctx.ptr, int(polls), ctypes.byref(st)))
+    return st.value
+
+
 def pb_launch_count() -> int:
     return int(N.load().pb_launch_count())
 

@@ -1392,3 +1392,37 @@ extern "C" int pb_autotune(pb_ctx* ctx, const pb_mesh* m, const pb_near* nf, con
     }
     return rc;
 }
+
+// -------------------------------------------------- failure detection self-test
+// The bounded mbarrier wait of the pair kernels, on a barrier that nothing
+// arrives at and no copy targets: after `polls` polls the wait gives up,
+// records PB_ETIMEOUT in the status word and the kernel returns normally.
+namespace pb {
+__global__ void k_wait_selftest(int64_t polls, int* status) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    bool done = false;
+    for (int64_t i = 0; i < polls && !done; ++i) done = mbar_try_wait(&bar, 0);
+    if (!done && threadIdx.x == 0) atomicExch(status, PB_ETIMEOUT);
+}
+}  // namespace pb
+
+extern "C" int pb_selftest_wait(pb_ctx* ctx, int64_t polls, int* status_out) {
+    using namespace pb;
+    if (!ctx || !status_out || polls < 1 || polls > ((int64_t)1 << 24))
+        return set_error(PB_EINVAL, "pb_selftest_wait: bad argument");
+    PB_CUDA(cudaSetDevice(ctx->device));
+    int* st = nullptr;
+    PB_TRY(dev_alloc((void**)&st, sizeof(int)));
+    cudaMemset(st, 0, sizeof(int));
+    k_wait_selftest<<<1, 32>>>(polls, st);
+    ::pb::count_launch();
+    cudaError_t e = cudaMemcpy(status_out, st, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(st);
+    if (e != cudaSuccess) return set_error(PB_ECUDA, "pb_selftest_wait: %s", cudaGetErrorString(e));
+    return PB_OK;
+}

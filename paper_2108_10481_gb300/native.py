@@ -85,6 +85,7 @@ SIGNATURES = {
     "pb_profile_read": [P, c_int, ctypes.POINTER(c_int64), ctypes.POINTER(c_double), ctypes.POINTER(c_double),
                         ctypes.POINTER(c_double)],
     "pb_launch_count": [],
+    "pb_selftest_wait": [P, c_int64, ctypes.POINTER(c_int)],
 }
 _RESTYPE = {"pb_last_error": c_char_p, "pb_version": c_char_p, "pb_launch_count": c_int64}
 
