@@ -285,9 +285,12 @@ static void pair_blocks(const double* verts, const int32_t* tris, int64_t ti, in
         singular_pair(&t, id, &s, id, COIN, 6, ng, gx, gw, kappa, blk);
     } else if (ns == 2) {
         /* reorder both so that the shared edge runs Q0 -> Q1 with the same
-         * orientation in both parameterisations */
-        int pt[3] = {sa[0], sa[1], 3 - sa[0] - sa[1]};
-        int ps[3] = {sb[0], sb[1], 3 - sb[0] - sb[1]};
+         * orientation in both parameterisations: from its lower to its higher
+         * global vertex index, so that the rule of (sigma, tau) is the rule of
+         * (tau, sigma) with the two roles exchanged */
+        int k0 = A[sa[0]] < A[sa[1]] ? 0 : 1, k1 = 1 - k0;
+        int pt[3] = {sa[k0], sa[k1], 3 - sa[0] - sa[1]};
+        int ps[3] = {sb[k0], sb[k1], 3 - sb[0] - sb[1]};
         singular_pair(&t, pt, &s, ps, EDGE, 6, ng, gx, gw, kappa, blk);
     } else {
         int pt[3] = {sa[0], (sa[0] + 1) % 3, (sa[0] + 2) % 3};

@@ -115,6 +115,10 @@ struct pb_mesh {
     // adjacent triangle pairs
     int64_t npairs = 0;
     int4* pairs = nullptr;      // (ti, tj, kind, perms): kind 0 coincident, 1 edge, 2 vertex
+    int32_t* pair_rev = nullptr;   // index of the reversed pair (tj, ti)
+    int32_t* pair_coin = nullptr;  // coincident pairs
+    int32_t* pair_prim = nullptr;  // pairs with ti < tj (each also gives its reverse)
+    int64_t n_coin = 0, n_prim = 0;
     // vertex-pair pattern of the near field (symmetric)
     int64_t nnz = 0;
     int32_t* row_ptr = nullptr; // nv + 1

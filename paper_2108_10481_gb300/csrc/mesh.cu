@@ -101,7 +101,8 @@ static int upload(void** dst, const void* src, size_t bytes, size_t* total) {
 static void free_mesh_arrays(pb_mesh* m) {
     void* ptrs[] = {m->verts, m->tris,  m->tgeo, m->pts64,    m->pts32,       m->pts32lo,
                     m->v2t_ptr, m->v2t, m->pairs, m->row_ptr, m->col,         m->tpos,
-                    m->diag_pos, m->contrib_ptr, m->contrib, m->status};
+                    m->diag_pos, m->contrib_ptr, m->contrib, m->status, m->pair_rev,
+                    m->pair_coin, m->pair_prim};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     ws_free(m->ws_src);
@@ -249,9 +250,12 @@ static int load(pb_ctx* ctx, const double* verts_in, int64_t nv, const int32_t* 
                     kind = 0;
                     for (int k = 0; k < 3; ++k) pt[k] = ps[k] = k;
                 } else if (ns == 2) {
-                    kind = 1;  // shared edge runs from reordered vertex 0 to 1 in both
-                    pt[0] = sa[0]; pt[1] = sa[1]; pt[2] = 3 - sa[0] - sa[1];
-                    ps[0] = sb[0]; ps[1] = sb[1]; ps[2] = 3 - sb[0] - sb[1];
+                    // shared edge from reordered vertex 0 to 1 in both, directed from its lower to its
+                    // higher global index: the rule of (s, t) is then that of (t, s) with roles exchanged
+                    kind = 1;
+                    const int k0 = T[3 * t + sa[0]] < T[3 * t + sa[1]] ? 0 : 1, k1 = 1 - k0;
+                    pt[0] = sa[k0]; pt[1] = sa[k1]; pt[2] = 3 - sa[0] - sa[1];
+                    ps[0] = sb[k0]; ps[1] = sb[k1]; ps[2] = 3 - sb[0] - sb[1];
                 } else if (ns == 1) {
                     kind = 2;  // shared vertex is reordered vertex 0 in both
                     for (int k = 0; k < 3; ++k) {
@@ -273,6 +277,22 @@ static int load(pb_ctx* ctx, const double* verts_in, int64_t nv, const int32_t* 
     std::vector<int32_t> pair_ptr(nt + 1, 0);
     for (const int4& p : pairs) pair_ptr[p.x + 1]++;
     for (int64_t t = 0; t < nt; ++t) pair_ptr[t + 1] += pair_ptr[t];
+    // each ordered pair's reverse, and the pairs the near kernel integrates:
+    // coincident ones, and one of every two reversed ones (t < s)
+    std::vector<int32_t> rev(pairs.size()), coin_list, prim_list;
+    for (size_t p = 0; p < pairs.size(); ++p) {
+        const int32_t t = pairs[p].x, u = pairs[p].y;
+        int32_t lo = pair_ptr[u], hi = pair_ptr[u + 1];
+        while (lo < hi) {
+            int32_t mid = (lo + hi) / 2;
+            if (pairs[mid].y < t) lo = mid + 1;
+            else hi = mid;
+        }
+        if (lo >= pair_ptr[u + 1] || pairs[lo].y != t) return set_error(PB_EMESH, "internal: pair without reverse");
+        rev[p] = lo;
+        if (t == u) coin_list.push_back((int32_t)p);
+        else if (t < u) prim_list.push_back((int32_t)p);
+    }
     std::vector<int32_t> row_ptr(nv + 1, 0), col, mark(nv, -1), colpos(nv, 0);
     col.reserve((size_t)24 * nv);
     for (int64_t i = 0; i < nv; ++i) {
@@ -342,6 +362,11 @@ static int load(pb_ctx* ctx, const double* verts_in, int64_t nv, const int32_t* 
     PB_TRY(upload((void**)&m->v2t_ptr, v2t_ptr.data(), sizeof(int32_t) * (nv + 1), &tot));
     PB_TRY(upload((void**)&m->v2t, v2t.data(), sizeof(int32_t) * 3 * nt, &tot));
     PB_TRY(upload((void**)&m->pairs, pairs.data(), sizeof(int4) * pairs.size(), &tot));
+    PB_TRY(upload((void**)&m->pair_rev, rev.data(), sizeof(int32_t) * rev.size(), &tot));
+    PB_TRY(upload((void**)&m->pair_coin, coin_list.data(), sizeof(int32_t) * coin_list.size(), &tot));
+    PB_TRY(upload((void**)&m->pair_prim, prim_list.data(), sizeof(int32_t) * prim_list.size(), &tot));
+    m->n_coin = (int64_t)coin_list.size();
+    m->n_prim = (int64_t)prim_list.size();
     PB_TRY(upload((void**)&m->row_ptr, row_ptr.data(), sizeof(int32_t) * (nv + 1), &tot));
     PB_TRY(upload((void**)&m->col, col.data(), sizeof(int32_t) * nnz, &tot));
     PB_TRY(upload((void**)&m->tpos, tpos.data(), sizeof(int32_t) * nnz, &tot));

@@ -144,12 +144,16 @@ __device__ __forceinline__ double corner(const TriFrame& f, int a, int k) {
     return f.q0[k] + (r >= 1 ? f.e1[k] : 0.0) + (r >= 2 ? f.e2[k] : 0.0);
 }
 
-// 38 accumulators: SL[9], SY[9], KL[9], KY[9], sum w G_L, sum w G_Y
+// Accumulators: SL[9], SY[9], KL[9], KY[9], sum w G_L, sum w G_Y (38); with
+// the reversed pair also KTL[9], KTY[9] (56): the double-layer kernel with the
+// normal of the first triangle, which is the K block of the reversed pair.
 #define NACC_NEAR 38
+#define NACC_SYM 56
 
+template <bool SYM>
 __device__ __forceinline__ void accum_point(double* acc, double w, const double* x, const double* y,
-                                            const double* ny, const double* lx, const double* ly,
-                                            double kappa) {
+                                            const double* nx, const double* ny, const double* lx,
+                                            const double* ly, double kappa) {
     const double d0 = x[0] - y[0], d1 = x[1] - y[1], d2 = x[2] - y[2];
     const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
     const double rinv = rsqrt(r2);
@@ -157,9 +161,17 @@ __device__ __forceinline__ void accum_point(double* acc, double w, const double*
     const double gl = rinv * 0.07957747154594767;  // 1 / (4 pi r)
     const double ek = exp(-kappa * r);
     const double gy = ek * gl;
+    const double fl = gl * rinv * rinv;            // 1 / (4 pi r^3)
+    const double fy_over_fl = ek * (1.0 + kappa * r);
     const double dn = d0 * ny[0] + d1 * ny[1] + d2 * ny[2];
-    const double kl = gl * dn * rinv * rinv;
-    const double ky = kl * ek * (1.0 + kappa * r);
+    const double kl = fl * dn;
+    const double ky = kl * fy_over_fl;
+    double ktl = 0.0, kty = 0.0;
+    if (SYM) {
+        const double dnx = -(d0 * nx[0] + d1 * nx[1] + d2 * nx[2]);  // (y - x).n_x
+        ktl = fl * dnx;
+        kty = ktl * fy_over_fl;
+    }
     for (int a = 0; a < 3; ++a) {
         const double wa = w * lx[a];
         for (int b = 0; b < 3; ++b) {
@@ -168,6 +180,10 @@ __device__ __forceinline__ void accum_point(double* acc, double w, const double*
             acc[9 + 3 * a + b] += gy * ll;
             acc[18 + 3 * a + b] += kl * ll;
             acc[27 + 3 * a + b] += ky * ll;
+            if (SYM) {
+                acc[38 + 3 * a + b] += ktl * ll;
+                acc[47 + 3 * a + b] += kty * ll;
+            }
         }
     }
     acc[36] += w * gl;
@@ -179,39 +195,47 @@ __device__ __forceinline__ double warp_sum(double v) {
     return v;
 }
 
-// Expand 38 reduced accumulators into six 3x3 blocks (V_L, K_L, D_L, V_Y, K_Y, D_Y).
+// Six 3x3 blocks (V_L, K_L, D_L, V_Y, K_Y, D_Y) of the pair (tau, sigma), or with
+// rev = true of the reversed pair (sigma, tau): every block transposed and the
+// double layer taken from the KT accumulators.
 __device__ void expand_blocks(const double* acc, const TriFrame& A, const TriFrame& B, const double* tgeoA,
-                              const double* tgeoB, double kappa, double* out) {
+                              const double* tgeoB, double kappa, bool rev, double* out) {
     double nn = A.n[0] * B.n[0] + A.n[1] * B.n[1] + A.n[2] * B.n[2];
     double f = 1.0 / (4.0 * A.area * B.area);
+    const int kL = rev ? 38 : 18, kY = rev ? 47 : 27;
     for (int a = 0; a < 3; ++a)
         for (int b = 0; b < 3; ++b) {
             const double* ea = tgeoA + 4 + 3 * a;
             const double* eb = tgeoB + 4 + 3 * b;
             double cc = f * (ea[0] * eb[0] + ea[1] * eb[1] + ea[2] * eb[2]);
-            int ab = 3 * a + b;
-            out[0 * 9 + ab] = acc[ab];
-            out[1 * 9 + ab] = acc[18 + ab];
-            out[2 * 9 + ab] = cc * acc[36];
-            out[3 * 9 + ab] = acc[9 + ab];
-            out[4 * 9 + ab] = acc[27 + ab];
-            out[5 * 9 + ab] = cc * acc[37] + kappa * kappa * nn * acc[9 + ab];
+            const int ab = 3 * a + b;
+            const int o = rev ? 3 * b + a : ab;
+            out[0 * 9 + o] = acc[ab];
+            out[1 * 9 + o] = acc[kL + ab];
+            out[2 * 9 + o] = cc * acc[36];
+            out[3 * 9 + o] = acc[9 + ab];
+            out[4 * 9 + o] = acc[kY + ab];
+            out[5 * 9 + o] = cc * acc[37] + kappa * kappa * nn * acc[9 + ab];
         }
 }
 
 constexpr int NEAR_THREADS = 128;
 
-// One warp per adjacent pair. Writes ss[p][54] (regularised) and far[p][54]
-// (far rule, identical points excluded).
-template <int MINB>
+// One warp per listed pair. Writes ss[p][54] (regularised) and far[p][54] (far
+// rule, identical points excluded); with SYM also the blocks of the reversed
+// pair rev[p], whose rule is this one with the roles exchanged.
+template <int MINB, bool SYM>
 __global__ void __launch_bounds__(NEAR_THREADS, MINB)
 k_near_pairs(const double* __restrict__ verts, const int32_t* __restrict__ tris, const double* __restrict__ tgeo,
-             const int4* __restrict__ pairs, int64_t npairs, Gauss gq, Rule rule, double kappa,
-             double* __restrict__ ss_out, double* __restrict__ far_out) {
+             const int4* __restrict__ pairs, const int32_t* __restrict__ list, int64_t nlist,
+             const int32_t* __restrict__ rev, Gauss gq, Rule rule, double kappa, double* __restrict__ ss_out,
+             double* __restrict__ far_out) {
+    constexpr int NA = SYM ? NACC_SYM : NACC_NEAR;
     __shared__ TriFrame frames[NEAR_THREADS / 32][2];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    const int64_t p = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    if (p >= npairs) return;  // whole warps leave together
+    const int64_t li = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (li >= nlist) return;  // whole warps leave together
+    const int64_t p = list[li];
     const int4 pr = pairs[p];
     TriFrame& A = frames[wid][0];
     TriFrame& B = frames[wid][1];
@@ -223,8 +247,8 @@ k_near_pairs(const double* __restrict__ verts, const int32_t* __restrict__ tris,
     const int n = gq.n;
     const int n2 = n * n, n4 = n2 * n2;
     const double jac_ab = (2.0 * A.area) * (2.0 * B.area);
-    double acc[NACC_NEAR];
-    for (int k = 0; k < NACC_NEAR; ++k) acc[k] = 0.0;
+    double acc[NA];
+    for (int k = 0; k < NA; ++k) acc[k] = 0.0;
     for (int idx = lane; idx < nreg * n4; idx += 32) {
         const int reg = idx / n4;
         const int r = idx - reg * n4;
@@ -235,13 +259,15 @@ k_near_pairs(const double* __restrict__ verts, const int32_t* __restrict__ tris,
         double x[3], y[3], lx[3], ly[3];
         frame_point(A, sx, tx, x, lx);
         frame_point(B, sy, ty, y, ly);
-        accum_point(acc, w, x, y, B.n, lx, ly, kappa);
+        accum_point<SYM>(acc, w, x, y, A.n, B.n, lx, ly, kappa);
     }
-    for (int k = 0; k < NACC_NEAR; ++k) acc[k] = warp_sum(acc[k]);
-    if (lane == 0)
-        expand_blocks(acc, A, B, tgeo + 16 * (int64_t)pr.x, tgeo + 16 * (int64_t)pr.y, kappa, ss_out + 54 * p);
+    for (int k = 0; k < NA; ++k) acc[k] = warp_sum(acc[k]);
+    const double* gA = tgeo + 16 * (int64_t)pr.x;
+    const double* gB = tgeo + 16 * (int64_t)pr.y;
+    if (lane == 0) expand_blocks(acc, A, B, gA, gB, kappa, false, ss_out + 54 * p);
+    if (SYM && lane == 1) expand_blocks(acc, A, B, gA, gB, kappa, true, ss_out + 54 * (int64_t)rev[p]);
     // far rule on the same pair (what the pair kernel adds for it)
-    for (int k = 0; k < NACC_NEAR; ++k) acc[k] = 0.0;
+    for (int k = 0; k < NA; ++k) acc[k] = 0.0;
     const int Q = rule.Q;
     for (int idx = lane; idx < Q * Q; idx += 32) {
         const int i = idx / Q, j = idx % Q;
@@ -252,11 +278,11 @@ k_near_pairs(const double* __restrict__ verts, const int32_t* __restrict__ tris,
             y[k] = rule.l[j][0] * corner(B, 0, k) + rule.l[j][1] * corner(B, 1, k) + rule.l[j][2] * corner(B, 2, k);
         }
         const double w = rule.w[i] * A.area * rule.w[j] * B.area;
-        accum_point(acc, w, x, y, B.n, rule.l[i], rule.l[j], kappa);
+        accum_point<SYM>(acc, w, x, y, A.n, B.n, rule.l[i], rule.l[j], kappa);
     }
-    for (int k = 0; k < NACC_NEAR; ++k) acc[k] = warp_sum(acc[k]);
-    if (lane == 0)
-        expand_blocks(acc, A, B, tgeo + 16 * (int64_t)pr.x, tgeo + 16 * (int64_t)pr.y, kappa, far_out + 54 * p);
+    for (int k = 0; k < NA; ++k) acc[k] = warp_sum(acc[k]);
+    if (lane == 0) expand_blocks(acc, A, B, gA, gB, kappa, false, far_out + 54 * p);
+    if (SYM && lane == 1) expand_blocks(acc, A, B, gA, gB, kappa, true, far_out + 54 * (int64_t)rev[p]);
 }
 
 // One thread per nonzero: sum the contributions in their fixed (pair) order.
@@ -316,18 +342,16 @@ static int build(pb_ctx* ctx, const pb_mesh* m, double kappa, pb_near* nf, cudaS
     if (rc == PB_OK) {
         Gauss gq = gauss01(m->n_ss);
         int threads = NEAR_THREADS;  // one warp per pair
-        int64_t blocks = (m->npairs * 32 + threads - 1) / threads;
-        const char* mb = getenv("PBBEM_NEAR_MINB");
-        const int minb = mb ? atoi(mb) : 3;
-        if (minb == 2)
-            k_near_pairs<2><<<(unsigned)blocks, threads, 0, s>>>(m->verts, m->tris, m->tgeo, m->pairs, m->npairs,
-                                                                gq, mesh_rule(m), kappa, ss, far);
-        else if (minb == 4)
-            k_near_pairs<4><<<(unsigned)blocks, threads, 0, s>>>(m->verts, m->tris, m->tgeo, m->pairs, m->npairs,
-                                                                gq, mesh_rule(m), kappa, ss, far);
-        else
-            k_near_pairs<3><<<(unsigned)blocks, threads, 0, s>>>(m->verts, m->tris, m->tgeo, m->pairs, m->npairs,
-                                                                gq, mesh_rule(m), kappa, ss, far);
+        // coincident pairs, then one of each pair of reversed pairs (which also writes the other)
+        unsigned bc = (unsigned)((m->n_coin * 32 + threads - 1) / threads);
+        unsigned bp = (unsigned)((m->n_prim * 32 + threads - 1) / threads);
+        if (bc)
+            k_near_pairs<3, false><<<bc, threads, 0, s>>>(m->verts, m->tris, m->tgeo, m->pairs, m->pair_coin,
+                                                          m->n_coin, m->pair_rev, gq, mesh_rule(m), kappa, ss, far);
+        ::pb::count_launch();
+        if (bp)
+            k_near_pairs<2, true><<<bp, threads, 0, s>>>(m->verts, m->tris, m->tgeo, m->pairs, m->pair_prim,
+                                                         m->n_prim, m->pair_rev, gq, mesh_rule(m), kappa, ss, far);
         ::pb::count_launch();
         k_row_of<<<(unsigned)((m->nv + 255) / 256), 256, 0, s>>>(m->nv, m->row_ptr, row_of); ::pb::count_launch();
         cudaMemsetAsync(nf->diag, 0, sizeof(double) * N_VALS * m->nv, s);
