@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-baseline", action="store_true")
     ap.add_argument("--no-check", action="store_true", help="skip the FP64 accuracy solve (profiling runs)")
+    ap.add_argument("--no-graphs", action="store_true", help="launch GMRES iterations kernel by kernel")
     ap.add_argument("--serve", type=int, default=0,
                     help="serving benchmark on the first N requests of the seeded request stream instead")
     ap.add_argument("--rate-scale", type=float, default=0.7,
@@ -205,6 +206,18 @@ def run_reference(args, rank):
 
 
 # ------------------------------------------------------------------- ours
+def stored_oracle_dG(args):
+    """Delta G (kcal/mol) of the FP64 oracle's dense-LU solve stored for the
+    default sphere workload (tests/golden/make_sphere_oracle.py), or None."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests", "golden",
+                        "multi_charge_sphere_oracle.json")
+    if args.workload != "sphere" or args.level != 5 or not os.path.exists(path):
+        return None
+    with open(path) as f:
+        case = json.load(f)["cases"].get(str(args.case))
+    return case["dG_kcal"] if case else None
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -219,6 +232,8 @@ def run_ours(args, rank, world, local_rank):
     precision = pb.PB_MIXED if args.precision == "mixed" else pb.PB_F64
     opts = pb.solve_opts(tol=args.tol, max_it=400, precision=precision, inner_tol=1e-4)
     ctx = pb.pb_init(local_rank)
+    if args.no_graphs:
+        pb.pb_set_graphs(ctx, False)
     dv = torch.as_tensor(v, device=dev)
     dt = torch.as_tensor(t, device=dev)
     dxq = torch.as_tensor(xq, device=dev)
@@ -338,6 +353,8 @@ def run_ours(args, rank, world, local_rank):
     traffic = NCU_TRAFFIC.get((fam_key, form, npts))
     lat = np.array(step_ms)
     dG_err = abs(float(np.mean(dGs)) / dG64 - 1.0) if dG64 is not None else None
+    dG_orc = stored_oracle_dG(args)
+    dG_err_orc = abs(float(np.mean(dGs)) / dG_orc - 1.0) if dG_orc is not None else None
     value = world * args.steps / (total_ms * 1e-3)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -347,10 +364,12 @@ def run_ours(args, rank, world, local_rank):
                    "case": args.case, "formulation": form, "preconditioner": prec, "precision": args.precision,
                    "gmres_tol": args.tol, "quadrature": "far 6-point degree-4 rule, singular 4^4 Gauss per region",
                    "points": npts, "l2": "flushed (256 MB write) before every timed step",
+                   "gmres_step": "CUDA graph replay" if not args.no_graphs else "kernel by kernel",
                    "parallelism": "replicas" if world > 1 else "1 GPU"},
         "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                        "min": float(lat.min()), "max": float(lat.max())},
-        "dG_kcal": float(np.mean(dGs)), "dG_rel_err_vs_f64_gpu": dG_err, "gmres_iters": int(np.median(iters)),
+        "dG_kcal": float(np.mean(dGs)), "dG_rel_err_vs_f64_gpu": dG_err, "dG_rel_err_vs_oracle": dG_err_orc,
+        "gmres_iters": int(np.median(iters)),
         "refinement_sweeps": int(np.median(outer)),
         "matvec": {"gpairs_per_s": npts * npts / (mv_ms * 1e-3) / 1e9, "ms": mv_ms, "points": npts,
                    "tri_pairs_per_s": t.shape[0] ** 2 / (mv_ms * 1e-3), "precision": "f32"},

@@ -354,8 +354,15 @@ int pb_profile_read(pb_ctx* ctx, int kernel, int64_t* launches, double* total_ms
  * *status_out receives the status word the kernel wrote (PB_ETIMEOUT when the
  * wait ran out). The kernel returns normally and the context stays usable. */
 int pb_selftest_wait(pb_ctx* ctx, int64_t polls, int* status_out);
-/* Number of kernels this library has launched in this process (all kinds). */
+/* Number of kernels this library has launched in this process (all kinds;
+ * a kernel inside a replayed CUDA graph counts once per replay). */
 int64_t pb_launch_count(void);
+/* GMRES iterations (pb_solve, pb_solvation_energy, the request server) are
+ * captured into a CUDA graph at their second iteration and replayed from then
+ * on (1, the default; the environment variable PBBEM_GRAPHS=0 starts with 0),
+ * or launched kernel by kernel (0). The same kernels run either way, so
+ * results are bitwise the same. Applies to solves started after the call. */
+int pb_set_graphs(pb_ctx* ctx, int enable);
 
 #ifdef __cplusplus
 }

@@ -142,6 +142,11 @@ def pb_launch_count() -> int:
     return int(N.load().pb_launch_count())
 
 
+def pb_set_graphs(ctx: Ctx, enable: bool = True):
+    """Replay GMRES iterations from CUDA graphs (default) or launch them kernel by kernel."""
+    _check(N.load().pb_set_graphs(ctx.ptr, 1 if enable else 0))
+
+
 def pb_version() -> str:
     return N.load().pb_version().decode()
 

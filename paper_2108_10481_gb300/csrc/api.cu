@@ -12,8 +12,79 @@ namespace pb {
 
 static thread_local char g_err[1024] = "";
 static std::atomic<int64_t> g_launches{0};
+static thread_local StepGraph* t_capture = nullptr;
+static std::atomic<uint64_t> g_ws_gen{1};
 
-void count_launch(int n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+uint64_t ws_generation() { return g_ws_gen.load(); }
+
+void count_launch(int n) {
+    if (t_capture) t_capture->launches += n;  // runs once per replay, counted then
+    else g_launches.fetch_add(n, std::memory_order_relaxed);
+}
+
+StepGraph* capturing() { return t_capture; }
+
+void graph_free(StepGraph& g) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    for (auto& t : g.timers) {
+        cudaEventDestroy(t.e0);
+        cudaEventDestroy(t.e1);
+    }
+    g = StepGraph();
+}
+
+int graph_capture(StepGraph& g, cudaStream_t s, const std::function<int()>& body) {
+    graph_free(g);
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+        cudaGetLastError();
+        g.failed = true;
+        return PB_OK;
+    }
+    const uint64_t gen = ws_generation();
+    t_capture = &g;
+    const int rc = body();
+    t_capture = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(s, &graph);
+    if (rc == PB_OK && e == cudaSuccess && graph) e = cudaGraphInstantiate(&g.exec, graph, 0);
+    if (graph) cudaGraphDestroy(graph);
+    if (rc != PB_OK || e != cudaSuccess || !g.exec) {
+        cudaGetLastError();
+        graph_free(g);
+        g.failed = true;
+        return rc;
+    }
+    if (ws_generation() != gen) {  // the body moved a workspace while it was captured
+        graph_free(g);
+        g.failed = true;
+        return PB_OK;
+    }
+    g.gen = gen;
+    return PB_OK;
+}
+
+void graph_check(StepGraph& g) {
+    if (g.exec && g.gen != ws_generation()) graph_free(g);
+}
+
+int graph_replay(StepGraph& g, cudaStream_t s) {
+    PB_CUDA(cudaGraphLaunch(g.exec, s));
+    g_launches.fetch_add(g.launches, std::memory_order_relaxed);
+    return PB_OK;
+}
+
+int graph_credit(pb_ctx* ctx, StepGraph& g) {
+    for (auto& t : g.timers) {
+        float ms = 0.0f;
+        PB_CUDA(cudaEventElapsedTime(&ms, t.e0, t.e1));
+        KernelStats& st = ctx->stats[t.id];
+        st.ms += ms;
+        st.launches += 1;
+        st.pairs += t.pairs;
+        st.ops += t.pairs * t.ops;
+    }
+    return PB_OK;
+}
 
 int set_error(int code, const char* fmt, ...) {
     va_list ap;
@@ -38,6 +109,7 @@ int dev_alloc(void** p, size_t bytes) {
 
 int ws_reserve(Workspace& w, size_t bytes) {
     if (bytes <= w.bytes) return PB_OK;
+    g_ws_gen.fetch_add(1);
     ws_free(w);
     PB_TRY(dev_alloc(&w.ptr, bytes));
     w.bytes = bytes;
@@ -45,6 +117,7 @@ int ws_reserve(Workspace& w, size_t bytes) {
 }
 
 void ws_free(Workspace& w) {
+    if (w.ptr) g_ws_gen.fetch_add(1);
     if (w.ptr) cudaFree(w.ptr);
     w.ptr = nullptr;
     w.bytes = 0;
@@ -86,6 +159,8 @@ extern "C" int pb_init(int device, pb_ctx** out) {
     c->encode_tiled = fn;
     const char* pk = getenv("PBBEM_PAIR_KERNEL");
     if (pk && pk[0] == '1') c->pair_kernel = 1;
+    const char* gr = getenv("PBBEM_GRAPHS");
+    if (gr && gr[0] == '0') c->graphs = 0;
     *out = c;
     return PB_OK;
 }
@@ -134,3 +209,9 @@ extern "C" int pb_profile_read(pb_ctx* ctx, int kernel, int64_t* launches, doubl
 }
 
 extern "C" int64_t pb_launch_count(void) { return g_launches.load(); }
+
+extern "C" int pb_set_graphs(pb_ctx* ctx, int enable) {
+    if (!ctx) return set_error(PB_EINVAL, "pb_set_graphs: NULL context");
+    ctx->graphs = enable ? 1 : 0;
+    return PB_OK;
+}

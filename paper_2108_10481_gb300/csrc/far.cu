@@ -894,11 +894,22 @@ struct Timer {
     double pairs, ops;
     Timer(pb_ctx* c, int k, cudaStream_t st, double p, double o) : ctx(c), id(k), s(st), pairs(p), ops(o) {
         if (ctx->profile && cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess)
-            cudaEventRecord(e0, s);
+            record(e0);
+    }
+    // inside a stream capture an event record becomes a graph node only when
+    // marked external (otherwise it only orders the captured work)
+    void record(cudaEvent_t e) {
+        if (capturing()) cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+        else cudaEventRecord(e, s);
     }
     void stop() {
         if (!e1) return;
-        cudaEventRecord(e1, s);
+        record(e1);
+        if (StepGraph* g = capturing()) {  // recorded again by every replay
+            g->timers.push_back({id, e0, e1, pairs, ops});
+            e0 = e1 = nullptr;
+            return;
+        }
         KernelStats& st = ctx->stats[id];
         st.events.push_back({e0, e1});
         st.launches += 1;

@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -74,6 +75,36 @@ struct KernelStats {
     double ms = 0.0, pairs = 0.0, ops = 0.0;
 };
 void count_launch(int n = 1);
+
+// A launch sequence captured once into a CUDA graph and then replayed (the
+// body of one GMRES iteration). Kernel launches and profiled pair-kernel
+// launches seen while capturing are credited again on every replay.
+struct CapturedTimer {
+    int id;
+    cudaEvent_t e0, e1;
+    double pairs, ops;
+};
+struct StepGraph {
+    cudaGraphExec_t exec = nullptr;
+    uint64_t gen = 0;                  // workspace generation the graph's pointers belong to
+    int64_t launches = 0;              // kernels per replay
+    int applies = 0;                   // operator applications per replay
+    std::vector<CapturedTimer> timers;  // event pairs recorded by every replay
+    bool failed = false;               // capture was refused: run the body directly
+};
+StepGraph* capturing();  // the graph this thread is capturing, or null
+// Counts workspace (re)allocations: a captured graph whose generation differs
+// may hold a freed pointer and must be captured again.
+uint64_t ws_generation();
+// Drop g if a workspace has moved since it was captured.
+void graph_check(StepGraph& g);
+// Capture body() on stream s (nothing runs); on failure g.failed is set and
+// PB_OK returned so that the caller runs the body directly.
+int graph_capture(StepGraph& g, cudaStream_t s, const std::function<int()>& body);
+int graph_replay(StepGraph& g, cudaStream_t s);
+// after a replay has completed: its profiled launches into the context's statistics
+int graph_credit(pb_ctx* ctx, StepGraph& g);
+void graph_free(StepGraph& g);
 }  // namespace pb
 
 namespace pb {
@@ -95,6 +126,7 @@ struct pb_ctx {
     int num_sms = 0;
     int cc_major = 0, cc_minor = 0;
     void* encode_tiled = nullptr;  // cuTensorMapEncodeTiled entry point
+    int graphs = 1;                // replay GMRES iterations from CUDA graphs
 };
 
 struct pb_mesh {

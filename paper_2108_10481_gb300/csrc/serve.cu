@@ -54,6 +54,8 @@ struct ServeReq {
     GmresWork G;
     bool mixed = false;
     int mmax = 0;
+    int slot = -1;            // row of the server's residual table while active
+    StepGraph g_mid, g_tail;  // captured iteration pieces (Calderon middle; preconditioner + Arnoldi)
     // iteration state
     int phase = PH_START;
     int j = 0, outer = 0, total_it = 0;
@@ -79,14 +81,17 @@ struct pb_server {
     std::thread admit_thread;
     cudaStream_t s_main = nullptr, s_setup = nullptr;
     pb::BatchScratch bs;
-    double* res_dev = nullptr;
+    double* res_dev = nullptr;   // 4 doubles per slot (max_active slots)
     double* res_host = nullptr;
-    int res_cap = 0;
+    std::vector<int> free_slots;
 };
 
 namespace pb {
 
 static int free_req(ServeReq* r) {
+    graph_free(r->g_mid);
+    graph_free(r->g_tail);
+    solver_release(r->S);
     if (r->buf) cudaFree(r->buf);
     r->buf = nullptr;
     gmres_free(r->G);
@@ -208,16 +213,22 @@ static int tick(pb_server* srv) {
     if (act.empty()) return PB_OK;
     cudaStream_t s = srv->s_main;
     const int n = (int)act.size();
-    if (n > srv->res_cap) {
-        if (srv->res_dev) cudaFree(srv->res_dev);
-        if (srv->res_host) cudaFreeHost(srv->res_host);
-        srv->res_dev = nullptr;
-        srv->res_host = nullptr;
-        int cap = std::max(64, 2 * n);
-        PB_TRY(dev_alloc((void**)&srv->res_dev, sizeof(double) * 4 * cap));
-        PB_CUDA(cudaMallocHost((void**)&srv->res_host, sizeof(double) * 4 * cap));
-        srv->res_cap = cap;
-    }
+    for (ServeReq* r : act)
+        if (r->slot < 0) {
+            r->slot = srv->free_slots.back();
+            srv->free_slots.pop_back();
+        }
+    // an iteration piece from its CUDA graph once the request has run it once
+    auto piece = [&](ServeReq* r, StepGraph& g, const std::function<int()>& body) -> int {
+        graph_check(g);
+        if (!srv->ctx->graphs || g.failed) return body();
+        if (!g.exec) {
+            if (r->j < 1) return body();
+            PB_TRY(graph_capture(g, s, body));
+            if (g.failed) return body();
+        }
+        return graph_replay(g, s);
+    };
     auto it_prec = [](const ServeReq* r) { return r->mixed ? PB_F32 : PB_F64; };
     auto res_prec = [](const ServeReq* r) { return r->mixed ? PB_F32_ACCURATE : PB_F64; };
 
@@ -225,7 +236,7 @@ static int tick(pb_server* srv) {
     std::vector<FarJob> jobs[4];  // by precision
     for (ServeReq* r : act) {
         if (r->phase == PH_ITER)
-            jobs[it_prec(r)].push_back({r->m, r->nf, r->S.A, r->G.V + (int64_t)r->j * r->G.n, r->S.t3});
+            jobs[it_prec(r)].push_back({r->m, r->nf, r->S.A, r->G.vin, r->S.t3});
         else if (r->phase == PH_START && r->mixed && r->outer > 0)
             jobs[res_prec(r)].push_back({r->m, r->nf, r->S.A, r->x, r->S.t3});
     }
@@ -238,6 +249,11 @@ static int tick(pb_server* srv) {
         const int64_t n2 = 2 * r->m->nv;
         if (r->phase == PH_ITER) {
             pin[k] = r->S.t3;
+            if (r->pc >= PB_PC_CALDERON_FULL) {
+                PB_TRY(piece(r, r->g_mid, [r] { return calderon_pre(r->S, r->S.t3); }));
+                jobs[it_prec(r)].push_back({r->m, r->nf, r->S.C, r->S.t1, r->S.t2});
+            }
+            continue;  // the rest of the iteration follows the batched operators
         } else if (r->phase == PH_START) {
             if (r->mixed && r->outer > 0) {
                 vec_sub(n2, r->rhs, r->S.t3, r->rr, s);
@@ -259,18 +275,27 @@ static int tick(pb_server* srv) {
     for (int k = 0; k < n; ++k) {
         ServeReq* r = act[k];
         if (!pin[k]) continue;
-        if (r->pc >= PB_PC_CALDERON_FULL) PB_TRY(calderon_post(r->S, r->w));
-        double* slot = srv->res_dev + 4 * k;
-        if (r->phase == PH_ITER) PB_TRY(gm_step(r->G, r->j, r->w, slot, s));
-        else gm_norm2(r->G, r->w, slot, s);
+        double* slot = srv->res_dev + 4 * r->slot;
+        if (r->phase == PH_ITER) {
+            const int prec = it_prec(r);
+            PB_TRY(piece(r, r->g_tail, [r, prec, slot, s] {
+                if (r->pc >= PB_PC_CALDERON_FULL) PB_TRY(calderon_post(r->S, r->w));
+                else PB_TRY(apply_prec(r->S, prec, r->S.t3, r->w));
+                return gm_step(r->G, r->w, slot, s);
+            }));
+        } else {
+            if (r->pc >= PB_PC_CALDERON_FULL) PB_TRY(calderon_post(r->S, r->w));
+            gm_norm2(r->G, r->w, slot, s);
+        }
     }
-    PB_CUDA(cudaMemcpyAsync(srv->res_host, srv->res_dev, sizeof(double) * 4 * n, cudaMemcpyDeviceToHost, s));
+    PB_CUDA(cudaMemcpyAsync(srv->res_host, srv->res_dev, sizeof(double) * 4 * srv->max_active,
+                            cudaMemcpyDeviceToHost, s));
     PB_CUDA(cudaStreamSynchronize(s));
 
     // host decisions
     for (int k = 0; k < n; ++k) {
         ServeReq* r = act[k];
-        const double* h = srv->res_host + 4 * k;
+        const double* h = srv->res_host + 4 * r->slot;
         const double tol = r->opts.tol;
         if (r->phase == PH_START) {
             const double beta = std::sqrt(h[0]);
@@ -289,7 +314,7 @@ static int tick(pb_server* srv) {
                 continue;
             }
             r->inner_tol = r->mixed ? std::min(0.5, std::max(r->opts.inner_tol, 0.5 * tol / r->rel)) : tol;
-            PB_TRY(gm_begin(r->G, r->w, srv->res_dev + 4 * k, s));
+            PB_TRY(gm_begin(r->G, r->w, srv->res_dev + 4 * r->slot, s));
             if (r->mixed) PB_CUDA(cudaMemsetAsync(r->dd, 0, sizeof(double) * 2 * r->m->nv, s));
             r->j = 0;
             r->phase = PH_ITER;
@@ -332,6 +357,8 @@ static int tick(pb_server* srv) {
                            &dGk, s);
         if (rc != PB_OK && r->status == PB_OK) r->status = rc;
         if (r->status == PB_OK) r->status = check_status(r->m, s);
+        srv->free_slots.push_back(r->slot);
+        r->slot = -1;
         finish(srv, r, dGp, dGk);
         delete r;
     }
@@ -357,6 +384,17 @@ extern "C" int pb_server_create(pb_ctx* ctx, int64_t hbm_budget_bytes, int max_a
         delete srv;
         return set_error(PB_ECUDA, "stream creation failed");
     }
+    // one residual row per slot, fixed for a request's lifetime (captured graphs write to it)
+    if (dev_alloc((void**)&srv->res_dev, sizeof(double) * 4 * max_active) != PB_OK ||
+        cudaMallocHost((void**)&srv->res_host, sizeof(double) * 4 * max_active) != cudaSuccess) {
+        if (srv->res_dev) cudaFree(srv->res_dev);
+        cudaStreamDestroy(srv->s_main);
+        cudaStreamDestroy(srv->s_setup);
+        delete srv;
+        return set_error(PB_ENOMEM, "pb_server_create: residual table");
+    }
+    cudaMemset(srv->res_dev, 0, sizeof(double) * 4 * max_active);
+    for (int k = max_active - 1; k >= 0; --k) srv->free_slots.push_back(k);
     srv->admit_thread = std::thread(admission_loop, srv);
     *out = srv;
     return PB_OK;

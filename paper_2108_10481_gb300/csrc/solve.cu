@@ -175,20 +175,85 @@ __global__ void k_vh(int64_t n, int nk, const double* __restrict__ V, int64_t ld
     for (int k = 0; k < nk; ++k) s += V[(int64_t)k * ldv + i] * h[k];
     w[i] += sign * s;
 }
-// normalise w into V[j+1] with its norm^2 in h[j+1]; zero vector on breakdown
-__global__ void k_normalize(int64_t n, const double* __restrict__ w, const double* __restrict__ hcol, int j,
-                            double* __restrict__ vout) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    double nrm = sqrt(hcol[j + 1]);
-    if (i < n) vout[i] = nrm > 1e-300 ? w[i] / nrm : 0.0;
-}
-__global__ void k_sqrt_entry(double* __restrict__ h, int j) { h[j] = sqrt(h[j]); }
+// ---- one Arnoldi step with the iteration index j read from the device
+constexpr int DOT_KY = 32;  // grid rows of the Gram-Schmidt dots (stride over k <= j)
 
-// Givens rotations on column j of the Hessenberg matrix (stored column-major,
-// ldh = m + 1), g the rotated right-hand side; res[0] = |g[j+1]| / beta.
-__global__ void k_givens(int j, double* __restrict__ H, int ldh, double* __restrict__ cs, double* __restrict__ sn,
-                         double* __restrict__ g, double beta, double* __restrict__ res) {
+// part[k * nchunk + c] = chunk c of V[k] . w for k = 0..j
+__global__ void k_dots_j(int64_t n, const double* __restrict__ V, const double* __restrict__ w,
+                         double* __restrict__ part, int nchunk, const int* __restrict__ jdev) {
+    __shared__ double red[DOT_THREADS / 32];
+    const int j = *jdev;
+    const int c = blockIdx.x;
+    const int64_t i0 = (int64_t)c * DOT_CHUNK;
+    const int64_t i1 = min(n, i0 + DOT_CHUNK);
+    for (int k = blockIdx.y; k <= j; k += gridDim.y) {
+        const double* vk = V + (int64_t)k * n;
+        double s = 0.0;
+        for (int64_t i = i0 + threadIdx.x; i < i1; i += DOT_THREADS) s += vk[i] * w[i];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double t = 0.0;
+            for (int q = 0; q < DOT_THREADS / 32; ++q) t += red[q];
+            part[(int64_t)k * nchunk + c] = t;
+        }
+        __syncthreads();
+    }
+}
+// pass 0: column j of H; pass 1: y (the second Gram-Schmidt pass); k = 0..j
+__global__ void k_dots_finish_j(int nchunk, const double* __restrict__ part, double* __restrict__ H, int ldh,
+                                double* __restrict__ y, const int* __restrict__ jdev, int pass) {
+    const int j = *jdev;
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k > j) return;
+    double t = 0.0;
+    for (int c = 0; c < nchunk; ++c) t += part[(int64_t)k * nchunk + c];
+    if (pass == 0) H[(int64_t)j * ldh + k] = t;
+    else y[k] = t;
+}
+// w -= sum_{k<=j} V[k] c[k], c = column j of H (pass 0) or y (pass 1)
+__global__ void k_vh_j(int64_t n, const double* __restrict__ V, const double* __restrict__ H, int ldh,
+                       const double* __restrict__ y, const int* __restrict__ jdev, int pass, double* __restrict__ w) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int j = *jdev;
+    const double* c = pass == 0 ? H + (int64_t)j * ldh : y;
+    double s = 0.0;
+    for (int k = 0; k <= j; ++k) s += V[(int64_t)k * n + i] * c[k];
+    w[i] -= s;
+}
+// column j of H += y (the second pass's coefficients); H[j+1, j] = ||w||^2
+__global__ void k_hcol_j(int nchunk, const double* __restrict__ part, double* __restrict__ H, int ldh,
+                         const double* __restrict__ y, const int* __restrict__ jdev) {
+    const int j = *jdev;
     double* h = H + (int64_t)j * ldh;
+    for (int k = threadIdx.x; k <= j; k += blockDim.x) h[k] += y[k];
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int c = 0; c < nchunk; ++c) t += part[c];
+        h[j + 1] = t;
+    }
+}
+// V[j+1] = vin = w / ||w|| (zero vector on breakdown)
+__global__ void k_normalize_j(int64_t n, const double* __restrict__ w, const double* __restrict__ H, int ldh,
+                              const int* __restrict__ jdev, double* __restrict__ V, double* __restrict__ vin) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int j = *jdev;
+    const double nrm = sqrt(H[(int64_t)j * ldh + j + 1]);
+    const double v = nrm > 1e-300 ? w[i] / nrm : 0.0;
+    V[(int64_t)(j + 1) * n + i] = v;
+    vin[i] = v;
+}
+// Givens rotations on column j of H (column-major, ldh = m + 1) and on g;
+// res[0] = |g[j+1]| / beta, res[1] = the new diagonal; then j += 1
+__global__ void k_givens_j(double* __restrict__ H, int ldh, double* __restrict__ cs, double* __restrict__ sn,
+                           double* __restrict__ g, const double* __restrict__ beta, double* __restrict__ res,
+                           int* __restrict__ jdev) {
+    const int j = *jdev;
+    double* h = H + (int64_t)j * ldh;
+    h[j + 1] = sqrt(h[j + 1]);
     for (int i = 0; i < j; ++i) {
         double t = cs[i] * h[i] + sn[i] * h[i + 1];
         h[i + 1] = -sn[i] * h[i] + cs[i] * h[i + 1];
@@ -203,9 +268,29 @@ __global__ void k_givens(int j, double* __restrict__ H, int ldh, double* __restr
     h[j + 1] = 0.0;
     g[j + 1] = -s * g[j];
     g[j] = c * g[j];
-    res[0] = fabs(g[j + 1]) / beta;
+    res[0] = fabs(g[j + 1]) / beta[0];
     res[1] = den;
+    *jdev = j + 1;
 }
+// g = beta e1, beta = sqrt(n2[0]), j = 0
+__global__ void k_gm_begin(const double* __restrict__ n2, double* __restrict__ g, double* __restrict__ beta,
+                           int* __restrict__ jdev) {
+    const double b = sqrt(n2[0]);
+    g[0] = b;
+    beta[0] = b;
+    *jdev = 0;
+}
+// V[0] = vin = w / beta
+__global__ void k_normalize0(int64_t n, const double* __restrict__ w, const double* __restrict__ n2,
+                             double* __restrict__ V, double* __restrict__ vin) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double nrm = sqrt(n2[0]);
+    const double v = nrm > 1e-300 ? w[i] / nrm : 0.0;
+    V[i] = v;
+    vin[i] = v;
+}
+
 // back substitution R y = g (R upper triangular k x k in H)
 __global__ void k_backsolve(int k, const double* __restrict__ H, int ldh, const double* __restrict__ g,
                             double* __restrict__ y) {
@@ -263,7 +348,7 @@ int gmres_alloc(GmresWork& G, int64_t n, int mmax) {
     // offsets (in doubles) of every array, then one allocation of the total
     const size_t oV = 0, ow = oV + (m + 1) * n, oH = ow + n, ocs = oH + (m + 1) * m, osn = ocs + m,
                  oy = osn + m, og = oy + m, opart = og + m + 2, ores = opart + (m + 2) * nchunk,
-                 total = ores + 16;
+                 ovin = ores + 16, ojd = ovin + n, total = ojd + 2;
     PB_TRY(dev_alloc(&G.block, sizeof(double) * total));
     double* p = (double*)G.block;
     G.V = p + oV;
@@ -274,7 +359,9 @@ int gmres_alloc(GmresWork& G, int64_t n, int mmax) {
     G.y = p + oy;
     G.g = p + og;
     G.part = p + opart;
-    G.res = p + ores;  // res[0..1] estimates, res[2..] scratch
+    G.res = p + ores;  // res[0..1] estimates, res[2..3] scratch, res[4] beta
+    G.vin = p + ovin;
+    G.jdev = (int*)(p + ojd);
     G.mmax = mmax;
     G.n = n;
     return PB_OK;
@@ -290,6 +377,36 @@ void dots(GmresWork& G, const double* V, int nk, const double* w, double* out, i
     dim3 grid(nchunk, nk);
     k_dots<<<grid, DOT_THREADS, 0, s>>>(G.n, V, G.n, w, G.part, nchunk); ::pb::count_launch();
     k_dots_finish<<<(nk + 127) / 128, 128, 0, s>>>(nk, nchunk, G.part, out, accumulate); ::pb::count_launch();
+}
+
+// One GMRES iteration: w = P^-1 A V[j], then the Arnoldi step.
+static int gm_iteration(Solver& S, GmresWork& G, int prec) {
+    PB_TRY(apply_op(S, prec, G.vin, G.w));
+    return gm_step(G, G.w, G.res, S.s);
+}
+
+// The iteration from its CUDA graph: captured at the second iteration (the
+// first has reserved every workspace) and replayed from then on.
+static int iterate(Solver& S, GmresWork& G, int prec, int j, StepGraph** replayed) {
+    *replayed = nullptr;
+    StepGraph& g = S.step[prec & 3];
+    graph_check(g);
+    if (!S.graphs || g.failed || (j == 0 && !g.exec)) return gm_iteration(S, G, prec);
+    if (!g.exec) {
+        const int a0 = S.applies;
+        PB_TRY(graph_capture(g, S.s, [&] { return gm_iteration(S, G, prec); }));
+        g.applies = S.applies - a0;
+        S.applies = a0;
+        if (g.failed) return gm_iteration(S, G, prec);
+    }
+    PB_TRY(graph_replay(g, S.s));
+    S.applies += g.applies;
+    *replayed = &g;
+    return PB_OK;
+}
+
+void solver_release(Solver& S) {
+    for (auto& g : S.step) graph_free(g);
 }
 
 // Left-preconditioned GMRES on A x = b from x (in/out; x_zero says x = 0, so
@@ -320,32 +437,17 @@ static int gmres(Solver& S, GmresWork& G, int prec, const double* b, double* x, 
     *res_out = denom > 0.0 ? beta / denom : 0.0;
     if (!std::isfinite(beta)) return set_error(PB_ENUMERIC, "GMRES: initial residual is not finite");
     if (beta == 0.0 || *res_out <= tol || max_it <= 0) return PB_OK;
-    const int ldh = G.mmax + 1;
-    PB_CUDA(cudaMemsetAsync(G.H, 0, sizeof(double) * (size_t)ldh * G.mmax, s));
-    PB_CUDA(cudaMemsetAsync(G.g, 0, sizeof(double) * (G.mmax + 2), s));
-    PB_CUDA(cudaMemcpyAsync(G.g, &beta, sizeof(double), cudaMemcpyHostToDevice, s));
-    k_normalize<<<nb(n), 256, 0, s>>>(n, G.w, scratch, 0, G.V); ::pb::count_launch();  // V[0] = w / beta
+    PB_TRY(gm_begin(G, G.w, scratch + 1, s));
     int k = 0;
     double res = *res_out;
     const int mmax = std::min(max_it, G.mmax);
     for (int j = 0; j < mmax; ++j) {
-        const double* vj = G.V + (int64_t)j * n;
-        PB_TRY(apply_op(S, prec, vj, G.w));
-        double* hcol = G.H + (int64_t)j * ldh;
-        // classical Gram-Schmidt, applied twice; the second pass's
-        // coefficients are added to the first
-        dots(G, G.V, j + 1, G.w, hcol, 0, s);
-        k_vh<<<nb(n), 256, 0, s>>>(n, j + 1, G.V, n, hcol, -1.0, G.w); ::pb::count_launch();
-        dots(G, G.V, j + 1, G.w, G.y, 0, s);
-        k_vh<<<nb(n), 256, 0, s>>>(n, j + 1, G.V, n, G.y, -1.0, G.w); ::pb::count_launch();
-        k_add_inplace<<<nb(j + 1), 256, 0, s>>>(j + 1, G.y, hcol); ::pb::count_launch();
-        dots(G, G.w, 1, G.w, hcol + j + 1, 0, s);                          // ||w||^2
-        k_normalize<<<nb(n), 256, 0, s>>>(n, G.w, hcol, j, G.V + (int64_t)(j + 1) * n); ::pb::count_launch();
-        k_sqrt_entry<<<1, 1, 0, s>>>(hcol, j + 1); ::pb::count_launch();
-        k_givens<<<1, 1, 0, s>>>(j, G.H, ldh, G.cs, G.sn, G.g, beta, G.res); ::pb::count_launch();
+        StepGraph* g = nullptr;
+        PB_TRY(iterate(S, G, prec, j, &g));
         double hr[2];
         PB_CUDA(cudaMemcpyAsync(hr, G.res, sizeof(hr), cudaMemcpyDeviceToHost, s));
         PB_CUDA(cudaStreamSynchronize(s));
+        if (g && S.m->ctx->profile) PB_TRY(graph_credit(S.m->ctx, *g));
         k = j + 1;
         res = hr[0] * beta / denom;
         if (!std::isfinite(res)) {
@@ -355,9 +457,7 @@ static int gmres(Solver& S, GmresWork& G, int prec, const double* b, double* x, 
         }
         if (res <= tol || hr[1] == 0.0) break;
     }
-    k_backsolve<<<1, 1, 0, s>>>(k, G.H, ldh, G.g, G.y); ::pb::count_launch();
-    k_vh<<<nb(n), 256, 0, s>>>(n, k, G.V, n, G.y, 1.0, x); ::pb::count_launch();
-    PB_CUDA(cudaGetLastError());
+    PB_TRY(gm_finish(G, k, x, s));
     *iters = k;
     *res_out = res;
     return PB_OK;
@@ -423,68 +523,40 @@ int check_status(const pb_mesh* m, cudaStream_t s) {
     return PB_OK;
 }
 
-// ---------------------------------------------- step-wise GMRES (the server)
-// The same arithmetic as gmres() above, split at the points where the host
-// needs a scalar, with every scalar kept on the device.
-__global__ void k_gm_begin(const double* __restrict__ n2, double* __restrict__ g, double* __restrict__ beta) {
-    const double b = sqrt(n2[0]);
-    g[0] = b;
-    beta[0] = b;
-}
-__global__ void k_givens_dev(int j, double* __restrict__ H, int ldh, double* __restrict__ cs, double* __restrict__ sn,
-                             double* __restrict__ g, const double* __restrict__ beta, double* __restrict__ res) {
-    double* h = H + (int64_t)j * ldh;
-    for (int i = 0; i < j; ++i) {
-        double t = cs[i] * h[i] + sn[i] * h[i + 1];
-        h[i + 1] = -sn[i] * h[i] + cs[i] * h[i + 1];
-        h[i] = t;
-    }
-    double a = h[j], b = h[j + 1];
-    double den = hypot(a, b);
-    double c = den > 0.0 ? a / den : 1.0, s = den > 0.0 ? b / den : 0.0;
-    cs[j] = c;
-    sn[j] = s;
-    h[j] = den;
-    h[j + 1] = 0.0;
-    g[j + 1] = -s * g[j];
-    g[j] = c * g[j];
-    res[0] = fabs(g[j + 1]) / beta[0];
-    res[1] = den;
-}
-
+// ---------------------------------------------- step-wise GMRES
 void gm_norm2(GmresWork& G, const double* w, double* dst, cudaStream_t s) { dots(G, w, 1, w, dst, 0, s); }
 
 int gm_begin(GmresWork& G, const double* w, const double* n2, cudaStream_t s) {
     const int ldh = G.mmax + 1;
     PB_CUDA(cudaMemsetAsync(G.H, 0, sizeof(double) * (size_t)ldh * G.mmax, s));
     PB_CUDA(cudaMemsetAsync(G.g, 0, sizeof(double) * (G.mmax + 2), s));
-    k_gm_begin<<<1, 1, 0, s>>>(n2, G.g, G.res + 4);
+    k_gm_begin<<<1, 1, 0, s>>>(n2, G.g, G.res + 4, G.jdev);
     ::pb::count_launch();
-    k_normalize<<<nb(G.n), 256, 0, s>>>(G.n, w, n2 - 1, 0, G.V);  // reads n2[0] as hcol[1]
+    k_normalize0<<<nb(G.n), 256, 0, s>>>(G.n, w, n2, G.V, G.vin);
     ::pb::count_launch();
     PB_CUDA(cudaGetLastError());
     return PB_OK;
 }
 
-int gm_step(GmresWork& G, int j, double* w, double* res_out, cudaStream_t s) {
+// Classical Gram-Schmidt applied twice (the second pass's coefficients are
+// added to the first), normalisation and the Givens update of column j.
+int gm_step(GmresWork& G, double* w, double* res_out, cudaStream_t s) {
     const int64_t n = G.n;
     const int ldh = G.mmax + 1;
-    double* hcol = G.H + (int64_t)j * ldh;
-    dots(G, G.V, j + 1, w, hcol, 0, s);
-    k_vh<<<nb(n), 256, 0, s>>>(n, j + 1, G.V, n, hcol, -1.0, w);
-    ::pb::count_launch();
-    dots(G, G.V, j + 1, w, G.y, 0, s);
-    k_vh<<<nb(n), 256, 0, s>>>(n, j + 1, G.V, n, G.y, -1.0, w);
-    ::pb::count_launch();
-    k_add_inplace<<<nb(j + 1), 256, 0, s>>>(j + 1, G.y, hcol);
-    ::pb::count_launch();
-    dots(G, w, 1, w, hcol + j + 1, 0, s);
-    k_normalize<<<nb(n), 256, 0, s>>>(n, w, hcol, j, G.V + (int64_t)(j + 1) * n);
-    ::pb::count_launch();
-    k_sqrt_entry<<<1, 1, 0, s>>>(hcol, j + 1);
-    ::pb::count_launch();
-    k_givens_dev<<<1, 1, 0, s>>>(j, G.H, ldh, G.cs, G.sn, G.g, G.res + 4, res_out);
-    ::pb::count_launch();
+    const int nchunk = (int)((n + DOT_CHUNK - 1) / DOT_CHUNK);
+    const dim3 grid(nchunk, std::min(DOT_KY, G.mmax + 1));
+    const unsigned kb = (unsigned)((G.mmax + 1 + 127) / 128);
+    for (int pass = 0; pass < 2; ++pass) {
+        k_dots_j<<<grid, DOT_THREADS, 0, s>>>(n, G.V, w, G.part, nchunk, G.jdev);
+        k_dots_finish_j<<<kb, 128, 0, s>>>(nchunk, G.part, G.H, ldh, G.y, G.jdev, pass);
+        k_vh_j<<<nb(n), 256, 0, s>>>(n, G.V, G.H, ldh, G.y, G.jdev, pass, w);
+        ::pb::count_launch(3);
+    }
+    k_dots<<<dim3(nchunk, 1), DOT_THREADS, 0, s>>>(n, w, n, w, G.part, nchunk);  // ||w||^2 partials
+    k_hcol_j<<<1, 128, 0, s>>>(nchunk, G.part, G.H, ldh, G.y, G.jdev);
+    k_normalize_j<<<nb(n), 256, 0, s>>>(n, w, G.H, ldh, G.jdev, G.V, G.vin);
+    k_givens_j<<<1, 1, 0, s>>>(G.H, ldh, G.cs, G.sn, G.g, G.res + 4, res_out, G.jdev);
+    ::pb::count_launch(4);
     PB_CUDA(cudaGetLastError());
     return PB_OK;
 }
@@ -520,14 +592,43 @@ void vec_add(int64_t n, const double* a, double* y, cudaStream_t s) {
     ::pb::count_launch();
 }
 
+static int solve_body(pb_ctx* ctx, const pb_mesh* m, const pb_near* nf, const pb_params* prm, int form, int pc,
+                      const pb_solve_opts* o, const double* b, double* x, pb_solve_info* info, cudaStream_t s,
+                      Solver& S);
+
+// The solve runs on a stream of its own, ordered after the caller's stream
+// and before what the caller queues next: CUDA graphs cannot be captured on
+// the legacy default stream.
 static int solve_impl(pb_ctx* ctx, const pb_mesh* m, const pb_near* nf, const pb_params* prm, int form, int pc,
-                      const pb_solve_opts* o, const double* b, double* x, pb_solve_info* info, cudaStream_t s) {
+                      const pb_solve_opts* o, const double* b, double* x, pb_solve_info* info, cudaStream_t caller) {
     pb_solve_opts d = {1e-6, 500, 0, PB_F64, 1e-4, 20, 0, 0, 0, 0};
     if (!o) o = &d;
     if (!(o->tol > 0.0) || o->max_it < 1) return set_error(PB_EINVAL, "need tol > 0 and max_it >= 1");
     if (o->precision != PB_F64 && o->precision != PB_MIXED) return set_error(PB_EINVAL, "precision must be PB_F64 or PB_MIXED");
+    cudaStream_t s = nullptr;
+    cudaEvent_t fence = nullptr;
+    PB_CUDA(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    if (cudaEventCreateWithFlags(&fence, cudaEventDisableTiming) != cudaSuccess) {
+        cudaStreamDestroy(s);
+        return set_error(PB_ECUDA, "cudaEventCreate failed");
+    }
+    cudaEventRecord(fence, caller);
+    cudaStreamWaitEvent(s, fence, 0);
     Solver S;
+    int rc = solve_body(ctx, m, nf, prm, form, pc, o, b, x, info, s, S);
+    solver_release(S);
+    cudaEventRecord(fence, s);
+    cudaStreamWaitEvent(caller, fence, 0);
+    cudaEventDestroy(fence);
+    cudaStreamDestroy(s);
+    return rc;
+}
+
+static int solve_body(pb_ctx* ctx, const pb_mesh* m, const pb_near* nf, const pb_params* prm, int form, int pc,
+                      const pb_solve_opts* o, const double* b, double* x, pb_solve_info* info, cudaStream_t s,
+                      Solver& S) {
     PB_TRY(setup_solver(S, m, nf, prm, form, pc, o, s));
+    S.graphs = ctx->graphs != 0;
     const int64_t n2 = 2 * m->nv;
     int mmax = o->restart > 0 ? std::min(o->restart, o->max_it) : o->max_it;
     GmresWork G;

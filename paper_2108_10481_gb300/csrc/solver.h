@@ -20,7 +20,10 @@ struct Solver {
     int cheb_iters = 34;
     int applies = 0;
     cudaStream_t s;
+    bool graphs = false;        // replay iterations from CUDA graphs
+    StepGraph step[4];          // GMRES iteration body, by operator precision
 };
+void solver_release(Solver& S);
 
 struct GmresWork {
     double* V = nullptr;     // (m+1) x n
@@ -31,7 +34,9 @@ struct GmresWork {
     double* g = nullptr;     // m + 1
     double* y = nullptr;     // m
     double* part = nullptr;  // (m+1) x nchunk
-    double* res = nullptr;   // 2 (device)
+    double* res = nullptr;   // res[0..1] estimates, res[4] beta (device)
+    double* vin = nullptr;   // n: copy of V[j], the operator's input
+    int* jdev = nullptr;     // the iteration index j, kept on the device
     int mmax = 0;
     int64_t n = 0;
     void* block = nullptr;
@@ -46,10 +51,14 @@ void gmres_free(GmresWork& G);
 void dots(GmresWork& G, const double* V, int nk, const double* w, double* out, int accumulate, cudaStream_t s);
 int check_status(const pb_mesh* m, cudaStream_t s);
 
-// step-wise GMRES: scalars stay on the device
+// step-wise GMRES: every scalar, the iteration index included, stays on the
+// device, so that one iteration is the same launch sequence for every j
 void gm_norm2(GmresWork& G, const double* w, double* dst, cudaStream_t s);
+// g = beta e1 with beta = sqrt(n2[0]); V[0] = vin = w / beta; j = 0
 int gm_begin(GmresWork& G, const double* w, const double* n2, cudaStream_t s);
-int gm_step(GmresWork& G, int j, double* w, double* res_out, cudaStream_t s);
+// w = P^-1 A V[j]: orthogonalise, append V[j+1] (and vin), rotate column j;
+// res_out[0] = |g[j+1]| / beta, res_out[1] = the new diagonal; j += 1
+int gm_step(GmresWork& G, double* w, double* res_out, cudaStream_t s);
 int gm_finish(GmresWork& G, int k, double* x, cudaStream_t s);
 // Calderon preconditioner split around its operator application (t1 -> t2)
 int calderon_pre(Solver& S, const double* x);

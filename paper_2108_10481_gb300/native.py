@@ -86,6 +86,7 @@ SIGNATURES = {
                         ctypes.POINTER(c_double)],
     "pb_launch_count": [],
     "pb_selftest_wait": [P, c_int64, ctypes.POINTER(c_int)],
+    "pb_set_graphs": [P, c_int],
 }
 _RESTYPE = {"pb_last_error": c_char_p, "pb_version": c_char_p, "pb_launch_count": c_int64}
 
