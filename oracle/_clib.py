@@ -17,7 +17,10 @@ def build(force: bool = False) -> str:
     os.makedirs(_OUT_DIR, exist_ok=True)
     if force or not os.path.exists(_OUT) or os.path.getmtime(_OUT) < os.path.getmtime(_SRC):
         tmp = _OUT + f".tmp{os.getpid()}"
-        cmd = ["gcc", "-O2", "-fPIC", "-shared", "-fopenmp", "-std=c11", _SRC, "-o", tmp, "-lm"]
+        # no contraction into fused multiply-adds: the distance band's decision
+        # is then the same on every machine and in the CUDA library's host code
+        cmd = ["gcc", "-O2", "-ffp-contract=off", "-fPIC", "-shared", "-fopenmp", "-std=c11", _SRC, "-o", tmp,
+               "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _OUT)
     return _OUT
@@ -33,9 +36,9 @@ def lib():
             I64 = ctypes.c_int64
             I = ctypes.c_int
             D = ctypes.c_double
-            L.oracle_pair_blocks.argtypes = [P, P, I64, I64, I, P, P, I, P, P, D, P]
-            L.oracle_assemble_dense.argtypes = [P, I64, P, I64, I, P, P, I, P, P, D, I] + [P] * 7
-            L.oracle_assemble_rows.argtypes = [P, I64, P, I64, P, I64, I, P, P, I, P, P, D, I] + [P] * 7
+            L.oracle_pair_blocks.argtypes = [P, P, I64, I64, I, P, P, I, P, P, D, D, I, P, P, P]
+            L.oracle_assemble_dense.argtypes = [P, I64, P, I64, I, P, P, I, P, P, D, D, I, P, P, I] + [P] * 7
+            L.oracle_assemble_rows.argtypes = [P, I64, P, I64, P, I64, I, P, P, I, P, P, D, D, I, P, P, I] + [P] * 7
             L.oracle_rhs.argtypes = [P, I64, P, I64, I, P, P, P, P, I64, D, P, P]
             L.oracle_reaction_potential.argtypes = [P, I64, P, I64, I, P, P, P, P, P, I64, P]
             for f in (L.oracle_pair_blocks, L.oracle_assemble_dense, L.oracle_assemble_rows,

@@ -21,7 +21,11 @@
  * Quadrature (the discrete definition shared with the GPU path by
  * specification, not by code):
  *   - triangle pairs sharing no vertex: the same symmetric triangle rule on
- *     both triangles (points/weights passed in by the caller);
+ *     both triangles (points/weights passed in by the caller); with a distance
+ *     band (band_eta > 0), pairs whose centroids are closer than band_eta
+ *     times the sum of their radii (largest centroid-vertex distance) take a
+ *     second, finer rule instead, so that the coarse rule only meets pairs
+ *     that are far apart relative to their size;
  *   - coincident, edge-adjacent and vertex-adjacent pairs: regularising maps
  *     of [0,1]^4 in the manner of Sauter and Schwab (6, 6 and 2 regions) with
  *     an n-point Gauss-Legendre rule per dimension (nodes/weights passed in).
@@ -263,10 +267,41 @@ static void singular_pair(const tri_geom* t, const int* pt, const tri_geom* s, c
                     }
 }
 
+/* The distance band of the quadrature plan: the finer rule used on pairs that
+ * share no vertex but lie closer than eta times the sum of their radii. */
+typedef struct {
+    double eta;         /* 0: no band */
+    int nq;
+    const double* rl;
+    const double* rw;
+} band_rule;
+
+/* centroid and radius (largest centroid-vertex distance) of a triangle */
+static void centroid_radius(const tri_geom* g, double* c, double* rho) {
+    for (int k = 0; k < 3; ++k) c[k] = (g->p[0][k] + g->p[1][k] + g->p[2][k]) / 3.0;
+    double r2 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        double d[3];
+        sub3(g->p[a], c, d);
+        double q = dot3(d, d);
+        if (q > r2) r2 = q;
+    }
+    *rho = sqrt(r2);
+}
+
+static int in_band(const tri_geom* t, const tri_geom* s, double eta) {
+    double ct[3], cs[3], rt, rs, d[3];
+    centroid_radius(t, ct, &rt);
+    centroid_radius(s, cs, &rs);
+    sub3(ct, cs, d);
+    double lim = eta * (rt + rs);
+    return dot3(d, d) < lim * lim;
+}
+
 /* Local blocks of one triangle pair (test tau = tri ti, trial sigma = tri tj). */
 static void pair_blocks(const double* verts, const int32_t* tris, int64_t ti, int64_t tj,
                         int nq, const double* rl, const double* rw, int ng, const double* gx,
-                        const double* gw, double kappa, double blk[NOPS][3][3]) {
+                        const double* gw, double kappa, const band_rule* band, double blk[NOPS][3][3]) {
     memset(blk, 0, sizeof(double) * NOPS * 9);
     const int32_t* A = tris + 3 * ti;
     const int32_t* B = tris + 3 * tj;
@@ -279,7 +314,10 @@ static void pair_blocks(const double* verts, const int32_t* tris, int64_t ti, in
         for (int b = 0; b < 3; ++b)
             if (A[a] == B[b]) { sa[ns] = a; sb[ns] = b; ++ns; }
     if (ns == 0) {
-        far_pair(&t, &s, nq, rl, rw, kappa, blk);
+        if (band && band->eta > 0.0 && in_band(&t, &s, band->eta))
+            far_pair(&t, &s, band->nq, band->rl, band->rw, kappa, blk);
+        else
+            far_pair(&t, &s, nq, rl, rw, kappa, blk);
     } else if (ns == 3) {
         int id[3] = {0, 1, 2};
         singular_pair(&t, id, &s, id, COIN, 6, ng, gx, gw, kappa, blk);
@@ -302,9 +340,11 @@ static void pair_blocks(const double* verts, const int32_t* tris, int64_t ti, in
 /* Exposed for unit tests: the six local blocks of one pair, [6][3][3]. */
 int oracle_pair_blocks(const double* verts, const int32_t* tris, int64_t ti, int64_t tj, int nq,
                        const double* rl, const double* rw, int ng, const double* gx,
-                       const double* gw, double kappa, double* out) {
+                       const double* gw, double kappa, double band_eta, int nbq, const double* brl,
+                       const double* brw, double* out) {
     double blk[NOPS][3][3];
-    pair_blocks(verts, tris, ti, tj, nq, rl, rw, ng, gx, gw, kappa, blk);
+    band_rule band = {band_eta, nbq, brl, brw};
+    pair_blocks(verts, tris, ti, tj, nq, rl, rw, ng, gx, gw, kappa, &band, blk);
     memcpy(out, blk, sizeof(blk));
     return 0;
 }
@@ -332,9 +372,11 @@ static int colour_triangles(const int32_t* tris, int64_t nt, int64_t nv, int* co
  * plus the mass matrix mass[nv*nv]. Matrices must be zeroed by the caller. */
 int oracle_assemble_dense(const double* verts, int64_t nv, const int32_t* tris, int64_t nt,
                           int nq, const double* rl, const double* rw, int ng, const double* gx,
-                          const double* gw, double kappa, int nthreads, double* VL, double* KL,
+                          const double* gw, double kappa, double band_eta, int nbq, const double* brl,
+                          const double* brw, int nthreads, double* VL, double* KL,
                           double* DL, double* VY, double* KY, double* DY, double* mass) {
     double* mats[NOPS] = {VL, KL, DL, VY, KY, DY};
+    band_rule band = {band_eta, nbq, brl, brw};
     int* colour = (int*)malloc(sizeof(int) * (size_t)(nt > 0 ? nt : 1));
     if (!colour) return -1;
     int ncol = colour_triangles(tris, nt, nv, colour);
@@ -349,7 +391,7 @@ int oracle_assemble_dense(const double* verts, int64_t nv, const int32_t* tris, 
             const int32_t* A = tris + 3 * ti;
             for (int64_t tj = 0; tj < nt; ++tj) {
                 double blk[NOPS][3][3];
-                pair_blocks(verts, tris, ti, tj, nq, rl, rw, ng, gx, gw, kappa, blk);
+                pair_blocks(verts, tris, ti, tj, nq, rl, rw, ng, gx, gw, kappa, &band, blk);
                 const int32_t* B = tris + 3 * tj;
                 for (int o = 0; o < NOPS; ++o)
                     for (int a = 0; a < 3; ++a)
@@ -374,9 +416,11 @@ int oracle_assemble_dense(const double* verts, int64_t nv, const int32_t* tris, 
 int oracle_assemble_rows(const double* verts, int64_t nv, const int32_t* tris, int64_t nt,
                          const int64_t* rows, int64_t nrows, int nq, const double* rl,
                          const double* rw, int ng, const double* gx, const double* gw,
-                         double kappa, int nthreads, double* VL, double* KL, double* DL,
+                         double kappa, double band_eta, int nbq, const double* brl, const double* brw,
+                         int nthreads, double* VL, double* KL, double* DL,
                          double* VY, double* KY, double* DY, double* mass) {
     double* mats[NOPS] = {VL, KL, DL, VY, KY, DY};
+    band_rule band = {band_eta, nbq, brl, brw};
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
 #endif
@@ -391,7 +435,7 @@ int oracle_assemble_rows(const double* verts, int64_t nv, const int32_t* tris, i
             if (a < 0) continue;
             for (int64_t tj = 0; tj < nt; ++tj) {
                 double blk[NOPS][3][3];
-                pair_blocks(verts, tris, ti, tj, nq, rl, rw, ng, gx, gw, kappa, blk);
+                pair_blocks(verts, tris, ti, tj, nq, rl, rw, ng, gx, gw, kappa, &band, blk);
                 const int32_t* B = tris + 3 * tj;
                 for (int o = 0; o < NOPS; ++o)
                     for (int b = 0; b < 3; ++b) mats[o][r * nv + B[b]] += blk[o][a][b];

@@ -44,9 +44,23 @@ KCAL_PER_PAPER_UNIT = 4.0 * np.pi * 332.0636  # A12 reading: kcal/mol per e^2/A 
 @dataclass(frozen=True)
 class Plan:
     """Quadrature plan: regular triangle rule size and Gauss points per
-    dimension of the singular (Sauter-Schwab) rule."""
+    dimension of the singular (Sauter-Schwab) rule; optionally a distance band
+    (band_eta > 0) inside which pairs that share no vertex take the finer rule
+    band_q, the coarse far_q then serving only pairs farther apart than
+    band_eta times the sum of their radii. The paper pairs low regular orders
+    with far interactions (its FMM runs use order 3 regular, 4 singular); the
+    band makes that distinction per triangle pair.
+
+    The right-hand side and the reaction potential use the plan's reference
+    rule: band_q with a band, far_q without."""
     far_q: int = 6
     n_ss: int = 4
+    band_eta: float = 0.0
+    band_q: int = 6
+
+    @property
+    def ref_q(self) -> int:
+        return self.band_q if self.band_eta > 0 else self.far_q
 
 
 def _ptr(a: np.ndarray):
@@ -63,6 +77,11 @@ def _rules(plan: Plan):
     rl, rw = triangle_rule(plan.far_q)
     gx, gw = gauss_legendre01(plan.n_ss)
     return rl, rw, gx, gw
+
+
+def _band(plan: Plan):
+    bl, bw = triangle_rule(plan.band_q)
+    return float(plan.band_eta), bl.shape[0], bl, bw
 
 
 @dataclass
@@ -94,9 +113,11 @@ def pair_blocks(verts, tris, ti, tj, kappa, plan=Plan()):
     """Six local 3x3 blocks (V_L, K_L, D_L, V_Y, K_Y, D_Y) of one triangle pair."""
     v, t = _mesh_arrays(verts, tris)
     rl, rw, gx, gw = _rules(plan)
+    eta, nb, bl, bw = _band(plan)
     out = np.zeros((6, 3, 3))
     _clib.lib().oracle_pair_blocks(_ptr(v), _ptr(t), ti, tj, rl.shape[0], _ptr(rl), _ptr(rw),
-                                   gx.shape[0], _ptr(gx), _ptr(gw), float(kappa), _ptr(out))
+                                   gx.shape[0], _ptr(gx), _ptr(gw), float(kappa), eta, nb, _ptr(bl), _ptr(bw),
+                                   _ptr(out))
     return out
 
 
@@ -105,10 +126,11 @@ def assemble(verts, tris, kappa, plan=Plan(), nthreads=0) -> Operators:
     v, t = _mesh_arrays(verts, tris)
     nv, nt = v.shape[0], t.shape[0]
     rl, rw, gx, gw = _rules(plan)
+    eta, nb, bl, bw = _band(plan)
     mats = [np.zeros((nv, nv)) for _ in range(7)]
     rc = _clib.lib().oracle_assemble_dense(
         _ptr(v), nv, _ptr(t), nt, rl.shape[0], _ptr(rl), _ptr(rw), gx.shape[0], _ptr(gx),
-        _ptr(gw), float(kappa), int(nthreads), *[_ptr(m) for m in mats])
+        _ptr(gw), float(kappa), eta, nb, _ptr(bl), _ptr(bw), int(nthreads), *[_ptr(m) for m in mats])
     if rc < 0:
         raise RuntimeError(f"oracle assembly failed ({rc})")
     return Operators(*mats, kappa=float(kappa))
@@ -120,10 +142,12 @@ def assemble_rows(verts, tris, rows, kappa, plan=Plan(), nthreads=0):
     nv, nt = v.shape[0], t.shape[0]
     r = np.ascontiguousarray(rows, dtype=np.int64)
     rl, rw, gx, gw = _rules(plan)
+    eta, nb, bl, bw = _band(plan)
     mats = [np.zeros((r.shape[0], nv)) for _ in range(7)]
     _clib.lib().oracle_assemble_rows(
         _ptr(v), nv, _ptr(t), nt, _ptr(r), r.shape[0], rl.shape[0], _ptr(rl), _ptr(rw),
-        gx.shape[0], _ptr(gx), _ptr(gw), float(kappa), int(nthreads), *[_ptr(m) for m in mats])
+        gx.shape[0], _ptr(gx), _ptr(gw), float(kappa), eta, nb, _ptr(bl), _ptr(bw), int(nthreads),
+        *[_ptr(m) for m in mats])
     return dict(zip(["VL", "KL", "DL", "VY", "KY", "DY", "M"], mats))
 
 
@@ -133,7 +157,7 @@ def source_projections(verts, tris, xq, q, eps_int, plan=Plan()):
     v, t = _mesh_arrays(verts, tris)
     x = np.ascontiguousarray(xq, dtype=np.float64).reshape(-1, 3)
     qq = np.ascontiguousarray(q, dtype=np.float64).reshape(-1)
-    rl, rw = triangle_rule(plan.far_q)
+    rl, rw = triangle_rule(plan.ref_q)
     bD = np.zeros(v.shape[0])
     bN = np.zeros(v.shape[0])
     _clib.lib().oracle_rhs(_ptr(v), v.shape[0], _ptr(t), t.shape[0], rl.shape[0], _ptr(rl),
@@ -148,7 +172,7 @@ def reaction_potential(verts, tris, u_int, v_int, xq, plan=Plan()):
     x = np.ascontiguousarray(xq, dtype=np.float64).reshape(-1, 3)
     uu = np.ascontiguousarray(u_int, dtype=np.float64)
     vv = np.ascontiguousarray(v_int, dtype=np.float64)
-    rl, rw = triangle_rule(plan.far_q)
+    rl, rw = triangle_rule(plan.ref_q)
     phi = np.zeros(x.shape[0])
     _clib.lib().oracle_reaction_potential(_ptr(v), v.shape[0], _ptr(t), t.shape[0], rl.shape[0],
                                           _ptr(rl), _ptr(rw), _ptr(uu), _ptr(vv), _ptr(x),
