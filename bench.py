@@ -56,6 +56,10 @@ def parse():
     ap.add_argument("--no-baseline", action="store_true")
     ap.add_argument("--no-check", action="store_true", help="skip the FP64 accuracy solve (profiling runs)")
     ap.add_argument("--no-graphs", action="store_true", help="launch GMRES iterations kernel by kernel")
+    ap.add_argument("--plan", default="reference", choices=["reference", "band"],
+                    help="quadrature plan: reference (6-point far rule everywhere) or band (3-point far rule "
+                         "beyond --band-eta radii, 6-point inside)")
+    ap.add_argument("--band-eta", type=float, default=3.0)
     ap.add_argument("--serve", type=int, default=0,
                     help="serving benchmark on the first N requests of the seeded request stream instead")
     ap.add_argument("--rate-scale", type=float, default=0.7,
@@ -218,6 +222,20 @@ def stored_oracle_dG(args):
     return case["dG_kcal"] if case else None
 
 
+def quad_plan(args):
+    if args.plan == "band":
+        return {"far_q": 3, "n_ss": 4, "band_eta": args.band_eta, "band_q": 6}
+    return {"far_q": 6, "n_ss": 4, "band_eta": 0.0, "band_q": 6}
+
+
+def plan_text(args):
+    if args.plan == "band":
+        return (f"3-point degree-2 rule on pairs farther apart than {args.band_eta:g} times the sum of their radii, "
+                "6-point degree-4 rule inside that band and for the right-hand side and energy, singular 4^4 "
+                "Gauss per region")
+    return "far 6-point degree-4 rule, singular 4^4 Gauss per region"
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import torch.distributed as dist
@@ -244,8 +262,10 @@ def run_ours(args, rank, world, local_rank):
         if world > 1:
             dist.barrier()
 
+    plan = quad_plan(args)
+
     def step():
-        m = pb.pb_mesh_load(ctx, dv, dt)
+        m = pb.pb_mesh_load(ctx, dv, dt, **plan)
         nf = pb.pb_near_build(ctx, m, P.kappa)
         rhs = pb.pb_rhs_charges(ctx, m, dxq, dq, P, form)
         x, info = pb.pb_solve(ctx, m, nf, P, form, prec, rhs, opts=opts)
@@ -260,7 +280,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
 
     # accuracy of the measured path: FP64 GPU solve of the same case (outside the timed region)
-    m = pb.pb_mesh_load(ctx, dv, dt)
+    m = pb.pb_mesh_load(ctx, dv, dt, **plan)
     nf = pb.pb_near_build(ctx, m, P.kappa)
     rhs = pb.pb_rhs_charges(ctx, m, dxq, dq, P, form)
     dG64 = None
@@ -324,13 +344,13 @@ def run_ours(args, rank, world, local_rank):
         ht = _t.from_numpy(t).pin_memory().numpy()
         hxq = _t.from_numpy(np.ascontiguousarray(xq)).pin_memory().numpy()
         hq = _t.from_numpy(q).pin_memory().numpy()
-        pb.pb_solvation_energy(ctx, hv, ht, hxq, hq, P, form, prec, opts=opts)
+        pb.pb_solvation_energy(ctx, hv, ht, hxq, hq, P, form, prec, opts=opts, **plan)
         torch.cuda.synchronize()
         barrier()
         k_e2e = max(3, args.steps // 2)
         w0 = time.perf_counter()
         for _ in range(k_e2e):
-            pb.pb_solvation_energy(ctx, hv, ht, hxq, hq, P, form, prec, opts=opts)
+            pb.pb_solvation_energy(ctx, hv, ht, hxq, hq, P, form, prec, opts=opts, **plan)
         torch.cuda.synchronize()
         e2e_s = cross_rank_max(time.perf_counter() - w0, world, dev)
         e2e = {"value": world * k_e2e / e2e_s, "unit": UNIT,
@@ -362,7 +382,7 @@ def run_ours(args, rank, world, local_rank):
         "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
         "config": {"workload": workload_text(args, v, t, xq),
                    "case": args.case, "formulation": form, "preconditioner": prec, "precision": args.precision,
-                   "gmres_tol": args.tol, "quadrature": "far 6-point degree-4 rule, singular 4^4 Gauss per region",
+                   "gmres_tol": args.tol, "quadrature": plan_text(args),
                    "points": npts, "l2": "flushed (256 MB write) before every timed step",
                    "gmres_step": "CUDA graph replay" if not args.no_graphs else "kernel by kernel",
                    "parallelism": "replicas" if world > 1 else "1 GPU"},

@@ -107,12 +107,21 @@ typedef struct {
     double kappa;   /* inverse Debye length, 1/Angstrom (>= 0) */
 } pb_params;
 
-/* quadrature plan: the discrete definition of every operator entry */
+/* quadrature plan: the discrete definition of every operator entry
+ * (paper, Results: the orders of the regular and singular rules). A zeroed
+ * struct is not a valid plan; {6, 4, 0.0, 6} is the reference plan. */
 typedef struct {
     int far_q; /* points of the symmetric triangle rule used on both triangles of
                   pairs that share no vertex: 1, 3 (degree 2) or 6 (degree 4) */
     int n_ss;  /* Gauss-Legendre points per dimension of the regularised [0,1]^4
                   rule for coincident, edge- and vertex-adjacent pairs (1..12) */
+    double band_eta; /* distance band (0 = none, else in (0, 64]): pairs sharing no
+                  vertex whose centroids are closer than band_eta times the sum
+                  of their radii (largest centroid-vertex distance) take the
+                  band rule instead of far_q; the far-field pair kernel then
+                  runs with far_q and the near field adds the difference */
+    int band_q; /* band rule (3 or 6, finer than far_q; 0 means 6). With a band,
+                  the right-hand side and the energy use the band rule. */
 } pb_quad_plan;
 
 /* memory kind of pb_mesh_load's inputs */

@@ -157,9 +157,15 @@ def pb_init(device: int = 0) -> Ctx:
     return Ctx(h.value)
 
 
-def pb_mesh_load(ctx: Ctx, verts, tris, far_q: int = 6, n_ss: int = 4) -> Mesh:
-    """verts [N_v,3] float64 and tris [N_t,3] int32, numpy (host) or CUDA tensors."""
-    plan = N.pb_quad_plan(far_q, n_ss)
+def _plan(far_q=6, n_ss=4, band_eta=0.0, band_q=6):
+    return N.pb_quad_plan(int(far_q), int(n_ss), float(band_eta), int(band_q))
+
+
+def pb_mesh_load(ctx: Ctx, verts, tris, far_q: int = 6, n_ss: int = 4, band_eta: float = 0.0,
+                 band_q: int = 6) -> Mesh:
+    """verts [N_v,3] float64 and tris [N_t,3] int32, numpy (host) or CUDA tensors; the quadrature plan
+    (far rule, singular rule, optional distance band and its rule)."""
+    plan = _plan(far_q, n_ss, band_eta, band_q)
     if isinstance(verts, torch.Tensor) and verts.is_cuda:
         v = verts.contiguous()
         t = tris.to(torch.int32).contiguous()
@@ -268,7 +274,7 @@ def pb_server_create(ctx: Ctx, hbm_budget_bytes: int, max_active: int = 64) -> S
 
 
 def pb_submit(srv: Server, verts, tris, xq, q, params: Params, form, precond, opts=None, tag: int = 0,
-              far_q: int = 6, n_ss: int = 4):
+              far_q: int = 6, n_ss: int = 4, band_eta: float = 0.0, band_q: int = 6):
     """Queue one molecule (host arrays, copied by the library)."""
     v = np.ascontiguousarray(verts, dtype=np.float64)
     t = np.ascontiguousarray(tris, dtype=np.int32)
@@ -281,7 +287,7 @@ def pb_submit(srv: Server, verts, tris, xq, q, params: Params, form, precond, op
     r.params = params.c()
     r.form, r.precond = _form(form), _prec(precond)
     r.opts = opts if opts is not None else solve_opts()
-    r.plan = N.pb_quad_plan(far_q, n_ss)
+    r.plan = _plan(far_q, n_ss, band_eta, band_q)
     r.tag = int(tag)
     _check(N.load().pb_submit(srv.ptr, ctypes.byref(r)))
 
@@ -313,13 +319,13 @@ def pb_autotune(ctx: Ctx, mesh: Mesh, near: Near, params: Params, form, stream=N
 def pb_autotune_plan(ctx: Ctx, verts, tris, xq, q, params: Params, form, precond, tol_dG: float = 1e-6,
                      reference=(6, 4), opts=None, stream=None):
     """Cheapest quadrature plan whose Delta G stays within tol_dG of the reference plan:
-    returns ((far_q, n_ss), relative change)."""
+    returns ((far_q, n_ss, band_eta, band_q), relative change)."""
     v = np.ascontiguousarray(verts, dtype=np.float64)
     t = np.ascontiguousarray(tris, dtype=np.int32)
     x = np.ascontiguousarray(xq, dtype=np.float64).reshape(-1, 3)
     qq = np.ascontiguousarray(q, dtype=np.float64).reshape(-1)
     p = params.c()
-    ref = N.pb_quad_plan(*reference)
+    ref = _plan(*reference)
     out = N.pb_quad_plan()
     ch = ctypes.c_double()
     o = opts if opts is not None else solve_opts()
@@ -328,18 +334,19 @@ def pb_autotune_plan(ctx: Ctx, verts, tris, xq, q, params: Params, form, precond
                                      ctypes.c_void_p(qq.ctypes.data), qq.shape[0], ctypes.byref(p), ctypes.byref(ref),
                                      _form(form), _prec(precond), ctypes.byref(o), float(tol_dG), ctypes.byref(out),
                                      ctypes.byref(ch), _stream(stream)))
-    return (out.far_q, out.n_ss), ch.value
+    return (out.far_q, out.n_ss, out.band_eta, out.band_q), ch.value
 
 
 def pb_solvation_energy(ctx: Ctx, verts: np.ndarray, tris: np.ndarray, xq: np.ndarray, q: np.ndarray,
-                        params: Params, form, precond, far_q: int = 6, n_ss: int = 4, opts=None, stream=None):
+                        params: Params, form, precond, far_q: int = 6, n_ss: int = 4, opts=None, stream=None,
+                        band_eta: float = 0.0, band_q: int = 6):
     """Whole path from host arrays; returns (dG kcal/mol, info dict)."""
     v = np.ascontiguousarray(verts, dtype=np.float64)
     t = np.ascontiguousarray(tris, dtype=np.int32)
     x = np.ascontiguousarray(xq, dtype=np.float64).reshape(-1, 3)
     qq = np.ascontiguousarray(q, dtype=np.float64).reshape(-1)
     p = params.c()
-    plan = N.pb_quad_plan(far_q, n_ss)
+    plan = _plan(far_q, n_ss, band_eta, band_q)
     o = opts if opts is not None else solve_opts()
     info = N.pb_solve_info()
     out = ctypes.c_double()

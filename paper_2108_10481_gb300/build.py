@@ -13,7 +13,10 @@ INC = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libpbbem.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INC, "-I" + SRC]
+# host code without FMA contraction: the distance-band decision (mesh.cu) is then
+# made with the same arithmetic as the oracle's
+FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off", "-I" + INC,
+         "-I" + SRC]
 SOURCES = ["api.cu", "mesh.cu", "near.cu", "far.cu", "form.cu", "solve.cu", "rhs.cu", "serve.cu"]
 
 

@@ -135,22 +135,31 @@ struct pb_mesh {
     int Q = 0, n_ss = 0;
     double rule_l[6][3];
     double rule_w[6];
+    // distance band of the plan, and its reference rule (right-hand side and
+    // energy): the band rule with a band, the far rule without
+    double band_eta = 0.0;
+    int Qr = 0;
+    int64_t np_ref = 0;
+    double ref_l[6][3];
+    double ref_w[6];
     // device arrays
     double* verts = nullptr;    // nv x 3
     int32_t* tris = nullptr;    // nt x 3
     double* tgeo = nullptr;     // nt x 16: n(3), area, e0(3), e1(3), e2(3), pad(3)
     double* pts64 = nullptr;    // np x 4: x, y, z, w (rule weight x area)
+    double* pts_ref = nullptr;  // np_ref x 4: points of the reference rule (== pts64 without a band)
     float* pts32 = nullptr;     // np x 4: x, y, z, w rounded to float
     float* pts32lo = nullptr;   // np x 4: x - float(x), ..., 0
     int32_t* v2t_ptr = nullptr; // nv + 1
     int32_t* v2t = nullptr;     // 3 nt entries: tri * 3 + local vertex
-    // adjacent triangle pairs
-    int64_t npairs = 0;
-    int4* pairs = nullptr;      // (ti, tj, kind, perms): kind 0 coincident, 1 edge, 2 vertex
+    // listed triangle pairs: the adjacent ones [0, n_adj), then the band pairs
+    int64_t npairs = 0, n_adj = 0;
+    int4* pairs = nullptr;      // (ti, tj, kind, perms): kind 0 coincident, 1 edge, 2 vertex, 3 band
     int32_t* pair_rev = nullptr;   // index of the reversed pair (tj, ti)
     int32_t* pair_coin = nullptr;  // coincident pairs
-    int32_t* pair_prim = nullptr;  // pairs with ti < tj (each also gives its reverse)
-    int64_t n_coin = 0, n_prim = 0;
+    int32_t* pair_prim = nullptr;  // adjacent pairs with ti < tj (each also gives its reverse)
+    int32_t* pair_band = nullptr;  // band pairs with ti < tj (each also gives its reverse)
+    int64_t n_coin = 0, n_prim = 0, n_band = 0;
     // vertex-pair pattern of the near field (symmetric)
     int64_t nnz = 0;
     int32_t* row_ptr = nullptr; // nv + 1
@@ -182,6 +191,16 @@ inline Rule mesh_rule(const pb_mesh* m) {
         r.w[q] = m->rule_w[q];
     }
     r.Q = m->Q;
+    return r;
+}
+// the plan's reference rule (band rule with a band, else the far rule)
+inline Rule mesh_ref_rule(const pb_mesh* m) {
+    Rule r;
+    for (int q = 0; q < 6; ++q) {
+        for (int c = 0; c < 3; ++c) r.l[q][c] = m->ref_l[q][c];
+        r.w[q] = m->ref_w[q];
+    }
+    r.Q = m->Qr;
     return r;
 }
 

@@ -5,11 +5,19 @@
 // elements on a triangular surface mesh, one unknown per vertex. Far
 // (non-adjacent) triangle pairs are integrated with one symmetric triangle
 // rule on both triangles; pairs that share a vertex are singular and get the
-// regularised rule of the near field (near.cu).
+// regularised rule of the near field (near.cu). With a distance band in the
+// quadrature plan, non-adjacent pairs closer than band_eta times the sum of
+// their radii are listed too: the near field adds to them the difference of
+// the finer band rule and the far rule.
+//
+// The host work (pairs, band search, near pattern, contribution lists) runs
+// on several threads; every list is built per triangle or per vertex row, so
+// its order does not depend on the thread count.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <numeric>
+#include <thread>
 
 #include "internal.h"
 
@@ -44,9 +52,9 @@ static void rule_points(int q, double l[6][3], double w[6]) {
 // Per-triangle geometry and the quadrature points (FP64, plus float copies
 // relative to the mesh centre split into hi and lo parts).
 __global__ void k_geometry(const double* __restrict__ verts, const int32_t* __restrict__ tris,
-                           int64_t nt, Rule rule, double cx, double cy, double cz,
+                           int64_t nt, Rule rule, Rule ref, double cx, double cy, double cz,
                            double* __restrict__ tgeo, double* __restrict__ pts64,
-                           float* __restrict__ pts32, float* __restrict__ pts32lo) {
+                           float* __restrict__ pts32, float* __restrict__ pts32lo, double* __restrict__ pts_ref) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= nt) return;
     double p[3][3];
@@ -89,6 +97,34 @@ __global__ void k_geometry(const double* __restrict__ verts, const int32_t* __re
         pts32[4 * i + 3] = (float)w;
         pts32lo[4 * i + 3] = 0.0f;
     }
+    if (pts_ref)  // the plan's reference rule (right-hand side and energy), when it differs
+        for (int q = 0; q < ref.Q; ++q) {
+            int64_t i = t * ref.Q + q;
+            for (int k = 0; k < 3; ++k)
+                pts_ref[4 * i + k] = ref.l[q][0] * p[0][k] + ref.l[q][1] * p[1][k] + ref.l[q][2] * p[2][k];
+            pts_ref[4 * i + 3] = ref.w[q] * area;
+        }
+}
+
+// f(begin, end) over [0, n) split across up to 16 host threads
+template <class F>
+static void parallel_for(int64_t n, F&& f) {
+    int nth = (int)std::min<int64_t>(std::max(1u, std::thread::hardware_concurrency()), 16);
+    nth = (int)std::min<int64_t>(nth, (n + 2047) / 2048);
+    if (nth <= 1) {
+        f((int64_t)0, n);
+        return;
+    }
+    std::vector<std::thread> th;
+    for (int i = 0; i < nth; ++i) th.emplace_back([&, i] { f(n * i / nth, n * (i + 1) / nth); });
+    for (auto& x : th) x.join();
+}
+
+static bool share_vertex(const int32_t* a, const int32_t* b) {
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j)
+            if (a[i] == b[j]) return true;
+    return false;
 }
 
 static int upload(void** dst, const void* src, size_t bytes, size_t* total) {
@@ -102,9 +138,10 @@ static void free_mesh_arrays(pb_mesh* m) {
     void* ptrs[] = {m->verts, m->tris,  m->tgeo, m->pts64,    m->pts32,       m->pts32lo,
                     m->v2t_ptr, m->v2t, m->pairs, m->row_ptr, m->col,         m->tpos,
                     m->diag_pos, m->contrib_ptr, m->contrib, m->status, m->pair_rev,
-                    m->pair_coin, m->pair_prim};
+                    m->pair_coin, m->pair_prim, m->pair_band};
     for (void* p : ptrs)
         if (p) cudaFree(p);
+    if (m->pts_ref && m->pts_ref != m->pts64) cudaFree(m->pts_ref);
     ws_free(m->ws_src);
     ws_free(m->ws_part);
     ws_free(m->ws_tri);
@@ -120,15 +157,23 @@ static int load(pb_ctx* ctx, const double* verts_in, int64_t nv, const int32_t* 
         return set_error(PB_EINVAL, "mesh too large for 32-bit indices");
     int Q = plan ? plan->far_q : 6;
     int nss = plan ? plan->n_ss : 4;
+    const double eta = plan ? plan->band_eta : 0.0;
+    const int bq = plan && plan->band_q ? plan->band_q : 6;
     if (Q != 1 && Q != 3 && Q != 6) return set_error(PB_EINVAL, "far_q must be 1, 3 or 6 (got %d)", Q);
     if (nss < 1 || nss > 12) return set_error(PB_EINVAL, "n_ss must be in 1..12 (got %d)", nss);
+    if (!(eta >= 0.0) || !(eta <= 64.0)) return set_error(PB_EINVAL, "band_eta must be in [0, 64] (got %g)", eta);
+    if (eta > 0.0 && ((bq != 3 && bq != 6) || bq <= Q))
+        return set_error(PB_EINVAL, "band_q must be 3 or 6 and finer than far_q (got %d, far_q %d)", bq, Q);
     m->ctx = ctx;
     m->nv = nv;
     m->nt = nt;
     m->Q = Q;
     m->n_ss = nss;
     m->np = nt * Q;
+    m->band_eta = eta;
+    m->Qr = eta > 0.0 ? bq : Q;
     rule_points(Q, m->rule_l, m->rule_w);
+    rule_points(m->Qr, m->ref_l, m->ref_w);
 
     std::vector<double> V(3 * nv);
     std::vector<int32_t> T(3 * nt);
@@ -217,25 +262,38 @@ static int load(pb_ctx* ctx, const double* verts_in, int64_t nv, const int32_t* 
         if (v2t_ptr[i + 1] == v2t_ptr[i])
             return set_error(PB_EMESH, "vertex %lld belongs to no triangle", (long long)i);
 
-    // ---- adjacent triangle pairs (share >= 1 vertex), ordered by (ti, tj)
-    std::vector<int4> pairs;
-    pairs.reserve(16 * nt);
-    {
-        std::vector<int32_t> mark(nt, -1);
-        std::vector<int32_t> nb;
-        for (int64_t t = 0; t < nt; ++t) {
-            nb.clear();
-            for (int a = 0; a < 3; ++a) {
-                int32_t i = T[3 * t + a];
-                for (int32_t k = v2t_ptr[i]; k < v2t_ptr[i + 1]; ++k) {
-                    int32_t s = v2t[k] / 3;
-                    if (mark[s] != (int32_t)t) {
-                        mark[s] = (int32_t)t;
-                        nb.push_back(s);
-                    }
+    // ---- adjacent triangle pairs (share >= 1 vertex), ordered by (ti, tj):
+    // counted, then filled, per triangle
+    std::vector<int32_t> adj_ptr(nt + 1, 0);
+    auto neighbours = [&](int64_t t, std::vector<int32_t>& mark, std::vector<int32_t>& nb) {
+        nb.clear();
+        for (int a = 0; a < 3; ++a) {
+            int32_t i = T[3 * t + a];
+            for (int32_t k = v2t_ptr[i]; k < v2t_ptr[i + 1]; ++k) {
+                int32_t s = v2t[k] / 3;
+                if (mark[s] != (int32_t)t) {
+                    mark[s] = (int32_t)t;
+                    nb.push_back(s);
                 }
             }
-            std::sort(nb.begin(), nb.end());
+        }
+        std::sort(nb.begin(), nb.end());
+    };
+    parallel_for(nt, [&](int64_t b0, int64_t b1) {
+        std::vector<int32_t> mark(nt, -1), nb;
+        for (int64_t t = b0; t < b1; ++t) {
+            neighbours(t, mark, nb);
+            adj_ptr[t + 1] = (int32_t)nb.size();
+        }
+    });
+    for (int64_t t = 0; t < nt; ++t) adj_ptr[t + 1] += adj_ptr[t];
+    const int64_t n_adj = adj_ptr[nt];
+    std::vector<int4> pairs(n_adj);
+    parallel_for(nt, [&](int64_t b0, int64_t b1) {
+        std::vector<int32_t> mark(nt, -1), nb;
+        for (int64_t t = b0; t < b1; ++t) {
+            neighbours(t, mark, nb);
+            int64_t o = adj_ptr[t];
             for (int32_t s : nb) {
                 int sa[3], sb[3], ns = 0;
                 for (int a = 0; a < 3; ++a)
@@ -256,104 +314,240 @@ static int load(pb_ctx* ctx, const double* verts_in, int64_t nv, const int32_t* 
                     const int k0 = T[3 * t + sa[0]] < T[3 * t + sa[1]] ? 0 : 1, k1 = 1 - k0;
                     pt[0] = sa[k0]; pt[1] = sa[k1]; pt[2] = 3 - sa[0] - sa[1];
                     ps[0] = sb[k0]; ps[1] = sb[k1]; ps[2] = 3 - sb[0] - sb[1];
-                } else if (ns == 1) {
-                    kind = 2;  // shared vertex is reordered vertex 0 in both
+                } else {
+                    kind = 2;  // shared vertex is reordered vertex 0 in both (ns == 1 by construction)
                     for (int k = 0; k < 3; ++k) {
                         pt[k] = (sa[0] + k) % 3;
                         ps[k] = (sb[0] + k) % 3;
                     }
-                } else {
-                    return set_error(PB_EMESH, "internal: neighbour without a shared vertex");
                 }
                 int code = pt[0] | pt[1] << 2 | pt[2] << 4 | ps[0] << 6 | ps[1] << 8 | ps[2] << 10;
-                pairs.push_back(make_int4((int)t, s, kind, code));
+                pairs[o++] = make_int4((int)t, s, kind, code);
             }
         }
+    });
+
+    // ---- distance band: pairs sharing no vertex whose centroids are closer than
+    // eta (rho_t + rho_s), rho the largest centroid-vertex distance (same
+    // arithmetic, operation by operation, as the oracle's test), found through
+    // a uniform grid of cell size 2 eta max(rho); listed after the adjacent
+    // pairs, ordered by (ti, tj)
+    std::vector<int32_t> band_ptr(nt + 1, 0);
+    std::vector<int32_t> band_s;
+    if (eta > 0.0) {
+        std::vector<double> C(3 * nt), R(nt);
+        double rmax = 0.0;
+        for (int64_t t = 0; t < nt; ++t) {
+            const double *p0 = &V[3 * T[3 * t]], *p1 = &V[3 * T[3 * t + 1]], *p2 = &V[3 * T[3 * t + 2]];
+            double c[3];
+            for (int k = 0; k < 3; ++k) c[k] = (p0[k] + p1[k] + p2[k]) / 3.0;
+            double r2 = 0.0;
+            const double* pp[3] = {p0, p1, p2};
+            for (int a = 0; a < 3; ++a) {
+                double d[3] = {pp[a][0] - c[0], pp[a][1] - c[1], pp[a][2] - c[2]};
+                double q = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+                if (q > r2) r2 = q;
+            }
+            for (int k = 0; k < 3; ++k) C[3 * t + k] = c[k];
+            R[t] = sqrt(r2);
+            rmax = std::max(rmax, R[t]);
+        }
+        double cell = 2.0 * eta * rmax;
+        int64_t dim[3];
+        for (;;) {
+            int64_t cells = 1;
+            for (int k = 0; k < 3; ++k) {
+                dim[k] = std::max<int64_t>(1, (int64_t)((hi[k] - lo[k]) / cell) + 1);
+                cells *= dim[k];
+            }
+            if (cells <= ((int64_t)1 << 24)) break;
+            cell *= 2.0;
+        }
+        const int64_t ncell = dim[0] * dim[1] * dim[2];
+        auto cell_of = [&](int64_t t, int k) {
+            return std::min<int64_t>(dim[k] - 1, std::max<int64_t>(0, (int64_t)((C[3 * t + k] - lo[k]) / cell)));
+        };
+        std::vector<int32_t> cstart(ncell + 1, 0), ctri(nt), tcell(nt);
+        for (int64_t t = 0; t < nt; ++t) {
+            tcell[t] = (int32_t)(cell_of(t, 0) + dim[0] * (cell_of(t, 1) + dim[1] * cell_of(t, 2)));
+            cstart[tcell[t] + 1]++;
+        }
+        for (int64_t c = 0; c < ncell; ++c) cstart[c + 1] += cstart[c];
+        {
+            std::vector<int32_t> fill(cstart.begin(), cstart.end() - 1);
+            for (int64_t t = 0; t < nt; ++t) ctri[fill[tcell[t]]++] = (int32_t)t;
+        }
+        auto partners = [&](int64_t t, std::vector<int32_t>& out) {
+            out.clear();
+            const int64_t c0 = cell_of(t, 0), c1 = cell_of(t, 1), c2 = cell_of(t, 2);
+            for (int64_t z = std::max<int64_t>(0, c2 - 1); z <= std::min(dim[2] - 1, c2 + 1); ++z)
+                for (int64_t y = std::max<int64_t>(0, c1 - 1); y <= std::min(dim[1] - 1, c1 + 1); ++y)
+                    for (int64_t x = std::max<int64_t>(0, c0 - 1); x <= std::min(dim[0] - 1, c0 + 1); ++x) {
+                        const int64_t c = x + dim[0] * (y + dim[1] * z);
+                        for (int32_t k = cstart[c]; k < cstart[c + 1]; ++k) {
+                            const int32_t s = ctri[k];
+                            if (s == (int32_t)t || share_vertex(&T[3 * t], &T[3 * (int64_t)s])) continue;
+                            double d[3] = {C[3 * t] - C[3 * (int64_t)s], C[3 * t + 1] - C[3 * (int64_t)s + 1],
+                                           C[3 * t + 2] - C[3 * (int64_t)s + 2]};
+                            const double lim = eta * (R[t] + R[s]);
+                            if (d[0] * d[0] + d[1] * d[1] + d[2] * d[2] < lim * lim) out.push_back(s);
+                        }
+                    }
+            std::sort(out.begin(), out.end());
+        };
+        parallel_for(nt, [&](int64_t b0, int64_t b1) {
+            std::vector<int32_t> out;
+            for (int64_t t = b0; t < b1; ++t) {
+                partners(t, out);
+                band_ptr[t + 1] = (int32_t)out.size();
+            }
+        });
+        for (int64_t t = 0; t < nt; ++t) band_ptr[t + 1] += band_ptr[t];
+        if ((int64_t)band_ptr[nt] + n_adj > (((int64_t)1 << 31) - 1) / 9)
+            return set_error(PB_EINVAL, "distance band too wide for this mesh (%lld pairs)",
+                             (long long)band_ptr[nt]);
+        band_s.resize(band_ptr[nt]);
+        parallel_for(nt, [&](int64_t b0, int64_t b1) {
+            std::vector<int32_t> out;
+            for (int64_t t = b0; t < b1; ++t) {
+                partners(t, out);
+                std::copy(out.begin(), out.end(), band_s.begin() + band_ptr[t]);
+            }
+        });
+        const int code = 0 | 1 << 2 | 2 << 4 | 0 << 6 | 1 << 8 | 2 << 10;  // frames in the original order
+        pairs.resize(n_adj + band_s.size());
+        for (int64_t t = 0; t < nt; ++t)
+            for (int32_t k = band_ptr[t]; k < band_ptr[t + 1]; ++k)
+                pairs[n_adj + k] = make_int4((int)t, band_s[k], 3, code);
     }
     m->npairs = (int64_t)pairs.size();
+    m->n_adj = n_adj;
+    const int64_t n_band = m->npairs - n_adj;
 
-    // ---- near pattern: row i holds every vertex of every triangle adjacent to a
-    // triangle at i (the 2-ring); built with a marker array, then sorted.
-    std::vector<int32_t> pair_ptr(nt + 1, 0);
-    for (const int4& p : pairs) pair_ptr[p.x + 1]++;
-    for (int64_t t = 0; t < nt; ++t) pair_ptr[t + 1] += pair_ptr[t];
-    // each ordered pair's reverse, and the pairs the near kernel integrates:
-    // coincident ones, and one of every two reversed ones (t < s)
-    std::vector<int32_t> rev(pairs.size()), coin_list, prim_list;
-    for (size_t p = 0; p < pairs.size(); ++p) {
+    // each pair's reverse (the band criterion is symmetric), and the pairs the
+    // near kernels integrate: coincident ones, and one of every two reversed
+    // adjacent or band pairs (t < s), which also gives the other
+    std::vector<int32_t> rev(pairs.size()), coin_list, prim_list, band_list;
+    auto find_rev = [&](int64_t p, const std::vector<int32_t>& ptr, int64_t base) -> int64_t {
         const int32_t t = pairs[p].x, u = pairs[p].y;
-        int32_t lo = pair_ptr[u], hi = pair_ptr[u + 1];
-        while (lo < hi) {
-            int32_t mid = (lo + hi) / 2;
-            if (pairs[mid].y < t) lo = mid + 1;
-            else hi = mid;
+        int64_t lo2 = base + ptr[u], hi2 = base + ptr[u + 1];
+        const int64_t end = hi2;
+        while (lo2 < hi2) {
+            int64_t mid = (lo2 + hi2) / 2;
+            if (pairs[mid].y < t) lo2 = mid + 1;
+            else hi2 = mid;
         }
-        if (lo >= pair_ptr[u + 1] || pairs[lo].y != t) return set_error(PB_EMESH, "internal: pair without reverse");
-        rev[p] = lo;
+        return (lo2 < end && pairs[lo2].y == t) ? lo2 : -1;
+    };
+    bool rev_ok = true;
+    parallel_for(m->npairs, [&](int64_t b0, int64_t b1) {
+        for (int64_t p = b0; p < b1; ++p) {
+            int64_t r = p < n_adj ? find_rev(p, adj_ptr, 0) : find_rev(p, band_ptr, n_adj);
+            if (r < 0) rev_ok = false;
+            rev[p] = (int32_t)r;
+        }
+    });
+    if (!rev_ok) return set_error(PB_EMESH, "internal: pair without reverse");
+    for (int64_t p = 0; p < m->npairs; ++p) {
+        const int32_t t = pairs[p].x, u = pairs[p].y;
         if (t == u) coin_list.push_back((int32_t)p);
-        else if (t < u) prim_list.push_back((int32_t)p);
+        else if (t < u) (p < n_adj ? prim_list : band_list).push_back((int32_t)p);
     }
-    std::vector<int32_t> row_ptr(nv + 1, 0), col, mark(nv, -1), colpos(nv, 0);
-    col.reserve((size_t)24 * nv);
-    for (int64_t i = 0; i < nv; ++i) {
-        size_t start = col.size();
-        for (int32_t k = v2t_ptr[i]; k < v2t_ptr[i + 1]; ++k) {
-            int32_t t = v2t[k] / 3;
-            for (int32_t p = pair_ptr[t]; p < pair_ptr[t + 1]; ++p) {
-                const int32_t* f = &T[3 * (int64_t)pairs[p].y];
-                for (int b = 0; b < 3; ++b)
-                    if (mark[f[b]] != (int32_t)i) {
-                        mark[f[b]] = (int32_t)i;
-                        col.push_back(f[b]);
-                    }
-            }
-        }
-        std::sort(col.begin() + start, col.end());
-        if (col.size() > (size_t)(((int64_t)1 << 31) - 1)) return set_error(PB_EINVAL, "near pattern too large");
-        row_ptr[i + 1] = (int32_t)col.size();
-    }
-    const int64_t nnz = (int64_t)col.size();
-    m->nnz = nnz;
-    std::vector<int32_t> tpos(nnz), diag_pos(nv, -1);
-    for (int64_t i = 0; i < nv; ++i)
-        for (int32_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
-            const int32_t j = col[k];
-            const int32_t* bg = col.data() + row_ptr[j];
-            const int32_t* en = col.data() + row_ptr[j + 1];
-            const int32_t* q = std::lower_bound(bg, en, (int32_t)i);
-            if (q == en || *q != (int32_t)i) return set_error(PB_EMESH, "internal: near pattern is not symmetric");
-            tpos[k] = (int32_t)(q - col.data());
-            if (j == i) diag_pos[i] = k;
-        }
 
-    // ---- contributions (pair * 9 + a * 3 + b) of every adjacent pair to each
-    // nonzero, listed row by row in a fixed order (corners of the row vertex,
-    // then its triangle's pairs, then the trial corner): a counting pass and a
-    // filling pass over the same loops.
+    // ---- near pattern: row i holds every vertex of every triangle paired with a
+    // triangle at i (the 2-ring, and the band); counted, then filled and sorted
+    auto row_vertices = [&](int64_t i, std::vector<int32_t>& mark, std::vector<int32_t>& out) {
+        out.clear();
+        for (int32_t k = v2t_ptr[i]; k < v2t_ptr[i + 1]; ++k) {
+            const int32_t t = v2t[k] / 3;
+            const int64_t ranges[2][2] = {{adj_ptr[t], adj_ptr[t + 1]},
+                                          {n_adj + band_ptr[t], n_adj + band_ptr[t + 1]}};
+            for (int r = 0; r < (eta > 0.0 ? 2 : 1); ++r)
+                for (int64_t p = ranges[r][0]; p < ranges[r][1]; ++p) {
+                    const int32_t* f = &T[3 * (int64_t)pairs[p].y];
+                    for (int b = 0; b < 3; ++b)
+                        if (mark[f[b]] != (int32_t)i) {
+                            mark[f[b]] = (int32_t)i;
+                            out.push_back(f[b]);
+                        }
+                }
+        }
+        std::sort(out.begin(), out.end());
+    };
+    std::vector<int64_t> row_cnt(nv + 1, 0);
+    parallel_for(nv, [&](int64_t b0, int64_t b1) {
+        std::vector<int32_t> mark(nv, -1), out;
+        for (int64_t i = b0; i < b1; ++i) {
+            row_vertices(i, mark, out);
+            row_cnt[i + 1] = (int64_t)out.size();
+        }
+    });
+    for (int64_t i = 0; i < nv; ++i) row_cnt[i + 1] += row_cnt[i];
+    if (row_cnt[nv] > ((int64_t)1 << 31) - 1) return set_error(PB_EINVAL, "near pattern too large");
+    const int64_t nnz = row_cnt[nv];
+    m->nnz = nnz;
+    std::vector<int32_t> row_ptr(nv + 1), col(nnz);
+    for (int64_t i = 0; i <= nv; ++i) row_ptr[i] = (int32_t)row_cnt[i];
+    parallel_for(nv, [&](int64_t b0, int64_t b1) {
+        std::vector<int32_t> mark(nv, -1), out;
+        for (int64_t i = b0; i < b1; ++i) {
+            row_vertices(i, mark, out);
+            std::copy(out.begin(), out.end(), col.begin() + row_ptr[i]);
+        }
+    });
+    std::vector<int32_t> tpos(nnz), diag_pos(nv, -1);
+    bool sym_ok = true;
+    parallel_for(nv, [&](int64_t b0, int64_t b1) {
+        for (int64_t i = b0; i < b1; ++i)
+            for (int32_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+                const int32_t j = col[k];
+                const int32_t* bg = col.data() + row_ptr[j];
+                const int32_t* en = col.data() + row_ptr[j + 1];
+                const int32_t* q = std::lower_bound(bg, en, (int32_t)i);
+                if (q == en || *q != (int32_t)i) {
+                    sym_ok = false;
+                    continue;
+                }
+                tpos[k] = (int32_t)(q - col.data());
+                if (j == i) diag_pos[i] = k;
+            }
+    });
+    if (!sym_ok) return set_error(PB_EMESH, "internal: near pattern is not symmetric");
+
+    // ---- contributions (pair * 9 + a * 3 + b) of every listed pair to each
+    // nonzero, row by row in a fixed order (corners of the row vertex, then its
+    // triangle's adjacent pairs and band pairs, then the trial corner): a
+    // counting pass and a filling pass over the same loops
     std::vector<int32_t> cnt(nnz + 1, 0);
     std::vector<int32_t> cidx((size_t)9 * pairs.size());
     for (int pass = 0; pass < 2; ++pass) {
-        std::vector<int32_t> fill;
-        if (pass == 1) {
+        if (pass == 1)
             for (int64_t k = 0; k < nnz; ++k) cnt[k + 1] += cnt[k];
-            fill.assign(cnt.begin(), cnt.end() - 1);
-        }
-        for (int64_t i = 0; i < nv; ++i) {
-            for (int32_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) colpos[col[k]] = k;
-            for (int32_t k = v2t_ptr[i]; k < v2t_ptr[i + 1]; ++k) {
-                const int32_t t = v2t[k] / 3, a = v2t[k] % 3;
-                for (int32_t p = pair_ptr[t]; p < pair_ptr[t + 1]; ++p) {
-                    const int32_t* f = &T[3 * (int64_t)pairs[p].y];
-                    for (int b = 0; b < 3; ++b) {
-                        const int32_t kk = colpos[f[b]];
-                        if (pass == 0) cnt[kk + 1]++;
-                        else cidx[fill[kk]++] = 9 * p + 3 * a + b;
-                    }
+        parallel_for(nv, [&](int64_t b0, int64_t b1) {
+            std::vector<int32_t> colpos(nv, 0);
+            std::vector<int32_t> fill;
+            for (int64_t i = b0; i < b1; ++i) {
+                for (int32_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) colpos[col[k]] = k;
+                if (pass == 1) fill.assign(cnt.begin() + row_ptr[i], cnt.begin() + row_ptr[i + 1]);
+                for (int32_t k = v2t_ptr[i]; k < v2t_ptr[i + 1]; ++k) {
+                    const int32_t t = v2t[k] / 3, a = v2t[k] % 3;
+                    const int64_t ranges[2][2] = {{adj_ptr[t], adj_ptr[t + 1]},
+                                                  {n_adj + band_ptr[t], n_adj + band_ptr[t + 1]}};
+                    for (int r = 0; r < (eta > 0.0 ? 2 : 1); ++r)
+                        for (int64_t p = ranges[r][0]; p < ranges[r][1]; ++p) {
+                            const int32_t* f = &T[3 * (int64_t)pairs[p].y];
+                            for (int b = 0; b < 3; ++b) {
+                                const int32_t kk = colpos[f[b]];
+                                if (pass == 0) cnt[kk + 1]++;
+                                else cidx[fill[kk - row_ptr[i]]++] = (int32_t)(9 * p + 3 * a + b);
+                            }
+                        }
                 }
             }
-        }
+        });
     }
     m->ncontrib = (int64_t)cidx.size();
+    (void)n_band;
 
     // ---- upload
     size_t tot = 0;
@@ -365,8 +559,10 @@ static int load(pb_ctx* ctx, const double* verts_in, int64_t nv, const int32_t* 
     PB_TRY(upload((void**)&m->pair_rev, rev.data(), sizeof(int32_t) * rev.size(), &tot));
     PB_TRY(upload((void**)&m->pair_coin, coin_list.data(), sizeof(int32_t) * coin_list.size(), &tot));
     PB_TRY(upload((void**)&m->pair_prim, prim_list.data(), sizeof(int32_t) * prim_list.size(), &tot));
+    PB_TRY(upload((void**)&m->pair_band, band_list.data(), sizeof(int32_t) * band_list.size(), &tot));
     m->n_coin = (int64_t)coin_list.size();
     m->n_prim = (int64_t)prim_list.size();
+    m->n_band = (int64_t)band_list.size();
     PB_TRY(upload((void**)&m->row_ptr, row_ptr.data(), sizeof(int32_t) * (nv + 1), &tot));
     PB_TRY(upload((void**)&m->col, col.data(), sizeof(int32_t) * nnz, &tot));
     PB_TRY(upload((void**)&m->tpos, tpos.data(), sizeof(int32_t) * nnz, &tot));
@@ -380,13 +576,21 @@ static int load(pb_ctx* ctx, const double* verts_in, int64_t nv, const int32_t* 
     PB_TRY(dev_alloc((void**)&m->pts32, sizeof(float) * 4 * m->np));
     PB_TRY(dev_alloc((void**)&m->pts32lo, sizeof(float) * 4 * m->np));
     tot += sizeof(double) * 16 * nt + (sizeof(double) + 2 * sizeof(float)) * 4 * m->np;
+    m->np_ref = nt * m->Qr;
+    if (m->Qr != m->Q) {
+        PB_TRY(dev_alloc((void**)&m->pts_ref, sizeof(double) * 4 * m->np_ref));
+        tot += sizeof(double) * 4 * m->np_ref;
+    } else {
+        m->pts_ref = m->pts64;
+    }
     m->device_bytes = tot;
 
     double cx = 0.5 * (lo[0] + hi[0]), cy = 0.5 * (lo[1] + hi[1]), cz = 0.5 * (lo[2] + hi[2]);
     int threads = 128;
     int blocks = (int)((nt + threads - 1) / threads);
-    k_geometry<<<blocks, threads>>>(m->verts, m->tris, nt, mesh_rule(m), cx, cy, cz, m->tgeo, m->pts64, m->pts32,
-                                    m->pts32lo); ::pb::count_launch();
+    k_geometry<<<blocks, threads>>>(m->verts, m->tris, nt, mesh_rule(m), mesh_ref_rule(m), cx, cy, cz, m->tgeo,
+                                    m->pts64, m->pts32, m->pts32lo, m->pts_ref != m->pts64 ? m->pts_ref : nullptr);
+    ::pb::count_launch();
     PB_CUDA(cudaGetLastError());
     PB_CUDA(cudaDeviceSynchronize());
     return PB_OK;

@@ -285,10 +285,63 @@ k_near_pairs(const double* __restrict__ verts, const int32_t* __restrict__ tris,
     if (SYM && lane == 1) expand_blocks(acc, A, B, gA, gB, kappa, true, far_out + 54 * (int64_t)rev[p]);
 }
 
+// Band pairs (share no vertex, closer than the plan's band): the blocks of the
+// band rule minus those of the far rule, for the pair and its reverse, one
+// thread per pair of reversed pairs. Points are the rules' barycentric
+// combinations of the corners, in the corners' original order.
+constexpr int BAND_THREADS = 128;
+
+__global__ void __launch_bounds__(BAND_THREADS, 2)
+k_band_pairs(const double* __restrict__ verts, const int32_t* __restrict__ tris, const double* __restrict__ tgeo,
+             const int4* __restrict__ pairs, const int32_t* __restrict__ list, int64_t nlist,
+             const int32_t* __restrict__ rev, Rule fine, Rule coarse, double kappa, double* __restrict__ ss_out) {
+    const int64_t li = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (li >= nlist) return;
+    const int64_t p = list[li];
+    const int4 pr = pairs[p];
+    double pa[3][3], pb[3][3];
+    for (int a = 0; a < 3; ++a)
+        for (int k = 0; k < 3; ++k) {
+            pa[a][k] = verts[3 * (int64_t)tris[3 * (int64_t)pr.x + a] + k];
+            pb[a][k] = verts[3 * (int64_t)tris[3 * (int64_t)pr.y + a] + k];
+        }
+    const double* gA = tgeo + 16 * (int64_t)pr.x;
+    const double* gB = tgeo + 16 * (int64_t)pr.y;
+    const double na[3] = {gA[0], gA[1], gA[2]}, nb[3] = {gB[0], gB[1], gB[2]};
+    double acc[NACC_SYM];
+    for (int k = 0; k < NACC_SYM; ++k) acc[k] = 0.0;
+    for (int pass = 0; pass < 2; ++pass) {
+        const Rule& R = pass == 0 ? fine : coarse;
+        const double sign = pass == 0 ? 1.0 : -1.0;
+        for (int i = 0; i < R.Q; ++i) {
+            double x[3];
+            for (int k = 0; k < 3; ++k) x[k] = R.l[i][0] * pa[0][k] + R.l[i][1] * pa[1][k] + R.l[i][2] * pa[2][k];
+            for (int j = 0; j < R.Q; ++j) {
+                double y[3];
+                for (int k = 0; k < 3; ++k)
+                    y[k] = R.l[j][0] * pb[0][k] + R.l[j][1] * pb[1][k] + R.l[j][2] * pb[2][k];
+                const double w = sign * (R.w[i] * gA[3]) * (R.w[j] * gB[3]);
+                accum_point<true>(acc, w, x, y, na, nb, R.l[i], R.l[j], kappa);
+            }
+        }
+    }
+    TriFrame A, B;  // expand_blocks reads the normals and areas only
+    for (int k = 0; k < 3; ++k) {
+        A.n[k] = na[k];
+        B.n[k] = nb[k];
+    }
+    A.area = gA[3];
+    B.area = gB[3];
+    expand_blocks(acc, A, B, gA, gB, kappa, false, ss_out + 54 * p);
+    expand_blocks(acc, A, B, gA, gB, kappa, true, ss_out + 54 * (int64_t)rev[p]);
+}
+
 // One thread per nonzero: sum the contributions in their fixed (pair) order.
+// Adjacent pairs (p < n_adj) hold the regularised blocks in ss and the far
+// rule's in far; band pairs hold the difference already in ss.
 __global__ void k_near_entries(int64_t nnz, int64_t nv, const int32_t* __restrict__ row_of,
                                const int32_t* __restrict__ col, const int32_t* __restrict__ cptr,
-                               const int32_t* __restrict__ contrib, const int4* __restrict__ pairs,
+                               const int32_t* __restrict__ contrib, const int4* __restrict__ pairs, int64_t n_adj,
                                const double* __restrict__ tgeo, const double* __restrict__ ss,
                                const double* __restrict__ far, double* __restrict__ val,
                                double* __restrict__ diag) {
@@ -299,13 +352,17 @@ __global__ void k_near_entries(int64_t nnz, int64_t nv, const int32_t* __restric
         int32_t code = contrib[c];
         int64_t p = code / 9;
         int ab = code - 9 * (int)p;
-        for (int o = 0; o < 6; ++o) {
-            double s = ss[54 * p + 9 * o + ab];
-            nearv[o] += s - far[54 * p + 9 * o + ab];
-            full[o] += s;
+        if (p < n_adj) {
+            for (int o = 0; o < 6; ++o) {
+                double s = ss[54 * p + 9 * o + ab];
+                nearv[o] += s - far[54 * p + 9 * o + ab];
+                full[o] += s;
+            }
+            int4 pr = pairs[p];
+            if (pr.z == 0) mass += tgeo[16 * (int64_t)pr.x + 3] / 12.0 * ((ab % 4 == 0) ? 2.0 : 1.0);
+        } else {
+            for (int o = 0; o < 6; ++o) nearv[o] += ss[54 * p + 9 * o + ab];  // never on the diagonal
         }
-        int4 pr = pairs[p];
-        if (pr.z == 0) mass += tgeo[16 * (int64_t)pr.x + 3] / 12.0 * ((ab % 4 == 0) ? 2.0 : 1.0);
     }
     const int map[6] = {N_VL, N_KL, N_DL, N_VY, N_KY, N_DY};
     for (int o = 0; o < 6; ++o) val[map[o] * nnz + e] = nearv[o];
@@ -337,7 +394,7 @@ static int build(pb_ctx* ctx, const pb_mesh* m, double kappa, pb_near* nf, cudaS
     double *ss = nullptr, *far = nullptr;
     int32_t* row_of = nullptr;
     int rc = dev_alloc((void**)&ss, sizeof(double) * 54 * m->npairs);
-    if (rc == PB_OK) rc = dev_alloc((void**)&far, sizeof(double) * 54 * m->npairs);
+    if (rc == PB_OK) rc = dev_alloc((void**)&far, sizeof(double) * 54 * m->n_adj);
     if (rc == PB_OK) rc = dev_alloc((void**)&row_of, sizeof(int32_t) * m->nnz);
     if (rc == PB_OK) {
         Gauss gq = gauss01(m->n_ss);
@@ -353,10 +410,16 @@ static int build(pb_ctx* ctx, const pb_mesh* m, double kappa, pb_near* nf, cudaS
             k_near_pairs<2, true><<<bp, threads, 0, s>>>(m->verts, m->tris, m->tgeo, m->pairs, m->pair_prim,
                                                          m->n_prim, m->pair_rev, gq, mesh_rule(m), kappa, ss, far);
         ::pb::count_launch();
+        if (m->n_band) {
+            Rule fine = mesh_ref_rule(m), coarse = mesh_rule(m);
+            k_band_pairs<<<(unsigned)((m->n_band + BAND_THREADS - 1) / BAND_THREADS), BAND_THREADS, 0, s>>>(
+                m->verts, m->tris, m->tgeo, m->pairs, m->pair_band, m->n_band, m->pair_rev, fine, coarse, kappa, ss);
+            ::pb::count_launch();
+        }
         k_row_of<<<(unsigned)((m->nv + 255) / 256), 256, 0, s>>>(m->nv, m->row_ptr, row_of); ::pb::count_launch();
         cudaMemsetAsync(nf->diag, 0, sizeof(double) * N_VALS * m->nv, s);
         k_near_entries<<<(unsigned)((m->nnz + 255) / 256), 256, 0, s>>>(
-            m->nnz, m->nv, row_of, m->col, m->contrib_ptr, m->contrib, m->pairs, m->tgeo, ss, far, nf->val,
+            m->nnz, m->nv, row_of, m->col, m->contrib_ptr, m->contrib, m->pairs, m->n_adj, m->tgeo, ss, far, nf->val,
             nf->diag); ::pb::count_launch();
         cudaError_t e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);

@@ -148,8 +148,9 @@ extern "C" int pb_rhs_charges(pb_ctx* ctx, const pb_mesh* m, const double* xq, c
     cudaStream_t s = (cudaStream_t)stream;
     PB_TRY(ws_reserve(const_cast<pb_mesh*>(m)->ws_tri, sizeof(double) * 6 * m->nt));
     double* tri = (double*)m->ws_tri.ptr;
-    k_rhs_points<<<(unsigned)((m->nt + 127) / 128), 128, 0, s>>>(m->nt, mesh_rule(m), m->pts64, m->tgeo, xq, q, n_q,
-                                                                prm->eps_int, tri); ::pb::count_launch();
+    // the plan's reference rule (the band rule when the plan has a band)
+    k_rhs_points<<<(unsigned)((m->nt + 127) / 128), 128, 0, s>>>(m->nt, mesh_ref_rule(m), m->pts_ref, m->tgeo, xq, q,
+                                                                n_q, prm->eps_int, tri); ::pb::count_launch();
     k_rhs_gather<<<(unsigned)((m->nv + 255) / 256), 256, 0, s>>>(m->nv, m->v2t_ptr, m->v2t, tri, d[0], d[1], n[0],
                                                                 n[1], rhs); ::pb::count_launch();
     PB_CUDA(cudaGetLastError());
@@ -165,13 +166,13 @@ extern "C" int pb_energy(pb_ctx* ctx, const pb_mesh* m, const double* x, int for
     cudaStream_t s = (cudaStream_t)stream;
     // exterior unknowns -> interior traces: u_int = u_ext, v_int = (eps_ext/eps_int) v_ext
     double vscale = form_is_exterior(form) ? prm->eps_ext / prm->eps_int : 1.0;
-    int nchunk = (int)((m->np + EN_CHUNK - 1) / EN_CHUNK);
+    int nchunk = (int)((m->np_ref + EN_CHUNK - 1) / EN_CHUNK);
     double* part = nullptr;
     PB_TRY(dev_alloc((void**)&part, sizeof(double) * (n_q * nchunk + 1)));
     double* dG = part + n_q * nchunk;
     dim3 grid(nchunk, (unsigned)n_q);
-    k_energy_part<<<grid, EN_THREADS, 0, s>>>(m->nt, mesh_rule(m), m->tris, m->tgeo, m->pts64, x, m->nv, vscale, xq, part,
-                                            nchunk); ::pb::count_launch();
+    k_energy_part<<<grid, EN_THREADS, 0, s>>>(m->nt, mesh_ref_rule(m), m->tris, m->tgeo, m->pts_ref, x, m->nv, vscale,
+                                            xq, part, nchunk); ::pb::count_launch();
     k_energy_final<<<1, 1, 0, s>>>(n_q, nchunk, part, q, phi, dG); ::pb::count_launch();
     double h = 0.0;
     cudaError_t e = cudaMemcpyAsync(&h, dG, sizeof(double), cudaMemcpyDeviceToHost, s);
@@ -215,25 +216,28 @@ extern "C" int pb_solvation_energy(pb_ctx* ctx, const double* verts, int64_t n_v
     return rc;
 }
 
-// a12, quadrature part: the cheapest of the relaxed plans {far_q 3, 1} (with
-// the singular rule kept) whose Delta G differs from the reference plan's by
-// at most tol_dG relative; the reference plan itself when none qualifies.
+// a12, quadrature part: the cheapest plan whose Delta G differs from the
+// reference plan's by at most tol_dG relative. Candidates, cheapest first: the
+// 3-point far rule with the reference's rule inside a distance band of
+// 2, 3, 4 and 6 radii (the far-field work is a quarter of the 6-point rule's;
+// the band's near-field work grows with its width). The reference plan itself
+// when none qualifies.
 extern "C" int pb_autotune_plan(pb_ctx* ctx, const double* verts, int64_t n_verts, const int32_t* tris,
                                 int64_t n_tris, const double* xq, const double* q, int64_t n_q, const pb_params* prm,
                                 const pb_quad_plan* reference, int form, int precond, const pb_solve_opts* opts,
                                 double tol_dG, pb_quad_plan* out_plan, double* out_change, void* stream) {
     if (!ctx || !verts || !tris || !xq || !q || !prm || !out_plan || !(tol_dG >= 0.0))
         return set_error(PB_EINVAL, "pb_autotune_plan: bad argument");
-    pb_quad_plan ref = reference ? *reference : pb_quad_plan{6, 4};
+    pb_quad_plan ref = reference ? *reference : pb_quad_plan{6, 4, 0.0, 6};
     double dref = 0.0;
     PB_TRY(pb_solvation_energy(ctx, verts, n_verts, tris, n_tris, xq, q, n_q, prm, &ref, form, precond, opts, &dref,
                                nullptr, stream));
     *out_plan = ref;
     if (out_change) *out_change = 0.0;
-    const int cands[2] = {3, 1};
-    for (int qn : cands) {
-        if (qn >= ref.far_q) continue;
-        pb_quad_plan p = {qn, ref.n_ss};
+    if (ref.far_q <= 3 || ref.band_eta > 0.0) return PB_OK;  // nothing cheaper to offer
+    const double etas[4] = {2.0, 3.0, 4.0, 6.0};
+    for (double eta : etas) {
+        pb_quad_plan p = {3, ref.n_ss, eta, ref.far_q};
         double d = 0.0;
         PB_TRY(pb_solvation_energy(ctx, verts, n_verts, tris, n_tris, xq, q, n_q, prm, &p, form, precond, opts, &d,
                                    nullptr, stream));
@@ -241,8 +245,7 @@ extern "C" int pb_autotune_plan(pb_ctx* ctx, const double* verts, int64_t n_vert
         if (change <= tol_dG) {
             *out_plan = p;
             if (out_change) *out_change = change;
-        } else {
-            break;  // a coarser rule will not do better
+            break;
         }
     }
     return PB_OK;

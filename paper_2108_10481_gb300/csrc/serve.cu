@@ -103,13 +103,18 @@ static int free_req(ServeReq* r) {
 }
 
 // Device bytes a request holds while resident (upper estimates of the
-// adjacency sizes: 16 adjacent pairs per triangle, 25 near nonzeros per vertex).
-static size_t footprint(pb_ctx* ctx, int64_t nv, int64_t nt, int Q, int mmax, int64_t nq) {
-    const double np = (double)Q * nt, npairs = 16.0 * nt, nnz = 25.0 * nv;
-    double mesh = 24 * nv + 12 * nt + 128 * nt + 64 * np + 8 * (nv + 1) + 12 * nt + 16 * npairs + 12 * nnz +
-                  4 * nv + 4 * (nnz + 1) + 36 * npairs;
+// adjacency sizes: 16 adjacent pairs per triangle, 25 near nonzeros per vertex;
+// a distance band of eta radii adds about 12 eta^2 pairs per triangle and
+// 7 eta^2 nonzeros per vertex).
+static size_t footprint(pb_ctx* ctx, int64_t nv, int64_t nt, const pb_quad_plan& plan, int mmax, int64_t nq) {
+    const int Q = plan.far_q;
+    const double eta = plan.band_eta, band = 12.0 * eta * eta * nt;
+    const double np = (double)Q * nt, nadj = 16.0 * nt, npairs = nadj + band, nnz = (25.0 + 7.0 * eta * eta) * nv;
+    const double npref = eta > 0.0 ? 6.0 * nt : 0.0;
+    double mesh = 24 * nv + 12 * nt + 128 * nt + 64 * np + 32 * npref + 8 * (nv + 1) + 12 * nt + 16 * npairs +
+                  12 * nnz + 4 * nv + 4 * (nnz + 1) + 36 * npairs;
     double nearb = 56 * nnz + 56 * nv;
-    double near_tmp = 864 * npairs + 4 * nnz;
+    double near_tmp = 432 * (npairs + nadj) + 4 * nnz;
     double src = 128 * (np + 64);
     int S = far_splits_estimate(ctx, (int64_t)np);
     double part = (double)S * 10 * np * 8;
@@ -440,13 +445,13 @@ extern "C" int pb_submit(pb_server* srv, const pb_request* req) {
     r->pc = req->precond;
     r->opts = req->opts;
     r->plan = req->plan;
-    if (r->plan.far_q == 0) r->plan = {6, 4};
+    if (r->plan.far_q == 0) r->plan = {6, 4, 0.0, 6};
     if (!(r->opts.tol > 0.0) || r->opts.max_it < 1) {
         delete r;
         return set_error(PB_EINVAL, "pb_submit: need tol > 0 and max_it >= 1");
     }
     r->mmax = r->opts.restart > 0 ? std::min(r->opts.restart, r->opts.max_it) : r->opts.max_it;
-    r->footprint = footprint(srv->ctx, req->n_verts, req->n_tris, r->plan.far_q, r->mmax, req->n_q);
+    r->footprint = footprint(srv->ctx, req->n_verts, req->n_tris, r->plan, r->mmax, req->n_q);
     if (r->footprint > srv->budget) {
         size_t fp = r->footprint;
         delete r;

@@ -19,7 +19,7 @@ class pb_params(ctypes.Structure):
 
 
 class pb_quad_plan(ctypes.Structure):
-    _fields_ = [("far_q", c_int), ("n_ss", c_int)]
+    _fields_ = [("far_q", c_int), ("n_ss", c_int), ("band_eta", c_double), ("band_q", c_int)]
 
 
 class pb_solve_opts(ctypes.Structure):

@@ -41,7 +41,7 @@ def test_plan_tuning_follows_the_rule(pb):
     P = pb.Params(4.0, 80.0, 0.125)
     opts = pb.solve_opts(tol=1e-10, max_it=300)
     strict, ch = pb.pb_autotune_plan(ctx, v, t, xq, q, P, "direct_int", "block_diag", tol_dG=1e-9, opts=opts)
-    assert strict == (6, 4) and ch == 0.0
+    assert strict == (6, 4, 0.0, 6) and ch == 0.0
     loose, ch2 = pb.pb_autotune_plan(ctx, v, t, xq, q, P, "direct_int", "block_diag", tol_dG=5e-2, opts=opts)
     print("plans", strict, loose, ch2)
-    assert loose[0] in (1, 3) and ch2 <= 5e-2
+    assert loose[0] == 3 and loose[2] > 0.0 and loose[3] == 6 and 0.0 < ch2 <= 5e-2
