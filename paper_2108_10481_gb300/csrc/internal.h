@@ -152,23 +152,27 @@ struct pb_mesh {
     float* pts32lo = nullptr;   // np x 4: x - float(x), ..., 0
     int32_t* v2t_ptr = nullptr; // nv + 1
     int32_t* v2t = nullptr;     // 3 nt entries: tri * 3 + local vertex
-    // listed triangle pairs: the adjacent ones [0, n_adj), then the band pairs
-    int64_t npairs = 0, n_adj = 0;
-    int4* pairs = nullptr;      // (ti, tj, kind, perms): kind 0 coincident, 1 edge, 2 vertex, 3 band
+    // adjacent triangle pairs (share a vertex), ordered by (ti, tj)
+    int64_t npairs = 0, n_adj = 0;  // npairs = n_adj + n_band
+    int4* pairs = nullptr;      // n_adj: (ti, tj, kind, perms): kind 0 coincident, 1 edge, 2 vertex
+    int32_t* adj_ptr = nullptr;    // nt + 1: pairs of triangle t
     int32_t* pair_rev = nullptr;   // index of the reversed pair (tj, ti)
     int32_t* pair_coin = nullptr;  // coincident pairs
     int32_t* pair_prim = nullptr;  // adjacent pairs with ti < tj (each also gives its reverse)
-    int32_t* pair_band = nullptr;  // band pairs with ti < tj (each also gives its reverse)
-    int64_t n_coin = 0, n_prim = 0, n_band = 0;
+    int64_t n_coin = 0, n_prim = 0;
+    // band pairs (no shared vertex, within the plan's band), ordered by (ti, tj):
+    // band pair q is (band_t[q], band_s[q]); triangle t's are band_ptr[t]..band_ptr[t+1]
+    int64_t n_band = 0;
+    int32_t* band_ptr = nullptr;
+    int32_t* band_s = nullptr;
+    int32_t* band_t = nullptr;
     // vertex-pair pattern of the near field (symmetric)
     int64_t nnz = 0;
     int32_t* row_ptr = nullptr; // nv + 1
     int32_t* col = nullptr;     // nnz
     int32_t* tpos = nullptr;    // nnz: index of the transposed entry
+    int32_t* row_of = nullptr;  // nnz: row of each entry
     int32_t* diag_pos = nullptr;// nv
-    int32_t* contrib_ptr = nullptr; // nnz + 1
-    int32_t* contrib = nullptr;     // pair * 9 + a * 3 + b
-    int64_t ncontrib = 0;
     int* status = nullptr;          // device status word of bounded waits (0 = fine)
     // workspaces (grown on demand)
     pb::Workspace ws_src, ws_part, ws_tri, ws_vec, ws_comb;

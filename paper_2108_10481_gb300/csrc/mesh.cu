@@ -10,9 +10,9 @@
 // their radii are listed too: the near field adds to them the difference of
 // the finer band rule and the far rule.
 //
-// The host work (pairs, band search, near pattern, contribution lists) runs
-// on several threads; every list is built per triangle or per vertex row, so
-// its order does not depend on the thread count.
+// The host work (adjacent pairs, near pattern) runs on several threads; every
+// list is built per triangle or per vertex row, so its order does not depend
+// on the thread count. The band search runs on the device.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
@@ -106,6 +106,129 @@ __global__ void k_geometry(const double* __restrict__ verts, const int32_t* __re
         }
 }
 
+// ---- distance band on the device. The test uses the same IEEE operations,
+// in the same order and without contraction, as the host code that computed
+// the centroids and radii (and as the oracle), so every decision is the same.
+__device__ __forceinline__ bool band_hit(const double* __restrict__ C, const double* __restrict__ R, int64_t t,
+                                         int64_t s, double eta) {
+    const double d0 = __dsub_rn(C[3 * t], C[3 * s]), d1 = __dsub_rn(C[3 * t + 1], C[3 * s + 1]),
+                 d2 = __dsub_rn(C[3 * t + 2], C[3 * s + 2]);
+    const double q = __dadd_rn(__dadd_rn(__dmul_rn(d0, d0), __dmul_rn(d1, d1)), __dmul_rn(d2, d2));
+    const double lim = __dmul_rn(eta, __dadd_rn(R[t], R[s]));
+    return q < __dmul_rn(lim, lim);
+}
+
+__device__ __forceinline__ bool share_vertex_dev(const int32_t* a, const int32_t* b) {
+    bool r = false;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) r |= a[i] == b[j];
+    return r;
+}
+
+struct BandGrid {
+    const double* C;      // nt x 3 centroids
+    const double* R;      // nt radii
+    const int32_t* cstart;  // ncell + 1
+    const int32_t* ctri;    // triangles by cell
+    const int32_t* tcell;   // cell of each triangle
+    int64_t dim[3];
+    double eta;
+};
+
+// pass 0: count the band partners of each triangle; pass 1: write them
+// (sorted) with their owner
+__global__ void k_band_search(int64_t nt, const int32_t* __restrict__ tris, BandGrid g, int pass,
+                              int32_t* __restrict__ cnt, const int32_t* __restrict__ ptr, int32_t* __restrict__ bs,
+                              int32_t* __restrict__ bt) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= nt) return;
+    const int64_t c = g.tcell[t];
+    const int64_t c0 = c % g.dim[0], c1 = (c / g.dim[0]) % g.dim[1], c2 = c / (g.dim[0] * g.dim[1]);
+    const int32_t* ft = tris + 3 * t;
+    int n = 0;
+    const int64_t base = pass ? ptr[t] : 0;
+    for (int64_t z = max((int64_t)0, c2 - 1); z <= min(g.dim[2] - 1, c2 + 1); ++z)
+        for (int64_t y = max((int64_t)0, c1 - 1); y <= min(g.dim[1] - 1, c1 + 1); ++y)
+            for (int64_t x = max((int64_t)0, c0 - 1); x <= min(g.dim[0] - 1, c0 + 1); ++x) {
+                const int64_t cc = x + g.dim[0] * (y + g.dim[1] * z);
+                for (int32_t k = g.cstart[cc]; k < g.cstart[cc + 1]; ++k) {
+                    const int32_t s = g.ctri[k];
+                    if (s == (int32_t)t || !band_hit(g.C, g.R, t, s, g.eta) ||
+                        share_vertex_dev(ft, tris + 3 * (int64_t)s))
+                        continue;
+                    if (pass) bs[base + n] = s;
+                    ++n;
+                }
+            }
+    if (!pass) {
+        cnt[t] = n;
+        return;
+    }
+    // insertion sort of this triangle's partners; owners alongside
+    for (int i = 1; i < n; ++i) {
+        const int32_t v = bs[base + i];
+        int j = i - 1;
+        while (j >= 0 && bs[base + j] > v) {
+            bs[base + j + 1] = bs[base + j];
+            --j;
+        }
+        bs[base + j + 1] = v;
+    }
+    for (int i = 0; i < n; ++i) bt[base + i] = (int32_t)t;
+}
+
+// exclusive scan of n counts into ptr[0..n] (one block; n up to 2^28), total in ptr[n]
+__global__ void k_scan(int64_t n, const int32_t* __restrict__ cnt, int32_t* __restrict__ ptr,
+                       int64_t* __restrict__ total) {
+    __shared__ int64_t part[1024];
+    const int64_t chunk = (n + blockDim.x - 1) / blockDim.x;
+    const int64_t b0 = threadIdx.x * chunk, b1 = min(n, b0 + chunk);
+    int64_t s = 0;
+    for (int64_t i = b0; i < b1; ++i) s += cnt[i];
+    part[threadIdx.x] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int64_t acc = 0;
+        for (int k = 0; k < (int)blockDim.x; ++k) {
+            const int64_t v = part[k];
+            part[k] = acc;
+            acc += v;
+        }
+        *total = acc;
+        ptr[n] = (int32_t)min(acc, (int64_t)INT32_MAX);
+    }
+    __syncthreads();
+    int64_t acc = part[threadIdx.x];
+    for (int64_t i = b0; i < b1; ++i) {
+        ptr[i] = (int32_t)min(acc, (int64_t)INT32_MAX);
+        acc += cnt[i];
+    }
+}
+
+// transposed positions, diagonal positions and the row of every nonzero
+__global__ void k_pattern_maps(int64_t nv, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
+                               int32_t* __restrict__ tpos, int32_t* __restrict__ diag_pos, int32_t* __restrict__ row_of,
+                               int* __restrict__ status) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nv) return;
+    for (int32_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+        const int32_t j = col[k];
+        row_of[k] = (int32_t)i;
+        int32_t lo = row_ptr[j], hi = row_ptr[j + 1];
+        while (lo < hi) {
+            const int32_t mid = (lo + hi) >> 1;
+            if (col[mid] < (int32_t)i) lo = mid + 1;
+            else hi = mid;
+        }
+        if (lo >= row_ptr[j + 1] || col[lo] != (int32_t)i) {
+            atomicExch(status, PB_EMESH);
+            continue;
+        }
+        tpos[k] = lo;
+        if (j == (int32_t)i) diag_pos[i] = k;
+    }
+}
+
 // f(begin, end) over [0, n) split across up to 16 host threads
 template <class F>
 static void parallel_for(int64_t n, F&& f) {
@@ -120,13 +243,6 @@ static void parallel_for(int64_t n, F&& f) {
     for (auto& x : th) x.join();
 }
 
-static bool share_vertex(const int32_t* a, const int32_t* b) {
-    for (int i = 0; i < 3; ++i)
-        for (int j = 0; j < 3; ++j)
-            if (a[i] == b[j]) return true;
-    return false;
-}
-
 static int upload(void** dst, const void* src, size_t bytes, size_t* total) {
     PB_TRY(dev_alloc(dst, bytes));
     if (bytes) PB_CUDA(cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice));
@@ -135,10 +251,10 @@ static int upload(void** dst, const void* src, size_t bytes, size_t* total) {
 }
 
 static void free_mesh_arrays(pb_mesh* m) {
-    void* ptrs[] = {m->verts, m->tris,  m->tgeo, m->pts64,    m->pts32,       m->pts32lo,
-                    m->v2t_ptr, m->v2t, m->pairs, m->row_ptr, m->col,         m->tpos,
-                    m->diag_pos, m->contrib_ptr, m->contrib, m->status, m->pair_rev,
-                    m->pair_coin, m->pair_prim, m->pair_band};
+    void* ptrs[] = {m->verts,    m->tris,     m->tgeo,     m->pts64,   m->pts32,  m->pts32lo, m->v2t_ptr,
+                    m->v2t,      m->pairs,    m->adj_ptr,  m->row_ptr, m->col,    m->tpos,    m->row_of,
+                    m->diag_pos, m->status,   m->pair_rev, m->pair_coin, m->pair_prim, m->band_ptr, m->band_s,
+                    m->band_t};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (m->pts_ref && m->pts_ref != m->pts64) cudaFree(m->pts_ref);
@@ -327,13 +443,42 @@ static int load(pb_ctx* ctx, const double* verts_in, int64_t nv, const int32_t* 
         }
     });
 
+    // ---- each adjacent pair's reverse; the pairs the near kernels integrate:
+    // coincident ones, and one of every two reversed ones (t < s)
+    m->n_adj = n_adj;
+    std::vector<int32_t> rev(n_adj), coin_list, prim_list;
+    bool rev_ok = true;
+    parallel_for(n_adj, [&](int64_t b0, int64_t b1) {
+        for (int64_t p = b0; p < b1; ++p) {
+            const int32_t t = pairs[p].x, u = pairs[p].y;
+            const int4* bg = pairs.data() + adj_ptr[u];
+            const int4* en = pairs.data() + adj_ptr[u + 1];
+            const int4* q = std::lower_bound(bg, en, t, [](const int4& x, int32_t v) { return x.y < v; });
+            if (q == en || q->y != t) {
+                rev_ok = false;
+                continue;
+            }
+            rev[p] = (int32_t)(q - pairs.data());
+        }
+    });
+    if (!rev_ok) return set_error(PB_EMESH, "internal: pair without reverse");
+    for (int64_t p = 0; p < n_adj; ++p) {
+        const int32_t t = pairs[p].x, u = pairs[p].y;
+        if (t == u) coin_list.push_back((int32_t)p);
+        else if (t < u) prim_list.push_back((int32_t)p);
+    }
+
+    size_t tot = 0;
+    PB_TRY(upload((void**)&m->verts, V.data(), sizeof(double) * 3 * nv, &tot));
+    PB_TRY(upload((void**)&m->tris, T.data(), sizeof(int32_t) * 3 * nt, &tot));
+
     // ---- distance band: pairs sharing no vertex whose centroids are closer than
-    // eta (rho_t + rho_s), rho the largest centroid-vertex distance (same
-    // arithmetic, operation by operation, as the oracle's test), found through
-    // a uniform grid of cell size 2 eta max(rho); listed after the adjacent
-    // pairs, ordered by (ti, tj)
-    std::vector<int32_t> band_ptr(nt + 1, 0);
-    std::vector<int32_t> band_s;
+    // eta (rho_t + rho_s), rho the largest centroid-vertex distance. Centroids
+    // and radii here, with the oracle's arithmetic; a uniform grid of cell size
+    // 2 eta max(rho) here; the search on the device (k_band_search), which
+    // lists each triangle's partners in increasing order.
+    std::vector<int32_t> band_ptr(nt + 1, 0), band_s;
+    m->n_band = 0;
     if (eta > 0.0) {
         std::vector<double> C(3 * nt), R(nt);
         double rmax = 0.0;
@@ -377,82 +522,62 @@ static int load(pb_ctx* ctx, const double* verts_in, int64_t nv, const int32_t* 
             std::vector<int32_t> fill(cstart.begin(), cstart.end() - 1);
             for (int64_t t = 0; t < nt; ++t) ctri[fill[tcell[t]]++] = (int32_t)t;
         }
-        auto partners = [&](int64_t t, std::vector<int32_t>& out) {
-            out.clear();
-            const int64_t c0 = cell_of(t, 0), c1 = cell_of(t, 1), c2 = cell_of(t, 2);
-            for (int64_t z = std::max<int64_t>(0, c2 - 1); z <= std::min(dim[2] - 1, c2 + 1); ++z)
-                for (int64_t y = std::max<int64_t>(0, c1 - 1); y <= std::min(dim[1] - 1, c1 + 1); ++y)
-                    for (int64_t x = std::max<int64_t>(0, c0 - 1); x <= std::min(dim[0] - 1, c0 + 1); ++x) {
-                        const int64_t c = x + dim[0] * (y + dim[1] * z);
-                        for (int32_t k = cstart[c]; k < cstart[c + 1]; ++k) {
-                            const int32_t s = ctri[k];
-                            if (s == (int32_t)t || share_vertex(&T[3 * t], &T[3 * (int64_t)s])) continue;
-                            double d[3] = {C[3 * t] - C[3 * (int64_t)s], C[3 * t + 1] - C[3 * (int64_t)s + 1],
-                                           C[3 * t + 2] - C[3 * (int64_t)s + 2]};
-                            const double lim = eta * (R[t] + R[s]);
-                            if (d[0] * d[0] + d[1] * d[1] + d[2] * d[2] < lim * lim) out.push_back(s);
-                        }
-                    }
-            std::sort(out.begin(), out.end());
-        };
-        parallel_for(nt, [&](int64_t b0, int64_t b1) {
-            std::vector<int32_t> out;
-            for (int64_t t = b0; t < b1; ++t) {
-                partners(t, out);
-                band_ptr[t + 1] = (int32_t)out.size();
+        // scratch on the device: C, R, grid, counts, total
+        const size_t sb = sizeof(double) * 4 * nt + sizeof(int32_t) * (ncell + 1 + 3 * nt) + 64;
+        char* scratch = nullptr;
+        PB_TRY(dev_alloc((void**)&scratch, sb));
+        double* dC = (double*)scratch;
+        double* dR = dC + 3 * nt;
+        int64_t* dtotal = (int64_t*)(dR + nt);
+        int32_t* dcs = (int32_t*)(dtotal + 1);
+        int32_t* dct = dcs + ncell + 1;
+        int32_t* dtc = dct + nt;
+        int32_t* dcnt = dtc + nt;
+        int rc = PB_OK;
+        int64_t total = 0;
+        do {
+            if (cudaMemcpy(dC, C.data(), sizeof(double) * 3 * nt, cudaMemcpyHostToDevice) != cudaSuccess ||
+                cudaMemcpy(dR, R.data(), sizeof(double) * nt, cudaMemcpyHostToDevice) != cudaSuccess ||
+                cudaMemcpy(dcs, cstart.data(), sizeof(int32_t) * (ncell + 1), cudaMemcpyHostToDevice) != cudaSuccess ||
+                cudaMemcpy(dct, ctri.data(), sizeof(int32_t) * nt, cudaMemcpyHostToDevice) != cudaSuccess ||
+                cudaMemcpy(dtc, tcell.data(), sizeof(int32_t) * nt, cudaMemcpyHostToDevice) != cudaSuccess) {
+                rc = set_error(PB_ECUDA, "band search upload failed");
+                break;
             }
-        });
-        for (int64_t t = 0; t < nt; ++t) band_ptr[t + 1] += band_ptr[t];
-        if ((int64_t)band_ptr[nt] + n_adj > (((int64_t)1 << 31) - 1) / 9)
-            return set_error(PB_EINVAL, "distance band too wide for this mesh (%lld pairs)",
-                             (long long)band_ptr[nt]);
-        band_s.resize(band_ptr[nt]);
-        parallel_for(nt, [&](int64_t b0, int64_t b1) {
-            std::vector<int32_t> out;
-            for (int64_t t = b0; t < b1; ++t) {
-                partners(t, out);
-                std::copy(out.begin(), out.end(), band_s.begin() + band_ptr[t]);
+            BandGrid g = {dC, dR, dcs, dct, dtc, {dim[0], dim[1], dim[2]}, eta};
+            const unsigned nb = (unsigned)((nt + 127) / 128);
+            rc = dev_alloc((void**)&m->band_ptr, sizeof(int32_t) * (nt + 1));
+            if (rc != PB_OK) break;
+            k_band_search<<<nb, 128>>>(nt, m->tris, g, 0, dcnt, nullptr, nullptr, nullptr);
+            k_scan<<<1, 1024>>>(nt, dcnt, m->band_ptr, dtotal);
+            ::pb::count_launch(2);
+            if (cudaMemcpy(&total, dtotal, sizeof(int64_t), cudaMemcpyDeviceToHost) != cudaSuccess) {
+                rc = set_error(PB_ECUDA, "band search failed");
+                break;
             }
-        });
-        const int code = 0 | 1 << 2 | 2 << 4 | 0 << 6 | 1 << 8 | 2 << 10;  // frames in the original order
-        pairs.resize(n_adj + band_s.size());
-        for (int64_t t = 0; t < nt; ++t)
-            for (int32_t k = band_ptr[t]; k < band_ptr[t + 1]; ++k)
-                pairs[n_adj + k] = make_int4((int)t, band_s[k], 3, code);
+            if (total + n_adj > (((int64_t)1 << 31) - 1) / 9) {
+                rc = set_error(PB_EINVAL, "distance band too wide for this mesh (%lld pairs)", (long long)total);
+                break;
+            }
+            m->n_band = total;
+            if ((rc = dev_alloc((void**)&m->band_s, sizeof(int32_t) * (total + 1))) != PB_OK) break;
+            if ((rc = dev_alloc((void**)&m->band_t, sizeof(int32_t) * (total + 1))) != PB_OK) break;
+            k_band_search<<<nb, 128>>>(nt, m->tris, g, 1, nullptr, m->band_ptr, m->band_s, m->band_t);
+            ::pb::count_launch();
+            band_s.resize(total);
+            if (cudaMemcpy(band_ptr.data(), m->band_ptr, sizeof(int32_t) * (nt + 1), cudaMemcpyDeviceToHost) !=
+                    cudaSuccess ||
+                (total && cudaMemcpy(band_s.data(), m->band_s, sizeof(int32_t) * total, cudaMemcpyDeviceToHost) !=
+                              cudaSuccess)) {
+                rc = set_error(PB_ECUDA, "band search failed");
+                break;
+            }
+        } while (false);
+        cudaFree(scratch);
+        if (rc != PB_OK) return rc;
+        tot += sizeof(int32_t) * (nt + 1 + 2 * (m->n_band + 1));
     }
-    m->npairs = (int64_t)pairs.size();
-    m->n_adj = n_adj;
-    const int64_t n_band = m->npairs - n_adj;
-
-    // each pair's reverse (the band criterion is symmetric), and the pairs the
-    // near kernels integrate: coincident ones, and one of every two reversed
-    // adjacent or band pairs (t < s), which also gives the other
-    std::vector<int32_t> rev(pairs.size()), coin_list, prim_list, band_list;
-    auto find_rev = [&](int64_t p, const std::vector<int32_t>& ptr, int64_t base) -> int64_t {
-        const int32_t t = pairs[p].x, u = pairs[p].y;
-        int64_t lo2 = base + ptr[u], hi2 = base + ptr[u + 1];
-        const int64_t end = hi2;
-        while (lo2 < hi2) {
-            int64_t mid = (lo2 + hi2) / 2;
-            if (pairs[mid].y < t) lo2 = mid + 1;
-            else hi2 = mid;
-        }
-        return (lo2 < end && pairs[lo2].y == t) ? lo2 : -1;
-    };
-    bool rev_ok = true;
-    parallel_for(m->npairs, [&](int64_t b0, int64_t b1) {
-        for (int64_t p = b0; p < b1; ++p) {
-            int64_t r = p < n_adj ? find_rev(p, adj_ptr, 0) : find_rev(p, band_ptr, n_adj);
-            if (r < 0) rev_ok = false;
-            rev[p] = (int32_t)r;
-        }
-    });
-    if (!rev_ok) return set_error(PB_EMESH, "internal: pair without reverse");
-    for (int64_t p = 0; p < m->npairs; ++p) {
-        const int32_t t = pairs[p].x, u = pairs[p].y;
-        if (t == u) coin_list.push_back((int32_t)p);
-        else if (t < u) (p < n_adj ? prim_list : band_list).push_back((int32_t)p);
-    }
+    m->npairs = n_adj + m->n_band;
 
     // ---- near pattern: row i holds every vertex of every triangle paired with a
     // triangle at i (the 2-ring, and the band); counted, then filled and sorted
@@ -460,17 +585,22 @@ static int load(pb_ctx* ctx, const double* verts_in, int64_t nv, const int32_t* 
         out.clear();
         for (int32_t k = v2t_ptr[i]; k < v2t_ptr[i + 1]; ++k) {
             const int32_t t = v2t[k] / 3;
-            const int64_t ranges[2][2] = {{adj_ptr[t], adj_ptr[t + 1]},
-                                          {n_adj + band_ptr[t], n_adj + band_ptr[t + 1]}};
-            for (int r = 0; r < (eta > 0.0 ? 2 : 1); ++r)
-                for (int64_t p = ranges[r][0]; p < ranges[r][1]; ++p) {
-                    const int32_t* f = &T[3 * (int64_t)pairs[p].y];
-                    for (int b = 0; b < 3; ++b)
-                        if (mark[f[b]] != (int32_t)i) {
-                            mark[f[b]] = (int32_t)i;
-                            out.push_back(f[b]);
-                        }
-                }
+            for (int32_t p = adj_ptr[t]; p < adj_ptr[t + 1]; ++p) {
+                const int32_t* f = &T[3 * (int64_t)pairs[p].y];
+                for (int b = 0; b < 3; ++b)
+                    if (mark[f[b]] != (int32_t)i) {
+                        mark[f[b]] = (int32_t)i;
+                        out.push_back(f[b]);
+                    }
+            }
+            for (int32_t q = band_ptr[t]; q < band_ptr[t + 1]; ++q) {
+                const int32_t* f = &T[3 * (int64_t)band_s[q]];
+                for (int b = 0; b < 3; ++b)
+                    if (mark[f[b]] != (int32_t)i) {
+                        mark[f[b]] = (int32_t)i;
+                        out.push_back(f[b]);
+                    }
+            }
         }
         std::sort(out.begin(), out.end());
     };
@@ -495,82 +625,28 @@ static int load(pb_ctx* ctx, const double* verts_in, int64_t nv, const int32_t* 
             std::copy(out.begin(), out.end(), col.begin() + row_ptr[i]);
         }
     });
-    std::vector<int32_t> tpos(nnz), diag_pos(nv, -1);
-    bool sym_ok = true;
-    parallel_for(nv, [&](int64_t b0, int64_t b1) {
-        for (int64_t i = b0; i < b1; ++i)
-            for (int32_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
-                const int32_t j = col[k];
-                const int32_t* bg = col.data() + row_ptr[j];
-                const int32_t* en = col.data() + row_ptr[j + 1];
-                const int32_t* q = std::lower_bound(bg, en, (int32_t)i);
-                if (q == en || *q != (int32_t)i) {
-                    sym_ok = false;
-                    continue;
-                }
-                tpos[k] = (int32_t)(q - col.data());
-                if (j == i) diag_pos[i] = k;
-            }
-    });
-    if (!sym_ok) return set_error(PB_EMESH, "internal: near pattern is not symmetric");
 
-    // ---- contributions (pair * 9 + a * 3 + b) of every listed pair to each
-    // nonzero, row by row in a fixed order (corners of the row vertex, then its
-    // triangle's adjacent pairs and band pairs, then the trial corner): a
-    // counting pass and a filling pass over the same loops
-    std::vector<int32_t> cnt(nnz + 1, 0);
-    std::vector<int32_t> cidx((size_t)9 * pairs.size());
-    for (int pass = 0; pass < 2; ++pass) {
-        if (pass == 1)
-            for (int64_t k = 0; k < nnz; ++k) cnt[k + 1] += cnt[k];
-        parallel_for(nv, [&](int64_t b0, int64_t b1) {
-            std::vector<int32_t> colpos(nv, 0);
-            std::vector<int32_t> fill;
-            for (int64_t i = b0; i < b1; ++i) {
-                for (int32_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) colpos[col[k]] = k;
-                if (pass == 1) fill.assign(cnt.begin() + row_ptr[i], cnt.begin() + row_ptr[i + 1]);
-                for (int32_t k = v2t_ptr[i]; k < v2t_ptr[i + 1]; ++k) {
-                    const int32_t t = v2t[k] / 3, a = v2t[k] % 3;
-                    const int64_t ranges[2][2] = {{adj_ptr[t], adj_ptr[t + 1]},
-                                                  {n_adj + band_ptr[t], n_adj + band_ptr[t + 1]}};
-                    for (int r = 0; r < (eta > 0.0 ? 2 : 1); ++r)
-                        for (int64_t p = ranges[r][0]; p < ranges[r][1]; ++p) {
-                            const int32_t* f = &T[3 * (int64_t)pairs[p].y];
-                            for (int b = 0; b < 3; ++b) {
-                                const int32_t kk = colpos[f[b]];
-                                if (pass == 0) cnt[kk + 1]++;
-                                else cidx[fill[kk - row_ptr[i]]++] = (int32_t)(9 * p + 3 * a + b);
-                            }
-                        }
-                }
-            }
-        });
-    }
-    m->ncontrib = (int64_t)cidx.size();
-    (void)n_band;
-
-    // ---- upload
-    size_t tot = 0;
-    PB_TRY(upload((void**)&m->verts, V.data(), sizeof(double) * 3 * nv, &tot));
-    PB_TRY(upload((void**)&m->tris, T.data(), sizeof(int32_t) * 3 * nt, &tot));
+    // ---- upload; transposed and diagonal positions on the device
     PB_TRY(upload((void**)&m->v2t_ptr, v2t_ptr.data(), sizeof(int32_t) * (nv + 1), &tot));
     PB_TRY(upload((void**)&m->v2t, v2t.data(), sizeof(int32_t) * 3 * nt, &tot));
     PB_TRY(upload((void**)&m->pairs, pairs.data(), sizeof(int4) * pairs.size(), &tot));
+    PB_TRY(upload((void**)&m->adj_ptr, adj_ptr.data(), sizeof(int32_t) * (nt + 1), &tot));
     PB_TRY(upload((void**)&m->pair_rev, rev.data(), sizeof(int32_t) * rev.size(), &tot));
     PB_TRY(upload((void**)&m->pair_coin, coin_list.data(), sizeof(int32_t) * coin_list.size(), &tot));
     PB_TRY(upload((void**)&m->pair_prim, prim_list.data(), sizeof(int32_t) * prim_list.size(), &tot));
-    PB_TRY(upload((void**)&m->pair_band, band_list.data(), sizeof(int32_t) * band_list.size(), &tot));
     m->n_coin = (int64_t)coin_list.size();
     m->n_prim = (int64_t)prim_list.size();
-    m->n_band = (int64_t)band_list.size();
     PB_TRY(upload((void**)&m->row_ptr, row_ptr.data(), sizeof(int32_t) * (nv + 1), &tot));
     PB_TRY(upload((void**)&m->col, col.data(), sizeof(int32_t) * nnz, &tot));
-    PB_TRY(upload((void**)&m->tpos, tpos.data(), sizeof(int32_t) * nnz, &tot));
-    PB_TRY(upload((void**)&m->diag_pos, diag_pos.data(), sizeof(int32_t) * nv, &tot));
-    PB_TRY(upload((void**)&m->contrib_ptr, cnt.data(), sizeof(int32_t) * (nnz + 1), &tot));
-    PB_TRY(upload((void**)&m->contrib, cidx.data(), sizeof(int32_t) * cidx.size(), &tot));
+    PB_TRY(dev_alloc((void**)&m->tpos, sizeof(int32_t) * nnz));
+    PB_TRY(dev_alloc((void**)&m->row_of, sizeof(int32_t) * nnz));
+    PB_TRY(dev_alloc((void**)&m->diag_pos, sizeof(int32_t) * nv));
+    tot += sizeof(int32_t) * (2 * nnz + nv);
     PB_TRY(dev_alloc((void**)&m->status, sizeof(int)));
     PB_CUDA(cudaMemset(m->status, 0, sizeof(int)));
+    k_pattern_maps<<<(unsigned)((nv + 127) / 128), 128>>>(nv, m->row_ptr, m->col, m->tpos, m->diag_pos, m->row_of,
+                                                          m->status);
+    ::pb::count_launch();
     PB_TRY(dev_alloc((void**)&m->tgeo, sizeof(double) * 16 * nt));
     PB_TRY(dev_alloc((void**)&m->pts64, sizeof(double) * 4 * m->np));
     PB_TRY(dev_alloc((void**)&m->pts32, sizeof(float) * 4 * m->np));
@@ -593,6 +669,9 @@ static int load(pb_ctx* ctx, const double* verts_in, int64_t nv, const int32_t* 
     ::pb::count_launch();
     PB_CUDA(cudaGetLastError());
     PB_CUDA(cudaDeviceSynchronize());
+    int st = 0;
+    PB_CUDA(cudaMemcpy(&st, m->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st != 0) return set_error(PB_EMESH, "internal: near pattern is not symmetric");
     return PB_OK;
 }
 

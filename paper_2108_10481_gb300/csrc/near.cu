@@ -287,18 +287,32 @@ k_near_pairs(const double* __restrict__ verts, const int32_t* __restrict__ tris,
 
 // Band pairs (share no vertex, closer than the plan's band): the blocks of the
 // band rule minus those of the far rule, for the pair and its reverse, one
-// thread per pair of reversed pairs. Points are the rules' barycentric
-// combinations of the corners, in the corners' original order.
+// thread per band pair (t, s) with t < s. Points are the rules' barycentric
+// combinations of the corners, in the corners' original order. Band pair q is
+// stored at n_adj + q.
 constexpr int BAND_THREADS = 128;
 
 __global__ void __launch_bounds__(BAND_THREADS, 2)
 k_band_pairs(const double* __restrict__ verts, const int32_t* __restrict__ tris, const double* __restrict__ tgeo,
-             const int4* __restrict__ pairs, const int32_t* __restrict__ list, int64_t nlist,
-             const int32_t* __restrict__ rev, Rule fine, Rule coarse, double kappa, double* __restrict__ ss_out) {
-    const int64_t li = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (li >= nlist) return;
-    const int64_t p = list[li];
-    const int4 pr = pairs[p];
+             const int32_t* __restrict__ band_ptr, const int32_t* __restrict__ band_s,
+             const int32_t* __restrict__ band_t, int64_t n_band, int64_t n_adj, Rule fine, Rule coarse, double kappa,
+             double* __restrict__ ss_out, int* __restrict__ status) {
+    const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (q >= n_band) return;
+    const int4 pr = make_int4(band_t[q], band_s[q], 3, 0);
+    if (pr.x > pr.y) return;  // the reverse of a pair handled by its other thread
+    // the reversed pair: t among the partners of s (sorted)
+    int32_t lo = band_ptr[pr.y], hi = band_ptr[pr.y + 1];
+    while (lo < hi) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (band_s[mid] < pr.x) lo = mid + 1;
+        else hi = mid;
+    }
+    if (lo >= band_ptr[pr.y + 1] || band_s[lo] != pr.x) {  // the band lists are symmetric by construction
+        atomicExch(status, PB_EMESH);
+        return;
+    }
+    const int64_t p = n_adj + q, pr_rev = n_adj + lo;
     double pa[3][3], pb[3][3];
     for (int a = 0; a < 3; ++a)
         for (int k = 0; k < 3; ++k) {
@@ -333,52 +347,62 @@ k_band_pairs(const double* __restrict__ verts, const int32_t* __restrict__ tris,
     A.area = gA[3];
     B.area = gB[3];
     expand_blocks(acc, A, B, gA, gB, kappa, false, ss_out + 54 * p);
-    expand_blocks(acc, A, B, gA, gB, kappa, true, ss_out + 54 * (int64_t)rev[p]);
+    expand_blocks(acc, A, B, gA, gB, kappa, true, ss_out + 54 * pr_rev);
 }
 
-// One thread per nonzero: sum the contributions in their fixed (pair) order.
-// Adjacent pairs (p < n_adj) hold the regularised blocks in ss and the far
-// rule's in far; band pairs hold the difference already in ss.
+// One thread per nonzero (i, j): walk the pairs of every triangle at i in a
+// fixed order (the triangles of i, then each one's adjacent pairs and band
+// pairs, then the trial corner) and sum the blocks of those whose trial
+// triangle has corner j. Adjacent pairs (p < n_adj) hold the regularised
+// blocks in ss and the far rule's in far; band pairs hold the difference in ss.
+// Threads of one row walk the same pairs, so the loads are shared.
 __global__ void k_near_entries(int64_t nnz, int64_t nv, const int32_t* __restrict__ row_of,
-                               const int32_t* __restrict__ col, const int32_t* __restrict__ cptr,
-                               const int32_t* __restrict__ contrib, const int4* __restrict__ pairs, int64_t n_adj,
-                               const double* __restrict__ tgeo, const double* __restrict__ ss,
+                               const int32_t* __restrict__ col, const int32_t* __restrict__ v2t_ptr,
+                               const int32_t* __restrict__ v2t, const int32_t* __restrict__ tris,
+                               const int32_t* __restrict__ adj_ptr, const int4* __restrict__ pairs,
+                               const int32_t* __restrict__ band_ptr, const int32_t* __restrict__ band_s,
+                               int64_t n_adj, const double* __restrict__ tgeo, const double* __restrict__ ss,
                                const double* __restrict__ far, double* __restrict__ val,
                                double* __restrict__ diag) {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= nnz) return;
+    const int32_t i = row_of[e], j = col[e];
     double nearv[6] = {0, 0, 0, 0, 0, 0}, full[6] = {0, 0, 0, 0, 0, 0}, mass = 0.0;
-    for (int32_t c = cptr[e]; c < cptr[e + 1]; ++c) {
-        int32_t code = contrib[c];
-        int64_t p = code / 9;
-        int ab = code - 9 * (int)p;
-        if (p < n_adj) {
-            for (int o = 0; o < 6; ++o) {
-                double s = ss[54 * p + 9 * o + ab];
-                nearv[o] += s - far[54 * p + 9 * o + ab];
-                full[o] += s;
+    for (int32_t k = v2t_ptr[i]; k < v2t_ptr[i + 1]; ++k) {
+        const int32_t t = v2t[k] / 3, a = v2t[k] % 3;
+        for (int32_t p = adj_ptr[t]; p < adj_ptr[t + 1]; ++p) {
+            const int4 pr = pairs[p];
+            const int32_t* f = tris + 3 * (int64_t)pr.y;
+            for (int b = 0; b < 3; ++b) {
+                if (f[b] != j) continue;
+                const int ab = 3 * a + b;
+                for (int o = 0; o < 6; ++o) {
+                    double s = ss[54 * (int64_t)p + 9 * o + ab];
+                    nearv[o] += s - far[54 * (int64_t)p + 9 * o + ab];
+                    full[o] += s;
+                }
+                if (pr.z == 0) mass += tgeo[16 * (int64_t)pr.x + 3] / 12.0 * ((ab % 4 == 0) ? 2.0 : 1.0);
             }
-            int4 pr = pairs[p];
-            if (pr.z == 0) mass += tgeo[16 * (int64_t)pr.x + 3] / 12.0 * ((ab % 4 == 0) ? 2.0 : 1.0);
-        } else {
-            for (int o = 0; o < 6; ++o) nearv[o] += ss[54 * p + 9 * o + ab];  // never on the diagonal
         }
+        if (band_ptr)
+            for (int32_t q = band_ptr[t]; q < band_ptr[t + 1]; ++q) {
+                const int32_t* f = tris + 3 * (int64_t)band_s[q];
+                for (int b = 0; b < 3; ++b) {
+                    if (f[b] != j) continue;
+                    const int64_t p = n_adj + q;
+                    for (int o = 0; o < 6; ++o) nearv[o] += ss[54 * p + 9 * o + 3 * a + b];  // never diagonal
+                }
+            }
     }
     const int map[6] = {N_VL, N_KL, N_DL, N_VY, N_KY, N_DY};
     for (int o = 0; o < 6; ++o) val[map[o] * nnz + e] = nearv[o];
     val[N_M * nnz + e] = mass;
-    int32_t i = row_of[e];
-    if (col[e] == i) {
+    if (j == i) {
         for (int o = 0; o < 6; ++o) diag[map[o] * nv + i] = full[o];
         diag[N_M * nv + i] = mass;
     }
 }
 
-__global__ void k_row_of(int64_t nv, const int32_t* __restrict__ row_ptr, int32_t* __restrict__ row_of) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= nv) return;
-    for (int32_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) row_of[k] = (int32_t)i;
-}
 
 static void free_near(pb_near* nf) {
     if (nf->val) cudaFree(nf->val);
@@ -392,10 +416,8 @@ static int build(pb_ctx* ctx, const pb_mesh* m, double kappa, pb_near* nf, cudaS
     PB_TRY(dev_alloc((void**)&nf->val, sizeof(double) * N_VALS * m->nnz));
     PB_TRY(dev_alloc((void**)&nf->diag, sizeof(double) * N_VALS * m->nv));
     double *ss = nullptr, *far = nullptr;
-    int32_t* row_of = nullptr;
     int rc = dev_alloc((void**)&ss, sizeof(double) * 54 * m->npairs);
     if (rc == PB_OK) rc = dev_alloc((void**)&far, sizeof(double) * 54 * m->n_adj);
-    if (rc == PB_OK) rc = dev_alloc((void**)&row_of, sizeof(int32_t) * m->nnz);
     if (rc == PB_OK) {
         Gauss gq = gauss01(m->n_ss);
         int threads = NEAR_THREADS;  // one warp per pair
@@ -413,21 +435,24 @@ static int build(pb_ctx* ctx, const pb_mesh* m, double kappa, pb_near* nf, cudaS
         if (m->n_band) {
             Rule fine = mesh_ref_rule(m), coarse = mesh_rule(m);
             k_band_pairs<<<(unsigned)((m->n_band + BAND_THREADS - 1) / BAND_THREADS), BAND_THREADS, 0, s>>>(
-                m->verts, m->tris, m->tgeo, m->pairs, m->pair_band, m->n_band, m->pair_rev, fine, coarse, kappa, ss);
+                m->verts, m->tris, m->tgeo, m->band_ptr, m->band_s, m->band_t, m->n_band, m->n_adj, fine, coarse,
+                kappa, ss, m->status);
             ::pb::count_launch();
         }
-        k_row_of<<<(unsigned)((m->nv + 255) / 256), 256, 0, s>>>(m->nv, m->row_ptr, row_of); ::pb::count_launch();
         cudaMemsetAsync(nf->diag, 0, sizeof(double) * N_VALS * m->nv, s);
         k_near_entries<<<(unsigned)((m->nnz + 255) / 256), 256, 0, s>>>(
-            m->nnz, m->nv, row_of, m->col, m->contrib_ptr, m->contrib, m->pairs, m->n_adj, m->tgeo, ss, far, nf->val,
-            nf->diag); ::pb::count_launch();
+            m->nnz, m->nv, m->row_of, m->col, m->v2t_ptr, m->v2t, m->tris, m->adj_ptr, m->pairs,
+            m->n_band ? m->band_ptr : nullptr, m->band_s, m->n_adj, m->tgeo, ss, far, nf->val, nf->diag);
+        ::pb::count_launch();
         cudaError_t e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        int st = 0;
+        if (e == cudaSuccess && m->n_band) e = cudaMemcpy(&st, m->status, sizeof(int), cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) rc = set_error(PB_ECUDA, "near build: %s", cudaGetErrorString(e));
+        else if (st == PB_EMESH) rc = set_error(PB_EMESH, "internal: band pair without reverse");
     }
     if (ss) cudaFree(ss);
     if (far) cudaFree(far);
-    if (row_of) cudaFree(row_of);
     return rc;
 }
 
