@@ -168,6 +168,7 @@ struct pb_mesh {
     int32_t* band_t = nullptr;
     // vertex-pair pattern of the near field (symmetric)
     int64_t nnz = 0;
+    int max_row = 0;            // longest row of the pattern
     int32_t* row_ptr = nullptr; // nv + 1
     int32_t* col = nullptr;     // nnz
     int32_t* tpos = nullptr;    // nnz: index of the transposed entry

@@ -616,6 +616,8 @@ static int load(pb_ctx* ctx, const double* verts_in, int64_t nv, const int32_t* 
     if (row_cnt[nv] > ((int64_t)1 << 31) - 1) return set_error(PB_EINVAL, "near pattern too large");
     const int64_t nnz = row_cnt[nv];
     m->nnz = nnz;
+    m->max_row = 0;
+    for (int64_t i = 0; i < nv; ++i) m->max_row = std::max(m->max_row, (int)(row_cnt[i + 1] - row_cnt[i]));
     std::vector<int32_t> row_ptr(nv + 1), col(nnz);
     for (int64_t i = 0; i <= nv; ++i) row_ptr[i] = (int32_t)row_cnt[i];
     parallel_for(nv, [&](int64_t b0, int64_t b1) {

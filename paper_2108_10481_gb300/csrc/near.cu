@@ -10,6 +10,7 @@
 //   D_ab = int int G [curl l_a . curl l_b + kappa^2 n_x.n_y l_a l_b]  (hypersingular,
 //          integrated by parts; curl l_a = -e_a / (2|tau|), e_a the edge opposite a)
 // with G_int = 1/(4 pi r), G_ext = exp(-kappa r)/(4 pi r).
+#include <algorithm>
 #include <cmath>
 #include <cstdlib>
 
@@ -285,6 +286,100 @@ k_near_pairs(const double* __restrict__ verts, const int32_t* __restrict__ tris,
     if (SYM && lane == 1) expand_blocks(acc, A, B, gA, gB, kappa, true, far_out + 54 * (int64_t)rev[p]);
 }
 
+// Coincident pairs (tau, tau). The double layer vanishes (x - y lies in the
+// plane of tau), and the single-layer integrand is symmetric in x and y, so
+// the three regions of the coincident map whose roles are exchanged (regions
+// 3..5) give the transposes of regions 0..2: integrate those and symmetrise.
+// Accumulators: S_L[9], S_Y[9], sum w G_L, sum w G_Y. The far rule likewise
+// over its point pairs i < j (identical points are skipped by the pair kernel).
+__device__ __forceinline__ void accum_v(double* acc, double w, const double* x, const double* y, const double* lx,
+                                        const double* ly, double kappa) {
+    const double d0 = x[0] - y[0], d1 = x[1] - y[1], d2 = x[2] - y[2];
+    const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+    const double rinv = rsqrt(r2);
+    const double gl = rinv * 0.07957747154594767;  // 1 / (4 pi r)
+    const double gy = exp(-kappa * (r2 * rinv)) * gl;
+    for (int a = 0; a < 3; ++a) {
+        const double wa = w * lx[a];
+        for (int b = 0; b < 3; ++b) {
+            const double ll = wa * ly[b];
+            acc[3 * a + b] += gl * ll;
+            acc[9 + 3 * a + b] += gy * ll;
+        }
+    }
+    acc[18] += w * gl;
+    acc[19] += w * gy;
+}
+
+__device__ void expand_coin(const double* acc, const TriFrame& A, const double* tgeoA, double kappa, double* out) {
+    const double nn = A.n[0] * A.n[0] + A.n[1] * A.n[1] + A.n[2] * A.n[2];
+    const double f = 1.0 / (4.0 * A.area * A.area);
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+            const double* ea = tgeoA + 4 + 3 * a;
+            const double* eb = tgeoA + 4 + 3 * b;
+            const double cc = f * (ea[0] * eb[0] + ea[1] * eb[1] + ea[2] * eb[2]);
+            const int ab = 3 * a + b, ba = 3 * b + a;
+            const double vl = acc[ab] + acc[ba], vy = acc[9 + ab] + acc[9 + ba];
+            out[0 * 9 + ab] = vl;
+            out[1 * 9 + ab] = 0.0;
+            out[2 * 9 + ab] = cc * (2.0 * acc[18]);
+            out[3 * 9 + ab] = vy;
+            out[4 * 9 + ab] = 0.0;
+            out[5 * 9 + ab] = cc * (2.0 * acc[19]) + kappa * kappa * nn * vy;
+        }
+}
+
+__global__ void __launch_bounds__(NEAR_THREADS, 4)
+k_coin_pairs(const double* __restrict__ verts, const int32_t* __restrict__ tris, const double* __restrict__ tgeo,
+             const int4* __restrict__ pairs, const int32_t* __restrict__ list, int64_t nlist, Gauss gq, Rule rule,
+             double kappa, double* __restrict__ ss_out, double* __restrict__ far_out) {
+    __shared__ TriFrame frames[NEAR_THREADS / 32];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int64_t li = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    if (li >= nlist) return;  // whole warps leave together
+    const int64_t p = list[li];
+    const int4 pr = pairs[p];
+    TriFrame& A = frames[wid];
+    if (lane == 0) make_frame(verts, tris, tgeo, pr.x, pr.w & 63, A);
+    __syncwarp();
+    const int n = gq.n;
+    const int n2 = n * n, n4 = n2 * n2;
+    const double jac_ab = (2.0 * A.area) * (2.0 * A.area);
+    double acc[20];
+    for (int k = 0; k < 20; ++k) acc[k] = 0.0;
+    for (int idx = lane; idx < 3 * n4; idx += 32) {
+        const int reg = idx / n4;
+        const int r = idx - reg * n4;
+        const int i0 = r / (n2 * n), i1 = (r / n2) % n, i2 = (r / n) % n, i3 = r % n;
+        double sx, tx, sy, ty;
+        const double jac = ss_map(0, reg, gq.x[i0], gq.x[i1], gq.x[i2], gq.x[i3], sx, tx, sy, ty);
+        const double w = gq.w[i0] * gq.w[i1] * gq.w[i2] * gq.w[i3] * jac * jac_ab;
+        double x[3], y[3], lx[3], ly[3];
+        frame_point(A, sx, tx, x, lx);
+        frame_point(A, sy, ty, y, ly);
+        accum_v(acc, w, x, y, lx, ly, kappa);
+    }
+    for (int k = 0; k < 20; ++k) acc[k] = warp_sum(acc[k]);
+    const double* gA = tgeo + 16 * (int64_t)pr.x;
+    if (lane == 0) expand_coin(acc, A, gA, kappa, ss_out + 54 * p);
+    for (int k = 0; k < 20; ++k) acc[k] = 0.0;
+    const int Q = rule.Q;
+    for (int idx = lane; idx < Q * Q; idx += 32) {
+        const int i = idx / Q, j = idx % Q;
+        if (j <= i) continue;
+        double x[3], y[3];
+        for (int k = 0; k < 3; ++k) {
+            x[k] = rule.l[i][0] * corner(A, 0, k) + rule.l[i][1] * corner(A, 1, k) + rule.l[i][2] * corner(A, 2, k);
+            y[k] = rule.l[j][0] * corner(A, 0, k) + rule.l[j][1] * corner(A, 1, k) + rule.l[j][2] * corner(A, 2, k);
+        }
+        const double w = rule.w[i] * A.area * rule.w[j] * A.area;
+        accum_v(acc, w, x, y, rule.l[i], rule.l[j], kappa);
+    }
+    for (int k = 0; k < 20; ++k) acc[k] = warp_sum(acc[k]);
+    if (lane == 0) expand_coin(acc, A, gA, kappa, far_out + 54 * p);
+}
+
 // Band pairs (share no vertex, closer than the plan's band): the blocks of the
 // band rule minus those of the far rule, for the pair and its reverse, one
 // thread per band pair (t, s) with t < s. Points are the rules' barycentric
@@ -350,59 +445,119 @@ k_band_pairs(const double* __restrict__ verts, const int32_t* __restrict__ tris,
     expand_blocks(acc, A, B, gA, gB, kappa, true, ss_out + 54 * pr_rev);
 }
 
-// One thread per nonzero (i, j): walk the pairs of every triangle at i in a
-// fixed order (the triangles of i, then each one's adjacent pairs and band
-// pairs, then the trial corner) and sum the blocks of those whose trial
-// triangle has corner j. Adjacent pairs (p < n_adj) hold the regularised
-// blocks in ss and the far rule's in far; band pairs hold the difference in ss.
-// Threads of one row walk the same pairs, so the loads are shared.
-__global__ void k_near_entries(int64_t nnz, int64_t nv, const int32_t* __restrict__ row_of,
-                               const int32_t* __restrict__ col, const int32_t* __restrict__ v2t_ptr,
-                               const int32_t* __restrict__ v2t, const int32_t* __restrict__ tris,
-                               const int32_t* __restrict__ adj_ptr, const int4* __restrict__ pairs,
-                               const int32_t* __restrict__ band_ptr, const int32_t* __restrict__ band_s,
-                               int64_t n_adj, const double* __restrict__ tgeo, const double* __restrict__ ss,
-                               const double* __restrict__ far, double* __restrict__ val,
-                               double* __restrict__ diag) {
-    int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (e >= nnz) return;
-    const int32_t i = row_of[e], j = col[e];
-    double nearv[6] = {0, 0, 0, 0, 0, 0}, full[6] = {0, 0, 0, 0, 0, 0}, mass = 0.0;
-    for (int32_t k = v2t_ptr[i]; k < v2t_ptr[i + 1]; ++k) {
-        const int32_t t = v2t[k] / 3, a = v2t[k] % 3;
-        for (int32_t p = adj_ptr[t]; p < adj_ptr[t + 1]; ++p) {
-            const int4 pr = pairs[p];
-            const int32_t* f = tris + 3 * (int64_t)pr.y;
-            for (int b = 0; b < 3; ++b) {
-                if (f[b] != j) continue;
-                const int ab = 3 * a + b;
-                for (int o = 0; o < 6; ++o) {
-                    double s = ss[54 * (int64_t)p + 9 * o + ab];
-                    nearv[o] += s - far[54 * (int64_t)p + 9 * o + ab];
-                    full[o] += s;
-                }
-                if (pr.z == 0) mass += tgeo[16 * (int64_t)pr.x + 3] / 12.0 * ((ab % 4 == 0) ? 2.0 : 1.0);
-            }
-        }
-        if (band_ptr)
-            for (int32_t q = band_ptr[t]; q < band_ptr[t + 1]; ++q) {
-                const int32_t* f = tris + 3 * (int64_t)band_s[q];
-                for (int b = 0; b < 3; ++b) {
-                    if (f[b] != j) continue;
-                    const int64_t p = n_adj + q;
-                    for (int o = 0; o < 6; ++o) nearv[o] += ss[54 * p + 9 * o + 3 * a + b];  // never diagonal
-                }
-            }
+// One warp per row i. The warp walks the contributions of the row in a fixed
+// order (the triangles t of i; each one's adjacent pairs, then its band pairs;
+// the trial corner b), 32 at a time: each lane finds its contribution's
+// column position (binary search in the row's sorted columns) and stages its
+// values; then the lane that owns a position (position mod 32) adds the
+// staged values for it in slot order. Every entry therefore sums its
+// contributions in the walk's order, whatever the scheduling. Adjacent pairs
+// (p < n_adj) hold the regularised blocks in ss and the far rule's in far;
+// band pairs hold the difference in ss. The row's accumulators (6 operators
+// and M) live in shared memory, maxrow entries per warp.
+constexpr int ROW_STAGE = 13;  // near[6], full[6] (kept for the diagonal), mass; positions apart (ints)
+
+__device__ __forceinline__ int row_lower_bound(const int32_t* c, int n, int32_t v) {
+    int lo = 0, hi = n;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (c[mid] < v) lo = mid + 1;
+        else hi = mid;
     }
-    const int map[6] = {N_VL, N_KL, N_DL, N_VY, N_KY, N_DY};
-    for (int o = 0; o < 6; ++o) val[map[o] * nnz + e] = nearv[o];
-    val[N_M * nnz + e] = mass;
-    if (j == i) {
-        for (int o = 0; o < 6; ++o) diag[map[o] * nv + i] = full[o];
-        diag[N_M * nv + i] = mass;
-    }
+    return lo;
 }
 
+// shared memory of one warp, in doubles
+__host__ __device__ inline size_t row_warp_doubles(int maxrow) {
+    return 32 * ROW_STAGE + 16 + 7 * (size_t)maxrow + ((size_t)maxrow + 1) / 2;
+}
+
+__global__ void k_near_rows(int64_t nv, int64_t nnz, int maxrow, int warps, const int32_t* __restrict__ row_ptr,
+                            const int32_t* __restrict__ col, const int32_t* __restrict__ v2t_ptr,
+                            const int32_t* __restrict__ v2t, const int32_t* __restrict__ tris,
+                            const int32_t* __restrict__ adj_ptr, const int4* __restrict__ pairs,
+                            const int32_t* __restrict__ band_ptr, const int32_t* __restrict__ band_s, int64_t n_adj,
+                            const double* __restrict__ tgeo, const double* __restrict__ ss,
+                            const double* __restrict__ far, double* __restrict__ val, double* __restrict__ diag) {
+    extern __shared__ double rsm[];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * warps + w;
+    if (i >= nv) return;  // whole warps
+    double* stage = rsm + (size_t)w * row_warp_doubles(maxrow);
+    int32_t* spos = (int32_t*)(stage + 32 * ROW_STAGE);  // 32 ints
+    double* acc = stage + 32 * ROW_STAGE + 16;
+    int32_t* scol = (int32_t*)(acc + 7 * (size_t)maxrow);
+    const int32_t r0 = row_ptr[i];
+    const int n = row_ptr[i + 1] - r0;  // <= maxrow
+    for (int k = lane; k < n; k += 32) scol[k] = col[r0 + k];
+    for (int k = lane; k < 7 * n; k += 32) acc[k] = 0.0;
+    __syncwarp();
+    const int diag_pos = row_lower_bound(scol, n, (int32_t)i);
+    double dfull[6] = {0, 0, 0, 0, 0, 0};  // the diagonal entry's full values (kept by its owner lane)
+    for (int32_t k = v2t_ptr[i]; k < v2t_ptr[i + 1]; ++k) {
+        const int32_t t = v2t[k] / 3, a = v2t[k] % 3;
+        const int32_t p0 = adj_ptr[t], L1 = adj_ptr[t + 1] - p0;
+        const int32_t q0 = band_ptr ? band_ptr[t] : 0, L2 = band_ptr ? band_ptr[t + 1] - q0 : 0;
+        const int total = 3 * (L1 + L2);
+        for (int c0 = 0; c0 < total; c0 += 32) {
+            const int c = c0 + lane;
+            if (c < total) {
+                double* my = stage + lane * ROW_STAGE;
+                const int idx = c / 3, b = c - 3 * idx, ab = 3 * a + b;
+                if (idx < L1) {
+                    const int64_t pp = p0 + idx;
+                    const int4 pr = pairs[pp];
+                    const int32_t j = tris[3 * (int64_t)pr.y + b];
+                    spos[lane] = row_lower_bound(scol, n, j);
+                    for (int o = 0; o < 6; ++o) {
+                        const double sv = ss[54 * pp + 9 * o + ab];
+                        my[o] = sv - far[54 * pp + 9 * o + ab];
+                        my[6 + o] = sv;
+                    }
+                    my[12] = pr.z == 0 ? tgeo[16 * (int64_t)pr.x + 3] / 12.0 * ((ab % 4 == 0) ? 2.0 : 1.0) : 0.0;
+                } else {
+                    const int32_t q = q0 + idx - L1;
+                    const int64_t pp = n_adj + q;
+                    const int32_t j = tris[3 * (int64_t)band_s[q] + b];
+                    spos[lane] = row_lower_bound(scol, n, j);
+                    for (int o = 0; o < 6; ++o) {
+                        my[o] = ss[54 * pp + 9 * o + ab];
+                        my[6 + o] = 0.0;  // band pairs never touch the diagonal
+                    }
+                    my[12] = 0.0;
+                }
+            }
+            __syncwarp();
+            // the slots this lane owns, then their values in slot order (lanes in parallel)
+            const int m = min(32, total - c0);
+            unsigned own = 0;
+            for (int sl = 0; sl < m; ++sl)
+                if ((spos[sl] & 31) == lane) own |= 1u << sl;
+            while (own) {
+                const int sl = __ffs(own) - 1;
+                own &= own - 1;
+                const double* st = stage + sl * ROW_STAGE;
+                const int pos = spos[sl];
+                double* e = acc + 7 * (size_t)pos;
+                for (int o = 0; o < 6; ++o) e[o] += st[o];
+                e[6] += st[12];
+                if (pos == diag_pos)
+                    for (int o = 0; o < 6; ++o) dfull[o] += st[6 + o];
+            }
+            __syncwarp();
+        }
+    }
+    const int map[6] = {N_VL, N_KL, N_DL, N_VY, N_KY, N_DY};
+    for (int k = lane; k < n; k += 32) {
+        const double* e = acc + 7 * (size_t)k;
+        for (int o = 0; o < 6; ++o) val[map[o] * nnz + r0 + k] = e[o];
+        val[N_M * nnz + r0 + k] = e[6];
+        if (k == diag_pos) {
+            for (int o = 0; o < 6; ++o) diag[map[o] * nv + i] = dfull[o];
+            diag[N_M * nv + i] = e[6];
+        }
+    }
+}
 
 static void free_near(pb_near* nf) {
     if (nf->val) cudaFree(nf->val);
@@ -425,8 +580,8 @@ static int build(pb_ctx* ctx, const pb_mesh* m, double kappa, pb_near* nf, cudaS
         unsigned bc = (unsigned)((m->n_coin * 32 + threads - 1) / threads);
         unsigned bp = (unsigned)((m->n_prim * 32 + threads - 1) / threads);
         if (bc)
-            k_near_pairs<3, false><<<bc, threads, 0, s>>>(m->verts, m->tris, m->tgeo, m->pairs, m->pair_coin,
-                                                          m->n_coin, m->pair_rev, gq, mesh_rule(m), kappa, ss, far);
+            k_coin_pairs<<<bc, threads, 0, s>>>(m->verts, m->tris, m->tgeo, m->pairs, m->pair_coin, m->n_coin, gq,
+                                                mesh_rule(m), kappa, ss, far);
         ::pb::count_launch();
         if (bp)
             k_near_pairs<2, true><<<bp, threads, 0, s>>>(m->verts, m->tris, m->tgeo, m->pairs, m->pair_prim,
@@ -440,10 +595,22 @@ static int build(pb_ctx* ctx, const pb_mesh* m, double kappa, pb_near* nf, cudaS
             ::pb::count_launch();
         }
         cudaMemsetAsync(nf->diag, 0, sizeof(double) * N_VALS * m->nv, s);
-        k_near_entries<<<(unsigned)((m->nnz + 255) / 256), 256, 0, s>>>(
-            m->nnz, m->nv, m->row_of, m->col, m->v2t_ptr, m->v2t, m->tris, m->adj_ptr, m->pairs,
-            m->n_band ? m->band_ptr : nullptr, m->band_s, m->n_adj, m->tgeo, ss, far, nf->val, nf->diag);
-        ::pb::count_launch();
+        {
+            const size_t per_warp = sizeof(double) * row_warp_doubles(m->max_row);
+            const int warps = (int)std::max<size_t>(1, std::min<size_t>(8, (200u << 10) / per_warp));
+            const size_t sm = per_warp * warps;
+            if (sm > (227u << 10)) {
+                rc = set_error(PB_EINVAL, "near pattern rows too long (%d entries) for one warp's shared memory",
+                               m->max_row);
+            } else {
+                cudaFuncSetAttribute(k_near_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+                k_near_rows<<<(unsigned)((m->nv + warps - 1) / warps), 32 * warps, sm, s>>>(
+                    m->nv, m->nnz, m->max_row, warps, m->row_ptr, m->col, m->v2t_ptr, m->v2t, m->tris, m->adj_ptr,
+                    m->pairs, m->n_band ? m->band_ptr : nullptr, m->band_s, m->n_adj, m->tgeo, ss, far, nf->val,
+                    nf->diag);
+                ::pb::count_launch();
+            }
+        }
         cudaError_t e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         int st = 0;
