@@ -56,10 +56,12 @@ def parse():
     ap.add_argument("--no-baseline", action="store_true")
     ap.add_argument("--no-check", action="store_true", help="skip the FP64 accuracy solve (profiling runs)")
     ap.add_argument("--no-graphs", action="store_true", help="launch GMRES iterations kernel by kernel")
-    ap.add_argument("--plan", default="reference", choices=["reference", "band"],
-                    help="quadrature plan: reference (6-point far rule everywhere) or band (3-point far rule "
-                         "beyond --band-eta radii, 6-point inside)")
+    ap.add_argument("--plan", default="auto", choices=["auto", "reference", "band"],
+                    help="quadrature plan: auto (the plan autotuner's choice within --plan-tol of the reference "
+                         "plan's Delta G, tuned before the timed region), reference (6-point far rule everywhere) "
+                         "or band (3-point far rule beyond --band-eta radii, 6-point inside)")
     ap.add_argument("--band-eta", type=float, default=3.0)
+    ap.add_argument("--plan-tol", type=float, default=1e-6)
     ap.add_argument("--serve", type=int, default=0,
                     help="serving benchmark on the first N requests of the seeded request stream instead")
     ap.add_argument("--rate-scale", type=float, default=0.7,
@@ -228,12 +230,21 @@ def quad_plan(args):
     return {"far_q": 6, "n_ss": 4, "band_eta": 0.0, "band_q": 6}
 
 
-def plan_text(args):
-    if args.plan == "band":
-        return (f"3-point degree-2 rule on pairs farther apart than {args.band_eta:g} times the sum of their radii, "
-                "6-point degree-4 rule inside that band and for the right-hand side and energy, singular 4^4 "
-                "Gauss per region")
-    return "far 6-point degree-4 rule, singular 4^4 Gauss per region"
+def tuned_plan(args, pb, ctx, v, t, xq, q, P, form, prec, opts):
+    """The plan autotuner's choice for this molecule and case (untimed)."""
+    # tighter than the timed solves, so that solver noise stays well below the tolerance
+    topts = pb.solve_opts(tol=1e-8, max_it=600, precision=pb.PB_MIXED, inner_tol=1e-4)
+    (fq, ns, eta, bq), change = pb.pb_autotune_plan(ctx, v, t, xq, q, P, form, prec, tol_dG=args.plan_tol,
+                                                    opts=topts)
+    return {"far_q": fq, "n_ss": ns, "band_eta": eta, "band_q": bq}, change
+
+
+def plan_text(plan):
+    if plan["band_eta"] > 0:
+        return (f"{plan['far_q']}-point rule on pairs farther apart than {plan['band_eta']:g} times the sum of their "
+                f"radii, {plan['band_q']}-point rule inside that band and for the right-hand side and energy, "
+                f"singular {plan['n_ss']}^4 Gauss per region")
+    return f"far {plan['far_q']}-point rule, singular {plan['n_ss']}^4 Gauss per region"
 
 
 def run_ours(args, rank, world, local_rank):
@@ -262,7 +273,9 @@ def run_ours(args, rank, world, local_rank):
         if world > 1:
             dist.barrier()
 
-    plan = quad_plan(args)
+    plan, plan_change = quad_plan(args), None
+    if args.plan == "auto":
+        plan, plan_change = tuned_plan(args, pb, ctx, v, t, xq, q, P, form, prec, opts)
 
     def step():
         m = pb.pb_mesh_load(ctx, dv, dt, **plan)
@@ -382,7 +395,9 @@ def run_ours(args, rank, world, local_rank):
         "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
         "config": {"workload": workload_text(args, v, t, xq),
                    "case": args.case, "formulation": form, "preconditioner": prec, "precision": args.precision,
-                   "gmres_tol": args.tol, "quadrature": plan_text(args),
+                   "gmres_tol": args.tol, "quadrature": plan_text(plan),
+                   "plan": dict(plan, tuned=args.plan == "auto", tol_dG=args.plan_tol if args.plan == "auto" else None,
+                                dG_change_vs_reference_plan=plan_change),
                    "points": npts, "l2": "flushed (256 MB write) before every timed step",
                    "gmres_step": "CUDA graph replay" if not args.no_graphs else "kernel by kernel",
                    "parallelism": "replicas" if world > 1 else "1 GPU"},

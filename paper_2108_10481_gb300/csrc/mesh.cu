@@ -205,6 +205,81 @@ __global__ void k_scan(int64_t n, const int32_t* __restrict__ cnt, int32_t* __re
     }
 }
 
+// ---- near pattern on the device: row i holds every vertex of every triangle
+// paired (adjacent or band) with a triangle at i. One warp per row inserts the
+// candidates into a shared-memory hash set, compacts it, and (pass 1) writes
+// the columns in increasing order (each one's rank among the row's values).
+constexpr int PAT_HASH = 1024;  // hash slots per warp: at most PAT_HASH / 2 columns per row
+constexpr int PAT_WARPS = 4;
+
+__global__ void __launch_bounds__(32 * PAT_WARPS)
+k_row_pattern(int64_t nv, int pass, const int32_t* __restrict__ v2t_ptr, const int32_t* __restrict__ v2t,
+              const int32_t* __restrict__ tris, const int32_t* __restrict__ adj_ptr, const int4* __restrict__ pairs,
+              const int32_t* __restrict__ band_ptr, const int32_t* __restrict__ band_s, int32_t* __restrict__ cnt,
+              int* __restrict__ maxrow, const int32_t* __restrict__ row_ptr, int32_t* __restrict__ col,
+              int* __restrict__ status) {
+    __shared__ int32_t table[PAT_WARPS][PAT_HASH];
+    __shared__ int32_t list[PAT_WARPS][PAT_HASH / 2];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t i = (int64_t)blockIdx.x * PAT_WARPS + w;
+    if (i >= nv) return;  // whole warps
+    int32_t* tb = table[w];
+    int32_t* ls = list[w];
+    for (int k = lane; k < PAT_HASH; k += 32) tb[k] = -1;
+    __syncwarp();
+    bool full = false;
+    for (int32_t k = v2t_ptr[i]; k < v2t_ptr[i + 1]; ++k) {
+        const int32_t t = v2t[k] / 3;
+        const int32_t p0 = adj_ptr[t], L1 = adj_ptr[t + 1] - p0;
+        const int32_t q0 = band_ptr ? band_ptr[t] : 0, L2 = band_ptr ? band_ptr[t + 1] - q0 : 0;
+        const int total = 3 * (L1 + L2);
+        for (int c = lane; c < total; c += 32) {
+            const int idx = c / 3, b = c - 3 * idx;
+            const int32_t sidx = idx < L1 ? pairs[p0 + idx].y : band_s[q0 + idx - L1];
+            const int32_t j = tris[3 * (int64_t)sidx + b];
+            uint32_t h = ((uint32_t)j * 2654435761u) & (PAT_HASH - 1);
+            int probe = 0;
+            for (; probe < PAT_HASH; ++probe) {
+                const int32_t old = atomicCAS(&tb[h], -1, j);
+                if (old == -1 || old == j) break;
+                h = (h + 1) & (PAT_HASH - 1);
+            }
+            full |= probe == PAT_HASH;
+        }
+    }
+    __syncwarp();
+    int n = 0;
+    for (int base = 0; base < PAT_HASH; base += 32) {
+        const int32_t v = tb[base + lane];
+        const unsigned bal = __ballot_sync(0xffffffffu, v >= 0);
+        if (v >= 0) {
+            const int pos = n + __popc(bal & ((1u << lane) - 1));
+            if (pos < PAT_HASH / 2) ls[pos] = v;
+        }
+        n += __popc(bal);
+    }
+    full = __any_sync(0xffffffffu, full) || n > PAT_HASH / 2;
+    if (full) {
+        if (lane == 0) atomicExch(status, PB_EINVAL);
+        return;
+    }
+    if (pass == 0) {
+        if (lane == 0) {
+            cnt[i] = n;
+            atomicMax(maxrow, n);
+        }
+        return;
+    }
+    __syncwarp();
+    const int32_t r0 = row_ptr[i];
+    for (int k = lane; k < n; k += 32) {
+        const int32_t v = ls[k];
+        int rank = 0;
+        for (int q = 0; q < n; ++q) rank += ls[q] < v;
+        col[r0 + rank] = v;
+    }
+}
+
 // transposed positions, diagonal positions and the row of every nonzero
 __global__ void k_pattern_maps(int64_t nv, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                                int32_t* __restrict__ tpos, int32_t* __restrict__ diag_pos, int32_t* __restrict__ row_of,
@@ -477,7 +552,6 @@ static int load(pb_ctx* ctx, const double* verts_in, int64_t nv, const int32_t* 
     // and radii here, with the oracle's arithmetic; a uniform grid of cell size
     // 2 eta max(rho) here; the search on the device (k_band_search), which
     // lists each triangle's partners in increasing order.
-    std::vector<int32_t> band_ptr(nt + 1, 0), band_s;
     m->n_band = 0;
     if (eta > 0.0) {
         std::vector<double> C(3 * nt), R(nt);
@@ -564,14 +638,6 @@ static int load(pb_ctx* ctx, const double* verts_in, int64_t nv, const int32_t* 
             if ((rc = dev_alloc((void**)&m->band_t, sizeof(int32_t) * (total + 1))) != PB_OK) break;
             k_band_search<<<nb, 128>>>(nt, m->tris, g, 1, nullptr, m->band_ptr, m->band_s, m->band_t);
             ::pb::count_launch();
-            band_s.resize(total);
-            if (cudaMemcpy(band_ptr.data(), m->band_ptr, sizeof(int32_t) * (nt + 1), cudaMemcpyDeviceToHost) !=
-                    cudaSuccess ||
-                (total && cudaMemcpy(band_s.data(), m->band_s, sizeof(int32_t) * total, cudaMemcpyDeviceToHost) !=
-                              cudaSuccess)) {
-                rc = set_error(PB_ECUDA, "band search failed");
-                break;
-            }
         } while (false);
         cudaFree(scratch);
         if (rc != PB_OK) return rc;
@@ -579,56 +645,8 @@ static int load(pb_ctx* ctx, const double* verts_in, int64_t nv, const int32_t* 
     }
     m->npairs = n_adj + m->n_band;
 
-    // ---- near pattern: row i holds every vertex of every triangle paired with a
-    // triangle at i (the 2-ring, and the band); counted, then filled and sorted
-    auto row_vertices = [&](int64_t i, std::vector<int32_t>& mark, std::vector<int32_t>& out) {
-        out.clear();
-        for (int32_t k = v2t_ptr[i]; k < v2t_ptr[i + 1]; ++k) {
-            const int32_t t = v2t[k] / 3;
-            for (int32_t p = adj_ptr[t]; p < adj_ptr[t + 1]; ++p) {
-                const int32_t* f = &T[3 * (int64_t)pairs[p].y];
-                for (int b = 0; b < 3; ++b)
-                    if (mark[f[b]] != (int32_t)i) {
-                        mark[f[b]] = (int32_t)i;
-                        out.push_back(f[b]);
-                    }
-            }
-            for (int32_t q = band_ptr[t]; q < band_ptr[t + 1]; ++q) {
-                const int32_t* f = &T[3 * (int64_t)band_s[q]];
-                for (int b = 0; b < 3; ++b)
-                    if (mark[f[b]] != (int32_t)i) {
-                        mark[f[b]] = (int32_t)i;
-                        out.push_back(f[b]);
-                    }
-            }
-        }
-        std::sort(out.begin(), out.end());
-    };
-    std::vector<int64_t> row_cnt(nv + 1, 0);
-    parallel_for(nv, [&](int64_t b0, int64_t b1) {
-        std::vector<int32_t> mark(nv, -1), out;
-        for (int64_t i = b0; i < b1; ++i) {
-            row_vertices(i, mark, out);
-            row_cnt[i + 1] = (int64_t)out.size();
-        }
-    });
-    for (int64_t i = 0; i < nv; ++i) row_cnt[i + 1] += row_cnt[i];
-    if (row_cnt[nv] > ((int64_t)1 << 31) - 1) return set_error(PB_EINVAL, "near pattern too large");
-    const int64_t nnz = row_cnt[nv];
-    m->nnz = nnz;
-    m->max_row = 0;
-    for (int64_t i = 0; i < nv; ++i) m->max_row = std::max(m->max_row, (int)(row_cnt[i + 1] - row_cnt[i]));
-    std::vector<int32_t> row_ptr(nv + 1), col(nnz);
-    for (int64_t i = 0; i <= nv; ++i) row_ptr[i] = (int32_t)row_cnt[i];
-    parallel_for(nv, [&](int64_t b0, int64_t b1) {
-        std::vector<int32_t> mark(nv, -1), out;
-        for (int64_t i = b0; i < b1; ++i) {
-            row_vertices(i, mark, out);
-            std::copy(out.begin(), out.end(), col.begin() + row_ptr[i]);
-        }
-    });
-
-    // ---- upload; transposed and diagonal positions on the device
+    // ---- near pattern (device): counts, row pointers, sorted columns, then the
+    // transposed and diagonal positions
     PB_TRY(upload((void**)&m->v2t_ptr, v2t_ptr.data(), sizeof(int32_t) * (nv + 1), &tot));
     PB_TRY(upload((void**)&m->v2t, v2t.data(), sizeof(int32_t) * 3 * nt, &tot));
     PB_TRY(upload((void**)&m->pairs, pairs.data(), sizeof(int4) * pairs.size(), &tot));
@@ -638,14 +656,56 @@ static int load(pb_ctx* ctx, const double* verts_in, int64_t nv, const int32_t* 
     PB_TRY(upload((void**)&m->pair_prim, prim_list.data(), sizeof(int32_t) * prim_list.size(), &tot));
     m->n_coin = (int64_t)coin_list.size();
     m->n_prim = (int64_t)prim_list.size();
-    PB_TRY(upload((void**)&m->row_ptr, row_ptr.data(), sizeof(int32_t) * (nv + 1), &tot));
-    PB_TRY(upload((void**)&m->col, col.data(), sizeof(int32_t) * nnz, &tot));
+    PB_TRY(dev_alloc((void**)&m->status, sizeof(int)));
+    PB_CUDA(cudaMemset(m->status, 0, sizeof(int)));
+    PB_TRY(dev_alloc((void**)&m->row_ptr, sizeof(int32_t) * (nv + 1)));
+    tot += sizeof(int32_t) * (nv + 1);
+    {
+        int32_t* cntv = nullptr;
+        PB_TRY(dev_alloc((void**)&cntv, sizeof(int32_t) * nv + 64));
+        int64_t* dtot = (int64_t*)(cntv + nv + (nv & 1));
+        int* dmax = (int*)(dtot + 1);
+        int rc = PB_OK;
+        int64_t nnz = 0;
+        int hmax = 0, st = 0;
+        const int32_t* bp = m->n_band ? m->band_ptr : nullptr;
+        const unsigned pb_blocks = (unsigned)((nv + PAT_WARPS - 1) / PAT_WARPS);
+        do {
+            if (cudaMemset(dmax, 0, sizeof(int)) != cudaSuccess) { rc = set_error(PB_ECUDA, "pattern"); break; }
+            k_row_pattern<<<pb_blocks, 32 * PAT_WARPS>>>(nv, 0, m->v2t_ptr, m->v2t, m->tris, m->adj_ptr, m->pairs, bp,
+                                                         m->band_s, cntv, dmax, nullptr, nullptr, m->status);
+            k_scan<<<1, 1024>>>(nv, cntv, m->row_ptr, dtot);
+            ::pb::count_launch(2);
+            if (cudaMemcpy(&nnz, dtot, sizeof(int64_t), cudaMemcpyDeviceToHost) != cudaSuccess ||
+                cudaMemcpy(&hmax, dmax, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
+                cudaMemcpy(&st, m->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+                rc = set_error(PB_ECUDA, "near pattern failed");
+                break;
+            }
+            if (st != 0) {
+                rc = set_error(PB_EINVAL, "near pattern: a row has more than %d columns (distance band too wide)",
+                               PAT_HASH / 2);
+                break;
+            }
+            if (nnz > ((int64_t)1 << 31) - 1) {
+                rc = set_error(PB_EINVAL, "near pattern too large");
+                break;
+            }
+            m->nnz = nnz;
+            m->max_row = hmax;
+            if ((rc = dev_alloc((void**)&m->col, sizeof(int32_t) * (nnz + 1))) != PB_OK) break;
+            k_row_pattern<<<pb_blocks, 32 * PAT_WARPS>>>(nv, 1, m->v2t_ptr, m->v2t, m->tris, m->adj_ptr, m->pairs, bp,
+                                                         m->band_s, nullptr, nullptr, m->row_ptr, m->col, m->status);
+            ::pb::count_launch();
+        } while (false);
+        cudaFree(cntv);
+        if (rc != PB_OK) return rc;
+    }
+    const int64_t nnz = m->nnz;
     PB_TRY(dev_alloc((void**)&m->tpos, sizeof(int32_t) * nnz));
     PB_TRY(dev_alloc((void**)&m->row_of, sizeof(int32_t) * nnz));
     PB_TRY(dev_alloc((void**)&m->diag_pos, sizeof(int32_t) * nv));
-    tot += sizeof(int32_t) * (2 * nnz + nv);
-    PB_TRY(dev_alloc((void**)&m->status, sizeof(int)));
-    PB_CUDA(cudaMemset(m->status, 0, sizeof(int)));
+    tot += sizeof(int32_t) * (3 * nnz + nv);
     k_pattern_maps<<<(unsigned)((nv + 127) / 128), 128>>>(nv, m->row_ptr, m->col, m->tpos, m->diag_pos, m->row_of,
                                                           m->status);
     ::pb::count_launch();
