@@ -33,6 +33,7 @@ METRIC = "PB solves/s and p50/p99 latency at dG rel err <=1e-5; BEM matvec Gpair
 UNIT = "solves/s"
 SM_COUNT_GB300 = 152
 FP32_LANES_PER_SM = 128  # FP32 pipe operations per SM per clock
+FP64_FLOPS_PER_SM = 4    # FP64 flops per SM per clock (two FMA lanes): 152 x 4 x 2.07 GHz = 1.26 TFLOP/s
 L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes per launch of the packed FP32 pair kernel in its V/K + D/T mode, from one ncu capture at 122,880
 # points (dram__bytes_read.sum + dram__bytes_write.sum; profiles/pair32x2_vkdt_multi_charge_sphere.md). Valid only
@@ -224,6 +225,20 @@ def stored_oracle_dG(args):
     return case["dG_kcal"] if case else None
 
 
+def _kernels():
+    import paper_2108_10481_gb300 as pb
+    return {pb.PB_KERNEL_PAIR32: ("k_pair32 (FP32 far field)", "pair32", FP32_LANES_PER_SM, "FP32 ops"),
+            pb.PB_KERNEL_PAIR32_ACCURATE: ("k_pair32 split-coordinate (FP32 far field, FP64 tile sums)", "pair32acc",
+                                           FP32_LANES_PER_SM, "FP32 ops"),
+            pb.PB_KERNEL_PAIR64: ("k_pair64 (FP64 far field)", "pair64", FP64_FLOPS_PER_SM, "FP64 flops"),
+            pb.PB_KERNEL_NEAR_ADJ: ("k_near_pairs (FP64 singular quadrature, edge/vertex pairs)", "near_adj",
+                                    FP64_FLOPS_PER_SM, "FP64 flops"),
+            pb.PB_KERNEL_NEAR_COIN: ("k_coin_pairs (FP64 singular quadrature, coincident pairs)", "near_coin",
+                                     FP64_FLOPS_PER_SM, "FP64 flops"),
+            pb.PB_KERNEL_NEAR_BAND: ("k_band_pairs (FP64 band-rule corrections)", "near_band", FP64_FLOPS_PER_SM,
+                                     "FP64 flops")}
+
+
 def quad_plan(args):
     if args.plan == "band":
         return {"far_q": 3, "n_ss": 4, "band_eta": args.band_eta, "band_q": 6}
@@ -248,11 +263,13 @@ def plan_text(plan):
 
 
 def run_ours(args, rank, world, local_rank):
+    global KERNELS
     import torch
     import torch.distributed as dist
 
     import paper_2108_10481_gb300 as pb
 
+    KERNELS = _kernels()
     dev = torch.device("cuda", local_rank)
     torch.cuda.set_device(dev)
     v, t, xq, q = workload(args.level, args.workload)
@@ -344,8 +361,7 @@ def run_ours(args, rank, world, local_rank):
     clocks = sampler.stop()
     for a, b in ev:
         step_ms.append(a.elapsed_time(b))
-    fam = {k: pb.pb_profile_read(ctx, k) for k in (pb.PB_KERNEL_PAIR32, pb.PB_KERNEL_PAIR32_ACCURATE,
-                                                   pb.PB_KERNEL_PAIR64)}
+    fam = {k: pb.pb_profile_read(ctx, k) for k in KERNELS}
     pb.pb_profile(ctx, False)
     total_ms = cross_rank_max(float(np.sum(step_ms)), world, dev)
 
@@ -371,19 +387,25 @@ def run_ours(args, rank, world, local_rank):
 
     if rank != 0:
         return
-    # roofline of the dominant kernel family (largest device time in the timed region)
-    kid = max(fam, key=lambda k: fam[k]["ms"])
-    st = fam[kid]
-    names = {pb.PB_KERNEL_PAIR32: "k_pair32 (FP32 far field)", pb.PB_KERNEL_PAIR32_ACCURATE:
-             "k_pair32 split-coordinate (FP32 far field, FP64 tile sums)", pb.PB_KERNEL_PAIR64: "k_pair64 (FP64)"}
-    avg_ms = st["ms"] / max(1, st["launches"])
-    ops_per_launch = st["ops"] / max(1, st["launches"])
-    achieved = ops_per_launch / (avg_ms * 1e-3) / 1e12 if avg_ms > 0 else 0.0
+    # roofline of every profiled kernel; the dominant one (largest device time in
+    # the timed region) is the line's "roofline"
     sm_max = clocks.get("sm_max_mhz") or 2070.0
-    peak = SM_COUNT_GB300 * FP32_LANES_PER_SM * sm_max * 1e6 / 1e12
-    fam_key = {pb.PB_KERNEL_PAIR32: "pair32", pb.PB_KERNEL_PAIR32_ACCURATE: "pair32acc",
-               pb.PB_KERNEL_PAIR64: "pair64"}[kid]
-    traffic = NCU_TRAFFIC.get((fam_key, form, npts))
+    rooflines = {}
+    for kid, st in fam.items():
+        if st["launches"] == 0:
+            continue
+        name, key, lanes, unit_ops = KERNELS[kid]
+        avg_ms = st["ms"] / st["launches"]
+        ops_per_launch = st["ops"] / st["launches"]
+        achieved = ops_per_launch / (avg_ms * 1e-3) / 1e12 if avg_ms > 0 else 0.0
+        peak = SM_COUNT_GB300 * lanes * sm_max * 1e6 / 1e12
+        rooflines[key] = {
+            "bound": "alu", "kernel": name, "achieved": achieved, "peak": peak, "unit": "Tops/s",
+            "frac": achieved / peak if peak > 0 else None, "traffic": NCU_TRAFFIC.get((key, form, npts)),
+            "launches": st["launches"], "avg_launch_ms": avg_ms, "total_ms": st["ms"],
+            "ops_per_pair": st["ops"] / max(1.0, st["pairs"]),
+            "peak_basis": "%d SMs x %d %s/clk x %.0f MHz" % (SM_COUNT_GB300, lanes, unit_ops, sm_max)}
+    dominant = max(rooflines, key=lambda k: rooflines[k]["total_ms"])
     lat = np.array(step_ms)
     dG_err = abs(float(np.mean(dGs)) / dG64 - 1.0) if dG64 is not None else None
     dG_orc = stored_oracle_dG(args)
@@ -408,11 +430,8 @@ def run_ours(args, rank, world, local_rank):
         "refinement_sweeps": int(np.median(outer)),
         "matvec": {"gpairs_per_s": npts * npts / (mv_ms * 1e-3) / 1e9, "ms": mv_ms, "points": npts,
                    "tri_pairs_per_s": t.shape[0] ** 2 / (mv_ms * 1e-3), "precision": "f32"},
-        "roofline": {"bound": "alu", "kernel": names[kid], "achieved": achieved, "peak": peak, "unit": "Tops/s",
-                     "frac": achieved / peak if peak > 0 else None, "traffic": traffic,
-                     "launches": st["launches"], "avg_launch_ms": avg_ms,
-                     "ops_per_pair": st["ops"] / max(1.0, st["pairs"]),
-                     "peak_basis": "%d SMs x %d FP32 ops/clk x %.0f MHz" % (SM_COUNT_GB300, FP32_LANES_PER_SM, sm_max)},
+        "roofline": rooflines[dominant],
+        "roofline_by_kernel": rooflines,
         "clocks": clocks, "gpu_launches": int(launches), "wall_s": wall,
     }
     if e2e:

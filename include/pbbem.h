@@ -349,6 +349,15 @@ int pb_autotune_plan(pb_ctx* ctx, const double* verts, int64_t n_verts, const in
 #define PB_KERNEL_PAIR32 0          /* FP32 far-field pair kernel (inner solves) */
 #define PB_KERNEL_PAIR32_ACCURATE 1 /* split-coordinate FP32 pair kernel (outer residuals) */
 #define PB_KERNEL_PAIR64 2          /* FP64 pair kernel */
+#define PB_KERNEL_NEAR_ADJ 3        /* FP64 regularised quadrature of edge- and vertex-adjacent pairs */
+#define PB_KERNEL_NEAR_COIN 4       /* FP64 regularised quadrature of coincident pairs */
+#define PB_KERNEL_NEAR_BAND 5       /* FP64 band-rule minus far-rule blocks of band pairs */
+#define PB_KERNEL_COUNT 6
+/* For the pair kernels, "pairs" are target-source point pairs and "ops" FP32
+ * (FP64 for PB_KERNEL_PAIR64) operations by the kernel's formula count; for
+ * the near-field kernels, "pairs" are quadrature point pairs (kernel
+ * evaluations) and "ops" FP64 flops by formula count (kernel evaluation and
+ * accumulation into the local blocks, a fused multiply-add counted as two). */
 /* enable (1) or disable (0) per-launch CUDA-event timing of the pair kernels
  * on their launching stream; either call resets the statistics. No effect on
  * results. */

@@ -7,7 +7,8 @@ from .api import (CASES, FORMS, PB_F32, PB_F32_ACCURATE, PB_F64, PB_LAPLACE, PB_
                   PB_OP_M, PB_OP_T, PB_OP_V, PB_YUKAWA, PRECONDS, Params, PBError, pb_energy, pb_init,
                   pb_mesh_load, pb_near_build, pb_op_apply, pb_rhs_charges, pb_solvation_energy, pb_solve,
                   pb_system_apply, pb_system_apply_noalloc, pb_version, solve_opts, pb_profile, pb_profile_read, pb_launch_count,
-                  PB_KERNEL_PAIR32, PB_KERNEL_PAIR32_ACCURATE, PB_KERNEL_PAIR64, pb_server_create, pb_submit,
+                  PB_KERNEL_PAIR32, PB_KERNEL_PAIR32_ACCURATE, PB_KERNEL_PAIR64, PB_KERNEL_NEAR_ADJ,
+                  PB_KERNEL_NEAR_COIN, PB_KERNEL_NEAR_BAND, pb_server_create, pb_submit,
                   pb_server_step, pb_poll, pb_autotune, pb_autotune_plan, pb_selftest_wait, pb_set_graphs)
 
 __all__ = ["CASES", "FORMS", "PRECONDS", "Params", "PBError", "PB_F32", "PB_F32_ACCURATE", "PB_F64",
@@ -15,5 +16,6 @@ __all__ = ["CASES", "FORMS", "PRECONDS", "Params", "PBError", "PB_F32", "PB_F32_
            "pb_energy", "pb_init", "pb_mesh_load", "pb_near_build", "pb_op_apply", "pb_rhs_charges",
            "pb_solvation_energy", "pb_solve", "pb_system_apply", "pb_system_apply_noalloc", "pb_version", "solve_opts", "pb_profile",
            "pb_profile_read", "pb_launch_count", "PB_KERNEL_PAIR32", "PB_KERNEL_PAIR32_ACCURATE", "PB_KERNEL_PAIR64",
+           "PB_KERNEL_NEAR_ADJ", "PB_KERNEL_NEAR_COIN", "PB_KERNEL_NEAR_BAND",
            "pb_server_create", "pb_submit", "pb_server_step", "pb_poll", "pb_autotune", "pb_autotune_plan",
            "pb_selftest_wait", "pb_set_graphs"]

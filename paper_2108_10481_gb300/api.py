@@ -116,6 +116,7 @@ class Near(_Handle):
 
 
 PB_KERNEL_PAIR32, PB_KERNEL_PAIR32_ACCURATE, PB_KERNEL_PAIR64 = 0, 1, 2
+PB_KERNEL_NEAR_ADJ, PB_KERNEL_NEAR_COIN, PB_KERNEL_NEAR_BAND = 3, 4, 5
 
 
 def pb_profile(ctx: Ctx, enable: bool = True):

@@ -190,7 +190,7 @@ extern "C" int pb_profile(pb_ctx* ctx, int enable) {
 
 extern "C" int pb_profile_read(pb_ctx* ctx, int kernel, int64_t* launches, double* total_ms, double* pairs,
                                double* ops) {
-    if (!ctx || kernel < 0 || kernel > 2) return set_error(PB_EINVAL, "pb_profile_read: bad argument");
+    if (!ctx || kernel < 0 || kernel >= PB_KERNEL_COUNT) return set_error(PB_EINVAL, "pb_profile_read: bad argument");
     KernelStats& st = ctx->stats[kernel];
     for (auto& e : st.events) {
         float ms = 0.0f;

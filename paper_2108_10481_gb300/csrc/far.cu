@@ -885,39 +885,6 @@ static int make_tmap(const pb_mesh* m, const float* rec, CUtensorMap* map, int r
 // shared geometry 17, a phi-row 4, a DT-row 15, split coordinates +6.
 constexpr double OPS_VK2 = 25.0, OPS_VKDT = 36.0, OPS_SPLIT = 6.0;
 
-// CUDA events around one launch on its stream, when the context profiles.
-struct Timer {
-    pb_ctx* ctx;
-    int id;
-    cudaStream_t s;
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    double pairs, ops;
-    Timer(pb_ctx* c, int k, cudaStream_t st, double p, double o) : ctx(c), id(k), s(st), pairs(p), ops(o) {
-        if (ctx->profile && cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess)
-            record(e0);
-    }
-    // inside a stream capture an event record becomes a graph node only when
-    // marked external (otherwise it only orders the captured work)
-    void record(cudaEvent_t e) {
-        if (capturing()) cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
-        else cudaEventRecord(e, s);
-    }
-    void stop() {
-        if (!e1) return;
-        record(e1);
-        if (StepGraph* g = capturing()) {  // recorded again by every replay
-            g->timers.push_back({id, e0, e1, pairs, ops});
-            e0 = e1 = nullptr;
-            return;
-        }
-        KernelStats& st = ctx->stats[id];
-        st.events.push_back({e0, e1});
-        st.launches += 1;
-        st.pairs += pairs;
-        st.ops += pairs * ops;
-        e0 = e1 = nullptr;
-    }
-};
 
 
 int apply_blockop(const pb_mesh* m, const pb_near* nf, const BlockOp& B, int prec, const double* x, double* y,

@@ -121,7 +121,7 @@ struct pb_ctx {
     int profile = 0;
     int pair_kernel = 2;  // FP32 far-field kernel: 2 = packed f32x2 (default), 1 = scalar
     pb::TuneEntry tune[2][2][pb::TUNE_BUCKETS];  // [mode][accurate][bucket]
-    pb::KernelStats stats[3];
+    pb::KernelStats stats[PB_KERNEL_COUNT];
     int device = 0;
     int num_sms = 0;
     int cc_major = 0, cc_minor = 0;
@@ -159,7 +159,7 @@ struct pb_mesh {
     int32_t* pair_rev = nullptr;   // index of the reversed pair (tj, ti)
     int32_t* pair_coin = nullptr;  // coincident pairs
     int32_t* pair_prim = nullptr;  // adjacent pairs with ti < tj (each also gives its reverse)
-    int64_t n_coin = 0, n_prim = 0;
+    int64_t n_coin = 0, n_prim = 0, n_prim_edge = 0;  // (the rest of n_prim share one vertex)
     // band pairs (no shared vertex, within the plan's band), ordered by (ti, tj):
     // band pair q is (band_t[q], band_s[q]); triangle t's are band_ptr[t]..band_ptr[t+1]
     int64_t n_band = 0;
@@ -185,6 +185,10 @@ struct pb_near {
     double kappa = 0.0;
     double* val = nullptr;   // N_VALS x nnz (near part = regularised - far rule; M exact)
     double* diag = nullptr;  // N_VALS x nv: full operator diagonals
+    // the mass matrix alone on its own pattern (vertices sharing a triangle)
+    int32_t* mrow_ptr = nullptr;  // nv + 1
+    int32_t* mcol = nullptr;
+    double* mval = nullptr;
 };
 
 namespace pb {
@@ -208,6 +212,9 @@ inline Rule mesh_ref_rule(const pb_mesh* m) {
     r.Q = m->Qr;
     return r;
 }
+
+// exclusive scan of n counts into ptr[0..n] on stream s; *total (device) = the sum
+int device_scan(int64_t n, const int32_t* cnt, int32_t* ptr, int64_t* total, cudaStream_t s);
 
 // device allocation helpers (track bytes on the mesh)
 int dev_alloc(void** p, size_t bytes);
@@ -251,5 +258,39 @@ int tune_bucket(int64_t np);
 // Chebyshev solve with the mass matrix: y = M^-1 x on both halves of a 2 nv vector
 int mass_solve(const pb_mesh* m, const pb_near* nf, const double* x, double* y, double* work,
                int iters, cudaStream_t s);
+
+// CUDA events around one launch on its stream, when the context profiles.
+struct Timer {
+    pb_ctx* ctx;
+    int id;
+    cudaStream_t s;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    double pairs, ops;
+    Timer(pb_ctx* c, int k, cudaStream_t st, double p, double o) : ctx(c), id(k), s(st), pairs(p), ops(o) {
+        if (ctx->profile && cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess)
+            record(e0);
+    }
+    // inside a stream capture an event record becomes a graph node only when
+    // marked external (otherwise it only orders the captured work)
+    void record(cudaEvent_t e) {
+        if (capturing()) cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+        else cudaEventRecord(e, s);
+    }
+    void stop() {
+        if (!e1) return;
+        record(e1);
+        if (StepGraph* g = capturing()) {  // recorded again by every replay
+            g->timers.push_back({id, e0, e1, pairs, ops});
+            e0 = e1 = nullptr;
+            return;
+        }
+        KernelStats& st = ctx->stats[id];
+        st.events.push_back({e0, e1});
+        st.launches += 1;
+        st.pairs += pairs;
+        st.ops += pairs * ops;
+        e0 = e1 = nullptr;
+    }
+};
 
 }  // namespace pb

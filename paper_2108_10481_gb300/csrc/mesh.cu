@@ -280,6 +280,13 @@ k_row_pattern(int64_t nv, int pass, const int32_t* __restrict__ v2t_ptr, const i
     }
 }
 
+int device_scan(int64_t n, const int32_t* cnt, int32_t* ptr, int64_t* total, cudaStream_t s) {
+    k_scan<<<1, 1024, 0, s>>>(n, cnt, ptr, total);
+    ::pb::count_launch();
+    PB_CUDA(cudaGetLastError());
+    return PB_OK;
+}
+
 // transposed positions, diagonal positions and the row of every nonzero
 __global__ void k_pattern_maps(int64_t nv, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                                int32_t* __restrict__ tpos, int32_t* __restrict__ diag_pos, int32_t* __restrict__ row_of,
@@ -540,7 +547,10 @@ static int load(pb_ctx* ctx, const double* verts_in, int64_t nv, const int32_t* 
     for (int64_t p = 0; p < n_adj; ++p) {
         const int32_t t = pairs[p].x, u = pairs[p].y;
         if (t == u) coin_list.push_back((int32_t)p);
-        else if (t < u) prim_list.push_back((int32_t)p);
+        else if (t < u) {
+            prim_list.push_back((int32_t)p);
+            m->n_prim_edge += pairs[p].z == 1;
+        }
     }
 
     size_t tot = 0;

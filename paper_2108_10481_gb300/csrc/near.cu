@@ -222,6 +222,16 @@ __device__ void expand_blocks(const double* acc, const TriFrame& A, const TriFra
 
 constexpr int NEAR_THREADS = 128;
 
+// FP64 flops per quadrature point pair by formula count (a fused multiply-add
+// counted as two). Kernel evaluation (difference, r^2, rsqrt, r, 1/(4 pi r),
+// exp(-kappa r), Yukawa factor, 1/r^3, (1 + kappa r), d.n_y, both double
+// layers): 24; with the reversed pair's double layer (d.n_x and its two
+// kernels): 33. Accumulation: w l_a (3), l_a l_b (9), one FMA per block entry
+// and per sum w G: 4 x 9 + 2 FMA (88 in all), 6 x 9 + 2 (124). Coincident
+// pairs: evaluation 15 (no double layer), accumulation 3 + 9 + 2 x 20 = 52.
+constexpr double NEAR_FLOPS_SYM = 33 + 124;
+constexpr double NEAR_FLOPS_COIN = 15 + 52;
+
 // One warp per listed pair. Writes ss[p][54] (regularised) and far[p][54] (far
 // rule, identical points excluded); with SYM also the blocks of the reversed
 // pair rev[p], whose rule is this one with the roles exchanged.
@@ -559,10 +569,33 @@ __global__ void k_near_rows(int64_t nv, int64_t nnz, int maxrow, int warps, cons
     }
 }
 
+// The mass matrix on its own pattern: the entries of each row whose mass value
+// is not zero (exactly the vertices sharing a triangle with the row's).
+__global__ void k_mass_rows(int64_t nv, int64_t nnz, int pass, const int32_t* __restrict__ row_ptr,
+                            const int32_t* __restrict__ col, const double* __restrict__ val,
+                            int32_t* __restrict__ cnt, const int32_t* __restrict__ mrow_ptr,
+                            int32_t* __restrict__ mcol, double* __restrict__ mval) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nv) return;
+    const double* mv = val + N_M * nnz;
+    int n = 0;
+    for (int32_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+        if (mv[k] == 0.0) continue;
+        if (pass) {
+            mcol[mrow_ptr[i] + n] = col[k];
+            mval[mrow_ptr[i] + n] = mv[k];
+        }
+        ++n;
+    }
+    if (!pass) cnt[i] = n;
+}
+
 static void free_near(pb_near* nf) {
     if (nf->val) cudaFree(nf->val);
     if (nf->diag) cudaFree(nf->diag);
+    if (nf->mrow_ptr) cudaFree(nf->mrow_ptr);
     nf->val = nf->diag = nullptr;
+    nf->mrow_ptr = nullptr;
 }
 
 static int build(pb_ctx* ctx, const pb_mesh* m, double kappa, pb_near* nf, cudaStream_t s) {
@@ -579,19 +612,32 @@ static int build(pb_ctx* ctx, const pb_mesh* m, double kappa, pb_near* nf, cudaS
         // coincident pairs, then one of each pair of reversed pairs (which also writes the other)
         unsigned bc = (unsigned)((m->n_coin * 32 + threads - 1) / threads);
         unsigned bp = (unsigned)((m->n_prim * 32 + threads - 1) / threads);
-        if (bc)
+        // quadrature point pairs of each kernel, for the profile (formula flop counts per pair in
+        // NEAR_FLOPS_*: kernel evaluation and accumulation, a fused multiply-add counted as two)
+        const double n4 = (double)m->n_ss * m->n_ss * m->n_ss * m->n_ss, Q = m->Q, Qb = m->Qr;
+        if (bc) {
+            Timer tm(ctx, PB_KERNEL_NEAR_COIN, s, m->n_coin * (3.0 * n4 + Q * (Q - 1) / 2), NEAR_FLOPS_COIN);
             k_coin_pairs<<<bc, threads, 0, s>>>(m->verts, m->tris, m->tgeo, m->pairs, m->pair_coin, m->n_coin, gq,
                                                 mesh_rule(m), kappa, ss, far);
+            tm.stop();
+        }
         ::pb::count_launch();
-        if (bp)
+        if (bp) {
+            const double evals = m->n_prim_edge * (6.0 * n4) + (m->n_prim - m->n_prim_edge) * (2.0 * n4) +
+                                 m->n_prim * Q * Q;
+            Timer tm(ctx, PB_KERNEL_NEAR_ADJ, s, evals, NEAR_FLOPS_SYM);
             k_near_pairs<2, true><<<bp, threads, 0, s>>>(m->verts, m->tris, m->tgeo, m->pairs, m->pair_prim,
                                                          m->n_prim, m->pair_rev, gq, mesh_rule(m), kappa, ss, far);
+            tm.stop();
+        }
         ::pb::count_launch();
         if (m->n_band) {
             Rule fine = mesh_ref_rule(m), coarse = mesh_rule(m);
+            Timer tm(ctx, PB_KERNEL_NEAR_BAND, s, 0.5 * m->n_band * (Qb * Qb + Q * Q), NEAR_FLOPS_SYM);
             k_band_pairs<<<(unsigned)((m->n_band + BAND_THREADS - 1) / BAND_THREADS), BAND_THREADS, 0, s>>>(
                 m->verts, m->tris, m->tgeo, m->band_ptr, m->band_s, m->band_t, m->n_band, m->n_adj, fine, coarse,
                 kappa, ss, m->status);
+            tm.stop();
             ::pb::count_launch();
         }
         cudaMemsetAsync(nf->diag, 0, sizeof(double) * N_VALS * m->nv, s);
@@ -608,6 +654,26 @@ static int build(pb_ctx* ctx, const pb_mesh* m, double kappa, pb_near* nf, cudaS
                     m->nv, m->nnz, m->max_row, warps, m->row_ptr, m->col, m->v2t_ptr, m->v2t, m->tris, m->adj_ptr,
                     m->pairs, m->n_band ? m->band_ptr : nullptr, m->band_s, m->n_adj, m->tgeo, ss, far, nf->val,
                     nf->diag);
+                ::pb::count_launch();
+            }
+        }
+        // the mass matrix on its own pattern (one allocation: pointers, columns, values)
+        if (rc == PB_OK) {
+            const int64_t nv = m->nv, cap = m->nnz;
+            const size_t bytes = sizeof(int32_t) * (2 * (nv + 1) + cap) + sizeof(double) * (cap + 2) + 64;
+            rc = dev_alloc((void**)&nf->mrow_ptr, bytes);
+            if (rc == PB_OK) {
+                int32_t* cnt = nf->mrow_ptr + (nv + 1);
+                nf->mcol = cnt + (nv + 1);
+                int64_t* total = (int64_t*)(((uintptr_t)(nf->mcol + cap) + 15) & ~(uintptr_t)15);
+                nf->mval = (double*)(total + 1);
+                const unsigned nb = (unsigned)((nv + 127) / 128);
+                k_mass_rows<<<nb, 128, 0, s>>>(nv, m->nnz, 0, m->row_ptr, m->col, nf->val, cnt, nullptr, nullptr,
+                                               nullptr);
+                ::pb::count_launch();
+                rc = device_scan(nv, cnt, nf->mrow_ptr, total, s);
+                k_mass_rows<<<nb, 128, 0, s>>>(nv, m->nnz, 1, m->row_ptr, m->col, nf->val, nullptr, nf->mrow_ptr,
+                                               nf->mcol, nf->mval);
                 ::pb::count_launch();
             }
         }

@@ -114,14 +114,14 @@ int mass_solve(const pb_mesh* m, const pb_near* nf, const double* b, double* x, 
     double* d0 = work + n2;
     double* d1 = work + 2 * n2;
     const double theta = 0.5 * (CH_HI + CH_LO), delta = 0.5 * (CH_HI - CH_LO), sigma = theta / delta;
-    const double* mval = nf->val + N_M * m->nnz;
+    const double* mval = nf->mval;  // the mass matrix on its own pattern
     const double* mdiag = nf->diag + N_M * nv;
     unsigned blocks = (unsigned)((n2 + 255) / 256);
     k_cheb_init<<<blocks, 256, 0, s>>>(nv, mdiag, b, x, r, d0, theta); ::pb::count_launch();
     double rho = 1.0 / sigma;
     for (int k = 0; k < iters; ++k) {
         double rho_n = 1.0 / (2.0 * sigma - rho);
-        k_cheb_step<<<blocks, 256, 0, s>>>(nv, m->row_ptr, m->col, mval, mdiag, d0, d1, x, r, rho_n * rho,
+        k_cheb_step<<<blocks, 256, 0, s>>>(nv, nf->mrow_ptr, nf->mcol, mval, mdiag, d0, d1, x, r, rho_n * rho,
                                            2.0 * rho_n / delta); ::pb::count_launch();
         rho = rho_n;
         double* t = d0;

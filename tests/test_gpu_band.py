@@ -143,6 +143,23 @@ def test_band_solve_matches_oracle_lu(pb, ctx, case):
     assert abs(dG2 / dG - 1) < 1e-5
 
 
+def test_near_kernels_are_profiled(pb, ctx):
+    """The near-field kernels report one timed launch each per build, with their point-pair counts."""
+    v, t, _, _ = mesh_case("uv")
+    m = pb.pb_mesh_load(ctx, v, t, far_q=3, n_ss=4, band_eta=2.5, band_q=6)
+    pb.pb_profile(ctx, True)
+    nf = pb.pb_near_build(ctx, m, PHYS.kappa)
+    stats = {k: pb.pb_profile_read(ctx, k) for k in (pb.PB_KERNEL_NEAR_ADJ, pb.PB_KERNEL_NEAR_COIN,
+                                                      pb.PB_KERNEL_NEAR_BAND)}
+    pb.pb_profile(ctx, False)
+    info = m.info()
+    for k, st in stats.items():
+        assert st["launches"] == 1 and st["ms"] > 0 and st["pairs"] > 0 and st["ops"] > st["pairs"], (k, st)
+    # coincident pairs: one per triangle, 3 regions of 4^4 points and 15 far-rule pairs (3-point rule: 3)
+    assert stats[pb.PB_KERNEL_NEAR_COIN]["pairs"] == info["n_tris"] * (3 * 256 + 3)
+    del nf
+
+
 def test_band_plan_errors(pb, ctx):
     v, t, _, _ = mesh_case("ico2")
     for bad in [dict(far_q=6, band_eta=2.0, band_q=6), dict(far_q=3, band_eta=-1.0), dict(far_q=3, band_eta=2.0,
