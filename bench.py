@@ -38,7 +38,12 @@ L2_FLUSH_BYTES = 256 << 20
 # DRAM bytes per launch of the packed FP32 pair kernel in its V/K + D/T mode, from one ncu capture at 122,880
 # points (dram__bytes_read.sum + dram__bytes_write.sum; profiles/pair32x2_vkdt_multi_charge_sphere.md). Valid only
 # for that kernel as captured; any other dominant kernel reports null.
-NCU_TRAFFIC = {("pair32", "juffer", 122880): 17.72e6}
+NCU_TRAFFIC = {  # (kernel family, formulation or "any", far-rule points, band) -> dram read + write per launch
+    ("pair32", "juffer", 122880, 0.0): 17.72e6,
+    ("near_adj", "any", 61440, 3.0): 170.35e6,
+    ("near_coin", "any", 61440, 3.0): 7.56e6,
+    ("near_band", "any", 61440, 3.0): 692.15e6,
+}
 
 
 def parse():
@@ -401,7 +406,8 @@ def run_ours(args, rank, world, local_rank):
         peak = SM_COUNT_GB300 * lanes * sm_max * 1e6 / 1e12
         rooflines[key] = {
             "bound": "alu", "kernel": name, "achieved": achieved, "peak": peak, "unit": "Tops/s",
-            "frac": achieved / peak if peak > 0 else None, "traffic": NCU_TRAFFIC.get((key, form, npts)),
+            "frac": achieved / peak if peak > 0 else None,
+            "traffic": NCU_TRAFFIC.get((key, "any" if key.startswith("near") else form, npts, plan["band_eta"])),
             "launches": st["launches"], "avg_launch_ms": avg_ms, "total_ms": st["ms"],
             "ops_per_pair": st["ops"] / max(1.0, st["pairs"]),
             "peak_basis": "%d SMs x %d %s/clk x %.0f MHz" % (SM_COUNT_GB300, lanes, unit_ops, sm_max)}
