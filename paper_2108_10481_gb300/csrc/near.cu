@@ -106,6 +106,42 @@ __device__ __forceinline__ double ss_map(int kind, int reg, double xi, double e1
     return jac;
 }
 
+// The regularised rule does not depend on the pair: every (region, Gauss
+// index) point of each kind, its reference points in both triangles and its
+// weight (Gauss weights times the region Jacobian, multiplied in the order the
+// pair kernels used to), computed once per build. Structure of arrays over
+// the entries of kind 1 (edge, 6 regions), kind 2 (vertex, 2) and kind 0
+// (coincident, regions 0..2), in that order.
+struct SSTable {
+    const double* sx;
+    const double* tx;
+    const double* sy;
+    const double* ty;
+    const double* w;
+    int off[3];  // first entry of kind 0, 1, 2
+    int n;       // entries in all
+};
+
+__global__ void k_ss_table(Gauss gq, int n, double* __restrict__ tab) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    const int q = gq.n, n4 = q * q * q * q;
+    // kind 1: entries [0, 6 n4); kind 2: [6 n4, 8 n4); kind 0: [8 n4, 11 n4)
+    int kind, idx;
+    if (e < 6 * n4) { kind = 1; idx = e; }
+    else if (e < 8 * n4) { kind = 2; idx = e - 6 * n4; }
+    else { kind = 0; idx = e - 8 * n4; }
+    const int reg = idx / n4, r = idx - reg * n4;
+    const int i0 = r / (q * q * q), i1 = (r / (q * q)) % q, i2 = (r / q) % q, i3 = r % q;
+    double sx, tx, sy, ty;
+    const double jac = ss_map(kind, reg, gq.x[i0], gq.x[i1], gq.x[i2], gq.x[i3], sx, tx, sy, ty);
+    tab[e] = sx;
+    tab[n + e] = tx;
+    tab[2 * n + e] = sy;
+    tab[3 * n + e] = ty;
+    tab[4 * n + e] = gq.w[i0] * gq.w[i1] * gq.w[i2] * gq.w[i3] * jac;
+}
+
 // Geometry of one triangle in the reordered frame of its singular map:
 // Q0, E1 = Q1 - Q0, E2 = Q2 - Q1 (x(s,t) = Q0 + s E1 + t E2), the inverse
 // permutation (original corner -> reordered), normal and area. Kept in shared
@@ -239,8 +275,8 @@ template <int MINB, bool SYM>
 __global__ void __launch_bounds__(NEAR_THREADS, MINB)
 k_near_pairs(const double* __restrict__ verts, const int32_t* __restrict__ tris, const double* __restrict__ tgeo,
              const int4* __restrict__ pairs, const int32_t* __restrict__ list, int64_t nlist,
-             const int32_t* __restrict__ rev, Gauss gq, Rule rule, double kappa, double* __restrict__ ss_out,
-             double* __restrict__ far_out) {
+             const int32_t* __restrict__ rev, SSTable tab, int n4, Rule rule, double kappa,
+             double* __restrict__ ss_out, double* __restrict__ far_out) {
     constexpr int NA = SYM ? NACC_SYM : NACC_NEAR;
     __shared__ TriFrame frames[NEAR_THREADS / 32][2];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -255,21 +291,16 @@ k_near_pairs(const double* __restrict__ verts, const int32_t* __restrict__ tris,
     __syncwarp();
     const int kind = pr.z;
     const int nreg = kind == 2 ? 2 : 6;
-    const int n = gq.n;
-    const int n2 = n * n, n4 = n2 * n2;
+    const int e0 = tab.off[kind];
     const double jac_ab = (2.0 * A.area) * (2.0 * B.area);
     double acc[NA];
     for (int k = 0; k < NA; ++k) acc[k] = 0.0;
     for (int idx = lane; idx < nreg * n4; idx += 32) {
-        const int reg = idx / n4;
-        const int r = idx - reg * n4;
-        const int i0 = r / (n2 * n), i1 = (r / n2) % n, i2 = (r / n) % n, i3 = r % n;
-        double sx, tx, sy, ty;
-        const double jac = ss_map(kind, reg, gq.x[i0], gq.x[i1], gq.x[i2], gq.x[i3], sx, tx, sy, ty);
-        const double w = gq.w[i0] * gq.w[i1] * gq.w[i2] * gq.w[i3] * jac * jac_ab;
+        const int e = e0 + idx;
+        const double w = tab.w[e] * jac_ab;
         double x[3], y[3], lx[3], ly[3];
-        frame_point(A, sx, tx, x, lx);
-        frame_point(B, sy, ty, y, ly);
+        frame_point(A, tab.sx[e], tab.tx[e], x, lx);
+        frame_point(B, tab.sy[e], tab.ty[e], y, ly);
         accum_point<SYM>(acc, w, x, y, A.n, B.n, lx, ly, kappa);
     }
     for (int k = 0; k < NA; ++k) acc[k] = warp_sum(acc[k]);
@@ -342,8 +373,8 @@ __device__ void expand_coin(const double* acc, const TriFrame& A, const double* 
 
 __global__ void __launch_bounds__(NEAR_THREADS, 4)
 k_coin_pairs(const double* __restrict__ verts, const int32_t* __restrict__ tris, const double* __restrict__ tgeo,
-             const int4* __restrict__ pairs, const int32_t* __restrict__ list, int64_t nlist, Gauss gq, Rule rule,
-             double kappa, double* __restrict__ ss_out, double* __restrict__ far_out) {
+             const int4* __restrict__ pairs, const int32_t* __restrict__ list, int64_t nlist, SSTable tab, int n4,
+             Rule rule, double kappa, double* __restrict__ ss_out, double* __restrict__ far_out) {
     __shared__ TriFrame frames[NEAR_THREADS / 32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t li = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -353,21 +384,16 @@ k_coin_pairs(const double* __restrict__ verts, const int32_t* __restrict__ tris,
     TriFrame& A = frames[wid];
     if (lane == 0) make_frame(verts, tris, tgeo, pr.x, pr.w & 63, A);
     __syncwarp();
-    const int n = gq.n;
-    const int n2 = n * n, n4 = n2 * n2;
+    const int e0 = tab.off[0];
     const double jac_ab = (2.0 * A.area) * (2.0 * A.area);
     double acc[20];
     for (int k = 0; k < 20; ++k) acc[k] = 0.0;
     for (int idx = lane; idx < 3 * n4; idx += 32) {
-        const int reg = idx / n4;
-        const int r = idx - reg * n4;
-        const int i0 = r / (n2 * n), i1 = (r / n2) % n, i2 = (r / n) % n, i3 = r % n;
-        double sx, tx, sy, ty;
-        const double jac = ss_map(0, reg, gq.x[i0], gq.x[i1], gq.x[i2], gq.x[i3], sx, tx, sy, ty);
-        const double w = gq.w[i0] * gq.w[i1] * gq.w[i2] * gq.w[i3] * jac * jac_ab;
+        const int e = e0 + idx;
+        const double w = tab.w[e] * jac_ab;
         double x[3], y[3], lx[3], ly[3];
-        frame_point(A, sx, tx, x, lx);
-        frame_point(A, sy, ty, y, ly);
+        frame_point(A, tab.sx[e], tab.tx[e], x, lx);
+        frame_point(A, tab.sy[e], tab.ty[e], y, ly);
         accum_v(acc, w, x, y, lx, ly, kappa);
     }
     for (int k = 0; k < 20; ++k) acc[k] = warp_sum(acc[k]);
@@ -608,6 +634,18 @@ static int build(pb_ctx* ctx, const pb_mesh* m, double kappa, pb_near* nf, cudaS
     if (rc == PB_OK) rc = dev_alloc((void**)&far, sizeof(double) * 54 * m->n_adj);
     if (rc == PB_OK) {
         Gauss gq = gauss01(m->n_ss);
+        const int n4i = m->n_ss * m->n_ss * m->n_ss * m->n_ss, ntab = 11 * n4i;
+        double* tabm = nullptr;
+        rc = dev_alloc((void**)&tabm, sizeof(double) * 5 * ntab);
+        if (rc != PB_OK) {
+            cudaFree(ss);
+            cudaFree(far);
+            return rc;
+        }
+        k_ss_table<<<(ntab + 127) / 128, 128, 0, s>>>(gq, ntab, tabm);
+        ::pb::count_launch();
+        SSTable tab = {tabm, tabm + ntab, tabm + 2 * ntab, tabm + 3 * ntab, tabm + 4 * ntab,
+                       {8 * n4i, 0, 6 * n4i}, ntab};
         int threads = NEAR_THREADS;  // one warp per pair
         // coincident pairs, then one of each pair of reversed pairs (which also writes the other)
         unsigned bc = (unsigned)((m->n_coin * 32 + threads - 1) / threads);
@@ -617,8 +655,8 @@ static int build(pb_ctx* ctx, const pb_mesh* m, double kappa, pb_near* nf, cudaS
         const double n4 = (double)m->n_ss * m->n_ss * m->n_ss * m->n_ss, Q = m->Q, Qb = m->Qr;
         if (bc) {
             Timer tm(ctx, PB_KERNEL_NEAR_COIN, s, m->n_coin * (3.0 * n4 + Q * (Q - 1) / 2), NEAR_FLOPS_COIN);
-            k_coin_pairs<<<bc, threads, 0, s>>>(m->verts, m->tris, m->tgeo, m->pairs, m->pair_coin, m->n_coin, gq,
-                                                mesh_rule(m), kappa, ss, far);
+            k_coin_pairs<<<bc, threads, 0, s>>>(m->verts, m->tris, m->tgeo, m->pairs, m->pair_coin, m->n_coin, tab,
+                                                n4i, mesh_rule(m), kappa, ss, far);
             tm.stop();
         }
         ::pb::count_launch();
@@ -627,7 +665,8 @@ static int build(pb_ctx* ctx, const pb_mesh* m, double kappa, pb_near* nf, cudaS
                                  m->n_prim * Q * Q;
             Timer tm(ctx, PB_KERNEL_NEAR_ADJ, s, evals, NEAR_FLOPS_SYM);
             k_near_pairs<2, true><<<bp, threads, 0, s>>>(m->verts, m->tris, m->tgeo, m->pairs, m->pair_prim,
-                                                         m->n_prim, m->pair_rev, gq, mesh_rule(m), kappa, ss, far);
+                                                         m->n_prim, m->pair_rev, tab, n4i, mesh_rule(m), kappa, ss,
+                                                         far);
             tm.stop();
         }
         ::pb::count_launch();
@@ -683,6 +722,7 @@ static int build(pb_ctx* ctx, const pb_mesh* m, double kappa, pb_near* nf, cudaS
         if (e == cudaSuccess && m->n_band) e = cudaMemcpy(&st, m->status, sizeof(int), cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) rc = set_error(PB_ECUDA, "near build: %s", cudaGetErrorString(e));
         else if (st == PB_EMESH) rc = set_error(PB_EMESH, "internal: band pair without reverse");
+        cudaFree(tabm);
     }
     if (ss) cudaFree(ss);
     if (far) cudaFree(far);
