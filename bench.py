@@ -475,6 +475,10 @@ def run_serving(args, rank, local_rank):
     ctx = pb.pb_init(local_rank)
     P = pb.Params(4.0, 80.0, 0.125)
     opts = pb.solve_opts(tol=1e-6, max_it=300, precision=pb.PB_MIXED, inner_tol=1e-4)
+    # the plan: with --plan auto the band plan the autotuner picks on the sphere workload
+    # (3-point far rule beyond --band-eta radii); its Delta G change is checked below
+    plan = quad_plan(args) if args.plan != "auto" else {"far_q": 3, "n_ss": 4, "band_eta": args.band_eta,
+                                                        "band_q": 6}
     free, total = torch.cuda.mem_get_info()
     budget = int(0.8 * free)
 
@@ -488,7 +492,7 @@ def run_serving(args, rank, local_rank):
             while k < len(order) and arrivals[order[k]] <= now:
                 spec, v, t, xq, q = reqs[order[k]]
                 form, prec = pb.CASES[spec["case"]]
-                pb.pb_submit(srv, v, t, xq, q, P, form, prec, opts=opts, tag=int(order[k]))
+                pb.pb_submit(srv, v, t, xq, q, P, form, prec, opts=opts, tag=int(order[k]), **plan)
                 k += 1
             a, p_ = pb.pb_server_step(srv)
             for r in pb.pb_poll(srv):
@@ -510,12 +514,46 @@ def run_serving(args, rank, local_rank):
     t0 = time.perf_counter()
     for spec, v, t, xq, q in reqs:
         form, prec = pb.CASES[spec["case"]]
-        pb.pb_solvation_energy(ctx, v, t, xq, q, P, form, prec, opts=opts)
+        pb.pb_solvation_energy(ctx, v, t, xq, q, P, form, prec, opts=opts, **plan)
     torch.cuda.synchronize()
     span_s = time.perf_counter() - t0
+    tris = np.array([r[2].shape[0] for r in reqs])
+    # the plan's Delta G change against the reference plan on the three smallest requests
+    tight = pb.solve_opts(tol=1e-9, max_it=600, precision=pb.PB_F64)
+    plan_change = 0.0
+    for i in np.argsort(tris)[:3]:
+        spec, v, t, xq, q = reqs[i]
+        form, prec = pb.CASES[spec["case"]]
+        d_plan, _ = pb.pb_solvation_energy(ctx, v, t, xq, q, P, form, prec, opts=tight, **plan)
+        d_ref, _ = pb.pb_solvation_energy(ctx, v, t, xq, q, P, form, prec, opts=tight)
+        plan_change = max(plan_change, abs(d_plan / d_ref - 1.0))
+    # sequential FP64 GPU solves: a stratified subset of the requests up to 40k triangles,
+    # t(N_t) = c0 + c2 N_t^2 fitted and summed over all requests (extrapolated)
+    small = [i for i in np.argsort(tris) if tris[i] <= 40000]
+    pick = [small[int(round(k))] for k in np.linspace(0, len(small) - 1, min(5, len(small)))] if small else []
+    f64 = pb.solve_opts(tol=1e-6, max_it=600, precision=pb.PB_F64)
+    tt, nn = [], []
+    for i in dict.fromkeys(pick):
+        spec, v, t, xq, q = reqs[i]
+        form, prec = pb.CASES[spec["case"]]
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        pb.pb_solvation_energy(ctx, v, t, xq, q, P, form, prec, opts=f64, **plan)
+        torch.cuda.synchronize()
+        tt.append(time.perf_counter() - t1)
+        nn.append(float(tris[i]))
+    seq64 = None
+    if len(tt) >= 2:
+        A = np.stack([np.ones(len(nn)), np.array(nn) ** 2], axis=1)
+        c0, c2 = np.linalg.lstsq(A, np.array(tt), rcond=None)[0]
+        if c0 < 0.0:  # no negative fixed cost: fit t = c2 N_t^2 alone
+            c0, c2 = 0.0, float(np.dot(A[:, 1], tt) / np.dot(A[:, 1], A[:, 1]))
+        total64 = float(np.sum(c0 + c2 * tris.astype(np.float64) ** 2))
+        seq64 = {"solves_per_s": len(reqs) / total64, "extrapolated": True, "timed_requests": len(tt),
+                 "timed_tris": [int(x) for x in nn], "timed_s": tt, "fit": "t = c0 + c2 N_t^2",
+                 "c0_s": float(c0), "c2_s": float(c2)}
     if rank != 0:
         return
-    tris = np.array([r[2].shape[0] for r in reqs])
     ok = all(opened[i]["status"] == 0 for i in range(len(reqs)))
     same = all(opened[i]["dG_kcal"] == closed[i]["dG_kcal"] for i in range(len(reqs)))
     line = {"metric": "PB solves/s and p50/p99 latency (serving stream)", "value": len(reqs) / span_o,
@@ -524,10 +562,12 @@ def run_serving(args, rank, local_rank):
             "config": {"workload": "serving stream: first %d of 512 seeded requests, atoms log-uniform in 50-3000 "
                                    "(%d-%d tris), cases 2/10/12/23, Poisson arrivals at %.2f x the closed-batch rate"
                                    % (len(reqs), tris.min(), tris.max(), args.rate_scale),
-                       "hbm_budget_bytes": budget, "max_active": 64, "gmres_tol": 1e-6, "precision": "mixed"},
+                       "hbm_budget_bytes": budget, "max_active": 64, "gmres_tol": 1e-6, "precision": "mixed",
+                       "quadrature": plan_text(plan), "plan_dG_change_vs_reference_max_of_3": plan_change},
             "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                            "max": float(lat.max())},
             "closed_batch_solves_per_s": rate, "sequential_solves_per_s": len(reqs) / span_s,
+            "sequential_f64_gpu": seq64,
             "all_converged": ok, "identical_open_vs_closed": same}
     print(json.dumps(line), flush=True)
 

@@ -49,10 +49,12 @@ int graph_capture(StepGraph& g, cudaStream_t s, const std::function<int()>& body
     if (rc == PB_OK && e == cudaSuccess && graph) e = cudaGraphInstantiate(&g.exec, graph, 0);
     if (graph) cudaGraphDestroy(graph);
     if (rc != PB_OK || e != cudaSuccess || !g.exec) {
+        // nothing of the body ran: the caller runs it directly (a capture that
+        // was invalidated reports its error through the body as well)
         cudaGetLastError();
         graph_free(g);
         g.failed = true;
-        return rc;
+        return PB_OK;
     }
     if (ws_generation() != gen) {  // the body moved a workspace while it was captured
         graph_free(g);

@@ -207,24 +207,37 @@ __global__ void k_scan(int64_t n, const int32_t* __restrict__ cnt, int32_t* __re
 
 // ---- near pattern on the device: row i holds every vertex of every triangle
 // paired (adjacent or band) with a triangle at i. One warp per row inserts the
-// candidates into a shared-memory hash set, compacts it, and (pass 1) writes
-// the columns in increasing order (each one's rank among the row's values).
-constexpr int PAT_HASH = 1024;  // hash slots per warp: at most PAT_HASH / 2 columns per row
-constexpr int PAT_WARPS = 4;
+// candidates into a shared-memory hash set of PAT_HASH slots (a power of two,
+// sized from the largest candidate count of any row), compacts it, and (pass 1)
+// writes the columns in increasing order (each one's rank among the row's values).
 
-__global__ void __launch_bounds__(32 * PAT_WARPS)
-k_row_pattern(int64_t nv, int pass, const int32_t* __restrict__ v2t_ptr, const int32_t* __restrict__ v2t,
-              const int32_t* __restrict__ tris, const int32_t* __restrict__ adj_ptr, const int4* __restrict__ pairs,
-              const int32_t* __restrict__ band_ptr, const int32_t* __restrict__ band_s, int32_t* __restrict__ cnt,
-              int* __restrict__ maxrow, const int32_t* __restrict__ row_ptr, int32_t* __restrict__ col,
-              int* __restrict__ status) {
-    __shared__ int32_t table[PAT_WARPS][PAT_HASH];
-    __shared__ int32_t list[PAT_WARPS][PAT_HASH / 2];
+// candidates of each row (with repetitions): an upper bound of its columns
+__global__ void k_row_candidates(int64_t nv, const int32_t* __restrict__ v2t_ptr, const int32_t* __restrict__ v2t,
+                                 const int32_t* __restrict__ adj_ptr, const int32_t* __restrict__ band_ptr,
+                                 int* __restrict__ maxc) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nv) return;
+    int64_t c = 0;
+    for (int32_t k = v2t_ptr[i]; k < v2t_ptr[i + 1]; ++k) {
+        const int32_t t = v2t[k] / 3;
+        c += 3 * (int64_t)(adj_ptr[t + 1] - adj_ptr[t]);
+        if (band_ptr) c += 3 * (int64_t)(band_ptr[t + 1] - band_ptr[t]);
+    }
+    atomicMax(maxc, (int)min(c, (int64_t)INT32_MAX));
+}
+
+__global__ void k_row_pattern(int64_t nv, int pass, int PAT_HASH, int PAT_WARPS, const int32_t* __restrict__ v2t_ptr,
+                              const int32_t* __restrict__ v2t, const int32_t* __restrict__ tris,
+                              const int32_t* __restrict__ adj_ptr, const int4* __restrict__ pairs,
+                              const int32_t* __restrict__ band_ptr, const int32_t* __restrict__ band_s,
+                              int32_t* __restrict__ cnt, int* __restrict__ maxrow, const int32_t* __restrict__ row_ptr,
+                              int32_t* __restrict__ col, int* __restrict__ status) {
+    extern __shared__ int32_t psm[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t i = (int64_t)blockIdx.x * PAT_WARPS + w;
     if (i >= nv) return;  // whole warps
-    int32_t* tb = table[w];
-    int32_t* ls = list[w];
+    int32_t* tb = psm + (size_t)w * (PAT_HASH + PAT_HASH / 2);
+    int32_t* ls = tb + PAT_HASH;
     for (int k = lane; k < PAT_HASH; k += 32) tb[k] = -1;
     __syncwarp();
     bool full = false;
@@ -675,15 +688,38 @@ static int load(pb_ctx* ctx, const double* verts_in, int64_t nv, const int32_t* 
         PB_TRY(dev_alloc((void**)&cntv, sizeof(int32_t) * nv + 64));
         int64_t* dtot = (int64_t*)(cntv + nv + (nv & 1));
         int* dmax = (int*)(dtot + 1);
+        int* dcand = dmax + 1;
         int rc = PB_OK;
         int64_t nnz = 0;
-        int hmax = 0, st = 0;
+        int hmax = 0, st = 0, maxc = 0;
         const int32_t* bp = m->n_band ? m->band_ptr : nullptr;
-        const unsigned pb_blocks = (unsigned)((nv + PAT_WARPS - 1) / PAT_WARPS);
+        int PAT_HASH = 0, PAT_WARPS = 1;
+        size_t psmem = 0;
+        unsigned pb_blocks = 0;
         do {
-            if (cudaMemset(dmax, 0, sizeof(int)) != cudaSuccess) { rc = set_error(PB_ECUDA, "pattern"); break; }
-            k_row_pattern<<<pb_blocks, 32 * PAT_WARPS>>>(nv, 0, m->v2t_ptr, m->v2t, m->tris, m->adj_ptr, m->pairs, bp,
-                                                         m->band_s, cntv, dmax, nullptr, nullptr, m->status);
+            if (cudaMemset(dmax, 0, 2 * sizeof(int)) != cudaSuccess) { rc = set_error(PB_ECUDA, "pattern"); break; }
+            k_row_candidates<<<(unsigned)((nv + 127) / 128), 128>>>(nv, m->v2t_ptr, m->v2t, m->adj_ptr, bp, dcand);
+            ::pb::count_launch();
+            if (cudaMemcpy(&maxc, dcand, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+                rc = set_error(PB_ECUDA, "near pattern failed");
+                break;
+            }
+            // hash slots: a power of two at least twice the candidates (at most 32768), warps per
+            // block so that a block stays within 160 KB of shared memory
+            PAT_HASH = 64;
+            while (PAT_HASH < 2 * maxc && PAT_HASH < 32768) PAT_HASH *= 2;
+            const size_t per_warp = sizeof(int32_t) * (size_t)(PAT_HASH + PAT_HASH / 2);
+            PAT_WARPS = (int)std::max<size_t>(1, std::min<size_t>(8, (160u << 10) / per_warp));
+            psmem = per_warp * PAT_WARPS;
+            pb_blocks = (unsigned)((nv + PAT_WARPS - 1) / PAT_WARPS);
+            if (cudaFuncSetAttribute(k_row_pattern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem) !=
+                cudaSuccess) {
+                rc = set_error(PB_ECUDA, "near pattern: shared memory of %zu bytes refused", psmem);
+                break;
+            }
+            k_row_pattern<<<pb_blocks, 32 * PAT_WARPS, psmem>>>(nv, 0, PAT_HASH, PAT_WARPS, m->v2t_ptr, m->v2t,
+                                                                 m->tris, m->adj_ptr, m->pairs, bp, m->band_s, cntv,
+                                                                 dmax, nullptr, nullptr, m->status);
             k_scan<<<1, 1024>>>(nv, cntv, m->row_ptr, dtot);
             ::pb::count_launch(2);
             if (cudaMemcpy(&nnz, dtot, sizeof(int64_t), cudaMemcpyDeviceToHost) != cudaSuccess ||
@@ -704,8 +740,9 @@ static int load(pb_ctx* ctx, const double* verts_in, int64_t nv, const int32_t* 
             m->nnz = nnz;
             m->max_row = hmax;
             if ((rc = dev_alloc((void**)&m->col, sizeof(int32_t) * (nnz + 1))) != PB_OK) break;
-            k_row_pattern<<<pb_blocks, 32 * PAT_WARPS>>>(nv, 1, m->v2t_ptr, m->v2t, m->tris, m->adj_ptr, m->pairs, bp,
-                                                         m->band_s, nullptr, nullptr, m->row_ptr, m->col, m->status);
+            k_row_pattern<<<pb_blocks, 32 * PAT_WARPS, psmem>>>(nv, 1, PAT_HASH, PAT_WARPS, m->v2t_ptr, m->v2t,
+                                                                 m->tris, m->adj_ptr, m->pairs, bp, m->band_s, nullptr,
+                                                                 nullptr, m->row_ptr, m->col, m->status);
             ::pb::count_launch();
         } while (false);
         cudaFree(cntv);

@@ -79,6 +79,10 @@ struct pb_server {
     int admitted = 0;  // admitted and not finished
     bool stop = false;
     std::thread admit_thread;
+    // Held by the admission thread while it sets a request up (its allocations,
+    // frees and synchronisations reach the whole device) and by the stepping
+    // thread while it captures a CUDA graph, which such calls would invalidate.
+    std::mutex device_mu;
     cudaStream_t s_main = nullptr, s_setup = nullptr;
     pb::BatchScratch bs;
     double* res_dev = nullptr;   // 4 doubles per slot (max_active slots)
@@ -191,11 +195,19 @@ static void admission_loop(pb_server* srv) {
             srv->used += r->footprint;
             srv->admitted += 1;
         }
-        int rc = setup_req(srv, r);
+        int rc;
+        {
+            std::lock_guard<std::mutex> dev_lock(srv->device_mu);
+            rc = setup_req(srv, r);
+        }
         r->t_ready = now_ms();
         if (rc != PB_OK) {
             r->status = rc;
             r->rel = 0.0;
+            {
+                std::lock_guard<std::mutex> dev_lock(srv->device_mu);
+                free_req(r);
+            }
             finish(srv, r, 0.0, 0.0);
             delete r;
             continue;
@@ -229,7 +241,10 @@ static int tick(pb_server* srv) {
         if (!srv->ctx->graphs || g.failed) return body();
         if (!g.exec) {
             if (r->j < 1) return body();
-            PB_TRY(graph_capture(g, s, body));
+            {
+                std::lock_guard<std::mutex> dev_lock(srv->device_mu);
+                PB_TRY(graph_capture(g, s, body));
+            }
             if (g.failed) return body();
         }
         return graph_replay(g, s);
