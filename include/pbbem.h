@@ -244,6 +244,16 @@ int pb_rhs_charges(pb_ctx* ctx, const pb_mesh* mesh, const double* xq, const dou
 int pb_solve(pb_ctx* ctx, const pb_mesh* mesh, const pb_near* near, const pb_params* prm, int form,
              int precond, const pb_solve_opts* opts, const double* rhs, double* x,
              pb_solve_info* info, void* stream);
+/* pb_solve with the Calderon preconditioner's operator taken from a second
+ * discretisation of the same surface (paper, "Fast Calderon preconditioning":
+ * relaxed quadrature orders for the preconditioner only, e.g. the 1-point far
+ * rule and 3 singular Gauss points; the solution is that of the system's own
+ * plan). pc_mesh must be the same vertices and triangles loaded with another
+ * plan (same counts, else PB_EINVAL) and pc_near its near field; precond must
+ * be one of the Calderon preconditioners. Otherwise as pb_solve. */
+int pb_solve_pc(pb_ctx* ctx, const pb_mesh* mesh, const pb_near* near, const pb_mesh* pc_mesh,
+                const pb_near* pc_near, const pb_params* prm, int form, int precond, const pb_solve_opts* opts,
+                const double* rhs, double* x, pb_solve_info* info, void* stream);
 
 /* ---- a10: reaction potential and solvation energy ------------------------ */
 /* phi_reac(x_j) = V_int[v_int](x_j) - K_int[u_int](x_j) (paper eq.

@@ -252,6 +252,25 @@ def pb_solve(ctx: Ctx, mesh: Mesh, near: Near, params: Params, form, precond, rh
     return x, d
 
 
+def pb_solve_pc(ctx: Ctx, mesh: Mesh, near: Near, pc_mesh: Mesh, pc_near: Near, params: Params, form, precond,
+                rhs: torch.Tensor, x: torch.Tensor | None = None, opts=None, stream=None,
+                raise_on_noconv: bool = True):
+    """Fast Calderon: pb_solve with the preconditioner's operator from pc_mesh/pc_near (the same surface
+    loaded with a relaxed plan). Returns (x, info dict)."""
+    if x is None:
+        x = torch.empty_like(rhs)
+    p = params.c()
+    o = opts if opts is not None else solve_opts()
+    info = N.pb_solve_info()
+    rc = N.load().pb_solve_pc(ctx.ptr, mesh.ptr, near.ptr, pc_mesh.ptr, pc_near.ptr, ctypes.byref(p), _form(form),
+                              _prec(precond), ctypes.byref(o), _dptr(rhs, "rhs"), _dptr(x, "x"), ctypes.byref(info),
+                              _stream(stream))
+    d = {k: getattr(info, k) for k, _ in N.pb_solve_info._fields_}
+    if rc != PB_OK and (raise_on_noconv or rc != PB_ENOCONV):
+        _check(rc)
+    return x, d
+
+
 def pb_energy(ctx: Ctx, mesh: Mesh, x: torch.Tensor, form, xq: torch.Tensor, q: torch.Tensor, params: Params,
               phi: torch.Tensor | None = None, stream=None):
     """Returns (dG in paper units, dG in kcal/mol); phi (optional, n_q) receives phi_reac."""

@@ -322,7 +322,7 @@ int apply_prec(Solver& S, int prec, const double* x, double* y) {
             break;
         default:  // Calderon: M^-1 C M^-1
             PB_TRY(mass_solve(m, S.nf, x, S.t1, S.cheb, S.cheb_iters, S.s));
-            PB_TRY(apply_blockop(m, S.nf, S.C, prec, S.t1, S.t2, S.s));
+            PB_TRY(apply_blockop(S.mc, S.nc, S.C, prec, S.t1, S.t2, S.s));
             S.applies++;
             PB_TRY(mass_solve(m, S.nf, S.t2, y, S.cheb, S.cheb_iters, S.s));
             break;
@@ -467,6 +467,8 @@ int setup_solver(Solver& S, const pb_mesh* m, const pb_near* nf, const pb_params
                         const pb_solve_opts* o, cudaStream_t s) {
     S.m = m;
     S.nf = nf;
+    S.mc = m;
+    S.nc = nf;
     S.prm = *prm;
     S.form = form;
     S.pc = pc;
@@ -594,13 +596,14 @@ void vec_add(int64_t n, const double* a, double* y, cudaStream_t s) {
 
 static int solve_body(pb_ctx* ctx, const pb_mesh* m, const pb_near* nf, const pb_params* prm, int form, int pc,
                       const pb_solve_opts* o, const double* b, double* x, pb_solve_info* info, cudaStream_t s,
-                      Solver& S);
+                      Solver& S, const pb_mesh* mc, const pb_near* nc);
 
 // The solve runs on a stream of its own, ordered after the caller's stream
 // and before what the caller queues next: CUDA graphs cannot be captured on
 // the legacy default stream.
 static int solve_impl(pb_ctx* ctx, const pb_mesh* m, const pb_near* nf, const pb_params* prm, int form, int pc,
-                      const pb_solve_opts* o, const double* b, double* x, pb_solve_info* info, cudaStream_t caller) {
+                      const pb_solve_opts* o, const double* b, double* x, pb_solve_info* info, cudaStream_t caller,
+                      const pb_mesh* mc = nullptr, const pb_near* nc = nullptr) {
     pb_solve_opts d = {1e-6, 500, 0, PB_F64, 1e-4, 20, 0, 0, 0, 0};
     if (!o) o = &d;
     if (!(o->tol > 0.0) || o->max_it < 1) return set_error(PB_EINVAL, "need tol > 0 and max_it >= 1");
@@ -615,7 +618,7 @@ static int solve_impl(pb_ctx* ctx, const pb_mesh* m, const pb_near* nf, const pb
     cudaEventRecord(fence, caller);
     cudaStreamWaitEvent(s, fence, 0);
     Solver S;
-    int rc = solve_body(ctx, m, nf, prm, form, pc, o, b, x, info, s, S);
+    int rc = solve_body(ctx, m, nf, prm, form, pc, o, b, x, info, s, S, mc, nc);
     solver_release(S);
     cudaEventRecord(fence, s);
     cudaStreamWaitEvent(caller, fence, 0);
@@ -626,8 +629,12 @@ static int solve_impl(pb_ctx* ctx, const pb_mesh* m, const pb_near* nf, const pb
 
 static int solve_body(pb_ctx* ctx, const pb_mesh* m, const pb_near* nf, const pb_params* prm, int form, int pc,
                       const pb_solve_opts* o, const double* b, double* x, pb_solve_info* info, cudaStream_t s,
-                      Solver& S) {
+                      Solver& S, const pb_mesh* mc, const pb_near* nc) {
     PB_TRY(setup_solver(S, m, nf, prm, form, pc, o, s));
+    if (mc) {
+        S.mc = mc;
+        S.nc = nc;
+    }
     S.graphs = ctx->graphs != 0;
     const int64_t n2 = 2 * m->nv;
     int mmax = o->restart > 0 ? std::min(o->restart, o->max_it) : o->max_it;
@@ -768,4 +775,22 @@ extern "C" int pb_solve(pb_ctx* ctx, const pb_mesh* m, const pb_near* nf, const 
     if (!prm) return set_error(PB_EINVAL, "NULL params");
     PB_CUDA(cudaSetDevice(ctx->device));
     return solve_impl(ctx, m, nf, prm, form, pc, opts, rhs, x, info, (cudaStream_t)stream);
+}
+
+// Fast Calderon (paper, "Fast Calderon preconditioning"): the preconditioner's
+// operator from a second plan of the same surface.
+extern "C" int pb_solve_pc(pb_ctx* ctx, const pb_mesh* m, const pb_near* nf, const pb_mesh* mc, const pb_near* nc,
+                           const pb_params* prm, int form, int pc, const pb_solve_opts* opts, const double* rhs,
+                           double* x, pb_solve_info* info, void* stream) {
+    PB_TRY(apply_args_ok(ctx, m, nf, rhs, x));
+    if (!prm || !mc || !nc) return set_error(PB_EINVAL, "NULL argument");
+    if (nc->mesh != mc) return set_error(PB_EINVAL, "preconditioner near field belongs to another mesh");
+    if (mc->nv != m->nv || mc->nt != m->nt)
+        return set_error(PB_EINVAL, "preconditioner mesh differs from the system's (%lld/%lld vs %lld/%lld)",
+                         (long long)mc->nv, (long long)mc->nt, (long long)m->nv, (long long)m->nt);
+    if (pc < PB_PC_CALDERON_FULL) return set_error(PB_EINVAL, "pb_solve_pc needs a Calderon preconditioner");
+    if (fabs(nc->kappa - nf->kappa) > 1e-12 * (1.0 + nf->kappa))
+        return set_error(PB_EINVAL, "the two near fields were built for different kappa");
+    PB_CUDA(cudaSetDevice(ctx->device));
+    return solve_impl(ctx, m, nf, prm, form, pc, opts, rhs, x, info, (cudaStream_t)stream, mc, nc);
 }

@@ -8,6 +8,8 @@ namespace pb {
 struct Solver {
     const pb_mesh* m;
     const pb_near* nf;
+    const pb_mesh* mc = nullptr;  // the Calderon preconditioner's operator (fast Calderon: another plan)
+    const pb_near* nc = nullptr;
     pb_params prm;
     int form, pc;
     BlockOp A, C;
