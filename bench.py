@@ -67,6 +67,9 @@ def parse():
                          "plan's Delta G, tuned before the timed region), reference (6-point far rule everywhere) "
                          "or band (3-point far rule beyond --band-eta radii, 6-point inside)")
     ap.add_argument("--band-eta", type=float, default=3.0)
+    ap.add_argument("--far", default="auto", choices=["auto", "direct", "tree"],
+                    help="far field of the FP32 inner iterations: the library's default (treecode from 100k "
+                         "points on), direct pair sums, or the treecode at every size")
     ap.add_argument("--fast-calderon", action="store_true",
                     help="Calderon cases (20, 23): the preconditioner's operator with relaxed quadrature (1-point "
                          "far rule, 3 singular Gauss points), the paper's Cases 20b/23b")
@@ -244,7 +247,9 @@ def _kernels():
             pb.PB_KERNEL_NEAR_COIN: ("k_coin_pairs (FP64 singular quadrature, coincident pairs)", "near_coin",
                                      FP64_FLOPS_PER_SM, "FP64 flops"),
             pb.PB_KERNEL_NEAR_BAND: ("k_band_pairs (FP64 band-rule corrections)", "near_band", FP64_FLOPS_PER_SM,
-                                     "FP64 flops")}
+                                     "FP64 flops"),
+            pb.PB_KERNEL_TREE32: ("k_tree_eval (FP32 treecode: proxy and direct interactions)", "tree32",
+                                  FP32_LANES_PER_SM, "FP32 ops")}
 
 
 def quad_plan(args):
@@ -295,6 +300,11 @@ def run_ours(args, rank, world, local_rank):
     ctx = pb.pb_init(local_rank)
     if args.no_graphs:
         pb.pb_set_graphs(ctx, False)
+    if args.far == "direct":
+        pb.pb_set_treecode(ctx, False)
+    elif args.far == "tree":
+        pb.pb_set_treecode(ctx, True, 6, 0.7, 0)
+
     dv = torch.as_tensor(v, device=dev)
     dt = torch.as_tensor(t, device=dev)
     dxq = torch.as_tensor(xq, device=dev)
@@ -362,6 +372,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     mv_ms = e0.elapsed_time(e1) / nmv
     npts = m.info()["n_points"]
+    uses_tree = args.far == "tree" or (args.far == "auto" and npts >= 100000)
     nf.free()
     m.free()
 
@@ -458,6 +469,8 @@ def run_ours(args, rank, world, local_rank):
                                 dG_change_vs_reference_plan=plan_change),
                    "points": npts, "l2": "flushed (256 MB write) before every timed step",
                    "gmres_step": "CUDA graph replay" if not args.no_graphs else "kernel by kernel",
+                   "far_field": ("treecode (order 6, theta 0.7) in the inner FP32 iterations, direct sums in the "
+                                 "outer residual" if uses_tree else "direct pair sums"),
                    "preconditioner_plan": (dict(PC_PLAN, note="fast Calderon: relaxed quadrature for the "
                                                 "preconditioner's operator") if fast else "the system's"),
                    "parallelism": "replicas" if world > 1 else "1 GPU"},

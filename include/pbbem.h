@@ -362,7 +362,8 @@ int pb_autotune_plan(pb_ctx* ctx, const double* verts, int64_t n_verts, const in
 #define PB_KERNEL_NEAR_ADJ 3        /* FP64 regularised quadrature of edge- and vertex-adjacent pairs */
 #define PB_KERNEL_NEAR_COIN 4       /* FP64 regularised quadrature of coincident pairs */
 #define PB_KERNEL_NEAR_BAND 5       /* FP64 band-rule minus far-rule blocks of band pairs */
-#define PB_KERNEL_COUNT 6
+#define PB_KERNEL_TREE32 6          /* FP32 treecode evaluation (proxy and direct interactions) */
+#define PB_KERNEL_COUNT 7
 /* For the pair kernels, "pairs" are target-source point pairs and "ops" FP32
  * (FP64 for PB_KERNEL_PAIR64) operations by the kernel's formula count; for
  * the near-field kernels, "pairs" are quadrature point pairs (kernel
@@ -391,6 +392,28 @@ int64_t pb_launch_count(void);
  * or launched kernel by kernel (0). The same kernels run either way, so
  * results are bitwise the same. Applies to solves started after the call. */
 int pb_set_graphs(pb_ctx* ctx, int enable);
+
+/* ---- treecode far field ---------------------------------------------------- */
+/* The paper computes its far field with a fast multipole method; this library
+ * sums it directly by default. With the treecode enabled (1), FP32 operator
+ * applications (the inner iterations of PB_MIXED solves, PB_F32 calls) of
+ * meshes with at least min_points far-rule points use a kd-tree of the points
+ * (leaves of 128): well-separated clusters (radius sum < theta x centre
+ * distance) act through (order+1)^3 proxy sources on Chebyshev points of their
+ * box, carrying the interpolated densities; all other pairs are summed
+ * directly. The split-coordinate and FP64 applications (PB_MIXED's outer
+ * residual, PB_F64 solves) stay direct, so mixed solves converge to the same
+ * solution. order 2..7, theta in (0, 1]. Default: enabled, order 6, theta 0.7,
+ * min_points 100000 (below that the direct sum is as fast on this GPU), or
+ * disabled when the environment variable PBBEM_TREECODE=0 is set at pb_init.
+ * The tree is built on the mesh's first
+ * treecode application (host work and a device allocation; before any stream
+ * capture). Applies to applications started after the call. */
+int pb_set_treecode(pb_ctx* ctx, int enable, int order, double theta, int64_t min_points);
+/* Sizes of a mesh's tree after its first treecode application: out[0..5] =
+ * leaves, proxied clusters, far (proxy) list entries, near list entries,
+ * direct point pairs and proxy point pairs of one application. */
+int pb_tree_info(const pb_mesh* mesh, int64_t out[6]);
 
 #ifdef __cplusplus
 }

@@ -117,6 +117,7 @@ class Near(_Handle):
 
 PB_KERNEL_PAIR32, PB_KERNEL_PAIR32_ACCURATE, PB_KERNEL_PAIR64 = 0, 1, 2
 PB_KERNEL_NEAR_ADJ, PB_KERNEL_NEAR_COIN, PB_KERNEL_NEAR_BAND = 3, 4, 5
+PB_KERNEL_TREE32 = 6
 
 
 def pb_profile(ctx: Ctx, enable: bool = True):
@@ -141,6 +142,19 @@ def pb_selftest_wait(ctx: Ctx, polls: int = 4096) -> int:
 
 def pb_launch_count() -> int:
     return int(N.load().pb_launch_count())
+
+
+def pb_set_treecode(ctx: Ctx, enable: bool = True, order: int = 6, theta: float = 0.7, min_points: int = 100000):
+    """Treecode far field for FP32 applications of meshes with >= min_points far-rule points."""
+    _check(N.load().pb_set_treecode(ctx.ptr, 1 if enable else 0, int(order), float(theta), int(min_points)))
+
+
+def pb_tree_info(mesh: Mesh):
+    """Sizes of the mesh's tree (after its first treecode application)."""
+    out = (ctypes.c_int64 * 6)()
+    _check(N.load().pb_tree_info(mesh.ptr, out))
+    return dict(zip(["leaves", "proxied_clusters", "far_entries", "near_entries", "direct_pairs", "proxy_pairs"],
+                    list(out)))
 
 
 def pb_set_graphs(ctx: Ctx, enable: bool = True):

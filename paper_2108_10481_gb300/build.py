@@ -17,7 +17,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # made with the same arithmetic as the oracle's
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-ffp-contract=off", "-I" + INC,
          "-I" + SRC]
-SOURCES = ["api.cu", "mesh.cu", "near.cu", "far.cu", "form.cu", "solve.cu", "rhs.cu", "serve.cu"]
+SOURCES = ["api.cu", "mesh.cu", "near.cu", "far.cu", "form.cu", "solve.cu", "rhs.cu", "serve.cu", "tree.cu"]
 
 
 def nvcc() -> str:

@@ -16,6 +16,7 @@ static thread_local StepGraph* t_capture = nullptr;
 static std::atomic<uint64_t> g_ws_gen{1};
 
 uint64_t ws_generation() { return g_ws_gen.load(); }
+void ws_bump() { g_ws_gen.fetch_add(1); }
 
 void count_launch(int n) {
     if (t_capture) t_capture->launches += n;  // runs once per replay, counted then
@@ -163,6 +164,8 @@ extern "C" int pb_init(int device, pb_ctx** out) {
     if (pk && pk[0] == '1') c->pair_kernel = 1;
     const char* gr = getenv("PBBEM_GRAPHS");
     if (gr && gr[0] == '0') c->graphs = 0;
+    const char* tc = getenv("PBBEM_TREECODE");
+    if (tc && tc[0] == '0') c->tree_enable = 0;
     *out = c;
     return PB_OK;
 }
@@ -211,6 +214,22 @@ extern "C" int pb_profile_read(pb_ctx* ctx, int kernel, int64_t* launches, doubl
 }
 
 extern "C" int64_t pb_launch_count(void) { return g_launches.load(); }
+
+extern "C" int pb_set_treecode(pb_ctx* ctx, int enable, int order, double theta, int64_t min_points) {
+    if (!ctx) return set_error(PB_EINVAL, "pb_set_treecode: NULL context");
+    if (order < 2 || order > 7 || !(theta > 0.0 && theta <= 1.0) || min_points < 0)
+        return set_error(PB_EINVAL, "pb_set_treecode: need order in 2..7, theta in (0, 1], min_points >= 0");
+    ctx->tree_enable = enable ? 1 : 0;
+    ctx->tree_order = order;
+    ctx->tree_theta = theta;
+    ctx->tree_min_points = min_points;
+    return PB_OK;
+}
+
+extern "C" int pb_tree_info(const pb_mesh* m, int64_t out[6]) {
+    if (!m || !out) return set_error(PB_EINVAL, "pb_tree_info: NULL argument");
+    return tree_info(m, out);
+}
 
 extern "C" int pb_set_graphs(pb_ctx* ctx, int enable) {
     if (!ctx) return set_error(PB_EINVAL, "pb_set_graphs: NULL context");

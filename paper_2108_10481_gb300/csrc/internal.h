@@ -96,6 +96,7 @@ StepGraph* capturing();  // the graph this thread is capturing, or null
 // Counts workspace (re)allocations: a captured graph whose generation differs
 // may hold a freed pointer and must be captured again.
 uint64_t ws_generation();
+void ws_bump();  // a buffer a graph may hold was freed
 // Drop g if a workspace has moved since it was captured.
 void graph_check(StepGraph& g);
 // Capture body() on stream s (nothing runs); on failure g.failed is set and
@@ -115,6 +116,7 @@ struct TuneEntry {
     double split_scale = 1;  // multiplier of the wave-filling split count
 };
 constexpr int TUNE_BUCKETS = 40;
+struct PbTree;  // treecode of a mesh (tree.cu)
 }  // namespace pb
 
 struct pb_ctx {
@@ -127,6 +129,11 @@ struct pb_ctx {
     int cc_major = 0, cc_minor = 0;
     void* encode_tiled = nullptr;  // cuTensorMapEncodeTiled entry point
     int graphs = 1;                // replay GMRES iterations from CUDA graphs
+    // treecode far field for FP32 applications (inner iterations)
+    int tree_enable = 1;           // on by default for meshes of at least tree_min_points points
+    int tree_order = 6;            // Chebyshev points per dimension - 1
+    double tree_theta = 0.7;       // separation: radius sum < theta x centre distance
+    int64_t tree_min_points = 100000;
 };
 
 struct pb_mesh {
@@ -176,7 +183,8 @@ struct pb_mesh {
     int32_t* diag_pos = nullptr;// nv
     int* status = nullptr;          // device status word of bounded waits (0 = fine)
     // workspaces (grown on demand)
-    pb::Workspace ws_src, ws_part, ws_tri, ws_vec, ws_comb;
+    pb::Workspace ws_src, ws_part, ws_tri, ws_vec, ws_comb, ws_tree;
+    pb::PbTree* tree = nullptr;  // built on the first treecode application
     size_t device_bytes = 0;
 };
 
@@ -246,6 +254,13 @@ struct BatchScratch {
     Workspace table;  // job and work-item tables on the device
 };
 int apply_blockops_batched(const std::vector<FarJob>& jobs, int prec, BatchScratch& bs, cudaStream_t s);
+
+// treecode far field (FP32): per-target partial sums in the direct kernel's
+// one-split layout; the tree is built on first use
+int tree_far(const pb_mesh* m, const FarPlan& fp, const double* x, bool need_u, bool need_v, float* part,
+             cudaStream_t s);
+void tree_free(PbTree* t);
+int tree_info(const pb_mesh* m, int64_t out[6]);
 
 // far-field split count for the pair kernels
 int far_splits(const pb_mesh* m, int targets_per_cta, int ctas_per_sm);

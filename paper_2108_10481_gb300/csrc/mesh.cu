@@ -358,6 +358,9 @@ static void free_mesh_arrays(pb_mesh* m) {
     ws_free(m->ws_tri);
     ws_free(m->ws_vec);
     ws_free(m->ws_comb);
+    ws_free(m->ws_tree);
+    tree_free(m->tree);
+    m->tree = nullptr;
 }
 
 static int load(pb_ctx* ctx, const double* verts_in, int64_t nv, const int32_t* tris_in, int64_t nt,

@@ -1,0 +1,583 @@
+// Treecode far field for the FP32 inner iterations (the survey's next step
+// after the direct pair sum, in place of the paper's FMM; the paper uses
+// ExaFMM with expansion order 3 for its far field).
+//
+// The quadrature points are sorted into a kd-tree (longest-axis median
+// splits, leaves of at most LEAF points). For a leaf of targets and a cluster
+// that is well separated (radius sum below theta times the centre distance),
+// the cluster's sources are replaced by proxy sources on an n x n x n tensor
+// grid of Chebyshev points of its bounding box: the y-dependence of every
+// kernel is interpolated by the tensor Lagrange basis L_k, so
+//   sum_j G(x, y_j) s_j            ~ sum_k G(x, z_k) S_k,     S_k = sum_j L_k(y_j) s_j
+//   sum_j grad_y G(x, y_j) . p_j   ~ sum_k G(x, z_k) Q_k,     Q_k = sum_j grad L_k(y_j) . p_j
+//   sum_j grad_x G(x, y_j) s_j     ~ sum_k grad_x G(x, z_k) S_k
+// and the vector charges (curl densities, normal densities) likewise, for
+// both kernels at once (the interpolation is kernel independent). Clusters
+// with fewer points than proxies, and all other pairs, are summed directly
+// with the same arithmetic as the direct FP32 pair kernel (identical points
+// skipped). The result approximates the direct far sum; the mixed-precision
+// solver uses it only for its inner iterations and keeps the exact sums for
+// the outer residual.
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+#include <vector>
+
+#include "internal.h"
+
+namespace pb {
+
+constexpr int TREE_LEAF = 128;     // targets per leaf (one CTA)
+constexpr int TREE_REC = 12;       // floats per tree source / proxy record
+constexpr int TREE_MAXN = 8;       // largest Chebyshev order + 1
+
+struct TreeCoef {
+    float k[2][4];
+    float kappa;
+    float mk2;  // -kappa log2(e)
+};
+
+__device__ __forceinline__ float t_rsqrt(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float t_ex2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+// ---------------------------------------------------------------- host tree
+struct HostNode {
+    float lo[3], hi[3];
+    int32_t b, e;     // points [b, e) in tree order
+    int32_t c0, c1;   // children (-1 for a leaf)
+    int32_t proxy;    // proxy slot (-1: fewer points than proxies)
+};
+
+struct PbTree {
+    int n = 0, nprox = 0;       // Chebyshev points per dimension, proxies per cluster
+    double theta = 0.0;
+    int64_t nleaf = 0, nslot = 0;
+    int32_t* perm = nullptr;      // tree index -> point index
+    int32_t* leaf_rng = nullptr;  // 2 per leaf
+    int32_t* far_ptr = nullptr;   // nleaf + 1
+    int32_t* far_idx = nullptr;   // proxy slots
+    int32_t* near_ptr = nullptr;  // nleaf + 1
+    int32_t* near_rng = nullptr;  // 2 per entry: [b, e) in tree order
+    int32_t* slot_rng = nullptr;  // 2 per proxy slot: its points [b, e)
+    int32_t* slot_kids = nullptr; // 6 per proxy slot: per child, its slot (-1: none) and points [b, e)
+    int32_t* slot_order = nullptr;// slots by height (children before parents)
+    std::vector<int64_t> height_ptr;  // slot_order ranges of each height
+    float* slot_box = nullptr;    // 6 per proxy slot: lo, hi
+    void* block = nullptr;        // one allocation holding the arrays above
+    int64_t n_far = 0, n_near = 0, direct_pairs = 0, proxy_pairs = 0;
+};
+
+void tree_free(PbTree* t) {
+    if (!t) return;
+    if (t->block) cudaFree(t->block);
+    delete t;
+}
+
+static int build_tree(pb_mesh* m, int order, double theta, PbTree** out) {
+    const int64_t np = m->np;
+    std::vector<float> P(4 * np);
+    PB_CUDA(cudaMemcpy(P.data(), m->pts32, sizeof(float) * 4 * np, cudaMemcpyDeviceToHost));
+    std::vector<int32_t> perm(np);
+    std::iota(perm.begin(), perm.end(), 0);
+    std::vector<HostNode> nodes;
+    nodes.reserve(2 * np / TREE_LEAF + 16);
+    const int n = order + 1, nprox = n * n * n;
+    // recursive median split on the longest axis (explicit stack)
+    struct Job { int32_t b, e, node; };
+    nodes.push_back(HostNode{});
+    std::vector<Job> stack{{0, (int32_t)np, 0}};
+    while (!stack.empty()) {
+        Job j = stack.back();
+        stack.pop_back();
+        HostNode nd;
+        for (int k = 0; k < 3; ++k) {
+            nd.lo[k] = INFINITY;
+            nd.hi[k] = -INFINITY;
+        }
+        for (int32_t i = j.b; i < j.e; ++i)
+            for (int k = 0; k < 3; ++k) {
+                nd.lo[k] = std::min(nd.lo[k], P[4 * perm[i] + k]);
+                nd.hi[k] = std::max(nd.hi[k], P[4 * perm[i] + k]);
+            }
+        nd.b = j.b;
+        nd.e = j.e;
+        nd.c0 = nd.c1 = -1;
+        nd.proxy = -1;
+        if (j.e - j.b > TREE_LEAF) {
+            int ax = 0;
+            for (int k = 1; k < 3; ++k)
+                if (nd.hi[k] - nd.lo[k] > nd.hi[ax] - nd.lo[ax]) ax = k;
+            const int32_t mid = j.b + (j.e - j.b) / 2;
+            std::nth_element(perm.begin() + j.b, perm.begin() + mid, perm.begin() + j.e,
+                             [&](int32_t a, int32_t c) { return P[4 * a + ax] < P[4 * c + ax]; });
+            nd.c0 = (int32_t)nodes.size();
+            nodes.push_back(HostNode{});
+            nd.c1 = (int32_t)nodes.size();
+            nodes.push_back(HostNode{});
+            stack.push_back({mid, j.e, nd.c1});
+            stack.push_back({j.b, mid, nd.c0});
+        }
+        nodes[j.node] = nd;
+    }
+    // proxy slots: clusters with more points than proxies
+    std::vector<int32_t> slot_rng, leaves;
+    std::vector<float> slot_box;
+    for (size_t k = 0; k < nodes.size(); ++k) {
+        HostNode& nd = nodes[k];
+        if (nd.e - nd.b > nprox) {
+            nd.proxy = (int32_t)(slot_rng.size() / 2);
+            slot_rng.push_back(nd.b);
+            slot_rng.push_back(nd.e);
+            // a box with room around degenerate sides, so that the Chebyshev points are distinct
+            float ext = 0.f;
+            for (int d = 0; d < 3; ++d) ext = std::max(ext, nd.hi[d] - nd.lo[d]);
+            for (int d = 0; d < 3; ++d) {
+                const float pad = std::max(1e-3f * ext, 1e-6f);
+                slot_box.push_back(nd.lo[d] - pad);
+            }
+            for (int d = 0; d < 3; ++d) {
+                const float pad = std::max(1e-3f * ext, 1e-6f);
+                slot_box.push_back(nd.hi[d] + pad);
+            }
+        }
+        if (nd.c0 < 0) leaves.push_back((int32_t)k);
+    }
+    // children of every slot (a slot always has two: it holds more points than a leaf), and the
+    // slots ordered by height so that children's proxies exist before their parents'
+    const int64_t nslot = (int64_t)(slot_rng.size() / 2);
+    std::vector<int32_t> slot_kids(6 * nslot), height(nslot, 0), slot_node(nslot);
+    for (size_t k = 0; k < nodes.size(); ++k)
+        if (nodes[k].proxy >= 0) slot_node[nodes[k].proxy] = (int32_t)k;
+    // nodes were created parents before children: a reverse sweep sees children first
+    for (int64_t sl = nslot - 1; sl >= 0; --sl) {
+        const HostNode& nd = nodes[slot_node[sl]];
+        const int32_t kids[2] = {nd.c0, nd.c1};
+        int h = 0;
+        for (int c = 0; c < 2; ++c) {
+            const HostNode& ch = nodes[kids[c]];
+            slot_kids[6 * sl + 3 * c] = ch.proxy;
+            slot_kids[6 * sl + 3 * c + 1] = ch.b;
+            slot_kids[6 * sl + 3 * c + 2] = ch.e;
+            if (ch.proxy >= 0) h = std::max(h, height[ch.proxy] + 1);
+        }
+        height[sl] = h;
+    }
+    int hmax = 0;
+    for (int64_t sl = 0; sl < nslot; ++sl) hmax = std::max(hmax, height[sl]);
+    std::vector<int32_t> slot_order;
+    std::vector<int64_t> height_ptr{0};
+    for (int h = 0; h <= hmax && nslot; ++h) {
+        for (int64_t sl = 0; sl < nslot; ++sl)
+            if (height[sl] == h) slot_order.push_back((int32_t)sl);
+        height_ptr.push_back((int64_t)slot_order.size());
+    }
+    auto center_radius = [&](const HostNode& nd, float* c) {
+        float r2 = 0.f;
+        for (int d = 0; d < 3; ++d) {
+            c[d] = 0.5f * (nd.lo[d] + nd.hi[d]);
+            const float h = 0.5f * (nd.hi[d] - nd.lo[d]);
+            r2 += h * h;
+        }
+        return std::sqrt(r2);
+    };
+    // interaction lists of every leaf
+    std::vector<int32_t> far_ptr{0}, far_idx, near_ptr{0}, near_rng, leaf_rng;
+    PbTree* t = new PbTree();
+    t->n = n;
+    t->nprox = nprox;
+    t->theta = theta;
+    std::vector<int32_t> st;
+    for (int32_t L : leaves) {
+        const HostNode& tl = nodes[L];
+        float cl[3];
+        const float rl = center_radius(tl, cl);
+        leaf_rng.push_back(tl.b);
+        leaf_rng.push_back(tl.e);
+        st.assign(1, 0);
+        while (!st.empty()) {
+            const HostNode& nd = nodes[st.back()];
+            st.pop_back();
+            float cn[3];
+            const float rn = center_radius(nd, cn);
+            float d2 = 0.f;
+            for (int d = 0; d < 3; ++d) d2 += (cl[d] - cn[d]) * (cl[d] - cn[d]);
+            const float lim = (rl + rn) / (float)theta;
+            const bool separated = d2 > lim * lim;
+            if (separated && nd.proxy >= 0) {
+                far_idx.push_back(nd.proxy);
+                t->proxy_pairs += (int64_t)(tl.e - tl.b) * nprox;
+            } else if (separated || nd.c0 < 0) {
+                near_rng.push_back(nd.b);
+                near_rng.push_back(nd.e);
+                t->direct_pairs += (int64_t)(tl.e - tl.b) * (nd.e - nd.b);
+            } else {
+                st.push_back(nd.c1);
+                st.push_back(nd.c0);
+            }
+        }
+        far_ptr.push_back((int32_t)far_idx.size());
+        near_ptr.push_back((int32_t)(near_rng.size() / 2));
+    }
+    t->nleaf = (int64_t)leaves.size();
+    t->nslot = (int64_t)(slot_rng.size() / 2);
+    t->n_far = (int64_t)far_idx.size();
+    t->n_near = (int64_t)(near_rng.size() / 2);
+    // one device allocation for all arrays
+    const size_t ints = perm.size() + leaf_rng.size() + far_ptr.size() + far_idx.size() + near_ptr.size() +
+                        near_rng.size() + slot_rng.size() + slot_kids.size() + slot_order.size();
+    const size_t bytes = sizeof(int32_t) * (ints + 8) + sizeof(float) * (slot_box.size() + 4);
+    int rc = dev_alloc(&t->block, bytes);
+    if (rc != PB_OK) {
+        delete t;
+        return rc;
+    }
+    int32_t* p = (int32_t*)t->block;
+    auto put = [&](const std::vector<int32_t>& v) {
+        int32_t* at = p;
+        if (!v.empty()) cudaMemcpy(at, v.data(), sizeof(int32_t) * v.size(), cudaMemcpyHostToDevice);
+        p += v.size();
+        return at;
+    };
+    t->perm = put(perm);
+    t->leaf_rng = put(leaf_rng);
+    t->far_ptr = put(far_ptr);
+    t->far_idx = put(far_idx);
+    t->near_ptr = put(near_ptr);
+    t->near_rng = put(near_rng);
+    t->slot_rng = put(slot_rng);
+    t->slot_kids = put(slot_kids);
+    t->slot_order = put(slot_order);
+    t->height_ptr = height_ptr;
+    t->slot_box = (float*)p;
+    if (!slot_box.empty())
+        cudaMemcpy(t->slot_box, slot_box.data(), sizeof(float) * slot_box.size(), cudaMemcpyHostToDevice);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        tree_free(t);
+        return set_error(PB_ECUDA, "tree upload: %s", cudaGetErrorString(e));
+    }
+    *out = t;
+    return PB_OK;
+}
+
+// ------------------------------------------------------------- device side
+// Source records in tree order: position (FP32, relative to the mesh centre),
+// s = w v, p = w u n, c = w curl u (the direct kernel's densities).
+__global__ void k_tree_sources(int64_t np, int Q, Rule rule, const int32_t* __restrict__ perm,
+                               const int32_t* __restrict__ tris, const double* __restrict__ tgeo,
+                               const double* __restrict__ pts64, const float* __restrict__ pts32,
+                               const double* __restrict__ u, const double* __restrict__ v, int need_u, int need_v,
+                               float* __restrict__ rec) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= np) return;
+    const int64_t pt = perm[i], t = pt / Q;
+    const int q = (int)(pt - t * Q);
+    const double* g = tgeo + 16 * t;
+    const int32_t i0 = tris[3 * t], i1 = tris[3 * t + 1], i2 = tris[3 * t + 2];
+    double ua[3] = {0, 0, 0}, va[3] = {0, 0, 0};
+    if (need_u) { ua[0] = u[i0]; ua[1] = u[i1]; ua[2] = u[i2]; }
+    if (need_v) { va[0] = v[i0]; va[1] = v[i1]; va[2] = v[i2]; }
+    const double inv2a = -1.0 / (2.0 * g[3]);
+    const double w = pts64[4 * pt + 3] * 0.07957747154594767;  // weight / (4 pi)
+    const double uq = rule.l[q][0] * ua[0] + rule.l[q][1] * ua[1] + rule.l[q][2] * ua[2];
+    const double vq = rule.l[q][0] * va[0] + rule.l[q][1] * va[1] + rule.l[q][2] * va[2];
+    float* r = rec + TREE_REC * i;
+    r[0] = pts32[4 * pt];
+    r[1] = pts32[4 * pt + 1];
+    r[2] = pts32[4 * pt + 2];
+    r[3] = (float)(w * vq);
+    for (int k = 0; k < 3; ++k) r[4 + k] = (float)(w * uq * g[k]);
+    for (int k = 0; k < 3; ++k)
+        r[7 + k] = (float)(w * inv2a * (ua[0] * g[4 + k] + ua[1] * g[7 + k] + ua[2] * g[10 + k]));
+    r[10] = r[11] = 0.f;
+}
+
+// Chebyshev points (second kind) of order n-1 on [-1, 1]
+__device__ __forceinline__ float cheb_node(int a, int n) {
+    return cospif((float)a / (float)(n - 1));
+}
+
+// Lagrange basis l_a(t) and its derivative on the n Chebyshev points, t in [-1, 1]
+__device__ void lagrange1(float t, int n, float* l, float* dl) {
+    float tn[TREE_MAXN];
+    for (int a = 0; a < n; ++a) tn[a] = cheb_node(a, n);
+    for (int a = 0; a < n; ++a) {
+        float den = 1.f, num = 1.f, dnum = 0.f;
+        for (int b = 0; b < n; ++b) {
+            if (b == a) continue;
+            den *= tn[a] - tn[b];
+            // product rule, running: d(num * (t - t_b)) = dnum (t - t_b) + num
+            dnum = dnum * (t - tn[b]) + num;
+            num *= t - tn[b];
+        }
+        l[a] = num / den;
+        dl[a] = dnum / den;
+    }
+}
+
+// Proxy charges of the slots of one height: one CTA per slot, threads over
+// proxies. A slot's charges come from its two children: a child with its own
+// proxies passes them on through the slot's interpolation (exact, the basis
+// polynomials having the same degree), any other child through its points.
+// Sources are staged 128 at a time with their 1-D basis values.
+// Proxy record: z (3), S, Q, C (3), N (3), 0.
+constexpr int PROXY_THREADS = 128;
+
+__global__ void __launch_bounds__(PROXY_THREADS)
+k_proxy_charges(int n, const int32_t* __restrict__ slots, const int32_t* __restrict__ slot_kids,
+                const float* __restrict__ slot_box, const float* __restrict__ rec, float* __restrict__ prox) {
+    __shared__ float sb[PROXY_THREADS][6 * TREE_MAXN + 8];  // lx, ly, lz, dlx, dly, dlz; 8 charges
+    const int slot = slots[blockIdx.x];
+    const int nprox = n * n * n;
+    const float* box = slot_box + 6 * slot;
+    float mid[3], half[3];
+    for (int d = 0; d < 3; ++d) {
+        mid[d] = 0.5f * (box[d] + box[3 + d]);
+        half[d] = 0.5f * (box[3 + d] - box[d]);
+    }
+    constexpr int PER = (TREE_MAXN * TREE_MAXN * TREE_MAXN + PROXY_THREADS - 1) / PROXY_THREADS;
+    float acc[PER][8];
+    for (int r = 0; r < PER; ++r)
+        for (int c = 0; c < 8; ++c) acc[r][c] = 0.f;
+    for (int kid = 0; kid < 2; ++kid) {
+        const int32_t ks = slot_kids[6 * slot + 3 * kid];
+        const bool raw = ks < 0;  // uniform across the block
+        const int32_t b = raw ? slot_kids[6 * slot + 3 * kid + 1] : 0;
+        const int32_t e = raw ? slot_kids[6 * slot + 3 * kid + 2] : nprox;
+        const float* src = raw ? rec : prox + (int64_t)ks * nprox * TREE_REC;
+        for (int c0 = b; c0 < e; c0 += PROXY_THREADS) {
+            const int i = c0 + threadIdx.x;
+            float* my = sb[threadIdx.x];
+            if (i < e) {
+                const float* r = src + TREE_REC * (int64_t)i;
+                for (int d = 0; d < 3; ++d) {
+                    const float t = (r[d] - mid[d]) / half[d];
+                    lagrange1(t, n, my + TREE_MAXN * d, my + TREE_MAXN * (3 + d));
+                    for (int a = 0; a < n; ++a) my[TREE_MAXN * (3 + d) + a] /= half[d];  // d/dy = d/dt / half
+                }
+                // raw point: s, p (3), c (3); child proxy: S, Q, C (3), N (3)
+                for (int c = 0; c < 8; ++c) my[6 * TREE_MAXN + c] = raw ? (c < 7 ? r[3 + c] : 0.f) : r[3 + c];
+            }
+            __syncthreads();
+            const int m = min(PROXY_THREADS, e - c0);
+            for (int j = 0; j < m; ++j) {
+                const float* pj = sb[j];
+                const float* q = pj + 6 * TREE_MAXN;
+                for (int r = 0; r < PER; ++r) {
+                    const int k = threadIdx.x + r * PROXY_THREADS;
+                    if (k >= nprox) break;
+                    const int a = k / (n * n), bb = (k / n) % n, cc = k % n;
+                    const float lx = pj[a], ly = pj[TREE_MAXN + bb], lz = pj[2 * TREE_MAXN + cc];
+                    const float L = lx * ly * lz;
+                    acc[r][0] += L * q[0];
+                    if (raw) {
+                        const float gx = pj[3 * TREE_MAXN + a] * ly * lz, gy = lx * pj[4 * TREE_MAXN + bb] * lz,
+                                    gz = lx * ly * pj[5 * TREE_MAXN + cc];
+                        acc[r][1] += gx * q[1] + gy * q[2] + gz * q[3];
+                        for (int c = 0; c < 3; ++c) acc[r][2 + c] += L * q[4 + c];
+                        for (int c = 0; c < 3; ++c) acc[r][5 + c] += L * q[1 + c];
+                    } else {
+                        for (int c = 1; c < 8; ++c) acc[r][c] += L * q[c];
+                    }
+                }
+            }
+            __syncthreads();
+        }
+    }
+    for (int r = 0; r < PER; ++r) {
+        const int k = threadIdx.x + r * PROXY_THREADS;
+        if (k >= nprox) break;
+        const int a = k / (n * n), bb = (k / n) % n, cc = k % n;
+        float* o = prox + ((int64_t)slot * nprox + k) * TREE_REC;
+        o[0] = mid[0] + half[0] * cheb_node(a, n);
+        o[1] = mid[1] + half[1] * cheb_node(bb, n);
+        o[2] = mid[2] + half[2] * cheb_node(cc, n);
+        for (int c = 0; c < 8; ++c) o[3 + c] = acc[r][c];
+        o[11] = 0.f;
+    }
+}
+
+// One CTA per leaf of targets (one target per thread). Far: proxies of the
+// well-separated clusters (kernel G with the interpolated charges). Near:
+// the other sources directly, with the direct pair kernel's arithmetic.
+template <int MODE>
+__global__ void __launch_bounds__(TREE_LEAF)
+k_tree_eval(int64_t np, int nprox, const int32_t* __restrict__ perm, const int32_t* __restrict__ leaf_rng,
+            const int32_t* __restrict__ far_ptr, const int32_t* __restrict__ far_idx,
+            const int32_t* __restrict__ near_ptr, const int32_t* __restrict__ near_rng,
+            const float* __restrict__ rec, const float* __restrict__ prox, TreeCoef cf, float* __restrict__ part) {
+    constexpr int NACC = MODE == 0 ? 2 : 10;
+    constexpr int TILE = 128;
+    __shared__ __align__(16) float tile[TILE * TREE_REC];
+    const int leaf = blockIdx.x;
+    const int32_t tb = leaf_rng[2 * leaf], te = leaf_rng[2 * leaf + 1];
+    const int32_t ti = tb + (int32_t)threadIdx.x;
+    const bool live = ti < te;
+    float x0 = 0.f, x1 = 0.f, x2 = 0.f;
+    if (live) {
+        x0 = rec[TREE_REC * (int64_t)ti];
+        x1 = rec[TREE_REC * (int64_t)ti + 1];
+        x2 = rec[TREE_REC * (int64_t)ti + 2];
+    }
+    float acc[NACC];
+    for (int k = 0; k < NACC; ++k) acc[k] = 0.f;
+    // far clusters through their proxies
+    for (int32_t f = far_ptr[leaf]; f < far_ptr[leaf + 1]; ++f) {
+        const float* pr = prox + (int64_t)far_idx[f] * nprox * TREE_REC;
+        for (int c0 = 0; c0 < nprox; c0 += TILE) {
+            const int cnt = min(TILE, nprox - c0);
+            __syncthreads();
+            for (int k = threadIdx.x; k < cnt * TREE_REC / 4; k += blockDim.x)
+                reinterpret_cast<float4*>(tile)[k] = reinterpret_cast<const float4*>(pr + (int64_t)c0 * TREE_REC)[k];
+            __syncthreads();
+            if (!live) continue;
+            for (int j = 0; j < cnt; ++j) {
+                const float* z = tile + TREE_REC * j;
+                const float d0 = x0 - z[0], d1 = x1 - z[1], d2 = x2 - z[2];
+                const float r2 = fmaf(d0, d0, fmaf(d1, d1, d2 * d2));
+                const float rinv = t_rsqrt(r2);
+                const float rr = r2 * rinv;
+                const float e = t_ex2(rr * cf.mk2);
+                const float gs = rinv * z[3], gq = rinv * z[4];
+                acc[0] = fmaf(fmaf(cf.k[0][1], e, cf.k[0][0]), gs, acc[0]);
+                acc[0] = fmaf(fmaf(cf.k[0][3], e, cf.k[0][2]), gq, acc[0]);
+                if (MODE == 0) {
+                    acc[1] = fmaf(fmaf(cf.k[1][1], e, cf.k[1][0]), gs, acc[1]);
+                    acc[1] = fmaf(fmaf(cf.k[1][3], e, cf.k[1][2]), gq, acc[1]);
+                } else {
+                    const float ek = fmaf(e, rr * cf.kappa, e);
+                    const float ts = fmaf(cf.k[1][3], ek, cf.k[1][2]) * (rinv * rinv * rinv * z[3]);
+                    acc[1] = fmaf(ts, d0, acc[1]);
+                    acc[2] = fmaf(ts, d1, acc[2]);
+                    acc[3] = fmaf(ts, d2, acc[3]);
+                    const float gc = fmaf(cf.k[1][1], e, cf.k[1][0]) * rinv;
+                    acc[4] = fmaf(gc, z[5], acc[4]);
+                    acc[5] = fmaf(gc, z[6], acc[5]);
+                    acc[6] = fmaf(gc, z[7], acc[6]);
+                    const float gb = e * rinv;
+                    acc[7] = fmaf(gb, z[8], acc[7]);
+                    acc[8] = fmaf(gb, z[9], acc[8]);
+                    acc[9] = fmaf(gb, z[10], acc[9]);
+                }
+            }
+        }
+    }
+    // near sources directly (identical points skipped)
+    for (int32_t q = near_ptr[leaf]; q < near_ptr[leaf + 1]; ++q) {
+        const int32_t sb = near_rng[2 * q], se = near_rng[2 * q + 1];
+        for (int32_t c0 = sb; c0 < se; c0 += TILE) {
+            const int cnt = min(TILE, se - c0);
+            __syncthreads();
+            for (int k = threadIdx.x; k < cnt * TREE_REC / 4; k += blockDim.x)
+                reinterpret_cast<float4*>(tile)[k] = reinterpret_cast<const float4*>(rec + (int64_t)c0 * TREE_REC)[k];
+            __syncthreads();
+            if (!live) continue;
+            for (int j = 0; j < cnt; ++j) {
+                const float* y = tile + TREE_REC * j;
+                const float d0 = x0 - y[0], d1 = x1 - y[1], d2 = x2 - y[2];
+                const float r2 = fmaf(d0, d0, fmaf(d1, d1, d2 * d2));
+                const float rinv = r2 > 0.f ? t_rsqrt(r2) : 0.f;
+                const float rr = r2 * rinv;
+                const float e = t_ex2(rr * cf.mk2);
+                const float ek = fmaf(e, rr * cf.kappa, e);
+                const float rinv3 = rinv * rinv * rinv;
+                const float dp = fmaf(d0, y[4], fmaf(d1, y[5], d2 * y[6]));
+                const float rs = rinv * y[3], r3dp = rinv3 * dp;
+                acc[0] = fmaf(fmaf(cf.k[0][1], e, cf.k[0][0]), rs, acc[0]);
+                acc[0] = fmaf(fmaf(cf.k[0][3], ek, cf.k[0][2]), r3dp, acc[0]);
+                if (MODE == 0) {
+                    acc[1] = fmaf(fmaf(cf.k[1][1], e, cf.k[1][0]), rs, acc[1]);
+                    acc[1] = fmaf(fmaf(cf.k[1][3], ek, cf.k[1][2]), r3dp, acc[1]);
+                } else {
+                    const float ts = fmaf(cf.k[1][3], ek, cf.k[1][2]) * (rinv3 * y[3]);
+                    acc[1] = fmaf(ts, d0, acc[1]);
+                    acc[2] = fmaf(ts, d1, acc[2]);
+                    acc[3] = fmaf(ts, d2, acc[3]);
+                    const float gc = fmaf(cf.k[1][1], e, cf.k[1][0]) * rinv;
+                    acc[4] = fmaf(gc, y[7], acc[4]);
+                    acc[5] = fmaf(gc, y[8], acc[5]);
+                    acc[6] = fmaf(gc, y[9], acc[6]);
+                    const float gb = e * rinv;
+                    acc[7] = fmaf(gb, y[4], acc[7]);
+                    acc[8] = fmaf(gb, y[5], acc[8]);
+                    acc[9] = fmaf(gb, y[6], acc[9]);
+                }
+            }
+        }
+    }
+    if (live) {
+        const int64_t pt = perm[ti];
+        for (int k = 0; k < NACC; ++k) part[(int64_t)k * np + pt] = acc[k];
+    }
+}
+
+// y-part of the far field by the treecode into part (one split, the direct
+// kernel's layout): builds the tree of the mesh on first use.
+int tree_far(const pb_mesh* mc, const FarPlan& fp, const double* x, bool need_u, bool need_v, float* part,
+             cudaStream_t s) {
+    pb_mesh* m = const_cast<pb_mesh*>(mc);
+    pb_ctx* ctx = m->ctx;
+    if (m->tree && (m->tree->n != ctx->tree_order + 1 || m->tree->theta != ctx->tree_theta)) {
+        tree_free(m->tree);  // the settings changed: a new tree (captured graphs must not keep the old one)
+        m->tree = nullptr;
+        ws_bump();
+    }
+    if (!m->tree) PB_TRY(build_tree(m, ctx->tree_order, ctx->tree_theta, &m->tree));
+    PbTree* t = m->tree;
+    const int64_t np = m->np, nv = m->nv;
+    PB_TRY(ws_reserve(m->ws_tree, sizeof(float) * TREE_REC * (np + (size_t)t->nslot * t->nprox) + 256));
+    float* rec = (float*)m->ws_tree.ptr;
+    float* prox = rec + TREE_REC * np;
+    k_tree_sources<<<(unsigned)((np + 127) / 128), 128, 0, s>>>(np, m->Q, mesh_rule(m), t->perm, m->tris, m->tgeo,
+                                                                m->pts64, m->pts32, x, x + nv, need_u, need_v, rec);
+    ::pb::count_launch();
+    for (size_t h = 0; h + 1 < t->height_ptr.size(); ++h) {  // children's proxies before their parents'
+        const int64_t b = t->height_ptr[h], e = t->height_ptr[h + 1];
+        if (e > b) {
+            k_proxy_charges<<<(unsigned)(e - b), PROXY_THREADS, 0, s>>>(t->n, t->slot_order + b, t->slot_kids,
+                                                                        t->slot_box, rec, prox);
+            ::pb::count_launch();
+        }
+    }
+    TreeCoef cf;
+    for (int R = 0; R < 2; ++R)
+        for (int j = 0; j < 4; ++j) cf.k[R][j] = (float)fp.k[R][j];
+    cf.kappa = (float)fp.kappa;
+    cf.mk2 = (float)(-fp.kappa * 1.4426950408889634);
+    Timer tm(ctx, PB_KERNEL_TREE32, s, (double)(t->direct_pairs + t->proxy_pairs),
+             fp.mode == 0 ? 25.0 : 36.0);
+    if (fp.mode == 0)
+        k_tree_eval<0><<<(unsigned)t->nleaf, TREE_LEAF, 0, s>>>(np, t->nprox, t->perm, t->leaf_rng, t->far_ptr,
+                                                                t->far_idx, t->near_ptr, t->near_rng, rec, prox, cf,
+                                                                part);
+    else
+        k_tree_eval<1><<<(unsigned)t->nleaf, TREE_LEAF, 0, s>>>(np, t->nprox, t->perm, t->leaf_rng, t->far_ptr,
+                                                                t->far_idx, t->near_ptr, t->near_rng, rec, prox, cf,
+                                                                part);
+    ::pb::count_launch();
+    tm.stop();
+    PB_CUDA(cudaGetLastError());
+    return PB_OK;
+}
+
+int tree_info(const pb_mesh* m, int64_t out[6]) {
+    const PbTree* t = m->tree;
+    if (!t) return set_error(PB_EINVAL, "pb_tree_info: the mesh has no tree (no treecode application yet)");
+    out[0] = t->nleaf;
+    out[1] = t->nslot;
+    out[2] = t->n_far;
+    out[3] = t->n_near;
+    out[4] = t->direct_pairs;
+    out[5] = t->proxy_pairs;
+    return PB_OK;
+}
+
+}  // namespace pb

@@ -89,6 +89,8 @@ SIGNATURES = {
     "pb_launch_count": [],
     "pb_selftest_wait": [P, c_int64, ctypes.POINTER(c_int)],
     "pb_set_graphs": [P, c_int],
+    "pb_set_treecode": [P, c_int, c_int, c_double, c_int64],
+    "pb_tree_info": [P, ctypes.POINTER(c_int64)],
 }
 _RESTYPE = {"pb_last_error": c_char_p, "pb_version": c_char_p, "pb_launch_count": c_int64}
 
