@@ -15,7 +15,8 @@
 //
 // Each request keeps the split decomposition it has alone, and all its
 // reductions run in a fixed order, so its result does not depend on what
-// else is in the batch.
+// else is in the batch. Requests large enough for the treecode (FP32 inner
+// iterations) take it on their own instead of the batched launch.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -123,6 +124,8 @@ static size_t footprint(pb_ctx* ctx, int64_t nv, int64_t nt, const pb_quad_plan&
     int S = far_splits_estimate(ctx, (int64_t)np);
     double part = (double)S * 10 * np * 8;
     double work = src + part + 48 * nt + 48 * nnz + 128 * nv;
+    if (ctx->tree_enable && np >= (double)ctx->tree_min_points)
+        work += 330 * np;  // treecode: tree-ordered sources, proxies of about np / 64 clusters, lists
     double n2 = 2.0 * nv;
     double nchunk = std::ceil(n2 / 2048.0);
     double gm = 8 * ((mmax + 1) * n2 + n2 + (double)(mmax + 1) * mmax + 4 * mmax + 2 + (mmax + 2) * nchunk + 16);
@@ -218,6 +221,27 @@ static void admission_loop(pb_server* srv) {
     }
 }
 
+// The operator applications of one round: FP32 applications of meshes large
+// enough for the treecode go through it one request at a time (such a request
+// fills the GPU by itself); everything else in one batched launch per
+// precision. The path a request takes depends only on its own size, so its
+// result does not depend on the batch.
+static int apply_round(pb_server* srv, std::vector<FarJob>* jobs, cudaStream_t s) {
+    const pb_ctx* ctx = srv->ctx;
+    std::vector<FarJob> rest;
+    for (int p = 0; p < 4; ++p) {
+        rest.clear();
+        for (const FarJob& j : jobs[p]) {
+            if (p == PB_F32 && ctx->tree_enable && j.m->np >= ctx->tree_min_points && j.m->np > 256)
+                PB_TRY(apply_blockop(j.m, j.nf, j.B, PB_F32, j.x, j.y, s));
+            else
+                rest.push_back(j);
+        }
+        PB_TRY(apply_blockops_batched(rest, p, srv->bs, s));
+    }
+    return PB_OK;
+}
+
 static int tick(pb_server* srv) {
     {
         std::lock_guard<std::mutex> lock(srv->mu);
@@ -260,7 +284,7 @@ static int tick(pb_server* srv) {
         else if (r->phase == PH_START && r->mixed && r->outer > 0)
             jobs[res_prec(r)].push_back({r->m, r->nf, r->S.A, r->x, r->S.t3});
     }
-    for (int p = 0; p < 4; ++p) PB_TRY(apply_blockops_batched(jobs[p], p, srv->bs, s));
+    PB_TRY(apply_round(srv, jobs, s));
     for (auto& v : jobs) v.clear();
     // preconditioner input; Calderon requests queue their second operator
     std::vector<const double*> pin(n, nullptr);
@@ -291,7 +315,7 @@ static int tick(pb_server* srv) {
             PB_TRY(apply_prec(r->S, prec, pin[k], r->w));
         }
     }
-    for (int p = 0; p < 4; ++p) PB_TRY(apply_blockops_batched(jobs[p], p, srv->bs, s));
+    PB_TRY(apply_round(srv, jobs, s));
     for (int k = 0; k < n; ++k) {
         ServeReq* r = act[k];
         if (!pin[k]) continue;
