@@ -255,6 +255,16 @@ int pb_solve_pc(pb_ctx* ctx, const pb_mesh* mesh, const pb_near* near, const pb_
                 const pb_near* pc_near, const pb_params* prm, int form, int precond, const pb_solve_opts* opts,
                 const double* rhs, double* x, pb_solve_info* info, void* stream);
 
+/* y = P^-1 x: the preconditioner of pb_solve for formulation `form` and
+ * preconditioner `precond` (paper, "Preconditioning": block diagonal, mass,
+ * scaled mass and the Calderon products, with the mass inverse by the same
+ * Chebyshev iteration), operator applications in precision prec (PB_F64 or
+ * PB_F32). opts supplies alpha, beta (CFIE) and pc_a, pc_b (scalings; NULL =
+ * defaults). x and y: device, 2*N_v, not overlapping. Used with
+ * pb_system_apply to form P^-1 A for spectra (paper, eigenvalue figures). */
+int pb_precond_apply(pb_ctx* ctx, const pb_mesh* mesh, const pb_near* near, const pb_params* prm, int form,
+                     int precond, const pb_solve_opts* opts, int prec, const double* x, double* y, void* stream);
+
 /* ---- a10: reaction potential and solvation energy ------------------------ */
 /* phi_reac(x_j) = V_int[v_int](x_j) - K_int[u_int](x_j) (paper eq.
  * phireac_bie) from the solution x of formulation `form` (exterior forms are

@@ -266,6 +266,18 @@ def pb_solve(ctx: Ctx, mesh: Mesh, near: Near, params: Params, form, precond, rh
     return x, d
 
 
+def pb_precond_apply(ctx: Ctx, mesh: Mesh, near: Near, params: Params, form, precond, x: torch.Tensor,
+                     y: torch.Tensor | None = None, opts=None, prec: int = PB_F64, stream=None):
+    """y = P^-1 x with the preconditioner pb_solve uses."""
+    if y is None:
+        y = torch.empty_like(x)
+    p = params.c()
+    o = opts if opts is not None else solve_opts()
+    _check(N.load().pb_precond_apply(ctx.ptr, mesh.ptr, near.ptr, ctypes.byref(p), _form(form), _prec(precond),
+                                     ctypes.byref(o), int(prec), _dptr(x, "x"), _dptr(y, "y"), _stream(stream)))
+    return y
+
+
 def pb_solve_pc(ctx: Ctx, mesh: Mesh, near: Near, pc_mesh: Mesh, pc_near: Near, params: Params, form, precond,
                 rhs: torch.Tensor, x: torch.Tensor | None = None, opts=None, stream=None,
                 raise_on_noconv: bool = True):

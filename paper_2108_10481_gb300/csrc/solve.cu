@@ -777,6 +777,21 @@ extern "C" int pb_solve(pb_ctx* ctx, const pb_mesh* m, const pb_near* nf, const 
     return solve_impl(ctx, m, nf, prm, form, pc, opts, rhs, x, info, (cudaStream_t)stream);
 }
 
+extern "C" int pb_precond_apply(pb_ctx* ctx, const pb_mesh* m, const pb_near* nf, const pb_params* prm, int form,
+                                int pc, const pb_solve_opts* opts, int prec, const double* x, double* y,
+                                void* stream) {
+    PB_TRY(apply_args_ok(ctx, m, nf, x, y));
+    if (!prm) return set_error(PB_EINVAL, "NULL params");
+    if (x == y) return set_error(PB_EINVAL, "x and y must not overlap");
+    if (prec != PB_F64 && prec != PB_F32) return set_error(PB_EINVAL, "precision must be PB_F64 or PB_F32");
+    PB_CUDA(cudaSetDevice(ctx->device));
+    Solver S;
+    PB_TRY(setup_solver(S, m, nf, prm, form, pc, opts, (cudaStream_t)stream));
+    const int rc = apply_prec(S, prec, x, y);
+    solver_release(S);
+    return rc;
+}
+
 // Fast Calderon (paper, "Fast Calderon preconditioning"): the preconditioner's
 // operator from a second plan of the same surface.
 extern "C" int pb_solve_pc(pb_ctx* ctx, const pb_mesh* m, const pb_near* nf, const pb_mesh* mc, const pb_near* nc,
