@@ -244,6 +244,15 @@ int pb_rhs_charges(pb_ctx* ctx, const pb_mesh* mesh, const double* xq, const dou
 int pb_solve(pb_ctx* ctx, const pb_mesh* mesh, const pb_near* near, const pb_params* prm, int form,
              int precond, const pb_solve_opts* opts, const double* rhs, double* x,
              pb_solve_info* info, void* stream);
+/* pb_solve for nrhs right-hand sides of the same system (paper: fast solves
+ * pay off for many right-hand sides, e.g. the charge sets of pKa
+ * calculations): rhs and x hold nrhs vectors of 2*N_v one after another
+ * (device), info (optional) nrhs records. The solver is set up once and the
+ * Krylov workspace and captured iteration graphs serve every right-hand side.
+ * Returns PB_ENOCONV when any did not converge (its info says which). */
+int pb_solve_many(pb_ctx* ctx, const pb_mesh* mesh, const pb_near* near, const pb_params* prm, int form,
+                  int precond, const pb_solve_opts* opts, int nrhs, const double* rhs, double* x,
+                  pb_solve_info* info, void* stream);
 /* pb_solve with the Calderon preconditioner's operator taken from a second
  * discretisation of the same surface (paper, "Fast Calderon preconditioning":
  * relaxed quadrature orders for the preconditioner only, e.g. the 1-point far

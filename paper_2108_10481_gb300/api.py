@@ -266,6 +266,24 @@ def pb_solve(ctx: Ctx, mesh: Mesh, near: Near, params: Params, form, precond, rh
     return x, d
 
 
+def pb_solve_many(ctx: Ctx, mesh: Mesh, near: Near, params: Params, form, precond, rhs: torch.Tensor,
+                  x: torch.Tensor | None = None, opts=None, stream=None, raise_on_noconv: bool = True):
+    """rhs: [K, 2 N_v] device tensor of K right-hand sides. Returns (x [K, 2 N_v], list of K info dicts)."""
+    rhs = rhs.contiguous()
+    if x is None:
+        x = torch.empty_like(rhs)
+    k = rhs.shape[0]
+    p = params.c()
+    o = opts if opts is not None else solve_opts()
+    infos = (N.pb_solve_info * k)()
+    rc = N.load().pb_solve_many(ctx.ptr, mesh.ptr, near.ptr, ctypes.byref(p), _form(form), _prec(precond),
+                                ctypes.byref(o), int(k), _dptr(rhs, "rhs"), _dptr(x, "x"), infos, _stream(stream))
+    d = [{f: getattr(infos[i], f) for f, _ in N.pb_solve_info._fields_} for i in range(k)]
+    if rc != PB_OK and (raise_on_noconv or rc != PB_ENOCONV):
+        _check(rc)
+    return x, d
+
+
 def pb_precond_apply(ctx: Ctx, mesh: Mesh, near: Near, params: Params, form, precond, x: torch.Tensor,
                      y: torch.Tensor | None = None, opts=None, prec: int = PB_F64, stream=None):
     """y = P^-1 x with the preconditioner pb_solve uses."""

@@ -595,15 +595,15 @@ void vec_add(int64_t n, const double* a, double* y, cudaStream_t s) {
 }
 
 static int solve_body(pb_ctx* ctx, const pb_mesh* m, const pb_near* nf, const pb_params* prm, int form, int pc,
-                      const pb_solve_opts* o, const double* b, double* x, pb_solve_info* info, cudaStream_t s,
-                      Solver& S, const pb_mesh* mc, const pb_near* nc);
+                      const pb_solve_opts* o, int nrhs, const double* b, double* x, pb_solve_info* info,
+                      cudaStream_t s, Solver& S, const pb_mesh* mc, const pb_near* nc);
 
 // The solve runs on a stream of its own, ordered after the caller's stream
 // and before what the caller queues next: CUDA graphs cannot be captured on
 // the legacy default stream.
 static int solve_impl(pb_ctx* ctx, const pb_mesh* m, const pb_near* nf, const pb_params* prm, int form, int pc,
                       const pb_solve_opts* o, const double* b, double* x, pb_solve_info* info, cudaStream_t caller,
-                      const pb_mesh* mc = nullptr, const pb_near* nc = nullptr) {
+                      const pb_mesh* mc = nullptr, const pb_near* nc = nullptr, int nrhs = 1) {
     pb_solve_opts d = {1e-6, 500, 0, PB_F64, 1e-4, 20, 0, 0, 0, 0};
     if (!o) o = &d;
     if (!(o->tol > 0.0) || o->max_it < 1) return set_error(PB_EINVAL, "need tol > 0 and max_it >= 1");
@@ -618,7 +618,7 @@ static int solve_impl(pb_ctx* ctx, const pb_mesh* m, const pb_near* nf, const pb
     cudaEventRecord(fence, caller);
     cudaStreamWaitEvent(s, fence, 0);
     Solver S;
-    int rc = solve_body(ctx, m, nf, prm, form, pc, o, b, x, info, s, S, mc, nc);
+    int rc = solve_body(ctx, m, nf, prm, form, pc, o, nrhs, b, x, info, s, S, mc, nc);
     solver_release(S);
     cudaEventRecord(fence, s);
     cudaStreamWaitEvent(caller, fence, 0);
@@ -627,9 +627,14 @@ static int solve_impl(pb_ctx* ctx, const pb_mesh* m, const pb_near* nf, const pb
     return rc;
 }
 
+static int solve_one(const pb_mesh* m, const pb_near* nf, const pb_solve_opts* o, const double* b, double* x,
+                     pb_solve_info* info, cudaStream_t s, Solver& S, GmresWork& G, int mmax);
+
+// Solver set up once; the right-hand sides one after the other with the same
+// Krylov workspace and the same captured iteration graphs.
 static int solve_body(pb_ctx* ctx, const pb_mesh* m, const pb_near* nf, const pb_params* prm, int form, int pc,
-                      const pb_solve_opts* o, const double* b, double* x, pb_solve_info* info, cudaStream_t s,
-                      Solver& S, const pb_mesh* mc, const pb_near* nc) {
+                      const pb_solve_opts* o, int nrhs, const double* b, double* x, pb_solve_info* info,
+                      cudaStream_t s, Solver& S, const pb_mesh* mc, const pb_near* nc) {
     PB_TRY(setup_solver(S, m, nf, prm, form, pc, o, s));
     if (mc) {
         S.mc = mc;
@@ -640,6 +645,26 @@ static int solve_body(pb_ctx* ctx, const pb_mesh* m, const pb_near* nf, const pb
     int mmax = o->restart > 0 ? std::min(o->restart, o->max_it) : o->max_it;
     GmresWork G;
     PB_TRY(gmres_alloc(G, n2, mmax));
+    int worst = PB_OK;
+    for (int k = 0; k < nrhs; ++k) {
+        const int rc = solve_one(m, nf, o, b + (size_t)k * n2, x + (size_t)k * n2, info ? info + k : nullptr, s, S,
+                                 G, mmax);
+        if (rc != PB_OK && rc != PB_ENOCONV) {
+            gmres_free(G);
+            return rc;
+        }
+        if (rc != PB_OK) worst = rc;
+    }
+    gmres_free(G);
+    if (worst != PB_OK && nrhs > 1)
+        set_error(worst, "GMRES did not reach tol %g for every right-hand side (see the infos)", o->tol);
+    return worst;
+}
+
+static int solve_one(const pb_mesh* m, const pb_near* nf, const pb_solve_opts* o, const double* b, double* x,
+                     pb_solve_info* info, cudaStream_t s, Solver& S, GmresWork& G, int mmax) {
+    const int64_t n2 = 2 * m->nv;
+    const int applies0 = S.applies;
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
@@ -706,7 +731,6 @@ static int solve_body(pb_ctx* ctx, const pb_mesh* m, const pb_near* nf, const pb
     cudaEventElapsedTime(&ms, e0, e1);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    gmres_free(G);
     if (rc == PB_OK) rc = check_status(m, s);
     if (rc == PB_OK && !(rel <= o->tol)) rc = set_error(PB_ENOCONV, "GMRES did not reach tol %g (residual %g after %d "
                                                         "iterations)", o->tol, rel, total_it);
@@ -714,7 +738,7 @@ static int solve_body(pb_ctx* ctx, const pb_mesh* m, const pb_near* nf, const pb
         info->status = rc;
         info->iters = total_it;
         info->outer_iters = outer;
-        info->system_applies = S.applies;
+        info->system_applies = S.applies - applies0;
         info->rel_residual = rel;
         info->time_ms = ms;
     }
@@ -790,6 +814,19 @@ extern "C" int pb_precond_apply(pb_ctx* ctx, const pb_mesh* m, const pb_near* nf
     const int rc = apply_prec(S, prec, x, y);
     solver_release(S);
     return rc;
+}
+
+// Several right-hand sides of one system (one charge set each, e.g. the
+// protonation states of a pKa calculation): one solver set-up, one Krylov
+// workspace and one set of captured iteration graphs for all of them.
+extern "C" int pb_solve_many(pb_ctx* ctx, const pb_mesh* m, const pb_near* nf, const pb_params* prm, int form, int pc,
+                             const pb_solve_opts* opts, int nrhs, const double* rhs, double* x, pb_solve_info* info,
+                             void* stream) {
+    PB_TRY(apply_args_ok(ctx, m, nf, rhs, x));
+    if (!prm) return set_error(PB_EINVAL, "NULL params");
+    if (nrhs < 1) return set_error(PB_EINVAL, "pb_solve_many: need nrhs >= 1");
+    PB_CUDA(cudaSetDevice(ctx->device));
+    return solve_impl(ctx, m, nf, prm, form, pc, opts, rhs, x, info, (cudaStream_t)stream, nullptr, nullptr, nrhs);
 }
 
 // Fast Calderon (paper, "Fast Calderon preconditioning"): the preconditioner's

@@ -68,6 +68,8 @@ SIGNATURES = {
                  ctypes.POINTER(pb_solve_info), P],
     "pb_precond_apply": [P, P, P, ctypes.POINTER(pb_params), c_int, c_int, ctypes.POINTER(pb_solve_opts), c_int, P, P,
                          P],
+    "pb_solve_many": [P, P, P, ctypes.POINTER(pb_params), c_int, c_int, ctypes.POINTER(pb_solve_opts), c_int, P, P,
+                      P, P],
     "pb_solve_pc": [P, P, P, P, P, ctypes.POINTER(pb_params), c_int, c_int, ctypes.POINTER(pb_solve_opts), P, P,
                     ctypes.POINTER(pb_solve_info), P],
     "pb_energy": [P, P, P, c_int, P, P, c_int64, ctypes.POINTER(pb_params), P, ctypes.POINTER(c_double),
