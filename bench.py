@@ -71,7 +71,7 @@ def parse():
                     help="charge sets per molecule (pKa-style): mesh and near field built once per step, the "
                          "sets solved together with pb_solve_many; the rate counts charge-set solves")
     ap.add_argument("--far", default="auto", choices=["auto", "direct", "tree"],
-                    help="far field of the FP32 inner iterations: the library's default (treecode from 100k "
+                    help="far field of the FP32 inner iterations: the library's default (treecode from 50k "
                          "points on), direct pair sums, or the treecode at every size")
     ap.add_argument("--fast-calderon", action="store_true",
                     help="Calderon cases (20, 23): the preconditioner's operator with relaxed quadrature (1-point "
@@ -385,7 +385,7 @@ def run_ours(args, rank, world, local_rank):
     torch.cuda.synchronize()
     mv_ms = e0.elapsed_time(e1) / nmv
     npts = m.info()["n_points"]
-    uses_tree = args.far == "tree" or (args.far == "auto" and npts >= 100000)
+    uses_tree = args.far == "tree" or (args.far == "auto" and npts >= 50000)
     nf.free()
     m.free()
 

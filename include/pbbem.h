@@ -423,7 +423,7 @@ int pb_set_graphs(pb_ctx* ctx, int enable);
  * directly. The split-coordinate and FP64 applications (PB_MIXED's outer
  * residual, PB_F64 solves) stay direct, so mixed solves converge to the same
  * solution. order 2..7, theta in (0, 1]. Default: enabled, order 6, theta 0.7,
- * min_points 100000 (below that the direct sum is as fast on this GPU), or
+ * min_points 50000 (below that the direct sum is as fast on this GPU), or
  * disabled when the environment variable PBBEM_TREECODE=0 is set at pb_init.
  * The tree is built on the mesh's first
  * treecode application (host work and a device allocation; before any stream

@@ -144,7 +144,7 @@ def pb_launch_count() -> int:
     return int(N.load().pb_launch_count())
 
 
-def pb_set_treecode(ctx: Ctx, enable: bool = True, order: int = 6, theta: float = 0.7, min_points: int = 100000):
+def pb_set_treecode(ctx: Ctx, enable: bool = True, order: int = 6, theta: float = 0.7, min_points: int = 50000):
     """Treecode far field for FP32 applications of meshes with >= min_points far-rule points."""
     _check(N.load().pb_set_treecode(ctx.ptr, 1 if enable else 0, int(order), float(theta), int(min_points)))
 

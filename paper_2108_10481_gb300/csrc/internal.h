@@ -133,7 +133,7 @@ struct pb_ctx {
     int tree_enable = 1;           // on by default for meshes of at least tree_min_points points
     int tree_order = 6;            // Chebyshev points per dimension - 1
     double tree_theta = 0.7;       // separation: radius sum < theta x centre distance
-    int64_t tree_min_points = 100000;
+    int64_t tree_min_points = 50000;
 };
 
 struct pb_mesh {

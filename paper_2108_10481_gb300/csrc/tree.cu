@@ -150,8 +150,9 @@ static int build_tree(pb_mesh* m, int order, double theta, PbTree** out) {
         }
         if (nd.c0 < 0) leaves.push_back((int32_t)k);
     }
-    // children of every slot (a slot always has two: it holds more points than a leaf), and the
-    // slots ordered by height so that children's proxies exist before their parents'
+    // children of every slot, and the slots ordered by height so that children's proxies exist
+    // before their parents'. A slot that is a leaf (fewer points per leaf than proxies) takes
+    // its own points as one raw child.
     const int64_t nslot = (int64_t)(slot_rng.size() / 2);
     std::vector<int32_t> slot_kids(6 * nslot), height(nslot, 0), slot_node(nslot);
     for (size_t k = 0; k < nodes.size(); ++k)
@@ -159,6 +160,12 @@ static int build_tree(pb_mesh* m, int order, double theta, PbTree** out) {
     // nodes were created parents before children: a reverse sweep sees children first
     for (int64_t sl = nslot - 1; sl >= 0; --sl) {
         const HostNode& nd = nodes[slot_node[sl]];
+        if (nd.c0 < 0) {
+            const int32_t own[6] = {-1, nd.b, nd.e, -1, nd.e, nd.e};
+            for (int c = 0; c < 6; ++c) slot_kids[6 * sl + c] = own[c];
+            height[sl] = 0;
+            continue;
+        }
         const int32_t kids[2] = {nd.c0, nd.c1};
         int h = 0;
         for (int c = 0; c < 2; ++c) {
@@ -334,7 +341,11 @@ constexpr int PROXY_THREADS = 128;
 __global__ void __launch_bounds__(PROXY_THREADS)
 k_proxy_charges(int n, const int32_t* __restrict__ slots, const int32_t* __restrict__ slot_kids,
                 const float* __restrict__ slot_box, const float* __restrict__ rec, float* __restrict__ prox) {
-    __shared__ float sb[PROXY_THREADS][6 * TREE_MAXN + 8];  // lx, ly, lz, dlx, dly, dlz; 8 charges
+    // staging of 128 points (lx, ly, lz, dlx, dly, dlz; 8 charges), or two n^3 x 8 buffers of the transfer
+    constexpr int SBW = 64;
+    static_assert(SBW >= 6 * TREE_MAXN + 8, "staging row");
+    static_assert(PROXY_THREADS * SBW >= 2 * TREE_MAXN * TREE_MAXN * TREE_MAXN * 8, "transfer buffers");
+    __shared__ float sb[PROXY_THREADS][SBW];
     const int slot = slots[blockIdx.x];
     const int nprox = n * n * n;
     const float* box = slot_box + 6 * slot;
@@ -347,9 +358,55 @@ k_proxy_charges(int n, const int32_t* __restrict__ slots, const int32_t* __restr
     float acc[PER][8];
     for (int r = 0; r < PER; ++r)
         for (int c = 0; c < 8; ++c) acc[r][c] = 0.f;
+    __shared__ float T[3][TREE_MAXN][TREE_MAXN];  // 1-D transfer matrices of a child with proxies
+    float* buf0 = &sb[0][0];                          // child charges, then the y pass
+    float* buf1 = buf0 + TREE_MAXN * TREE_MAXN * TREE_MAXN * 8;  // the x pass
     for (int kid = 0; kid < 2; ++kid) {
         const int32_t ks = slot_kids[6 * slot + 3 * kid];
         const bool raw = ks < 0;  // uniform across the block
+        if (!raw) {
+            // A child with proxies: its charges sit on the tensor grid of its box, so the transfer
+            // to this slot's grid is a tensor product of three n x n matrices
+            // T_d[a][a'] = l_a(child node a' in this slot's coordinates), applied one axis at a time.
+            const float* cb = slot_box + 6 * ks;
+            if (threadIdx.x < 3 * n) {
+                const int d = threadIdx.x / n, a2 = threadIdx.x % n;
+                const float zc = 0.5f * (cb[d] + cb[3 + d]) + 0.5f * (cb[3 + d] - cb[d]) * cheb_node(a2, n);
+                float l[TREE_MAXN], dl[TREE_MAXN];
+                lagrange1((zc - mid[d]) / half[d], n, l, dl);
+                for (int a = 0; a < n; ++a) T[d][a][a2] = l[a];
+            }
+            const float* cp = prox + (int64_t)ks * nprox * TREE_REC;
+            for (int k = threadIdx.x; k < nprox * 8; k += PROXY_THREADS) buf0[k] = cp[(k >> 3) * TREE_REC + 3 + (k & 7)];
+            __syncthreads();
+            const int n2 = n * n;
+            for (int k = threadIdx.x; k < nprox * 8; k += PROXY_THREADS) {  // x pass
+                const int c = k & 7, idx = k >> 3, a = idx / n2, rest = idx - a * n2;
+                float v = 0.f;
+                for (int a2 = 0; a2 < n; ++a2) v += T[0][a][a2] * buf0[(a2 * n2 + rest) * 8 + c];
+                buf1[k] = v;
+            }
+            __syncthreads();
+            for (int k = threadIdx.x; k < nprox * 8; k += PROXY_THREADS) {  // y pass
+                const int c = k & 7, idx = k >> 3, a = idx / n2, bb = (idx / n) % n, cc = idx % n;
+                float v = 0.f;
+                for (int b2 = 0; b2 < n; ++b2) v += T[1][bb][b2] * buf1[((a * n + b2) * n + cc) * 8 + c];
+                buf0[k] = v;
+            }
+            __syncthreads();
+            for (int r = 0; r < PER; ++r) {  // z pass into this thread's proxies
+                const int k = threadIdx.x + r * PROXY_THREADS;
+                if (k >= nprox) break;
+                const int a = k / n2, bb = (k / n) % n, cc = k % n;
+                for (int c = 0; c < 8; ++c) {
+                    float v = 0.f;
+                    for (int c2 = 0; c2 < n; ++c2) v += T[2][cc][c2] * buf0[((a * n + bb) * n + c2) * 8 + c];
+                    acc[r][c] += v;
+                }
+            }
+            __syncthreads();
+            continue;
+        }
         const int32_t b = raw ? slot_kids[6 * slot + 3 * kid + 1] : 0;
         const int32_t e = raw ? slot_kids[6 * slot + 3 * kid + 2] : nprox;
         const float* src = raw ? rec : prox + (int64_t)ks * nprox * TREE_REC;

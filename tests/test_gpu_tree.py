@@ -44,6 +44,7 @@ def test_tree_application_accuracy(pb, sphere, form):
     P = pb.Params(4.0, 80.0, 0.125)
     x = torch.randn(2 * m.info()["n_verts"], dtype=torch.float64, device="cuda")
     ref = pb.pb_system_apply(ctx, m, nf, P, form, x, pb.PB_F64)
+    pb.pb_set_treecode(ctx, False)
     direct32 = pb.pb_system_apply(ctx, m, nf, P, form, x, pb.PB_F32)
     errs = {}
     for order in (3, 6):
