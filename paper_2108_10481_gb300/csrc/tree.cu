@@ -462,11 +462,40 @@ k_proxy_charges(int n, const int32_t* __restrict__ slots, const int32_t* __restr
     }
 }
 
-// One CTA per leaf of targets (one target per thread). Far: proxies of the
-// well-separated clusters (kernel G with the interpolated charges). Near:
-// the other sources directly, with the direct pair kernel's arithmetic.
+// Packed pairs of FP32 values (f32x2 instructions: two targets per thread).
+__device__ __forceinline__ float2 t_sub2(float2 a, float2 b) {
+    float2 d;
+    asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n sub.rn.f32x2 rd, ra, rb;\n"
+        " mov.b64 {%0, %1}, rd;\n}\n" : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 t_mul2(float2 a, float2 b) {
+    float2 d;
+    asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n mul.rn.f32x2 rd, ra, rb;\n"
+        " mov.b64 {%0, %1}, rd;\n}\n" : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 t_fma2(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("{\n .reg .b64 ra, rb, rc, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n mov.b64 rc, {%6, %7};\n"
+        " fma.rn.f32x2 rd, ra, rb, rc;\n mov.b64 {%0, %1}, rd;\n}\n"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+__device__ __forceinline__ float2 t_splat(float v) { return make_float2(v, v); }
+
+// One CTA per leaf of targets, TREE_LEAF threads in two halves. A thread holds
+// two targets (the leaf's i-th and (i + TREE_LEAF/2)-th points) in packed
+// f32x2 arithmetic; the two halves take alternate sources of every staged
+// tile and add their sums through shared memory at the end.
+// Far: proxies of the well-separated clusters (kernel G with the interpolated
+// charges). Near: the other sources directly, with the direct pair kernel's
+// arithmetic (identical points skipped).
+constexpr int TREE_TPB = TREE_LEAF;
+constexpr int TREE_HALF = TREE_LEAF / 2;
+
 template <int MODE>
-__global__ void __launch_bounds__(TREE_LEAF)
+__global__ void __launch_bounds__(TREE_TPB)
 k_tree_eval(int64_t np, int nprox, const int32_t* __restrict__ perm, const int32_t* __restrict__ leaf_rng,
             const int32_t* __restrict__ far_ptr, const int32_t* __restrict__ far_idx,
             const int32_t* __restrict__ near_ptr, const int32_t* __restrict__ near_rng,
@@ -476,16 +505,27 @@ k_tree_eval(int64_t np, int nprox, const int32_t* __restrict__ perm, const int32
     __shared__ __align__(16) float tile[TILE * TREE_REC];
     const int leaf = blockIdx.x;
     const int32_t tb = leaf_rng[2 * leaf], te = leaf_rng[2 * leaf + 1];
-    const int32_t ti = tb + (int32_t)threadIdx.x;
-    const bool live = ti < te;
-    float x0 = 0.f, x1 = 0.f, x2 = 0.f;
-    if (live) {
-        x0 = rec[TREE_REC * (int64_t)ti];
-        x1 = rec[TREE_REC * (int64_t)ti + 1];
-        x2 = rec[TREE_REC * (int64_t)ti + 2];
+    const int half = (int)threadIdx.x / TREE_HALF;
+    const int32_t ti0 = tb + (int32_t)(threadIdx.x % TREE_HALF), ti1 = ti0 + TREE_HALF;
+    const bool live0 = ti0 < te, live1 = ti1 < te;
+    float2 X0 = t_splat(0.f), X1 = X0, X2 = X0;
+    if (live0) {
+        X0.x = rec[TREE_REC * (int64_t)ti0];
+        X1.x = rec[TREE_REC * (int64_t)ti0 + 1];
+        X2.x = rec[TREE_REC * (int64_t)ti0 + 2];
     }
-    float acc[NACC];
-    for (int k = 0; k < NACC; ++k) acc[k] = 0.f;
+    if (live1) {
+        X0.y = rec[TREE_REC * (int64_t)ti1];
+        X1.y = rec[TREE_REC * (int64_t)ti1 + 1];
+        X2.y = rec[TREE_REC * (int64_t)ti1 + 2];
+    }
+    const float2 c00 = t_splat(cf.k[0][0]), c01 = t_splat(cf.k[0][1]), c02 = t_splat(cf.k[0][2]),
+                 c03 = t_splat(cf.k[0][3]), c10 = t_splat(cf.k[1][0]), c11 = t_splat(cf.k[1][1]),
+                 c12 = t_splat(cf.k[1][2]), c13 = t_splat(cf.k[1][3]), kap = t_splat(cf.kappa),
+                 mk2 = t_splat(cf.mk2);
+    float2 acc[NACC];
+    for (int k = 0; k < NACC; ++k) acc[k] = t_splat(0.f);
+    const bool any = live0;  // the first target of a thread is live whenever the second is
     // far clusters through their proxies
     for (int32_t f = far_ptr[leaf]; f < far_ptr[leaf + 1]; ++f) {
         const float* pr = prox + (int64_t)far_idx[f] * nprox * TREE_REC;
@@ -495,34 +535,37 @@ k_tree_eval(int64_t np, int nprox, const int32_t* __restrict__ perm, const int32
             for (int k = threadIdx.x; k < cnt * TREE_REC / 4; k += blockDim.x)
                 reinterpret_cast<float4*>(tile)[k] = reinterpret_cast<const float4*>(pr + (int64_t)c0 * TREE_REC)[k];
             __syncthreads();
-            if (!live) continue;
-            for (int j = 0; j < cnt; ++j) {
+            if (!any) continue;
+#pragma unroll 2
+            for (int j = half; j < cnt; j += 2) {
                 const float* z = tile + TREE_REC * j;
-                const float d0 = x0 - z[0], d1 = x1 - z[1], d2 = x2 - z[2];
-                const float r2 = fmaf(d0, d0, fmaf(d1, d1, d2 * d2));
-                const float rinv = t_rsqrt(r2);
-                const float rr = r2 * rinv;
-                const float e = t_ex2(rr * cf.mk2);
-                const float gs = rinv * z[3], gq = rinv * z[4];
-                acc[0] = fmaf(fmaf(cf.k[0][1], e, cf.k[0][0]), gs, acc[0]);
-                acc[0] = fmaf(fmaf(cf.k[0][3], e, cf.k[0][2]), gq, acc[0]);
+                const float2 d0 = t_sub2(X0, t_splat(z[0])), d1 = t_sub2(X1, t_splat(z[1])),
+                             d2 = t_sub2(X2, t_splat(z[2]));
+                const float2 r2 = t_fma2(d0, d0, t_fma2(d1, d1, t_mul2(d2, d2)));
+                const float2 rinv = make_float2(t_rsqrt(r2.x), t_rsqrt(r2.y));
+                const float2 rr = t_mul2(r2, rinv);
+                const float2 arg = t_mul2(rr, mk2);
+                const float2 e = make_float2(t_ex2(arg.x), t_ex2(arg.y));
+                const float2 gs = t_mul2(rinv, t_splat(z[3])), gq = t_mul2(rinv, t_splat(z[4]));
+                acc[0] = t_fma2(t_fma2(c01, e, c00), gs, acc[0]);
+                acc[0] = t_fma2(t_fma2(c03, e, c02), gq, acc[0]);
                 if (MODE == 0) {
-                    acc[1] = fmaf(fmaf(cf.k[1][1], e, cf.k[1][0]), gs, acc[1]);
-                    acc[1] = fmaf(fmaf(cf.k[1][3], e, cf.k[1][2]), gq, acc[1]);
+                    acc[1] = t_fma2(t_fma2(c11, e, c10), gs, acc[1]);
+                    acc[1] = t_fma2(t_fma2(c13, e, c12), gq, acc[1]);
                 } else {
-                    const float ek = fmaf(e, rr * cf.kappa, e);
-                    const float ts = fmaf(cf.k[1][3], ek, cf.k[1][2]) * (rinv * rinv * rinv * z[3]);
-                    acc[1] = fmaf(ts, d0, acc[1]);
-                    acc[2] = fmaf(ts, d1, acc[2]);
-                    acc[3] = fmaf(ts, d2, acc[3]);
-                    const float gc = fmaf(cf.k[1][1], e, cf.k[1][0]) * rinv;
-                    acc[4] = fmaf(gc, z[5], acc[4]);
-                    acc[5] = fmaf(gc, z[6], acc[5]);
-                    acc[6] = fmaf(gc, z[7], acc[6]);
-                    const float gb = e * rinv;
-                    acc[7] = fmaf(gb, z[8], acc[7]);
-                    acc[8] = fmaf(gb, z[9], acc[8]);
-                    acc[9] = fmaf(gb, z[10], acc[9]);
+                    const float2 ek = t_fma2(e, t_mul2(rr, kap), e);
+                    const float2 ts = t_mul2(t_fma2(c13, ek, c12), t_mul2(t_mul2(rinv, rinv), gs));
+                    acc[1] = t_fma2(ts, d0, acc[1]);
+                    acc[2] = t_fma2(ts, d1, acc[2]);
+                    acc[3] = t_fma2(ts, d2, acc[3]);
+                    const float2 gc = t_mul2(t_fma2(c11, e, c10), rinv);
+                    acc[4] = t_fma2(gc, t_splat(z[5]), acc[4]);
+                    acc[5] = t_fma2(gc, t_splat(z[6]), acc[5]);
+                    acc[6] = t_fma2(gc, t_splat(z[7]), acc[6]);
+                    const float2 gb = t_mul2(e, rinv);
+                    acc[7] = t_fma2(gb, t_splat(z[8]), acc[7]);
+                    acc[8] = t_fma2(gb, t_splat(z[9]), acc[8]);
+                    acc[9] = t_fma2(gb, t_splat(z[10]), acc[9]);
                 }
             }
         }
@@ -536,43 +579,65 @@ k_tree_eval(int64_t np, int nprox, const int32_t* __restrict__ perm, const int32
             for (int k = threadIdx.x; k < cnt * TREE_REC / 4; k += blockDim.x)
                 reinterpret_cast<float4*>(tile)[k] = reinterpret_cast<const float4*>(rec + (int64_t)c0 * TREE_REC)[k];
             __syncthreads();
-            if (!live) continue;
-            for (int j = 0; j < cnt; ++j) {
+            if (!any) continue;
+#pragma unroll 2
+            for (int j = half; j < cnt; j += 2) {
                 const float* y = tile + TREE_REC * j;
-                const float d0 = x0 - y[0], d1 = x1 - y[1], d2 = x2 - y[2];
-                const float r2 = fmaf(d0, d0, fmaf(d1, d1, d2 * d2));
-                const float rinv = r2 > 0.f ? t_rsqrt(r2) : 0.f;
-                const float rr = r2 * rinv;
-                const float e = t_ex2(rr * cf.mk2);
-                const float ek = fmaf(e, rr * cf.kappa, e);
-                const float rinv3 = rinv * rinv * rinv;
-                const float dp = fmaf(d0, y[4], fmaf(d1, y[5], d2 * y[6]));
-                const float rs = rinv * y[3], r3dp = rinv3 * dp;
-                acc[0] = fmaf(fmaf(cf.k[0][1], e, cf.k[0][0]), rs, acc[0]);
-                acc[0] = fmaf(fmaf(cf.k[0][3], ek, cf.k[0][2]), r3dp, acc[0]);
+                const float2 d0 = t_sub2(X0, t_splat(y[0])), d1 = t_sub2(X1, t_splat(y[1])),
+                             d2 = t_sub2(X2, t_splat(y[2]));
+                const float2 r2 = t_fma2(d0, d0, t_fma2(d1, d1, t_mul2(d2, d2)));
+                const float2 rinv = make_float2(r2.x > 0.f ? t_rsqrt(r2.x) : 0.f, r2.y > 0.f ? t_rsqrt(r2.y) : 0.f);
+                const float2 rr = t_mul2(r2, rinv);
+                const float2 arg = t_mul2(rr, mk2);
+                const float2 e = make_float2(t_ex2(arg.x), t_ex2(arg.y));
+                const float2 ek = t_fma2(e, t_mul2(rr, kap), e);
+                const float2 rinv3 = t_mul2(t_mul2(rinv, rinv), rinv);
+                const float2 dp = t_fma2(d0, t_splat(y[4]), t_fma2(d1, t_splat(y[5]), t_mul2(d2, t_splat(y[6]))));
+                const float2 rs = t_mul2(rinv, t_splat(y[3])), r3dp = t_mul2(rinv3, dp);
+                acc[0] = t_fma2(t_fma2(c01, e, c00), rs, acc[0]);
+                acc[0] = t_fma2(t_fma2(c03, ek, c02), r3dp, acc[0]);
                 if (MODE == 0) {
-                    acc[1] = fmaf(fmaf(cf.k[1][1], e, cf.k[1][0]), rs, acc[1]);
-                    acc[1] = fmaf(fmaf(cf.k[1][3], ek, cf.k[1][2]), r3dp, acc[1]);
+                    acc[1] = t_fma2(t_fma2(c11, e, c10), rs, acc[1]);
+                    acc[1] = t_fma2(t_fma2(c13, ek, c12), r3dp, acc[1]);
                 } else {
-                    const float ts = fmaf(cf.k[1][3], ek, cf.k[1][2]) * (rinv3 * y[3]);
-                    acc[1] = fmaf(ts, d0, acc[1]);
-                    acc[2] = fmaf(ts, d1, acc[2]);
-                    acc[3] = fmaf(ts, d2, acc[3]);
-                    const float gc = fmaf(cf.k[1][1], e, cf.k[1][0]) * rinv;
-                    acc[4] = fmaf(gc, y[7], acc[4]);
-                    acc[5] = fmaf(gc, y[8], acc[5]);
-                    acc[6] = fmaf(gc, y[9], acc[6]);
-                    const float gb = e * rinv;
-                    acc[7] = fmaf(gb, y[4], acc[7]);
-                    acc[8] = fmaf(gb, y[5], acc[8]);
-                    acc[9] = fmaf(gb, y[6], acc[9]);
+                    const float2 ts = t_mul2(t_fma2(c13, ek, c12), t_mul2(rinv3, t_splat(y[3])));
+                    acc[1] = t_fma2(ts, d0, acc[1]);
+                    acc[2] = t_fma2(ts, d1, acc[2]);
+                    acc[3] = t_fma2(ts, d2, acc[3]);
+                    const float2 gc = t_mul2(t_fma2(c11, e, c10), rinv);
+                    acc[4] = t_fma2(gc, t_splat(y[7]), acc[4]);
+                    acc[5] = t_fma2(gc, t_splat(y[8]), acc[5]);
+                    acc[6] = t_fma2(gc, t_splat(y[9]), acc[6]);
+                    const float2 gb = t_mul2(e, rinv);
+                    acc[7] = t_fma2(gb, t_splat(y[4]), acc[7]);
+                    acc[8] = t_fma2(gb, t_splat(y[5]), acc[8]);
+                    acc[9] = t_fma2(gb, t_splat(y[6]), acc[9]);
                 }
             }
         }
     }
-    if (live) {
-        const int64_t pt = perm[ti];
-        for (int k = 0; k < NACC; ++k) part[(int64_t)k * np + pt] = acc[k];
+    // the second half's sums join the first half's
+    static_assert(NACC * TREE_LEAF <= TILE * TREE_REC, "reduction buffer");
+    __syncthreads();
+    const int tl = (int)threadIdx.x % TREE_HALF;
+    if (half == 1)
+        for (int k = 0; k < NACC; ++k) {
+            tile[k * TREE_LEAF + tl] = acc[k].x;
+            tile[k * TREE_LEAF + TREE_HALF + tl] = acc[k].y;
+        }
+    __syncthreads();
+    if (half == 1) return;
+    for (int k = 0; k < NACC; ++k) {
+        acc[k].x += tile[k * TREE_LEAF + tl];
+        acc[k].y += tile[k * TREE_LEAF + TREE_HALF + tl];
+    }
+    if (live0) {
+        const int64_t pt = perm[ti0];
+        for (int k = 0; k < NACC; ++k) part[(int64_t)k * np + pt] = acc[k].x;
+    }
+    if (live1) {
+        const int64_t pt = perm[ti1];
+        for (int k = 0; k < NACC; ++k) part[(int64_t)k * np + pt] = acc[k].y;
     }
 }
 
@@ -612,11 +677,11 @@ int tree_far(const pb_mesh* mc, const FarPlan& fp, const double* x, bool need_u,
     Timer tm(ctx, PB_KERNEL_TREE32, s, (double)(t->direct_pairs + t->proxy_pairs),
              fp.mode == 0 ? 25.0 : 36.0);
     if (fp.mode == 0)
-        k_tree_eval<0><<<(unsigned)t->nleaf, TREE_LEAF, 0, s>>>(np, t->nprox, t->perm, t->leaf_rng, t->far_ptr,
+        k_tree_eval<0><<<(unsigned)t->nleaf, TREE_TPB, 0, s>>>(np, t->nprox, t->perm, t->leaf_rng, t->far_ptr,
                                                                 t->far_idx, t->near_ptr, t->near_rng, rec, prox, cf,
                                                                 part);
     else
-        k_tree_eval<1><<<(unsigned)t->nleaf, TREE_LEAF, 0, s>>>(np, t->nprox, t->perm, t->leaf_rng, t->far_ptr,
+        k_tree_eval<1><<<(unsigned)t->nleaf, TREE_TPB, 0, s>>>(np, t->nprox, t->perm, t->leaf_rng, t->far_ptr,
                                                                 t->far_idx, t->near_ptr, t->near_rng, rec, prox, cf,
                                                                 part);
     ::pb::count_launch();
