@@ -312,151 +312,176 @@ __device__ __forceinline__ float cheb_node(int a, int n) {
     return cospif((float)a / (float)(n - 1));
 }
 
-// Lagrange basis l_a(t) and its derivative on the n Chebyshev points, t in [-1, 1]
-__device__ void lagrange1(float t, int n, float* l, float* dl) {
-    float tn[TREE_MAXN];
-    for (int a = 0; a < n; ++a) tn[a] = cheb_node(a, n);
-    for (int a = 0; a < n; ++a) {
-        float den = 1.f, num = 1.f, dnum = 0.f;
-        for (int b = 0; b < n; ++b) {
+// Lagrange basis l_a(t) and its derivative on the N Chebyshev points tn,
+// t in [-1, 1]; iden[a] = 1 / prod_{b != a} (tn[a] - tn[b]).
+template <int N>
+__device__ __forceinline__ void lagrange_n(float t, const float* tn, const float* iden, float* l, float* dl) {
+#pragma unroll
+    for (int a = 0; a < N; ++a) {
+        float num = 1.f, dnum = 0.f;
+#pragma unroll
+        for (int b = 0; b < N; ++b) {
             if (b == a) continue;
-            den *= tn[a] - tn[b];
             // product rule, running: d(num * (t - t_b)) = dnum (t - t_b) + num
             dnum = dnum * (t - tn[b]) + num;
             num *= t - tn[b];
         }
-        l[a] = num / den;
-        dl[a] = dnum / den;
+        l[a] = num * iden[a];
+        dl[a] = dnum * iden[a];
     }
 }
 
 // Proxy charges of the slots of one height: one CTA per slot, threads over
-// proxies. A slot's charges come from its two children: a child with its own
-// proxies passes them on through the slot's interpolation (exact, the basis
-// polynomials having the same degree), any other child through its points.
-// Sources are staged 128 at a time with their 1-D basis values.
+// proxies, N Chebyshev points per axis (N^3 proxies). A slot's charges come
+// from its two children: a child with its own proxies passes them on through
+// the slot's interpolation (exact, the basis polynomials having the same
+// degree), any other child through its points. Sources are staged 128 at a
+// time with their 1-D basis values.
 // Proxy record: z (3), S, Q, C (3), N (3), 0.
 constexpr int PROXY_THREADS = 128;
 
+template <int N>
 __global__ void __launch_bounds__(PROXY_THREADS)
-k_proxy_charges(int n, const int32_t* __restrict__ slots, const int32_t* __restrict__ slot_kids,
+k_proxy_charges(const int32_t* __restrict__ slots, const int32_t* __restrict__ slot_kids,
                 const float* __restrict__ slot_box, const float* __restrict__ rec, float* __restrict__ prox) {
-    // staging of 128 points (lx, ly, lz, dlx, dly, dlz; 8 charges), or two n^3 x 8 buffers of the transfer
-    constexpr int SBW = 64;
-    static_assert(SBW >= 6 * TREE_MAXN + 8, "staging row");
-    static_assert(PROXY_THREADS * SBW >= 2 * TREE_MAXN * TREE_MAXN * TREE_MAXN * 8, "transfer buffers");
-    __shared__ float sb[PROXY_THREADS][SBW];
+    constexpr int NP = N * N * N, N2 = N * N;
+    constexpr int PER = (NP + PROXY_THREADS - 1) / PROXY_THREADS;
+    // a staged point: lx, ly, lz, dlx, dly, dlz (N each), 8 charges; odd row length (no bank conflicts)
+    constexpr int SBW = 6 * N + 9;
+    constexpr int SB = PROXY_THREADS * SBW > 2 * NP * 8 ? PROXY_THREADS * SBW : 2 * NP * 8;
+    __shared__ __align__(16) float sb[SB];
+    __shared__ float tn[N], iden[N];
+    __shared__ float T[3][N][N];  // 1-D transfer matrices of a child with proxies
     const int slot = slots[blockIdx.x];
-    const int nprox = n * n * n;
+    if (threadIdx.x < N) tn[threadIdx.x] = cheb_node(threadIdx.x, N);
+    __syncthreads();
+    if (threadIdx.x < N) {
+        float den = 1.f;
+        for (int b = 0; b < N; ++b)
+            if (b != (int)threadIdx.x) den *= tn[threadIdx.x] - tn[b];
+        iden[threadIdx.x] = 1.f / den;
+    }
     const float* box = slot_box + 6 * slot;
-    float mid[3], half[3];
+    float mid[3], half[3], ihalf[3];
+#pragma unroll
     for (int d = 0; d < 3; ++d) {
         mid[d] = 0.5f * (box[d] + box[3 + d]);
         half[d] = 0.5f * (box[3 + d] - box[d]);
+        ihalf[d] = 1.f / half[d];
     }
-    constexpr int PER = (TREE_MAXN * TREE_MAXN * TREE_MAXN + PROXY_THREADS - 1) / PROXY_THREADS;
+    // this thread's proxies and their grid indices
+    int ka[PER], kb[PER], kc[PER];
     float acc[PER][8];
-    for (int r = 0; r < PER; ++r)
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+        const int k = min((int)threadIdx.x + r * PROXY_THREADS, NP - 1);
+        ka[r] = k / N2;
+        kb[r] = (k / N) % N;
+        kc[r] = k % N;
+#pragma unroll
         for (int c = 0; c < 8; ++c) acc[r][c] = 0.f;
-    __shared__ float T[3][TREE_MAXN][TREE_MAXN];  // 1-D transfer matrices of a child with proxies
-    float* buf0 = &sb[0][0];                          // child charges, then the y pass
-    float* buf1 = buf0 + TREE_MAXN * TREE_MAXN * TREE_MAXN * 8;  // the x pass
+    }
+    __syncthreads();
+    float* buf0 = sb;                // child charges, then the y pass
+    float* buf1 = sb + NP * 8;       // the x pass
     for (int kid = 0; kid < 2; ++kid) {
         const int32_t ks = slot_kids[6 * slot + 3 * kid];
-        const bool raw = ks < 0;  // uniform across the block
-        if (!raw) {
+        if (ks >= 0) {  // uniform across the block
             // A child with proxies: its charges sit on the tensor grid of its box, so the transfer
-            // to this slot's grid is a tensor product of three n x n matrices
+            // to this slot's grid is a tensor product of three N x N matrices
             // T_d[a][a'] = l_a(child node a' in this slot's coordinates), applied one axis at a time.
             const float* cb = slot_box + 6 * ks;
-            if (threadIdx.x < 3 * n) {
-                const int d = threadIdx.x / n, a2 = threadIdx.x % n;
-                const float zc = 0.5f * (cb[d] + cb[3 + d]) + 0.5f * (cb[3 + d] - cb[d]) * cheb_node(a2, n);
-                float l[TREE_MAXN], dl[TREE_MAXN];
-                lagrange1((zc - mid[d]) / half[d], n, l, dl);
-                for (int a = 0; a < n; ++a) T[d][a][a2] = l[a];
+            if (threadIdx.x < 3 * N) {
+                const int d = threadIdx.x / N, a2 = threadIdx.x % N;
+                const float zc = 0.5f * (cb[d] + cb[3 + d]) + 0.5f * (cb[3 + d] - cb[d]) * tn[a2];
+                float l[N], dl[N];
+                lagrange_n<N>((zc - mid[d]) * ihalf[d], tn, iden, l, dl);
+#pragma unroll
+                for (int a = 0; a < N; ++a) T[d][a][a2] = l[a];
             }
-            const float* cp = prox + (int64_t)ks * nprox * TREE_REC;
-            for (int k = threadIdx.x; k < nprox * 8; k += PROXY_THREADS) buf0[k] = cp[(k >> 3) * TREE_REC + 3 + (k & 7)];
+            const float* cp = prox + (int64_t)ks * NP * TREE_REC;
+            for (int k = threadIdx.x; k < NP * 8; k += PROXY_THREADS) buf0[k] = cp[(k >> 3) * TREE_REC + 3 + (k & 7)];
             __syncthreads();
-            const int n2 = n * n;
-            for (int k = threadIdx.x; k < nprox * 8; k += PROXY_THREADS) {  // x pass
-                const int c = k & 7, idx = k >> 3, a = idx / n2, rest = idx - a * n2;
+            for (int k = threadIdx.x; k < NP * 8; k += PROXY_THREADS) {  // x pass
+                const int c = k & 7, idx = k >> 3, a = idx / N2, rest = idx - a * N2;
                 float v = 0.f;
-                for (int a2 = 0; a2 < n; ++a2) v += T[0][a][a2] * buf0[(a2 * n2 + rest) * 8 + c];
+#pragma unroll
+                for (int a2 = 0; a2 < N; ++a2) v += T[0][a][a2] * buf0[(a2 * N2 + rest) * 8 + c];
                 buf1[k] = v;
             }
             __syncthreads();
-            for (int k = threadIdx.x; k < nprox * 8; k += PROXY_THREADS) {  // y pass
-                const int c = k & 7, idx = k >> 3, a = idx / n2, bb = (idx / n) % n, cc = idx % n;
+            for (int k = threadIdx.x; k < NP * 8; k += PROXY_THREADS) {  // y pass
+                const int c = k & 7, idx = k >> 3, a = idx / N2, bb = (idx / N) % N, cc = idx % N;
                 float v = 0.f;
-                for (int b2 = 0; b2 < n; ++b2) v += T[1][bb][b2] * buf1[((a * n + b2) * n + cc) * 8 + c];
+#pragma unroll
+                for (int b2 = 0; b2 < N; ++b2) v += T[1][bb][b2] * buf1[((a * N + b2) * N + cc) * 8 + c];
                 buf0[k] = v;
             }
             __syncthreads();
+#pragma unroll
             for (int r = 0; r < PER; ++r) {  // z pass into this thread's proxies
-                const int k = threadIdx.x + r * PROXY_THREADS;
-                if (k >= nprox) break;
-                const int a = k / n2, bb = (k / n) % n, cc = k % n;
-                for (int c = 0; c < 8; ++c) {
-                    float v = 0.f;
-                    for (int c2 = 0; c2 < n; ++c2) v += T[2][cc][c2] * buf0[((a * n + bb) * n + c2) * 8 + c];
-                    acc[r][c] += v;
+                if ((int)threadIdx.x + r * PROXY_THREADS < NP) {
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        float v = 0.f;
+#pragma unroll
+                        for (int c2 = 0; c2 < N; ++c2)
+                            v += T[2][kc[r]][c2] * buf0[((ka[r] * N + kb[r]) * N + c2) * 8 + c];
+                        acc[r][c] += v;
+                    }
                 }
             }
             __syncthreads();
             continue;
         }
-        const int32_t b = raw ? slot_kids[6 * slot + 3 * kid + 1] : 0;
-        const int32_t e = raw ? slot_kids[6 * slot + 3 * kid + 2] : nprox;
-        const float* src = raw ? rec : prox + (int64_t)ks * nprox * TREE_REC;
+        // raw points of the child: s, p (3), c (3)
+        const int32_t b = slot_kids[6 * slot + 3 * kid + 1];
+        const int32_t e = slot_kids[6 * slot + 3 * kid + 2];
         for (int c0 = b; c0 < e; c0 += PROXY_THREADS) {
             const int i = c0 + threadIdx.x;
-            float* my = sb[threadIdx.x];
+            float* my = sb + threadIdx.x * SBW;
             if (i < e) {
-                const float* r = src + TREE_REC * (int64_t)i;
+                const float* r = rec + TREE_REC * (int64_t)i;
+#pragma unroll
                 for (int d = 0; d < 3; ++d) {
-                    const float t = (r[d] - mid[d]) / half[d];
-                    lagrange1(t, n, my + TREE_MAXN * d, my + TREE_MAXN * (3 + d));
-                    for (int a = 0; a < n; ++a) my[TREE_MAXN * (3 + d) + a] /= half[d];  // d/dy = d/dt / half
+                    lagrange_n<N>((r[d] - mid[d]) * ihalf[d], tn, iden, my + N * d, my + N * (3 + d));
+#pragma unroll
+                    for (int a = 0; a < N; ++a) my[N * (3 + d) + a] *= ihalf[d];  // d/dy = d/dt / half
                 }
-                // raw point: s, p (3), c (3); child proxy: S, Q, C (3), N (3)
-                for (int c = 0; c < 8; ++c) my[6 * TREE_MAXN + c] = raw ? (c < 7 ? r[3 + c] : 0.f) : r[3 + c];
+#pragma unroll
+                for (int c = 0; c < 7; ++c) my[6 * N + c] = r[3 + c];
             }
             __syncthreads();
             const int m = min(PROXY_THREADS, e - c0);
             for (int j = 0; j < m; ++j) {
-                const float* pj = sb[j];
-                const float* q = pj + 6 * TREE_MAXN;
+                const float* pj = sb + j * SBW;
+                const float* q = pj + 6 * N;
+#pragma unroll
                 for (int r = 0; r < PER; ++r) {
-                    const int k = threadIdx.x + r * PROXY_THREADS;
-                    if (k >= nprox) break;
-                    const int a = k / (n * n), bb = (k / n) % n, cc = k % n;
-                    const float lx = pj[a], ly = pj[TREE_MAXN + bb], lz = pj[2 * TREE_MAXN + cc];
-                    const float L = lx * ly * lz;
+                    const float lx = pj[ka[r]], ly = pj[N + kb[r]], lz = pj[2 * N + kc[r]];
+                    const float lyz = ly * lz, L = lx * lyz;
+                    const float gx = pj[3 * N + ka[r]] * lyz, gy = lx * pj[4 * N + kb[r]] * lz,
+                                gz = lx * ly * pj[5 * N + kc[r]];
                     acc[r][0] += L * q[0];
-                    if (raw) {
-                        const float gx = pj[3 * TREE_MAXN + a] * ly * lz, gy = lx * pj[4 * TREE_MAXN + bb] * lz,
-                                    gz = lx * ly * pj[5 * TREE_MAXN + cc];
-                        acc[r][1] += gx * q[1] + gy * q[2] + gz * q[3];
-                        for (int c = 0; c < 3; ++c) acc[r][2 + c] += L * q[4 + c];
-                        for (int c = 0; c < 3; ++c) acc[r][5 + c] += L * q[1 + c];
-                    } else {
-                        for (int c = 1; c < 8; ++c) acc[r][c] += L * q[c];
-                    }
+                    acc[r][1] += gx * q[1] + gy * q[2] + gz * q[3];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) acc[r][2 + c] += L * q[4 + c];
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) acc[r][5 + c] += L * q[1 + c];
                 }
             }
             __syncthreads();
         }
     }
+#pragma unroll
     for (int r = 0; r < PER; ++r) {
         const int k = threadIdx.x + r * PROXY_THREADS;
-        if (k >= nprox) break;
-        const int a = k / (n * n), bb = (k / n) % n, cc = k % n;
-        float* o = prox + ((int64_t)slot * nprox + k) * TREE_REC;
-        o[0] = mid[0] + half[0] * cheb_node(a, n);
-        o[1] = mid[1] + half[1] * cheb_node(bb, n);
-        o[2] = mid[2] + half[2] * cheb_node(cc, n);
+        if (k >= NP) break;
+        float* o = prox + ((int64_t)slot * NP + k) * TREE_REC;
+        o[0] = mid[0] + half[0] * tn[ka[r]];
+        o[1] = mid[1] + half[1] * tn[kb[r]];
+        o[2] = mid[2] + half[2] * tn[kc[r]];
+#pragma unroll
         for (int c = 0; c < 8; ++c) o[3 + c] = acc[r][c];
         o[11] = 0.f;
     }
@@ -664,8 +689,16 @@ int tree_far(const pb_mesh* mc, const FarPlan& fp, const double* x, bool need_u,
     for (size_t h = 0; h + 1 < t->height_ptr.size(); ++h) {  // children's proxies before their parents'
         const int64_t b = t->height_ptr[h], e = t->height_ptr[h + 1];
         if (e > b) {
-            k_proxy_charges<<<(unsigned)(e - b), PROXY_THREADS, 0, s>>>(t->n, t->slot_order + b, t->slot_kids,
-                                                                        t->slot_box, rec, prox);
+            const unsigned g = (unsigned)(e - b);
+            const int32_t* so = t->slot_order + b;
+            switch (t->n) {
+                case 3: k_proxy_charges<3><<<g, PROXY_THREADS, 0, s>>>(so, t->slot_kids, t->slot_box, rec, prox); break;
+                case 4: k_proxy_charges<4><<<g, PROXY_THREADS, 0, s>>>(so, t->slot_kids, t->slot_box, rec, prox); break;
+                case 5: k_proxy_charges<5><<<g, PROXY_THREADS, 0, s>>>(so, t->slot_kids, t->slot_box, rec, prox); break;
+                case 6: k_proxy_charges<6><<<g, PROXY_THREADS, 0, s>>>(so, t->slot_kids, t->slot_box, rec, prox); break;
+                case 7: k_proxy_charges<7><<<g, PROXY_THREADS, 0, s>>>(so, t->slot_kids, t->slot_box, rec, prox); break;
+                default: k_proxy_charges<8><<<g, PROXY_THREADS, 0, s>>>(so, t->slot_kids, t->slot_box, rec, prox); break;
+            }
             ::pb::count_launch();
         }
     }
