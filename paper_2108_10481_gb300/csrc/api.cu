@@ -1,3 +1,4 @@
+#include <chrono>
 // Context, error reporting and device allocation helpers of the C ABI.
 #include <cudaTypedefs.h>
 #include <stdarg.h>
@@ -95,6 +96,30 @@ int set_error(int code, const char* fmt, ...) {
     vsnprintf(g_err, sizeof(g_err), fmt, ap);
     va_end(ap);
     return code;
+}
+
+static bool trace_enabled() {
+    static const bool on = getenv("PBBEM_TRACE") != nullptr;
+    return on;
+}
+
+static double wall_ms() {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+PhaseTrace::PhaseTrace(const char* s) : scope(s), t0(0.0), on(trace_enabled()) {
+    if (on) {
+        cudaDeviceSynchronize();
+        t0 = wall_ms();
+    }
+}
+
+void PhaseTrace::lap(const char* label) {
+    if (!on) return;
+    cudaDeviceSynchronize();
+    const double t = wall_ms();
+    fprintf(stderr, "[pbbem] %s/%s %.3f ms\n", scope, label, t - t0);
+    t0 = t;
 }
 
 int dev_alloc(void** p, size_t bytes) {

@@ -275,6 +275,17 @@ int mass_solve(const pb_mesh* m, const pb_near* nf, const double* x, double* y, 
                int iters, cudaStream_t s);
 
 // CUDA events around one launch on its stream, when the context profiles.
+// Host-side phase trace: with PBBEM_TRACE set in the environment, lap() prints
+// the wall time since the previous lap (stderr), after synchronising the device
+// so that the time belongs to the phase that queued the work.
+struct PhaseTrace {
+    const char* scope;
+    double t0;
+    bool on;
+    explicit PhaseTrace(const char* s);
+    void lap(const char* label);
+};
+
 struct Timer {
     pb_ctx* ctx;
     int id;

@@ -346,6 +346,7 @@ static int upload(void** dst, const void* src, size_t bytes, size_t* total) {
 }
 
 static void free_mesh_arrays(pb_mesh* m) {
+    PhaseTrace tr("mesh_free");
     void* ptrs[] = {m->verts,    m->tris,     m->tgeo,     m->pts64,   m->pts32,  m->pts32lo, m->v2t_ptr,
                     m->v2t,      m->pairs,    m->adj_ptr,  m->row_ptr, m->col,    m->tpos,    m->row_of,
                     m->diag_pos, m->status,   m->pair_rev, m->pair_coin, m->pair_prim, m->band_ptr, m->band_s,
@@ -361,6 +362,7 @@ static void free_mesh_arrays(pb_mesh* m) {
     ws_free(m->ws_tree);
     tree_free(m->tree);
     m->tree = nullptr;
+    tr.lap("all");
 }
 
 static int load(pb_ctx* ctx, const double* verts_in, int64_t nv, const int32_t* tris_in, int64_t nt,
@@ -389,6 +391,7 @@ static int load(pb_ctx* ctx, const double* verts_in, int64_t nv, const int32_t* 
     rule_points(Q, m->rule_l, m->rule_w);
     rule_points(m->Qr, m->ref_l, m->ref_w);
 
+    PhaseTrace tr("mesh_load");
     std::vector<double> V(3 * nv);
     std::vector<int32_t> T(3 * nt);
     if (mem == PB_MEM_DEVICE) {
@@ -401,6 +404,7 @@ static int load(pb_ctx* ctx, const double* verts_in, int64_t nv, const int32_t* 
         return set_error(PB_EINVAL, "mem must be PB_MEM_HOST or PB_MEM_DEVICE");
     }
 
+    tr.lap("copy_in");
     // ---- validation
     double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
     for (int64_t i = 0; i < nv; ++i)
@@ -433,6 +437,7 @@ static int load(pb_ctx* ctx, const double* verts_in, int64_t nv, const int32_t* 
         vol6 += p0[0] * (p1[1] * p2[2] - p1[2] * p2[1]) - p0[1] * (p1[0] * p2[2] - p1[2] * p2[0]) +
                 p0[2] * (p1[0] * p2[1] - p1[1] * p2[0]);
     }
+    tr.lap("validate");
     // every undirected edge must appear exactly twice, once in each direction
     {
         std::vector<std::pair<uint64_t, int>> e;
@@ -463,6 +468,7 @@ static int load(pb_ctx* ctx, const double* verts_in, int64_t nv, const int32_t* 
         return set_error(PB_EMESH, "enclosed volume is not positive (triangles must be counter-clockwise "
                          "seen from outside)");
 
+    tr.lap("edges");
     // ---- vertex -> triangle map
     std::vector<int32_t> v2t_ptr(nv + 1, 0), v2t(3 * nt);
     for (int64_t k = 0; k < 3 * nt; ++k) v2t_ptr[T[k] + 1]++;
@@ -476,6 +482,7 @@ static int load(pb_ctx* ctx, const double* verts_in, int64_t nv, const int32_t* 
         if (v2t_ptr[i + 1] == v2t_ptr[i])
             return set_error(PB_EMESH, "vertex %lld belongs to no triangle", (long long)i);
 
+    tr.lap("v2t");
     // ---- adjacent triangle pairs (share >= 1 vertex), ordered by (ti, tj):
     // counted, then filled, per triangle
     std::vector<int32_t> adj_ptr(nt + 1, 0);
@@ -541,6 +548,7 @@ static int load(pb_ctx* ctx, const double* verts_in, int64_t nv, const int32_t* 
         }
     });
 
+    tr.lap("adjacency");
     // ---- each adjacent pair's reverse; the pairs the near kernels integrate:
     // coincident ones, and one of every two reversed ones (t < s)
     m->n_adj = n_adj;
@@ -569,6 +577,7 @@ static int load(pb_ctx* ctx, const double* verts_in, int64_t nv, const int32_t* 
         }
     }
 
+    tr.lap("reverse");
     size_t tot = 0;
     PB_TRY(upload((void**)&m->verts, V.data(), sizeof(double) * 3 * nv, &tot));
     PB_TRY(upload((void**)&m->tris, T.data(), sizeof(int32_t) * 3 * nt, &tot));
@@ -578,6 +587,7 @@ static int load(pb_ctx* ctx, const double* verts_in, int64_t nv, const int32_t* 
     // and radii here, with the oracle's arithmetic; a uniform grid of cell size
     // 2 eta max(rho) here; the search on the device (k_band_search), which
     // lists each triangle's partners in increasing order.
+    tr.lap("upload_mesh");
     m->n_band = 0;
     if (eta > 0.0) {
         std::vector<double> C(3 * nt), R(nt);
@@ -670,6 +680,7 @@ static int load(pb_ctx* ctx, const double* verts_in, int64_t nv, const int32_t* 
         tot += sizeof(int32_t) * (nt + 1 + 2 * (m->n_band + 1));
     }
     m->npairs = n_adj + m->n_band;
+    tr.lap("band");
 
     // ---- near pattern (device): counts, row pointers, sorted columns, then the
     // transposed and diagonal positions
@@ -682,6 +693,7 @@ static int load(pb_ctx* ctx, const double* verts_in, int64_t nv, const int32_t* 
     PB_TRY(upload((void**)&m->pair_prim, prim_list.data(), sizeof(int32_t) * prim_list.size(), &tot));
     m->n_coin = (int64_t)coin_list.size();
     m->n_prim = (int64_t)prim_list.size();
+    tr.lap("upload_pairs");
     PB_TRY(dev_alloc((void**)&m->status, sizeof(int)));
     PB_CUDA(cudaMemset(m->status, 0, sizeof(int)));
     PB_TRY(dev_alloc((void**)&m->row_ptr, sizeof(int32_t) * (nv + 1)));
@@ -751,6 +763,7 @@ static int load(pb_ctx* ctx, const double* verts_in, int64_t nv, const int32_t* 
         cudaFree(cntv);
         if (rc != PB_OK) return rc;
     }
+    tr.lap("pattern");
     const int64_t nnz = m->nnz;
     PB_TRY(dev_alloc((void**)&m->tpos, sizeof(int32_t) * nnz));
     PB_TRY(dev_alloc((void**)&m->row_of, sizeof(int32_t) * nnz));
@@ -784,6 +797,7 @@ static int load(pb_ctx* ctx, const double* verts_in, int64_t nv, const int32_t* 
     int st = 0;
     PB_CUDA(cudaMemcpy(&st, m->status, sizeof(int), cudaMemcpyDeviceToHost));
     if (st != 0) return set_error(PB_EMESH, "internal: near pattern is not symmetric");
+    tr.lap("geometry");
     return PB_OK;
 }
 

@@ -421,55 +421,135 @@ k_coin_pairs(const double* __restrict__ verts, const int32_t* __restrict__ tris,
 // thread per band pair (t, s) with t < s. Points are the rules' barycentric
 // combinations of the corners, in the corners' original order. Band pair q is
 // stored at n_adj + q.
+//
+// Both rules are products of one triangle rule on each triangle, so every block
+// entry factors as sum_i w_i l_a(x_i) [sum_j w_j l_b(y_j) g(x_i, y_j)]: for each
+// x point the thread first sums the six kernels against the y points' three
+// basis values (18 FMA per point pair), then adds those partial sums into the
+// 3x3 blocks (54 FMA per x point). The sums of w G over the pair follow from
+// the single-layer blocks, the basis functions summing to one at every point.
+// The y points of both rules are staged in shared memory, per thread.
 constexpr int BAND_THREADS = 128;
 
+// FP64 flops of one band pair under a Q-point rule by formula count: per point
+// pair the kernel evaluation (33, as for the regularised pairs) and the partial
+// sums (18 FMA); per point of either triangle its position (15); per x point
+// its weights (4) and the block updates (54 FMA).
+__host__ __device__ constexpr double band_flops(int Q) { return Q * Q * (33.0 + 36.0) + Q * (30.0 + 4.0 + 108.0); }
+
+template <int Q>
+__device__ __forceinline__ void band_pass(double* acc, const double (&pa)[3][3], const double* ys,
+                                          const double (*wl)[3], const Rule& R, double wscale, const double* na,
+                                          const double* nb, double kappa) {
+#pragma unroll 1
+    for (int i = 0; i < Q; ++i) {
+        double x[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) x[k] = R.l[i][0] * pa[0][k] + R.l[i][1] * pa[1][k] + R.l[i][2] * pa[2][k];
+        double u[6][3];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) u[k][0] = u[k][1] = u[k][2] = 0.0;
+#pragma unroll 1
+        for (int j = 0; j < Q; ++j) {
+            const double d0 = x[0] - ys[(3 * j) * BAND_THREADS], d1 = x[1] - ys[(3 * j + 1) * BAND_THREADS],
+                         d2 = x[2] - ys[(3 * j + 2) * BAND_THREADS];
+            const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+            const double rinv = rsqrt(r2);
+            const double r = r2 * rinv;
+            const double gl = rinv * 0.07957747154594767;  // 1 / (4 pi r)
+            const double ek = exp(-kappa * r);
+            const double fl = gl * rinv * rinv;  // 1 / (4 pi r^3)
+            const double fy_over_fl = ek * (1.0 + kappa * r);
+            const double kl = fl * (d0 * nb[0] + d1 * nb[1] + d2 * nb[2]);
+            const double ktl = fl * -(d0 * na[0] + d1 * na[1] + d2 * na[2]);  // (y - x).n_x
+            const double g[6] = {gl, ek * gl, kl, kl * fy_over_fl, ktl, ktl * fy_over_fl};
+#pragma unroll
+            for (int k = 0; k < 6; ++k)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) u[k][c] += g[k] * wl[j][c];
+        }
+        // blocks: V_L, V_Y, K_L, K_Y at 0, 9, 18, 27; the reversed pair's K_L, K_Y at 38, 47
+        const double wi = wscale * R.w[i];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const double wa = wi * R.l[i][a];
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                const int base = k < 4 ? 9 * k : 38 + 9 * (k - 4);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) acc[base + 3 * a + c] += wa * u[k][c];
+            }
+        }
+    }
+}
+
+template <int QF, int QC>
 __global__ void __launch_bounds__(BAND_THREADS, 2)
 k_band_pairs(const double* __restrict__ verts, const int32_t* __restrict__ tris, const double* __restrict__ tgeo,
              const int32_t* __restrict__ band_ptr, const int32_t* __restrict__ band_s,
              const int32_t* __restrict__ band_t, int64_t n_band, int64_t n_adj, Rule fine, Rule coarse, double kappa,
              double* __restrict__ ss_out, int* __restrict__ status) {
+    __shared__ double ysm[(QF + QC) * 3 * BAND_THREADS];
+    __shared__ double wl[2][6][3];  // w_j l_b(y_j) of the fine and the coarse rule
+    if (threadIdx.x < 36) {
+        const int r = threadIdx.x / 18, j = (threadIdx.x / 3) % 6, c = threadIdx.x % 3;
+        const Rule& R = r == 0 ? fine : coarse;
+        wl[r][j][c] = R.w[j] * R.l[j][c];
+    }
+    __syncthreads();
     const int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (q >= n_band) return;
-    const int4 pr = make_int4(band_t[q], band_s[q], 3, 0);
-    if (pr.x > pr.y) return;  // the reverse of a pair handled by its other thread
+    if (q >= n_band) return;  // no barrier follows
+    const int32_t pt = band_t[q], ps = band_s[q];
+    if (pt > ps) return;  // the reverse of a pair handled by its other thread
     // the reversed pair: t among the partners of s (sorted)
-    int32_t lo = band_ptr[pr.y], hi = band_ptr[pr.y + 1];
+    int32_t lo = band_ptr[ps], hi = band_ptr[ps + 1];
     while (lo < hi) {
         const int32_t mid = (lo + hi) >> 1;
-        if (band_s[mid] < pr.x) lo = mid + 1;
+        if (band_s[mid] < pt) lo = mid + 1;
         else hi = mid;
     }
-    if (lo >= band_ptr[pr.y + 1] || band_s[lo] != pr.x) {  // the band lists are symmetric by construction
+    if (lo >= band_ptr[ps + 1] || band_s[lo] != pt) {  // the band lists are symmetric by construction
         atomicExch(status, PB_EMESH);
         return;
     }
     const int64_t p = n_adj + q, pr_rev = n_adj + lo;
-    double pa[3][3], pb[3][3];
-    for (int a = 0; a < 3; ++a)
-        for (int k = 0; k < 3; ++k) {
-            pa[a][k] = verts[3 * (int64_t)tris[3 * (int64_t)pr.x + a] + k];
-            pb[a][k] = verts[3 * (int64_t)tris[3 * (int64_t)pr.y + a] + k];
-        }
-    const double* gA = tgeo + 16 * (int64_t)pr.x;
-    const double* gB = tgeo + 16 * (int64_t)pr.y;
-    const double na[3] = {gA[0], gA[1], gA[2]}, nb[3] = {gB[0], gB[1], gB[2]};
-    double acc[NACC_SYM];
-    for (int k = 0; k < NACC_SYM; ++k) acc[k] = 0.0;
-    for (int pass = 0; pass < 2; ++pass) {
-        const Rule& R = pass == 0 ? fine : coarse;
-        const double sign = pass == 0 ? 1.0 : -1.0;
-        for (int i = 0; i < R.Q; ++i) {
-            double x[3];
-            for (int k = 0; k < 3; ++k) x[k] = R.l[i][0] * pa[0][k] + R.l[i][1] * pa[1][k] + R.l[i][2] * pa[2][k];
-            for (int j = 0; j < R.Q; ++j) {
-                double y[3];
-                for (int k = 0; k < 3; ++k)
-                    y[k] = R.l[j][0] * pb[0][k] + R.l[j][1] * pb[1][k] + R.l[j][2] * pb[2][k];
-                const double w = sign * (R.w[i] * gA[3]) * (R.w[j] * gB[3]);
-                accum_point<true>(acc, w, x, y, na, nb, R.l[i], R.l[j], kappa);
+    double pa[3][3];
+    {
+        double pb[3][3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                pa[a][k] = verts[3 * (int64_t)tris[3 * (int64_t)pt + a] + k];
+                pb[a][k] = verts[3 * (int64_t)tris[3 * (int64_t)ps + a] + k];
             }
+        double* ys = ysm + threadIdx.x;
+#pragma unroll
+        for (int j = 0; j < QF + QC; ++j) {
+            const Rule& R = j < QF ? fine : coarse;
+            const int jj = j < QF ? j : j - QF;
+#pragma unroll
+            for (int k = 0; k < 3; ++k)
+                ys[(3 * j + k) * BAND_THREADS] = R.l[jj][0] * pb[0][k] + R.l[jj][1] * pb[1][k] + R.l[jj][2] * pb[2][k];
         }
     }
+    const double* gA = tgeo + 16 * (int64_t)pt;
+    const double* gB = tgeo + 16 * (int64_t)ps;
+    const double na[3] = {gA[0], gA[1], gA[2]}, nb[3] = {gB[0], gB[1], gB[2]};
+    double acc[NACC_SYM];
+#pragma unroll
+    for (int k = 0; k < NACC_SYM; ++k) acc[k] = 0.0;
+    const double area2 = gA[3] * gB[3];
+    band_pass<QF>(acc, pa, ysm + threadIdx.x, wl[0], fine, area2, na, nb, kappa);
+    band_pass<QC>(acc, pa, ysm + threadIdx.x + 3 * QF * BAND_THREADS, wl[1], coarse, -area2, na, nb, kappa);
+    double s0 = 0.0, s1 = 0.0;  // sums of w G_L and w G_Y over the pair
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        s0 += acc[k];
+        s1 += acc[9 + k];
+    }
+    acc[36] = s0;
+    acc[37] = s1;
     TriFrame A, B;  // expand_blocks reads the normals and areas only
     for (int k = 0; k < 3; ++k) {
         A.n[k] = na[k];
@@ -672,10 +752,17 @@ static int build(pb_ctx* ctx, const pb_mesh* m, double kappa, pb_near* nf, cudaS
         ::pb::count_launch();
         if (m->n_band) {
             Rule fine = mesh_ref_rule(m), coarse = mesh_rule(m);
-            Timer tm(ctx, PB_KERNEL_NEAR_BAND, s, 0.5 * m->n_band * (Qb * Qb + Q * Q), NEAR_FLOPS_SYM);
-            k_band_pairs<<<(unsigned)((m->n_band + BAND_THREADS - 1) / BAND_THREADS), BAND_THREADS, 0, s>>>(
-                m->verts, m->tris, m->tgeo, m->band_ptr, m->band_s, m->band_t, m->n_band, m->n_adj, fine, coarse,
-                kappa, ss, m->status);
+            const double ppairs = 0.5 * m->n_band * (Qb * Qb + Q * Q);
+            Timer tm(ctx, PB_KERNEL_NEAR_BAND, s, ppairs,
+                     0.5 * m->n_band * (band_flops(m->Qr) + band_flops(m->Q)) / ppairs);
+            const unsigned gb = (unsigned)((m->n_band + BAND_THREADS - 1) / BAND_THREADS);
+#define PB_BAND_ARGS m->verts, m->tris, m->tgeo, m->band_ptr, m->band_s, m->band_t, m->n_band, m->n_adj, fine, \
+                     coarse, kappa, ss, m->status
+            if (m->Qr == 6 && m->Q == 3) k_band_pairs<6, 3><<<gb, BAND_THREADS, 0, s>>>(PB_BAND_ARGS);
+            else if (m->Qr == 6 && m->Q == 1) k_band_pairs<6, 1><<<gb, BAND_THREADS, 0, s>>>(PB_BAND_ARGS);
+            else if (m->Qr == 3 && m->Q == 1) k_band_pairs<3, 1><<<gb, BAND_THREADS, 0, s>>>(PB_BAND_ARGS);
+            else rc = set_error(PB_EINVAL, "band rule %d with far rule %d", m->Qr, m->Q);
+#undef PB_BAND_ARGS
             tm.stop();
             ::pb::count_launch();
         }
