@@ -402,6 +402,12 @@ int pb_profile_read(pb_ctx* ctx, int kernel, int64_t* launches, double* total_ms
  * *status_out receives the status word the kernel wrote (PB_ETIMEOUT when the
  * wait ran out). The kernel returns normally and the context stays usable. */
 int pb_selftest_wait(pb_ctx* ctx, int64_t polls, int* status_out);
+/* Self-test of the exponential the FP64 near-field kernels use for the Yukawa
+ * factor e^{-kappa r} (a table-driven e^x for x <= 0 after Tang, ACM TOMS
+ * 15(2), 1989): y[i] = e^{x[i]} for the n device doubles x (each <= 0; 0 is
+ * returned below -700), on `stream` (NULL: the default stream), synchronised
+ * before return. x and y are caller-owned device buffers of n doubles. */
+int pb_selftest_exp(pb_ctx* ctx, const double* x, double* y, int64_t n, void* stream);
 /* Number of kernels this library has launched in this process (all kinds;
  * a kernel inside a replayed CUDA graph counts once per replay). */
 int64_t pb_launch_count(void);

@@ -140,6 +140,14 @@ def pb_selftest_wait(ctx: Ctx, polls: int = 4096) -> int:
     return st.value
 
 
+def pb_selftest_exp(ctx: Ctx, x: torch.Tensor, stream=None) -> torch.Tensor:
+    """e^x (x <= 0) by the near-field kernels' exponential, for x a CUDA float64 tensor."""
+    xx = x.contiguous()
+    y = torch.empty_like(xx)
+    _check(N.load().pb_selftest_exp(ctx.ptr, _dptr(xx, "x"), _dptr(y, "y"), xx.numel(), _stream(stream)))
+    return y
+
+
 def pb_launch_count() -> int:
     return int(N.load().pb_launch_count())
 

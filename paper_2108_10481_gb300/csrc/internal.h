@@ -275,6 +275,13 @@ int mass_solve(const pb_mesh* m, const pb_near* nf, const double* x, double* y, 
                int iters, cudaStream_t s);
 
 // CUDA events around one launch on its stream, when the context profiles.
+// Host worker pool, created on first use and kept for the life of the process:
+// host_parallel(n, f) calls f(0) ... f(n - 1) across the workers and the
+// calling thread and returns when all have returned. A call made while
+// another is running (another host thread) runs its jobs on the caller alone.
+int host_threads();
+void host_parallel(int n, const std::function<void(int)>& f);
+
 // Host-side phase trace: with PBBEM_TRACE set in the environment, lap() prints
 // the wall time since the previous lap (stderr), after synchronising the device
 // so that the time belongs to the phase that queued the work.

@@ -14,6 +14,8 @@
 // list is built per triangle or per vertex row, so its order does not depend
 // on the thread count. The band search runs on the device.
 #include <algorithm>
+#include <atomic>
+#include <climits>
 #include <cmath>
 #include <cstring>
 #include <numeric>
@@ -135,46 +137,54 @@ struct BandGrid {
     double eta;
 };
 
-// pass 0: count the band partners of each triangle; pass 1: write them
-// (sorted) with their owner
+// One warp per triangle, lanes over the candidates of the 27 cells around its
+// cell. Pass 0 counts the band partners of each triangle; pass 1 writes them
+// (sorted) with their owner: the hits are compacted in candidate order into
+// the owner slots (scratch), then each one is placed at its rank among them
+// (the partners are distinct), and the owner slots are filled.
 __global__ void k_band_search(int64_t nt, const int32_t* __restrict__ tris, BandGrid g, int pass,
                               int32_t* __restrict__ cnt, const int32_t* __restrict__ ptr, int32_t* __restrict__ bs,
                               int32_t* __restrict__ bt) {
-    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= nt) return;
+    const int64_t t = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (t >= nt) return;  // whole warps
     const int64_t c = g.tcell[t];
     const int64_t c0 = c % g.dim[0], c1 = (c / g.dim[0]) % g.dim[1], c2 = c / (g.dim[0] * g.dim[1]);
     const int32_t* ft = tris + 3 * t;
-    int n = 0;
+    int n = 0;  // hits so far (the same in every lane)
     const int64_t base = pass ? ptr[t] : 0;
     for (int64_t z = max((int64_t)0, c2 - 1); z <= min(g.dim[2] - 1, c2 + 1); ++z)
         for (int64_t y = max((int64_t)0, c1 - 1); y <= min(g.dim[1] - 1, c1 + 1); ++y)
             for (int64_t x = max((int64_t)0, c0 - 1); x <= min(g.dim[0] - 1, c0 + 1); ++x) {
                 const int64_t cc = x + g.dim[0] * (y + g.dim[1] * z);
-                for (int32_t k = g.cstart[cc]; k < g.cstart[cc + 1]; ++k) {
-                    const int32_t s = g.ctri[k];
-                    if (s == (int32_t)t || !band_hit(g.C, g.R, t, s, g.eta) ||
-                        share_vertex_dev(ft, tris + 3 * (int64_t)s))
-                        continue;
-                    if (pass) bs[base + n] = s;
-                    ++n;
+                const int32_t k1 = g.cstart[cc + 1];
+                for (int32_t kb = g.cstart[cc]; kb < k1; kb += 32) {
+                    const int32_t k = kb + lane;
+                    int32_t s = 0;
+                    bool hit = false;
+                    if (k < k1) {
+                        s = g.ctri[k];
+                        hit = s != (int32_t)t && band_hit(g.C, g.R, t, s, g.eta) &&
+                              !share_vertex_dev(ft, tris + 3 * (int64_t)s);
+                    }
+                    const unsigned m = __ballot_sync(0xffffffffu, hit);
+                    if (pass && hit) bt[base + n + __popc(m & ((1u << lane) - 1u))] = s;
+                    n += __popc(m);
                 }
             }
     if (!pass) {
-        cnt[t] = n;
+        if (lane == 0) cnt[t] = n;
         return;
     }
-    // insertion sort of this triangle's partners; owners alongside
-    for (int i = 1; i < n; ++i) {
-        const int32_t v = bs[base + i];
-        int j = i - 1;
-        while (j >= 0 && bs[base + j] > v) {
-            bs[base + j + 1] = bs[base + j];
-            --j;
-        }
-        bs[base + j + 1] = v;
+    __syncwarp();
+    for (int i = lane; i < n; i += 32) {
+        const int32_t v = bt[base + i];
+        int r = 0;
+        for (int j = 0; j < n; ++j) r += bt[base + j] < v;
+        bs[base + r] = v;
     }
-    for (int i = 0; i < n; ++i) bt[base + i] = (int32_t)t;
+    __syncwarp();
+    for (int i = lane; i < n; i += 32) bt[base + i] = (int32_t)t;
 }
 
 // exclusive scan of n counts into ptr[0..n] (one block; n up to 2^28), total in ptr[n]
@@ -301,12 +311,15 @@ int device_scan(int64_t n, const int32_t* cnt, int32_t* ptr, int64_t* total, cud
 }
 
 // transposed positions, diagonal positions and the row of every nonzero
+// one warp per row i, lanes over its entries: the position of each entry's
+// transpose, the row of each entry and the diagonal's position
 __global__ void k_pattern_maps(int64_t nv, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                                int32_t* __restrict__ tpos, int32_t* __restrict__ diag_pos, int32_t* __restrict__ row_of,
                                int* __restrict__ status) {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t i = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
     if (i >= nv) return;
-    for (int32_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+    for (int32_t k = row_ptr[i] + lane; k < row_ptr[i + 1]; k += 32) {
         const int32_t j = col[k];
         row_of[k] = (int32_t)i;
         int32_t lo = row_ptr[j], hi = row_ptr[j + 1];
@@ -324,18 +337,16 @@ __global__ void k_pattern_maps(int64_t nv, const int32_t* __restrict__ row_ptr, 
     }
 }
 
-// f(begin, end) over [0, n) split across up to 16 host threads
+constexpr int MAX_HOST_THREADS = 16;
+
+// f(chunk, begin, end) over [0, n) in contiguous chunks on the host worker
+// pool; returns the number of chunks (chunk c covers [n c / k, n (c + 1) / k))
 template <class F>
-static void parallel_for(int64_t n, F&& f) {
-    int nth = (int)std::min<int64_t>(std::max(1u, std::thread::hardware_concurrency()), 16);
-    nth = (int)std::min<int64_t>(nth, (n + 2047) / 2048);
-    if (nth <= 1) {
-        f((int64_t)0, n);
-        return;
-    }
-    std::vector<std::thread> th;
-    for (int i = 0; i < nth; ++i) th.emplace_back([&, i] { f(n * i / nth, n * (i + 1) / nth); });
-    for (auto& x : th) x.join();
+static int parallel_chunks(int64_t n, F&& f) {
+    const int nth = (int)std::max<int64_t>(
+        1, std::min<int64_t>(std::min(host_threads(), MAX_HOST_THREADS), (n + 2047) / 2048));
+    host_parallel(nth, [&](int i) { f(i, n * i / nth, n * (i + 1) / nth); });
+    return nth;
 }
 
 static int upload(void** dst, const void* src, size_t bytes, size_t* total) {
@@ -438,37 +449,7 @@ static int load(pb_ctx* ctx, const double* verts_in, int64_t nv, const int32_t* 
                 p0[2] * (p1[0] * p2[1] - p1[1] * p2[0]);
     }
     tr.lap("validate");
-    // every undirected edge must appear exactly twice, once in each direction
-    {
-        std::vector<std::pair<uint64_t, int>> e;
-        e.reserve(3 * nt);
-        for (int64_t t = 0; t < nt; ++t)
-            for (int a = 0; a < 3; ++a) {
-                uint64_t i = T[3 * t + a], j = T[3 * t + (a + 1) % 3];
-                uint64_t key = i < j ? (i << 32 | j) : (j << 32 | i);
-                e.push_back({key, i < j ? 1 : -1});
-            }
-        std::sort(e.begin(), e.end());
-        for (size_t k = 0; k < e.size();) {
-            size_t l = k;
-            int s = 0;
-            while (l < e.size() && e[l].first == e[k].first) s += e[l++].second;
-            if (l - k != 2)
-                return set_error(PB_EMESH, "edge (%llu,%llu) is shared by %zu triangles (mesh not closed "
-                                 "or not manifold)", (unsigned long long)(e[k].first >> 32),
-                                 (unsigned long long)(e[k].first & 0xffffffffu), l - k);
-            if (s != 0)
-                return set_error(PB_EMESH, "edge (%llu,%llu) has the same direction in both triangles "
-                                 "(inconsistent orientation)", (unsigned long long)(e[k].first >> 32),
-                                 (unsigned long long)(e[k].first & 0xffffffffu));
-            k = l;
-        }
-    }
-    if (!(vol6 > 0.0))
-        return set_error(PB_EMESH, "enclosed volume is not positive (triangles must be counter-clockwise "
-                         "seen from outside)");
 
-    tr.lap("edges");
     // ---- vertex -> triangle map
     std::vector<int32_t> v2t_ptr(nv + 1, 0), v2t(3 * nt);
     for (int64_t k = 0; k < 3 * nt; ++k) v2t_ptr[T[k] + 1]++;
@@ -478,13 +459,60 @@ static int load(pb_ctx* ctx, const double* verts_in, int64_t nv, const int32_t* 
         for (int64_t t = 0; t < nt; ++t)
             for (int a = 0; a < 3; ++a) v2t[fill[T[3 * t + a]]++] = (int32_t)(3 * t + a);
     }
+    // every undirected edge must lie in exactly two triangles, traversed in
+    // opposite directions: for the edge i -> j of triangle t, the triangles of
+    // vertex i that follow i by j (t itself) and those that precede i by j
+    {
+        std::atomic<int64_t> first_bad{INT64_MAX};  // lowest failing 3 t + a (deterministic report)
+        auto census = [&](int64_t t, int a, int* same, int* opp) {
+            const int32_t i = T[3 * t + a], j = T[3 * t + (a + 1) % 3];
+            *same = *opp = 0;
+            for (int32_t k = v2t_ptr[i]; k < v2t_ptr[i + 1]; ++k) {
+                const int64_t u = v2t[k] / 3;
+                const int c = v2t[k] % 3;
+                *same += T[3 * u + (c + 1) % 3] == j;
+                *opp += T[3 * u + (c + 2) % 3] == j;
+            }
+        };
+        parallel_chunks(nt, [&](int, int64_t b0, int64_t b1) {
+            for (int64_t t = b0; t < b1; ++t)
+                for (int a = 0; a < 3; ++a) {
+                    int same, opp;
+                    census(t, a, &same, &opp);
+                    if (same != 1 || opp != 1) {
+                        int64_t cur = first_bad.load();
+                        while (3 * t + a < cur && !first_bad.compare_exchange_weak(cur, 3 * t + a)) {
+                        }
+                        return;
+                    }
+                }
+        });
+        const int64_t bad = first_bad.load();
+        if (bad != INT64_MAX) {
+            const int64_t t = bad / 3;
+            const int a = (int)(bad % 3);
+            int same, opp;
+            census(t, a, &same, &opp);
+            const int32_t i = T[3 * t + a], j = T[3 * t + (a + 1) % 3];
+            const unsigned long long e0 = (unsigned long long)std::min(i, j), e1 = (unsigned long long)std::max(i, j);
+            if (same + opp != 2)
+                return set_error(PB_EMESH, "edge (%llu,%llu) is shared by %d triangles (mesh not closed or not "
+                                 "manifold)", e0, e1, same + opp);
+            return set_error(PB_EMESH, "edge (%llu,%llu) has the same direction in both triangles (inconsistent "
+                             "orientation)", e0, e1);
+        }
+    }
+    tr.lap("edges");
+    if (!(vol6 > 0.0))
+        return set_error(PB_EMESH, "enclosed volume is not positive (triangles must be counter-clockwise "
+                         "seen from outside)");
     for (int64_t i = 0; i < nv; ++i)
         if (v2t_ptr[i + 1] == v2t_ptr[i])
             return set_error(PB_EMESH, "vertex %lld belongs to no triangle", (long long)i);
 
     tr.lap("v2t");
-    // ---- adjacent triangle pairs (share >= 1 vertex), ordered by (ti, tj):
-    // counted, then filled, per triangle
+    // ---- adjacent triangle pairs (share >= 1 vertex), ordered by (ti, tj),
+    // listed per triangle
     std::vector<int32_t> adj_ptr(nt + 1, 0);
     auto neighbours = [&](int64_t t, std::vector<int32_t>& mark, std::vector<int32_t>& nb) {
         nb.clear();
@@ -500,21 +528,16 @@ static int load(pb_ctx* ctx, const double* verts_in, int64_t nv, const int32_t* 
         }
         std::sort(nb.begin(), nb.end());
     };
-    parallel_for(nt, [&](int64_t b0, int64_t b1) {
+    // one pass: each chunk of triangles lists its pairs in its own buffer, in
+    // triangle order; the buffers are then laid end to end
+    std::vector<std::vector<int4>> chunk_pairs(MAX_HOST_THREADS);
+    const int nchunk = parallel_chunks(nt, [&](int c, int64_t b0, int64_t b1) {
         std::vector<int32_t> mark(nt, -1), nb;
+        std::vector<int4>& out = chunk_pairs[c];
+        out.reserve((size_t)(b1 - b0) * 16);
         for (int64_t t = b0; t < b1; ++t) {
             neighbours(t, mark, nb);
             adj_ptr[t + 1] = (int32_t)nb.size();
-        }
-    });
-    for (int64_t t = 0; t < nt; ++t) adj_ptr[t + 1] += adj_ptr[t];
-    const int64_t n_adj = adj_ptr[nt];
-    std::vector<int4> pairs(n_adj);
-    parallel_for(nt, [&](int64_t b0, int64_t b1) {
-        std::vector<int32_t> mark(nt, -1), nb;
-        for (int64_t t = b0; t < b1; ++t) {
-            neighbours(t, mark, nb);
-            int64_t o = adj_ptr[t];
             for (int32_t s : nb) {
                 int sa[3], sb[3], ns = 0;
                 for (int a = 0; a < 3; ++a)
@@ -543,18 +566,30 @@ static int load(pb_ctx* ctx, const double* verts_in, int64_t nv, const int32_t* 
                     }
                 }
                 int code = pt[0] | pt[1] << 2 | pt[2] << 4 | ps[0] << 6 | ps[1] << 8 | ps[2] << 10;
-                pairs[o++] = make_int4((int)t, s, kind, code);
+                out.push_back(make_int4((int)t, s, kind, code));
             }
         }
     });
+    for (int64_t t = 0; t < nt; ++t) adj_ptr[t + 1] += adj_ptr[t];
+    const int64_t n_adj = adj_ptr[nt];
+    std::vector<int4> pairs(n_adj);
+    {
+        int64_t o = 0;
+        for (int c = 0; c < nchunk; ++c) {
+            std::copy(chunk_pairs[c].begin(), chunk_pairs[c].end(), pairs.begin() + o);
+            o += (int64_t)chunk_pairs[c].size();
+        }
+    }
 
     tr.lap("adjacency");
     // ---- each adjacent pair's reverse; the pairs the near kernels integrate:
     // coincident ones, and one of every two reversed ones (t < s)
     m->n_adj = n_adj;
     std::vector<int32_t> rev(n_adj), coin_list, prim_list;
-    bool rev_ok = true;
-    parallel_for(n_adj, [&](int64_t b0, int64_t b1) {
+    std::atomic<bool> rev_ok{true};
+    std::vector<std::vector<int32_t>> chunk_coin(MAX_HOST_THREADS), chunk_prim(MAX_HOST_THREADS);
+    std::vector<int64_t> chunk_edge(MAX_HOST_THREADS, 0);
+    const int nrc = parallel_chunks(n_adj, [&](int c, int64_t b0, int64_t b1) {
         for (int64_t p = b0; p < b1; ++p) {
             const int32_t t = pairs[p].x, u = pairs[p].y;
             const int4* bg = pairs.data() + adj_ptr[u];
@@ -565,16 +600,19 @@ static int load(pb_ctx* ctx, const double* verts_in, int64_t nv, const int32_t* 
                 continue;
             }
             rev[p] = (int32_t)(q - pairs.data());
+            if (t == u) {
+                chunk_coin[c].push_back((int32_t)p);
+            } else if (t < u) {
+                chunk_prim[c].push_back((int32_t)p);
+                chunk_edge[c] += pairs[p].z == 1;
+            }
         }
     });
     if (!rev_ok) return set_error(PB_EMESH, "internal: pair without reverse");
-    for (int64_t p = 0; p < n_adj; ++p) {
-        const int32_t t = pairs[p].x, u = pairs[p].y;
-        if (t == u) coin_list.push_back((int32_t)p);
-        else if (t < u) {
-            prim_list.push_back((int32_t)p);
-            m->n_prim_edge += pairs[p].z == 1;
-        }
+    for (int c = 0; c < nrc; ++c) {  // in pair order
+        coin_list.insert(coin_list.end(), chunk_coin[c].begin(), chunk_coin[c].end());
+        prim_list.insert(prim_list.end(), chunk_prim[c].begin(), chunk_prim[c].end());
+        m->n_prim_edge += chunk_edge[c];
     }
 
     tr.lap("reverse");
@@ -655,7 +693,7 @@ static int load(pb_ctx* ctx, const double* verts_in, int64_t nv, const int32_t* 
                 break;
             }
             BandGrid g = {dC, dR, dcs, dct, dtc, {dim[0], dim[1], dim[2]}, eta};
-            const unsigned nb = (unsigned)((nt + 127) / 128);
+            const unsigned nb = (unsigned)((nt * 32 + 127) / 128);  // a warp per triangle
             rc = dev_alloc((void**)&m->band_ptr, sizeof(int32_t) * (nt + 1));
             if (rc != PB_OK) break;
             k_band_search<<<nb, 128>>>(nt, m->tris, g, 0, dcnt, nullptr, nullptr, nullptr);
@@ -769,7 +807,7 @@ static int load(pb_ctx* ctx, const double* verts_in, int64_t nv, const int32_t* 
     PB_TRY(dev_alloc((void**)&m->row_of, sizeof(int32_t) * nnz));
     PB_TRY(dev_alloc((void**)&m->diag_pos, sizeof(int32_t) * nv));
     tot += sizeof(int32_t) * (3 * nnz + nv);
-    k_pattern_maps<<<(unsigned)((nv + 127) / 128), 128>>>(nv, m->row_ptr, m->col, m->tpos, m->diag_pos, m->row_of,
+    k_pattern_maps<<<(unsigned)((nv * 32 + 127) / 128), 128>>>(nv, m->row_ptr, m->col, m->tpos, m->diag_pos, m->row_of,
                                                           m->status);
     ::pb::count_launch();
     PB_TRY(dev_alloc((void**)&m->tgeo, sizeof(double) * 16 * nt));

@@ -181,6 +181,41 @@ __device__ __forceinline__ double corner(const TriFrame& f, int a, int k) {
     return f.q0[k] + (r >= 1 ? f.e1[k] : 0.0) + (r >= 2 ? f.e2[k] : 0.0);
 }
 
+// e^x for x <= 0 (the Yukawa factor e^{-kappa r}) by the table-driven method
+// of Tang (ACM Trans. Math. Software 15(2), 1989): x = (32 m + j) ln2/32 + r
+// with |r| <= ln2/64, and e^x = 2^m 2^{j/32} e^r, with 2^{j/32} from a table
+// (correctly rounded doubles) and e^r its Taylor polynomial of degree 6
+// (remainder below 2e-18). The reduction subtracts n ln2/32 in two parts, the
+// first with 37 significant bits so that n times it is exact for |n| < 2^15.
+// Arguments below -700 give 0 (the exact value is below 1e-304).
+__device__ const double g_exp2_32[32] = {
+    0x1.0000000000000p+0, 0x1.059b0d3158574p+0, 0x1.0b5586cf9890fp+0, 0x1.11301d0125b51p+0,
+    0x1.172b83c7d517bp+0, 0x1.1d4873168b9aap+0, 0x1.2387a6e756238p+0, 0x1.29e9df51fdee1p+0,
+    0x1.306fe0a31b715p+0, 0x1.371a7373aa9cbp+0, 0x1.3dea64c123422p+0, 0x1.44e086061892dp+0,
+    0x1.4bfdad5362a27p+0, 0x1.5342b569d4f82p+0, 0x1.5ab07dd485429p+0, 0x1.6247eb03a5585p+0,
+    0x1.6a09e667f3bcdp+0, 0x1.71f75e8ec5f74p+0, 0x1.7a11473eb0187p+0, 0x1.82589994cce13p+0,
+    0x1.8ace5422aa0dbp+0, 0x1.93737b0cdc5e5p+0, 0x1.9c49182a3f090p+0, 0x1.a5503b23e255dp+0,
+    0x1.ae89f995ad3adp+0, 0x1.b7f76f2fb5e47p+0, 0x1.c199bdd85529cp+0, 0x1.cb720dcef9069p+0,
+    0x1.d5818dcfba487p+0, 0x1.dfc97337b9b5fp+0, 0x1.ea4afa2a490dap+0, 0x1.f50765b6e4540p+0};
+
+__device__ __forceinline__ double exp_nonpos(double x) {
+    const double shifter = 0x1.8p52;  // adding it rounds to an integer held in the low mantissa bits
+    const double tn = __fma_rn(x, 0x1.71547652b82fep+5, shifter);  // x 32/ln2, rounded
+    const int n = __double2loint(tn);
+    const double nd = __dsub_rn(tn, shifter);
+    const double r = __fma_rn(-nd, 0x1.cf79abc9e3b3ap-45, __fma_rn(-nd, 0x1.62e42fefa0000p-6, x));
+    double q = 1.0 / 720.0;
+    q = __fma_rn(q, r, 1.0 / 120.0);
+    q = __fma_rn(q, r, 1.0 / 24.0);
+    q = __fma_rn(q, r, 1.0 / 6.0);
+    q = __fma_rn(q, r, 0.5);
+    q = __fma_rn(q, r, 1.0);
+    q = __fma_rn(q, r, 1.0);
+    const double v = __ldg(g_exp2_32 + (n & 31)) * q;
+    const long long bits = __double_as_longlong(v) + ((long long)(n >> 5) << 52);  // times 2^m
+    return x < -700.0 ? 0.0 : __longlong_as_double(bits);
+}
+
 // Accumulators: SL[9], SY[9], KL[9], KY[9], sum w G_L, sum w G_Y (38); with
 // the reversed pair also KTL[9], KTY[9] (56): the double-layer kernel with the
 // normal of the first triangle, which is the K block of the reversed pair.
@@ -196,7 +231,7 @@ __device__ __forceinline__ void accum_point(double* acc, double w, const double*
     const double rinv = rsqrt(r2);
     const double r = r2 * rinv;
     const double gl = rinv * 0.07957747154594767;  // 1 / (4 pi r)
-    const double ek = exp(-kappa * r);
+    const double ek = exp_nonpos(-kappa * r);
     const double gy = ek * gl;
     const double fl = gl * rinv * rinv;            // 1 / (4 pi r^3)
     const double fy_over_fl = ek * (1.0 + kappa * r);
@@ -225,6 +260,85 @@ __device__ __forceinline__ void accum_point(double* acc, double w, const double*
     }
     acc[36] += w * gl;
     acc[37] += w * gy;
+}
+
+// Regularised rules in the frames' own coordinates. A point of a frame is
+// q0 + s e1 + t e2 and its corner basis values are mu = (1 - s, s - t, t) in the
+// frame's corner order; so the quadrature sums are taken as moments in the
+// monomial bases (1, s, t) x (1, s', t') and turned into the corner blocks once
+// per pair (frame_to_corner). For an adjacent pair both frames start at the
+// shared vertex, and d = x - y is formed from the frame vectors directly.
+// mom[9 k + 3 alpha + beta], k = G_L, G_Y, K_L, K_Y (and with SYM the reversed
+// pair's double layers K^T_L, K^T_Y).
+template <bool SYM>
+__device__ __forceinline__ void accum_frame(double* mom, double w, double s, double t, double s2, double t2,
+                                            const double* dq, const TriFrame& A, const TriFrame& B, double kappa) {
+    double d[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k)
+        d[k] = __fma_rn(-t2, B.e2[k], __fma_rn(-s2, B.e1[k], __fma_rn(t, A.e2[k], __fma_rn(s, A.e1[k], dq[k]))));
+    const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    const double rinv = rsqrt(r2);
+    const double r = r2 * rinv;
+    const double gl = rinv * 0.07957747154594767;  // 1 / (4 pi r)
+    const double ek = exp_nonpos(-kappa * r);
+    const double fl = gl * rinv * rinv;  // 1 / (4 pi r^3)
+    const double fy_over_fl = ek * (1.0 + kappa * r);
+    const double kl = fl * (d[0] * B.n[0] + d[1] * B.n[1] + d[2] * B.n[2]);
+    double g[6] = {gl, ek * gl, kl, kl * fy_over_fl, 0.0, 0.0};
+    if (SYM) {
+        const double ktl = fl * -(d[0] * A.n[0] + d[1] * A.n[1] + d[2] * A.n[2]);  // (y - x).n_x
+        g[4] = ktl;
+        g[5] = ktl * fy_over_fl;
+    }
+    const double ws = w * s, wt = w * t;
+    const double m[9] = {w, w * s2, w * t2, ws, ws * s2, ws * t2, wt, wt * s2, wt * t2};
+    constexpr int NK = SYM ? 6 : 4;
+#pragma unroll
+    for (int k = 0; k < NK; ++k)
+#pragma unroll
+        for (int c = 0; c < 9; ++c) mom[9 * k + c] += g[k] * m[c];
+}
+
+// coincident pair: one frame, d = (s - s') e1 + (t - t') e2; k = G_L, G_Y
+__device__ __forceinline__ void accum_coin_frame(double* mom, double w, double s, double t, double s2, double t2,
+                                                 const TriFrame& A, double kappa) {
+    const double ds = s - s2, dt = t - t2;
+    double d[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) d[k] = __fma_rn(dt, A.e2[k], ds * A.e1[k]);
+    const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
+    const double rinv = rsqrt(r2);
+    const double gl = rinv * 0.07957747154594767;  // 1 / (4 pi r)
+    const double gy = exp_nonpos(-kappa * (r2 * rinv)) * gl;
+    const double ws = w * s, wt = w * t;
+    const double m[9] = {w, w * s2, w * t2, ws, ws * s2, ws * t2, wt, wt * s2, wt * t2};
+#pragma unroll
+    for (int c = 0; c < 9; ++c) {
+        mom[c] += gl * m[c];
+        mom[9 + c] += gy * m[c];
+    }
+}
+
+// moments of one kernel (mom[3 alpha + beta] over (1, s, t) x (1, s', t')) into
+// its corner block out[3 a + b] = sum w g l_a(x) l_b(y)
+__device__ __forceinline__ void frame_to_corner(const double* mom, const TriFrame& A, const TriFrame& B,
+                                                double* out) {
+    double R[3][3], U[3][3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {  // mu_0 = 1 - s, mu_1 = s - t, mu_2 = t on the first frame
+        R[0][b] = mom[b] - mom[3 + b];
+        R[1][b] = mom[3 + b] - mom[6 + b];
+        R[2][b] = mom[6 + b];
+    }
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {  // and on the second
+        U[a][0] = R[a][0] - R[a][1];
+        U[a][1] = R[a][1] - R[a][2];
+        U[a][2] = R[a][2];
+    }
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) out[3 * a + b] = U[A.inv[a]][B.inv[b]];
 }
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -278,6 +392,7 @@ k_near_pairs(const double* __restrict__ verts, const int32_t* __restrict__ tris,
              const int32_t* __restrict__ rev, SSTable tab, int n4, Rule rule, double kappa,
              double* __restrict__ ss_out, double* __restrict__ far_out) {
     constexpr int NA = SYM ? NACC_SYM : NACC_NEAR;
+    constexpr int NM = SYM ? 54 : 36;  // frame moments
     __shared__ TriFrame frames[NEAR_THREADS / 32][2];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t li = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
@@ -293,17 +408,21 @@ k_near_pairs(const double* __restrict__ verts, const int32_t* __restrict__ tris,
     const int nreg = kind == 2 ? 2 : 6;
     const int e0 = tab.off[kind];
     const double jac_ab = (2.0 * A.area) * (2.0 * B.area);
+    const double dq[3] = {A.q0[0] - B.q0[0], A.q0[1] - B.q0[1], A.q0[2] - B.q0[2]};  // 0: the shared vertex
     double acc[NA];
-    for (int k = 0; k < NA; ++k) acc[k] = 0.0;
-    for (int idx = lane; idx < nreg * n4; idx += 32) {
-        const int e = e0 + idx;
-        const double w = tab.w[e] * jac_ab;
-        double x[3], y[3], lx[3], ly[3];
-        frame_point(A, tab.sx[e], tab.tx[e], x, lx);
-        frame_point(B, tab.sy[e], tab.ty[e], y, ly);
-        accum_point<SYM>(acc, w, x, y, A.n, B.n, lx, ly, kappa);
+    {
+        double mom[NM];
+        for (int k = 0; k < NM; ++k) mom[k] = 0.0;
+        for (int idx = lane; idx < nreg * n4; idx += 32) {
+            const int e = e0 + idx;
+            accum_frame<SYM>(mom, tab.w[e] * jac_ab, tab.sx[e], tab.tx[e], tab.sy[e], tab.ty[e], dq, A, B, kappa);
+        }
+        for (int k = 0; k < NM; ++k) mom[k] = warp_sum(mom[k]);
+        // corner blocks in the accumulator layout of accum_point
+        for (int k = 0; k < NM / 9; ++k) frame_to_corner(mom + 9 * k, A, B, acc + (k < 4 ? 9 * k : 38 + 9 * (k - 4)));
+        acc[36] = mom[0];  // sum w G_L: the (1, 1) moment
+        acc[37] = mom[9];
     }
-    for (int k = 0; k < NA; ++k) acc[k] = warp_sum(acc[k]);
     const double* gA = tgeo + 16 * (int64_t)pr.x;
     const double* gB = tgeo + 16 * (int64_t)pr.y;
     if (lane == 0) expand_blocks(acc, A, B, gA, gB, kappa, false, ss_out + 54 * p);
@@ -339,7 +458,7 @@ __device__ __forceinline__ void accum_v(double* acc, double w, const double* x, 
     const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
     const double rinv = rsqrt(r2);
     const double gl = rinv * 0.07957747154594767;  // 1 / (4 pi r)
-    const double gy = exp(-kappa * (r2 * rinv)) * gl;
+    const double gy = exp_nonpos(-kappa * (r2 * rinv)) * gl;
     for (int a = 0; a < 3; ++a) {
         const double wa = w * lx[a];
         for (int b = 0; b < 3; ++b) {
@@ -387,16 +506,19 @@ k_coin_pairs(const double* __restrict__ verts, const int32_t* __restrict__ tris,
     const int e0 = tab.off[0];
     const double jac_ab = (2.0 * A.area) * (2.0 * A.area);
     double acc[20];
-    for (int k = 0; k < 20; ++k) acc[k] = 0.0;
-    for (int idx = lane; idx < 3 * n4; idx += 32) {
-        const int e = e0 + idx;
-        const double w = tab.w[e] * jac_ab;
-        double x[3], y[3], lx[3], ly[3];
-        frame_point(A, tab.sx[e], tab.tx[e], x, lx);
-        frame_point(A, tab.sy[e], tab.ty[e], y, ly);
-        accum_v(acc, w, x, y, lx, ly, kappa);
+    {
+        double mom[18];
+        for (int k = 0; k < 18; ++k) mom[k] = 0.0;
+        for (int idx = lane; idx < 3 * n4; idx += 32) {
+            const int e = e0 + idx;
+            accum_coin_frame(mom, tab.w[e] * jac_ab, tab.sx[e], tab.tx[e], tab.sy[e], tab.ty[e], A, kappa);
+        }
+        for (int k = 0; k < 18; ++k) mom[k] = warp_sum(mom[k]);
+        frame_to_corner(mom, A, A, acc);
+        frame_to_corner(mom + 9, A, A, acc + 9);
+        acc[18] = mom[0];
+        acc[19] = mom[9];
     }
-    for (int k = 0; k < 20; ++k) acc[k] = warp_sum(acc[k]);
     const double* gA = tgeo + 16 * (int64_t)pr.x;
     if (lane == 0) expand_coin(acc, A, gA, kappa, ss_out + 54 * p);
     for (int k = 0; k < 20; ++k) acc[k] = 0.0;
@@ -457,7 +579,7 @@ __device__ __forceinline__ void band_pass(double* acc, const double (&pa)[3][3],
             const double rinv = rsqrt(r2);
             const double r = r2 * rinv;
             const double gl = rinv * 0.07957747154594767;  // 1 / (4 pi r)
-            const double ek = exp(-kappa * r);
+            const double ek = exp_nonpos(-kappa * r);
             const double fl = gl * rinv * rinv;  // 1 / (4 pi r^3)
             const double fy_over_fl = ek * (1.0 + kappa * r);
             const double kl = fl * (d0 * nb[0] + d1 * nb[1] + d2 * nb[2]);
@@ -833,6 +955,25 @@ extern "C" int pb_near_build(pb_ctx* ctx, const pb_mesh* mesh, double kappa, pb_
         return rc;
     }
     *out = nf;
+    return PB_OK;
+}
+
+namespace pb {
+__global__ void k_exp_selftest(const double* __restrict__ x, double* __restrict__ y, int64_t n) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) y[i] = exp_nonpos(x[i]);
+}
+}  // namespace pb
+
+extern "C" int pb_selftest_exp(pb_ctx* ctx, const double* x, double* y, int64_t n, void* stream) {
+    if (!ctx || (n > 0 && (!x || !y)) || n < 0) return set_error(PB_EINVAL, "pb_selftest_exp: bad argument");
+    if (n == 0) return PB_OK;
+    PB_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t s = (cudaStream_t)stream;
+    k_exp_selftest<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(x, y, n);
+    ::pb::count_launch();
+    PB_CUDA(cudaGetLastError());
+    PB_CUDA(cudaStreamSynchronize(s));
     return PB_OK;
 }
 
