@@ -936,11 +936,11 @@ int apply_blockop(const pb_mesh* m, const pb_near* nf, const BlockOp& B, int pre
             k_tri_reduce<double><<<tb, 128, 0, s>>>(nt, np, rule, S, fp.mode, fp, m->tgeo, m->pts64, part, tri);
             ::pb::count_launch();
         } else if (prec == PB_F32 && m->ctx->tree_enable && np >= m->ctx->tree_min_points && np > 256) {
-            // treecode far field (inner iterations), one split of partial sums
-            PB_TRY(ws_reserve(const_cast<pb_mesh*>(m)->ws_part, sizeof(float) * (size_t)nacc * np));
-            float* part = (float*)m->ws_part.ptr;
-            PB_TRY(tree_far(m, fp, x, need_u, need_v, part, s));
-            k_tri_reduce<float><<<tb, 128, 0, s>>>(nt, np, rule, 1, fp.mode, fp, m->tgeo, m->pts64, part, tri);
+            // treecode far field (inner iterations)
+            float* part = nullptr;
+            int S = 1;
+            PB_TRY(tree_far(m, fp, x, need_u, need_v, &part, &S, s));
+            k_tri_reduce<float><<<tb, 128, 0, s>>>(nt, np, rule, S, fp.mode, fp, m->tgeo, m->pts64, part, tri);
             ::pb::count_launch();
         } else if (tuned(m->ctx, np, fp.mode, prec == PB_F32_ACCURATE).kernel == 2 ||
                    (tuned(m->ctx, np, fp.mode, prec == PB_F32_ACCURATE).kernel == 0 && m->ctx->pair_kernel == 2)) {

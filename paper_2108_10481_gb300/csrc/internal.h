@@ -256,9 +256,10 @@ struct BatchScratch {
 int apply_blockops_batched(const std::vector<FarJob>& jobs, int prec, BatchScratch& bs, cudaStream_t s);
 
 // treecode far field (FP32): per-target partial sums in the direct kernel's
-// one-split layout; the tree is built on first use
-int tree_far(const pb_mesh* m, const FarPlan& fp, const double* x, bool need_u, bool need_v, float* part,
-             cudaStream_t s);
+// split layout, in the mesh's ws_part (*part_out, *nsplit slices); the tree is
+// built on first use
+int tree_far(const pb_mesh* m, const FarPlan& fp, const double* x, bool need_u, bool need_v, float** part_out,
+             int* nsplit, cudaStream_t s);
 void tree_free(PbTree* t);
 int tree_info(const pb_mesh* m, int64_t out[6]);
 

@@ -372,15 +372,17 @@ __device__ void expand_blocks(const double* acc, const TriFrame& A, const TriFra
 
 constexpr int NEAR_THREADS = 128;
 
-// FP64 flops per quadrature point pair by formula count (a fused multiply-add
-// counted as two). Kernel evaluation (difference, r^2, rsqrt, r, 1/(4 pi r),
-// exp(-kappa r), Yukawa factor, 1/r^3, (1 + kappa r), d.n_y, both double
-// layers): 24; with the reversed pair's double layer (d.n_x and its two
-// kernels): 33. Accumulation: w l_a (3), l_a l_b (9), one FMA per block entry
-// and per sum w G: 4 x 9 + 2 FMA (88 in all), 6 x 9 + 2 (124). Coincident
-// pairs: evaluation 15 (no double layer), accumulation 3 + 9 + 2 x 20 = 52.
-constexpr double NEAR_FLOPS_SYM = 33 + 124;
-constexpr double NEAR_FLOPS_COIN = 15 + 52;
+// FP64 flops per quadrature point pair of a regularised rule by formula count
+// (a fused multiply-add counted as two). Kernel evaluation: d = x - y from the
+// frame vectors (24); r^2 (5), rsqrt, r, 1/(4 pi r), kappa r, exp, the Yukawa
+// single layer (6), 1/r^3 (2), (1 + kappa r) and the Yukawa double-layer
+// factor (3), d.n_y (5) and both double layers (2): 47; with the reversed
+// pair's double layer, d.n_x (5) and its two kernels (2): 54. Accumulation:
+// the eight products of w with (1, s, t) x (1, s', t') and one FMA per kernel
+// and moment, 8 + 2 x 6 x 9 (116). Coincident pairs: d from (s - s', t - t')
+// (11), r^2 to the Yukawa single layer (11); 8 + 2 x 2 x 9 (44).
+constexpr double NEAR_FLOPS_SYM = 54 + 116;
+constexpr double NEAR_FLOPS_COIN = 22 + 44;
 
 // One warp per listed pair. Writes ss[p][54] (regularised) and far[p][54] (far
 // rule, identical points excluded); with SYM also the blocks of the reversed

@@ -124,8 +124,10 @@ static size_t footprint(pb_ctx* ctx, int64_t nv, int64_t nt, const pb_quad_plan&
     int S = far_splits_estimate(ctx, (int64_t)np);
     double part = (double)S * 10 * np * 8;
     double work = src + part + 48 * nt + 48 * nnz + 128 * nv;
-    if (ctx->tree_enable && np >= (double)ctx->tree_min_points)
+    if (ctx->tree_enable && np >= (double)ctx->tree_min_points) {
         work += 330 * np;  // treecode: tree-ordered sources, proxies of about np / 64 clusters, lists
+        work += std::max(0.0, 8.0 * 10 * 4 * np - part);  // its partial sums: up to 8 FP32 slices
+    }
     double n2 = 2.0 * nv;
     double nchunk = std::ceil(n2 / 2048.0);
     double gm = 8 * ((mmax + 1) * n2 + n2 + (double)(mmax + 1) * mmax + 4 * mmax + 2 + (mmax + 2) * nchunk + 16);

@@ -394,7 +394,9 @@ static int iterate(Solver& S, GmresWork& G, int prec, int j, StepGraph** replaye
     if (!S.graphs || g.failed || (j == 0 && !g.exec)) return gm_iteration(S, G, prec);
     if (!g.exec) {
         const int a0 = S.applies;
+        PhaseTrace tr("gmres");
         PB_TRY(graph_capture(g, S.s, [&] { return gm_iteration(S, G, prec); }));
+        tr.lap("capture");
         g.applies = S.applies - a0;
         S.applies = a0;
         if (g.failed) return gm_iteration(S, G, prec);
@@ -690,6 +692,7 @@ static int solve_one(const pb_mesh* m, const pb_near* nf, const pb_solve_opts* o
         // Iterative refinement. Outer residual: split-coordinate FP32 pair sums
         // accumulated in FP64 per source tile plus the FP64 near field. Inner:
         // GMRES (FP64 Arnoldi) on A d = r with the FP32 operator.
+        PhaseTrace tr("mixed");
         double* rr = nullptr;
         rc = dev_alloc((void**)&rr, sizeof(double) * 2 * n2);
         if (rc == PB_OK) {
@@ -706,9 +709,11 @@ static int solve_one(const pb_mesh* m, const pb_near* nf, const pb_solve_opts* o
                     S.applies++;
                     k_sub<<<nb(n2), 256, 0, s>>>(n2, b, S.t3, rr); ::pb::count_launch();
                 }
+                tr.lap("outer_residual");
                 // ||P^-1 r|| with the accurate operator (no iterations)
                 rc = gmres(S, G, PB_F32_ACCURATE, rr, dd, true, 0.0, 0.0, 0, &it, &res, &beta);
                 if (rc != PB_OK) break;
+                tr.lap("outer_norm");
                 if (outer == 0) bnorm = beta;
                 double prev = rel;
                 rel = bnorm > 0.0 ? beta / bnorm : 0.0;
@@ -720,6 +725,7 @@ static int solve_one(const pb_mesh* m, const pb_near* nf, const pb_solve_opts* o
                 rc = gmres(S, G, PB_F32, rr, dd, true, inner, 0.0, o->max_it, &it, &res, &beta);
                 total_it += it;
                 if (rc != PB_OK) break;
+                tr.lap("inner_gmres");
                 k_add_inplace<<<nb(n2), 256, 0, s>>>(n2, dd, x); ::pb::count_launch();
             }
             cudaFree(rr);

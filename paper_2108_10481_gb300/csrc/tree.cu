@@ -29,7 +29,8 @@ namespace pb {
 
 constexpr int TREE_LEAF = 128;     // targets per leaf (one CTA)
 constexpr int TREE_REC = 12;       // floats per tree source / proxy record
-constexpr int TREE_MAXN = 8;       // largest Chebyshev order + 1
+constexpr int TREE_MAXN = 8;
+constexpr int TREE_MAX_SPLITS = 8;  // CTAs sharing one leaf's interaction lists       // largest Chebyshev order + 1
 
 struct TreeCoef {
     float k[2][4];
@@ -509,7 +510,9 @@ __device__ __forceinline__ float2 t_fma2(float2 a, float2 b, float2 c) {
 }
 __device__ __forceinline__ float2 t_splat(float v) { return make_float2(v, v); }
 
-// One CTA per leaf of targets, TREE_LEAF threads in two halves. A thread holds
+// One CTA per leaf of targets and split (blockIdx.y of gridDim.y: the split
+// takes that share of the leaf's far list and of its near list and writes its
+// own slice of partial sums), TREE_LEAF threads in two halves. A thread holds
 // two targets (the leaf's i-th and (i + TREE_LEAF/2)-th points) in packed
 // f32x2 arithmetic; the two halves take alternate sources of every staged
 // tile and add their sums through shared memory at the end.
@@ -529,6 +532,12 @@ k_tree_eval(int64_t np, int nprox, const int32_t* __restrict__ perm, const int32
     constexpr int TILE = 128;
     __shared__ __align__(16) float tile[TILE * TREE_REC];
     const int leaf = blockIdx.x;
+    const int sp = blockIdx.y, nsp = gridDim.y;
+    const int32_t fb0 = far_ptr[leaf], nfar = far_ptr[leaf + 1] - fb0;
+    const int32_t qb0 = near_ptr[leaf], nnear = near_ptr[leaf + 1] - qb0;
+    const int32_t fb = fb0 + (int32_t)((int64_t)nfar * sp / nsp), fe = fb0 + (int32_t)((int64_t)nfar * (sp + 1) / nsp);
+    const int32_t qb = qb0 + (int32_t)((int64_t)nnear * sp / nsp), qe = qb0 + (int32_t)((int64_t)nnear * (sp + 1) / nsp);
+    part += (int64_t)sp * NACC * np;
     const int32_t tb = leaf_rng[2 * leaf], te = leaf_rng[2 * leaf + 1];
     const int half = (int)threadIdx.x / TREE_HALF;
     const int32_t ti0 = tb + (int32_t)(threadIdx.x % TREE_HALF), ti1 = ti0 + TREE_HALF;
@@ -552,7 +561,7 @@ k_tree_eval(int64_t np, int nprox, const int32_t* __restrict__ perm, const int32
     for (int k = 0; k < NACC; ++k) acc[k] = t_splat(0.f);
     const bool any = live0;  // the first target of a thread is live whenever the second is
     // far clusters through their proxies
-    for (int32_t f = far_ptr[leaf]; f < far_ptr[leaf + 1]; ++f) {
+    for (int32_t f = fb; f < fe; ++f) {
         const float* pr = prox + (int64_t)far_idx[f] * nprox * TREE_REC;
         for (int c0 = 0; c0 < nprox; c0 += TILE) {
             const int cnt = min(TILE, nprox - c0);
@@ -596,7 +605,7 @@ k_tree_eval(int64_t np, int nprox, const int32_t* __restrict__ perm, const int32
         }
     }
     // near sources directly (identical points skipped)
-    for (int32_t q = near_ptr[leaf]; q < near_ptr[leaf + 1]; ++q) {
+    for (int32_t q = qb; q < qe; ++q) {
         const int32_t sb = near_rng[2 * q], se = near_rng[2 * q + 1];
         for (int32_t c0 = sb; c0 < se; c0 += TILE) {
             const int cnt = min(TILE, se - c0);
@@ -668,8 +677,8 @@ k_tree_eval(int64_t np, int nprox, const int32_t* __restrict__ perm, const int32
 
 // y-part of the far field by the treecode into part (one split, the direct
 // kernel's layout): builds the tree of the mesh on first use.
-int tree_far(const pb_mesh* mc, const FarPlan& fp, const double* x, bool need_u, bool need_v, float* part,
-             cudaStream_t s) {
+int tree_far(const pb_mesh* mc, const FarPlan& fp, const double* x, bool need_u, bool need_v, float** part_out,
+             int* nsplit, cudaStream_t s) {
     pb_mesh* m = const_cast<pb_mesh*>(mc);
     pb_ctx* ctx = m->ctx;
     if (m->tree && (m->tree->n != ctx->tree_order + 1 || m->tree->theta != ctx->tree_theta)) {
@@ -707,19 +716,26 @@ int tree_far(const pb_mesh* mc, const FarPlan& fp, const double* x, bool need_u,
         for (int j = 0; j < 4; ++j) cf.k[R][j] = (float)fp.k[R][j];
     cf.kappa = (float)fp.kappa;
     cf.mk2 = (float)(-fp.kappa * 1.4426950408889634);
+    // splits of each leaf's lists, so that the grid holds about eight CTAs per SM
+    const int nacc = fp.mode == 0 ? 2 : 10;
+    const int S = (int)std::min<int64_t>(
+        TREE_MAX_SPLITS, std::max<int64_t>(1, (8LL * std::max(1, ctx->num_sms) + t->nleaf - 1) / t->nleaf));
+    PB_TRY(ws_reserve(m->ws_part, sizeof(float) * (size_t)S * nacc * np));
+    float* part = (float*)m->ws_part.ptr;
+    const dim3 grid((unsigned)t->nleaf, (unsigned)S);
     Timer tm(ctx, PB_KERNEL_TREE32, s, (double)(t->direct_pairs + t->proxy_pairs),
              fp.mode == 0 ? 25.0 : 36.0);
     if (fp.mode == 0)
-        k_tree_eval<0><<<(unsigned)t->nleaf, TREE_TPB, 0, s>>>(np, t->nprox, t->perm, t->leaf_rng, t->far_ptr,
-                                                                t->far_idx, t->near_ptr, t->near_rng, rec, prox, cf,
-                                                                part);
+        k_tree_eval<0><<<grid, TREE_TPB, 0, s>>>(np, t->nprox, t->perm, t->leaf_rng, t->far_ptr, t->far_idx,
+                                                 t->near_ptr, t->near_rng, rec, prox, cf, part);
     else
-        k_tree_eval<1><<<(unsigned)t->nleaf, TREE_TPB, 0, s>>>(np, t->nprox, t->perm, t->leaf_rng, t->far_ptr,
-                                                                t->far_idx, t->near_ptr, t->near_rng, rec, prox, cf,
-                                                                part);
+        k_tree_eval<1><<<grid, TREE_TPB, 0, s>>>(np, t->nprox, t->perm, t->leaf_rng, t->far_ptr, t->far_idx,
+                                                 t->near_ptr, t->near_rng, rec, prox, cf, part);
     ::pb::count_launch();
     tm.stop();
     PB_CUDA(cudaGetLastError());
+    *part_out = part;
+    *nsplit = S;
     return PB_OK;
 }
 
