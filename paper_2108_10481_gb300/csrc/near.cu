@@ -118,9 +118,13 @@ struct SSTable {
     const double* sy;
     const double* ty;
     const double* w;
+    // w times the monomials (s', t', s, s s', s t', t, t s', t t') of the
+    // entry's frame coordinates: mono[c * n + e]
+    const double* mono;
     int off[3];  // first entry of kind 0, 1, 2
     int n;       // entries in all
 };
+constexpr int SS_TABLE_ARRAYS = 13;  // sx, tx, sy, ty, w and the eight weighted monomials
 
 __global__ void k_ss_table(Gauss gq, int n, double* __restrict__ tab) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
@@ -139,7 +143,11 @@ __global__ void k_ss_table(Gauss gq, int n, double* __restrict__ tab) {
     tab[n + e] = tx;
     tab[2 * n + e] = sy;
     tab[3 * n + e] = ty;
-    tab[4 * n + e] = gq.w[i0] * gq.w[i1] * gq.w[i2] * gq.w[i3] * jac;
+    const double w = gq.w[i0] * gq.w[i1] * gq.w[i2] * gq.w[i3] * jac;
+    tab[4 * n + e] = w;
+    const double ws = w * sx, wt = w * tx;
+    const double mono[8] = {w * sy, w * ty, ws, ws * sy, ws * ty, wt, wt * sy, wt * ty};
+    for (int c = 0; c < 8; ++c) tab[(5 + c) * n + e] = mono[c];
 }
 
 // Geometry of one triangle in the reordered frame of its singular map:
@@ -271,8 +279,9 @@ __device__ __forceinline__ void accum_point(double* acc, double w, const double*
 // mom[9 k + 3 alpha + beta], k = G_L, G_Y, K_L, K_Y (and with SYM the reversed
 // pair's double layers K^T_L, K^T_Y).
 template <bool SYM>
-__device__ __forceinline__ void accum_frame(double* mom, double w, double s, double t, double s2, double t2,
-                                            const double* dq, const TriFrame& A, const TriFrame& B, double kappa) {
+__device__ __forceinline__ void accum_frame(double* mom, const SSTable& tab, int e, const double* dq,
+                                            const TriFrame& A, const TriFrame& B, double kappa) {
+    const double s = tab.sx[e], t = tab.tx[e], s2 = tab.sy[e], t2 = tab.ty[e];
     double d[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k)
@@ -291,8 +300,10 @@ __device__ __forceinline__ void accum_frame(double* mom, double w, double s, dou
         g[4] = ktl;
         g[5] = ktl * fy_over_fl;
     }
-    const double ws = w * s, wt = w * t;
-    const double m[9] = {w, w * s2, w * t2, ws, ws * s2, ws * t2, wt, wt * s2, wt * t2};
+    double m[9];  // w (1, s, t) x (1, s', t'), from the table
+    m[0] = tab.w[e];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) m[1 + c] = tab.mono[c * tab.n + e];
     constexpr int NK = SYM ? 6 : 4;
 #pragma unroll
     for (int k = 0; k < NK; ++k)
@@ -301,9 +312,9 @@ __device__ __forceinline__ void accum_frame(double* mom, double w, double s, dou
 }
 
 // coincident pair: one frame, d = (s - s') e1 + (t - t') e2; k = G_L, G_Y
-__device__ __forceinline__ void accum_coin_frame(double* mom, double w, double s, double t, double s2, double t2,
-                                                 const TriFrame& A, double kappa) {
-    const double ds = s - s2, dt = t - t2;
+__device__ __forceinline__ void accum_coin_frame(double* mom, const SSTable& tab, int e, const TriFrame& A,
+                                                 double kappa) {
+    const double ds = tab.sx[e] - tab.sy[e], dt = tab.tx[e] - tab.ty[e];
     double d[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) d[k] = __fma_rn(dt, A.e2[k], ds * A.e1[k]);
@@ -311,8 +322,10 @@ __device__ __forceinline__ void accum_coin_frame(double* mom, double w, double s
     const double rinv = rsqrt(r2);
     const double gl = rinv * 0.07957747154594767;  // 1 / (4 pi r)
     const double gy = exp_nonpos(-kappa * (r2 * rinv)) * gl;
-    const double ws = w * s, wt = w * t;
-    const double m[9] = {w, w * s2, w * t2, ws, ws * s2, ws * t2, wt, wt * s2, wt * t2};
+    double m[9];
+    m[0] = tab.w[e];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) m[1 + c] = tab.mono[c * tab.n + e];
 #pragma unroll
     for (int c = 0; c < 9; ++c) {
         mom[c] += gl * m[c];
@@ -378,11 +391,12 @@ constexpr int NEAR_THREADS = 128;
 // single layer (6), 1/r^3 (2), (1 + kappa r) and the Yukawa double-layer
 // factor (3), d.n_y (5) and both double layers (2): 47; with the reversed
 // pair's double layer, d.n_x (5) and its two kernels (2): 54. Accumulation:
-// the eight products of w with (1, s, t) x (1, s', t') and one FMA per kernel
-// and moment, 8 + 2 x 6 x 9 (116). Coincident pairs: d from (s - s', t - t')
-// (11), r^2 to the Yukawa single layer (11); 8 + 2 x 2 x 9 (44).
-constexpr double NEAR_FLOPS_SYM = 54 + 116;
-constexpr double NEAR_FLOPS_COIN = 22 + 44;
+// one FMA per kernel and moment, 2 x 6 x 9 (108); the weighted monomials
+// w (1, s, t) x (1, s', t') come from the rule's table and the pair's Jacobian
+// multiplies the finished moments. Coincident pairs: d from (s - s', t - t')
+// (11), r^2 to the Yukawa single layer (11); 2 x 2 x 9 (36).
+constexpr double NEAR_FLOPS_SYM = 54 + 108;
+constexpr double NEAR_FLOPS_COIN = 22 + 36;
 
 // One warp per listed pair. Writes ss[p][54] (regularised) and far[p][54] (far
 // rule, identical points excluded); with SYM also the blocks of the reversed
@@ -415,11 +429,8 @@ k_near_pairs(const double* __restrict__ verts, const int32_t* __restrict__ tris,
     {
         double mom[NM];
         for (int k = 0; k < NM; ++k) mom[k] = 0.0;
-        for (int idx = lane; idx < nreg * n4; idx += 32) {
-            const int e = e0 + idx;
-            accum_frame<SYM>(mom, tab.w[e] * jac_ab, tab.sx[e], tab.tx[e], tab.sy[e], tab.ty[e], dq, A, B, kappa);
-        }
-        for (int k = 0; k < NM; ++k) mom[k] = warp_sum(mom[k]);
+        for (int idx = lane; idx < nreg * n4; idx += 32) accum_frame<SYM>(mom, tab, e0 + idx, dq, A, B, kappa);
+        for (int k = 0; k < NM; ++k) mom[k] = warp_sum(mom[k]) * jac_ab;  // the pair's Jacobian, once
         // corner blocks in the accumulator layout of accum_point
         for (int k = 0; k < NM / 9; ++k) frame_to_corner(mom + 9 * k, A, B, acc + (k < 4 ? 9 * k : 38 + 9 * (k - 4)));
         acc[36] = mom[0];  // sum w G_L: the (1, 1) moment
@@ -511,11 +522,8 @@ k_coin_pairs(const double* __restrict__ verts, const int32_t* __restrict__ tris,
     {
         double mom[18];
         for (int k = 0; k < 18; ++k) mom[k] = 0.0;
-        for (int idx = lane; idx < 3 * n4; idx += 32) {
-            const int e = e0 + idx;
-            accum_coin_frame(mom, tab.w[e] * jac_ab, tab.sx[e], tab.tx[e], tab.sy[e], tab.ty[e], A, kappa);
-        }
-        for (int k = 0; k < 18; ++k) mom[k] = warp_sum(mom[k]);
+        for (int idx = lane; idx < 3 * n4; idx += 32) accum_coin_frame(mom, tab, e0 + idx, A, kappa);
+        for (int k = 0; k < 18; ++k) mom[k] = warp_sum(mom[k]) * jac_ab;
         frame_to_corner(mom, A, A, acc);
         frame_to_corner(mom + 9, A, A, acc + 9);
         acc[18] = mom[0];
@@ -840,7 +848,7 @@ static int build(pb_ctx* ctx, const pb_mesh* m, double kappa, pb_near* nf, cudaS
         Gauss gq = gauss01(m->n_ss);
         const int n4i = m->n_ss * m->n_ss * m->n_ss * m->n_ss, ntab = 11 * n4i;
         double* tabm = nullptr;
-        rc = dev_alloc((void**)&tabm, sizeof(double) * 5 * ntab);
+        rc = dev_alloc((void**)&tabm, sizeof(double) * SS_TABLE_ARRAYS * ntab);
         if (rc != PB_OK) {
             cudaFree(ss);
             cudaFree(far);
@@ -848,7 +856,7 @@ static int build(pb_ctx* ctx, const pb_mesh* m, double kappa, pb_near* nf, cudaS
         }
         k_ss_table<<<(ntab + 127) / 128, 128, 0, s>>>(gq, ntab, tabm);
         ::pb::count_launch();
-        SSTable tab = {tabm, tabm + ntab, tabm + 2 * ntab, tabm + 3 * ntab, tabm + 4 * ntab,
+        SSTable tab = {tabm, tabm + ntab, tabm + 2 * ntab, tabm + 3 * ntab, tabm + 4 * ntab, tabm + 5 * ntab,
                        {8 * n4i, 0, 6 * n4i}, ntab};
         int threads = NEAR_THREADS;  // one warp per pair
         // coincident pairs, then one of each pair of reversed pairs (which also writes the other)
