@@ -267,7 +267,8 @@ int pb_solve_pc(pb_ctx* ctx, const pb_mesh* mesh, const pb_near* near, const pb_
 /* y = P^-1 x: the preconditioner of pb_solve for formulation `form` and
  * preconditioner `precond` (paper, "Preconditioning": block diagonal, mass,
  * scaled mass and the Calderon products, with the mass inverse by the same
- * Chebyshev iteration), operator applications in precision prec (PB_F64 or
+ * Chebyshev iteration: 34 steps, 16 with prec = PB_F32, the count the FP32
+ * inner iterations use), operator applications in precision prec (PB_F64 or
  * PB_F32). opts supplies alpha, beta (CFIE) and pc_a, pc_b (scalings; NULL =
  * defaults). x and y: device, 2*N_v, not overlapping. Used with
  * pb_system_apply to form P^-1 A for spectra (paper, eigenvalue figures). */

@@ -178,15 +178,6 @@ static int build_tree(pb_mesh* m, int order, double theta, PbTree** out) {
         }
         height[sl] = h;
     }
-    int hmax = 0;
-    for (int64_t sl = 0; sl < nslot; ++sl) hmax = std::max(hmax, height[sl]);
-    std::vector<int32_t> slot_order;
-    std::vector<int64_t> height_ptr{0};
-    for (int h = 0; h <= hmax && nslot; ++h) {
-        for (int64_t sl = 0; sl < nslot; ++sl)
-            if (height[sl] == h) slot_order.push_back((int32_t)sl);
-        height_ptr.push_back((int64_t)slot_order.size());
-    }
     auto center_radius = [&](const HostNode& nd, float* c) {
         float r2 = 0.f;
         for (int d = 0; d < 3; ++d) {
@@ -233,6 +224,23 @@ static int build_tree(pb_mesh* m, int order, double theta, PbTree** out) {
         }
         far_ptr.push_back((int32_t)far_idx.size());
         near_ptr.push_back((int32_t)(near_rng.size() / 2));
+    }
+    // the slots whose proxies are read: those in a far list, and (for the transfer) every slot
+    // below one of them; parents have lower slot numbers than their children
+    std::vector<char> needed(nslot, 0);
+    for (int32_t f : far_idx) needed[f] = 1;
+    for (int64_t sl = 0; sl < nslot; ++sl)
+        if (needed[sl])
+            for (int c = 0; c < 2; ++c)
+                if (slot_kids[6 * sl + 3 * c] >= 0) needed[slot_kids[6 * sl + 3 * c]] = 1;
+    int hmax = 0;
+    for (int64_t sl = 0; sl < nslot; ++sl) hmax = std::max(hmax, height[sl]);
+    std::vector<int32_t> slot_order;
+    std::vector<int64_t> height_ptr{0};
+    for (int h = 0; h <= hmax && nslot; ++h) {
+        for (int64_t sl = 0; sl < nslot; ++sl)
+            if (height[sl] == h && needed[sl]) slot_order.push_back((int32_t)sl);
+        if ((int64_t)slot_order.size() > height_ptr.back()) height_ptr.push_back((int64_t)slot_order.size());
     }
     t->nleaf = (int64_t)leaves.size();
     t->nslot = (int64_t)(slot_rng.size() / 2);
