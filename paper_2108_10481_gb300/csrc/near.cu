@@ -354,10 +354,49 @@ __device__ __forceinline__ void frame_to_corner(const double* mom, const TriFram
         for (int b = 0; b < 3; ++b) out[3 * a + b] = U[A.inv[a]][B.inv[b]];
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
+// One level of a warp reduce-scatter: a lane keeps half of its first 2H
+// entries (the upper half when its bit o is set) and adds its partner's copy.
+template <int H>
+__device__ __forceinline__ void rs_level(double* v, int lane, int o) {
+    const bool up = lane & o;
+#pragma unroll
+    for (int i = 0; i < H; ++i) {
+        const double lo = v[i], hi = v[i + H];
+        v[i] = (up ? hi : lo) + __shfl_xor_sync(0xffffffffu, up ? lo : hi, o);
+    }
 }
+
+// Warp sums of v[0..NV) into every lane's v. A reduce-scatter over the five
+// lane bits (offsets 16 .. 1, N the power of two with NV <= N <= 2 NV, entries
+// past NV being zero) leaves lane L with the totals of entries [L N/32,
+// (L + 1) N/32) after N/2 + N/4 + ... + N/32 additions, against 5 NV for a
+// butterfly on every entry; the totals go through the warp's shared buffer
+// (N doubles) back to all lanes. Fixed order: deterministic.
+template <int NV, int N>
+__device__ __forceinline__ void warp_allsum(double* v, int lane, double* buf) {
+    static_assert(N >= 32 && (N & (N - 1)) == 0 && NV <= N && 2 * NV >= N, "reduce-scatter size");
+    {
+        constexpr int h = N / 2;
+        const bool up = lane & 16;
+#pragma unroll
+        for (int i = 0; i < h; ++i) {
+            const double lo = v[i], hi = i + h < NV ? v[i + h] : 0.0;
+            v[i] = (up ? hi : lo) + __shfl_xor_sync(0xffffffffu, up ? lo : hi, 16);
+        }
+    }
+    rs_level<N / 4>(v, lane, 8);
+    rs_level<N / 8>(v, lane, 4);
+    rs_level<N / 16>(v, lane, 2);
+    rs_level<N / 32>(v, lane, 1);
+    constexpr int K = N / 32;
+#pragma unroll
+    for (int j = 0; j < K; ++j) buf[lane * K + j] = v[j];
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = buf[k];
+    __syncwarp();  // the buffer is free again
+}
+
 
 // Six 3x3 blocks (V_L, K_L, D_L, V_Y, K_Y, D_Y) of the pair (tau, sigma), or with
 // rev = true of the reversed pair (sigma, tau): every block transposed and the
@@ -410,6 +449,7 @@ k_near_pairs(const double* __restrict__ verts, const int32_t* __restrict__ tris,
     constexpr int NA = SYM ? NACC_SYM : NACC_NEAR;
     constexpr int NM = SYM ? 54 : 36;  // frame moments
     __shared__ TriFrame frames[NEAR_THREADS / 32][2];
+    __shared__ double red[NEAR_THREADS / 32][64];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t li = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (li >= nlist) return;  // whole warps leave together
@@ -430,7 +470,8 @@ k_near_pairs(const double* __restrict__ verts, const int32_t* __restrict__ tris,
         double mom[NM];
         for (int k = 0; k < NM; ++k) mom[k] = 0.0;
         for (int idx = lane; idx < nreg * n4; idx += 32) accum_frame<SYM>(mom, tab, e0 + idx, dq, A, B, kappa);
-        for (int k = 0; k < NM; ++k) mom[k] = warp_sum(mom[k]) * jac_ab;  // the pair's Jacobian, once
+        warp_allsum<NM, 64>(mom, lane, red[wid]);
+        for (int k = 0; k < NM; ++k) mom[k] *= jac_ab;  // the pair's Jacobian, once
         // corner blocks in the accumulator layout of accum_point
         for (int k = 0; k < NM / 9; ++k) frame_to_corner(mom + 9 * k, A, B, acc + (k < 4 ? 9 * k : 38 + 9 * (k - 4)));
         acc[36] = mom[0];  // sum w G_L: the (1, 1) moment
@@ -454,7 +495,7 @@ k_near_pairs(const double* __restrict__ verts, const int32_t* __restrict__ tris,
         const double w = rule.w[i] * A.area * rule.w[j] * B.area;
         accum_point<SYM>(acc, w, x, y, A.n, B.n, rule.l[i], rule.l[j], kappa);
     }
-    for (int k = 0; k < NA; ++k) acc[k] = warp_sum(acc[k]);
+    warp_allsum<NA, 64>(acc, lane, red[wid]);
     if (lane == 0) expand_blocks(acc, A, B, gA, gB, kappa, false, far_out + 54 * p);
     if (SYM && lane == 1) expand_blocks(acc, A, B, gA, gB, kappa, true, far_out + 54 * (int64_t)rev[p]);
 }
@@ -508,6 +549,7 @@ k_coin_pairs(const double* __restrict__ verts, const int32_t* __restrict__ tris,
              const int4* __restrict__ pairs, const int32_t* __restrict__ list, int64_t nlist, SSTable tab, int n4,
              Rule rule, double kappa, double* __restrict__ ss_out, double* __restrict__ far_out) {
     __shared__ TriFrame frames[NEAR_THREADS / 32];
+    __shared__ double red[NEAR_THREADS / 32][32];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     const int64_t li = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
     if (li >= nlist) return;  // whole warps leave together
@@ -523,7 +565,8 @@ k_coin_pairs(const double* __restrict__ verts, const int32_t* __restrict__ tris,
         double mom[18];
         for (int k = 0; k < 18; ++k) mom[k] = 0.0;
         for (int idx = lane; idx < 3 * n4; idx += 32) accum_coin_frame(mom, tab, e0 + idx, A, kappa);
-        for (int k = 0; k < 18; ++k) mom[k] = warp_sum(mom[k]) * jac_ab;
+        warp_allsum<18, 32>(mom, lane, red[wid]);
+        for (int k = 0; k < 18; ++k) mom[k] *= jac_ab;
         frame_to_corner(mom, A, A, acc);
         frame_to_corner(mom + 9, A, A, acc + 9);
         acc[18] = mom[0];
@@ -544,7 +587,7 @@ k_coin_pairs(const double* __restrict__ verts, const int32_t* __restrict__ tris,
         const double w = rule.w[i] * A.area * rule.w[j] * A.area;
         accum_v(acc, w, x, y, rule.l[i], rule.l[j], kappa);
     }
-    for (int k = 0; k < 20; ++k) acc[k] = warp_sum(acc[k]);
+    warp_allsum<20, 32>(acc, lane, red[wid]);
     if (lane == 0) expand_coin(acc, A, gA, kappa, far_out + 54 * p);
 }
 
