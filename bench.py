@@ -40,8 +40,8 @@ L2_FLUSH_BYTES = 256 << 20
 # for that kernel as captured; any other dominant kernel reports null.
 NCU_TRAFFIC = {  # (kernel family, formulation or "any", far-rule points, band) -> dram read + write per launch
     ("pair32", "juffer", 122880, 0.0): 17.72e6,
-    ("near_adj", "any", 61440, 3.0): 173.87e6,
-    ("near_coin", "any", 61440, 3.0): 6.97e6,
+    ("near_adj", "any", 61440, 3.0): 172.08e6,
+    ("near_coin", "any", 61440, 3.0): 6.95e6,
     ("near_band", "any", 61440, 3.0): 690.51e6,
     ("tree32", "juffer", 61440, 3.0): 7.47e6,
 }
