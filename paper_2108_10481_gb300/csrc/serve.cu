@@ -296,7 +296,8 @@ static int tick(pb_server* srv) {
         if (r->phase == PH_ITER) {
             pin[k] = r->S.t3;
             if (r->pc >= PB_PC_CALDERON_FULL) {
-                PB_TRY(piece(r, r->g_mid, [r] { return calderon_pre(r->S, r->S.t3); }));
+                const int ip = it_prec(r);
+                PB_TRY(piece(r, r->g_mid, [r, ip] { return calderon_pre(r->S, ip, r->S.t3); }));
                 jobs[it_prec(r)].push_back({r->m, r->nf, r->S.C, r->S.t1, r->S.t2});
             }
             continue;  // the rest of the iteration follows the batched operators
@@ -311,7 +312,7 @@ static int tick(pb_server* srv) {
         if (!pin[k]) continue;
         const int prec = r->phase == PH_ITER ? it_prec(r) : res_prec(r);
         if (r->pc >= PB_PC_CALDERON_FULL) {
-            PB_TRY(calderon_pre(r->S, pin[k]));
+            PB_TRY(calderon_pre(r->S, prec, pin[k]));
             jobs[prec].push_back({r->m, r->nf, r->S.C, r->S.t1, r->S.t2});
         } else {
             PB_TRY(apply_prec(r->S, prec, pin[k], r->w));
@@ -325,12 +326,12 @@ static int tick(pb_server* srv) {
         if (r->phase == PH_ITER) {
             const int prec = it_prec(r);
             PB_TRY(piece(r, r->g_tail, [r, prec, slot, s] {
-                if (r->pc >= PB_PC_CALDERON_FULL) PB_TRY(calderon_post(r->S, r->w));
+                if (r->pc >= PB_PC_CALDERON_FULL) PB_TRY(calderon_post(r->S, prec, r->w));
                 else PB_TRY(apply_prec(r->S, prec, r->S.t3, r->w));
                 return gm_step(r->G, r->w, slot, s);
             }));
         } else {
-            if (r->pc >= PB_PC_CALDERON_FULL) PB_TRY(calderon_post(r->S, r->w));
+            if (r->pc >= PB_PC_CALDERON_FULL) PB_TRY(calderon_post(r->S, res_prec(r), r->w));
             gm_norm2(r->G, r->w, slot, s);
         }
     }

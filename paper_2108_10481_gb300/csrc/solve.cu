@@ -313,11 +313,15 @@ static unsigned nb(int64_t n) { return (unsigned)((n + 255) / 256); }
 // outer residual's norm) keep the full count.
 constexpr int CHEB_ITERS_F32 = 16;
 
+static int cheb_count(const Solver& S, int prec) {
+    return prec == PB_F32 ? std::min(S.cheb_iters, CHEB_ITERS_F32) : S.cheb_iters;
+}
+
 // y = P^-1 x
 int apply_prec(Solver& S, int prec, const double* x, double* y) {
     const pb_mesh* m = S.m;
     const int64_t nv = m->nv, n2 = 2 * nv;
-    const int ci = prec == PB_F32 ? std::min(S.cheb_iters, CHEB_ITERS_F32) : S.cheb_iters;
+    const int ci = cheb_count(S, prec);
     switch (S.pc) {
         case PB_PC_NONE:
             k_copy<<<nb(n2), 256, 0, S.s>>>(n2, x, y); ::pb::count_launch();
@@ -584,10 +588,12 @@ int gm_finish(GmresWork& G, int k, double* x, cudaStream_t s) {
     return PB_OK;
 }
 
-int calderon_pre(Solver& S, const double* x) { return mass_solve(S.m, S.nf, x, S.t1, S.cheb, S.cheb_iters, S.s); }
+int calderon_pre(Solver& S, int prec, const double* x) {
+    return mass_solve(S.m, S.nf, x, S.t1, S.cheb, cheb_count(S, prec), S.s);
+}
 
-int calderon_post(Solver& S, double* y) {
-    PB_TRY(mass_solve(S.m, S.nf, S.t2, y, S.cheb, S.cheb_iters, S.s));
+int calderon_post(Solver& S, int prec, double* y) {
+    PB_TRY(mass_solve(S.m, S.nf, S.t2, y, S.cheb, cheb_count(S, prec), S.s));
     if (S.sa != 1.0 || S.sb != 1.0) {
         k_scale_halves<<<nb(2 * S.m->nv), 256, 0, S.s>>>(S.m->nv, 1.0 / S.sa, 1.0 / S.sb, y);
         ::pb::count_launch();

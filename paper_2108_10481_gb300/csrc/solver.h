@@ -63,8 +63,8 @@ int gm_begin(GmresWork& G, const double* w, const double* n2, cudaStream_t s);
 int gm_step(GmresWork& G, double* w, double* res_out, cudaStream_t s);
 int gm_finish(GmresWork& G, int k, double* x, cudaStream_t s);
 // Calderon preconditioner split around its operator application (t1 -> t2)
-int calderon_pre(Solver& S, const double* x);
-int calderon_post(Solver& S, double* y);
+int calderon_pre(Solver& S, int prec, const double* x);
+int calderon_post(Solver& S, int prec, double* y);
 void vec_sub(int64_t n, const double* a, const double* b, double* y, cudaStream_t s);
 void vec_add(int64_t n, const double* a, double* y, cudaStream_t s);
 
