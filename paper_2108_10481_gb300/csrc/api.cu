@@ -11,6 +11,7 @@
 #include <mutex>
 #include <thread>
 
+#include "host_pool.h"
 #include "internal.h"
 
 namespace pb {
@@ -103,57 +104,6 @@ int set_error(int code, const char* fmt, ...) {
 }
 
 namespace {
-struct HostPool {
-    std::vector<std::thread> workers;
-    std::mutex run_mu;  // one parallel call at a time
-    std::mutex mu;
-    std::condition_variable cv, done_cv;
-    const std::function<void(int)>* job = nullptr;
-    int njobs = 0, next = 0, remaining = 0;
-    uint64_t gen = 0;
-
-    explicit HostPool(int nworkers) {
-        for (int w = 0; w < nworkers; ++w) workers.emplace_back([this] { loop(); });
-    }
-    // take jobs of the current call until none is left (mu held on entry and exit)
-    void drain(std::unique_lock<std::mutex>& lk) {
-        while (job && next < njobs) {
-            const int i = next++;
-            const std::function<void(int)>* f = job;
-            lk.unlock();
-            (*f)(i);
-            lk.lock();
-            if (--remaining == 0) done_cv.notify_all();
-        }
-    }
-    void loop() {
-        uint64_t seen = 0;
-        std::unique_lock<std::mutex> lk(mu);
-        for (;;) {
-            cv.wait(lk, [&] { return gen != seen; });
-            seen = gen;
-            drain(lk);
-        }
-    }
-    void run(int n, const std::function<void(int)>& f) {
-        std::unique_lock<std::mutex> busy(run_mu, std::try_to_lock);
-        if (!busy.owns_lock() || workers.empty() || n <= 1) {
-            for (int i = 0; i < n; ++i) f(i);
-            return;
-        }
-        std::unique_lock<std::mutex> lk(mu);
-        job = &f;
-        njobs = n;
-        next = 0;
-        remaining = n;
-        ++gen;
-        cv.notify_all();
-        drain(lk);
-        done_cv.wait(lk, [&] { return remaining == 0; });
-        job = nullptr;
-    }
-};
-
 HostPool& host_pool() {
     // never destroyed: the workers wait on the pool until the process ends
     static HostPool* pool = new HostPool(host_threads() - 1);
