@@ -177,12 +177,6 @@ __device__ void make_frame(const double* verts, const int32_t* tris, const doubl
     for (int k = 0; k < 3; ++k) f.inv[o[k]] = k;
 }
 
-// reference (s,t) in the reordered frame -> point and original barycentrics
-__device__ __forceinline__ void frame_point(const TriFrame& f, double s, double t, double* x, double* lam) {
-    const double mu[3] = {1.0 - s, s - t, t};
-    for (int a = 0; a < 3; ++a) lam[a] = mu[f.inv[a]];
-    for (int k = 0; k < 3; ++k) x[k] = f.q0[k] + s * f.e1[k] + t * f.e2[k];
-}
 // original corner a of the triangle
 __device__ __forceinline__ double corner(const TriFrame& f, int a, int k) {
     int r = f.inv[a];

@@ -683,8 +683,9 @@ k_tree_eval(int64_t np, int nprox, const int32_t* __restrict__ perm, const int32
     }
 }
 
-// y-part of the far field by the treecode into part (one split, the direct
-// kernel's layout): builds the tree of the mesh on first use.
+// y-part of the far field by the treecode: per-target partial sums in the
+// direct kernel's split layout (*nsplit slices in the mesh's ws_part, returned
+// in *part_out); builds the tree of the mesh on first use.
 int tree_far(const pb_mesh* mc, const FarPlan& fp, const double* x, bool need_u, bool need_v, float** part_out,
              int* nsplit, cudaStream_t s) {
     pb_mesh* m = const_cast<pb_mesh*>(mc);
