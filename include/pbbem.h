@@ -204,11 +204,18 @@ int pb_system_apply(pb_ctx* ctx, const pb_mesh* mesh, const pb_near* near, const
                     void* stream);
 
 /* Allocation-free FP32 system application (the paper has no counterpart: it
- * exists for callers that cannot call cudaMalloc). It computes what
- * pb_system_apply(..., PB_F32, ...) computes, with the same kernels, but keeps
- * every temporary in one file-scope device array of 16 MiB that each GPU
+ * exists for callers that cannot call cudaMalloc). It computes the FP32
+ * system application of pb_system_apply(..., PB_F32, ...) - the same sources,
+ * per-triangle reduction, gather and FP32 near field - but always with the
+ * direct scalar FP32 pair kernel (k_pair32, at most 4 source splits), and it
+ * keeps every temporary in one file-scope device array of 16 MiB that each GPU
  * loading the library holds until the process exits; it calls no cudaMalloc,
- * cudaFree or other allocating routine. The callers it is for: processes
+ * cudaFree or other allocating routine. Its result therefore differs from
+ * pb_system_apply's by FP32 rounding in another summation order (the packed
+ * kernel or another split count; about 1e-6 relative), and by the treecode's
+ * approximation (about 1e-5) where pb_system_apply uses the treecode (meshes
+ * with at least pb_set_treecode's min_points far-rule points). The mesh and
+ * near field must come from ctx (else PB_EINVAL). The callers it is for: processes
  * whose device memory belongs to another allocator that reserves it up front
  * (a raw cudaMalloc would fail or take memory that allocator counts on), and
  * latency-bound loops that cannot afford the device-wide synchronisation that
@@ -383,12 +390,18 @@ int pb_autotune_plan(pb_ctx* ctx, const double* verts, int64_t n_verts, const in
 #define PB_KERNEL_NEAR_COIN 4       /* FP64 regularised quadrature of coincident pairs */
 #define PB_KERNEL_NEAR_BAND 5       /* FP64 band-rule minus far-rule blocks of band pairs */
 #define PB_KERNEL_TREE32 6          /* FP32 treecode evaluation (proxy and direct interactions) */
-#define PB_KERNEL_COUNT 7
+#define PB_KERNEL_SPMV 7            /* gather of the triangle sums + near-field SpMV (memory-bound) */
+#define PB_KERNEL_CHEB 8            /* one Chebyshev step of the mass solve (memory-bound) */
+#define PB_KERNEL_KRYLOV 9          /* Gram-Schmidt dots and updates of the Arnoldi step (memory-bound) */
+#define PB_KERNEL_COUNT 10
 /* For the pair kernels, "pairs" are target-source point pairs and "ops" FP32
  * (FP64 for PB_KERNEL_PAIR64) operations by the kernel's formula count; for
  * the near-field kernels, "pairs" are quadrature point pairs (kernel
  * evaluations) and "ops" FP64 flops by formula count (kernel evaluation and
- * accumulation into the local blocks, a fused multiply-add counted as two). */
+ * accumulation into the local blocks, a fused multiply-add counted as two).
+ * For the memory-bound families (SPMV, CHEB, KRYLOV) "pairs" and "ops" are
+ * both the algorithmic bytes of the launches: every array element the launch
+ * must read or write, counted once. */
 /* enable (1) or disable (0) per-launch CUDA-event timing of the pair kernels
  * on their launching stream; either call resets the statistics. No effect on
  * results. */
@@ -409,6 +422,13 @@ int pb_selftest_wait(pb_ctx* ctx, int64_t polls, int* status_out);
  * returned below -700), on `stream` (NULL: the default stream), synchronised
  * before return. x and y are caller-owned device buffers of n doubles. */
 int pb_selftest_exp(pb_ctx* ctx, const double* x, double* y, int64_t n, void* stream);
+/* Arithmetic peak of this GPU by microbenchmark (the denominator of the pair
+ * and near-field kernels' rooflines): independent fused multiply-add chains on
+ * four CTAs of 256 threads per SM, the best of three timed launches of about
+ * 20 ms. kind 0 = FP32 fma.rn.f32, 1 = FP64 fma.rn.f64, 2 = packed
+ * fma.rn.f32x2 (two FMAs per instruction). *fma_per_s receives FMAs per second
+ * (a flop count is twice that). Not in the paper. */
+int pb_measure_peak(pb_ctx* ctx, int kind, double* fma_per_s);
 /* Number of kernels this library has launched in this process (all kinds;
  * a kernel inside a replayed CUDA graph counts once per replay). */
 int64_t pb_launch_count(void);

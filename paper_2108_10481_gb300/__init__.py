@@ -12,6 +12,8 @@ from .api import (CASES, FORMS, PB_F32, PB_F32_ACCURATE, PB_F64, PB_LAPLACE, PB_
                   PB_KERNEL_NEAR_COIN, PB_KERNEL_NEAR_BAND, pb_server_create, pb_submit,
                   pb_server_step, pb_poll, pb_autotune, pb_autotune_plan, pb_selftest_wait, pb_selftest_exp,
                   pb_set_graphs, pb_set_treecode, pb_tree_info, PB_KERNEL_TREE32)
+from .api import PB_KERNEL_SPMV, PB_KERNEL_CHEB, PB_KERNEL_KRYLOV, pb_measure_peak
+from .api import PB_OK, PB_EINVAL, PB_EMESH, PB_ENOMEM, PB_ENOCONV, PB_ENUMERIC, PB_ECUDA, PB_ETIMEOUT
 
 __all__ = ["CASES", "FORMS", "PRECONDS", "Params", "PBError", "PB_F32", "PB_F32_ACCURATE", "PB_F64",
            "PB_LAPLACE", "PB_MIXED", "PB_OP_D", "PB_OP_K", "PB_OP_M", "PB_OP_T", "PB_OP_V", "PB_YUKAWA",
@@ -20,4 +22,5 @@ __all__ = ["CASES", "FORMS", "PRECONDS", "Params", "PBError", "PB_F32", "PB_F32_
            "pb_profile_read", "pb_launch_count", "PB_KERNEL_PAIR32", "PB_KERNEL_PAIR32_ACCURATE", "PB_KERNEL_PAIR64",
            "PB_KERNEL_NEAR_ADJ", "PB_KERNEL_NEAR_COIN", "PB_KERNEL_NEAR_BAND",
            "pb_server_create", "pb_submit", "pb_server_step", "pb_poll", "pb_autotune", "pb_autotune_plan",
-           "pb_selftest_wait", "pb_selftest_exp", "pb_set_graphs", "pb_set_treecode", "pb_tree_info", "PB_KERNEL_TREE32"]
+           "pb_selftest_wait", "pb_selftest_exp", "pb_set_graphs", "pb_set_treecode", "pb_tree_info", "PB_KERNEL_TREE32",
+           "pb_measure_peak", "PB_KERNEL_SPMV", "PB_KERNEL_CHEB", "PB_KERNEL_KRYLOV", "PB_OK", "PB_EINVAL", "PB_EMESH", "PB_ENOMEM", "PB_ENOCONV", "PB_ENUMERIC", "PB_ECUDA", "PB_ETIMEOUT"]

@@ -118,6 +118,7 @@ class Near(_Handle):
 PB_KERNEL_PAIR32, PB_KERNEL_PAIR32_ACCURATE, PB_KERNEL_PAIR64 = 0, 1, 2
 PB_KERNEL_NEAR_ADJ, PB_KERNEL_NEAR_COIN, PB_KERNEL_NEAR_BAND = 3, 4, 5
 PB_KERNEL_TREE32 = 6
+PB_KERNEL_SPMV, PB_KERNEL_CHEB, PB_KERNEL_KRYLOV = 7, 8, 9  # memory-bound: pairs = ops = algorithmic bytes
 
 
 def pb_profile(ctx: Ctx, enable: bool = True):
@@ -138,6 +139,13 @@ def pb_selftest_wait(ctx: Ctx, polls: int = 4096) -> int:
     st = ctypes.c_int()
     _check(N.load().pb_selftest_wait(ctx.ptr, int(polls), ctypes.byref(st)))
     return st.value
+
+
+def pb_measure_peak(ctx: Ctx, kind: int) -> float:
+    """FMAs per second of this GPU by microbenchmark: kind 0 FP32, 1 FP64, 2 packed f32x2."""
+    out = ctypes.c_double()
+    _check(N.load().pb_measure_peak(ctx.ptr, int(kind), ctypes.byref(out)))
+    return out.value
 
 
 def pb_selftest_exp(ctx: Ctx, x: torch.Tensor, stream=None) -> torch.Tensor:

@@ -82,17 +82,23 @@ int graph_replay(StepGraph& g, cudaStream_t s) {
     return PB_OK;
 }
 
-int graph_credit(pb_ctx* ctx, StepGraph& g) {
+int graph_credit(pb_ctx* ctx, StepGraph& g, int j) {
     for (auto& t : g.timers) {
         float ms = 0.0f;
         PB_CUDA(cudaEventElapsedTime(&ms, t.e0, t.e1));
         KernelStats& st = ctx->stats[t.id];
+        const double p = t.pairs + t.pairs_j * (double)(j + 1);
         st.ms += ms;
         st.launches += 1;
-        st.pairs += t.pairs;
-        st.ops += t.pairs * t.ops;
+        st.pairs += p;
+        st.ops += p * t.ops;
     }
     return PB_OK;
+}
+
+int& arnoldi_j() {
+    static thread_local int j = 0;
+    return j;
 }
 
 int set_error(int code, const char* fmt, ...) {

@@ -168,6 +168,24 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase, int* st
     atomicExch(status, PB_ETIMEOUT);
     return false;
 }
+// The CTA acts on a wait's outcome as one: every thread polls the barrier
+// (bounded), and the tile is used only if all of them saw it complete, so a
+// wait that runs out in one thread sends every thread down the same exit path
+// (no thread is left at a barrier the others never reach).
+__device__ __forceinline__ bool cta_wait(uint64_t* bar, uint32_t phase, int* status) {
+    return __syncthreads_and(mbar_wait(bar, phase, status) ? 1 : 0) != 0;
+}
+// Exit path after a failed wait at tile `it`: the copies still in flight are
+// those of tiles it .. min(ntiles, it + stages) - 1, tile k on stage k % stages
+// with phase parity (k / stages) & 1. One thread waits for each (bounded)
+// before the CTA leaves, so no copy lands in shared memory after it is gone.
+__device__ __forceinline__ void cta_drain(uint64_t* bar, int stages, int it, int ntiles) {
+    if (threadIdx.x == 0)
+        for (int k = it; k < ntiles && k < it + stages; ++k)
+            for (int i = 0; i < (1 << 20); ++i)
+                if (mbar_try_wait(&bar[k % stages], (uint32_t)((k / stages) & 1))) break;
+    __syncthreads();
+}
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int c0, int c1, uint64_t* bar) {
     asm volatile(
         "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
@@ -235,11 +253,11 @@ __global__ void __launch_bounds__(TPB32) k_pair32(const __grid_constant__ CUtens
         for (int a = 0; a < (ACC ? NACC : 1); ++a) accd[t][a] = 0.0;
     }
     const float kap = cf.kappa, mk2 = cf.mk2;
-    bool ok = true;
+    int failed_at = -1;
     for (int it = 0; it < ntiles; ++it) {
         const int st = it % ST32;
         const uint32_t phase = (uint32_t)((it / ST32) & 1);
-        if (!mbar_wait(&bar[st], phase, status)) { ok = false; break; }
+        if (!cta_wait(&bar[st], phase, status)) { failed_at = it; break; }
         const float* tile = sh[st];
 #pragma unroll 2
         for (int j = 0; j < TS32; ++j) {
@@ -295,14 +313,8 @@ __global__ void __launch_bounds__(TPB32) k_pair32(const __grid_constant__ CUtens
             tma_load_2d(sh[st], &tmap, 0, (int)(j0 + (int64_t)(it + ST32) * TS32), &bar[st]);
         }
     }
-    if (!ok) {
-        // drain: wait (bounded) for the copies this CTA issued, then leave
-        if (threadIdx.x == 0)
-            for (int s = 0; s < ST32; ++s) {
-                for (int i = 0; i < (1 << 20); ++i)
-                    if (mbar_try_wait(&bar[s], 0) || mbar_try_wait(&bar[s], 1)) break;
-            }
-        __syncthreads();
+    if (failed_at >= 0) {
+        cta_drain(bar, ST32, failed_at, ntiles);
         return;
     }
     for (int t = 0; t < TGT32; ++t) {
@@ -503,11 +515,11 @@ __global__ void __launch_bounds__(TPB2) k_pair32x2(const __grid_constant__ CUten
         for (int a = 0; a < NACC; ++a) acc[p][a] = make_float2(0.f, 0.f);
     for (int t = 0; t < TGT; ++t)
         for (int a = 0; a < (ACC ? NACC : 1); ++a) accd[t][a] = 0.0;
-    bool ok = true;
+    int failed_at = -1;
     for (int it = 0; it < ntiles; ++it) {
         const int st = it % ST2;
         const uint32_t phase = (uint32_t)((it / ST2) & 1);
-        if (!mbar_wait(&bar[st], phase, status)) { ok = false; break; }
+        if (!cta_wait(&bar[st], phase, status)) { failed_at = it; break; }
         const int64_t jt = j0 + (int64_t)it * TS2;
         const bool guard = (jt < blk1 && jt + TS2 > blk0) || jt + TS2 > np;
         if (guard) tile_x2<MODE, ACC, NPK, true>(sh[st], X, XL, acc, cf);
@@ -527,12 +539,8 @@ __global__ void __launch_bounds__(TPB2) k_pair32x2(const __grid_constant__ CUten
             tma_load_2d(sh[st], &tmap, 0, (int)(j0 + (int64_t)(it + ST2) * TS2), &bar[st]);
         }
     }
-    if (!ok) {
-        if (threadIdx.x == 0)
-            for (int s = 0; s < ST2; ++s)
-                for (int i = 0; i < (1 << 20); ++i)
-                    if (mbar_try_wait(&bar[s], 0) || mbar_try_wait(&bar[s], 1)) break;
-        __syncthreads();
+    if (failed_at >= 0) {
+        cta_drain(bar, ST2, failed_at, ntiles);
         return;
     }
     for (int t = 0; t < TGT; ++t) {
@@ -628,11 +636,11 @@ __global__ void __launch_bounds__(TPB2) k_pair32x2_multi(const PairJob* __restri
         for (int a = 0; a < NACC; ++a) acc[p][a] = make_float2(0.f, 0.f);
     for (int t = 0; t < TGT; ++t)
         for (int a = 0; a < (ACC ? NACC : 1); ++a) accd[t][a] = 0.0;
-    bool ok = true;
+    int failed_at = -1;
     for (int it = 0; it < ntiles; ++it) {
         const int st = it % ST2;
         const uint32_t phase = (uint32_t)((it / ST2) & 1);
-        if (!mbar_wait(&bar[st], phase, status)) { ok = false; break; }
+        if (!cta_wait(&bar[st], phase, status)) { failed_at = it; break; }
         const int64_t jt = j0 + (int64_t)it * TS2;
         const bool guard = (jt < blk1 && jt + TS2 > blk0) || jt + TS2 > np;
         if (guard) tile_x2<MODE, ACC, NPK, true>(sh[st], X, XL, acc, cf);
@@ -652,12 +660,8 @@ __global__ void __launch_bounds__(TPB2) k_pair32x2_multi(const PairJob* __restri
             bulk_load(sh[st], J.rec + (j0 + (int64_t)(it + ST2) * TS2) * REC2, tile_bytes, &bar[st]);
         }
     }
-    if (!ok) {
-        if (threadIdx.x == 0)
-            for (int st = 0; st < ST2; ++st)
-                for (int i = 0; i < (1 << 20); ++i)
-                    if (mbar_try_wait(&bar[st], 0) || mbar_try_wait(&bar[st], 1)) break;
-        __syncthreads();
+    if (failed_at >= 0) {
+        cta_drain(bar, ST2, failed_at, ntiles);
         return;
     }
     for (int t = 0; t < TGT; ++t) {
@@ -887,6 +891,17 @@ constexpr double OPS_VK2 = 25.0, OPS_VKDT = 36.0, OPS_SPLIT = 6.0;
 
 
 
+// Algorithmic bytes of one gather + near-field SpMV launch: the pattern
+// (row pointers, columns) and the four combined block values of every entry
+// (value bytes vb each), x and y (2 nv doubles each) once, and with a far
+// field the vertex->triangle list and the per-triangle sums (6 doubles).
+static double spmv_bytes(const pb_mesh* m, bool far, int vb) {
+    const double nv = (double)m->nv, nt = (double)m->nt, nnz = (double)m->nnz;
+    double b = 4.0 * (nv + 1.0) + nnz * (4.0 + 4.0 * vb) + 2.0 * 16.0 * nv;
+    if (far) b += 4.0 * (nv + 1.0) + 4.0 * 3.0 * nt + 48.0 * nt;
+    return b;
+}
+
 int apply_blockop(const pb_mesh* m, const pb_near* nf, const BlockOp& B, int prec, const double* x, double* y,
                   cudaStream_t s) {
     if (prec != PB_F64 && prec != PB_F32 && prec != PB_F32_ACCURATE)
@@ -1027,6 +1042,7 @@ int apply_blockop(const pb_mesh* m, const pb_near* nf, const BlockOp& B, int pre
         }
     }
     unsigned gb = (unsigned)((nv * 8 + 255) / 256);
+    Timer tm(m->ctx, PB_KERNEL_SPMV, s, spmv_bytes(m, fp.any, prec == PB_F32 ? 4 : 8), 1.0);
     if (prec == PB_F32)
         k_gather_spmv<float><<<gb, 256, 0, s>>>(nv, m->v2t_ptr, m->v2t, tri, fp.any ? 1 : 0, m->row_ptr, m->col,
                                                 c32, m->nnz, x, y);
@@ -1034,6 +1050,7 @@ int apply_blockop(const pb_mesh* m, const pb_near* nf, const BlockOp& B, int pre
         k_gather_spmv<double><<<gb, 256, 0, s>>>(nv, m->v2t_ptr, m->v2t, tri, fp.any ? 1 : 0, m->row_ptr, m->col,
                                                  c64, m->nnz, x, y);
     ::pb::count_launch();
+    tm.stop();
     PB_CUDA(cudaGetLastError());
     return PB_OK;
 }
@@ -1237,6 +1254,7 @@ extern "C" int pb_system_apply_noalloc(pb_ctx* ctx, const pb_mesh* m, const pb_n
     using namespace pb;
     if (!ctx || !m || !nf || !prm || !x || !y) return set_error(PB_EINVAL, "pb_system_apply_noalloc: NULL argument");
     if (nf->mesh != m) return set_error(PB_EINVAL, "near field belongs to another mesh");
+    if (m->ctx != ctx) return set_error(PB_EINVAL, "pb_system_apply_noalloc: the mesh was loaded in another context");
     if (x == y) return set_error(PB_EINVAL, "x and y must not overlap");
     BlockOp B;
     PB_TRY(system_blockop(prm, form, alpha, beta, &B));
@@ -1253,9 +1271,10 @@ extern "C" int pb_system_apply_noalloc(pb_ctx* ctx, const pb_mesh* m, const pb_n
     if (need > NOALLOC_SCRATCH_BYTES)
         return set_error(PB_EINVAL, "pb_system_apply_noalloc: mesh needs %zu bytes of scratch, the limit is %zu "
                          "(%lld triangles here)", need, NOALLOC_SCRATCH_BYTES, (long long)nt);
-    PB_CUDA(cudaSetDevice(ctx->device));
+    // the mesh's device: its arrays, tensor map and occupancy queries all live there
+    PB_CUDA(cudaSetDevice(m->ctx->device));
     unsigned char* base = nullptr;
-    PB_TRY(noalloc_scratch(ctx->device, &base));
+    PB_TRY(noalloc_scratch(m->ctx->device, &base));
     float* rec = (float*)base;
     float* part = (float*)(base + b_src);
     double* tri = (double*)(base + b_src + b_part);
@@ -1409,5 +1428,78 @@ extern "C" int pb_selftest_wait(pb_ctx* ctx, int64_t polls, int* status_out) {
     cudaError_t e = cudaMemcpy(status_out, st, sizeof(int), cudaMemcpyDeviceToHost);
     cudaFree(st);
     if (e != cudaSuccess) return set_error(PB_ECUDA, "pb_selftest_wait: %s", cudaGetErrorString(e));
+    return PB_OK;
+}
+
+// ----------------------------------------------- arithmetic peak microbenchmark
+// Independent fused multiply-add chains (eight per thread, so that the pipe,
+// not the dependency latency, sets the rate) on a grid of four CTAs per SM:
+// the issue rate the roofline of the pair and near-field kernels is measured
+// against. The chains' sum is stored only when it equals an impossible value,
+// so the compiler keeps every FMA.
+namespace pb {
+template <typename T>
+__global__ void __launch_bounds__(256) k_fma_peak(int iters, T b, T c, T* __restrict__ out) {
+    T a[8];
+    for (int k = 0; k < 8; ++k) a[k] = (T)(threadIdx.x + k) * (T)1e-3;
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int u = 0; u < 16; ++u)
+#pragma unroll
+            for (int k = 0; k < 8; ++k) a[k] = fma(a[k], b, c);
+    }
+    T t = 0;
+    for (int k = 0; k < 8; ++k) t += a[k];
+    if (t == (T)-12345.0) out[0] = t;
+}
+__global__ void __launch_bounds__(256) k_fma2_peak(int iters, float b, float c, float* __restrict__ out) {
+    float2 a[8];
+    for (int k = 0; k < 8; ++k) a[k] = make_float2((threadIdx.x + k) * 1e-3f, (threadIdx.x - k) * 1e-3f);
+    const float2 bb = splat(b), cc = splat(c);
+    for (int i = 0; i < iters; ++i) {
+#pragma unroll
+        for (int u = 0; u < 16; ++u)
+#pragma unroll
+            for (int k = 0; k < 8; ++k) a[k] = fma2(a[k], bb, cc);
+    }
+    float t = 0;
+    for (int k = 0; k < 8; ++k) t += a[k].x + a[k].y;
+    if (t == -12345.0f) out[0] = t;
+}
+}  // namespace pb
+
+extern "C" int pb_measure_peak(pb_ctx* ctx, int kind, double* fma_per_s) {
+    using namespace pb;
+    if (!ctx || !fma_per_s || kind < 0 || kind > 2) return set_error(PB_EINVAL, "pb_measure_peak: bad argument");
+    PB_CUDA(cudaSetDevice(ctx->device));
+    double* out = nullptr;
+    PB_TRY(dev_alloc((void**)&out, 64));
+    const unsigned blocks = (unsigned)(4 * ctx->num_sms);
+    // about 20 ms per launch at the nominal rates
+    const int iters = kind == 1 ? 600 : 40000;
+    cudaEvent_t e0, e1;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    float best = 1e30f;
+    for (int rep = 0; rep < 4; ++rep) {  // the first launch warms up
+        cudaEventRecord(e0);
+        if (kind == 0) k_fma_peak<float><<<blocks, 256>>>(iters, 0.999999f, 1e-7f, (float*)out);
+        else if (kind == 1) k_fma_peak<double><<<blocks, 256>>>(iters, 0.999999, 1e-7, out);
+        else k_fma2_peak<<<blocks, 256>>>(iters / 2, 0.999999f, 1e-7f, (float*)out);
+        ::pb::count_launch();
+        cudaEventRecord(e1);
+        cudaEventSynchronize(e1);
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (rep > 0) best = std::min(best, ms);
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(out);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return set_error(PB_ECUDA, "pb_measure_peak: %s", cudaGetErrorString(e));
+    // FMAs per launch: threads x iterations x 16 x 8 chains (x 2 lanes for f32x2 at half the iterations)
+    const double fmas = (double)blocks * 256.0 * (double)iters * 128.0;
+    *fma_per_s = fmas / (best * 1e-3);
     return PB_OK;
 }

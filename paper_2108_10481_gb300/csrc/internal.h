@@ -83,6 +83,7 @@ struct CapturedTimer {
     int id;
     cudaEvent_t e0, e1;
     double pairs, ops;
+    double pairs_j;  // + pairs_j x (j + 1) for the Arnoldi step j the replay runs
 };
 struct StepGraph {
     cudaGraphExec_t exec = nullptr;
@@ -103,8 +104,12 @@ void graph_check(StepGraph& g);
 // PB_OK returned so that the caller runs the body directly.
 int graph_capture(StepGraph& g, cudaStream_t s, const std::function<int()>& body);
 int graph_replay(StepGraph& g, cudaStream_t s);
-// after a replay has completed: its profiled launches into the context's statistics
-int graph_credit(pb_ctx* ctx, StepGraph& g);
+// after a replay has completed: its profiled launches into the context's
+// statistics; j = the Arnoldi step the replay ran (work that grows with j)
+int graph_credit(pb_ctx* ctx, StepGraph& g, int j = 0);
+// the Arnoldi step the calling thread's GMRES is at (profiling of launches
+// whose work grows with j; set by the GMRES loop before each iteration)
+int& arnoldi_j();
 void graph_free(StepGraph& g);
 }  // namespace pb
 
@@ -300,8 +305,10 @@ struct Timer {
     cudaStream_t s;
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     double pairs, ops;
-    Timer(pb_ctx* c, int k, cudaStream_t st, double p, double o) : ctx(c), id(k), s(st), pairs(p), ops(o) {
-        if (ctx->profile && cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess)
+    double pairs_j;  // work that grows with the Arnoldi step: pairs + pairs_j (j + 1)
+    Timer(pb_ctx* c, int k, cudaStream_t st, double p, double o, double pj = 0.0)
+        : ctx(c), id(k), s(st), pairs(p), ops(o), pairs_j(pj) {
+        if (ctx && ctx->profile && cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess)
             record(e0);
     }
     // inside a stream capture an event record becomes a graph node only when
@@ -314,15 +321,16 @@ struct Timer {
         if (!e1) return;
         record(e1);
         if (StepGraph* g = capturing()) {  // recorded again by every replay
-            g->timers.push_back({id, e0, e1, pairs, ops});
+            g->timers.push_back({id, e0, e1, pairs, ops, pairs_j});
             e0 = e1 = nullptr;
             return;
         }
         KernelStats& st = ctx->stats[id];
+        const double p = pairs + pairs_j * (double)(arnoldi_j() + 1);
         st.events.push_back({e0, e1});
         st.launches += 1;
-        st.pairs += pairs;
-        st.ops += pairs * ops;
+        st.pairs += p;
+        st.ops += p * ops;
         e0 = e1 = nullptr;
     }
 };

@@ -119,11 +119,18 @@ int mass_solve(const pb_mesh* m, const pb_near* nf, const double* b, double* x, 
     const double* mdiag = nf->diag + N_M * nv;
     unsigned blocks = (unsigned)((n2 + 255) / 256);
     k_cheb_init<<<blocks, 256, 0, s>>>(nv, mdiag, b, x, r, d0, theta); ::pb::count_launch();
+    // algorithmic bytes of one step: the mass pattern once (row pointers, columns and
+    // values; nv + 3 nt entries on a closed surface) and its diagonal, d read, the
+    // next d written, x and r read and written (2 nv doubles each)
+    const double mnnz = (double)nv + 3.0 * (double)m->nt;
+    const double step_bytes = 4.0 * (double)(nv + 1) + 12.0 * mnnz + 8.0 * (double)nv + 6.0 * 8.0 * (double)n2;
     double rho = 1.0 / sigma;
     for (int k = 0; k < iters; ++k) {
         double rho_n = 1.0 / (2.0 * sigma - rho);
+        Timer tm(m->ctx, PB_KERNEL_CHEB, s, step_bytes, 1.0);
         k_cheb_step<<<blocks, 256, 0, s>>>(nv, nf->mrow_ptr, nf->mcol, mval, mdiag, d0, d1, x, r, rho_n * rho,
                                            2.0 * rho_n / delta); ::pb::count_launch();
+        tm.stop();
         rho = rho_n;
         double* t = d0;
         d0 = d1;
@@ -458,11 +465,12 @@ static int gmres(Solver& S, GmresWork& G, int prec, const double* b, double* x, 
     const int mmax = std::min(max_it, G.mmax);
     for (int j = 0; j < mmax; ++j) {
         StepGraph* g = nullptr;
+        arnoldi_j() = j;
         PB_TRY(iterate(S, G, prec, j, &g));
         double hr[2];
         PB_CUDA(cudaMemcpyAsync(hr, G.res, sizeof(hr), cudaMemcpyDeviceToHost, s));
         PB_CUDA(cudaStreamSynchronize(s));
-        if (g && S.m->ctx->profile) PB_TRY(graph_credit(S.m->ctx, *g));
+        if (g && S.m->ctx->profile) PB_TRY(graph_credit(S.m->ctx, *g, j));
         k = j + 1;
         res = hr[0] * beta / denom;
         if (!std::isfinite(res)) {
@@ -563,10 +571,21 @@ int gm_step(GmresWork& G, double* w, double* res_out, cudaStream_t s) {
     const int nchunk = (int)((n + DOT_CHUNK - 1) / DOT_CHUNK);
     const dim3 grid(nchunk, std::min(DOT_KY, G.mmax + 1));
     const unsigned kb = (unsigned)((G.mmax + 1 + 127) / 128);
+    // algorithmic bytes at step j: the dots read V[0..j] and w once ((j + 2) n
+    // doubles); the update reads V[0..j] and w and writes w ((j + 3) n doubles)
+    const double nb8 = 8.0 * (double)n;
     for (int pass = 0; pass < 2; ++pass) {
-        k_dots_j<<<grid, DOT_THREADS, 0, s>>>(n, G.V, w, G.part, nchunk, G.jdev);
+        {
+            Timer tm(G.ctx, PB_KERNEL_KRYLOV, s, nb8, 1.0, nb8);
+            k_dots_j<<<grid, DOT_THREADS, 0, s>>>(n, G.V, w, G.part, nchunk, G.jdev);
+            tm.stop();
+        }
         k_dots_finish_j<<<kb, 128, 0, s>>>(nchunk, G.part, G.H, ldh, G.y, G.jdev, pass);
-        k_vh_j<<<nb(n), 256, 0, s>>>(n, G.V, G.H, ldh, G.y, G.jdev, pass, w);
+        {
+            Timer tm(G.ctx, PB_KERNEL_KRYLOV, s, 2.0 * nb8, 1.0, nb8);
+            k_vh_j<<<nb(n), 256, 0, s>>>(n, G.V, G.H, ldh, G.y, G.jdev, pass, w);
+            tm.stop();
+        }
         ::pb::count_launch(3);
     }
     k_dots<<<dim3(nchunk, 1), DOT_THREADS, 0, s>>>(n, w, n, w, G.part, nchunk);  // ||w||^2 partials
@@ -662,6 +681,7 @@ static int solve_body(pb_ctx* ctx, const pb_mesh* m, const pb_near* nf, const pb
     int mmax = o->restart > 0 ? std::min(o->restart, o->max_it) : o->max_it;
     GmresWork G;
     PB_TRY(gmres_alloc(G, n2, mmax));
+    G.ctx = ctx;
     int worst = PB_OK;
     for (int k = 0; k < nrhs; ++k) {
         const int rc = solve_one(m, nf, o, b + (size_t)k * n2, x + (size_t)k * n2, info ? info + k : nullptr, s, S,

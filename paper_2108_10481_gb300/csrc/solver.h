@@ -40,6 +40,7 @@ struct GmresWork {
     double* vin = nullptr;   // n: copy of V[j], the operator's input
     int* jdev = nullptr;     // the iteration index j, kept on the device
     int mmax = 0;
+    pb_ctx* ctx = nullptr;   // profiled context of the Gram-Schmidt kernels (null: not profiled)
     int64_t n = 0;
     void* block = nullptr;
 };

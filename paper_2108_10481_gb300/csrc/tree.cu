@@ -1,6 +1,6 @@
-// Treecode far field for the FP32 inner iterations (the survey's next step
-// after the direct pair sum, in place of the paper's FMM; the paper uses
-// ExaFMM with expansion order 3 for its far field).
+// Treecode far field for the FP32 inner iterations: a fast far field in place
+// of the direct pair sum for large meshes, where the paper uses a fast
+// multipole method (ExaFMM, expansion order 3).
 //
 // The quadrature points are sorted into a kd-tree (longest-axis median
 // splits, leaves of at most LEAF points). For a leaf of targets and a cluster

@@ -93,6 +93,7 @@ SIGNATURES = {
     "pb_launch_count": [],
     "pb_selftest_wait": [P, c_int64, ctypes.POINTER(c_int)],
     "pb_selftest_exp": [P, P, P, c_int64, P],
+    "pb_measure_peak": [P, c_int, ctypes.POINTER(c_double)],
     "pb_set_graphs": [P, c_int],
     "pb_set_treecode": [P, c_int, c_int, c_double, c_int64],
     "pb_tree_info": [P, ctypes.POINTER(c_int64)],

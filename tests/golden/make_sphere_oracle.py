@@ -4,9 +4,13 @@ the cases of Table 1 that the sphere workload runs, under quadrature plan D0.
 
 Only the oracle runs here (dense assembly, dense preconditioned LU). Stored per
 case: Delta G (paper units and kcal/mol), the M-norms of the interior traces
-and the traces at 64 seeded vertices, which the GPU tests compare with.
+and the traces at 64 seeded vertices, which the GPU tests compare with. For
+the cases in TRACE_CASES the whole interior traces (u_int, v_int at every
+vertex) go to multi_charge_sphere_traces.npz, so that the GPU tests can take
+the M-norm of the difference itself.
 
-    python tests/golden/make_sphere_oracle.py      # ~30 min on 8 cores, ~25 GB
+    python tests/golden/make_sphere_oracle.py           # ~30 min on 8 cores, ~25 GB
+    python tests/golden/make_sphere_oracle.py --traces  # only the npz (TRACE_CASES)
 """
 import json
 import os
@@ -24,8 +28,28 @@ from oracle.closed_forms import kirkwood_energy  # noqa: E402
 from synth import multi_charge_sphere  # noqa: E402
 
 CASES = (2, 10, 12, 13, 14, 15, 19, 20, 23)
+TRACE_CASES = (2, 10, 20)
 SAMPLE_SEED = 11
 N_SAMPLE = 64
+
+
+def traces(out=os.path.join(HERE, "multi_charge_sphere_traces.npz")):
+    """Full interior traces of the TRACE_CASES solutions (dense LU)."""
+    phys = O.Physics()
+    v, t, xq, q = multi_charge_sphere()
+    t0 = time.time()
+    ops = oracle.assemble(v, t, phys.kappa)
+    print(f"assembled {len(v)} vertices in {time.time() - t0:.0f} s", flush=True)
+    arrays = {}
+    for case in TRACE_CASES:
+        t1 = time.time()
+        r = O.solve(v, t, xq, q, phys, case=case, ops=ops)
+        u, w = O.interior_traces(O.CASES[case][0], r.x, phys)
+        arrays[f"u_int_{case}"] = u
+        arrays[f"v_int_{case}"] = w
+        arrays[f"dG_kcal_{case}"] = np.array(r.dG_kcal)
+        print(f"case {case}: dG {r.dG_kcal:.8f} kcal/mol ({time.time() - t1:.0f} s)", flush=True)
+    np.savez_compressed(out, **arrays)
 
 
 def main(out=os.path.join(HERE, "multi_charge_sphere_oracle.json")):
@@ -63,4 +87,7 @@ def main(out=os.path.join(HERE, "multi_charge_sphere_oracle.json")):
 
 
 if __name__ == "__main__":
-    main()
+    if "--traces" in sys.argv:
+        traces()
+    else:
+        main()

@@ -7,7 +7,11 @@ oracle's dense-LU solutions stored in tests/golden/multi_charge_sphere_oracle.js
   interior Dirichlet trace within 1e-7 (a lower bound of the M-norm error) and
   the traces at 64 sampled vertices within 1e-6 of the trace's RMS value;
 - mixed precision (tol 1e-6, the benchmark's setting) for every case the
-  sphere workload runs: Delta G within 1e-5 relative.
+  sphere workload runs: Delta G within 1e-5 relative;
+- for Cases 2, 10 and 20, the whole interior traces of the oracle's solution
+  (tests/golden/multi_charge_sphere_traces.npz, same script): the M-norm of
+  the difference of the FP64 GPU traces (tol 1e-10) from them within 1e-7 of
+  the oracle traces' M-norm, for the Dirichlet and the Neumann trace.
 """
 import json
 import os
@@ -21,6 +25,7 @@ torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden", "multi_charge_sphere_oracle.json")
+TRACES = os.path.join(os.path.dirname(__file__), "golden", "multi_charge_sphere_traces.npz")
 
 
 @pytest.fixture(scope="module")
@@ -97,3 +102,24 @@ def test_mixed_matches_oracle_at_full_size(pb, golden, setup, case):
     print(f"case {case} mixed: {info['iters']} iterations, {info['outer_iters']} sweeps in {1e3 * dt:.0f} ms, "
           f"dG rel {e:.1e}")
     assert e < 1e-5
+
+
+@pytest.mark.parametrize("case", [2, 10, 20])
+def test_f64_traces_match_oracle_in_the_m_norm(pb, setup, case):
+    """||x_gpu - x_oracle||_M / ||x_oracle||_M <= 1e-7 for both interior traces."""
+    ctx, m, nf, xq, q, nv = setup
+    ref = np.load(TRACES)
+    x, info, dG, dt = _solve(pb, setup, case, pb.PB_F64, 1e-10)
+    form = pb.CASES[case][0]
+    u = x[:nv].contiguous()
+    w = x[nv:].contiguous()
+    if form in ("direct_ext", "direct_ext_perm", "cfie_ext", "pmchwt_ext", "muller_ext", "lu"):
+        w = w * (80.0 / 4.0)  # interface condition: eps_int v_int = eps_ext v_ext
+    for name, a in (("u", u), ("v", w)):
+        r = torch.as_tensor(ref[f"{name}_int_{case}"], device="cuda")
+        d = (a - r).contiguous()
+        Md = pb.pb_op_apply(ctx, m, nf, pb.PB_OP_M, pb.PB_LAPLACE, pb.PB_F64, d)
+        Mr = pb.pb_op_apply(ctx, m, nf, pb.PB_OP_M, pb.PB_LAPLACE, pb.PB_F64, r.contiguous())
+        e = float(torch.sqrt((d @ Md) / (r @ Mr)))
+        print(f"case {case} f64 {name}_int: M-norm of the difference {e:.1e} of the oracle's")
+        assert e < 1e-7, (case, name, e)

@@ -6,7 +6,10 @@ server whose device-memory budget admits only part of them at once (the rest
 queue and enter as memory frees). The energies must be identical (the batched
 pair kernel keeps every request's own decomposition and fixed reduction
 order), every request must converge, and each must agree with pb_solve of the
-same molecule within the mixed-precision tolerance (1e-5 relative)."""
+same molecule within the mixed-precision tolerance (1e-5 relative). Each
+served Delta G is also checked against the FP64 oracle's dense-LU solve of
+the same molecule and case (1e-5 relative), so that a fault common to the
+server and pb_solve cannot pass."""
 import numpy as np
 import pytest
 
@@ -52,7 +55,8 @@ def _run(pb, ctx, mols, idx, budget, max_active=8):
     return out, max_active_seen
 
 
-def test_server_results_alone_equal_in_mix(pb, molecules):
+@pytest.fixture(scope="module")
+def served(pb, molecules):
     ctx = pb.pb_init(0)
     alone = {}
     for i in range(len(CASES)):
@@ -60,6 +64,11 @@ def test_server_results_alone_equal_in_mix(pb, molecules):
         alone.update(r)
     # a budget that holds roughly two of these molecules at a time
     mixed, seen = _run(pb, ctx, molecules, list(range(len(CASES))), 600 << 20, max_active=3)
+    return ctx, alone, mixed, seen
+
+
+def test_server_results_alone_equal_in_mix(pb, molecules, served):
+    ctx, alone, mixed, seen = served
     for i in range(len(CASES)):
         a, m = alone[i], mixed[i]
         print(f"request {i}: atoms {CASES[i][0]} case {CASES[i][1]} dG {a['dG_kcal']:.8f} / {m['dG_kcal']:.8f} "
@@ -80,6 +89,21 @@ def test_server_results_alone_equal_in_mix(pb, molecules):
                               opts=pb.solve_opts(tol=1e-6, max_it=300, precision=pb.PB_MIXED))
         _, dGk = pb.pb_energy(ctx, m_, x, form, dxq, dq, P)
         assert abs(mixed[i]["dG_kcal"] / dGk - 1) < 1e-5, (i, mixed[i]["dG_kcal"], dGk)
+
+
+def test_served_results_match_the_oracle(pb, molecules, served):
+    """Every served Delta G against the FP64 oracle (dense assembly, dense LU
+    of the preconditioned system) of the same molecule, case and plan."""
+    import oracle
+    _, _, mixed, _ = served
+    phys = oracle.Physics(4.0, 80.0, 0.125)
+    for i, (atoms, case) in enumerate(CASES):
+        v, t, xq, q = molecules[i]
+        ref = oracle.solve(v, t, xq, q, phys, case=case)
+        e = abs(mixed[i]["dG_kcal"] / ref.dG_kcal - 1)
+        print(f"request {i}: atoms {atoms} case {case} ({len(t)} tris): served {mixed[i]['dG_kcal']:.8f}, "
+              f"oracle {ref.dG_kcal:.8f}, rel {e:.1e}")
+        assert e < 1e-5, (i, mixed[i]["dG_kcal"], ref.dG_kcal)
 
 
 def test_server_rejects_what_cannot_fit(pb, molecules):

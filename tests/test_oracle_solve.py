@@ -157,3 +157,36 @@ def test_interior_trace_conversion():
     ui, vi = O.interior_traces("direct_int", si.x, PH)
     ue, ve = O.interior_traces("direct_ext", se.x, PH)
     assert np.allclose(ui, ue, rtol=1e-9, atol=1e-14) and np.allclose(vi, ve, rtol=1e-9, atol=1e-14)
+
+
+def test_block_diagonal_preconditioner_inverts_the_per_dof_blocks():
+    """Pin of the block-diagonal preconditioner (paper, "Algebraic
+    preconditioners": the inverse of the diagonals of each block). For every
+    DOF i, P restricted to rows and columns (i, n+i) times A restricted to the
+    same positions is the 2x2 identity, and P has no entry anywhere else. A
+    wrong inverse (a swapped or mis-signed term, a transposed block) fails the
+    first check; a fill outside the per-DOF pattern fails the second. Cases 2,
+    4, 6 and 8 (direct and permuted forms, interior and exterior) on the
+    level-2 sphere."""
+    v, t, xq, q, o = _setup()
+    n = o.n
+    idx = np.arange(n)
+    mask = np.zeros((2 * n, 2 * n), dtype=bool)
+    for r0 in (0, n):
+        for c0 in (0, n):
+            mask[r0 + idx, c0 + idx] = True
+    for case in (2, 4, 6, 8):
+        s = oracle.solve(v, t, xq, q, PH, case=case, ops=o, keep=True)
+        P, A = s.P, s.A
+        assert np.all(P[~mask] == 0.0), case
+        # the 2x2 blocks of P and of A at (i, n+i), stacked per DOF
+        Pb = np.stack([[P[idx, idx], P[idx, n + idx]], [P[n + idx, idx], P[n + idx, n + idx]]]).transpose(2, 0, 1)
+        Ab = np.stack([[A[idx, idx], A[idx, n + idx]], [A[n + idx, idx], A[n + idx, n + idx]]]).transpose(2, 0, 1)
+        prod = Pb @ Ab
+        err = np.abs(prod - np.eye(2)[None]).max()
+        assert err < 1e-13, (case, err)
+        # and the 2x2 restriction of P A (not only of A) is the identity too: P A's
+        # diagonal blocks pick up nothing from A's off-diagonal entries
+        PA = P @ A
+        PAb = np.stack([[PA[idx, idx], PA[idx, n + idx]], [PA[n + idx, idx], PA[n + idx, n + idx]]])
+        assert np.abs(PAb.transpose(2, 0, 1) - np.eye(2)[None]).max() < 1e-13, case
