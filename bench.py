@@ -386,6 +386,11 @@ def run_ours(args, rank, world, local_rank):
         m.free()
         return dGk, info
 
+    # arithmetic issue rates by microbenchmark (FMAs per second), beside the unit-count peaks the
+    # rooflines use
+    alu_peaks = {"fp32_fma_per_s": pb.pb_measure_peak(ctx, 0), "fp64_fma_per_s": pb.pb_measure_peak(ctx, 1),
+                 "f32x2_fma_per_s": pb.pb_measure_peak(ctx, 2)}
+
     # warm-up (untimed)
     for _ in range(args.warmup):
         dGk, info = step()
@@ -588,6 +593,7 @@ def run_ours(args, rank, world, local_rank):
         "matvec": matvec,
         "roofline": rooflines[dominant],
         "roofline_by_kernel": rooflines,
+        "alu_microbenchmark": dict(alu_peaks, sms=n_sm, note="independent FMA chains, 4 CTAs x 256 threads per SM"),
         "clocks": clocks, "gpu_launches": int(launches), "wall_s": wall,
     }
     if e2e:
