@@ -150,6 +150,60 @@ __global__ void k_ss_table(Gauss gq, int n, double* __restrict__ tab) {
     for (int c = 0; c < 8; ++c) tab[(5 + c) * n + e] = mono[c];
 }
 
+// Outer points of the edge (kind 1, 6 regions) and vertex (kind 2, 2 regions)
+// maps: one entry per (region, xi, eta1, eta2). In both maps the innermost
+// Gauss variable eta3 enters a single coordinate, the second one (t) of one
+// frame, and linearly, while the region Jacobian does not involve it; so
+// over the eta3 points of an entry x - y = D0 + eta3 D1 and every weighted
+// monomial is affine in eta3. A pair's kernel sums then take two partial sums
+// per kernel over eta3 (sum w3 g, sum w3 eta3 g) and expand them into the
+// nine moments once per entry. Per entry (array c at v[c * n + e]):
+//   0..3  sa, ta, sa', ta': the frame coordinates at eta3 = 0 (x: s, t; y: s', t')
+//   4, 5  tb, tb': the slopes of t and t' in eta3 (one of them is zero)
+//   6..14 c0[3 alpha + beta] = W P_alpha Q_beta, P = (1, sa, ta), Q = (1, sa', ta'),
+//         W = the Gauss weights of xi, eta1, eta2 times the Jacobian
+//   15..19 the eta3-slope coefficients of the moments that change with eta3:
+//         (0,2) W tb', (1,2) W sa tb', (2,0) W tb, (2,1) W tb sa', (2,2) W (ta tb' + tb ta')
+// followed by the eta3 Gauss nodes and weights (2 n doubles).
+struct SSOuter {
+    const double* v;
+    int n;        // entries
+    int off[3];   // first entry of kind 1 and 2 (kind 0 unused)
+    int nss;      // Gauss points per dimension
+};
+constexpr int SS_OUTER_ARRAYS = 20;
+
+__global__ void k_ss_outer(Gauss gq, int n, double* __restrict__ tab) {
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    const int q = gq.n, n3 = q * q * q;
+    if (e < 2 * q) {  // the eta3 rule after the entries
+        tab[SS_OUTER_ARRAYS * n + e] = e < q ? gq.x[e] : gq.w[e - q];
+    }
+    if (e >= n) return;
+    int kind, idx;
+    if (e < 6 * n3) { kind = 1; idx = e; }
+    else { kind = 2; idx = e - 6 * n3; }
+    const int reg = idx / n3, r = idx - reg * n3;
+    const int i0 = r / (q * q), i1 = (r / q) % q, i2 = r % q;
+    double sx0, tx0, sy0, ty0, sx1, tx1, sy1, ty1;
+    const double jac = ss_map(kind, reg, gq.x[i0], gq.x[i1], gq.x[i2], 0.0, sx0, tx0, sy0, ty0);
+    const double jac1 = ss_map(kind, reg, gq.x[i0], gq.x[i1], gq.x[i2], 1.0, sx1, tx1, sy1, ty1);
+    const double tb = tx1 - tx0, tb2 = ty1 - ty0;
+    const double W = gq.w[i0] * gq.w[i1] * gq.w[i2] * jac;
+    // the structure the factorisation relies on: s, s' and the Jacobian free of eta3
+    const bool ok = sx1 == sx0 && sy1 == sy0 && jac1 == jac;
+    const double P[3] = {1.0, sx0, tx0}, Q[3] = {1.0, sy0, ty0};
+    double v[SS_OUTER_ARRAYS] = {sx0, tx0, sy0, ty0, tb, tb2};
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) v[6 + 3 * a + b] = ok ? W * P[a] * Q[b] : __longlong_as_double(0x7ff8000000000000LL);
+    v[15] = W * tb2;
+    v[16] = W * sx0 * tb2;
+    v[17] = W * tb;
+    v[18] = W * tb * sy0;
+    v[19] = W * (tx0 * tb2 + tb * ty0);
+    for (int c = 0; c < SS_OUTER_ARRAYS; ++c) tab[c * n + e] = v[c];
+}
+
 // Geometry of one triangle in the reordered frame of its singular map:
 // Q0, E1 = Q1 - Q0, E2 = Q2 - Q1 (x(s,t) = Q0 + s E1 + t E2), the inverse
 // permutation (original corner -> reordered), normal and area. Kept in shared
@@ -272,14 +326,12 @@ __device__ __forceinline__ void accum_point(double* acc, double w, const double*
 // shared vertex, and d = x - y is formed from the frame vectors directly.
 // mom[9 k + 3 alpha + beta], k = G_L, G_Y, K_L, K_Y (and with SYM the reversed
 // pair's double layers K^T_L, K^T_Y).
+// Kernel values at x - y = d for an adjacent pair: G_L, G_Y, the double layers
+// K_L, K_Y with the second triangle's normal and (SYM) the reversed pair's with
+// the first triangle's normal.
 template <bool SYM>
-__device__ __forceinline__ void accum_frame(double* mom, const SSTable& tab, int e, const double* dq,
-                                            const TriFrame& A, const TriFrame& B, double kappa) {
-    const double s = tab.sx[e], t = tab.tx[e], s2 = tab.sy[e], t2 = tab.ty[e];
-    double d[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k)
-        d[k] = __fma_rn(-t2, B.e2[k], __fma_rn(-s2, B.e1[k], __fma_rn(t, A.e2[k], __fma_rn(s, A.e1[k], dq[k]))));
+__device__ __forceinline__ void adj_kernels(const double* d, const TriFrame& A, const TriFrame& B, double kappa,
+                                            double* g) {
     const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
     const double rinv = rsqrt(r2);
     const double r = r2 * rinv;
@@ -288,21 +340,70 @@ __device__ __forceinline__ void accum_frame(double* mom, const SSTable& tab, int
     const double fl = gl * rinv * rinv;  // 1 / (4 pi r^3)
     const double fy_over_fl = ek * (1.0 + kappa * r);
     const double kl = fl * (d[0] * B.n[0] + d[1] * B.n[1] + d[2] * B.n[2]);
-    double g[6] = {gl, ek * gl, kl, kl * fy_over_fl, 0.0, 0.0};
+    g[0] = gl;
+    g[1] = ek * gl;
+    g[2] = kl;
+    g[3] = kl * fy_over_fl;
     if (SYM) {
         const double ktl = fl * -(d[0] * A.n[0] + d[1] * A.n[1] + d[2] * A.n[2]);  // (y - x).n_x
         g[4] = ktl;
         g[5] = ktl * fy_over_fl;
     }
-    double m[9];  // w (1, s, t) x (1, s', t'), from the table
-    m[0] = tab.w[e];
-#pragma unroll
-    for (int c = 0; c < 8; ++c) m[1 + c] = tab.mono[c * tab.n + e];
+}
+
+// One outer entry (region, xi, eta1, eta2) of an edge- or vertex-adjacent pair:
+// the NSS eta3 points summed per kernel into a0 = sum w3 g and a1 = sum w3 eta3 g,
+// then expanded into the moments (nine per kernel from a0, five from a1).
+// NSS = 0: the rule's size is read at run time.
+template <bool SYM, int NSS>
+__device__ __forceinline__ void accum_outer(double* mom, const SSOuter& tab, int e, const double* dq,
+                                            const TriFrame& A, const TriFrame& B, double kappa, const double* x3,
+                                            const double* w3) {
     constexpr int NK = SYM ? 6 : 4;
+    const int n = tab.n;
+    const double sa = tab.v[e], ta = tab.v[n + e], sa2 = tab.v[2 * n + e], ta2 = tab.v[3 * n + e];
+    const double tb = tab.v[4 * n + e], tb2 = tab.v[5 * n + e];
+    double D0[3], D1[3];
 #pragma unroll
-    for (int k = 0; k < NK; ++k)
+    for (int k = 0; k < 3; ++k) {
+        D0[k] = __fma_rn(-ta2, B.e2[k], __fma_rn(-sa2, B.e1[k], __fma_rn(ta, A.e2[k], __fma_rn(sa, A.e1[k], dq[k]))));
+        D1[k] = __fma_rn(tb, A.e2[k], -tb2 * B.e2[k]);
+    }
+    double a0[NK], a1[NK];
 #pragma unroll
-        for (int c = 0; c < 9; ++c) mom[9 * k + c] += g[k] * m[c];
+    for (int k = 0; k < NK; ++k) a0[k] = a1[k] = 0.0;
+    const int nss = NSS > 0 ? NSS : tab.nss;
+#pragma unroll
+    for (int j = 0; j < (NSS > 0 ? NSS : 12); ++j) {
+        if (NSS == 0 && j >= nss) break;
+        const double x = x3[j], w = w3[j], wx = w * x;
+        double d[3];
+#pragma unroll
+        for (int k = 0; k < 3; ++k) d[k] = __fma_rn(x, D1[k], D0[k]);
+        double g[6];
+        adj_kernels<SYM>(d, A, B, kappa, g);
+#pragma unroll
+        for (int k = 0; k < NK; ++k) {
+            a0[k] = __fma_rn(w, g[k], a0[k]);
+            a1[k] = __fma_rn(wx, g[k], a1[k]);
+        }
+    }
+    double c0[9], c1[5];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) c0[c] = tab.v[(6 + c) * n + e];
+#pragma unroll
+    for (int c = 0; c < 5; ++c) c1[c] = tab.v[(15 + c) * n + e];
+#pragma unroll
+    for (int k = 0; k < NK; ++k) {
+        double* mk = mom + 9 * k;
+#pragma unroll
+        for (int c = 0; c < 9; ++c) mk[c] = __fma_rn(c0[c], a0[k], mk[c]);
+        mk[2] = __fma_rn(c1[0], a1[k], mk[2]);
+        mk[5] = __fma_rn(c1[1], a1[k], mk[5]);
+        mk[6] = __fma_rn(c1[2], a1[k], mk[6]);
+        mk[7] = __fma_rn(c1[3], a1[k], mk[7]);
+        mk[8] = __fma_rn(c1[4], a1[k], mk[8]);
+    }
 }
 
 // coincident pair: one frame, d = (s - s') e1 + (t - t') e2; k = G_L, G_Y
@@ -418,27 +519,34 @@ __device__ void expand_blocks(const double* acc, const TriFrame& A, const TriFra
 
 constexpr int NEAR_THREADS = 128;
 
-// FP64 flops per quadrature point pair of a regularised rule by formula count
-// (a fused multiply-add counted as two). Kernel evaluation: d = x - y from the
-// frame vectors (24); r^2 (5), rsqrt, r, 1/(4 pi r), kappa r, exp, the Yukawa
-// single layer (6), 1/r^3 (2), (1 + kappa r) and the Yukawa double-layer
-// factor (3), d.n_y (5) and both double layers (2): 47; with the reversed
-// pair's double layer, d.n_x (5) and its two kernels (2): 54. Accumulation:
-// one FMA per kernel and moment, 2 x 6 x 9 (108); the weighted monomials
-// w (1, s, t) x (1, s', t') come from the rule's table and the pair's Jacobian
-// multiplies the finished moments. Coincident pairs: d from (s - s', t - t')
-// (11), r^2 to the Yukawa single layer (11); 2 x 2 x 9 (36).
+// FP64 flops per quadrature point pair by formula count (a fused multiply-add
+// counted as two). NEAR_FLOPS_SYM: one point pair with all six kernels and a
+// direct accumulation into the 3x3 blocks (the far-rule pairs of an adjacent
+// pair, accum_point). Kernel evaluation: d = x - y (24 when formed from frame
+// vectors); r^2 (5), rsqrt, r, 1/(4 pi r), kappa r, exp, the Yukawa single
+// layer (6), 1/r^3 (2), (1 + kappa r) and the Yukawa double-layer factor (3),
+// d.n_y (5) and both double layers (2): 47; with the reversed pair's double
+// layer, d.n_x (5) and its two kernels (2): 54. Accumulation: one FMA per
+// kernel and block entry, 2 x 6 x 9 (108). Coincident pairs (moments from the
+// rule's table of weighted monomials): d from (s - s', t - t') (11), r^2 to
+// the Yukawa single layer (11); 2 x 2 x 9 (36).
 constexpr double NEAR_FLOPS_SYM = 54 + 108;
 constexpr double NEAR_FLOPS_COIN = 22 + 36;
+// The factorised adjacent-pair sums (accum_outer): per quadrature point pair
+// the kernel evaluation with d = D0 + eta3 D1 (3 FMA instead of 12: 36) and the
+// two partial sums per kernel (2 x 6 FMA: 24); per outer entry D0 and D1
+// (12 FMA, 3 FMA and 3 products: 33) and the moments (6 kernels x 14 FMA: 168).
+constexpr double NEAR_FLOPS_ADJ_POINT = 36 + 24;
+constexpr double NEAR_FLOPS_ADJ_OUTER = 33 + 168;
 
 // One warp per listed pair. Writes ss[p][54] (regularised) and far[p][54] (far
 // rule, identical points excluded); with SYM also the blocks of the reversed
 // pair rev[p], whose rule is this one with the roles exchanged.
-template <int MINB, bool SYM>
+template <int MINB, bool SYM, int NSS>
 __global__ void __launch_bounds__(NEAR_THREADS, MINB)
 k_near_pairs(const double* __restrict__ verts, const int32_t* __restrict__ tris, const double* __restrict__ tgeo,
              const int4* __restrict__ pairs, const int32_t* __restrict__ list, int64_t nlist,
-             const int32_t* __restrict__ rev, SSTable tab, int n4, Rule rule, double kappa,
+             const int32_t* __restrict__ rev, SSOuter tab, Rule rule, double kappa,
              double* __restrict__ ss_out, double* __restrict__ far_out) {
     constexpr int NA = SYM ? NACC_SYM : NACC_NEAR;
     constexpr int NM = SYM ? 54 : 36;  // frame moments
@@ -457,13 +565,26 @@ k_near_pairs(const double* __restrict__ verts, const int32_t* __restrict__ tris,
     const int kind = pr.z;
     const int nreg = kind == 2 ? 2 : 6;
     const int e0 = tab.off[kind];
+    const int n3 = tab.nss * tab.nss * tab.nss;
     const double jac_ab = (2.0 * A.area) * (2.0 * B.area);
     const double dq[3] = {A.q0[0] - B.q0[0], A.q0[1] - B.q0[1], A.q0[2] - B.q0[2]};  // 0: the shared vertex
+    // the eta3 rule, in registers for a fixed size
+    double x3[NSS > 0 ? NSS : 1], w3[NSS > 0 ? NSS : 1];
+    const double* rule3 = tab.v + (size_t)SS_OUTER_ARRAYS * tab.n;
+    if (NSS > 0) {
+#pragma unroll
+        for (int j = 0; j < (NSS > 0 ? NSS : 1); ++j) {
+            x3[j] = rule3[j];
+            w3[j] = rule3[tab.nss + j];
+        }
+    }
     double acc[NA];
     {
         double mom[NM];
         for (int k = 0; k < NM; ++k) mom[k] = 0.0;
-        for (int idx = lane; idx < nreg * n4; idx += 32) accum_frame<SYM>(mom, tab, e0 + idx, dq, A, B, kappa);
+        for (int idx = lane; idx < nreg * n3; idx += 32)
+            accum_outer<SYM, NSS>(mom, tab, e0 + idx, dq, A, B, kappa, NSS > 0 ? x3 : rule3,
+                                  NSS > 0 ? w3 : rule3 + tab.nss);
         warp_allsum<NM, 64>(mom, lane, red[wid]);
         for (int k = 0; k < NM; ++k) mom[k] *= jac_ab;  // the pair's Jacobian, once
         // corner blocks in the accumulator layout of accum_point
@@ -895,6 +1016,19 @@ static int build(pb_ctx* ctx, const pb_mesh* m, double kappa, pb_near* nf, cudaS
         ::pb::count_launch();
         SSTable tab = {tabm, tabm + ntab, tabm + 2 * ntab, tabm + 3 * ntab, tabm + 4 * ntab, tabm + 5 * ntab,
                        {8 * n4i, 0, 6 * n4i}, ntab};
+        // the outer entries of the edge and vertex maps (factorised adjacent-pair sums)
+        const int n3i = m->n_ss * m->n_ss * m->n_ss, nout = 8 * n3i;
+        double* tabo = nullptr;
+        rc = dev_alloc((void**)&tabo, sizeof(double) * ((size_t)SS_OUTER_ARRAYS * nout + 2 * m->n_ss));
+        if (rc != PB_OK) {
+            cudaFree(tabm);
+            cudaFree(ss);
+            cudaFree(far);
+            return rc;
+        }
+        k_ss_outer<<<(std::max(nout, 2 * m->n_ss) + 127) / 128, 128, 0, s>>>(gq, nout, tabo);
+        ::pb::count_launch();
+        SSOuter outer = {tabo, nout, {0, 0, 6 * n3i}, m->n_ss};
         int threads = NEAR_THREADS;  // one warp per pair
         // coincident pairs, then one of each pair of reversed pairs (which also writes the other)
         unsigned bc = (unsigned)((m->n_coin * 32 + threads - 1) / threads);
@@ -910,12 +1044,16 @@ static int build(pb_ctx* ctx, const pb_mesh* m, double kappa, pb_near* nf, cudaS
         }
         ::pb::count_launch();
         if (bp) {
-            const double evals = m->n_prim_edge * (6.0 * n4) + (m->n_prim - m->n_prim_edge) * (2.0 * n4) +
-                                 m->n_prim * Q * Q;
-            Timer tm(ctx, PB_KERNEL_NEAR_ADJ, s, evals, NEAR_FLOPS_SYM);
-            k_near_pairs<2, true><<<bp, threads, 0, s>>>(m->verts, m->tris, m->tgeo, m->pairs, m->pair_prim,
-                                                         m->n_prim, m->pair_rev, tab, n4i, mesh_rule(m), kappa, ss,
-                                                         far);
+            const double outer_pts = (m->n_prim_edge * 6.0 + (m->n_prim - m->n_prim_edge) * 2.0) * n3i;
+            const double reg = outer_pts * m->n_ss, farp = m->n_prim * Q * Q;
+            const double flops = reg * NEAR_FLOPS_ADJ_POINT + outer_pts * NEAR_FLOPS_ADJ_OUTER + farp * NEAR_FLOPS_SYM;
+            Timer tm(ctx, PB_KERNEL_NEAR_ADJ, s, reg + farp, flops / (reg + farp));
+#define PB_NEAR_ARGS m->verts, m->tris, m->tgeo, m->pairs, m->pair_prim, m->n_prim, m->pair_rev, outer, mesh_rule(m), \
+                     kappa, ss, far
+            if (m->n_ss == 4) k_near_pairs<2, true, 4><<<bp, threads, 0, s>>>(PB_NEAR_ARGS);
+            else if (m->n_ss == 3) k_near_pairs<2, true, 3><<<bp, threads, 0, s>>>(PB_NEAR_ARGS);
+            else k_near_pairs<2, true, 0><<<bp, threads, 0, s>>>(PB_NEAR_ARGS);
+#undef PB_NEAR_ARGS
             tm.stop();
         }
         ::pb::count_launch();
@@ -979,6 +1117,7 @@ static int build(pb_ctx* ctx, const pb_mesh* m, double kappa, pb_near* nf, cudaS
         if (e != cudaSuccess) rc = set_error(PB_ECUDA, "near build: %s", cudaGetErrorString(e));
         else if (st == PB_EMESH) rc = set_error(PB_EMESH, "internal: band pair without reverse");
         cudaFree(tabm);
+        cudaFree(tabo);
     }
     if (ss) cudaFree(ss);
     if (far) cudaFree(far);

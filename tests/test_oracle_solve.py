@@ -190,3 +190,21 @@ def test_block_diagonal_preconditioner_inverts_the_per_dof_blocks():
         PA = P @ A
         PAb = np.stack([[PA[idx, idx], PA[idx, n + idx]], [PA[n + idx, idx], PA[n + idx, n + idx]]])
         assert np.abs(PAb.transpose(2, 0, 1) - np.eye(2)[None]).max() < 1e-13, case
+
+
+def test_stored_sphere_traces_agree_with_the_stored_samples():
+    """The whole traces stored for the full-size GPU parity tests (npz) and the
+    samples, M-norms' companions and energies stored with them (json) come
+    from the same oracle solves: the traces at the sampled vertices and Delta G
+    must agree to rounding."""
+    here = os.path.join(os.path.dirname(__file__), "golden")
+    js = json.load(open(os.path.join(here, "multi_charge_sphere_oracle.json")))
+    tr = np.load(os.path.join(here, "multi_charge_sphere_traces.npz"))
+    idx = np.asarray(js["sample_vertices"])
+    for case in (2, 10, 20):
+        ref = js["cases"][str(case)]
+        assert abs(float(tr[f"dG_kcal_{case}"]) / ref["dG_kcal"] - 1) < 1e-12
+        for name in ("u", "v"):
+            full = tr[f"{name}_int_{case}"]
+            samp = np.asarray(ref[f"{name}_int_sample"])
+            assert np.abs(full[idx] - samp).max() <= 1e-10 * np.abs(samp).max(), (case, name)
