@@ -36,9 +36,10 @@ def lib():
             I64 = ctypes.c_int64
             I = ctypes.c_int
             D = ctypes.c_double
-            L.oracle_pair_blocks.argtypes = [P, P, I64, I64, I, P, P, I, P, P, D, D, I, P, P, P]
-            L.oracle_assemble_dense.argtypes = [P, I64, P, I64, I, P, P, I, P, P, D, D, I, P, P, I] + [P] * 7
-            L.oracle_assemble_rows.argtypes = [P, I64, P, I64, P, I64, I, P, P, I, P, P, D, D, I, P, P, I] + [P] * 7
+            # singular rules: sizes int[3] (coincident, edge, vertex), nodes and weights concatenated
+            L.oracle_pair_blocks.argtypes = [P, P, I64, I64, I, P, P, P, P, P, D, D, I, P, P, P]
+            L.oracle_assemble_dense.argtypes = [P, I64, P, I64, I, P, P, P, P, P, D, D, I, P, P, I] + [P] * 7
+            L.oracle_assemble_rows.argtypes = [P, I64, P, I64, P, I64, I, P, P, P, P, P, D, D, I, P, P, I] + [P] * 7
             L.oracle_rhs.argtypes = [P, I64, P, I64, I, P, P, P, P, I64, D, P, P]
             L.oracle_reaction_potential.argtypes = [P, I64, P, I64, I, P, P, P, P, P, I64, P]
             for f in (L.oracle_pair_blocks, L.oracle_assemble_dense, L.oracle_assemble_rows,

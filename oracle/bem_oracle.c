@@ -28,7 +28,9 @@
  *     that are far apart relative to their size;
  *   - coincident, edge-adjacent and vertex-adjacent pairs: regularising maps
  *     of [0,1]^4 in the manner of Sauter and Schwab (6, 6 and 2 regions) with
- *     an n-point Gauss-Legendre rule per dimension (nodes/weights passed in).
+ *     an n-point Gauss-Legendre rule per dimension (nodes/weights passed in),
+ *     n chosen per class: ng[0] coincident, ng[1] edge, ng[2] vertex, the
+ *     three rules' nodes (and weights) one after another in gx (gw).
  *
  * Reference triangle for the singular maps: T^ = {(s,t): 0 <= t <= s <= 1},
  * vertices (0,0), (1,0), (1,1); a triangle with reordered vertices (Q0,Q1,Q2)
@@ -300,7 +302,7 @@ static int in_band(const tri_geom* t, const tri_geom* s, double eta) {
 
 /* Local blocks of one triangle pair (test tau = tri ti, trial sigma = tri tj). */
 static void pair_blocks(const double* verts, const int32_t* tris, int64_t ti, int64_t tj,
-                        int nq, const double* rl, const double* rw, int ng, const double* gx,
+                        int nq, const double* rl, const double* rw, const int* ng, const double* gx,
                         const double* gw, double kappa, const band_rule* band, double blk[NOPS][3][3]) {
     memset(blk, 0, sizeof(double) * NOPS * 9);
     const int32_t* A = tris + 3 * ti;
@@ -320,7 +322,7 @@ static void pair_blocks(const double* verts, const int32_t* tris, int64_t ti, in
             far_pair(&t, &s, nq, rl, rw, kappa, blk);
     } else if (ns == 3) {
         int id[3] = {0, 1, 2};
-        singular_pair(&t, id, &s, id, COIN, 6, ng, gx, gw, kappa, blk);
+        singular_pair(&t, id, &s, id, COIN, 6, ng[0], gx, gw, kappa, blk);
     } else if (ns == 2) {
         /* reorder both so that the shared edge runs Q0 -> Q1 with the same
          * orientation in both parameterisations: from its lower to its higher
@@ -329,17 +331,17 @@ static void pair_blocks(const double* verts, const int32_t* tris, int64_t ti, in
         int k0 = A[sa[0]] < A[sa[1]] ? 0 : 1, k1 = 1 - k0;
         int pt[3] = {sa[k0], sa[k1], 3 - sa[0] - sa[1]};
         int ps[3] = {sb[k0], sb[k1], 3 - sb[0] - sb[1]};
-        singular_pair(&t, pt, &s, ps, EDGE, 6, ng, gx, gw, kappa, blk);
+        singular_pair(&t, pt, &s, ps, EDGE, 6, ng[1], gx + ng[0], gw + ng[0], kappa, blk);
     } else {
         int pt[3] = {sa[0], (sa[0] + 1) % 3, (sa[0] + 2) % 3};
         int ps[3] = {sb[0], (sb[0] + 1) % 3, (sb[0] + 2) % 3};
-        singular_pair(&t, pt, &s, ps, VERT, 2, ng, gx, gw, kappa, blk);
+        singular_pair(&t, pt, &s, ps, VERT, 2, ng[2], gx + ng[0] + ng[1], gw + ng[0] + ng[1], kappa, blk);
     }
 }
 
 /* Exposed for unit tests: the six local blocks of one pair, [6][3][3]. */
 int oracle_pair_blocks(const double* verts, const int32_t* tris, int64_t ti, int64_t tj, int nq,
-                       const double* rl, const double* rw, int ng, const double* gx,
+                       const double* rl, const double* rw, const int* ng, const double* gx,
                        const double* gw, double kappa, double band_eta, int nbq, const double* brl,
                        const double* brw, double* out) {
     double blk[NOPS][3][3];
@@ -371,7 +373,7 @@ static int colour_triangles(const int32_t* tris, int64_t nt, int64_t nv, int* co
 /* Dense assembly. out: NOPS matrices of nv*nv doubles (row = test vertex),
  * plus the mass matrix mass[nv*nv]. Matrices must be zeroed by the caller. */
 int oracle_assemble_dense(const double* verts, int64_t nv, const int32_t* tris, int64_t nt,
-                          int nq, const double* rl, const double* rw, int ng, const double* gx,
+                          int nq, const double* rl, const double* rw, const int* ng, const double* gx,
                           const double* gw, double kappa, double band_eta, int nbq, const double* brl,
                           const double* brw, int nthreads, double* VL, double* KL,
                           double* DL, double* VY, double* KY, double* DY, double* mass) {
@@ -415,7 +417,7 @@ int oracle_assemble_dense(const double* verts, int64_t nv, const int32_t* tris, 
  * they are processed in parallel without any shared writes. */
 int oracle_assemble_rows(const double* verts, int64_t nv, const int32_t* tris, int64_t nt,
                          const int64_t* rows, int64_t nrows, int nq, const double* rl,
-                         const double* rw, int ng, const double* gx, const double* gw,
+                         const double* rw, const int* ng, const double* gx, const double* gw,
                          double kappa, double band_eta, int nbq, const double* brl, const double* brw,
                          int nthreads, double* VL, double* KL, double* DL,
                          double* VY, double* KY, double* DY, double* mass) {

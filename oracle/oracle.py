@@ -57,10 +57,21 @@ class Plan:
     n_ss: int = 4
     band_eta: float = 0.0
     band_q: int = 6
+    # Gauss points per dimension of the singular rule for each class of pair
+    # (None: n_ss). The paper states one singular order; a per-class order is
+    # the same definition with the rule chosen by the pair's class.
+    n_ss_coin: int | None = None
+    n_ss_edge: int | None = None
+    n_ss_vert: int | None = None
 
     @property
     def ref_q(self) -> int:
         return self.band_q if self.band_eta > 0 else self.far_q
+
+    @property
+    def n_ss_classes(self) -> tuple:
+        """(coincident, edge, vertex) Gauss points per dimension."""
+        return tuple(self.n_ss if n is None else n for n in (self.n_ss_coin, self.n_ss_edge, self.n_ss_vert))
 
 
 def _ptr(a: np.ndarray):
@@ -74,9 +85,15 @@ def _mesh_arrays(verts, tris):
 
 
 def _rules(plan: Plan):
+    """Far triangle rule and the three singular Gauss rules (coincident, edge,
+    vertex) one after another, with their sizes."""
     rl, rw = triangle_rule(plan.far_q)
-    gx, gw = gauss_legendre01(plan.n_ss)
-    return rl, rw, gx, gw
+    ns = plan.n_ss_classes
+    rules = [gauss_legendre01(n) for n in ns]
+    gx = np.ascontiguousarray(np.concatenate([r[0] for r in rules]))
+    gw = np.ascontiguousarray(np.concatenate([r[1] for r in rules]))
+    ng = np.ascontiguousarray(np.array(ns, dtype=np.int32))
+    return rl, rw, ng, gx, gw
 
 
 def _band(plan: Plan):
@@ -112,11 +129,11 @@ class Operators:
 def pair_blocks(verts, tris, ti, tj, kappa, plan=Plan()):
     """Six local 3x3 blocks (V_L, K_L, D_L, V_Y, K_Y, D_Y) of one triangle pair."""
     v, t = _mesh_arrays(verts, tris)
-    rl, rw, gx, gw = _rules(plan)
+    rl, rw, ng, gx, gw = _rules(plan)
     eta, nb, bl, bw = _band(plan)
     out = np.zeros((6, 3, 3))
     _clib.lib().oracle_pair_blocks(_ptr(v), _ptr(t), ti, tj, rl.shape[0], _ptr(rl), _ptr(rw),
-                                   gx.shape[0], _ptr(gx), _ptr(gw), float(kappa), eta, nb, _ptr(bl), _ptr(bw),
+                                   _ptr(ng), _ptr(gx), _ptr(gw), float(kappa), eta, nb, _ptr(bl), _ptr(bw),
                                    _ptr(out))
     return out
 
@@ -125,11 +142,11 @@ def assemble(verts, tris, kappa, plan=Plan(), nthreads=0) -> Operators:
     """Dense assembly of all operators (loop over all triangle pairs)."""
     v, t = _mesh_arrays(verts, tris)
     nv, nt = v.shape[0], t.shape[0]
-    rl, rw, gx, gw = _rules(plan)
+    rl, rw, ng, gx, gw = _rules(plan)
     eta, nb, bl, bw = _band(plan)
     mats = [np.zeros((nv, nv)) for _ in range(7)]
     rc = _clib.lib().oracle_assemble_dense(
-        _ptr(v), nv, _ptr(t), nt, rl.shape[0], _ptr(rl), _ptr(rw), gx.shape[0], _ptr(gx),
+        _ptr(v), nv, _ptr(t), nt, rl.shape[0], _ptr(rl), _ptr(rw), _ptr(ng), _ptr(gx),
         _ptr(gw), float(kappa), eta, nb, _ptr(bl), _ptr(bw), int(nthreads), *[_ptr(m) for m in mats])
     if rc < 0:
         raise RuntimeError(f"oracle assembly failed ({rc})")
@@ -141,12 +158,12 @@ def assemble_rows(verts, tris, rows, kappa, plan=Plan(), nthreads=0):
     v, t = _mesh_arrays(verts, tris)
     nv, nt = v.shape[0], t.shape[0]
     r = np.ascontiguousarray(rows, dtype=np.int64)
-    rl, rw, gx, gw = _rules(plan)
+    rl, rw, ng, gx, gw = _rules(plan)
     eta, nb, bl, bw = _band(plan)
     mats = [np.zeros((r.shape[0], nv)) for _ in range(7)]
     _clib.lib().oracle_assemble_rows(
         _ptr(v), nv, _ptr(t), nt, _ptr(r), r.shape[0], rl.shape[0], _ptr(rl), _ptr(rw),
-        gx.shape[0], _ptr(gx), _ptr(gw), float(kappa), eta, nb, _ptr(bl), _ptr(bw), int(nthreads),
+        _ptr(ng), _ptr(gx), _ptr(gw), float(kappa), eta, nb, _ptr(bl), _ptr(bw), int(nthreads),
         *[_ptr(m) for m in mats])
     return dict(zip(["VL", "KL", "DL", "VY", "KY", "DY", "M"], mats))
 

@@ -198,3 +198,40 @@ def test_far_pair_uses_the_triangle_rule():
     assert np.allclose(blk[0], V, rtol=1e-13, atol=0)
     assert np.allclose(blk[1], K, rtol=1e-12, atol=1e-18)
     assert np.allclose(blk[3], VY, rtol=1e-13, atol=0)
+
+
+def _shared(t, i, j):
+    return len(set(t[i]) & set(t[j]))
+
+
+def test_per_class_singular_orders():
+    """A plan with a singular order per class of pair (coincident, edge,
+    vertex) uses, for every pair, the plain plan's rule of its own class's
+    order, and nothing else changes: the blocks of a pair of class c under
+    (n_coin, n_edge, n_vert) equal its blocks under the plain plan with
+    n_ss = n_c, bit for bit; per-class orders all equal to n_ss are the plain
+    plan, bit for bit, for the whole assembly."""
+    from synth import icosphere
+    v, t = icosphere(1, 1.5)
+    kappa = 0.125
+    by_class = {3: [], 2: [], 1: [], 0: []}
+    for i in range(len(t)):
+        for j in range(len(t)):
+            k = _shared(t, i, j)
+            if len(by_class[k]) < 3:
+                by_class[k].append((i, j))
+    mixed = Plan(6, 4, n_ss_coin=5, n_ss_edge=3, n_ss_vert=2)
+    order = {3: 5, 2: 3, 1: 2}
+    for k, pairs in by_class.items():
+        assert pairs, k
+        for i, j in pairs:
+            got = pair_blocks(v, t, i, j, kappa, mixed)
+            want = pair_blocks(v, t, i, j, kappa, Plan(6, order.get(k, 4)))
+            assert np.array_equal(got, want), (k, i, j)
+            if k in order:  # and the order matters for that class
+                assert not np.array_equal(got, pair_blocks(v, t, i, j, kappa, Plan(6, 4))), (k, i, j)
+    import oracle
+    a = oracle.assemble(v, t, kappa, Plan(6, 4))
+    b = oracle.assemble(v, t, kappa, Plan(6, 4, n_ss_coin=4, n_ss_edge=4, n_ss_vert=4))
+    for name in ("VL", "KL", "DL", "VY", "KY", "DY", "M"):
+        assert np.array_equal(getattr(a, name), getattr(b, name)), name
