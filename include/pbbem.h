@@ -109,7 +109,7 @@ typedef struct {
 
 /* quadrature plan: the discrete definition of every operator entry
  * (paper, Results: the orders of the regular and singular rules). A zeroed
- * struct is not a valid plan; {6, 4, 0.0, 6} is the reference plan. */
+ * struct is not a valid plan; {6, 4, 0.0, 6, 0, 0, 0} is the reference plan. */
 typedef struct {
     int far_q; /* points of the symmetric triangle rule used on both triangles of
                   pairs that share no vertex: 1, 3 (degree 2) or 6 (degree 4) */
@@ -122,6 +122,9 @@ typedef struct {
                   runs with far_q and the near field adds the difference */
     int band_q; /* band rule (3 or 6, finer than far_q; 0 means 6). With a band,
                   the right-hand side and the energy use the band rule. */
+    int n_ss_coin; /* Gauss points per dimension of the singular rule for each */
+    int n_ss_edge; /* class of adjacent pair: coincident, edge-adjacent, vertex- */
+    int n_ss_vert; /* adjacent (1..12; 0 means n_ss). The paper states one order. */
 } pb_quad_plan;
 
 /* memory kind of pb_mesh_load's inputs */
@@ -360,22 +363,40 @@ int pb_poll(pb_server* srv, pb_result* out, int max, int* n_out);
 /* Launch tuning of the FP32 far field (not in the paper: its software uses
  * fixed FMM and quadrature settings). */
 typedef struct {
-    int kernel;          /* chosen FP32 kernel: 1 scalar, 2 packed f32x2 */
-    double split_scale;  /* chosen multiplier of the wave-filling split count */
-    double best_ms;      /* one FP32 system application with the choice */
-    double default_ms;   /* ... with the untuned default (packed, x1) */
+    int kernel;             /* chosen FP32 kernel: 1 scalar, 2 packed f32x2 */
+    int shape;              /* launch shape of the packed kernel (0 = default) */
+    int tile_records;       /* source records per TMA tile of the chosen launch */
+    int stages;             /* its pipeline stages */
+    int targets_per_thread; /* its targets per thread */
+    double split_scale;     /* chosen multiplier of the wave-filling split count */
+    double best_ms;         /* one FP32 system application with the choice */
+    double default_ms;      /* ... with the untuned default (packed, shape 0, x1) */
+} pb_tune_choice;
+typedef struct {
+    pb_tune_choice fast;     /* PB_F32 applications (FP32 tile sums) */
+    pb_tune_choice accurate; /* PB_F32_ACCURATE applications (split coordinates, FP64 tile sums) */
 } pb_tune_result;
 /* Time every candidate launch of formulation `form`'s FP32 system application
- * on this mesh (fast and split-coordinate variants) and keep the fastest in
- * ctx for meshes of this size (same power-of-two bucket of quadrature points).
- * Later applications, solves and the server use it. out may be NULL. */
+ * on this mesh (fast and split-coordinate variants; the scalar kernel and the
+ * packed kernel in each of its launch shapes - records per TMA tile 32, 64
+ * or 128, 2 to 8 pipeline stages, 2 or 4 targets per thread - each with the
+ * wave-filling split count x0.5, x1 and x2) and keep the fastest of each
+ * variant in ctx for meshes of this size (same power-of-two bucket of
+ * quadrature points). Later applications, solves and the server use it. out
+ * may be NULL. PB_F32 applications of meshes that take the treecode do not
+ * use the pair kernel, so their timings are all alike there. */
 int pb_autotune(pb_ctx* ctx, const pb_mesh* mesh, const pb_near* near, const pb_params* prm, int form,
                 pb_tune_result* out, void* stream);
 /* Quadrature plan for a molecule: solve it (host arrays, like
- * pb_solvation_energy) with `reference` (NULL = {6, 4}) and with the cheaper
- * far rules {3, 4} and {1, 4}, and return in out_plan the cheapest plan whose
- * Delta G differs from the reference one by at most tol_dG relative (the
- * reference plan when none does); *out_change (optional) = that difference. */
+ * pb_solvation_energy) with `reference` (NULL = {6, 4}) and with cheaper
+ * plans, and return in out_plan the cheapest plan whose Delta G differs from
+ * the reference one by at most tol_dG relative (the reference plan when none
+ * does); *out_change (optional) = that difference. Candidates: first the
+ * 3-point far rule with the reference's rule inside a distance band of 2, 3,
+ * 4 and 6 radii (the first that qualifies is kept), then, one class at a
+ * time (vertex-adjacent, edge-adjacent, coincident pairs), one Gauss point
+ * fewer per dimension of that class's singular rule, each kept if the plan
+ * still qualifies. */
 int pb_autotune_plan(pb_ctx* ctx, const double* verts, int64_t n_verts, const int32_t* tris, int64_t n_tris,
                      const double* xq, const double* q, int64_t n_q, const pb_params* prm,
                      const pb_quad_plan* reference, int form, int precond, const pb_solve_opts* opts, double tol_dG,

@@ -188,15 +188,21 @@ def pb_init(device: int = 0) -> Ctx:
     return Ctx(h.value)
 
 
-def _plan(far_q=6, n_ss=4, band_eta=0.0, band_q=6):
-    return N.pb_quad_plan(int(far_q), int(n_ss), float(band_eta), int(band_q))
+def _plan(far_q=6, n_ss=4, band_eta=0.0, band_q=6, n_ss_coin=0, n_ss_edge=0, n_ss_vert=0):
+    return N.pb_quad_plan(int(far_q), int(n_ss), float(band_eta), int(band_q), int(n_ss_coin), int(n_ss_edge),
+                          int(n_ss_vert))
+
+
+def plan_dict(p) -> dict:
+    """A pb_quad_plan as keyword arguments of pb_mesh_load / pb_submit / pb_solvation_energy."""
+    return {k: getattr(p, k) for k, _ in N.pb_quad_plan._fields_}
 
 
 def pb_mesh_load(ctx: Ctx, verts, tris, far_q: int = 6, n_ss: int = 4, band_eta: float = 0.0,
-                 band_q: int = 6) -> Mesh:
+                 band_q: int = 6, n_ss_coin: int = 0, n_ss_edge: int = 0, n_ss_vert: int = 0) -> Mesh:
     """verts [N_v,3] float64 and tris [N_t,3] int32, numpy (host) or CUDA tensors; the quadrature plan
-    (far rule, singular rule, optional distance band and its rule)."""
-    plan = _plan(far_q, n_ss, band_eta, band_q)
+    (far rule, singular rule and its per-class orders (0: n_ss), optional distance band and its rule)."""
+    plan = _plan(far_q, n_ss, band_eta, band_q, n_ss_coin, n_ss_edge, n_ss_vert)
     if isinstance(verts, torch.Tensor) and verts.is_cuda:
         v = verts.contiguous()
         t = tris.to(torch.int32).contiguous()
@@ -354,7 +360,8 @@ def pb_server_create(ctx: Ctx, hbm_budget_bytes: int, max_active: int = 64) -> S
 
 
 def pb_submit(srv: Server, verts, tris, xq, q, params: Params, form, precond, opts=None, tag: int = 0,
-              far_q: int = 6, n_ss: int = 4, band_eta: float = 0.0, band_q: int = 6):
+              far_q: int = 6, n_ss: int = 4, band_eta: float = 0.0, band_q: int = 6, n_ss_coin: int = 0,
+              n_ss_edge: int = 0, n_ss_vert: int = 0):
     """Queue one molecule (host arrays, copied by the library)."""
     v = np.ascontiguousarray(verts, dtype=np.float64)
     t = np.ascontiguousarray(tris, dtype=np.int32)
@@ -367,7 +374,7 @@ def pb_submit(srv: Server, verts, tris, xq, q, params: Params, form, precond, op
     r.params = params.c()
     r.form, r.precond = _form(form), _prec(precond)
     r.opts = opts if opts is not None else solve_opts()
-    r.plan = _plan(far_q, n_ss, band_eta, band_q)
+    r.plan = _plan(far_q, n_ss, band_eta, band_q, n_ss_coin, n_ss_edge, n_ss_vert)
     r.tag = int(tag)
     _check(N.load().pb_submit(srv.ptr, ctypes.byref(r)))
 
@@ -388,18 +395,20 @@ def pb_poll(srv: Server, max_results: int = 1024):
 
 
 def pb_autotune(ctx: Ctx, mesh: Mesh, near: Near, params: Params, form, stream=None):
-    """Tune the FP32 far-field launch for this mesh size; returns the choice."""
+    """Tune the FP32 far-field launch for this mesh size; returns the choices
+    {"fast": {...}, "accurate": {...}} (kernel, shape, tile records, stages,
+    targets per thread, split scale, best and default ms)."""
     r = N.pb_tune_result()
     p = params.c()
     _check(N.load().pb_autotune(ctx.ptr, mesh.ptr, near.ptr, ctypes.byref(p), _form(form), ctypes.byref(r),
                                 _stream(stream)))
-    return {k: getattr(r, k) for k, _ in N.pb_tune_result._fields_}
+    return {v: {k: getattr(getattr(r, v), k) for k, _ in N.pb_tune_choice._fields_} for v in ("fast", "accurate")}
 
 
 def pb_autotune_plan(ctx: Ctx, verts, tris, xq, q, params: Params, form, precond, tol_dG: float = 1e-6,
                      reference=(6, 4), opts=None, stream=None):
     """Cheapest quadrature plan whose Delta G stays within tol_dG of the reference plan:
-    returns ((far_q, n_ss, band_eta, band_q), relative change)."""
+    returns (plan as a dict of pb_mesh_load's keyword arguments, relative change)."""
     v = np.ascontiguousarray(verts, dtype=np.float64)
     t = np.ascontiguousarray(tris, dtype=np.int32)
     x = np.ascontiguousarray(xq, dtype=np.float64).reshape(-1, 3)
@@ -414,19 +423,20 @@ def pb_autotune_plan(ctx: Ctx, verts, tris, xq, q, params: Params, form, precond
                                      ctypes.c_void_p(qq.ctypes.data), qq.shape[0], ctypes.byref(p), ctypes.byref(ref),
                                      _form(form), _prec(precond), ctypes.byref(o), float(tol_dG), ctypes.byref(out),
                                      ctypes.byref(ch), _stream(stream)))
-    return (out.far_q, out.n_ss, out.band_eta, out.band_q), ch.value
+    return plan_dict(out), ch.value
 
 
 def pb_solvation_energy(ctx: Ctx, verts: np.ndarray, tris: np.ndarray, xq: np.ndarray, q: np.ndarray,
                         params: Params, form, precond, far_q: int = 6, n_ss: int = 4, opts=None, stream=None,
-                        band_eta: float = 0.0, band_q: int = 6):
+                        band_eta: float = 0.0, band_q: int = 6, n_ss_coin: int = 0, n_ss_edge: int = 0,
+                        n_ss_vert: int = 0):
     """Whole path from host arrays; returns (dG kcal/mol, info dict)."""
     v = np.ascontiguousarray(verts, dtype=np.float64)
     t = np.ascontiguousarray(tris, dtype=np.int32)
     x = np.ascontiguousarray(xq, dtype=np.float64).reshape(-1, 3)
     qq = np.ascontiguousarray(q, dtype=np.float64).reshape(-1)
     p = params.c()
-    plan = _plan(far_q, n_ss, band_eta, band_q)
+    plan = _plan(far_q, n_ss, band_eta, band_q, n_ss_coin, n_ss_edge, n_ss_vert)
     o = opts if opts is not None else solve_opts()
     info = N.pb_solve_info()
     out = ctypes.c_double()

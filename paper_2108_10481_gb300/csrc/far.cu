@@ -402,12 +402,12 @@ struct Coef2 {
     float2 kap, mk2;
 };
 
-template <int MODE, bool ACC, int NPK, bool GUARD>
+template <int MODE, bool ACC, int NPK, bool GUARD, int TS>
 __device__ __forceinline__ void tile_x2(const float* __restrict__ tile, const float2 (&X)[NPK][3],
                                         const float2 (&XL)[NPK][3], float2 (&acc)[NPK][MODE == 0 ? 2 : 10],
                                         const Coef2& cf) {
 #pragma unroll 2
-    for (int j = 0; j < TS2; ++j) {
+    for (int j = 0; j < TS; ++j) {
         const float* r = tile + REC2 * j;
         const float4 q0 = *reinterpret_cast<const float4*>(r);
         const float4 q1 = *reinterpret_cast<const float4*>(r + 4);
@@ -466,31 +466,33 @@ __device__ __forceinline__ void tile_x2(const float* __restrict__ tile, const fl
     }
 }
 
-template <int MODE, bool ACC>
+// Templated on its launch shape: source records per TMA tile (TS), pipeline
+// stages (ST) and packed target pairs per thread (NPK); the autotuner picks
+// the shape per mesh-size bucket.
+template <int MODE, bool ACC, int TS, int ST, int NPK>
 __global__ void __launch_bounds__(TPB2) k_pair32x2(const __grid_constant__ CUtensorMap tmap, int64_t np,
                                                    const float* __restrict__ pts32, const float* __restrict__ pts32lo,
                                                    Coef32 c32, int64_t chunk, void* __restrict__ part_out,
                                                    int* __restrict__ status) {
     constexpr int NACC = MODE == 0 ? 2 : 10;
-    constexpr int NPK = ACC ? 1 : 2;   // packed target pairs per thread
     constexpr int TGT = 2 * NPK;
-    __shared__ __align__(128) float sh[ST2][TS2 * REC2];
-    __shared__ __align__(8) uint64_t bar[ST2];
+    __shared__ __align__(128) float sh[ST][TS * REC2];
+    __shared__ __align__(8) uint64_t bar[ST];
     const int split = blockIdx.y;
     const int64_t j0 = split * chunk;
     const int64_t j1 = min(np, j0 + chunk);
-    const int ntiles = (int)((j1 - j0 + TS2 - 1) / TS2);
+    const int ntiles = (int)((j1 - j0 + TS - 1) / TS);
     const int64_t blk0 = blockIdx.x * (int64_t)(TPB2 * TGT), blk1 = blk0 + TPB2 * TGT;
 
     if (threadIdx.x == 0) {
-        for (int s = 0; s < ST2; ++s) mbar_init(&bar[s], 1);
+        for (int s = 0; s < ST; ++s) mbar_init(&bar[s], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
     if (threadIdx.x == 0) {
-        for (int s = 0; s < ST2 && s < ntiles; ++s) {
-            mbar_expect_tx(&bar[s], TS2 * REC2 * sizeof(float));
-            tma_load_2d(sh[s], &tmap, 0, (int)(j0 + (int64_t)s * TS2), &bar[s]);
+        for (int s = 0; s < ST && s < ntiles; ++s) {
+            mbar_expect_tx(&bar[s], TS * REC2 * sizeof(float));
+            tma_load_2d(sh[s], &tmap, 0, (int)(j0 + (int64_t)s * TS), &bar[s]);
         }
     }
     Coef2 cf;
@@ -517,13 +519,13 @@ __global__ void __launch_bounds__(TPB2) k_pair32x2(const __grid_constant__ CUten
         for (int a = 0; a < (ACC ? NACC : 1); ++a) accd[t][a] = 0.0;
     int failed_at = -1;
     for (int it = 0; it < ntiles; ++it) {
-        const int st = it % ST2;
-        const uint32_t phase = (uint32_t)((it / ST2) & 1);
+        const int st = it % ST;
+        const uint32_t phase = (uint32_t)((it / ST) & 1);
         if (!cta_wait(&bar[st], phase, status)) { failed_at = it; break; }
-        const int64_t jt = j0 + (int64_t)it * TS2;
-        const bool guard = (jt < blk1 && jt + TS2 > blk0) || jt + TS2 > np;
-        if (guard) tile_x2<MODE, ACC, NPK, true>(sh[st], X, XL, acc, cf);
-        else tile_x2<MODE, ACC, NPK, false>(sh[st], X, XL, acc, cf);
+        const int64_t jt = j0 + (int64_t)it * TS;
+        const bool guard = (jt < blk1 && jt + TS > blk0) || jt + TS > np;
+        if (guard) tile_x2<MODE, ACC, NPK, true, TS>(sh[st], X, XL, acc, cf);
+        else tile_x2<MODE, ACC, NPK, false, TS>(sh[st], X, XL, acc, cf);
         if (ACC) {
             for (int p = 0; p < NPK; ++p)
                 for (int a = 0; a < NACC; ++a) {
@@ -533,14 +535,14 @@ __global__ void __launch_bounds__(TPB2) k_pair32x2(const __grid_constant__ CUten
                 }
         }
         __syncthreads();  // every thread is done with this stage
-        if (threadIdx.x == 0 && it + ST2 < ntiles) {
+        if (threadIdx.x == 0 && it + ST < ntiles) {
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            mbar_expect_tx(&bar[st], TS2 * REC2 * sizeof(float));
-            tma_load_2d(sh[st], &tmap, 0, (int)(j0 + (int64_t)(it + ST2) * TS2), &bar[st]);
+            mbar_expect_tx(&bar[st], TS * REC2 * sizeof(float));
+            tma_load_2d(sh[st], &tmap, 0, (int)(j0 + (int64_t)(it + ST) * TS), &bar[st]);
         }
     }
     if (failed_at >= 0) {
-        cta_drain(bar, ST2, failed_at, ntiles);
+        cta_drain(bar, ST, failed_at, ntiles);
         return;
     }
     for (int t = 0; t < TGT; ++t) {
@@ -552,6 +554,50 @@ __global__ void __launch_bounds__(TPB2) k_pair32x2(const __grid_constant__ CUten
             else static_cast<float*>(part_out)[o] = h ? acc[p][a].y : acc[p][a].x;
         }
     }
+}
+
+// Launch shapes of the packed kernel, one table per row mode and variant; the
+// autotuner picks one per mesh-size bucket (shape 0: the default).
+// Shapes: (records per tile, stages, packed target pairs per thread).
+typedef void (*X2Launch)(dim3, cudaStream_t, const CUtensorMap&, int64_t, const float*, const float*, Coef32,
+                         int64_t, void*, int*);
+struct X2Entry {
+    int ts, st, npk;
+    const void* fn;
+    X2Launch launch;
+};
+constexpr int X2_SHAPES = 4;
+
+template <int MODE, bool ACC, int TS, int ST, int NPK>
+static void x2_launch(dim3 g, cudaStream_t s, const CUtensorMap& map, int64_t np, const float* p32,
+                      const float* plo, Coef32 cf, int64_t chunk, void* part, int* status) {
+    k_pair32x2<MODE, ACC, TS, ST, NPK><<<g, TPB2, 0, s>>>(map, np, p32, plo, cf, chunk, part, status);
+}
+template <int MODE, bool ACC, int TS, int ST, int NPK>
+static X2Entry x2_entry() {
+    return {TS, ST, NPK, (const void*)k_pair32x2<MODE, ACC, TS, ST, NPK>, x2_launch<MODE, ACC, TS, ST, NPK>};
+}
+template <int MODE>
+static void x2_row(X2Entry (&fast)[X2_SHAPES], X2Entry (&acc)[X2_SHAPES]) {
+    fast[0] = x2_entry<MODE, false, 64, 4, 2>();
+    fast[1] = x2_entry<MODE, false, 32, 4, 2>();
+    fast[2] = x2_entry<MODE, false, 128, 2, 2>();
+    fast[3] = x2_entry<MODE, false, 64, 4, 1>();
+    acc[0] = x2_entry<MODE, true, 64, 4, 1>();
+    acc[1] = x2_entry<MODE, true, 32, 4, 1>();
+    acc[2] = x2_entry<MODE, true, 128, 2, 1>();
+    acc[3] = x2_entry<MODE, true, 32, 8, 1>();
+}
+static const X2Entry& x2_kernel(int mode, bool acc, int shape) {
+    struct Table {
+        X2Entry e[2][2][X2_SHAPES];
+        Table() {
+            x2_row<0>(e[0][0], e[0][1]);
+            x2_row<1>(e[1][0], e[1][1]);
+        }
+    };
+    static const Table t;
+    return t.e[mode ? 1 : 0][acc ? 1 : 0][(shape >= 0 && shape < X2_SHAPES) ? shape : 0];
 }
 
 // ------------------------- batched FP32 pair kernel: many meshes in one launch
@@ -643,8 +689,8 @@ __global__ void __launch_bounds__(TPB2) k_pair32x2_multi(const PairJob* __restri
         if (!cta_wait(&bar[st], phase, status)) { failed_at = it; break; }
         const int64_t jt = j0 + (int64_t)it * TS2;
         const bool guard = (jt < blk1 && jt + TS2 > blk0) || jt + TS2 > np;
-        if (guard) tile_x2<MODE, ACC, NPK, true>(sh[st], X, XL, acc, cf);
-        else tile_x2<MODE, ACC, NPK, false>(sh[st], X, XL, acc, cf);
+        if (guard) tile_x2<MODE, ACC, NPK, true, TS2>(sh[st], X, XL, acc, cf);
+        else tile_x2<MODE, ACC, NPK, false, TS2>(sh[st], X, XL, acc, cf);
         if (ACC) {
             for (int p = 0; p < NPK; ++p)
                 for (int a = 0; a < NACC; ++a) {
@@ -963,15 +1009,15 @@ int apply_blockop(const pb_mesh* m, const pb_near* nf, const BlockOp& B, int pre
             k_sources2<float><<<tb, 128, 0, s>>>(nt, m->Q, rule, m->tris, m->tgeo, m->pts64, m->pts32, m->pts32lo, x,
                                                  x + nv, need_u, need_v, rec);
             ::pb::count_launch();
-            CUtensorMap map;
-            PB_TRY(make_tmap(m, rec, &map, REC2, TS2));
             bool acc = prec == PB_F32_ACCURATE;
-            const int tpc = TPB2 * (acc ? 2 : 4);
-            const void* kern = fp.mode == 0 ? (acc ? (const void*)k_pair32x2<0, true> : (const void*)k_pair32x2<0, false>)
-                                            : (acc ? (const void*)k_pair32x2<1, true> : (const void*)k_pair32x2<1, false>);
-            int S = choose_splits(np, tpc, TS2, occupancy_slots(m, kern, TPB2));
-            S = scaled_splits(S, tuned(m->ctx, np, fp.mode, acc).split_scale, np, TS2);
-            int64_t chunk = ((np + S - 1) / S + TS2 - 1) / TS2 * TS2;
+            const TuneEntry te = tuned(m->ctx, np, fp.mode, acc);
+            const X2Entry& xk = x2_kernel(fp.mode, acc, te.shape);
+            CUtensorMap map;
+            PB_TRY(make_tmap(m, rec, &map, REC2, xk.ts));
+            const int tpc = TPB2 * 2 * xk.npk;
+            int S = choose_splits(np, tpc, xk.ts, occupancy_slots(m, xk.fn, TPB2));
+            S = scaled_splits(S, te.split_scale, np, xk.ts);
+            int64_t chunk = ((np + S - 1) / S + xk.ts - 1) / xk.ts * xk.ts;
             S = (int)((np + chunk - 1) / chunk);
             Coef32 cf;
             for (int R = 0; R < 2; ++R)
@@ -983,13 +1029,7 @@ int apply_blockop(const pb_mesh* m, const pb_near* nf, const BlockOp& B, int pre
             void* part = m->ws_part.ptr;
             double ops = (fp.mode == 0 ? OPS_VK2 : OPS_VKDT) + (acc ? OPS_SPLIT : 0.0);
             Timer tm(m->ctx, acc ? PB_KERNEL_PAIR32_ACCURATE : PB_KERNEL_PAIR32, s, (double)np * (double)np, ops);
-            if (fp.mode == 0) {
-                if (acc) k_pair32x2<0, true><<<grid, TPB2, 0, s>>>(map, np, m->pts32, m->pts32lo, cf, chunk, part, status);
-                else k_pair32x2<0, false><<<grid, TPB2, 0, s>>>(map, np, m->pts32, m->pts32lo, cf, chunk, part, status);
-            } else {
-                if (acc) k_pair32x2<1, true><<<grid, TPB2, 0, s>>>(map, np, m->pts32, m->pts32lo, cf, chunk, part, status);
-                else k_pair32x2<1, false><<<grid, TPB2, 0, s>>>(map, np, m->pts32, m->pts32lo, cf, chunk, part, status);
-            }
+            xk.launch(grid, s, map, np, m->pts32, m->pts32lo, cf, chunk, part, status);
             ::pb::count_launch();
             tm.stop();
             if (acc)
@@ -1106,8 +1146,7 @@ int apply_blockops_batched(const std::vector<FarJob>& jobs, int prec, BatchScrat
         ::pb::count_launch();
         if (np_pad > np) PB_CUDA(cudaMemsetAsync(rec + REC2 * np, 0, sizeof(float) * REC2 * (np_pad - np), s));
         // the single-mesh decomposition (same kernel occupancy as that path)
-        const void* kern = P.fp.mode == 0 ? (acc ? (const void*)k_pair32x2<0, true> : (const void*)k_pair32x2<0, false>)
-                                          : (acc ? (const void*)k_pair32x2<1, true> : (const void*)k_pair32x2<1, false>);
+        const void* kern = x2_kernel(P.fp.mode, acc, 0).fn;  // the default shape's occupancy (the batched kernel's)
         int S = choose_splits(np, tpc, TS2, occupancy_slots(m, kern, TPB2));
         S = scaled_splits(S, tuned(m->ctx, np, P.fp.mode, acc).split_scale, np, TS2);
         P.chunk = ((np + S - 1) / S + TS2 - 1) / TS2 * TS2;
@@ -1192,7 +1231,7 @@ int apply_blockops_batched(const std::vector<FarJob>& jobs, int prec, BatchScrat
 
 int far_splits_estimate(pb_ctx* ctx, int64_t np) {
     int best = 1;
-    const void* kerns[2] = {(const void*)k_pair32x2<1, true>, (const void*)k_pair32x2<1, false>};
+    const void* kerns[2] = {x2_kernel(1, true, 0).fn, x2_kernel(1, false, 0).fn};
     const int tpcs[2] = {TPB2 * 2, TPB2 * 4};
     for (int k = 0; k < 2; ++k) {
         int per_sm = 1;
@@ -1326,11 +1365,13 @@ extern "C" int pb_system_apply_noalloc(pb_ctx* ctx, const pb_mesh* m, const pb_n
 
 // ------------------------------------------------------------------ a12: autotuner
 // Times the FP32 far-field application of one formulation on the caller's
-// mesh for every candidate launch (scalar or packed kernel; split count x0.5,
-// x1, x2 of the wave-filling choice; both the fast and the split-coordinate
-// variant), keeps the fastest per variant in the context's table for this
-// size bucket, and reports the gain. Results of the tuned launches are the
-// same sums in another split order (FP32 rounding differences only).
+// mesh for every candidate launch (the scalar kernel, or the packed kernel in
+// each of its launch shapes - records per TMA tile, pipeline stages, targets
+// per thread; split count x0.5, x1, x2 of the wave-filling choice; both the
+// fast and the split-coordinate variant), keeps the fastest per variant in the
+// context's table for this size bucket, and reports the gain. Results of the
+// tuned launches are the same sums in another split and tile order (FP32
+// rounding differences only).
 extern "C" int pb_autotune(pb_ctx* ctx, const pb_mesh* m, const pb_near* nf, const pb_params* prm, int form,
                            pb_tune_result* out, void* stream) {
     using namespace pb;
@@ -1347,7 +1388,10 @@ extern "C" int pb_autotune(pb_ctx* ctx, const pb_mesh* m, const pb_near* nf, con
     for (int64_t i = 0; i < n2; ++i) hx[i] = std::sin(0.37 * (double)i) + 0.5;
     cudaMemcpy(xy, hx.data(), sizeof(double) * n2, cudaMemcpyHostToDevice);
     const int bucket = tune_bucket(m->np);
-    const int kernels[2] = {2, 1};
+    // candidates: (kernel, shape): the packed kernel in every shape, then the scalar kernel
+    std::vector<std::pair<int, int>> cands;
+    for (int sh = 0; sh < X2_SHAPES; ++sh) cands.push_back({2, sh});
+    cands.push_back({1, 0});
     const double scales[3] = {1.0, 0.5, 2.0};
     cudaEvent_t e0, e1;
     cudaEventCreate(&e0);
@@ -1359,32 +1403,44 @@ extern "C" int pb_autotune(pb_ctx* ctx, const pb_mesh* m, const pb_near* nf, con
         const TuneEntry saved = slot;
         double best = 1e300, dflt = 0.0;
         TuneEntry best_e;
-        for (int k : kernels)
+        for (const auto& kc : cands)
             for (double sc : scales) {
+                const int k = kc.first;
                 slot.kernel = k;
+                slot.shape = kc.second;
                 slot.split_scale = sc;
+                cudaEventRecord(e0, s);
                 rc = apply_blockop(m, nf, B, prec, xy, xy + n2, s);  // warm-up and workspace growth
                 if (rc != PB_OK) break;
+                cudaEventRecord(e1, s);
+                cudaEventSynchronize(e1);
                 float ms_total = 0.0f;
-                const int reps = 3;
+                cudaEventElapsedTime(&ms_total, e0, e1);
+                const int reps = ms_total > 50.0f ? 1 : 3;  // long launches: one timed run each
                 cudaEventRecord(e0, s);
                 for (int r = 0; r < reps && rc == PB_OK; ++r) rc = apply_blockop(m, nf, B, prec, xy, xy + n2, s);
                 cudaEventRecord(e1, s);
                 cudaEventSynchronize(e1);
                 cudaEventElapsedTime(&ms_total, e0, e1);
                 const double ms = ms_total / reps;
-                if (k == 2 && sc == 1.0) dflt = ms;
+                if (k == 2 && kc.second == 0 && sc == 1.0) dflt = ms;
                 if (ms < best) {
                     best = ms;
                     best_e = slot;
                 }
             }
         slot = rc == PB_OK ? best_e : saved;
-        if (out && !acc) {
-            out->kernel = best_e.kernel;
-            out->split_scale = best_e.split_scale;
-            out->best_ms = best;
-            out->default_ms = dflt;
+        if (out) {
+            pb_tune_choice& o = acc ? out->accurate : out->fast;
+            o.kernel = best_e.kernel;
+            o.shape = best_e.shape;
+            const X2Entry& xk = x2_kernel(fp.mode, acc != 0, best_e.shape);
+            o.tile_records = best_e.kernel == 2 ? xk.ts : (int)TS32;
+            o.stages = best_e.kernel == 2 ? xk.st : (int)ST32;
+            o.targets_per_thread = best_e.kernel == 2 ? 2 * xk.npk : (int)TGT32;
+            o.split_scale = best_e.split_scale;
+            o.best_ms = best;
+            o.default_ms = dflt;
         }
     }
     cudaEventDestroy(e0);

@@ -119,6 +119,7 @@ namespace pb {
 struct TuneEntry {
     int kernel = 0;          // 0 = not tuned, 1 = scalar, 2 = packed f32x2
     double split_scale = 1;  // multiplier of the wave-filling split count
+    int shape = 0;           // launch shape of the packed kernel (tile records, stages, targets per thread)
 };
 constexpr int TUNE_BUCKETS = 40;
 struct PbTree;  // treecode of a mesh (tree.cu)
@@ -145,6 +146,7 @@ struct pb_mesh {
     pb_ctx* ctx = nullptr;
     int64_t nv = 0, nt = 0, np = 0;
     int Q = 0, n_ss = 0;
+    int n_ss_cls[3] = {0, 0, 0};  // singular Gauss points per dimension: coincident, edge, vertex pairs
     double rule_l[6][3];
     double rule_w[6];
     // distance band of the plan, and its reference rule (right-hand side and

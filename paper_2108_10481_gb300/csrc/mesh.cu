@@ -388,6 +388,12 @@ static int load(pb_ctx* ctx, const double* verts_in, int64_t nv, const int32_t* 
     const int bq = plan && plan->band_q ? plan->band_q : 6;
     if (Q != 1 && Q != 3 && Q != 6) return set_error(PB_EINVAL, "far_q must be 1, 3 or 6 (got %d)", Q);
     if (nss < 1 || nss > 12) return set_error(PB_EINVAL, "n_ss must be in 1..12 (got %d)", nss);
+    int ncls[3] = {plan ? plan->n_ss_coin : 0, plan ? plan->n_ss_edge : 0, plan ? plan->n_ss_vert : 0};
+    for (int c = 0; c < 3; ++c) {
+        if (ncls[c] == 0) ncls[c] = nss;
+        if (ncls[c] < 1 || ncls[c] > 12)
+            return set_error(PB_EINVAL, "per-class singular orders must be 0 or in 1..12 (got %d)", ncls[c]);
+    }
     if (!(eta >= 0.0) || !(eta <= 64.0)) return set_error(PB_EINVAL, "band_eta must be in [0, 64] (got %g)", eta);
     if (eta > 0.0 && ((bq != 3 && bq != 6) || bq <= Q))
         return set_error(PB_EINVAL, "band_q must be 3 or 6 and finer than far_q (got %d, far_q %d)", bq, Q);
@@ -396,6 +402,7 @@ static int load(pb_ctx* ctx, const double* verts_in, int64_t nv, const int32_t* 
     m->nt = nt;
     m->Q = Q;
     m->n_ss = nss;
+    for (int c = 0; c < 3; ++c) m->n_ss_cls[c] = ncls[c];
     m->np = nt * Q;
     m->band_eta = eta;
     m->Qr = eta > 0.0 ? bq : Q;
@@ -587,7 +594,10 @@ static int load(pb_ctx* ctx, const double* verts_in, int64_t nv, const int32_t* 
     m->n_adj = n_adj;
     std::vector<int32_t> rev(n_adj), coin_list, prim_list;
     std::atomic<bool> rev_ok{true};
-    std::vector<std::vector<int32_t>> chunk_coin(MAX_HOST_THREADS), chunk_prim(MAX_HOST_THREADS);
+    // primary pairs: the edge-adjacent ones first, then the vertex-adjacent ones (each class
+    // is integrated by its own launch with its own rule)
+    std::vector<std::vector<int32_t>> chunk_coin(MAX_HOST_THREADS), chunk_prim(MAX_HOST_THREADS),
+        chunk_primv(MAX_HOST_THREADS);
     std::vector<int64_t> chunk_edge(MAX_HOST_THREADS, 0);
     const int nrc = parallel_chunks(n_adj, [&](int c, int64_t b0, int64_t b1) {
         for (int64_t p = b0; p < b1; ++p) {
@@ -603,8 +613,12 @@ static int load(pb_ctx* ctx, const double* verts_in, int64_t nv, const int32_t* 
             if (t == u) {
                 chunk_coin[c].push_back((int32_t)p);
             } else if (t < u) {
-                chunk_prim[c].push_back((int32_t)p);
-                chunk_edge[c] += pairs[p].z == 1;
+                if (pairs[p].z == 1) {
+                    chunk_prim[c].push_back((int32_t)p);
+                    chunk_edge[c] += 1;
+                } else {
+                    chunk_primv[c].push_back((int32_t)p);
+                }
             }
         }
     });
@@ -614,6 +628,7 @@ static int load(pb_ctx* ctx, const double* verts_in, int64_t nv, const int32_t* 
         prim_list.insert(prim_list.end(), chunk_prim[c].begin(), chunk_prim[c].end());
         m->n_prim_edge += chunk_edge[c];
     }
+    for (int c = 0; c < nrc; ++c) prim_list.insert(prim_list.end(), chunk_primv[c].begin(), chunk_primv[c].end());
 
     tr.lap("reverse");
     size_t tot = 0;

@@ -106,12 +106,11 @@ __device__ __forceinline__ double ss_map(int kind, int reg, double xi, double e1
     return jac;
 }
 
-// The regularised rule does not depend on the pair: every (region, Gauss
-// index) point of each kind, its reference points in both triangles and its
-// weight (Gauss weights times the region Jacobian, multiplied in the order the
-// pair kernels used to), computed once per build. Structure of arrays over
-// the entries of kind 1 (edge, 6 regions), kind 2 (vertex, 2) and kind 0
-// (coincident, regions 0..2), in that order.
+// The regularised rule of the coincident pairs does not depend on the pair:
+// every (region, Gauss index) point of regions 0..2 of the coincident map, its
+// reference points in both copies of the triangle and its weight (Gauss
+// weights times the region Jacobian), computed once per build. Structure of
+// arrays over the entries.
 struct SSTable {
     const double* sx;
     const double* tx;
@@ -121,8 +120,7 @@ struct SSTable {
     // w times the monomials (s', t', s, s s', s t', t, t s', t t') of the
     // entry's frame coordinates: mono[c * n + e]
     const double* mono;
-    int off[3];  // first entry of kind 0, 1, 2
-    int n;       // entries in all
+    int n;       // entries in all (3 n^4)
 };
 constexpr int SS_TABLE_ARRAYS = 13;  // sx, tx, sy, ty, w and the eight weighted monomials
 
@@ -130,15 +128,10 @@ __global__ void k_ss_table(Gauss gq, int n, double* __restrict__ tab) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n) return;
     const int q = gq.n, n4 = q * q * q * q;
-    // kind 1: entries [0, 6 n4); kind 2: [6 n4, 8 n4); kind 0: [8 n4, 11 n4)
-    int kind, idx;
-    if (e < 6 * n4) { kind = 1; idx = e; }
-    else if (e < 8 * n4) { kind = 2; idx = e - 6 * n4; }
-    else { kind = 0; idx = e - 8 * n4; }
-    const int reg = idx / n4, r = idx - reg * n4;
+    const int reg = e / n4, r = e - reg * n4;
     const int i0 = r / (q * q * q), i1 = (r / (q * q)) % q, i2 = (r / q) % q, i3 = r % q;
     double sx, tx, sy, ty;
-    const double jac = ss_map(kind, reg, gq.x[i0], gq.x[i1], gq.x[i2], gq.x[i3], sx, tx, sy, ty);
+    const double jac = ss_map(0, reg, gq.x[i0], gq.x[i1], gq.x[i2], gq.x[i3], sx, tx, sy, ty);
     tab[e] = sx;
     tab[n + e] = tx;
     tab[2 * n + e] = sy;
@@ -165,25 +158,23 @@ __global__ void k_ss_table(Gauss gq, int n, double* __restrict__ tab) {
 //   15..19 the eta3-slope coefficients of the moments that change with eta3:
 //         (0,2) W tb', (1,2) W sa tb', (2,0) W tb, (2,1) W tb sa', (2,2) W (ta tb' + tb ta')
 // followed by the eta3 Gauss nodes and weights (2 n doubles).
+// One table per class (edge or vertex), each with its own Gauss rule.
 struct SSOuter {
     const double* v;
-    int n;        // entries
-    int off[3];   // first entry of kind 1 and 2 (kind 0 unused)
+    int n;        // entries (regions x nss^3)
     int nss;      // Gauss points per dimension
+    int nreg;     // regions of the map: 6 (edge) or 2 (vertex)
 };
 constexpr int SS_OUTER_ARRAYS = 20;
 
-__global__ void k_ss_outer(Gauss gq, int n, double* __restrict__ tab) {
+__global__ void k_ss_outer(Gauss gq, int kind, int n, double* __restrict__ tab) {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     const int q = gq.n, n3 = q * q * q;
     if (e < 2 * q) {  // the eta3 rule after the entries
         tab[SS_OUTER_ARRAYS * n + e] = e < q ? gq.x[e] : gq.w[e - q];
     }
     if (e >= n) return;
-    int kind, idx;
-    if (e < 6 * n3) { kind = 1; idx = e; }
-    else { kind = 2; idx = e - 6 * n3; }
-    const int reg = idx / n3, r = idx - reg * n3;
+    const int reg = e / n3, r = e - reg * n3;
     const int i0 = r / (q * q), i1 = (r / q) % q, i2 = r % q;
     double sx0, tx0, sy0, ty0, sx1, tx1, sy1, ty1;
     const double jac = ss_map(kind, reg, gq.x[i0], gq.x[i1], gq.x[i2], 0.0, sx0, tx0, sy0, ty0);
@@ -562,9 +553,8 @@ k_near_pairs(const double* __restrict__ verts, const int32_t* __restrict__ tris,
     if (lane == 0) make_frame(verts, tris, tgeo, pr.x, pr.w & 63, A);
     if (lane == 1) make_frame(verts, tris, tgeo, pr.y, (pr.w >> 6) & 63, B);
     __syncwarp();
-    const int kind = pr.z;
-    const int nreg = kind == 2 ? 2 : 6;
-    const int e0 = tab.off[kind];
+    const int nreg = tab.nreg;  // every pair of the list has the table's class
+    const int e0 = 0;
     const int n3 = tab.nss * tab.nss * tab.nss;
     const double jac_ab = (2.0 * A.area) * (2.0 * B.area);
     const double dq[3] = {A.q0[0] - B.q0[0], A.q0[1] - B.q0[1], A.q0[2] - B.q0[2]};  // 0: the shared vertex
@@ -601,7 +591,6 @@ k_near_pairs(const double* __restrict__ verts, const int32_t* __restrict__ tris,
     const int Q = rule.Q;
     for (int idx = lane; idx < Q * Q; idx += 32) {
         const int i = idx / Q, j = idx % Q;
-        if (kind == 0 && i == j) continue;  // identical points are skipped by the pair kernel
         double x[3], y[3];
         for (int k = 0; k < 3; ++k) {
             x[k] = rule.l[i][0] * corner(A, 0, k) + rule.l[i][1] * corner(A, 1, k) + rule.l[i][2] * corner(A, 2, k);
@@ -673,7 +662,7 @@ k_coin_pairs(const double* __restrict__ verts, const int32_t* __restrict__ tris,
     TriFrame& A = frames[wid];
     if (lane == 0) make_frame(verts, tris, tgeo, pr.x, pr.w & 63, A);
     __syncwarp();
-    const int e0 = tab.off[0];
+    const int e0 = 0;
     const double jac_ab = (2.0 * A.area) * (2.0 * A.area);
     double acc[20];
     {
@@ -1003,39 +992,36 @@ static int build(pb_ctx* ctx, const pb_mesh* m, double kappa, pb_near* nf, cudaS
     int rc = dev_alloc((void**)&ss, sizeof(double) * 54 * m->npairs);
     if (rc == PB_OK) rc = dev_alloc((void**)&far, sizeof(double) * 54 * m->n_adj);
     if (rc == PB_OK) {
-        Gauss gq = gauss01(m->n_ss);
-        const int n4i = m->n_ss * m->n_ss * m->n_ss * m->n_ss, ntab = 11 * n4i;
+        // coincident pairs: the table of their regularised rule
+        const int nc = m->n_ss_cls[0], ne = m->n_ss_cls[1], nvx = m->n_ss_cls[2];
+        const Gauss gq = gauss01(nc);
+        const int n4i = nc * nc * nc * nc, ntab = 3 * n4i;
+        // edge and vertex pairs: the outer entries of their maps, each with its own rule
+        const int nout_e = 6 * ne * ne * ne, nout_v = 2 * nvx * nvx * nvx;
+        const size_t bt = sizeof(double) * SS_TABLE_ARRAYS * ntab;
+        const size_t be = sizeof(double) * ((size_t)SS_OUTER_ARRAYS * nout_e + 2 * ne);
+        const size_t bv = sizeof(double) * ((size_t)SS_OUTER_ARRAYS * nout_v + 2 * nvx);
         double* tabm = nullptr;
-        rc = dev_alloc((void**)&tabm, sizeof(double) * SS_TABLE_ARRAYS * ntab);
+        rc = dev_alloc((void**)&tabm, bt + be + bv);
         if (rc != PB_OK) {
             cudaFree(ss);
             cudaFree(far);
             return rc;
         }
+        double* tabe = tabm + bt / sizeof(double);
+        double* tabv = tabe + be / sizeof(double);
         k_ss_table<<<(ntab + 127) / 128, 128, 0, s>>>(gq, ntab, tabm);
-        ::pb::count_launch();
-        SSTable tab = {tabm, tabm + ntab, tabm + 2 * ntab, tabm + 3 * ntab, tabm + 4 * ntab, tabm + 5 * ntab,
-                       {8 * n4i, 0, 6 * n4i}, ntab};
-        // the outer entries of the edge and vertex maps (factorised adjacent-pair sums)
-        const int n3i = m->n_ss * m->n_ss * m->n_ss, nout = 8 * n3i;
-        double* tabo = nullptr;
-        rc = dev_alloc((void**)&tabo, sizeof(double) * ((size_t)SS_OUTER_ARRAYS * nout + 2 * m->n_ss));
-        if (rc != PB_OK) {
-            cudaFree(tabm);
-            cudaFree(ss);
-            cudaFree(far);
-            return rc;
-        }
-        k_ss_outer<<<(std::max(nout, 2 * m->n_ss) + 127) / 128, 128, 0, s>>>(gq, nout, tabo);
-        ::pb::count_launch();
-        SSOuter outer = {tabo, nout, {0, 0, 6 * n3i}, m->n_ss};
+        k_ss_outer<<<(std::max(nout_e, 2 * ne) + 127) / 128, 128, 0, s>>>(gauss01(ne), 1, nout_e, tabe);
+        k_ss_outer<<<(std::max(nout_v, 2 * nvx) + 127) / 128, 128, 0, s>>>(gauss01(nvx), 2, nout_v, tabv);
+        ::pb::count_launch(3);
+        SSTable tab = {tabm, tabm + ntab, tabm + 2 * ntab, tabm + 3 * ntab, tabm + 4 * ntab, tabm + 5 * ntab, ntab};
+        const SSOuter outer_e = {tabe, nout_e, ne, 6}, outer_v = {tabv, nout_v, nvx, 2};
         int threads = NEAR_THREADS;  // one warp per pair
         // coincident pairs, then one of each pair of reversed pairs (which also writes the other)
         unsigned bc = (unsigned)((m->n_coin * 32 + threads - 1) / threads);
-        unsigned bp = (unsigned)((m->n_prim * 32 + threads - 1) / threads);
         // quadrature point pairs of each kernel, for the profile (formula flop counts per pair in
         // NEAR_FLOPS_*: kernel evaluation and accumulation, a fused multiply-add counted as two)
-        const double n4 = (double)m->n_ss * m->n_ss * m->n_ss * m->n_ss, Q = m->Q, Qb = m->Qr;
+        const double n4 = (double)n4i, Q = m->Q, Qb = m->Qr;
         if (bc) {
             Timer tm(ctx, PB_KERNEL_NEAR_COIN, s, m->n_coin * (3.0 * n4 + Q * (Q - 1) / 2), NEAR_FLOPS_COIN);
             k_coin_pairs<<<bc, threads, 0, s>>>(m->verts, m->tris, m->tgeo, m->pairs, m->pair_coin, m->n_coin, tab,
@@ -1043,20 +1029,25 @@ static int build(pb_ctx* ctx, const pb_mesh* m, double kappa, pb_near* nf, cudaS
             tm.stop();
         }
         ::pb::count_launch();
-        if (bp) {
-            const double outer_pts = (m->n_prim_edge * 6.0 + (m->n_prim - m->n_prim_edge) * 2.0) * n3i;
-            const double reg = outer_pts * m->n_ss, farp = m->n_prim * Q * Q;
+        // edge-adjacent pairs (the first n_prim_edge of the primary list), then vertex-adjacent ones
+        for (int cls = 0; cls < 2; ++cls) {
+            const int64_t nlist = cls == 0 ? m->n_prim_edge : m->n_prim - m->n_prim_edge;
+            if (nlist == 0) continue;
+            const int32_t* list = m->pair_prim + (cls == 0 ? 0 : m->n_prim_edge);
+            const SSOuter& ot = cls == 0 ? outer_e : outer_v;
+            const unsigned bp = (unsigned)((nlist * 32 + threads - 1) / threads);
+            const double outer_pts = (double)nlist * ot.n;
+            const double reg = outer_pts * ot.nss, farp = (double)nlist * Q * Q;
             const double flops = reg * NEAR_FLOPS_ADJ_POINT + outer_pts * NEAR_FLOPS_ADJ_OUTER + farp * NEAR_FLOPS_SYM;
             Timer tm(ctx, PB_KERNEL_NEAR_ADJ, s, reg + farp, flops / (reg + farp));
-#define PB_NEAR_ARGS m->verts, m->tris, m->tgeo, m->pairs, m->pair_prim, m->n_prim, m->pair_rev, outer, mesh_rule(m), \
-                     kappa, ss, far
-            if (m->n_ss == 4) k_near_pairs<2, true, 4><<<bp, threads, 0, s>>>(PB_NEAR_ARGS);
-            else if (m->n_ss == 3) k_near_pairs<2, true, 3><<<bp, threads, 0, s>>>(PB_NEAR_ARGS);
+#define PB_NEAR_ARGS m->verts, m->tris, m->tgeo, m->pairs, list, nlist, m->pair_rev, ot, mesh_rule(m), kappa, ss, far
+            if (ot.nss == 4) k_near_pairs<2, true, 4><<<bp, threads, 0, s>>>(PB_NEAR_ARGS);
+            else if (ot.nss == 3) k_near_pairs<2, true, 3><<<bp, threads, 0, s>>>(PB_NEAR_ARGS);
             else k_near_pairs<2, true, 0><<<bp, threads, 0, s>>>(PB_NEAR_ARGS);
 #undef PB_NEAR_ARGS
+            ::pb::count_launch();
             tm.stop();
         }
-        ::pb::count_launch();
         if (m->n_band) {
             Rule fine = mesh_ref_rule(m), coarse = mesh_rule(m);
             const double ppairs = 0.5 * m->n_band * (Qb * Qb + Q * Q);
@@ -1117,7 +1108,6 @@ static int build(pb_ctx* ctx, const pb_mesh* m, double kappa, pb_near* nf, cudaS
         if (e != cudaSuccess) rc = set_error(PB_ECUDA, "near build: %s", cudaGetErrorString(e));
         else if (st == PB_EMESH) rc = set_error(PB_EMESH, "internal: band pair without reverse");
         cudaFree(tabm);
-        cudaFree(tabo);
     }
     if (ss) cudaFree(ss);
     if (far) cudaFree(far);

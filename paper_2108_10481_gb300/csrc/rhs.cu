@@ -220,33 +220,65 @@ extern "C" int pb_solvation_energy(pb_ctx* ctx, const double* verts, int64_t n_v
 // reference plan's by at most tol_dG relative. Candidates, cheapest first: the
 // 3-point far rule with the reference's rule inside a distance band of
 // 2, 3, 4 and 6 radii (the far-field work is a quarter of the 6-point rule's;
-// the band's near-field work grows with its width). The reference plan itself
-// when none qualifies.
+// the band's near-field work grows with its width); then one Gauss point fewer
+// per dimension in the singular rule of one class of pair at a time
+// (vertex-adjacent, edge-adjacent, coincident: the classes in order of their
+// share of the near-field work on a closed surface), each kept while the plan
+// still qualifies. The reference plan itself when nothing qualifies. The
+// returned plan names its three singular orders explicitly.
 extern "C" int pb_autotune_plan(pb_ctx* ctx, const double* verts, int64_t n_verts, const int32_t* tris,
                                 int64_t n_tris, const double* xq, const double* q, int64_t n_q, const pb_params* prm,
                                 const pb_quad_plan* reference, int form, int precond, const pb_solve_opts* opts,
                                 double tol_dG, pb_quad_plan* out_plan, double* out_change, void* stream) {
     if (!ctx || !verts || !tris || !xq || !q || !prm || !out_plan || !(tol_dG >= 0.0))
         return set_error(PB_EINVAL, "pb_autotune_plan: bad argument");
-    pb_quad_plan ref = reference ? *reference : pb_quad_plan{6, 4, 0.0, 6};
+    pb_quad_plan ref = reference ? *reference : pb_quad_plan{6, 4, 0.0, 6, 0, 0, 0};
+    int* cls[3] = {&ref.n_ss_coin, &ref.n_ss_edge, &ref.n_ss_vert};
+    for (int c = 0; c < 3; ++c)
+        if (*cls[c] == 0) *cls[c] = ref.n_ss;
     double dref = 0.0;
     PB_TRY(pb_solvation_energy(ctx, verts, n_verts, tris, n_tris, xq, q, n_q, prm, &ref, form, precond, opts, &dref,
                                nullptr, stream));
-    *out_plan = ref;
-    if (out_change) *out_change = 0.0;
-    if (ref.far_q <= 3 || ref.band_eta > 0.0) return PB_OK;  // nothing cheaper to offer
-    const double etas[4] = {2.0, 3.0, 4.0, 6.0};
-    for (double eta : etas) {
-        pb_quad_plan p = {3, ref.n_ss, eta, ref.far_q};
+    pb_quad_plan best = ref;
+    double best_change = 0.0;
+    auto change_of = [&](const pb_quad_plan& p, double* change) -> int {
         double d = 0.0;
         PB_TRY(pb_solvation_energy(ctx, verts, n_verts, tris, n_tris, xq, q, n_q, prm, &p, form, precond, opts, &d,
                                    nullptr, stream));
-        const double change = std::fabs(d / dref - 1.0);
-        if (change <= tol_dG) {
-            *out_plan = p;
-            if (out_change) *out_change = change;
-            break;
+        *change = std::fabs(d / dref - 1.0);
+        return PB_OK;
+    };
+    if (ref.far_q > 3 && ref.band_eta == 0.0) {
+        const double etas[4] = {2.0, 3.0, 4.0, 6.0};
+        for (double eta : etas) {
+            pb_quad_plan p = ref;
+            p.far_q = 3;
+            p.band_eta = eta;
+            p.band_q = ref.far_q;
+            double change = 0.0;
+            PB_TRY(change_of(p, &change));
+            if (change <= tol_dG) {
+                best = p;
+                best_change = change;
+                break;
+            }
         }
     }
+    // vertex, edge, coincident
+    int* bcls[3] = {&best.n_ss_vert, &best.n_ss_edge, &best.n_ss_coin};
+    for (int c = 0; c < 3; ++c) {
+        if (*bcls[c] <= 1) continue;
+        pb_quad_plan p = best;
+        int* pc = c == 0 ? &p.n_ss_vert : c == 1 ? &p.n_ss_edge : &p.n_ss_coin;
+        *pc -= 1;
+        double change = 0.0;
+        PB_TRY(change_of(p, &change));
+        if (change <= tol_dG) {
+            best = p;
+            best_change = change;
+        }
+    }
+    *out_plan = best;
+    if (out_change) *out_change = best_change;
     return PB_OK;
 }

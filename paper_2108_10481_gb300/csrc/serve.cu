@@ -360,7 +360,7 @@ static int tick(pb_server* srv) {
                 r->phase = PH_ENERGY;
                 continue;
             }
-            r->inner_tol = r->mixed ? std::min(0.5, std::max(r->opts.inner_tol, 0.5 * tol / r->rel)) : tol;
+            r->inner_tol = r->mixed ? std::min(0.5, std::max(r->opts.inner_tol, INNER_AIM * tol / r->rel)) : tol;
             PB_TRY(gm_begin(r->G, r->w, srv->res_dev + 4 * r->slot, s));
             if (r->mixed) PB_CUDA(cudaMemsetAsync(r->dd, 0, sizeof(double) * 2 * r->m->nv, s));
             r->j = 0;

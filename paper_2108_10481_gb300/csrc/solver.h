@@ -5,6 +5,14 @@
 
 namespace pb {
 
+// Mixed-precision refinement: an inner solve asks for max(inner_tol,
+// INNER_AIM x tol / rel) relative to the current outer residual rel, so that
+// the sweep that can finish aims well under the tolerance. The FP32 operator's
+// own error (the treecode's about 5e-6) eats into each sweep's reduction; with
+// an aim of 1/2 the last sweep often lands just above the tolerance and a
+// further sweep and outer residual follow.
+constexpr double INNER_AIM = 0.2;
+
 struct Solver {
     const pb_mesh* m;
     const pb_near* nf;

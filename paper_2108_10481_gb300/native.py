@@ -19,7 +19,8 @@ class pb_params(ctypes.Structure):
 
 
 class pb_quad_plan(ctypes.Structure):
-    _fields_ = [("far_q", c_int), ("n_ss", c_int), ("band_eta", c_double), ("band_q", c_int)]
+    _fields_ = [("far_q", c_int), ("n_ss", c_int), ("band_eta", c_double), ("band_q", c_int),
+                ("n_ss_coin", c_int), ("n_ss_edge", c_int), ("n_ss_vert", c_int)]
 
 
 class pb_solve_opts(ctypes.Structure):
@@ -45,8 +46,14 @@ class pb_result(ctypes.Structure):
                 ("latency_ms", c_double), ("queue_ms", c_double)]
 
 
+class pb_tune_choice(ctypes.Structure):
+    _fields_ = [("kernel", c_int), ("shape", c_int), ("tile_records", c_int), ("stages", c_int),
+                ("targets_per_thread", c_int), ("split_scale", c_double), ("best_ms", c_double),
+                ("default_ms", c_double)]
+
+
 class pb_tune_result(ctypes.Structure):
-    _fields_ = [("kernel", c_int), ("split_scale", c_double), ("best_ms", c_double), ("default_ms", c_double)]
+    _fields_ = [("fast", pb_tune_choice), ("accurate", pb_tune_choice)]
 
 
 P = c_void_p

@@ -24,10 +24,12 @@ def test_launch_tuning_keeps_results(pb):
     nf = pb.pb_near_build(ctx, m, P.kappa)
     x = torch.as_tensor(np.random.default_rng(1).standard_normal(2 * len(v)), device="cuda")
     ref = pb.pb_system_apply(ctx, m, nf, P, "juffer", x, pb.PB_F64)
-    r = pb.pb_autotune(ctx, m, nf, P, "juffer")
-    print("tuned", r)
-    assert r["kernel"] in (1, 2) and r["split_scale"] in (0.5, 1.0, 2.0)
-    assert 0 < r["best_ms"] <= r["default_ms"]
+    rr = pb.pb_autotune(ctx, m, nf, P, "juffer")
+    print("tuned", rr)
+    for r in rr.values():
+        assert r["kernel"] in (1, 2) and r["split_scale"] in (0.5, 1.0, 2.0) and 0 <= r["shape"] < 4
+        assert r["tile_records"] in (32, 64, 128) and r["targets_per_thread"] in (2, 4)
+        assert 0 < r["best_ms"] <= r["default_ms"]
     for prec in (pb.PB_F32, pb.PB_F32_ACCURATE):
         y = pb.pb_system_apply(ctx, m, nf, P, "juffer", x, prec)
         assert float(torch.linalg.norm(y - ref) / torch.linalg.norm(ref)) < 2e-5
@@ -41,7 +43,14 @@ def test_plan_tuning_follows_the_rule(pb):
     P = pb.Params(4.0, 80.0, 0.125)
     opts = pb.solve_opts(tol=1e-10, max_it=300)
     strict, ch = pb.pb_autotune_plan(ctx, v, t, xq, q, P, "direct_int", "block_diag", tol_dG=1e-9, opts=opts)
-    assert strict == (6, 4, 0.0, 6) and ch == 0.0
+    assert strict == {"far_q": 6, "n_ss": 4, "band_eta": 0.0, "band_q": 6, "n_ss_coin": 4, "n_ss_edge": 4,
+                      "n_ss_vert": 4} and ch == 0.0
     loose, ch2 = pb.pb_autotune_plan(ctx, v, t, xq, q, P, "direct_int", "block_diag", tol_dG=5e-2, opts=opts)
     print("plans", strict, loose, ch2)
-    assert loose[0] == 3 and loose[2] > 0.0 and loose[3] == 6 and 0.0 < ch2 <= 5e-2
+    assert loose["far_q"] == 3 and loose["band_eta"] > 0.0 and loose["band_q"] == 6 and 0.0 < ch2 <= 5e-2
+    # a loose tolerance also takes one Gauss point off every class's singular rule
+    assert (loose["n_ss_coin"], loose["n_ss_edge"], loose["n_ss_vert"]) == (3, 3, 3)
+    # and the reported change is that of the returned plan
+    d_ref, _ = pb.pb_solvation_energy(ctx, v, t, xq, q, P, "direct_int", "block_diag", opts=opts)
+    d_new, _ = pb.pb_solvation_energy(ctx, v, t, xq, q, P, "direct_int", "block_diag", opts=opts, **loose)
+    assert abs(abs(d_new / d_ref - 1) - ch2) < 1e-9
