@@ -148,6 +148,10 @@ void PhaseTrace::lap(const char* label) {
     t0 = t;
 }
 
+void PhaseTrace::note(const char* label, double value) const {
+    if (on) fprintf(stderr, "[pbbem] %s/%s %.3e\n", scope, label, value);
+}
+
 int dev_alloc(void** p, size_t bytes) {
     *p = nullptr;
     if (bytes == 0) return PB_OK;

@@ -28,6 +28,7 @@
 #include <mutex>
 
 #include "internal.h"
+#include "tree_eval.cuh"
 
 namespace pb {
 
@@ -618,10 +619,10 @@ struct PairJob {
     int pad;
 };
 struct PairItem {
-    int job;
-    int tb;
-    int split;
-    int pad;
+    int job;    // index into the pair jobs (kind 0) or the tree jobs (kind 1)
+    int tb;     // target block (kind 0) or leaf (kind 1)
+    int split;  // source split (kind 0) or split of the leaf's lists (kind 1)
+    int kind;
 };
 
 __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
@@ -630,94 +631,132 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t b
                  : "memory");
 }
 
+// Persistent form: a grid of at most one wave of CTAs (the SM count times the
+// resident CTAs per SM) that take work items from the table in order through
+// a global counter until it runs out; the host lists the items most expensive
+// first, so that the last wave is made of short items. An item's sums do not
+// depend on which CTA takes it. Two kinds of item share the table: a target
+// block and source split of a direct pair sum (kind 0), and a leaf and list
+// split of a treecode evaluation (kind 1, FP32 only: tree_leaf_body on the
+// CTA's 256 threads, four groups of 64 over the sources, the staging buffer
+// as its scratch). The staging pipeline of the pair items runs on across
+// items: g counts the tiles a CTA has consumed, so tile it of the current item
+// sits on stage (g + it) % ST2 with phase parity ((g + it) / ST2) & 1.
 template <int MODE, bool ACC>
-__global__ void __launch_bounds__(TPB2) k_pair32x2_multi(const PairJob* __restrict__ jobs,
-                                                         const PairItem* __restrict__ items,
-                                                         int* __restrict__ status) {
+__global__ void __launch_bounds__(TPB2) k_pair32x2_queue(const PairJob* __restrict__ jobs,
+                                                         const TreeJob* __restrict__ tjobs,
+                                                         const PairItem* __restrict__ items, int n_items,
+                                                         int* __restrict__ counter, int* __restrict__ status) {
     constexpr int NACC = MODE == 0 ? 2 : 10;
     constexpr int NPK = ACC ? 1 : 2;
     constexpr int TGT = 2 * NPK;
     __shared__ __align__(128) float sh[ST2][TS2 * REC2];
     __shared__ __align__(8) uint64_t bar[ST2];
-    const PairItem it0 = items[blockIdx.x];
-    const PairJob& J = jobs[it0.job];
-    const int64_t np = J.np;
-    const int split = it0.split;
-    const int64_t j0 = split * J.chunk;
-    const int64_t j1 = min(np, j0 + J.chunk);
-    const int ntiles = (int)((j1 - j0 + TS2 - 1) / TS2);
-    const int64_t blk0 = (int64_t)it0.tb * (TPB2 * TGT), blk1 = blk0 + TPB2 * TGT;
+    __shared__ int s_item;
     const uint32_t tile_bytes = TS2 * REC2 * sizeof(float);
-
     if (threadIdx.x == 0) {
         for (int st = 0; st < ST2; ++st) mbar_init(&bar[st], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
-        for (int st = 0; st < ST2 && st < ntiles; ++st) {
-            mbar_expect_tx(&bar[st], tile_bytes);
-            bulk_load(sh[st], J.rec + (j0 + (int64_t)st * TS2) * REC2, tile_bytes, &bar[st]);
-        }
-    }
-    Coef2 cf;
-    for (int R = 0; R < 2; ++R)
-        for (int k = 0; k < 4; ++k) cf.c[R][k] = splat(J.cf.k[R][k]);
-    cf.kap = splat(J.cf.kappa);
-    cf.mk2 = splat(J.cf.mk2);
-    float2 X[NPK][3], XL[NPK][3];
-    int64_t tg[TGT];
-    for (int t = 0; t < TGT; ++t) tg[t] = blk0 + t * TPB2 + threadIdx.x;
-    for (int p = 0; p < NPK; ++p) {
-        int64_t a = tg[2 * p] < np ? tg[2 * p] : np - 1;
-        int64_t b = tg[2 * p + 1] < np ? tg[2 * p + 1] : np - 1;
-        for (int k = 0; k < 3; ++k) {
-            X[p][k] = make_float2(J.pts32[4 * a + k], J.pts32[4 * b + k]);
-            XL[p][k] = ACC ? make_float2(J.pts32lo[4 * a + k], J.pts32lo[4 * b + k]) : make_float2(0.f, 0.f);
-        }
-    }
-    float2 acc[NPK][NACC];
-    double accd[TGT][ACC ? NACC : 1];
-    for (int p = 0; p < NPK; ++p)
-        for (int a = 0; a < NACC; ++a) acc[p][a] = make_float2(0.f, 0.f);
-    for (int t = 0; t < TGT; ++t)
-        for (int a = 0; a < (ACC ? NACC : 1); ++a) accd[t][a] = 0.0;
-    int failed_at = -1;
-    for (int it = 0; it < ntiles; ++it) {
-        const int st = it % ST2;
-        const uint32_t phase = (uint32_t)((it / ST2) & 1);
-        if (!cta_wait(&bar[st], phase, status)) { failed_at = it; break; }
-        const int64_t jt = j0 + (int64_t)it * TS2;
-        const bool guard = (jt < blk1 && jt + TS2 > blk0) || jt + TS2 > np;
-        if (guard) tile_x2<MODE, ACC, NPK, true, TS2>(sh[st], X, XL, acc, cf);
-        else tile_x2<MODE, ACC, NPK, false, TS2>(sh[st], X, XL, acc, cf);
-        if (ACC) {
-            for (int p = 0; p < NPK; ++p)
-                for (int a = 0; a < NACC; ++a) {
-                    accd[2 * p][a] += (double)acc[p][a].x;
-                    accd[2 * p + 1][a] += (double)acc[p][a].y;
-                    acc[p][a] = make_float2(0.f, 0.f);
-                }
-        }
+    uint32_t g = 0;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
         __syncthreads();
-        if (threadIdx.x == 0 && it + ST2 < ntiles) {
+        const int item = s_item;
+        __syncthreads();  // every thread has read s_item before it is written again
+        if (item >= n_items) break;
+        const PairItem it0 = items[item];
+        if (it0.kind == 1) {
+            if (!ACC) {
+                static_assert(ST2 * TS2 * REC2 >= TREE_EVAL_TILE * TREE_REC &&
+                              ST2 * TS2 * REC2 >= 3 * (MODE == 0 ? 2 : 10) * TREE_LEAF, "tree scratch");
+                static_assert(TPB2 == 4 * (TREE_LEAF / 2), "tree groups");
+                tree_leaf_body<MODE, 4>(tjobs[it0.job], it0.tb, it0.split, &sh[0][0]);
+            }
+            continue;
+        }
+        const PairJob& J = jobs[it0.job];
+        const int64_t np = J.np;
+        const int split = it0.split;
+        const int64_t j0 = split * J.chunk;
+        const int64_t j1 = min(np, j0 + J.chunk);
+        const int ntiles = (int)((j1 - j0 + TS2 - 1) / TS2);
+        const int64_t blk0 = (int64_t)it0.tb * (TPB2 * TGT), blk1 = blk0 + TPB2 * TGT;
+        if (threadIdx.x == 0) {
+            // the stages were last read through the generic proxy
             asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-            mbar_expect_tx(&bar[st], tile_bytes);
-            bulk_load(sh[st], J.rec + (j0 + (int64_t)(it + ST2) * TS2) * REC2, tile_bytes, &bar[st]);
+            for (int k = 0; k < ST2 && k < ntiles; ++k) {
+                const int st = (int)((g + k) % ST2);
+                mbar_expect_tx(&bar[st], tile_bytes);
+                bulk_load(sh[st], J.rec + (j0 + (int64_t)k * TS2) * REC2, tile_bytes, &bar[st]);
+            }
         }
-    }
-    if (failed_at >= 0) {
-        cta_drain(bar, ST2, failed_at, ntiles);
-        return;
-    }
-    for (int t = 0; t < TGT; ++t) {
-        if (tg[t] >= np) continue;
-        const int p = t >> 1, h = t & 1;
-        for (int a = 0; a < NACC; ++a) {
-            int64_t o = ((int64_t)split * NACC + a) * np + tg[t];
-            if (ACC) static_cast<double*>(J.part)[o] = accd[t][a];
-            else static_cast<float*>(J.part)[o] = h ? acc[p][a].y : acc[p][a].x;
+        Coef2 cf;
+        for (int R = 0; R < 2; ++R)
+            for (int k = 0; k < 4; ++k) cf.c[R][k] = splat(J.cf.k[R][k]);
+        cf.kap = splat(J.cf.kappa);
+        cf.mk2 = splat(J.cf.mk2);
+        float2 X[NPK][3], XL[NPK][3];
+        int64_t tg[TGT];
+        for (int t = 0; t < TGT; ++t) tg[t] = blk0 + t * TPB2 + threadIdx.x;
+        for (int p = 0; p < NPK; ++p) {
+            int64_t a = tg[2 * p] < np ? tg[2 * p] : np - 1;
+            int64_t b = tg[2 * p + 1] < np ? tg[2 * p + 1] : np - 1;
+            for (int k = 0; k < 3; ++k) {
+                X[p][k] = make_float2(J.pts32[4 * a + k], J.pts32[4 * b + k]);
+                XL[p][k] = ACC ? make_float2(J.pts32lo[4 * a + k], J.pts32lo[4 * b + k]) : make_float2(0.f, 0.f);
+            }
         }
+        float2 acc[NPK][NACC];
+        double accd[TGT][ACC ? NACC : 1];
+        for (int p = 0; p < NPK; ++p)
+            for (int a = 0; a < NACC; ++a) acc[p][a] = make_float2(0.f, 0.f);
+        for (int t = 0; t < TGT; ++t)
+            for (int a = 0; a < (ACC ? NACC : 1); ++a) accd[t][a] = 0.0;
+        int failed_at = -1;
+        for (int it = 0; it < ntiles; ++it) {
+            const int st = (int)((g + it) % ST2);
+            const uint32_t phase = (uint32_t)(((g + it) / ST2) & 1);
+            if (!cta_wait(&bar[st], phase, status)) { failed_at = it; break; }
+            const int64_t jt = j0 + (int64_t)it * TS2;
+            const bool guard = (jt < blk1 && jt + TS2 > blk0) || jt + TS2 > np;
+            if (guard) tile_x2<MODE, ACC, NPK, true, TS2>(sh[st], X, XL, acc, cf);
+            else tile_x2<MODE, ACC, NPK, false, TS2>(sh[st], X, XL, acc, cf);
+            if (ACC) {
+                for (int p = 0; p < NPK; ++p)
+                    for (int a = 0; a < NACC; ++a) {
+                        accd[2 * p][a] += (double)acc[p][a].x;
+                        accd[2 * p + 1][a] += (double)acc[p][a].y;
+                        acc[p][a] = make_float2(0.f, 0.f);
+                    }
+            }
+            __syncthreads();
+            if (threadIdx.x == 0 && it + ST2 < ntiles) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                mbar_expect_tx(&bar[st], tile_bytes);
+                bulk_load(sh[st], J.rec + (j0 + (int64_t)(it + ST2) * TS2) * REC2, tile_bytes, &bar[st]);
+            }
+        }
+        if (failed_at >= 0) {
+            // the copies still in flight (tiles failed_at .. failed_at + ST2 - 1), then leave
+            if (threadIdx.x == 0)
+                for (int k = failed_at; k < ntiles && k < failed_at + ST2; ++k)
+                    for (int i = 0; i < (1 << 20); ++i)
+                        if (mbar_try_wait(&bar[(g + k) % ST2], (uint32_t)(((g + k) / ST2) & 1))) break;
+            __syncthreads();
+            return;
+        }
+        for (int t = 0; t < TGT; ++t) {
+            if (tg[t] >= np) continue;
+            const int p = t >> 1, h = t & 1;
+            for (int a = 0; a < NACC; ++a) {
+                int64_t o = ((int64_t)split * NACC + a) * np + tg[t];
+                if (ACC) static_cast<double*>(J.part)[o] = accd[t][a];
+                else static_cast<float*>(J.part)[o] = h ? acc[p][a].y : acc[p][a].x;
+            }
+        }
+        g += (uint32_t)ntiles;
     }
 }
 
@@ -1095,15 +1134,21 @@ int apply_blockop(const pb_mesh* m, const pb_near* nf, const BlockOp& B, int pre
     return PB_OK;
 }
 
-// y_j = B_j x_j for many meshes: sources per job, one packed pair-kernel
-// launch per row mode over all jobs' work items, then each job's reduction
-// and gather. prec: PB_F32 or PB_F32_ACCURATE (PB_F64 runs the jobs one by one).
+// y_j = B_j x_j for many meshes: sources per job, one persistent packed
+// pair-kernel launch per row mode over all jobs' work items, then each job's
+// reduction and gather. prec: PB_F32 or PB_F32_ACCURATE (PB_F64 runs the jobs one by one).
 int apply_blockops_batched(const std::vector<FarJob>& jobs, int prec, BatchScratch& bs, cudaStream_t s) {
     if (jobs.empty()) return PB_OK;
     if (prec == PB_F64) {
-        for (const FarJob& j : jobs) PB_TRY(apply_blockop(j.m, j.nf, j.B, PB_F64, j.x, j.y, s));
+        for (const FarJob& j : jobs) PB_TRY(apply_blockop(j.m, j.nf, j.B, PB_F64, j.x, j.y, j.s ? j.s : s));
         return PB_OK;
     }
+    while (bs.ev.size() < jobs.size()) {
+        cudaEvent_t e = nullptr;
+        PB_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        bs.ev.push_back(e);
+    }
+    if (!bs.ev_main) PB_CUDA(cudaEventCreateWithFlags(&bs.ev_main, cudaEventDisableTiming));
     if (prec != PB_F32 && prec != PB_F32_ACCURATE) return set_error(PB_EINVAL, "unknown precision %d", prec);
     const bool acc = prec == PB_F32_ACCURATE;
     const int tpc = TPB2 * (acc ? 2 : 4);
@@ -1118,10 +1163,13 @@ int apply_blockops_batched(const std::vector<FarJob>& jobs, int prec, BatchScrat
     std::vector<Prep> prep(jobs.size());
     std::vector<PairJob> hjobs[2];
     std::vector<int> hjob_of[2];
+    std::vector<TreeJob> tjobs[2];
+    std::vector<int> tjob_of[2];
     for (size_t k = 0; k < jobs.size(); ++k) {
         const FarJob& J = jobs[k];
         pb_mesh* m = const_cast<pb_mesh*>(J.m);
         Prep& P = prep[k];
+        cudaStream_t js = J.s ? J.s : s;
         PB_TRY(make_far_plan(J.B, J.nf->kappa, &P.fp));
         const int64_t nt = m->nt, np = m->np;
         const int64_t np_pad = (np + TS2 - 1) / TS2 * TS2;
@@ -1131,7 +1179,7 @@ int apply_blockops_batched(const std::vector<FarJob>& jobs, int prec, BatchScrat
         P.tri = (double*)m->ws_tri.ptr;
         P.c64 = (double*)m->ws_comb.ptr;
         P.c32 = (float*)(P.c64 + 4 * m->nnz);
-        PB_TRY(combine_near(m, J.nf, J.B, P.c64, P.c32, s));
+        PB_TRY(combine_near(m, J.nf, J.B, P.c64, P.c32, js));
         if (!P.fp.any) continue;
         bool need_u = false, need_v = false;
         for (int R = 0; R < 2; ++R)
@@ -1139,12 +1187,21 @@ int apply_blockops_batched(const std::vector<FarJob>& jobs, int prec, BatchScrat
                 need_u = need_u || J.B.c[R][0][o] != 0.0;
                 need_v = need_v || J.B.c[R][1][o] != 0.0;
             }
+        if (!acc && m->ctx->tree_enable && np >= m->ctx->tree_min_points && np > 256) {
+            // treecode: its sources and proxy charges now, its leaves in the shared launch
+            TreeJob tj;
+            PB_TRY(tree_prepare(m, P.fp, J.x, need_u, need_v, &tj, js));
+            P.S = tj.nsplit;
+            tjobs[P.fp.mode].push_back(tj);
+            tjob_of[P.fp.mode].push_back((int)k);
+            continue;
+        }
         float* rec = (float*)m->ws_src.ptr;
         unsigned tb = (unsigned)((nt + 127) / 128);
-        k_sources2<float><<<tb, 128, 0, s>>>(nt, m->Q, mesh_rule(m), m->tris, m->tgeo, m->pts64, m->pts32,
-                                             m->pts32lo, J.x, J.x + m->nv, need_u, need_v, rec);
+        k_sources2<float><<<tb, 128, 0, js>>>(nt, m->Q, mesh_rule(m), m->tris, m->tgeo, m->pts64, m->pts32,
+                                              m->pts32lo, J.x, J.x + m->nv, need_u, need_v, rec);
         ::pb::count_launch();
-        if (np_pad > np) PB_CUDA(cudaMemsetAsync(rec + REC2 * np, 0, sizeof(float) * REC2 * (np_pad - np), s));
+        if (np_pad > np) PB_CUDA(cudaMemsetAsync(rec + REC2 * np, 0, sizeof(float) * REC2 * (np_pad - np), js));
         // the single-mesh decomposition (same kernel occupancy as that path)
         const void* kern = x2_kernel(P.fp.mode, acc, 0).fn;  // the default shape's occupancy (the batched kernel's)
         int S = choose_splits(np, tpc, TS2, occupancy_slots(m, kern, TPB2));
@@ -1169,64 +1226,110 @@ int apply_blockops_batched(const std::vector<FarJob>& jobs, int prec, BatchScrat
         hjobs[P.fp.mode].push_back(pj);
         hjob_of[P.fp.mode].push_back((int)k);
     }
+    // the jobs' own streams' work (sources, near values, tree preparation) before the shared launch
+    for (size_t k = 0; k < jobs.size(); ++k)
+        if (jobs[k].s && jobs[k].s != s) {
+            PB_CUDA(cudaEventRecord(bs.ev[k], jobs[k].s));
+            PB_CUDA(cudaStreamWaitEvent(s, bs.ev[k], 0));
+        }
     for (int mode = 0; mode < 2; ++mode) {
-        if (hjobs[mode].empty()) continue;
-        std::vector<PairItem> items;
+        if (hjobs[mode].empty() && tjobs[mode].empty()) continue;
+        // work items, the most expensive first (longest processing time first): a pair item
+        // costs its target block times its split's sources; a tree item the average pairs of
+        // its tree's leaves and splits, weighted by the tree kernel's lower rate per pair
+        std::vector<std::pair<double, PairItem>> costed;
         for (size_t q = 0; q < hjobs[mode].size(); ++q) {
             const PairJob& pj = hjobs[mode][q];
             const int ntb = (int)((pj.np + tpc - 1) / tpc);
-            for (int tb = 0; tb < ntb; ++tb)
-                for (int sp = 0; sp < pj.nsplit; ++sp) items.push_back({(int)q, tb, sp, 0});
+            for (int sp = 0; sp < pj.nsplit; ++sp) {
+                const int64_t j0 = sp * pj.chunk, j1 = std::min(pj.np, j0 + pj.chunk);
+                const double cost = (double)tpc * (double)((j1 - j0 + TS2 - 1) / TS2 * TS2);
+                for (int tb = 0; tb < ntb; ++tb) costed.push_back({cost, {(int)q, tb, sp, 0}});
+            }
         }
-        const size_t jb = sizeof(PairJob) * hjobs[mode].size(), ib = sizeof(PairItem) * items.size();
-        PB_TRY(ws_reserve(bs.table, jb + ib + 256));
+        for (size_t q = 0; q < tjobs[mode].size(); ++q) {
+            const pb_mesh* tm_ = jobs[tjob_of[mode][q]].m;
+            const TreeJob& tj = tjobs[mode][q];
+            const int64_t nleaf = tree_leaves(tm_);
+            const double cost = 1.4 * (double)tree_interactions(tm_) / (double)std::max<int64_t>(1, nleaf * tj.nsplit);
+            for (int64_t leaf = 0; leaf < nleaf; ++leaf)
+                for (int sp = 0; sp < tj.nsplit; ++sp) costed.push_back({cost, {(int)q, (int)leaf, sp, 1}});
+        }
+        std::stable_sort(costed.begin(), costed.end(),
+                         [](const std::pair<double, PairItem>& a, const std::pair<double, PairItem>& b) {
+                             return a.first > b.first;
+                         });
+        std::vector<PairItem> items(costed.size());
+        for (size_t i = 0; i < costed.size(); ++i) items[i] = costed[i].second;
+        const size_t jb = sizeof(PairJob) * hjobs[mode].size(), tjb = sizeof(TreeJob) * tjobs[mode].size();
+        const size_t ib = sizeof(PairItem) * items.size();
+        const size_t jb_al = (jb + 255) / 256 * 256, tjb_al = (tjb + 255) / 256 * 256, ib_al = (ib + 255) / 256 * 256;
+        PB_TRY(ws_reserve(bs.table, jb_al + tjb_al + ib_al + 256));
         char* base = (char*)bs.table.ptr;
         PairJob* djobs = (PairJob*)base;
-        PairItem* ditems = (PairItem*)(base + (jb + 255) / 256 * 256);
-        if ((jb + 255) / 256 * 256 + ib > bs.table.bytes) {
-            PB_TRY(ws_reserve(bs.table, (jb + 255) / 256 * 256 + ib + 256));
-            base = (char*)bs.table.ptr;
-            djobs = (PairJob*)base;
-            ditems = (PairItem*)(base + (jb + 255) / 256 * 256);
-        }
-        PB_CUDA(cudaMemcpyAsync(djobs, hjobs[mode].data(), jb, cudaMemcpyHostToDevice, s));
+        TreeJob* dtjobs = (TreeJob*)(base + jb_al);
+        PairItem* ditems = (PairItem*)(base + jb_al + tjb_al);
+        int* counter = (int*)(base + jb_al + tjb_al + ib_al);
+        if (jb) PB_CUDA(cudaMemcpyAsync(djobs, hjobs[mode].data(), jb, cudaMemcpyHostToDevice, s));
+        if (tjb) PB_CUDA(cudaMemcpyAsync(dtjobs, tjobs[mode].data(), tjb, cudaMemcpyHostToDevice, s));
         PB_CUDA(cudaMemcpyAsync(ditems, items.data(), ib, cudaMemcpyHostToDevice, s));
-        int* status = jobs[hjob_of[mode][0]].m->status;
-        const unsigned n_items = (unsigned)items.size();
+        PB_CUDA(cudaMemsetAsync(counter, 0, sizeof(int), s));
+        int* status = jobs[hjob_of[mode].empty() ? tjob_of[mode][0] : hjob_of[mode][0]].m->status;
+        const int n_items = (int)items.size();
+        const void* kern = mode == 0 ? (acc ? (const void*)k_pair32x2_queue<0, true> : (const void*)k_pair32x2_queue<0, false>)
+                                     : (acc ? (const void*)k_pair32x2_queue<1, true> : (const void*)k_pair32x2_queue<1, false>);
+        const pb_ctx* ctx = jobs[hjob_of[mode].empty() ? tjob_of[mode][0] : hjob_of[mode][0]].m->ctx;
+        int per_sm = 1;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TPB2, 0) != cudaSuccess || per_sm < 1) per_sm = 1;
+        cudaGetLastError();
+        const unsigned grid = (unsigned)std::max(1, std::min(n_items, per_sm * ctx->num_sms));
         if (mode == 0) {
-            if (acc) k_pair32x2_multi<0, true><<<n_items, TPB2, 0, s>>>(djobs, ditems, status);
-            else k_pair32x2_multi<0, false><<<n_items, TPB2, 0, s>>>(djobs, ditems, status);
+            if (acc) k_pair32x2_queue<0, true><<<grid, TPB2, 0, s>>>(djobs, dtjobs, ditems, n_items, counter, status);
+            else k_pair32x2_queue<0, false><<<grid, TPB2, 0, s>>>(djobs, dtjobs, ditems, n_items, counter, status);
         } else {
-            if (acc) k_pair32x2_multi<1, true><<<n_items, TPB2, 0, s>>>(djobs, ditems, status);
-            else k_pair32x2_multi<1, false><<<n_items, TPB2, 0, s>>>(djobs, ditems, status);
+            if (acc) k_pair32x2_queue<1, true><<<grid, TPB2, 0, s>>>(djobs, dtjobs, ditems, n_items, counter, status);
+            else k_pair32x2_queue<1, false><<<grid, TPB2, 0, s>>>(djobs, dtjobs, ditems, n_items, counter, status);
         }
         ::pb::count_launch();
     }
+    // and the shared launch before the jobs' own reductions
+    PB_CUDA(cudaEventRecord(bs.ev_main, s));
+    for (size_t k = 0; k < jobs.size(); ++k)
+        if (jobs[k].s && jobs[k].s != s) PB_CUDA(cudaStreamWaitEvent(jobs[k].s, bs.ev_main, 0));
     for (size_t k = 0; k < jobs.size(); ++k) {
         const FarJob& J = jobs[k];
         const pb_mesh* m = J.m;
         const Prep& P = prep[k];
+        cudaStream_t js = J.s ? J.s : s;
         if (P.fp.any) {
             unsigned tb = (unsigned)((m->nt + 127) / 128);
             if (acc)
-                k_tri_reduce<double><<<tb, 128, 0, s>>>(m->nt, m->np, mesh_rule(m), P.S, P.fp.mode, P.fp, m->tgeo,
-                                                        m->pts64, (const double*)m->ws_part.ptr, P.tri);
+                k_tri_reduce<double><<<tb, 128, 0, js>>>(m->nt, m->np, mesh_rule(m), P.S, P.fp.mode, P.fp, m->tgeo,
+                                                         m->pts64, (const double*)m->ws_part.ptr, P.tri);
             else
-                k_tri_reduce<float><<<tb, 128, 0, s>>>(m->nt, m->np, mesh_rule(m), P.S, P.fp.mode, P.fp, m->tgeo,
-                                                       m->pts64, (const float*)m->ws_part.ptr, P.tri);
+                k_tri_reduce<float><<<tb, 128, 0, js>>>(m->nt, m->np, mesh_rule(m), P.S, P.fp.mode, P.fp, m->tgeo,
+                                                        m->pts64, (const float*)m->ws_part.ptr, P.tri);
             ::pb::count_launch();
         }
         unsigned gb = (unsigned)((m->nv * 8 + 255) / 256);
         if (prec == PB_F32)
-            k_gather_spmv<float><<<gb, 256, 0, s>>>(m->nv, m->v2t_ptr, m->v2t, P.tri, P.fp.any ? 1 : 0, m->row_ptr,
-                                                    m->col, P.c32, m->nnz, J.x, J.y);
+            k_gather_spmv<float><<<gb, 256, 0, js>>>(m->nv, m->v2t_ptr, m->v2t, P.tri, P.fp.any ? 1 : 0, m->row_ptr,
+                                                     m->col, P.c32, m->nnz, J.x, J.y);
         else
-            k_gather_spmv<double><<<gb, 256, 0, s>>>(m->nv, m->v2t_ptr, m->v2t, P.tri, P.fp.any ? 1 : 0, m->row_ptr,
-                                                     m->col, P.c64, m->nnz, J.x, J.y);
+            k_gather_spmv<double><<<gb, 256, 0, js>>>(m->nv, m->v2t_ptr, m->v2t, P.tri, P.fp.any ? 1 : 0,
+                                                      m->row_ptr, m->col, P.c64, m->nnz, J.x, J.y);
         ::pb::count_launch();
     }
     PB_CUDA(cudaGetLastError());
     return PB_OK;
+}
+
+void batch_scratch_free(BatchScratch& bs) {
+    ws_free(bs.table);
+    for (cudaEvent_t e : bs.ev) cudaEventDestroy(e);
+    bs.ev.clear();
+    if (bs.ev_main) cudaEventDestroy(bs.ev_main);
+    bs.ev_main = nullptr;
 }
 
 int far_splits_estimate(pb_ctx* ctx, int64_t np) {

@@ -256,10 +256,14 @@ struct FarJob {
     BlockOp B;
     const double* x;
     double* y;
+    cudaStream_t s = nullptr;  // the job's own stream for its per-job kernels (null: the batch's stream)
 };
 struct BatchScratch {
-    Workspace table;  // job and work-item tables on the device
+    Workspace table;                  // job and work-item tables on the device
+    std::vector<cudaEvent_t> ev;      // per job: its stream's work before the shared launch
+    cudaEvent_t ev_main = nullptr;    // the shared launch, before the jobs' own reductions
 };
+void batch_scratch_free(BatchScratch& bs);
 int apply_blockops_batched(const std::vector<FarJob>& jobs, int prec, BatchScratch& bs, cudaStream_t s);
 
 // treecode far field (FP32): per-target partial sums in the direct kernel's
@@ -299,6 +303,7 @@ struct PhaseTrace {
     bool on;
     explicit PhaseTrace(const char* s);
     void lap(const char* label);
+    void note(const char* label, double value) const;  // a value beside the laps (no timing)
 };
 
 struct Timer {

@@ -7,16 +7,17 @@
 // non-blocking stream (so near-field builds overlap the other requests'
 // iterations), and hands them to the active set. Every pb_server_step then
 // advances each active request by one GMRES step: all their operator
-// applications go into one batched pair-kernel launch per row mode over a
-// table of (request, target block, source split) work items, followed by each
-// request's own preconditioner, Gram-Schmidt and Givens kernels, and one
-// read-back of all residual estimates. A request that converges computes its
-// energy, reports its result and frees its memory, making room for the next.
+// applications go into one persistent launch per row mode over a table of
+// work items - (request, target block, source split) of the direct pair sums
+// and (request, leaf, list split) of the treecode for requests large enough
+// for it - taken by the CTAs most expensive first, followed by each request's
+// own preconditioner, Gram-Schmidt and Givens kernels, and one read-back of
+// all residual estimates. A request that converges computes its energy,
+// reports its result and frees its memory, making room for the next.
 //
-// Each request keeps the split decomposition it has alone, and all its
-// reductions run in a fixed order, so its result does not depend on what
-// else is in the batch. Requests large enough for the treecode (FP32 inner
-// iterations) take it on their own instead of the batched launch.
+// Each request keeps the decomposition it has alone, and all its reductions
+// run in a fixed order, so its result does not depend on what else is in the
+// batch.
 #include <algorithm>
 #include <chrono>
 #include <cmath>
@@ -89,6 +90,10 @@ struct pb_server {
     double* res_dev = nullptr;   // 4 doubles per slot (max_active slots)
     double* res_host = nullptr;
     std::vector<int> free_slots;
+    // per slot: the stream of the active request that holds it (its own kernels, so that the small
+    // kernels of different requests overlap on the device) and an event joining it to s_main
+    std::vector<cudaStream_t> slot_stream;
+    std::vector<cudaEvent_t> slot_event;
 };
 
 namespace pb {
@@ -158,7 +163,7 @@ static int setup_req(pb_server* srv, ServeReq* r) {
     PB_TRY(setup_solver(r->S, r->m, r->nf, &r->prm, r->form, r->pc, &r->opts, s));
     PB_TRY(gmres_alloc(r->G, 2 * nv, r->mmax));
     PB_CUDA(cudaStreamSynchronize(s));
-    r->S.s = srv->s_main;
+    r->S.s = srv->s_main;  // until the request holds a slot (and its stream)
     r->mixed = r->opts.precision == PB_MIXED;
     r->phase = PH_START;
     return PB_OK;
@@ -223,24 +228,13 @@ static void admission_loop(pb_server* srv) {
     }
 }
 
-// The operator applications of one round: FP32 applications of meshes large
-// enough for the treecode go through it one request at a time (such a request
-// fills the GPU by itself); everything else in one batched launch per
-// precision. The path a request takes depends only on its own size, so its
-// result does not depend on the batch.
+// The operator applications of one round: per precision, one persistent launch
+// over the work items of every request (pair items of the direct sums and, for
+// FP32 applications of meshes large enough for the treecode, the leaves of
+// their trees). The path a request takes, and its decomposition into items,
+// depend only on its own size, so its result does not depend on the batch.
 static int apply_round(pb_server* srv, std::vector<FarJob>* jobs, cudaStream_t s) {
-    const pb_ctx* ctx = srv->ctx;
-    std::vector<FarJob> rest;
-    for (int p = 0; p < 4; ++p) {
-        rest.clear();
-        for (const FarJob& j : jobs[p]) {
-            if (p == PB_F32 && ctx->tree_enable && j.m->np >= ctx->tree_min_points && j.m->np > 256)
-                PB_TRY(apply_blockop(j.m, j.nf, j.B, PB_F32, j.x, j.y, s));
-            else
-                rest.push_back(j);
-        }
-        PB_TRY(apply_blockops_batched(rest, p, srv->bs, s));
-    }
+    for (int p = 0; p < 4; ++p) PB_TRY(apply_blockops_batched(jobs[p], p, srv->bs, s));
     return PB_OK;
 }
 
@@ -260,7 +254,9 @@ static int tick(pb_server* srv) {
         if (r->slot < 0) {
             r->slot = srv->free_slots.back();
             srv->free_slots.pop_back();
+            r->S.s = srv->slot_stream[r->slot];
         }
+    auto rs_of = [&](const ServeReq* r) { return srv->slot_stream[r->slot]; };
     // an iteration piece from its CUDA graph once the request has run it once
     auto piece = [&](ServeReq* r, StepGraph& g, const std::function<int()>& body) -> int {
         graph_check(g);
@@ -269,11 +265,11 @@ static int tick(pb_server* srv) {
             if (r->j < 1) return body();
             {
                 std::lock_guard<std::mutex> dev_lock(srv->device_mu);
-                PB_TRY(graph_capture(g, s, body));
+                PB_TRY(graph_capture(g, rs_of(r), body));
             }
             if (g.failed) return body();
         }
-        return graph_replay(g, s);
+        return graph_replay(g, rs_of(r));
     };
     auto it_prec = [](const ServeReq* r) { return r->mixed ? PB_F32 : PB_F64; };
     auto res_prec = [](const ServeReq* r) { return r->mixed ? PB_F32_ACCURATE : PB_F64; };
@@ -282,9 +278,9 @@ static int tick(pb_server* srv) {
     std::vector<FarJob> jobs[4];  // by precision
     for (ServeReq* r : act) {
         if (r->phase == PH_ITER)
-            jobs[it_prec(r)].push_back({r->m, r->nf, r->S.A, r->G.vin, r->S.t3});
+            jobs[it_prec(r)].push_back({r->m, r->nf, r->S.A, r->G.vin, r->S.t3, rs_of(r)});
         else if (r->phase == PH_START && r->mixed && r->outer > 0)
-            jobs[res_prec(r)].push_back({r->m, r->nf, r->S.A, r->x, r->S.t3});
+            jobs[res_prec(r)].push_back({r->m, r->nf, r->S.A, r->x, r->S.t3, rs_of(r)});
     }
     PB_TRY(apply_round(srv, jobs, s));
     for (auto& v : jobs) v.clear();
@@ -298,12 +294,12 @@ static int tick(pb_server* srv) {
             if (r->pc >= PB_PC_CALDERON_FULL) {
                 const int ip = it_prec(r);
                 PB_TRY(piece(r, r->g_mid, [r, ip] { return calderon_pre(r->S, ip, r->S.t3); }));
-                jobs[it_prec(r)].push_back({r->m, r->nf, r->S.C, r->S.t1, r->S.t2});
+                jobs[it_prec(r)].push_back({r->m, r->nf, r->S.C, r->S.t1, r->S.t2, rs_of(r)});
             }
             continue;  // the rest of the iteration follows the batched operators
         } else if (r->phase == PH_START) {
             if (r->mixed && r->outer > 0) {
-                vec_sub(n2, r->rhs, r->S.t3, r->rr, s);
+                vec_sub(n2, r->rhs, r->S.t3, r->rr, rs_of(r));
                 pin[k] = r->rr;
             } else {
                 pin[k] = r->rhs;
@@ -313,7 +309,7 @@ static int tick(pb_server* srv) {
         const int prec = r->phase == PH_ITER ? it_prec(r) : res_prec(r);
         if (r->pc >= PB_PC_CALDERON_FULL) {
             PB_TRY(calderon_pre(r->S, prec, pin[k]));
-            jobs[prec].push_back({r->m, r->nf, r->S.C, r->S.t1, r->S.t2});
+            jobs[prec].push_back({r->m, r->nf, r->S.C, r->S.t1, r->S.t2, rs_of(r)});
         } else {
             PB_TRY(apply_prec(r->S, prec, pin[k], r->w));
         }
@@ -323,17 +319,23 @@ static int tick(pb_server* srv) {
         ServeReq* r = act[k];
         if (!pin[k]) continue;
         double* slot = srv->res_dev + 4 * r->slot;
+        cudaStream_t rs = rs_of(r);
         if (r->phase == PH_ITER) {
             const int prec = it_prec(r);
-            PB_TRY(piece(r, r->g_tail, [r, prec, slot, s] {
+            PB_TRY(piece(r, r->g_tail, [r, prec, slot, rs] {
                 if (r->pc >= PB_PC_CALDERON_FULL) PB_TRY(calderon_post(r->S, prec, r->w));
                 else PB_TRY(apply_prec(r->S, prec, r->S.t3, r->w));
-                return gm_step(r->G, r->w, slot, s);
+                return gm_step(r->G, r->w, slot, rs);
             }));
         } else {
             if (r->pc >= PB_PC_CALDERON_FULL) PB_TRY(calderon_post(r->S, res_prec(r), r->w));
-            gm_norm2(r->G, r->w, slot, s);
+            gm_norm2(r->G, r->w, slot, rs);
         }
+    }
+    // every request's estimates, after its own stream's work
+    for (ServeReq* r : act) {
+        PB_CUDA(cudaEventRecord(srv->slot_event[r->slot], rs_of(r)));
+        PB_CUDA(cudaStreamWaitEvent(s, srv->slot_event[r->slot], 0));
     }
     PB_CUDA(cudaMemcpyAsync(srv->res_host, srv->res_dev, sizeof(double) * 4 * srv->max_active,
                             cudaMemcpyDeviceToHost, s));
@@ -361,8 +363,8 @@ static int tick(pb_server* srv) {
                 continue;
             }
             r->inner_tol = r->mixed ? std::min(0.5, std::max(r->opts.inner_tol, INNER_AIM * tol / r->rel)) : tol;
-            PB_TRY(gm_begin(r->G, r->w, srv->res_dev + 4 * r->slot, s));
-            if (r->mixed) PB_CUDA(cudaMemsetAsync(r->dd, 0, sizeof(double) * 2 * r->m->nv, s));
+            PB_TRY(gm_begin(r->G, r->w, srv->res_dev + 4 * r->slot, rs_of(r)));
+            if (r->mixed) PB_CUDA(cudaMemsetAsync(r->dd, 0, sizeof(double) * 2 * r->m->nv, rs_of(r)));
             r->j = 0;
             r->phase = PH_ITER;
         } else if (r->phase == PH_ITER) {
@@ -376,9 +378,9 @@ static int tick(pb_server* srv) {
             }
             const bool conv = res <= r->inner_tol;
             if (conv || h[1] == 0.0 || r->j >= r->mmax || r->total_it >= r->opts.max_it) {
-                PB_TRY(gm_finish(r->G, r->j, r->mixed ? r->dd : r->x, s));
+                PB_TRY(gm_finish(r->G, r->j, r->mixed ? r->dd : r->x, rs_of(r)));
                 if (r->mixed) {
-                    vec_add(2 * r->m->nv, r->dd, r->x, s);
+                    vec_add(2 * r->m->nv, r->dd, r->x, rs_of(r));
                     r->outer += 1;
                     r->phase = r->total_it >= r->opts.max_it || r->outer >= std::max(1, r->opts.max_outer)
                                    ? PH_ENERGY : PH_START;
@@ -401,9 +403,9 @@ static int tick(pb_server* srv) {
         }
         double dGp = 0.0, dGk = 0.0;
         int rc = pb_energy(srv->ctx, r->m, r->x, r->form, r->dxq, r->dq, (int64_t)r->q.size(), &r->prm, nullptr, &dGp,
-                           &dGk, s);
+                           &dGk, rs_of(r));
         if (rc != PB_OK && r->status == PB_OK) r->status = rc;
-        if (r->status == PB_OK) r->status = check_status(r->m, s);
+        if (r->status == PB_OK) r->status = check_status(r->m, rs_of(r));
         srv->free_slots.push_back(r->slot);
         r->slot = -1;
         finish(srv, r, dGp, dGk);
@@ -442,6 +444,22 @@ extern "C" int pb_server_create(pb_ctx* ctx, int64_t hbm_budget_bytes, int max_a
     }
     cudaMemset(srv->res_dev, 0, sizeof(double) * 4 * max_active);
     for (int k = max_active - 1; k >= 0; --k) srv->free_slots.push_back(k);
+    srv->slot_stream.assign(max_active, nullptr);
+    srv->slot_event.assign(max_active, nullptr);
+    for (int k = 0; k < max_active; ++k)
+        if (cudaStreamCreateWithFlags(&srv->slot_stream[k], cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&srv->slot_event[k], cudaEventDisableTiming) != cudaSuccess) {
+            for (cudaStream_t q : srv->slot_stream)
+                if (q) cudaStreamDestroy(q);
+            for (cudaEvent_t e : srv->slot_event)
+                if (e) cudaEventDestroy(e);
+            cudaFree(srv->res_dev);
+            cudaFreeHost(srv->res_host);
+            cudaStreamDestroy(srv->s_main);
+            cudaStreamDestroy(srv->s_setup);
+            delete srv;
+            return set_error(PB_ECUDA, "pb_server_create: request streams");
+        }
     srv->admit_thread = std::thread(admission_loop, srv);
     *out = srv;
     return PB_OK;
@@ -460,7 +478,11 @@ extern "C" int pb_server_destroy(pb_server* srv) {
     for (ServeReq* r : srv->active) { free_req(r); delete r; }
     for (ServeReq* r : srv->ready) { free_req(r); delete r; }
     for (ServeReq* r : srv->waiting) delete r;
-    ws_free(srv->bs.table);
+    batch_scratch_free(srv->bs);
+    for (cudaStream_t q : srv->slot_stream)
+        if (q) cudaStreamDestroy(q);
+    for (cudaEvent_t e : srv->slot_event)
+        if (e) cudaEventDestroy(e);
     if (srv->res_dev) cudaFree(srv->res_dev);
     if (srv->res_host) cudaFreeHost(srv->res_host);
     cudaStreamDestroy(srv->s_main);

@@ -752,6 +752,7 @@ static int solve_one(const pb_mesh* m, const pb_near* nf, const pb_solve_opts* o
                 if (outer == 0) bnorm = beta;
                 double prev = rel;
                 rel = bnorm > 0.0 ? beta / bnorm : 0.0;
+                tr.note("outer_rel", rel);
                 if (rel <= o->tol) break;
                 // the outer residual no longer falls: its own accuracy is reached
                 if (outer >= 2 && rel > 0.5 * prev) break;

@@ -23,31 +23,12 @@
 #include <numeric>
 #include <vector>
 
-#include "internal.h"
+#include "tree_eval.cuh"
 
 namespace pb {
 
-constexpr int TREE_LEAF = 128;     // targets per leaf (one CTA)
-constexpr int TREE_REC = 12;       // floats per tree source / proxy record
 constexpr int TREE_MAXN = 8;
 constexpr int TREE_MAX_SPLITS = 8;  // CTAs sharing one leaf's interaction lists       // largest Chebyshev order + 1
-
-struct TreeCoef {
-    float k[2][4];
-    float kappa;
-    float mk2;  // -kappa log2(e)
-};
-
-__device__ __forceinline__ float t_rsqrt(float x) {
-    float y;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-__device__ __forceinline__ float t_ex2(float x) {
-    float y;
-    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
 
 // ---------------------------------------------------------------- host tree
 struct HostNode {
@@ -497,197 +478,20 @@ k_proxy_charges(const int32_t* __restrict__ slots, const int32_t* __restrict__ s
 }
 
 // Packed pairs of FP32 values (f32x2 instructions: two targets per thread).
-__device__ __forceinline__ float2 t_sub2(float2 a, float2 b) {
-    float2 d;
-    asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n sub.rn.f32x2 rd, ra, rb;\n"
-        " mov.b64 {%0, %1}, rd;\n}\n" : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
-    return d;
-}
-__device__ __forceinline__ float2 t_mul2(float2 a, float2 b) {
-    float2 d;
-    asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n mul.rn.f32x2 rd, ra, rb;\n"
-        " mov.b64 {%0, %1}, rd;\n}\n" : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
-    return d;
-}
-__device__ __forceinline__ float2 t_fma2(float2 a, float2 b, float2 c) {
-    float2 d;
-    asm("{\n .reg .b64 ra, rb, rc, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n mov.b64 rc, {%6, %7};\n"
-        " fma.rn.f32x2 rd, ra, rb, rc;\n mov.b64 {%0, %1}, rd;\n}\n"
-        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
-    return d;
-}
-__device__ __forceinline__ float2 t_splat(float v) { return make_float2(v, v); }
-
-// One CTA per leaf of targets and split (blockIdx.y of gridDim.y: the split
-// takes that share of the leaf's far list and of its near list and writes its
-// own slice of partial sums), TREE_LEAF threads in two halves. A thread holds
-// two targets (the leaf's i-th and (i + TREE_LEAF/2)-th points) in packed
-// f32x2 arithmetic; the two halves take alternate sources of every staged
-// tile and add their sums through shared memory at the end.
-// Far: proxies of the well-separated clusters (kernel G with the interpolated
-// charges). Near: the other sources directly, with the direct pair kernel's
-// arithmetic (identical points skipped).
-constexpr int TREE_TPB = TREE_LEAF;
-constexpr int TREE_HALF = TREE_LEAF / 2;
-
+// The treecode's own launch: one CTA per leaf of targets and split
+// (blockIdx.y), TREE_LEAF threads in two groups (tree_leaf_body with NQ = 2).
 template <int MODE>
-__global__ void __launch_bounds__(TREE_TPB)
-k_tree_eval(int64_t np, int nprox, const int32_t* __restrict__ perm, const int32_t* __restrict__ leaf_rng,
-            const int32_t* __restrict__ far_ptr, const int32_t* __restrict__ far_idx,
-            const int32_t* __restrict__ near_ptr, const int32_t* __restrict__ near_rng,
-            const float* __restrict__ rec, const float* __restrict__ prox, TreeCoef cf, float* __restrict__ part) {
-    constexpr int NACC = MODE == 0 ? 2 : 10;
-    constexpr int TILE = 128;
-    __shared__ __align__(16) float tile[TILE * TREE_REC];
-    const int leaf = blockIdx.x;
-    const int sp = blockIdx.y, nsp = gridDim.y;
-    const int32_t fb0 = far_ptr[leaf], nfar = far_ptr[leaf + 1] - fb0;
-    const int32_t qb0 = near_ptr[leaf], nnear = near_ptr[leaf + 1] - qb0;
-    const int32_t fb = fb0 + (int32_t)((int64_t)nfar * sp / nsp), fe = fb0 + (int32_t)((int64_t)nfar * (sp + 1) / nsp);
-    const int32_t qb = qb0 + (int32_t)((int64_t)nnear * sp / nsp), qe = qb0 + (int32_t)((int64_t)nnear * (sp + 1) / nsp);
-    part += (int64_t)sp * NACC * np;
-    const int32_t tb = leaf_rng[2 * leaf], te = leaf_rng[2 * leaf + 1];
-    const int half = (int)threadIdx.x / TREE_HALF;
-    const int32_t ti0 = tb + (int32_t)(threadIdx.x % TREE_HALF), ti1 = ti0 + TREE_HALF;
-    const bool live0 = ti0 < te, live1 = ti1 < te;
-    float2 X0 = t_splat(0.f), X1 = X0, X2 = X0;
-    if (live0) {
-        X0.x = rec[TREE_REC * (int64_t)ti0];
-        X1.x = rec[TREE_REC * (int64_t)ti0 + 1];
-        X2.x = rec[TREE_REC * (int64_t)ti0 + 2];
-    }
-    if (live1) {
-        X0.y = rec[TREE_REC * (int64_t)ti1];
-        X1.y = rec[TREE_REC * (int64_t)ti1 + 1];
-        X2.y = rec[TREE_REC * (int64_t)ti1 + 2];
-    }
-    const float2 c00 = t_splat(cf.k[0][0]), c01 = t_splat(cf.k[0][1]), c02 = t_splat(cf.k[0][2]),
-                 c03 = t_splat(cf.k[0][3]), c10 = t_splat(cf.k[1][0]), c11 = t_splat(cf.k[1][1]),
-                 c12 = t_splat(cf.k[1][2]), c13 = t_splat(cf.k[1][3]), kap = t_splat(cf.kappa),
-                 mk2 = t_splat(cf.mk2);
-    float2 acc[NACC];
-    for (int k = 0; k < NACC; ++k) acc[k] = t_splat(0.f);
-    const bool any = live0;  // the first target of a thread is live whenever the second is
-    // far clusters through their proxies
-    for (int32_t f = fb; f < fe; ++f) {
-        const float* pr = prox + (int64_t)far_idx[f] * nprox * TREE_REC;
-        for (int c0 = 0; c0 < nprox; c0 += TILE) {
-            const int cnt = min(TILE, nprox - c0);
-            __syncthreads();
-            for (int k = threadIdx.x; k < cnt * TREE_REC / 4; k += blockDim.x)
-                reinterpret_cast<float4*>(tile)[k] = reinterpret_cast<const float4*>(pr + (int64_t)c0 * TREE_REC)[k];
-            __syncthreads();
-            if (!any) continue;
-#pragma unroll 2
-            for (int j = half; j < cnt; j += 2) {
-                const float* z = tile + TREE_REC * j;
-                const float2 d0 = t_sub2(X0, t_splat(z[0])), d1 = t_sub2(X1, t_splat(z[1])),
-                             d2 = t_sub2(X2, t_splat(z[2]));
-                const float2 r2 = t_fma2(d0, d0, t_fma2(d1, d1, t_mul2(d2, d2)));
-                const float2 rinv = make_float2(t_rsqrt(r2.x), t_rsqrt(r2.y));
-                const float2 rr = t_mul2(r2, rinv);
-                const float2 arg = t_mul2(rr, mk2);
-                const float2 e = make_float2(t_ex2(arg.x), t_ex2(arg.y));
-                const float2 gs = t_mul2(rinv, t_splat(z[3])), gq = t_mul2(rinv, t_splat(z[4]));
-                acc[0] = t_fma2(t_fma2(c01, e, c00), gs, acc[0]);
-                acc[0] = t_fma2(t_fma2(c03, e, c02), gq, acc[0]);
-                if (MODE == 0) {
-                    acc[1] = t_fma2(t_fma2(c11, e, c10), gs, acc[1]);
-                    acc[1] = t_fma2(t_fma2(c13, e, c12), gq, acc[1]);
-                } else {
-                    const float2 ek = t_fma2(e, t_mul2(rr, kap), e);
-                    const float2 ts = t_mul2(t_fma2(c13, ek, c12), t_mul2(t_mul2(rinv, rinv), gs));
-                    acc[1] = t_fma2(ts, d0, acc[1]);
-                    acc[2] = t_fma2(ts, d1, acc[2]);
-                    acc[3] = t_fma2(ts, d2, acc[3]);
-                    const float2 gc = t_mul2(t_fma2(c11, e, c10), rinv);
-                    acc[4] = t_fma2(gc, t_splat(z[5]), acc[4]);
-                    acc[5] = t_fma2(gc, t_splat(z[6]), acc[5]);
-                    acc[6] = t_fma2(gc, t_splat(z[7]), acc[6]);
-                    const float2 gb = t_mul2(e, rinv);
-                    acc[7] = t_fma2(gb, t_splat(z[8]), acc[7]);
-                    acc[8] = t_fma2(gb, t_splat(z[9]), acc[8]);
-                    acc[9] = t_fma2(gb, t_splat(z[10]), acc[9]);
-                }
-            }
-        }
-    }
-    // near sources directly (identical points skipped)
-    for (int32_t q = qb; q < qe; ++q) {
-        const int32_t sb = near_rng[2 * q], se = near_rng[2 * q + 1];
-        for (int32_t c0 = sb; c0 < se; c0 += TILE) {
-            const int cnt = min(TILE, se - c0);
-            __syncthreads();
-            for (int k = threadIdx.x; k < cnt * TREE_REC / 4; k += blockDim.x)
-                reinterpret_cast<float4*>(tile)[k] = reinterpret_cast<const float4*>(rec + (int64_t)c0 * TREE_REC)[k];
-            __syncthreads();
-            if (!any) continue;
-#pragma unroll 2
-            for (int j = half; j < cnt; j += 2) {
-                const float* y = tile + TREE_REC * j;
-                const float2 d0 = t_sub2(X0, t_splat(y[0])), d1 = t_sub2(X1, t_splat(y[1])),
-                             d2 = t_sub2(X2, t_splat(y[2]));
-                const float2 r2 = t_fma2(d0, d0, t_fma2(d1, d1, t_mul2(d2, d2)));
-                const float2 rinv = make_float2(r2.x > 0.f ? t_rsqrt(r2.x) : 0.f, r2.y > 0.f ? t_rsqrt(r2.y) : 0.f);
-                const float2 rr = t_mul2(r2, rinv);
-                const float2 arg = t_mul2(rr, mk2);
-                const float2 e = make_float2(t_ex2(arg.x), t_ex2(arg.y));
-                const float2 ek = t_fma2(e, t_mul2(rr, kap), e);
-                const float2 rinv3 = t_mul2(t_mul2(rinv, rinv), rinv);
-                const float2 dp = t_fma2(d0, t_splat(y[4]), t_fma2(d1, t_splat(y[5]), t_mul2(d2, t_splat(y[6]))));
-                const float2 rs = t_mul2(rinv, t_splat(y[3])), r3dp = t_mul2(rinv3, dp);
-                acc[0] = t_fma2(t_fma2(c01, e, c00), rs, acc[0]);
-                acc[0] = t_fma2(t_fma2(c03, ek, c02), r3dp, acc[0]);
-                if (MODE == 0) {
-                    acc[1] = t_fma2(t_fma2(c11, e, c10), rs, acc[1]);
-                    acc[1] = t_fma2(t_fma2(c13, ek, c12), r3dp, acc[1]);
-                } else {
-                    const float2 ts = t_mul2(t_fma2(c13, ek, c12), t_mul2(rinv3, t_splat(y[3])));
-                    acc[1] = t_fma2(ts, d0, acc[1]);
-                    acc[2] = t_fma2(ts, d1, acc[2]);
-                    acc[3] = t_fma2(ts, d2, acc[3]);
-                    const float2 gc = t_mul2(t_fma2(c11, e, c10), rinv);
-                    acc[4] = t_fma2(gc, t_splat(y[7]), acc[4]);
-                    acc[5] = t_fma2(gc, t_splat(y[8]), acc[5]);
-                    acc[6] = t_fma2(gc, t_splat(y[9]), acc[6]);
-                    const float2 gb = t_mul2(e, rinv);
-                    acc[7] = t_fma2(gb, t_splat(y[4]), acc[7]);
-                    acc[8] = t_fma2(gb, t_splat(y[5]), acc[8]);
-                    acc[9] = t_fma2(gb, t_splat(y[6]), acc[9]);
-                }
-            }
-        }
-    }
-    // the second half's sums join the first half's
-    static_assert(NACC * TREE_LEAF <= TILE * TREE_REC, "reduction buffer");
-    __syncthreads();
-    const int tl = (int)threadIdx.x % TREE_HALF;
-    if (half == 1)
-        for (int k = 0; k < NACC; ++k) {
-            tile[k * TREE_LEAF + tl] = acc[k].x;
-            tile[k * TREE_LEAF + TREE_HALF + tl] = acc[k].y;
-        }
-    __syncthreads();
-    if (half == 1) return;
-    for (int k = 0; k < NACC; ++k) {
-        acc[k].x += tile[k * TREE_LEAF + tl];
-        acc[k].y += tile[k * TREE_LEAF + TREE_HALF + tl];
-    }
-    if (live0) {
-        const int64_t pt = perm[ti0];
-        for (int k = 0; k < NACC; ++k) part[(int64_t)k * np + pt] = acc[k].x;
-    }
-    if (live1) {
-        const int64_t pt = perm[ti1];
-        for (int k = 0; k < NACC; ++k) part[(int64_t)k * np + pt] = acc[k].y;
-    }
+__global__ void __launch_bounds__(TREE_LEAF) k_tree_eval(TreeJob job) {
+    __shared__ __align__(16) float tile[TREE_EVAL_TILE * TREE_REC];
+    static_assert((MODE == 0 ? 2 : 10) * TREE_LEAF <= TREE_EVAL_TILE * TREE_REC, "reduction buffer");
+    tree_leaf_body<MODE, 2>(job, blockIdx.x, blockIdx.y, tile);
 }
 
 // y-part of the far field by the treecode: per-target partial sums in the
 // direct kernel's split layout (*nsplit slices in the mesh's ws_part, returned
 // in *part_out); builds the tree of the mesh on first use.
-int tree_far(const pb_mesh* mc, const FarPlan& fp, const double* x, bool need_u, bool need_v, float** part_out,
-             int* nsplit, cudaStream_t s) {
+int tree_prepare(const pb_mesh* mc, const FarPlan& fp, const double* x, bool need_u, bool need_v, TreeJob* job,
+                 cudaStream_t s) {
     pb_mesh* m = const_cast<pb_mesh*>(mc);
     pb_ctx* ctx = m->ctx;
     if (m->tree && (m->tree->n != ctx->tree_order + 1 || m->tree->theta != ctx->tree_theta)) {
@@ -720,31 +524,49 @@ int tree_far(const pb_mesh* mc, const FarPlan& fp, const double* x, bool need_u,
             ::pb::count_launch();
         }
     }
-    TreeCoef cf;
+    TreeJob& J = *job;
     for (int R = 0; R < 2; ++R)
-        for (int j = 0; j < 4; ++j) cf.k[R][j] = (float)fp.k[R][j];
-    cf.kappa = (float)fp.kappa;
-    cf.mk2 = (float)(-fp.kappa * 1.4426950408889634);
+        for (int j = 0; j < 4; ++j) J.cf.k[R][j] = (float)fp.k[R][j];
+    J.cf.kappa = (float)fp.kappa;
+    J.cf.mk2 = (float)(-fp.kappa * 1.4426950408889634);
     // splits of each leaf's lists, so that the grid holds about eight CTAs per SM
     const int nacc = fp.mode == 0 ? 2 : 10;
     const int S = (int)std::min<int64_t>(
         TREE_MAX_SPLITS, std::max<int64_t>(1, (8LL * std::max(1, ctx->num_sms) + t->nleaf - 1) / t->nleaf));
     PB_TRY(ws_reserve(m->ws_part, sizeof(float) * (size_t)S * nacc * np));
-    float* part = (float*)m->ws_part.ptr;
-    const dim3 grid((unsigned)t->nleaf, (unsigned)S);
-    Timer tm(ctx, PB_KERNEL_TREE32, s, (double)(t->direct_pairs + t->proxy_pairs),
-             fp.mode == 0 ? 25.0 : 36.0);
-    if (fp.mode == 0)
-        k_tree_eval<0><<<grid, TREE_TPB, 0, s>>>(np, t->nprox, t->perm, t->leaf_rng, t->far_ptr, t->far_idx,
-                                                 t->near_ptr, t->near_rng, rec, prox, cf, part);
-    else
-        k_tree_eval<1><<<grid, TREE_TPB, 0, s>>>(np, t->nprox, t->perm, t->leaf_rng, t->far_ptr, t->far_idx,
-                                                 t->near_ptr, t->near_rng, rec, prox, cf, part);
+    J.np = np;
+    J.nprox = t->nprox;
+    J.nsplit = S;
+    J.perm = t->perm;
+    J.leaf_rng = t->leaf_rng;
+    J.far_ptr = t->far_ptr;
+    J.far_idx = t->far_idx;
+    J.near_ptr = t->near_ptr;
+    J.near_rng = t->near_rng;
+    J.rec = rec;
+    J.prox = prox;
+    J.part = (float*)m->ws_part.ptr;
+    PB_CUDA(cudaGetLastError());
+    return PB_OK;
+}
+
+int64_t tree_interactions(const pb_mesh* m) { return m->tree ? m->tree->direct_pairs + m->tree->proxy_pairs : 0; }
+int64_t tree_leaves(const pb_mesh* m) { return m->tree ? m->tree->nleaf : 0; }
+
+int tree_far(const pb_mesh* m, const FarPlan& fp, const double* x, bool need_u, bool need_v, float** part_out,
+             int* nsplit, cudaStream_t s) {
+    TreeJob job;
+    PB_TRY(tree_prepare(m, fp, x, need_u, need_v, &job, s));
+    const PbTree* t = m->tree;
+    const dim3 grid((unsigned)t->nleaf, (unsigned)job.nsplit);
+    Timer tm(m->ctx, PB_KERNEL_TREE32, s, (double)(t->direct_pairs + t->proxy_pairs), fp.mode == 0 ? 25.0 : 36.0);
+    if (fp.mode == 0) k_tree_eval<0><<<grid, TREE_LEAF, 0, s>>>(job);
+    else k_tree_eval<1><<<grid, TREE_LEAF, 0, s>>>(job);
     ::pb::count_launch();
     tm.stop();
     PB_CUDA(cudaGetLastError());
-    *part_out = part;
-    *nsplit = S;
+    *part_out = job.part;
+    *nsplit = job.nsplit;
     return PB_OK;
 }
 

@@ -1,0 +1,248 @@
+// Treecode evaluation body (shared by the treecode's own launch and the
+// request server's persistent launch). Not part of the C ABI.
+#pragma once
+
+#include "internal.h"
+
+namespace pb {
+
+constexpr int TREE_LEAF = 128;     // targets per leaf
+constexpr int TREE_REC = 12;       // floats per tree source / proxy record
+constexpr int TREE_EVAL_TILE = 128;  // sources staged per round
+
+struct TreeCoef {
+    float k[2][4];
+    float kappa;
+    float mk2;  // -kappa log2(e)
+};
+
+__device__ __forceinline__ float t_rsqrt(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+__device__ __forceinline__ float t_ex2(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+__device__ __forceinline__ float2 t_sub2(float2 a, float2 b) {
+    float2 d;
+    asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n sub.rn.f32x2 rd, ra, rb;\n"
+        " mov.b64 {%0, %1}, rd;\n}\n" : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 t_mul2(float2 a, float2 b) {
+    float2 d;
+    asm("{\n .reg .b64 ra, rb, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n mul.rn.f32x2 rd, ra, rb;\n"
+        " mov.b64 {%0, %1}, rd;\n}\n" : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 t_fma2(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("{\n .reg .b64 ra, rb, rc, rd;\n mov.b64 ra, {%2, %3};\n mov.b64 rb, {%4, %5};\n mov.b64 rc, {%6, %7};\n"
+        " fma.rn.f32x2 rd, ra, rb, rc;\n mov.b64 {%0, %1}, rd;\n}\n"
+        : "=f"(d.x), "=f"(d.y) : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+__device__ __forceinline__ float2 t_splat(float v) { return make_float2(v, v); }
+
+
+// One evaluation job: a mesh's tree with its source and proxy records in
+// tree order, the kernel coefficients and the partial-sum slices.
+struct TreeJob {
+    int64_t np;
+    int nprox;
+    int nsplit;                 // slices of partial sums (the leaves' lists are cut into nsplit shares)
+    const int32_t* perm;        // tree index -> point index
+    const int32_t* leaf_rng;    // 2 per leaf
+    const int32_t* far_ptr;     // per leaf: its proxied clusters
+    const int32_t* far_idx;
+    const int32_t* near_ptr;    // per leaf: its directly summed source ranges
+    const int32_t* near_rng;
+    const float* rec;           // source records in tree order
+    const float* prox;          // proxy records per slot
+    float* part;                // nsplit x NACC x np
+    TreeCoef cf;
+};
+
+// One leaf of targets and one split of its lists, on 64 NQ threads: a thread
+// holds two targets (the leaf's i-th and (i + 64)-th points) in packed f32x2
+// arithmetic; the NQ thread groups of 64 take every NQ-th source of each staged
+// tile and add their sums through shared memory at the end, group 0 adding
+// groups 1 .. NQ-1 in that order. Far: proxies of the well-separated clusters
+// (kernel G with the interpolated charges). Near: the other sources directly,
+// with the direct pair kernel's arithmetic (identical points skipped).
+// `tile` holds at least TREE_EVAL_TILE x TREE_REC floats and
+// (NQ - 1) x NACC x TREE_LEAF floats. Every thread of the group calls it (it
+// synchronises the CTA) and returns; nothing is left in flight.
+template <int MODE, int NQ>
+__device__ __forceinline__ void tree_leaf_body(const TreeJob& T, int leaf, int sp, float* tile) {
+    constexpr int NACC = MODE == 0 ? 2 : 10;
+    constexpr int TILE = TREE_EVAL_TILE;
+    constexpr int HALF = TREE_LEAF / 2;
+    constexpr int NTH = HALF * NQ;
+    const int nsp = T.nsplit;
+    const int32_t fb0 = T.far_ptr[leaf], nfar = T.far_ptr[leaf + 1] - fb0;
+    const int32_t qb0 = T.near_ptr[leaf], nnear = T.near_ptr[leaf + 1] - qb0;
+    const int32_t fb = fb0 + (int32_t)((int64_t)nfar * sp / nsp), fe = fb0 + (int32_t)((int64_t)nfar * (sp + 1) / nsp);
+    const int32_t qb = qb0 + (int32_t)((int64_t)nnear * sp / nsp), qe = qb0 + (int32_t)((int64_t)nnear * (sp + 1) / nsp);
+    const int64_t np = T.np;
+    float* part = T.part + (int64_t)sp * NACC * np;
+    const float* rec = T.rec;
+    const int32_t tb = T.leaf_rng[2 * leaf], te = T.leaf_rng[2 * leaf + 1];
+    const int grp = (int)threadIdx.x / HALF;
+    const int32_t ti0 = tb + (int32_t)(threadIdx.x % HALF), ti1 = ti0 + HALF;
+    const bool live0 = ti0 < te, live1 = ti1 < te;
+    float2 X0 = t_splat(0.f), X1 = X0, X2 = X0;
+    if (live0) {
+        X0.x = rec[TREE_REC * (int64_t)ti0];
+        X1.x = rec[TREE_REC * (int64_t)ti0 + 1];
+        X2.x = rec[TREE_REC * (int64_t)ti0 + 2];
+    }
+    if (live1) {
+        X0.y = rec[TREE_REC * (int64_t)ti1];
+        X1.y = rec[TREE_REC * (int64_t)ti1 + 1];
+        X2.y = rec[TREE_REC * (int64_t)ti1 + 2];
+    }
+    const TreeCoef& cf = T.cf;
+    const float2 c00 = t_splat(cf.k[0][0]), c01 = t_splat(cf.k[0][1]), c02 = t_splat(cf.k[0][2]),
+                 c03 = t_splat(cf.k[0][3]), c10 = t_splat(cf.k[1][0]), c11 = t_splat(cf.k[1][1]),
+                 c12 = t_splat(cf.k[1][2]), c13 = t_splat(cf.k[1][3]), kap = t_splat(cf.kappa),
+                 mk2 = t_splat(cf.mk2);
+    float2 acc[NACC];
+    for (int k = 0; k < NACC; ++k) acc[k] = t_splat(0.f);
+    const bool any = live0;  // the first target of a thread is live whenever the second is
+    // far clusters through their proxies
+    for (int32_t f = fb; f < fe; ++f) {
+        const float* pr = T.prox + (int64_t)T.far_idx[f] * T.nprox * TREE_REC;
+        for (int c0 = 0; c0 < T.nprox; c0 += TILE) {
+            const int cnt = min(TILE, T.nprox - c0);
+            __syncthreads();
+            for (int k = threadIdx.x; k < cnt * TREE_REC / 4; k += NTH)
+                reinterpret_cast<float4*>(tile)[k] = reinterpret_cast<const float4*>(pr + (int64_t)c0 * TREE_REC)[k];
+            __syncthreads();
+            if (!any) continue;
+#pragma unroll 2
+            for (int j = grp; j < cnt; j += NQ) {
+                const float* z = tile + TREE_REC * j;
+                const float2 d0 = t_sub2(X0, t_splat(z[0])), d1 = t_sub2(X1, t_splat(z[1])),
+                             d2 = t_sub2(X2, t_splat(z[2]));
+                const float2 r2 = t_fma2(d0, d0, t_fma2(d1, d1, t_mul2(d2, d2)));
+                const float2 rinv = make_float2(t_rsqrt(r2.x), t_rsqrt(r2.y));
+                const float2 rr = t_mul2(r2, rinv);
+                const float2 arg = t_mul2(rr, mk2);
+                const float2 e = make_float2(t_ex2(arg.x), t_ex2(arg.y));
+                const float2 gs = t_mul2(rinv, t_splat(z[3])), gq = t_mul2(rinv, t_splat(z[4]));
+                acc[0] = t_fma2(t_fma2(c01, e, c00), gs, acc[0]);
+                acc[0] = t_fma2(t_fma2(c03, e, c02), gq, acc[0]);
+                if (MODE == 0) {
+                    acc[1] = t_fma2(t_fma2(c11, e, c10), gs, acc[1]);
+                    acc[1] = t_fma2(t_fma2(c13, e, c12), gq, acc[1]);
+                } else {
+                    const float2 ek = t_fma2(e, t_mul2(rr, kap), e);
+                    const float2 ts = t_mul2(t_fma2(c13, ek, c12), t_mul2(t_mul2(rinv, rinv), gs));
+                    acc[1] = t_fma2(ts, d0, acc[1]);
+                    acc[2] = t_fma2(ts, d1, acc[2]);
+                    acc[3] = t_fma2(ts, d2, acc[3]);
+                    const float2 gc = t_mul2(t_fma2(c11, e, c10), rinv);
+                    acc[4] = t_fma2(gc, t_splat(z[5]), acc[4]);
+                    acc[5] = t_fma2(gc, t_splat(z[6]), acc[5]);
+                    acc[6] = t_fma2(gc, t_splat(z[7]), acc[6]);
+                    const float2 gb = t_mul2(e, rinv);
+                    acc[7] = t_fma2(gb, t_splat(z[8]), acc[7]);
+                    acc[8] = t_fma2(gb, t_splat(z[9]), acc[8]);
+                    acc[9] = t_fma2(gb, t_splat(z[10]), acc[9]);
+                }
+            }
+        }
+    }
+    // near sources directly (identical points skipped)
+    for (int32_t q = qb; q < qe; ++q) {
+        const int32_t sb = T.near_rng[2 * q], se = T.near_rng[2 * q + 1];
+        for (int32_t c0 = sb; c0 < se; c0 += TILE) {
+            const int cnt = min(TILE, se - c0);
+            __syncthreads();
+            for (int k = threadIdx.x; k < cnt * TREE_REC / 4; k += NTH)
+                reinterpret_cast<float4*>(tile)[k] = reinterpret_cast<const float4*>(rec + (int64_t)c0 * TREE_REC)[k];
+            __syncthreads();
+            if (!any) continue;
+#pragma unroll 2
+            for (int j = grp; j < cnt; j += NQ) {
+                const float* y = tile + TREE_REC * j;
+                const float2 d0 = t_sub2(X0, t_splat(y[0])), d1 = t_sub2(X1, t_splat(y[1])),
+                             d2 = t_sub2(X2, t_splat(y[2]));
+                const float2 r2 = t_fma2(d0, d0, t_fma2(d1, d1, t_mul2(d2, d2)));
+                const float2 rinv = make_float2(r2.x > 0.f ? t_rsqrt(r2.x) : 0.f, r2.y > 0.f ? t_rsqrt(r2.y) : 0.f);
+                const float2 rr = t_mul2(r2, rinv);
+                const float2 arg = t_mul2(rr, mk2);
+                const float2 e = make_float2(t_ex2(arg.x), t_ex2(arg.y));
+                const float2 ek = t_fma2(e, t_mul2(rr, kap), e);
+                const float2 rinv3 = t_mul2(t_mul2(rinv, rinv), rinv);
+                const float2 dp = t_fma2(d0, t_splat(y[4]), t_fma2(d1, t_splat(y[5]), t_mul2(d2, t_splat(y[6]))));
+                const float2 rs = t_mul2(rinv, t_splat(y[3])), r3dp = t_mul2(rinv3, dp);
+                acc[0] = t_fma2(t_fma2(c01, e, c00), rs, acc[0]);
+                acc[0] = t_fma2(t_fma2(c03, ek, c02), r3dp, acc[0]);
+                if (MODE == 0) {
+                    acc[1] = t_fma2(t_fma2(c11, e, c10), rs, acc[1]);
+                    acc[1] = t_fma2(t_fma2(c13, ek, c12), r3dp, acc[1]);
+                } else {
+                    const float2 ts = t_mul2(t_fma2(c13, ek, c12), t_mul2(rinv3, t_splat(y[3])));
+                    acc[1] = t_fma2(ts, d0, acc[1]);
+                    acc[2] = t_fma2(ts, d1, acc[2]);
+                    acc[3] = t_fma2(ts, d2, acc[3]);
+                    const float2 gc = t_mul2(t_fma2(c11, e, c10), rinv);
+                    acc[4] = t_fma2(gc, t_splat(y[7]), acc[4]);
+                    acc[5] = t_fma2(gc, t_splat(y[8]), acc[5]);
+                    acc[6] = t_fma2(gc, t_splat(y[9]), acc[6]);
+                    const float2 gb = t_mul2(e, rinv);
+                    acc[7] = t_fma2(gb, t_splat(y[4]), acc[7]);
+                    acc[8] = t_fma2(gb, t_splat(y[5]), acc[8]);
+                    acc[9] = t_fma2(gb, t_splat(y[6]), acc[9]);
+                }
+            }
+        }
+    }
+    // the other groups' sums join group 0's, in group order
+    __syncthreads();
+    const int tl = (int)threadIdx.x % HALF;
+    if (grp > 0) {
+        float* slot = tile + (grp - 1) * NACC * TREE_LEAF;
+        for (int k = 0; k < NACC; ++k) {
+            slot[k * TREE_LEAF + tl] = acc[k].x;
+            slot[k * TREE_LEAF + HALF + tl] = acc[k].y;
+        }
+    }
+    __syncthreads();
+    if (grp == 0) {
+        for (int g2 = 1; g2 < NQ; ++g2) {
+            const float* slot = tile + (g2 - 1) * NACC * TREE_LEAF;
+            for (int k = 0; k < NACC; ++k) {
+                acc[k].x += slot[k * TREE_LEAF + tl];
+                acc[k].y += slot[k * TREE_LEAF + HALF + tl];
+            }
+        }
+        if (live0) {
+            const int64_t pt = T.perm[ti0];
+            for (int k = 0; k < NACC; ++k) part[(int64_t)k * np + pt] = acc[k].x;
+        }
+        if (live1) {
+            const int64_t pt = T.perm[ti1];
+            for (int k = 0; k < NACC; ++k) part[(int64_t)k * np + pt] = acc[k].y;
+        }
+    }
+    __syncthreads();  // the buffer is free for the caller
+}
+
+// host side (tree.cu): the mesh's tree built if needed, its source records and
+// proxy charges computed on stream s for the far-field plan fp and the
+// coefficients x, and the evaluation job described (partial sums in the mesh's
+// ws_part, nsplit slices).
+int tree_prepare(const pb_mesh* m, const FarPlan& fp, const double* x, bool need_u, bool need_v, TreeJob* job,
+                 cudaStream_t s);
+// pairs of one application (direct + proxy) and leaves, for cost estimates
+int64_t tree_interactions(const pb_mesh* m);
+int64_t tree_leaves(const pb_mesh* m);
+
+}  // namespace pb
