@@ -17,14 +17,29 @@ int rhs_coefs(const pb_params* prm, int form, double alpha, double beta, double 
 
 constexpr int QTILE = 256;
 
+// 1/sqrt(x) in FP64 for x in the normal FP32 range (squared distances here):
+// the FP32 hardware estimate (relative error below 2^-22) refined by two
+// Newton steps for f(y) = y^-2 - x, y <- y + y (1 - x y^2) / 2; each step squares
+// the relative error (2^-44, then rounding level), about 2 ulp in all.
+__device__ __forceinline__ double rsqrt_nr(double x) {
+    float yf;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(__double2float_rn(x)));
+    double y = (double)yf;
+    double e = __fma_rn(-(x * y), y, 1.0);
+    y = __fma_rn(0.5 * y, e, y);
+    e = __fma_rn(-(x * y), y, 1.0);
+    return __fma_rn(0.5 * y, e, y);
+}
+
 // per point: phi_D and phi_N of all charges, then per triangle the tested sums
+// (templated on the rule's point count, so that the per-point sums stay in registers)
+template <int Q>
 __global__ void k_rhs_points(int64_t nt, Rule rule, const double* __restrict__ pts64, const double* __restrict__ tgeo,
                              const double* __restrict__ xq, const double* __restrict__ q, int64_t nq, double eps_int,
                              double* __restrict__ tri_out) {
     __shared__ double sq[QTILE * 4];
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     bool live = t < nt;
-    const int Q = rule.Q;
     double pd[6] = {0, 0, 0, 0, 0, 0}, pn[6] = {0, 0, 0, 0, 0, 0};
     double nx = 0, ny = 0, nz = 0;
     if (live) { nx = tgeo[16 * t]; ny = tgeo[16 * t + 1]; nz = tgeo[16 * t + 2]; }
@@ -38,12 +53,13 @@ __global__ void k_rhs_points(int64_t nt, Rule rule, const double* __restrict__ p
         }
         __syncthreads();
         if (live)
+#pragma unroll
             for (int k = 0; k < Q; ++k) {
                 const double* x = pts64 + 4 * (t * Q + k);
                 for (int j = 0; j < cnt; ++j) {
                     double d0 = x[0] - sq[4 * j], d1 = x[1] - sq[4 * j + 1], d2 = x[2] - sq[4 * j + 2];
                     double r2 = d0 * d0 + d1 * d1 + d2 * d2;
-                    double rinv = 1.0 / sqrt(r2);
+                    double rinv = rsqrt_nr(r2);
                     double c = sq[4 * j + 3] * rinv;
                     pd[k] += c;
                     pn[k] -= c * rinv * rinv * (d0 * nx + d1 * ny + d2 * nz);
@@ -54,6 +70,7 @@ __global__ void k_rhs_points(int64_t nt, Rule rule, const double* __restrict__ p
     if (!live) return;
     const double f = 1.0 / (4.0 * M_PI * eps_int);
     double out[6] = {0, 0, 0, 0, 0, 0};
+#pragma unroll
     for (int k = 0; k < Q; ++k) {
         double w = pts64[4 * (t * Q + k) + 3] * f;
         for (int a = 0; a < 3; ++a) {
@@ -81,35 +98,52 @@ __global__ void k_rhs_gather(int64_t nv, const int32_t* __restrict__ v2t_ptr, co
     rhs[nv + i] = d1 * bd + n1 * bn;
 }
 
-// phi_reac partial sums: grid (chunks, charges)
+// phi_reac: the interior traces at every point of the reference rule once
+// (position, w v_int and w u_int n_y), then per charge and chunk of points the
+// partial sums of G_L v - dG_L/dn_y u (1/(4 pi) applied at the end).
 constexpr int EN_THREADS = 256;
 constexpr int EN_CHUNK = 8192;
 
-__global__ void k_energy_part(int64_t nt, Rule rule, const int32_t* __restrict__ tris, const double* __restrict__ tgeo,
-                              const double* __restrict__ pts64, const double* __restrict__ x, int64_t nv,
-                              double vscale, const double* __restrict__ xq, double* __restrict__ part, int nchunk) {
-    __shared__ double red[EN_THREADS / 32];
+__global__ void k_energy_points(int64_t nt, Rule rule, const int32_t* __restrict__ tris,
+                                const double* __restrict__ tgeo, const double* __restrict__ pts64,
+                                const double* __restrict__ x, int64_t nv, double vscale, double* __restrict__ pv) {
     const int Q = rule.Q;
-    const int64_t np = nt * Q;
-    int c = blockIdx.x;
-    int64_t j = blockIdx.y;
-    double qx = xq[3 * j], qy = xq[3 * j + 1], qz = xq[3 * j + 2];
-    int64_t i0 = (int64_t)c * EN_CHUNK, i1 = min(np, i0 + EN_CHUNK);
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nt * Q) return;
+    const int64_t t = i / Q;
+    const int k = (int)(i - t * Q);
+    const int32_t* f = tris + 3 * t;
+    const double u = rule.l[k][0] * x[f[0]] + rule.l[k][1] * x[f[1]] + rule.l[k][2] * x[f[2]];
+    const double v = vscale * (rule.l[k][0] * x[nv + f[0]] + rule.l[k][1] * x[nv + f[1]] + rule.l[k][2] * x[nv + f[2]]);
+    const double* y = pts64 + 4 * i;
+    const double* g = tgeo + 16 * t;
+    double* o = pv + 8 * i;
+    o[0] = y[0];
+    o[1] = y[1];
+    o[2] = y[2];
+    o[3] = y[3] * v;
+    o[4] = y[3] * u * g[0];
+    o[5] = y[3] * u * g[1];
+    o[6] = y[3] * u * g[2];
+    o[7] = 0.0;
+}
+
+__global__ void k_energy_part(int64_t np, const double* __restrict__ pv, const double* __restrict__ xq,
+                              double* __restrict__ part, int nchunk) {
+    __shared__ double red[EN_THREADS / 32];
+    const int c = blockIdx.x;
+    const int64_t j = blockIdx.y;
+    const double qx = xq[3 * j], qy = xq[3 * j + 1], qz = xq[3 * j + 2];
+    const int64_t i0 = (int64_t)c * EN_CHUNK, i1 = min(np, i0 + EN_CHUNK);
     double s = 0.0;
     for (int64_t i = i0 + threadIdx.x; i < i1; i += EN_THREADS) {
-        int64_t t = i / Q;
-        int k = (int)(i - t * Q);
-        const int32_t* f = tris + 3 * t;
-        double u = rule.l[k][0] * x[f[0]] + rule.l[k][1] * x[f[1]] + rule.l[k][2] * x[f[2]];
-        double v = vscale * (rule.l[k][0] * x[nv + f[0]] + rule.l[k][1] * x[nv + f[1]] + rule.l[k][2] * x[nv + f[2]]);
-        const double* y = pts64 + 4 * i;
-        double d0 = qx - y[0], d1 = qy - y[1], d2 = qz - y[2];
-        double r2 = d0 * d0 + d1 * d1 + d2 * d2;
-        double rinv = 1.0 / sqrt(r2);
-        const double* g = tgeo + 16 * t;
-        double dn = d0 * g[0] + d1 * g[1] + d2 * g[2];
-        // G_L v - dG_L/dn_y u, with 1/(4 pi) applied at the end
-        s += y[3] * (rinv * v - rinv * rinv * rinv * dn * u);
+        const double4 a = *reinterpret_cast<const double4*>(pv + 8 * i);
+        const double4 b = *reinterpret_cast<const double4*>(pv + 8 * i + 4);
+        const double d0 = qx - a.x, d1 = qy - a.y, d2 = qz - a.z;
+        const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
+        const double rinv = rsqrt_nr(r2);
+        const double dn = d0 * b.x + d1 * b.y + d2 * b.z;  // w u (x_j - y).n_y
+        s += rinv * a.w - rinv * rinv * rinv * dn;
     }
     for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
     if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
@@ -121,14 +155,20 @@ __global__ void k_energy_part(int64_t nt, Rule rule, const int32_t* __restrict__
     }
 }
 
-__global__ void k_energy_final(int64_t nq, int nchunk, const double* __restrict__ part, const double* __restrict__ q,
+// phi_reac(x_j) per charge (its chunks in order), then Delta G by one thread
+// over the charges in order: the summation order is fixed.
+__global__ void k_energy_rows(int64_t nq, int nchunk, const double* __restrict__ part, double* __restrict__ phi) {
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= nq) return;
+    double p = 0.0;
+    for (int c = 0; c < nchunk; ++c) p += part[j * nchunk + c];
+    phi[j] = p * (1.0 / (4.0 * M_PI));
+}
+__global__ void k_energy_final(int64_t nq, const double* __restrict__ phi_all, const double* __restrict__ q,
                                double* __restrict__ phi, double* __restrict__ dG) {
-    // one thread: fixed summation order
     double e = 0.0;
     for (int64_t j = 0; j < nq; ++j) {
-        double p = 0.0;
-        for (int c = 0; c < nchunk; ++c) p += part[j * nchunk + c];
-        p *= 1.0 / (4.0 * M_PI);
+        const double p = phi_all[j];
         if (phi) phi[j] = p;
         e += q[j] * p;
     }
@@ -149,8 +189,12 @@ extern "C" int pb_rhs_charges(pb_ctx* ctx, const pb_mesh* m, const double* xq, c
     PB_TRY(ws_reserve(const_cast<pb_mesh*>(m)->ws_tri, sizeof(double) * 6 * m->nt));
     double* tri = (double*)m->ws_tri.ptr;
     // the plan's reference rule (the band rule when the plan has a band)
-    k_rhs_points<<<(unsigned)((m->nt + 127) / 128), 128, 0, s>>>(m->nt, mesh_ref_rule(m), m->pts_ref, m->tgeo, xq, q,
-                                                                n_q, prm->eps_int, tri); ::pb::count_launch();
+    const Rule rr = mesh_ref_rule(m);
+    const unsigned nbk = (unsigned)((m->nt + 127) / 128);
+    if (rr.Q == 6) k_rhs_points<6><<<nbk, 128, 0, s>>>(m->nt, rr, m->pts_ref, m->tgeo, xq, q, n_q, prm->eps_int, tri);
+    else if (rr.Q == 3) k_rhs_points<3><<<nbk, 128, 0, s>>>(m->nt, rr, m->pts_ref, m->tgeo, xq, q, n_q, prm->eps_int, tri);
+    else k_rhs_points<1><<<nbk, 128, 0, s>>>(m->nt, rr, m->pts_ref, m->tgeo, xq, q, n_q, prm->eps_int, tri);
+    ::pb::count_launch();
     k_rhs_gather<<<(unsigned)((m->nv + 255) / 256), 256, 0, s>>>(m->nv, m->v2t_ptr, m->v2t, tri, d[0], d[1], n[0],
                                                                 n[1], rhs); ::pb::count_launch();
     PB_CUDA(cudaGetLastError());
@@ -168,12 +212,20 @@ extern "C" int pb_energy(pb_ctx* ctx, const pb_mesh* m, const double* x, int for
     double vscale = form_is_exterior(form) ? prm->eps_ext / prm->eps_int : 1.0;
     int nchunk = (int)((m->np_ref + EN_CHUNK - 1) / EN_CHUNK);
     double* part = nullptr;
-    PB_TRY(dev_alloc((void**)&part, sizeof(double) * (n_q * nchunk + 1)));
-    double* dG = part + n_q * nchunk;
+    // partial sums, phi per charge, Delta G, then the point values (32-byte aligned)
+    const size_t n_part = (size_t)n_q * nchunk, n_head = (n_part + 2 * (size_t)n_q + 1 + 3) / 4 * 4;
+    PB_TRY(dev_alloc((void**)&part, sizeof(double) * (n_head + 8 * (size_t)m->np_ref)));
+    double* phi_all = part + n_part;
+    double* dG = phi_all + n_q;
+    double* pv = part + n_head;
+    const Rule rr = mesh_ref_rule(m);
+    k_energy_points<<<(unsigned)((m->np_ref + 255) / 256), 256, 0, s>>>(m->nt, rr, m->tris, m->tgeo, m->pts_ref, x,
+                                                                         m->nv, vscale, pv);
     dim3 grid(nchunk, (unsigned)n_q);
-    k_energy_part<<<grid, EN_THREADS, 0, s>>>(m->nt, mesh_ref_rule(m), m->tris, m->tgeo, m->pts_ref, x, m->nv, vscale,
-                                            xq, part, nchunk); ::pb::count_launch();
-    k_energy_final<<<1, 1, 0, s>>>(n_q, nchunk, part, q, phi, dG); ::pb::count_launch();
+    k_energy_part<<<grid, EN_THREADS, 0, s>>>(m->np_ref, pv, xq, part, nchunk);
+    k_energy_rows<<<(unsigned)((n_q + 127) / 128), 128, 0, s>>>(n_q, nchunk, part, phi_all);
+    k_energy_final<<<1, 1, 0, s>>>(n_q, phi_all, q, phi, dG);
+    ::pb::count_launch(4);
     double h = 0.0;
     cudaError_t e = cudaMemcpyAsync(&h, dG, sizeof(double), cudaMemcpyDeviceToHost, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
