@@ -68,6 +68,8 @@ def parse():
                          "molecules' default, where an FP64 direct far field is out of reach)")
     ap.add_argument("--ref-tol", type=float, default=1e-10)
     ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--inner-tol", type=float, default=1e-4,
+                    help="relative tolerance of each FP32 inner solve of the mixed-precision refinement")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-baseline", action="store_true")
     ap.add_argument("--no-check", action="store_true", help="skip the FP64 accuracy solve (profiling runs)")
@@ -88,6 +90,10 @@ def parse():
                          "far rule, 3 singular Gauss points), the paper's Cases 20b/23b")
     ap.add_argument("--plan-tol", type=float, default=1e-6)
     ap.add_argument("--no-tune", action="store_true", help="skip the launch autotuner (default launches)")
+    ap.add_argument("--tune", action="store_true", help="with --bare: run the launch autotuner all the same")
+    ap.add_argument("--bare", action="store_true",
+                    help="profiling runs (ncu): only the warm-up and timed solves, no peaks, tuning, accuracy "
+                         "reference, matvec rates, e2e or CPU baseline")
     ap.add_argument("--serve", type=int, default=0,
                     help="serving benchmark on the first N requests of the seeded request stream instead")
     ap.add_argument("--rate-scale", type=float, default=0.7,
@@ -332,7 +338,7 @@ def run_ours(args, rank, world, local_rank):
     form, prec = pb.CASES[args.case]
     P = pb.Params(4.0, 80.0, 0.125)
     precision = pb.PB_MIXED if args.precision == "mixed" else pb.PB_F64
-    opts = pb.solve_opts(tol=args.tol, max_it=400, precision=precision, inner_tol=1e-4)
+    opts = pb.solve_opts(tol=args.tol, max_it=400, precision=precision, inner_tol=args.inner_tol)
     ctx = pb.pb_init(local_rank)
     if args.no_graphs:
         pb.pb_set_graphs(ctx, False)
@@ -401,8 +407,9 @@ def run_ours(args, rank, world, local_rank):
 
     # arithmetic issue rates by microbenchmark (FMAs per second), beside the unit-count peaks the
     # rooflines use
-    alu_peaks = {"fp32_fma_per_s": pb.pb_measure_peak(ctx, 0), "fp64_fma_per_s": pb.pb_measure_peak(ctx, 1),
-                 "f32x2_fma_per_s": pb.pb_measure_peak(ctx, 2)}
+    alu_peaks = {} if args.bare else {"fp32_fma_per_s": pb.pb_measure_peak(ctx, 0),
+                                      "fp64_fma_per_s": pb.pb_measure_peak(ctx, 1),
+                                      "f32x2_fma_per_s": pb.pb_measure_peak(ctx, 2)}
 
     # warm-up (untimed)
     for _ in range(args.warmup):
@@ -448,7 +455,7 @@ def run_ours(args, rank, world, local_rank):
 
     uses_tree = args.far == "tree" or (args.far == "auto" and npts >= 50000)
     tree_mv = None
-    if uses_tree:
+    if uses_tree and not args.bare:
         tree_ms = time_apply(10)
         ti = pb.pb_tree_info(m)
         inter = float(ti["direct_pairs"] + ti["proxy_pairs"])
@@ -458,8 +465,8 @@ def run_ours(args, rank, world, local_rank):
                    "note": "interactions = direct point pairs + point-proxy pairs of one application; the "
                            "system application (sources, reduction, gather, near SpMV included) timed whole"}
         pb.pb_set_treecode(ctx, False)
-    direct_ms = time_apply(3 if npts > 300000 else 10)
-    if uses_tree:
+    direct_ms = time_apply(3 if npts > 300000 else 10) if not args.bare else float("nan")
+    if uses_tree and not args.bare:
         if args.far == "tree":
             pb.pb_set_treecode(ctx, True, 6, 0.7, 0)
         else:
@@ -585,7 +592,7 @@ def run_ours(args, rank, world, local_rank):
         "config": {"workload": workload_text(args, v, t, xq),
                    "n_verts": int(v.shape[0]), "n_tris": int(t.shape[0]), "n_charges": int(xq.shape[0]),
                    "case": args.case, "formulation": form, "preconditioner": prec, "precision": args.precision,
-                   "gmres_tol": args.tol, "quadrature": plan_text(plan),
+                   "gmres_tol": args.tol, "inner_tol": args.inner_tol, "quadrature": plan_text(plan),
                    "plan": dict(plan, tuned=args.plan == "auto", tol_dG=args.plan_tol if args.plan == "auto" else None,
                                 dG_change_vs_reference_plan=plan_change),
                    "points": npts, "launch_tuning": launch_tuning,
@@ -744,6 +751,10 @@ def run_serving(args, rank, local_rank):
 
 def main():
     args = parse()
+    if args.bare:
+        args.no_tune = not args.tune
+        args.no_e2e = args.no_baseline = True
+        args.check = "none"
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
