@@ -96,6 +96,9 @@ def parse():
                          "reference, matvec rates, e2e or CPU baseline")
     ap.add_argument("--serve", type=int, default=0,
                     help="serving benchmark on the first N requests of the seeded request stream instead")
+    ap.add_argument("--serve-sample", type=int, default=64,
+                    help="requests of the serving stream measured after the timed solves and reported under "
+                         "'serving' in the line (closed batch, Poisson arrivals, sequential; 0: none; 1 GPU only)")
     ap.add_argument("--rate-scale", type=float, default=0.7,
                     help="serving: Poisson arrival rate as a fraction of the closed-batch solve rate")
     return ap.parse_args()
@@ -622,6 +625,12 @@ def run_ours(args, rank, world, local_rank):
     if not args.no_baseline:
         sec, cores, text = oracle_sample(v, t, xq, q, args.case)
         line["cpu_baseline"] = {"value": 1.0 / sec, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": text}
+    if args.serve_sample > 0 and world == 1 and not args.bare:
+        # the request server on the first requests of the seeded serving stream (outside the timed region)
+        try:
+            line["serving"] = serving_record(args, args.serve_sample, local_rank, full=False)
+        except Exception as e:  # the main measurement stands on its own
+            line["serving"] = {"error": str(e)[:300]}
     print(json.dumps(line), flush=True)
 
 
@@ -632,16 +641,18 @@ def _build_request(spec):
     return spec, v, t, xq, q
 
 
-def run_serving(args, rank, local_rank):
-    """Continuous batching through the request server on the first N requests
+def serving_record(args, n_req, local_rank, full=True):
+    """Continuous batching through the request server on the first n_req requests
     of the seeded stream (atom counts log-uniform in 50-3000, cases 2/10/12/23):
     a closed batch gives the sustainable rate R; then Poisson arrivals at
     rate_scale * R give the latency distribution; the same requests solved one
-    at a time (pb_solve, same precision) are the sequential comparison."""
+    at a time (pb_solvation_energy, same precision and plan) are the sequential
+    comparison. With full, also the plan's Delta G change on the three smallest
+    requests and the sequential FP64 rate (a stratified subset, extrapolated)."""
     import multiprocessing as mp
 
     from synth import serving_stream
-    specs = serving_stream(512, 5)[:args.serve]
+    specs = serving_stream(512, 5)[:n_req]
     with mp.get_context("spawn").Pool(max(1, min(16, (os.cpu_count() or 2)))) as pool:
         reqs = pool.map(_build_request, specs)
     import torch
@@ -695,6 +706,17 @@ def run_serving(args, rank, local_rank):
     torch.cuda.synchronize()
     span_s = time.perf_counter() - t0
     tris = np.array([r[2].shape[0] for r in reqs])
+    ok = all(opened[i]["status"] == 0 for i in range(len(reqs)))
+    same = all(opened[i]["dG_kcal"] == closed[i]["dG_kcal"] for i in range(len(reqs)))
+    rec = {"requests": len(reqs), "tris_min": int(tris.min()), "tris_max": int(tris.max()),
+           "closed_batch_solves_per_s": rate, "sequential_solves_per_s": len(reqs) / span_s,
+           "open_arrivals_solves_per_s": len(reqs) / span_o, "arrival_rate_fraction": args.rate_scale,
+           "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                          "max": float(lat.max())},
+           "all_converged": ok, "identical_open_vs_closed": same, "hbm_budget_bytes": budget, "max_active": 64,
+           "quadrature": plan_text(plan)}
+    if not full:
+        return rec
     # the plan's Delta G change against the reference plan on the three smallest requests
     tight = pb.solve_opts(tol=1e-9, max_it=600, precision=pb.PB_F64)
     plan_change = 0.0
@@ -729,23 +751,24 @@ def run_serving(args, rank, local_rank):
         seq64 = {"solves_per_s": len(reqs) / total64, "extrapolated": True, "timed_requests": len(tt),
                  "timed_tris": [int(x) for x in nn], "timed_s": tt, "fit": "t = c0 + c2 N_t^2",
                  "c0_s": float(c0), "c2_s": float(c2)}
+    rec["sequential_f64_gpu"] = seq64
+    rec["plan_dG_change_vs_reference_max_of_3"] = plan_change
+    return rec
+
+
+def run_serving(args, rank, local_rank):
+    """The serving benchmark alone (bench.py --serve N): one JSON line."""
+    rec = serving_record(args, args.serve, local_rank, full=True)
     if rank != 0:
         return
-    ok = all(opened[i]["status"] == 0 for i in range(len(reqs)))
-    same = all(opened[i]["dG_kcal"] == closed[i]["dG_kcal"] for i in range(len(reqs)))
-    line = {"metric": "PB solves/s and p50/p99 latency (serving stream)", "value": len(reqs) / span_o,
-            "unit": "solves/s", "n_gpus": 1, "steps": len(reqs), "warmup": 0, "higher_is_better": True,
+    line = {"metric": "PB solves/s and p50/p99 latency (serving stream)", "value": rec["open_arrivals_solves_per_s"],
+            "unit": "solves/s", "n_gpus": 1, "steps": rec["requests"], "warmup": 0, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": "serving stream: first %d of 512 seeded requests, atoms log-uniform in 50-3000 "
                                    "(%d-%d tris), cases 2/10/12/23, Poisson arrivals at %.2f x the closed-batch rate"
-                                   % (len(reqs), tris.min(), tris.max(), args.rate_scale),
-                       "hbm_budget_bytes": budget, "max_active": 64, "gmres_tol": 1e-6, "precision": "mixed",
-                       "quadrature": plan_text(plan), "plan_dG_change_vs_reference_max_of_3": plan_change},
-            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                           "max": float(lat.max())},
-            "closed_batch_solves_per_s": rate, "sequential_solves_per_s": len(reqs) / span_s,
-            "sequential_f64_gpu": seq64,
-            "all_converged": ok, "identical_open_vs_closed": same}
+                                   % (rec["requests"], rec["tris_min"], rec["tris_max"], args.rate_scale),
+                       "gmres_tol": 1e-6, "precision": "mixed"},
+            "serving": rec}
     print(json.dumps(line), flush=True)
 
 
