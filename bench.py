@@ -376,6 +376,8 @@ def run_ours(args, rank, world, local_rank):
 
     fast = args.fast_calderon and prec.startswith(("calderon", "scaled_calderon"))
     PC_PLAN = {"far_q": 1, "n_ss": 3}
+    # the charge sums' arithmetic: FP32 on split coordinates with FP64 tile sums in the mixed path
+    cprec = pb.PB_F32_ACCURATE if precision == pb.PB_MIXED else pb.PB_F64
 
     def step(vv=None, tt=None, qx=None, qq=None):
         """One solve; with host arrays (e2e) the mesh and charges go up and Delta G comes back inside."""
@@ -387,20 +389,20 @@ def run_ours(args, rank, world, local_rank):
             # the first set is the workload's charges; the others seeded variations of them
             qs = [qq] + [qq * (1.0 + 0.5 * torch.as_tensor(np.random.default_rng(100 + k).standard_normal(qq.shape[0]),
                                                            device=dev)) for k in range(1, args.rhs)]
-            R = torch.stack([pb.pb_rhs_charges(ctx, m, qx, qk, P, form) for qk in qs])
+            R = torch.stack([pb.pb_rhs_charges(ctx, m, qx, qk, P, form, prec=cprec) for qk in qs])
             X, infos = pb.pb_solve_many(ctx, m, nf, P, form, prec, R, opts=opts)
-            dGk = [pb.pb_energy(ctx, m, X[k], form, qx, qs[k], P)[1] for k in range(args.rhs)][0]
+            dGk = [pb.pb_energy(ctx, m, X[k], form, qx, qs[k], P, prec=cprec)[1] for k in range(args.rhs)][0]
             nf.free()
             m.free()
             return dGk, infos[0]
-        rhs = pb.pb_rhs_charges(ctx, m, qx, qq, P, form)
+        rhs = pb.pb_rhs_charges(ctx, m, qx, qq, P, form, prec=cprec)
         if fast:
             mc = pb.pb_mesh_load(ctx, vv, tt, **PC_PLAN)
             nc = pb.pb_near_build(ctx, mc, P.kappa)
             x, info = pb.pb_solve_pc(ctx, m, nf, mc, nc, P, form, prec, rhs, opts=opts)
         else:
             x, info = pb.pb_solve(ctx, m, nf, P, form, prec, rhs, opts=opts)
-        dG, dGk = pb.pb_energy(ctx, m, x, form, qx, qq, P)
+        dG, dGk = pb.pb_energy(ctx, m, x, form, qx, qq, P, prec=cprec)
         if fast:
             nc.free()
             mc.free()
@@ -425,7 +427,7 @@ def run_ours(args, rank, world, local_rank):
         check = "f64" if args.workload == "sphere" else "refined"
     m = pb.pb_mesh_load(ctx, dv, dt, **plan)
     nf = pb.pb_near_build(ctx, m, P.kappa)
-    rhs = pb.pb_rhs_charges(ctx, m, dxq, dq, P, form)
+    rhs = pb.pb_rhs_charges(ctx, m, dxq, dq, P, form)  # the reference in FP64 charge sums
     dG_ref, ref_info = None, None
     if check == "f64":
         xr, ref_info = pb.pb_solve(ctx, m, nf, P, form, prec, rhs, opts=pb.solve_opts(tol=1e-8, max_it=600))

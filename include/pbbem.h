@@ -240,10 +240,14 @@ int pb_system_apply_noalloc(pb_ctx* ctx, const pb_mesh* mesh, const pb_near* nea
 /* ---- a6: right-hand side ------------------------------------------------ */
 /* rhs = the formulation's right-hand side built from the source projections
  * (paper eq. sources: phi_D = sum_j q_j/(4 pi eps_int |x - x_j|), phi_N its
- * normal derivative), tested against the P1 basis with the far rule.
- * xq (n_q x 3) and q (n_q) are device arrays; rhs is device, 2*N_v. */
+ * normal derivative), tested against the P1 basis with the plan's reference
+ * rule. xq (n_q x 3) and q (n_q) are device arrays; rhs is device, 2*N_v.
+ * prec: PB_F64 (FP64 pair arithmetic) or PB_F32_ACCURATE (FP32 pair arithmetic
+ * on split hi + lo coordinates relative to the mesh centre, FP32 sums over
+ * tiles of 256 charges added in FP64: about 1e-7 relative, for the
+ * mixed-precision path). */
 int pb_rhs_charges(pb_ctx* ctx, const pb_mesh* mesh, const double* xq, const double* q, int64_t n_q,
-                   const pb_params* prm, int form, double alpha, double beta, double* rhs,
+                   const pb_params* prm, int form, double alpha, double beta, double* rhs, int prec,
                    void* stream);
 
 /* ---- a7 + a8 + a9: preconditioned GMRES --------------------------------- */
@@ -291,15 +295,18 @@ int pb_precond_apply(pb_ctx* ctx, const pb_mesh* mesh, const pb_near* near, cons
  * converted by u_int = u_ext, v_int = (eps_ext/eps_int) v_ext), and
  * Delta G = 1/2 sum_j q_j phi_reac(x_j) (paper eq. dG), reduced in FP64.
  * xq, q device; dG_paper and dG_kcal host (either may be NULL); phi (device,
- * n_q, may be NULL) receives phi_reac. */
+ * n_q, may be NULL) receives phi_reac. prec: PB_F64 or PB_F32_ACCURATE (the
+ * point-charge pair sums in FP32 on split coordinates, FP32 sums over tiles
+ * of 256 points added in FP64; the reduction over charges in FP64 either way). */
 int pb_energy(pb_ctx* ctx, const pb_mesh* mesh, const double* x, int form, const double* xq,
               const double* q, int64_t n_q, const pb_params* prm, double* phi, double* dG_paper,
-              double* dG_kcal, void* stream);
+              double* dG_kcal, int prec, void* stream);
 
 /* ---- whole path from host buffers --------------------------------------- */
 /* One solve from host arrays: mesh load, near build, right-hand side, solve
  * and energy, freeing everything it made. verts/tris/xq/q are host arrays;
- * dG_kcal (host) receives the energy in kcal/mol. */
+ * dG_kcal (host) receives the energy in kcal/mol. With opts->precision =
+ * PB_MIXED the right-hand side and the energy take PB_F32_ACCURATE. */
 int pb_solvation_energy(pb_ctx* ctx, const double* verts, int64_t n_verts, const int32_t* tris,
                         int64_t n_tris, const double* xq, const double* q, int64_t n_q,
                         const pb_params* prm, const pb_quad_plan* plan, int form, int precond,
@@ -368,6 +375,7 @@ typedef struct {
     int tile_records;       /* source records per TMA tile of the chosen launch */
     int stages;             /* its pipeline stages */
     int targets_per_thread; /* its targets per thread */
+    int tiles_per_fp64_sum; /* split-coordinate variant: tiles whose FP32 sums go into FP64 at a time */
     double split_scale;     /* chosen multiplier of the wave-filling split count */
     double best_ms;         /* one FP32 system application with the choice */
     double default_ms;      /* ... with the untuned default (packed, shape 0, x1) */
@@ -379,7 +387,8 @@ typedef struct {
 /* Time every candidate launch of formulation `form`'s FP32 system application
  * on this mesh (fast and split-coordinate variants; the scalar kernel and the
  * packed kernel in each of its launch shapes - records per TMA tile 32, 64
- * or 128, 2 to 8 pipeline stages, 2 or 4 targets per thread - each with the
+ * or 128, 2 or 4 pipeline stages, 2 or 4 targets per thread, for the
+ * split-coordinate variant 1, 2 or 4 tiles per FP64 addition - each with the
  * wave-filling split count x0.5, x1 and x2) and keep the fastest of each
  * variant in ctx for meshes of this size (same power-of-two bucket of
  * quadrature points). Later applications, solves and the server use it. out

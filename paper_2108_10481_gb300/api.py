@@ -257,13 +257,15 @@ def pb_system_apply_noalloc(ctx: Ctx, mesh: Mesh, near: Near, params: Params, fo
 
 
 def pb_rhs_charges(ctx: Ctx, mesh: Mesh, xq: torch.Tensor, q: torch.Tensor, params: Params, form,
-                   alpha: float = 0.0, beta: float = 0.0, rhs: torch.Tensor | None = None, stream=None):
+                   alpha: float = 0.0, beta: float = 0.0, rhs: torch.Tensor | None = None, stream=None,
+                   prec: int = PB_F64):
+    """prec: PB_F64, or PB_F32_ACCURATE (split-coordinate FP32 pair sums, FP64 tile sums)."""
     nv = mesh.info()["n_verts"]
     if rhs is None:
         rhs = torch.empty(2 * nv, dtype=torch.float64, device=xq.device)
     p = params.c()
     _check(N.load().pb_rhs_charges(ctx.ptr, mesh.ptr, _dptr(xq, "xq"), _dptr(q, "q"), q.numel(), ctypes.byref(p),
-                                   _form(form), alpha, beta, _dptr(rhs, "rhs"), _stream(stream)))
+                                   _form(form), alpha, beta, _dptr(rhs, "rhs"), int(prec), _stream(stream)))
     return rhs
 
 
@@ -338,13 +340,14 @@ def pb_solve_pc(ctx: Ctx, mesh: Mesh, near: Near, pc_mesh: Mesh, pc_near: Near, 
 
 
 def pb_energy(ctx: Ctx, mesh: Mesh, x: torch.Tensor, form, xq: torch.Tensor, q: torch.Tensor, params: Params,
-              phi: torch.Tensor | None = None, stream=None):
-    """Returns (dG in paper units, dG in kcal/mol); phi (optional, n_q) receives phi_reac."""
+              phi: torch.Tensor | None = None, stream=None, prec: int = PB_F64):
+    """Returns (dG in paper units, dG in kcal/mol); phi (optional, n_q) receives phi_reac.
+    prec: PB_F64, or PB_F32_ACCURATE (split-coordinate FP32 pair sums, FP64 tile sums)."""
     p = params.c()
     a, b = ctypes.c_double(), ctypes.c_double()
     _check(N.load().pb_energy(ctx.ptr, mesh.ptr, _dptr(x, "x"), _form(form), _dptr(xq, "xq"), _dptr(q, "q"),
                               q.numel(), ctypes.byref(p), _dptr(phi, "phi") if phi is not None else None,
-                              ctypes.byref(a), ctypes.byref(b), _stream(stream)))
+                              ctypes.byref(a), ctypes.byref(b), int(prec), _stream(stream)))
     return a.value, b.value
 
 

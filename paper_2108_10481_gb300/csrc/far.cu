@@ -468,9 +468,12 @@ __device__ __forceinline__ void tile_x2(const float* __restrict__ tile, const fl
 }
 
 // Templated on its launch shape: source records per TMA tile (TS), pipeline
-// stages (ST) and packed target pairs per thread (NPK); the autotuner picks
+// stages (ST), packed target pairs per thread (NPK) and, for the
+// split-coordinate variant, the tiles whose FP32 sums are added into the FP64
+// sums at a time (PROMO: each FP64 addition takes about as much of the GB300's
+// FP64 pipe as 64 FP32 operations take of the FMA pipe); the autotuner picks
 // the shape per mesh-size bucket.
-template <int MODE, bool ACC, int TS, int ST, int NPK>
+template <int MODE, bool ACC, int TS, int ST, int NPK, int PROMO = 1>
 __global__ void __launch_bounds__(TPB2) k_pair32x2(const __grid_constant__ CUtensorMap tmap, int64_t np,
                                                    const float* __restrict__ pts32, const float* __restrict__ pts32lo,
                                                    Coef32 c32, int64_t chunk, void* __restrict__ part_out,
@@ -527,7 +530,7 @@ __global__ void __launch_bounds__(TPB2) k_pair32x2(const __grid_constant__ CUten
         const bool guard = (jt < blk1 && jt + TS > blk0) || jt + TS > np;
         if (guard) tile_x2<MODE, ACC, NPK, true, TS>(sh[st], X, XL, acc, cf);
         else tile_x2<MODE, ACC, NPK, false, TS>(sh[st], X, XL, acc, cf);
-        if (ACC) {
+        if (ACC && ((it + 1) % PROMO == 0 || it + 1 == ntiles)) {
             for (int p = 0; p < NPK; ++p)
                 for (int a = 0; a < NACC; ++a) {
                     accd[2 * p][a] += (double)acc[p][a].x;
@@ -559,24 +562,26 @@ __global__ void __launch_bounds__(TPB2) k_pair32x2(const __grid_constant__ CUten
 
 // Launch shapes of the packed kernel, one table per row mode and variant; the
 // autotuner picks one per mesh-size bucket (shape 0: the default).
-// Shapes: (records per tile, stages, packed target pairs per thread).
+// Shapes: (records per tile, stages, packed target pairs per thread, tiles per
+// FP64 addition of the split-coordinate variant).
 typedef void (*X2Launch)(dim3, cudaStream_t, const CUtensorMap&, int64_t, const float*, const float*, Coef32,
                          int64_t, void*, int*);
 struct X2Entry {
-    int ts, st, npk;
+    int ts, st, npk, promo;
     const void* fn;
     X2Launch launch;
 };
 constexpr int X2_SHAPES = 4;
 
-template <int MODE, bool ACC, int TS, int ST, int NPK>
+template <int MODE, bool ACC, int TS, int ST, int NPK, int PROMO>
 static void x2_launch(dim3 g, cudaStream_t s, const CUtensorMap& map, int64_t np, const float* p32,
                       const float* plo, Coef32 cf, int64_t chunk, void* part, int* status) {
-    k_pair32x2<MODE, ACC, TS, ST, NPK><<<g, TPB2, 0, s>>>(map, np, p32, plo, cf, chunk, part, status);
+    k_pair32x2<MODE, ACC, TS, ST, NPK, PROMO><<<g, TPB2, 0, s>>>(map, np, p32, plo, cf, chunk, part, status);
 }
-template <int MODE, bool ACC, int TS, int ST, int NPK>
+template <int MODE, bool ACC, int TS, int ST, int NPK, int PROMO = 1>
 static X2Entry x2_entry() {
-    return {TS, ST, NPK, (const void*)k_pair32x2<MODE, ACC, TS, ST, NPK>, x2_launch<MODE, ACC, TS, ST, NPK>};
+    return {TS, ST, NPK, PROMO, (const void*)k_pair32x2<MODE, ACC, TS, ST, NPK, PROMO>,
+            x2_launch<MODE, ACC, TS, ST, NPK, PROMO>};
 }
 template <int MODE>
 static void x2_row(X2Entry (&fast)[X2_SHAPES], X2Entry (&acc)[X2_SHAPES]) {
@@ -585,9 +590,9 @@ static void x2_row(X2Entry (&fast)[X2_SHAPES], X2Entry (&acc)[X2_SHAPES]) {
     fast[2] = x2_entry<MODE, false, 128, 2, 2>();
     fast[3] = x2_entry<MODE, false, 64, 4, 1>();
     acc[0] = x2_entry<MODE, true, 64, 4, 1>();
-    acc[1] = x2_entry<MODE, true, 32, 4, 1>();
-    acc[2] = x2_entry<MODE, true, 128, 2, 1>();
-    acc[3] = x2_entry<MODE, true, 32, 8, 1>();
+    acc[1] = x2_entry<MODE, true, 128, 2, 1>();
+    acc[2] = x2_entry<MODE, true, 128, 2, 1, 2>();
+    acc[3] = x2_entry<MODE, true, 64, 4, 1, 4>();
 }
 static const X2Entry& x2_kernel(int mode, bool acc, int shape) {
     struct Table {
@@ -1541,6 +1546,7 @@ extern "C" int pb_autotune(pb_ctx* ctx, const pb_mesh* m, const pb_near* nf, con
             o.tile_records = best_e.kernel == 2 ? xk.ts : (int)TS32;
             o.stages = best_e.kernel == 2 ? xk.st : (int)ST32;
             o.targets_per_thread = best_e.kernel == 2 ? 2 * xk.npk : (int)TGT32;
+            o.tiles_per_fp64_sum = best_e.kernel == 2 && acc ? xk.promo : 1;
             o.split_scale = best_e.split_scale;
             o.best_ms = best;
             o.default_ms = dflt;

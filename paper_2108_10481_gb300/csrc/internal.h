@@ -146,6 +146,7 @@ struct pb_mesh {
     pb_ctx* ctx = nullptr;
     int64_t nv = 0, nt = 0, np = 0;
     int Q = 0, n_ss = 0;
+    double ctr[3] = {0.0, 0.0, 0.0};  // centre of the bounding box: origin of the split FP32 coordinates
     int n_ss_cls[3] = {0, 0, 0};  // singular Gauss points per dimension: coincident, edge, vertex pairs
     double rule_l[6][3];
     double rule_w[6];

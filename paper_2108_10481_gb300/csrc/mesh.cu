@@ -840,6 +840,9 @@ static int load(pb_ctx* ctx, const double* verts_in, int64_t nv, const int32_t* 
     m->device_bytes = tot;
 
     double cx = 0.5 * (lo[0] + hi[0]), cy = 0.5 * (lo[1] + hi[1]), cz = 0.5 * (lo[2] + hi[2]);
+    m->ctr[0] = cx;
+    m->ctr[1] = cy;
+    m->ctr[2] = cz;
     int threads = 128;
     int blocks = (int)((nt + threads - 1) / threads);
     k_geometry<<<blocks, threads>>>(m->verts, m->tris, nt, mesh_rule(m), mesh_ref_rule(m), cx, cy, cz, m->tgeo,

@@ -158,7 +158,9 @@ static int setup_req(pb_server* srv, ServeReq* r) {
     r->w = r->dd + 2 * nv;
     PB_CUDA(cudaMemcpyAsync(r->dxq, r->xq.data(), sizeof(double) * 3 * nq, cudaMemcpyHostToDevice, s));
     PB_CUDA(cudaMemcpyAsync(r->dq, r->q.data(), sizeof(double) * nq, cudaMemcpyHostToDevice, s));
-    PB_TRY(pb_rhs_charges(ctx, r->m, r->dxq, r->dq, nq, &r->prm, r->form, r->opts.alpha, r->opts.beta, r->rhs, s));
+    const int cprec = r->opts.precision == PB_MIXED ? PB_F32_ACCURATE : PB_F64;  // the charge sums' arithmetic
+    PB_TRY(pb_rhs_charges(ctx, r->m, r->dxq, r->dq, nq, &r->prm, r->form, r->opts.alpha, r->opts.beta, r->rhs, cprec,
+                          s));
     PB_CUDA(cudaMemsetAsync(r->x, 0, sizeof(double) * 2 * nv, s));
     PB_TRY(setup_solver(r->S, r->m, r->nf, &r->prm, r->form, r->pc, &r->opts, s));
     PB_TRY(gmres_alloc(r->G, 2 * nv, r->mmax));
@@ -403,7 +405,7 @@ static int tick(pb_server* srv) {
         }
         double dGp = 0.0, dGk = 0.0;
         int rc = pb_energy(srv->ctx, r->m, r->x, r->form, r->dxq, r->dq, (int64_t)r->q.size(), &r->prm, nullptr, &dGp,
-                           &dGk, rs_of(r));
+                           &dGk, r->mixed ? PB_F32_ACCURATE : PB_F64, rs_of(r));
         if (rc != PB_OK && r->status == PB_OK) r->status = rc;
         if (r->status == PB_OK) r->status = check_status(r->m, rs_of(r));
         srv->free_slots.push_back(r->slot);

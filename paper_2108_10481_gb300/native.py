@@ -48,7 +48,8 @@ class pb_result(ctypes.Structure):
 
 class pb_tune_choice(ctypes.Structure):
     _fields_ = [("kernel", c_int), ("shape", c_int), ("tile_records", c_int), ("stages", c_int),
-                ("targets_per_thread", c_int), ("split_scale", c_double), ("best_ms", c_double),
+                ("targets_per_thread", c_int), ("tiles_per_fp64_sum", c_int), ("split_scale", c_double),
+                ("best_ms", c_double),
                 ("default_ms", c_double)]
 
 
@@ -70,7 +71,7 @@ SIGNATURES = {
     "pb_free_near": [P],
     "pb_op_apply": [P, P, P, c_int, c_int, c_int, P, P, P],
     "pb_system_apply": [P, P, P, ctypes.POINTER(pb_params), c_int, c_double, c_double, c_int, P, P, P],
-    "pb_rhs_charges": [P, P, P, P, c_int64, ctypes.POINTER(pb_params), c_int, c_double, c_double, P, P],
+    "pb_rhs_charges": [P, P, P, P, c_int64, ctypes.POINTER(pb_params), c_int, c_double, c_double, P, c_int, P],
     "pb_solve": [P, P, P, ctypes.POINTER(pb_params), c_int, c_int, ctypes.POINTER(pb_solve_opts), P, P,
                  ctypes.POINTER(pb_solve_info), P],
     "pb_precond_apply": [P, P, P, ctypes.POINTER(pb_params), c_int, c_int, ctypes.POINTER(pb_solve_opts), c_int, P, P,
@@ -80,7 +81,7 @@ SIGNATURES = {
     "pb_solve_pc": [P, P, P, P, P, ctypes.POINTER(pb_params), c_int, c_int, ctypes.POINTER(pb_solve_opts), P, P,
                     ctypes.POINTER(pb_solve_info), P],
     "pb_energy": [P, P, P, c_int, P, P, c_int64, ctypes.POINTER(pb_params), P, ctypes.POINTER(c_double),
-                  ctypes.POINTER(c_double), P],
+                  ctypes.POINTER(c_double), c_int, P],
     "pb_solvation_energy": [P, P, c_int64, P, c_int64, P, P, c_int64, ctypes.POINTER(pb_params),
                             ctypes.POINTER(pb_quad_plan), c_int, c_int, ctypes.POINTER(pb_solve_opts),
                             ctypes.POINTER(c_double), ctypes.POINTER(pb_solve_info), P],

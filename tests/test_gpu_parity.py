@@ -110,6 +110,31 @@ def test_system_apply_and_rhs(pb, ctx, form):
     assert rel(rhs, b) < 1e-13
 
 
+@pytest.mark.parametrize("form", ["direct_int", "juffer", "pmchwt_ext"])
+def test_split_fp32_charge_sums(pb, ctx, form):
+    """The right-hand side and the energy with FP32 pair arithmetic on split
+    coordinates (PB_F32_ACCURATE, the mixed-precision path) against the
+    oracle's FP64 projections and reaction potential: 1e-6 relative (per-pair
+    FP32 rounding of about 6e-8, summed with FP64 tile sums)."""
+    name = "uv"
+    m, nf = gpu_mesh(pb, ctx, name)
+    o = oracle_ops(name)
+    v, t, xq, q = mesh_case(name)
+    bD, bN = oracle.source_projections(v, t, xq, q, PHYS.eps_int)
+    _, b = O.system(form, o, PHYS, bD, bN)
+    rhs = pb.pb_rhs_charges(ctx, m, cuda(xq), cuda(q), params(pb), form, prec=pb.PB_F32_ACCURATE).cpu().numpy()
+    e_rhs = rel(rhs, b)
+    x = np.random.default_rng(17).standard_normal(2 * len(v))
+    u, w = O.interior_traces(form, x, PHYS)
+    phi_ref = oracle.reaction_potential(v, t, u, w, xq)
+    phi = torch.empty(len(q), dtype=torch.float64, device="cuda")
+    _, dG32 = pb.pb_energy(ctx, m, cuda(x), form, cuda(xq), cuda(q), params(pb), phi=phi, prec=pb.PB_F32_ACCURATE)
+    _, dG64 = pb.pb_energy(ctx, m, cuda(x), form, cuda(xq), cuda(q), params(pb))
+    e_phi = rel(phi.cpu().numpy(), phi_ref)
+    print(f"{form}: split FP32 rhs rel {e_rhs:.1e}, phi_reac rel {e_phi:.1e}, dG rel {abs(dG32 / dG64 - 1):.1e}")
+    assert e_rhs < 1e-6 and e_phi < 1e-6 and abs(dG32 / dG64 - 1) < 1e-6
+
+
 def _solve_gpu(pb, ctx, name, case, precision, tol=1e-12, far_q=6):
     m, nf = gpu_mesh(pb, ctx, name, far_q=far_q)
     v, t, xq, q = mesh_case(name)

@@ -29,6 +29,7 @@ def test_launch_tuning_keeps_results(pb):
     for r in rr.values():
         assert r["kernel"] in (1, 2) and r["split_scale"] in (0.5, 1.0, 2.0) and 0 <= r["shape"] < 4
         assert r["tile_records"] in (32, 64, 128) and r["targets_per_thread"] in (2, 4)
+        assert r["tiles_per_fp64_sum"] in (1, 2, 4)
         assert 0 < r["best_ms"] <= r["default_ms"]
     for prec in (pb.PB_F32, pb.PB_F32_ACCURATE):
         y = pb.pb_system_apply(ctx, m, nf, P, "juffer", x, prec)
