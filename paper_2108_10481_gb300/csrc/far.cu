@@ -812,6 +812,8 @@ __global__ void k_tri_reduce(int64_t nt, int64_t np, Rule rule, int nsplit, int 
 
 // ------------------------------------- gather + near-field SpMV (a4 ii + a5)
 // 8 lanes per vertex; lane-strided sums reduced by shuffles in a fixed order.
+// The four combined block values of an entry lie together (comb[4 k + 2 r + c]),
+// so one vector load (float4, or two double2) brings them.
 template <typename V>
 __global__ void k_gather_spmv(int64_t nv, const int32_t* __restrict__ v2t_ptr, const int32_t* __restrict__ v2t,
                               const double* __restrict__ tri, int use_far, const int32_t* __restrict__ row_ptr,
@@ -833,9 +835,19 @@ __global__ void k_gather_spmv(int64_t nv, const int32_t* __restrict__ v2t_ptr, c
         const double* u = x;
         const double* v = x + nv;
         for (int32_t k = row_ptr[i] + lane; k < row_ptr[i + 1]; k += 8) {
-            double uc = u[col[k]], vc = v[col[k]];
-            y0 += (double)comb[k] * uc + (double)comb[nnz + k] * vc;
-            y1 += (double)comb[2 * nnz + k] * uc + (double)comb[3 * nnz + k] * vc;
+            const int32_t c = col[k];
+            const double uc = u[c], vc = v[c];
+            double b0, b1, b2, b3;
+            if (sizeof(V) == 4) {
+                const float4 f = reinterpret_cast<const float4*>(comb)[k];
+                b0 = f.x; b1 = f.y; b2 = f.z; b3 = f.w;
+            } else {
+                const double2 lo = reinterpret_cast<const double2*>(comb)[2 * k];
+                const double2 hi = reinterpret_cast<const double2*>(comb)[2 * k + 1];
+                b0 = lo.x; b1 = lo.y; b2 = hi.x; b3 = hi.y;
+            }
+            y0 += b0 * uc + b1 * vc;
+            y1 += b2 * uc + b3 * vc;
         }
     }
     for (int o = 4; o > 0; o >>= 1) {
@@ -868,8 +880,8 @@ __global__ void k_combine(int64_t nnz, const double* __restrict__ val, const int
         for (int c = 0; c < 2; ++c) {
             double s = 0.0;
             for (int o = 0; o < O_N; ++o) s += B.c[r][c][o] * vals[o];
-            c64[(2 * r + c) * nnz + e] = s;
-            c32[(2 * r + c) * nnz + e] = (float)s;
+            c64[4 * e + 2 * r + c] = s;
+            c32[4 * e + 2 * r + c] = (float)s;
         }
 }
 

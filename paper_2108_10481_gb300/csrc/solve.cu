@@ -92,20 +92,29 @@ __global__ void k_cheb_init(int64_t nv, const double* __restrict__ mdiag, const 
     x[i] = 0.0;
     d[i] = b[i] / (theta * mdiag[row]);
 }
+// one thread per vertex: row i of both halves (they share the pattern and values)
 __global__ void k_cheb_step(int64_t nv, const int32_t* __restrict__ row_ptr, const int32_t* __restrict__ col,
                             const double* __restrict__ mval, const double* __restrict__ mdiag,
                             const double* __restrict__ d, double* __restrict__ dn, double* __restrict__ x,
                             double* __restrict__ r, double c_d, double c_r) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= 2 * nv) return;
-    int64_t row = i < nv ? i : i - nv;
-    const double* dh = d + (i < nv ? 0 : nv);
-    double md = 0.0;
-    for (int32_t k = row_ptr[row]; k < row_ptr[row + 1]; ++k) md += mval[k] * dh[col[k]];
-    double rn = r[i] - md;
-    x[i] += d[i];
-    r[i] = rn;
-    dn[i] = c_d * d[i] + c_r * rn / mdiag[row];
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= nv) return;
+    double md0 = 0.0, md1 = 0.0;
+    for (int32_t k = row_ptr[i]; k < row_ptr[i + 1]; ++k) {
+        const double mv = mval[k];
+        const int32_t c = col[k];
+        md0 += mv * d[c];
+        md1 += mv * d[nv + c];
+    }
+    const double md[2] = {md0, md1};
+    const double inv = mdiag[i];
+    for (int h = 0; h < 2; ++h) {
+        const int64_t ii = i + h * nv;
+        const double rn = r[ii] - md[h];
+        x[ii] += d[ii];
+        r[ii] = rn;
+        dn[ii] = c_d * d[ii] + c_r * rn / inv;
+    }
 }
 
 int mass_solve(const pb_mesh* m, const pb_near* nf, const double* b, double* x, double* work, int iters,
@@ -128,8 +137,9 @@ int mass_solve(const pb_mesh* m, const pb_near* nf, const double* b, double* x, 
     for (int k = 0; k < iters; ++k) {
         double rho_n = 1.0 / (2.0 * sigma - rho);
         Timer tm(m->ctx, PB_KERNEL_CHEB, s, step_bytes, 1.0);
-        k_cheb_step<<<blocks, 256, 0, s>>>(nv, nf->mrow_ptr, nf->mcol, mval, mdiag, d0, d1, x, r, rho_n * rho,
-                                           2.0 * rho_n / delta); ::pb::count_launch();
+        k_cheb_step<<<(unsigned)((nv + 255) / 256), 256, 0, s>>>(nv, nf->mrow_ptr, nf->mcol, mval, mdiag, d0, d1, x,
+                                                                  r, rho_n * rho, 2.0 * rho_n / delta);
+        ::pb::count_launch();
         tm.stop();
         rho = rho_n;
         double* t = d0;
