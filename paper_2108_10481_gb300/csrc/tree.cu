@@ -482,8 +482,8 @@ k_proxy_charges(const int32_t* __restrict__ slots, const int32_t* __restrict__ s
 // (blockIdx.y), TREE_LEAF threads in two groups (tree_leaf_body with NQ = 2).
 template <int MODE>
 __global__ void __launch_bounds__(TREE_LEAF) k_tree_eval(TreeJob job) {
-    __shared__ __align__(16) float tile[TREE_EVAL_TILE * TREE_REC];
-    static_assert((MODE == 0 ? 2 : 10) * TREE_LEAF <= TREE_EVAL_TILE * TREE_REC, "reduction buffer");
+    __shared__ __align__(16) float tile[2 * TREE_EVAL_TILE * TREE_REC];
+    static_assert((MODE == 0 ? 2 : 10) * TREE_LEAF <= 2 * TREE_EVAL_TILE * TREE_REC, "reduction buffer");
     tree_leaf_body<MODE, 2>(job, blockIdx.x, blockIdx.y, tile);
 }
 

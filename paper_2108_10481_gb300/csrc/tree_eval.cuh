@@ -67,16 +67,59 @@ struct TreeJob {
     TreeCoef cf;
 };
 
+// Asynchronous 16-byte copies global -> shared (cp.async), committed in groups:
+// the staging of the next tile runs while the current one is summed.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// The tiles of one leaf's share of its lists, in order: every proxied cluster's
+// proxies (far, in tiles of TREE_EVAL_TILE records), then every directly summed
+// source range (near, likewise).
+struct TreeTiles {
+    int32_t f, fe, q, qe;  // list cursors
+    int32_t off;           // records done in the current cluster or range
+    __device__ __forceinline__ bool next(const TreeJob& T, const float** src, int* cnt, bool* far) {
+        constexpr int TILE = TREE_EVAL_TILE;
+        if (f < fe) {
+            *src = T.prox + ((int64_t)T.far_idx[f] * T.nprox + off) * TREE_REC;
+            *cnt = min(TILE, T.nprox - off);
+            *far = true;
+            off += TILE;
+            if (off >= T.nprox) { ++f; off = 0; }
+            return true;
+        }
+        while (q < qe) {
+            const int32_t sb = T.near_rng[2 * q], se = T.near_rng[2 * q + 1];
+            if (sb + off >= se) { ++q; off = 0; continue; }
+            *src = T.rec + (int64_t)(sb + off) * TREE_REC;
+            *cnt = min(TILE, se - sb - off);
+            *far = false;
+            off += TILE;
+            if (sb + off >= se) { ++q; off = 0; }
+            return true;
+        }
+        return false;
+    }
+};
+
 // One leaf of targets and one split of its lists, on 64 NQ threads: a thread
 // holds two targets (the leaf's i-th and (i + 64)-th points) in packed f32x2
 // arithmetic; the NQ thread groups of 64 take every NQ-th source of each staged
 // tile and add their sums through shared memory at the end, group 0 adding
 // groups 1 .. NQ-1 in that order. Far: proxies of the well-separated clusters
 // (kernel G with the interpolated charges). Near: the other sources directly,
-// with the direct pair kernel's arithmetic (identical points skipped).
-// `tile` holds at least TREE_EVAL_TILE x TREE_REC floats and
-// (NQ - 1) x NACC x TREE_LEAF floats. Every thread of the group calls it (it
-// synchronises the CTA) and returns; nothing is left in flight.
+// with the direct pair kernel's arithmetic (identical points skipped). Tiles
+// are staged in two buffers by asynchronous copies, the next one in flight
+// while the current one is summed. `tile` holds at least
+// 2 x TREE_EVAL_TILE x TREE_REC floats and (NQ - 1) x NACC x TREE_LEAF floats.
+// Every thread of the group calls it (it synchronises the CTA) and returns
+// with no copy in flight.
 template <int MODE, int NQ>
 __device__ __forceinline__ void tree_leaf_body(const TreeJob& T, int leaf, int sp, float* tile) {
     constexpr int NACC = MODE == 0 ? 2 : 10;
@@ -114,19 +157,31 @@ __device__ __forceinline__ void tree_leaf_body(const TreeJob& T, int leaf, int s
     float2 acc[NACC];
     for (int k = 0; k < NACC; ++k) acc[k] = t_splat(0.f);
     const bool any = live0;  // the first target of a thread is live whenever the second is
-    // far clusters through their proxies
-    for (int32_t f = fb; f < fe; ++f) {
-        const float* pr = T.prox + (int64_t)T.far_idx[f] * T.nprox * TREE_REC;
-        for (int c0 = 0; c0 < T.nprox; c0 += TILE) {
-            const int cnt = min(TILE, T.nprox - c0);
-            __syncthreads();
-            for (int k = threadIdx.x; k < cnt * TREE_REC / 4; k += NTH)
-                reinterpret_cast<float4*>(tile)[k] = reinterpret_cast<const float4*>(pr + (int64_t)c0 * TREE_REC)[k];
-            __syncthreads();
-            if (!any) continue;
+    TreeTiles it = {fb, fe, qb, qe, 0};
+    const float* src = nullptr;
+    int cnt = 0, cnt_next = 0;
+    bool far = false, far_next = false;
+    bool have = it.next(T, &src, &cnt, &far);
+    __syncthreads();  // the buffers may still be read by the caller's previous work
+    if (have) {
+        for (int k = threadIdx.x; k < cnt * TREE_REC / 4; k += NTH) cp_async16(tile + 4 * k, src + 4 * k);
+    }
+    cp_async_commit();
+    for (int buf = 0; have; buf ^= 1) {
+        const float* nsrc = nullptr;
+        const bool have_next = it.next(T, &nsrc, &cnt_next, &far_next);
+        if (have_next) {
+            float* nb = tile + (buf ^ 1) * TILE * TREE_REC;
+            for (int k = threadIdx.x; k < cnt_next * TREE_REC / 4; k += NTH) cp_async16(nb + 4 * k, nsrc + 4 * k);
+        }
+        cp_async_commit();
+        cp_async_wait<1>();  // this thread's copies of the current tile have landed
+        __syncthreads();     // and every thread's
+        const float* cur = tile + buf * TILE * TREE_REC;
+        if (any && far) {
 #pragma unroll 2
             for (int j = grp; j < cnt; j += NQ) {
-                const float* z = tile + TREE_REC * j;
+                const float* z = cur + TREE_REC * j;
                 const float2 d0 = t_sub2(X0, t_splat(z[0])), d1 = t_sub2(X1, t_splat(z[1])),
                              d2 = t_sub2(X2, t_splat(z[2]));
                 const float2 r2 = t_fma2(d0, d0, t_fma2(d1, d1, t_mul2(d2, d2)));
@@ -156,21 +211,10 @@ __device__ __forceinline__ void tree_leaf_body(const TreeJob& T, int leaf, int s
                     acc[9] = t_fma2(gb, t_splat(z[10]), acc[9]);
                 }
             }
-        }
-    }
-    // near sources directly (identical points skipped)
-    for (int32_t q = qb; q < qe; ++q) {
-        const int32_t sb = T.near_rng[2 * q], se = T.near_rng[2 * q + 1];
-        for (int32_t c0 = sb; c0 < se; c0 += TILE) {
-            const int cnt = min(TILE, se - c0);
-            __syncthreads();
-            for (int k = threadIdx.x; k < cnt * TREE_REC / 4; k += NTH)
-                reinterpret_cast<float4*>(tile)[k] = reinterpret_cast<const float4*>(rec + (int64_t)c0 * TREE_REC)[k];
-            __syncthreads();
-            if (!any) continue;
+        } else if (any) {
 #pragma unroll 2
             for (int j = grp; j < cnt; j += NQ) {
-                const float* y = tile + TREE_REC * j;
+                const float* y = cur + TREE_REC * j;
                 const float2 d0 = t_sub2(X0, t_splat(y[0])), d1 = t_sub2(X1, t_splat(y[1])),
                              d2 = t_sub2(X2, t_splat(y[2]));
                 const float2 r2 = t_fma2(d0, d0, t_fma2(d1, d1, t_mul2(d2, d2)));
@@ -203,7 +247,12 @@ __device__ __forceinline__ void tree_leaf_body(const TreeJob& T, int leaf, int s
                 }
             }
         }
+        __syncthreads();  // every thread is done with this buffer before it is refilled
+        have = have_next;
+        cnt = cnt_next;
+        far = far_next;
     }
+    cp_async_wait<0>();  // nothing in flight (the last group is empty)
     // the other groups' sums join group 0's, in group order
     __syncthreads();
     const int tl = (int)threadIdx.x % HALF;
