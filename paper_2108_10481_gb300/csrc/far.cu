@@ -1005,7 +1005,7 @@ static double spmv_bytes(const pb_mesh* m, bool far, int vb) {
 }
 
 int apply_blockop(const pb_mesh* m, const pb_near* nf, const BlockOp& B, int prec, const double* x, double* y,
-                  cudaStream_t s) {
+                  cudaStream_t s, const double* comb) {
     if (prec != PB_F64 && prec != PB_F32 && prec != PB_F32_ACCURATE)
         return set_error(PB_EINVAL, "unknown precision %d", prec);
     FarPlan fp;
@@ -1013,12 +1013,16 @@ int apply_blockop(const pb_mesh* m, const pb_near* nf, const BlockOp& B, int pre
     const int64_t nv = m->nv, nt = m->nt, np = m->np;
     PB_TRY(ws_reserve(const_cast<pb_mesh*>(m)->ws_src, sizeof(float) * REC2 * np + 256));  // >= REC64 doubles
     PB_TRY(ws_reserve(const_cast<pb_mesh*>(m)->ws_tri, sizeof(double) * 6 * nt));
-    PB_TRY(ws_reserve(const_cast<pb_mesh*>(m)->ws_comb, (sizeof(double) + sizeof(float)) * 4 * m->nnz));
     double* tri = (double*)m->ws_tri.ptr;
     int* status = m->status;
-    double* c64 = (double*)m->ws_comb.ptr;
-    float* c32 = (float*)(c64 + 4 * m->nnz);
-    PB_TRY(combine_near(m, nf, B, c64, c32, s));
+    const double* c64 = comb;
+    if (!comb) {
+        PB_TRY(ws_reserve(const_cast<pb_mesh*>(m)->ws_comb, (sizeof(double) + sizeof(float)) * 4 * m->nnz));
+        double* w64 = (double*)m->ws_comb.ptr;
+        PB_TRY(combine_near(m, nf, B, w64, (float*)(w64 + 4 * m->nnz), s));
+        c64 = w64;
+    }
+    const float* c32 = (const float*)(c64 + 4 * m->nnz);
 
     if (fp.any) {
         bool need_u = false, need_v = false;
@@ -1157,7 +1161,7 @@ int apply_blockop(const pb_mesh* m, const pb_near* nf, const BlockOp& B, int pre
 int apply_blockops_batched(const std::vector<FarJob>& jobs, int prec, BatchScratch& bs, cudaStream_t s) {
     if (jobs.empty()) return PB_OK;
     if (prec == PB_F64) {
-        for (const FarJob& j : jobs) PB_TRY(apply_blockop(j.m, j.nf, j.B, PB_F64, j.x, j.y, j.s ? j.s : s));
+        for (const FarJob& j : jobs) PB_TRY(apply_blockop(j.m, j.nf, j.B, PB_F64, j.x, j.y, j.s ? j.s : s, j.comb));
         return PB_OK;
     }
     while (bs.ev.size() < jobs.size()) {
@@ -1192,11 +1196,15 @@ int apply_blockops_batched(const std::vector<FarJob>& jobs, int prec, BatchScrat
         const int64_t np_pad = (np + TS2 - 1) / TS2 * TS2;
         PB_TRY(ws_reserve(m->ws_src, sizeof(float) * REC2 * np_pad + 256));
         PB_TRY(ws_reserve(m->ws_tri, sizeof(double) * 6 * nt));
-        PB_TRY(ws_reserve(m->ws_comb, (sizeof(double) + sizeof(float)) * 4 * m->nnz));
         P.tri = (double*)m->ws_tri.ptr;
-        P.c64 = (double*)m->ws_comb.ptr;
+        if (J.comb) {
+            P.c64 = const_cast<double*>(J.comb);
+        } else {
+            PB_TRY(ws_reserve(m->ws_comb, (sizeof(double) + sizeof(float)) * 4 * m->nnz));
+            P.c64 = (double*)m->ws_comb.ptr;
+            PB_TRY(combine_near(m, J.nf, J.B, P.c64, (float*)(P.c64 + 4 * m->nnz), js));
+        }
         P.c32 = (float*)(P.c64 + 4 * m->nnz);
-        PB_TRY(combine_near(m, J.nf, J.B, P.c64, P.c32, js));
         if (!P.fp.any) continue;
         bool need_u = false, need_v = false;
         for (int R = 0; R < 2; ++R)

@@ -243,9 +243,11 @@ int calderon_blockop(const pb_params* prm, int form, int which /*0 int, 1 ext*/,
 bool form_is_exterior(int form);
 int make_far_plan(const BlockOp& B, double kappa, FarPlan* out);
 
-// a3 + a4 + a5: y = B x (x, y device, 2 nv doubles)
+// a3 + a4 + a5: y = B x (x, y device, 2 nv doubles). comb: B's near values
+// already combined (4 nnz doubles then 4 nnz floats, from combine_near), or
+// null to combine them into the mesh's workspace first.
 int apply_blockop(const pb_mesh* m, const pb_near* nf, const BlockOp& B, int prec, const double* x,
-                  double* y, cudaStream_t s);
+                  double* y, cudaStream_t s, const double* comb = nullptr);
 // near values combined for a block operator (FP64 and FP32 copies) and diagonals
 int combine_near(const pb_mesh* m, const pb_near* nf, const BlockOp& B, double* comb64, float* comb32,
                  cudaStream_t s);
@@ -258,6 +260,7 @@ struct FarJob {
     const double* x;
     double* y;
     cudaStream_t s = nullptr;  // the job's own stream for its per-job kernels (null: the batch's stream)
+    const double* comb = nullptr;  // B's combined near values (null: combined into the mesh's workspace)
 };
 struct BatchScratch {
     Workspace table;                  // job and work-item tables on the device

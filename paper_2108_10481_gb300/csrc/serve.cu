@@ -273,6 +273,11 @@ static int tick(pb_server* srv) {
         }
         return graph_replay(g, rs_of(r));
     };
+    // a request's combined near values (made on its first application, kept for its solve)
+    auto comb_of = [](ServeReq* r, bool calderon) -> const double* {
+        const double* c = nullptr;
+        return solver_comb(r->S, calderon, &c) == PB_OK ? c : nullptr;
+    };
     auto it_prec = [](const ServeReq* r) { return r->mixed ? PB_F32 : PB_F64; };
     auto res_prec = [](const ServeReq* r) { return r->mixed ? PB_F32_ACCURATE : PB_F64; };
 
@@ -280,9 +285,9 @@ static int tick(pb_server* srv) {
     std::vector<FarJob> jobs[4];  // by precision
     for (ServeReq* r : act) {
         if (r->phase == PH_ITER)
-            jobs[it_prec(r)].push_back({r->m, r->nf, r->S.A, r->G.vin, r->S.t3, rs_of(r)});
+            jobs[it_prec(r)].push_back({r->m, r->nf, r->S.A, r->G.vin, r->S.t3, rs_of(r), comb_of(r, false)});
         else if (r->phase == PH_START && r->mixed && r->outer > 0)
-            jobs[res_prec(r)].push_back({r->m, r->nf, r->S.A, r->x, r->S.t3, rs_of(r)});
+            jobs[res_prec(r)].push_back({r->m, r->nf, r->S.A, r->x, r->S.t3, rs_of(r), comb_of(r, false)});
     }
     PB_TRY(apply_round(srv, jobs, s));
     for (auto& v : jobs) v.clear();
@@ -296,7 +301,7 @@ static int tick(pb_server* srv) {
             if (r->pc >= PB_PC_CALDERON_FULL) {
                 const int ip = it_prec(r);
                 PB_TRY(piece(r, r->g_mid, [r, ip] { return calderon_pre(r->S, ip, r->S.t3); }));
-                jobs[it_prec(r)].push_back({r->m, r->nf, r->S.C, r->S.t1, r->S.t2, rs_of(r)});
+                jobs[it_prec(r)].push_back({r->m, r->nf, r->S.C, r->S.t1, r->S.t2, rs_of(r), comb_of(r, true)});
             }
             continue;  // the rest of the iteration follows the batched operators
         } else if (r->phase == PH_START) {
@@ -311,7 +316,7 @@ static int tick(pb_server* srv) {
         const int prec = r->phase == PH_ITER ? it_prec(r) : res_prec(r);
         if (r->pc >= PB_PC_CALDERON_FULL) {
             PB_TRY(calderon_pre(r->S, prec, pin[k]));
-            jobs[prec].push_back({r->m, r->nf, r->S.C, r->S.t1, r->S.t2, rs_of(r)});
+            jobs[prec].push_back({r->m, r->nf, r->S.C, r->S.t1, r->S.t2, rs_of(r), comb_of(r, true)});
         } else {
             PB_TRY(apply_prec(r->S, prec, pin[k], r->w));
         }

@@ -352,7 +352,11 @@ int apply_prec(Solver& S, int prec, const double* x, double* y) {
             break;
         default:  // Calderon: M^-1 C M^-1
             PB_TRY(mass_solve(m, S.nf, x, S.t1, S.cheb, ci, S.s));
-            PB_TRY(apply_blockop(S.mc, S.nc, S.C, prec, S.t1, S.t2, S.s));
+            {
+                const double* cc = nullptr;
+                PB_TRY(solver_comb(S, true, &cc));
+                PB_TRY(apply_blockop(S.mc, S.nc, S.C, prec, S.t1, S.t2, S.s, cc));
+            }
             S.applies++;
             PB_TRY(mass_solve(m, S.nf, S.t2, y, S.cheb, ci, S.s));
             break;
@@ -367,7 +371,9 @@ int apply_prec(Solver& S, int prec, const double* x, double* y) {
 
 // y = P^-1 A x
 static int apply_op(Solver& S, int prec, const double* x, double* y) {
-    PB_TRY(apply_blockop(S.m, S.nf, S.A, prec, x, S.t3, S.s));
+    const double* ca = nullptr;
+    PB_TRY(solver_comb(S, false, &ca));
+    PB_TRY(apply_blockop(S.m, S.nf, S.A, prec, x, S.t3, S.s, ca));
     S.applies++;
     return apply_prec(S, prec, S.t3, y);
 }
@@ -439,6 +445,26 @@ static int iterate(Solver& S, GmresWork& G, int prec, int j, StepGraph** replaye
 
 void solver_release(Solver& S) {
     for (auto& g : S.step) graph_free(g);
+    if (S.combA) cudaFree(S.combA);
+    if (S.combC) cudaFree(S.combC);
+    S.combA = S.combC = nullptr;
+}
+
+// The near values combined for a block operator depend only on the near field
+// and the operator's coefficients, both fixed for a solve: combined once, on the
+// first application (before any iteration is captured into a graph), instead of
+// once per application.
+int solver_comb(Solver& S, bool calderon, const double** out) {
+    double*& c = calderon ? S.combC : S.combA;
+    if (!c) {
+        const pb_mesh* m = calderon ? S.mc : S.m;
+        const pb_near* nf = calderon ? S.nc : S.nf;
+        const BlockOp& B = calderon ? S.C : S.A;
+        PB_TRY(dev_alloc((void**)&c, (sizeof(double) + sizeof(float)) * 4 * (size_t)m->nnz));
+        PB_TRY(combine_near(m, nf, B, c, (float*)(c + 4 * m->nnz), S.s));
+    }
+    *out = c;
+    return PB_OK;
 }
 
 // Left-preconditioned GMRES on A x = b from x (in/out; x_zero says x = 0, so
@@ -453,7 +479,9 @@ static int gmres(Solver& S, GmresWork& G, int prec, const double* b, double* x, 
     if (x_zero) {
         PB_TRY(apply_prec(S, prec, b, G.w));
     } else {
-        PB_TRY(apply_blockop(S.m, S.nf, S.A, prec, x, S.t3, s));
+        const double* ca = nullptr;
+        PB_TRY(solver_comb(S, false, &ca));
+        PB_TRY(apply_blockop(S.m, S.nf, S.A, prec, x, S.t3, s, ca));
         S.applies++;
         k_sub<<<nb(n), 256, 0, s>>>(n, b, S.t3, S.t2); ::pb::count_launch();
         PB_TRY(apply_prec(S, prec, S.t2, G.w));
@@ -749,7 +777,9 @@ static int solve_one(const pb_mesh* m, const pb_near* nf, const pb_solve_opts* o
                 if (outer == 0) {
                     PB_CUDA(cudaMemcpyAsync(rr, b, sizeof(double) * n2, cudaMemcpyDeviceToDevice, s));
                 } else {
-                    rc = apply_blockop(m, nf, S.A, PB_F32_ACCURATE, x, S.t3, s);
+                    const double* ca = nullptr;
+                    rc = solver_comb(S, false, &ca);
+                    if (rc == PB_OK) rc = apply_blockop(m, nf, S.A, PB_F32_ACCURATE, x, S.t3, s, ca);
                     if (rc != PB_OK) break;
                     S.applies++;
                     k_sub<<<nb(n2), 256, 0, s>>>(n2, b, S.t3, rr); ::pb::count_launch();

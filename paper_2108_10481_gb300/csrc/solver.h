@@ -32,7 +32,13 @@ struct Solver {
     cudaStream_t s;
     bool graphs = false;        // replay iterations from CUDA graphs
     StepGraph step[4];          // GMRES iteration body, by operator precision
+    // the near values combined for A and for C (4 nnz doubles, then 4 nnz floats each),
+    // made on first use and kept for the solve
+    double* combA = nullptr;
+    double* combC = nullptr;
 };
+// the combined near values of the system (calderon = false) or of the Calderon operator
+int solver_comb(Solver& S, bool calderon, const double** out);
 void solver_release(Solver& S);
 
 struct GmresWork {
