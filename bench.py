@@ -695,6 +695,7 @@ def serving_record(args, n_req, local_rank, full=True):
 
     closed, span_c = serve(np.zeros(len(reqs)))            # all at once
     rate = len(reqs) / span_c
+    ready_ms = np.array([closed[i]["queue_ms"] for i in range(len(reqs))])
     rng = np.random.default_rng(55)
     arr = np.cumsum(rng.exponential(1.0 / (args.rate_scale * rate), size=len(reqs)))
     arr -= arr[0]
@@ -715,6 +716,9 @@ def serving_record(args, n_req, local_rank, full=True):
            "open_arrivals_solves_per_s": len(reqs) / span_o, "arrival_rate_fraction": args.rate_scale,
            "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                           "max": float(lat.max())},
+           "closed_batch_ready_ms": {"mean": float(ready_ms.mean()), "max": float(ready_ms.max()),
+                                     "span": span_c * 1e3,
+                                     "note": "submit -> set up and ready to iterate, all submitted at once"},
            "all_converged": ok, "identical_open_vs_closed": same, "hbm_budget_bytes": budget, "max_active": 64,
            "quadrature": plan_text(plan)}
     if not full:
