@@ -780,7 +780,10 @@ static int load(pb_ctx* ctx, const double* verts_in, int64_t nv, const int32_t* 
             PAT_WARPS = (int)std::max<size_t>(1, std::min<size_t>(8, (160u << 10) / per_warp));
             psmem = per_warp * PAT_WARPS;
             pb_blocks = (unsigned)((nv + PAT_WARPS - 1) / PAT_WARPS);
-            if (cudaFuncSetAttribute(k_row_pattern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem) !=
+            // the largest allowed (227 KB; psmem is at most 6 x 32768 x 4 B = 192 KB), whatever
+            // psmem is: another host thread may load a mesh at the same time, and a smaller
+            // limit set by it must not stand when this launch runs
+            if (cudaFuncSetAttribute(k_row_pattern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 << 10) !=
                 cudaSuccess) {
                 rc = set_error(PB_ECUDA, "near pattern: shared memory of %zu bytes refused", psmem);
                 break;

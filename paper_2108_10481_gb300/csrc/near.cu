@@ -1087,7 +1087,9 @@ static int build(pb_ctx* ctx, const pb_mesh* m, double kappa, pb_near* nf, cudaS
                 rc = set_error(PB_EINVAL, "near pattern rows too long (%d entries) for one warp's shared memory",
                                m->max_row);
             } else {
-                cudaFuncSetAttribute(k_near_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+                // the largest allowed (227 KB), not this launch's sm: builds on other host threads
+                // set the same value, so none lowers it under another's launch
+                cudaFuncSetAttribute(k_near_rows, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 << 10);
                 k_near_rows<<<(unsigned)((m->nv + warps - 1) / warps), 32 * warps, sm, s>>>(
                     m->nv, m->nnz, m->max_row, warps, m->row_ptr, m->col, m->v2t_ptr, m->v2t, m->tris, m->adj_ptr,
                     m->pairs, m->n_band ? m->band_ptr : nullptr, m->band_s, m->n_adj, m->tgeo, ss, far, nf->val,

@@ -24,6 +24,7 @@
 #include <condition_variable>
 #include <deque>
 #include <mutex>
+#include <shared_mutex>
 #include <thread>
 
 #include "solver.h"
@@ -80,12 +81,14 @@ struct pb_server {
     size_t used = 0;
     int admitted = 0;  // admitted and not finished
     bool stop = false;
-    std::thread admit_thread;
-    // Held by the admission thread while it sets a request up (its allocations,
-    // frees and synchronisations reach the whole device) and by the stepping
-    // thread while it captures a CUDA graph, which such calls would invalidate.
-    std::mutex device_mu;
-    cudaStream_t s_main = nullptr, s_setup = nullptr;
+    std::vector<std::thread> admit_threads;
+    // Held shared by the admission threads while they set requests up (their
+    // allocations, frees and synchronisations reach the whole device) and
+    // exclusively by the stepping thread while it captures a CUDA graph, which
+    // such calls would invalidate.
+    std::shared_mutex device_mu;
+    cudaStream_t s_main = nullptr;
+    std::vector<cudaStream_t> s_setup;  // one per admission thread
     pb::BatchScratch bs;
     double* res_dev = nullptr;   // 4 doubles per slot (max_active slots)
     double* res_host = nullptr;
@@ -141,9 +144,8 @@ static size_t footprint(pb_ctx* ctx, int64_t nv, int64_t nt, const pb_quad_plan&
 }
 
 // load, near field, right-hand side and solver state, on the setup stream
-static int setup_req(pb_server* srv, ServeReq* r) {
+static int setup_req(pb_server* srv, ServeReq* r, cudaStream_t s) {
     pb_ctx* ctx = srv->ctx;
-    cudaStream_t s = srv->s_setup;
     PB_TRY(pb_mesh_load(ctx, r->V.data(), (int64_t)r->V.size() / 3, r->T.data(), (int64_t)r->T.size() / 3,
                         &r->plan, PB_MEM_HOST, &r->m));
     PB_TRY(pb_near_build(ctx, r->m, r->prm.kappa, &r->nf, s));
@@ -191,7 +193,7 @@ static void finish(pb_server* srv, ServeReq* r, double dGp, double dGk) {
     srv->cv.notify_all();
 }
 
-static void admission_loop(pb_server* srv) {
+static void admission_loop(pb_server* srv, int k) {
     cudaSetDevice(srv->ctx->device);
     for (;;) {
         ServeReq* r = nullptr;
@@ -209,15 +211,15 @@ static void admission_loop(pb_server* srv) {
         }
         int rc;
         {
-            std::lock_guard<std::mutex> dev_lock(srv->device_mu);
-            rc = setup_req(srv, r);
+            std::shared_lock<std::shared_mutex> dev_lock(srv->device_mu);
+            rc = setup_req(srv, r, srv->s_setup[k]);
         }
         r->t_ready = now_ms();
         if (rc != PB_OK) {
             r->status = rc;
             r->rel = 0.0;
             {
-                std::lock_guard<std::mutex> dev_lock(srv->device_mu);
+                std::shared_lock<std::shared_mutex> dev_lock(srv->device_mu);
                 free_req(r);
             }
             finish(srv, r, 0.0, 0.0);
@@ -266,7 +268,7 @@ static int tick(pb_server* srv) {
         if (!g.exec) {
             if (r->j < 1) return body();
             {
-                std::lock_guard<std::mutex> dev_lock(srv->device_mu);
+                std::unique_lock<std::shared_mutex> dev_lock(srv->device_mu);
                 PB_TRY(graph_capture(g, rs_of(r), body));
             }
             if (g.failed) return body();
@@ -426,6 +428,24 @@ static int tick(pb_server* srv) {
 
 using namespace pb;
 
+// Admission threads: each sets up one request at a time on its own stream, so
+// the host work of one request's mesh ingest overlaps another's near build.
+constexpr int ADMIT_THREADS = 2;
+
+static void destroy_streams(pb_server* srv) {
+    for (cudaStream_t q : srv->slot_stream)
+        if (q) cudaStreamDestroy(q);
+    for (cudaEvent_t e : srv->slot_event)
+        if (e) cudaEventDestroy(e);
+    for (cudaStream_t q : srv->s_setup)
+        if (q) cudaStreamDestroy(q);
+    if (srv->s_main) cudaStreamDestroy(srv->s_main);
+    srv->slot_stream.clear();
+    srv->slot_event.clear();
+    srv->s_setup.clear();
+    srv->s_main = nullptr;
+}
+
 extern "C" int pb_server_create(pb_ctx* ctx, int64_t hbm_budget_bytes, int max_active, pb_server** out) {
     if (!ctx || !out || hbm_budget_bytes <= 0 || max_active < 1)
         return set_error(PB_EINVAL, "pb_server_create: bad argument");
@@ -435,39 +455,32 @@ extern "C" int pb_server_create(pb_ctx* ctx, int64_t hbm_budget_bytes, int max_a
     srv->ctx = ctx;
     srv->budget = (size_t)hbm_budget_bytes;
     srv->max_active = max_active;
-    if (cudaStreamCreateWithFlags(&srv->s_main, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&srv->s_setup, cudaStreamNonBlocking) != cudaSuccess) {
+    srv->s_setup.assign(ADMIT_THREADS, nullptr);
+    srv->slot_stream.assign(max_active, nullptr);
+    srv->slot_event.assign(max_active, nullptr);
+    bool ok = cudaStreamCreateWithFlags(&srv->s_main, cudaStreamNonBlocking) == cudaSuccess;
+    for (int k = 0; ok && k < ADMIT_THREADS; ++k)
+        ok = cudaStreamCreateWithFlags(&srv->s_setup[k], cudaStreamNonBlocking) == cudaSuccess;
+    // per slot: the active request's stream and its join event
+    for (int k = 0; ok && k < max_active; ++k)
+        ok = cudaStreamCreateWithFlags(&srv->slot_stream[k], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&srv->slot_event[k], cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        destroy_streams(srv);
         delete srv;
-        return set_error(PB_ECUDA, "stream creation failed");
+        return set_error(PB_ECUDA, "pb_server_create: stream creation failed");
     }
     // one residual row per slot, fixed for a request's lifetime (captured graphs write to it)
     if (dev_alloc((void**)&srv->res_dev, sizeof(double) * 4 * max_active) != PB_OK ||
         cudaMallocHost((void**)&srv->res_host, sizeof(double) * 4 * max_active) != cudaSuccess) {
         if (srv->res_dev) cudaFree(srv->res_dev);
-        cudaStreamDestroy(srv->s_main);
-        cudaStreamDestroy(srv->s_setup);
+        destroy_streams(srv);
         delete srv;
         return set_error(PB_ENOMEM, "pb_server_create: residual table");
     }
     cudaMemset(srv->res_dev, 0, sizeof(double) * 4 * max_active);
     for (int k = max_active - 1; k >= 0; --k) srv->free_slots.push_back(k);
-    srv->slot_stream.assign(max_active, nullptr);
-    srv->slot_event.assign(max_active, nullptr);
-    for (int k = 0; k < max_active; ++k)
-        if (cudaStreamCreateWithFlags(&srv->slot_stream[k], cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&srv->slot_event[k], cudaEventDisableTiming) != cudaSuccess) {
-            for (cudaStream_t q : srv->slot_stream)
-                if (q) cudaStreamDestroy(q);
-            for (cudaEvent_t e : srv->slot_event)
-                if (e) cudaEventDestroy(e);
-            cudaFree(srv->res_dev);
-            cudaFreeHost(srv->res_host);
-            cudaStreamDestroy(srv->s_main);
-            cudaStreamDestroy(srv->s_setup);
-            delete srv;
-            return set_error(PB_ECUDA, "pb_server_create: request streams");
-        }
-    srv->admit_thread = std::thread(admission_loop, srv);
+    for (int k = 0; k < ADMIT_THREADS; ++k) srv->admit_threads.emplace_back(admission_loop, srv, k);
     *out = srv;
     return PB_OK;
 }
@@ -479,21 +492,17 @@ extern "C" int pb_server_destroy(pb_server* srv) {
         srv->stop = true;
         srv->cv.notify_all();
     }
-    if (srv->admit_thread.joinable()) srv->admit_thread.join();
+    for (std::thread& t : srv->admit_threads)
+        if (t.joinable()) t.join();
     cudaSetDevice(srv->ctx->device);
     cudaDeviceSynchronize();
     for (ServeReq* r : srv->active) { free_req(r); delete r; }
     for (ServeReq* r : srv->ready) { free_req(r); delete r; }
     for (ServeReq* r : srv->waiting) delete r;
     batch_scratch_free(srv->bs);
-    for (cudaStream_t q : srv->slot_stream)
-        if (q) cudaStreamDestroy(q);
-    for (cudaEvent_t e : srv->slot_event)
-        if (e) cudaEventDestroy(e);
     if (srv->res_dev) cudaFree(srv->res_dev);
     if (srv->res_host) cudaFreeHost(srv->res_host);
-    cudaStreamDestroy(srv->s_main);
-    cudaStreamDestroy(srv->s_setup);
+    destroy_streams(srv);
     delete srv;
     return PB_OK;
 }
