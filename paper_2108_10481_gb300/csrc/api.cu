@@ -21,7 +21,9 @@ static std::atomic<int64_t> g_launches{0};
 static thread_local StepGraph* t_capture = nullptr;
 static std::atomic<uint64_t> g_ws_gen{1};
 
-uint64_t ws_generation() { return g_ws_gen.load(); }
+uint64_t ws_generation(const uint64_t* d0, const uint64_t* d1) {
+    return g_ws_gen.load() + (d0 ? *d0 : 0) + (d1 ? *d1 : 0);
+}
 void ws_bump() { g_ws_gen.fetch_add(1); }
 
 void count_launch(int n) {
@@ -40,14 +42,15 @@ void graph_free(StepGraph& g) {
     g = StepGraph();
 }
 
-int graph_capture(StepGraph& g, cudaStream_t s, const std::function<int()>& body) {
+int graph_capture(StepGraph& g, cudaStream_t s, const std::function<int()>& body, const uint64_t* d0,
+                  const uint64_t* d1) {
     graph_free(g);
     if (cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
         cudaGetLastError();
         g.failed = true;
         return PB_OK;
     }
-    const uint64_t gen = ws_generation();
+    const uint64_t gen = ws_generation(d0, d1);
     t_capture = &g;
     const int rc = body();
     t_capture = nullptr;
@@ -63,7 +66,7 @@ int graph_capture(StepGraph& g, cudaStream_t s, const std::function<int()>& body
         g.failed = true;
         return PB_OK;
     }
-    if (ws_generation() != gen) {  // the body moved a workspace while it was captured
+    if (ws_generation(d0, d1) != gen) {  // the body moved a workspace while it was captured
         graph_free(g);
         g.failed = true;
         return PB_OK;
@@ -72,8 +75,8 @@ int graph_capture(StepGraph& g, cudaStream_t s, const std::function<int()>& body
     return PB_OK;
 }
 
-void graph_check(StepGraph& g) {
-    if (g.exec && g.gen != ws_generation()) graph_free(g);
+void graph_check(StepGraph& g, const uint64_t* d0, const uint64_t* d1) {
+    if (g.exec && g.gen != ws_generation(d0, d1)) graph_free(g);
 }
 
 int graph_replay(StepGraph& g, cudaStream_t s) {
@@ -167,7 +170,8 @@ int dev_alloc(void** p, size_t bytes) {
 
 int ws_reserve(Workspace& w, size_t bytes) {
     if (bytes <= w.bytes) return PB_OK;
-    g_ws_gen.fetch_add(1);
+    if (w.gen) ++*w.gen;
+    else g_ws_gen.fetch_add(1);
     ws_free(w);
     PB_TRY(dev_alloc(&w.ptr, bytes));
     w.bytes = bytes;
@@ -175,7 +179,10 @@ int ws_reserve(Workspace& w, size_t bytes) {
 }
 
 void ws_free(Workspace& w) {
-    if (w.ptr) g_ws_gen.fetch_add(1);
+    if (w.ptr) {
+        if (w.gen) ++*w.gen;
+        else g_ws_gen.fetch_add(1);
+    }
     if (w.ptr) cudaFree(w.ptr);
     w.ptr = nullptr;
     w.bytes = 0;

@@ -64,6 +64,10 @@ struct Rule {
 struct Workspace {
     void* ptr = nullptr;
     size_t bytes = 0;
+    // generation counter bumped when the buffer moves or is freed: its owning
+    // mesh's (graphs capturing that mesh's work check it), or null for the
+    // process-wide counter
+    uint64_t* gen = nullptr;
 };
 
 }  // namespace pb
@@ -95,14 +99,18 @@ struct StepGraph {
 };
 StepGraph* capturing();  // the graph this thread is capturing, or null
 // Counts workspace (re)allocations: a captured graph whose generation differs
-// may hold a freed pointer and must be captured again.
-uint64_t ws_generation();
-void ws_bump();  // a buffer a graph may hold was freed
-// Drop g if a workspace has moved since it was captured.
-void graph_check(StepGraph& g);
+// may hold a freed pointer and must be captured again. The generation a graph
+// depends on is the process-wide counter plus the counters of the meshes whose
+// workspaces it uses (d0, d1; null: none), so that a mesh loaded or freed for
+// one request does not invalidate the graphs of another.
+uint64_t ws_generation(const uint64_t* d0 = nullptr, const uint64_t* d1 = nullptr);
+void ws_bump();  // a buffer a graph may hold was freed (process-wide)
+// Drop g if a workspace it depends on has moved since it was captured.
+void graph_check(StepGraph& g, const uint64_t* d0 = nullptr, const uint64_t* d1 = nullptr);
 // Capture body() on stream s (nothing runs); on failure g.failed is set and
 // PB_OK returned so that the caller runs the body directly.
-int graph_capture(StepGraph& g, cudaStream_t s, const std::function<int()>& body);
+int graph_capture(StepGraph& g, cudaStream_t s, const std::function<int()>& body, const uint64_t* d0 = nullptr,
+                  const uint64_t* d1 = nullptr);
 int graph_replay(StepGraph& g, cudaStream_t s);
 // after a replay has completed: its profiled launches into the context's
 // statistics; j = the Arnoldi step the replay ran (work that grows with j)
@@ -192,6 +200,7 @@ struct pb_mesh {
     int* status = nullptr;          // device status word of bounded waits (0 = fine)
     // workspaces (grown on demand)
     pb::Workspace ws_src, ws_part, ws_tri, ws_vec, ws_comb, ws_tree;
+    uint64_t ws_gen = 0;  // bumped when one of the workspaces above moves or is freed
     pb::PbTree* tree = nullptr;  // built on the first treecode application
     size_t device_bytes = 0;
 };
@@ -263,6 +272,8 @@ struct FarJob {
     const double* comb = nullptr;  // B's combined near values (null: combined into the mesh's workspace)
 };
 struct BatchScratch {
+    BatchScratch() { table.gen = &table_gen; }
+    uint64_t table_gen = 0;           // the table's own counter: no captured graph uses the table
     Workspace table;                  // job and work-item tables on the device
     std::vector<cudaEvent_t> ev;      // per job: its stream's work before the shared launch
     cudaEvent_t ev_main = nullptr;    // the shared launch, before the jobs' own reductions

@@ -870,6 +870,7 @@ extern "C" int pb_mesh_load(pb_ctx* ctx, const double* verts, int64_t n_verts, c
     *out = nullptr;
     PB_CUDA(cudaSetDevice(ctx->device));
     pb_mesh* m = new pb_mesh();
+    for (Workspace* w : {&m->ws_src, &m->ws_part, &m->ws_tri, &m->ws_vec, &m->ws_comb, &m->ws_tree}) w->gen = &m->ws_gen;
     int rc = load(ctx, verts, n_verts, tris, n_tris, plan, mem, m);
     if (rc != PB_OK) {
         free_mesh_arrays(m);

@@ -263,13 +263,13 @@ static int tick(pb_server* srv) {
     auto rs_of = [&](const ServeReq* r) { return srv->slot_stream[r->slot]; };
     // an iteration piece from its CUDA graph once the request has run it once
     auto piece = [&](ServeReq* r, StepGraph& g, const std::function<int()>& body) -> int {
-        graph_check(g);
+        graph_check(g, &r->m->ws_gen);
         if (!srv->ctx->graphs || g.failed) return body();
         if (!g.exec) {
             if (r->j < 1) return body();
             {
                 std::unique_lock<std::shared_mutex> dev_lock(srv->device_mu);
-                PB_TRY(graph_capture(g, rs_of(r), body));
+                PB_TRY(graph_capture(g, rs_of(r), body, &r->m->ws_gen));
             }
             if (g.failed) return body();
         }

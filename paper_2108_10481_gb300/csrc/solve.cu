@@ -426,12 +426,14 @@ static int gm_iteration(Solver& S, GmresWork& G, int prec) {
 static int iterate(Solver& S, GmresWork& G, int prec, int j, StepGraph** replayed) {
     *replayed = nullptr;
     StepGraph& g = S.step[prec & 3];
-    graph_check(g);
+    const uint64_t* d0 = &S.m->ws_gen;
+    const uint64_t* d1 = S.mc != S.m ? &S.mc->ws_gen : nullptr;
+    graph_check(g, d0, d1);
     if (!S.graphs || g.failed || (j == 0 && !g.exec)) return gm_iteration(S, G, prec);
     if (!g.exec) {
         const int a0 = S.applies;
         PhaseTrace tr("gmres");
-        PB_TRY(graph_capture(g, S.s, [&] { return gm_iteration(S, G, prec); }));
+        PB_TRY(graph_capture(g, S.s, [&] { return gm_iteration(S, G, prec); }, d0, d1));
         tr.lap("capture");
         g.applies = S.applies - a0;
         S.applies = a0;

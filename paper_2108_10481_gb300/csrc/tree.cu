@@ -497,7 +497,7 @@ int tree_prepare(const pb_mesh* mc, const FarPlan& fp, const double* x, bool nee
     if (m->tree && (m->tree->n != ctx->tree_order + 1 || m->tree->theta != ctx->tree_theta)) {
         tree_free(m->tree);  // the settings changed: a new tree (captured graphs must not keep the old one)
         m->tree = nullptr;
-        ws_bump();
+        ++m->ws_gen;
     }
     if (!m->tree) PB_TRY(build_tree(m, ctx->tree_order, ctx->tree_theta, &m->tree));
     PbTree* t = m->tree;
