@@ -213,6 +213,26 @@ def test_relaxed_plan_matches_oracle(pb, ctx):
         assert rel(y, getattr(o, op) @ x) < 1e-12
 
 
+@pytest.mark.parametrize("orders", [(3, 5, 2), (5, 2, 3), (2, 4, 5)])
+def test_per_class_singular_orders_match_oracle(pb, ctx, orders):
+    """Plans with a singular order per class of pair (coincident, edge,
+    vertex; the edge and vertex classes take their own launches and outer
+    tables, with and without the fixed-size inner loop) against the oracle
+    assembled with the same plan: every FP64 operator to 1e-12."""
+    name = "uv"
+    nc, ne, nv_ = orders
+    v, t, _, _ = mesh_case(name)
+    m = pb.pb_mesh_load(ctx, v, t, far_q=6, n_ss=4, n_ss_coin=nc, n_ss_edge=ne, n_ss_vert=nv_)
+    nf = pb.pb_near_build(ctx, m, PHYS.kappa)
+    o = oracle.assemble(v, t, PHYS.kappa, O.Plan(6, 4, n_ss_coin=nc, n_ss_edge=ne, n_ss_vert=nv_))
+    x = np.random.default_rng(9).standard_normal(o.n)
+    for op in ("VL", "KL", "DL", "VY", "KY", "DY", "TY"):
+        code, kern = OPS[op]
+        y = pb.pb_op_apply(ctx, m, nf, code, kern, pb.PB_F64, cuda(x)).cpu().numpy()
+        e = rel(y, getattr(o, op) @ x)
+        assert e < 1e-12, (orders, op, e)
+
+
 def test_errors_are_reported(pb, ctx):
     from synth import icosphere
     v, t = icosphere(1, 1.0)
@@ -233,6 +253,9 @@ def test_errors_are_reported(pb, ctx):
     with pytest.raises(pb.PBError) as e:
         pb.pb_mesh_load(ctx, v, t, far_q=5)
     assert e.value.code == -1
+    with pytest.raises(pb.PBError) as e:  # a per-class singular order out of range
+        pb.pb_mesh_load(ctx, v, t, n_ss_vert=13)
+    assert e.value.code == -1
     m, nf = gpu_mesh(pb, ctx, "ico2")
     vv, tt, xq, q = mesh_case("ico2")
     P = params(pb)
@@ -245,4 +268,7 @@ def test_errors_are_reported(pb, ctx):
     assert info["status"] == -4 and info["iters"] == 1 and info["rel_residual"] < 1.0
     with pytest.raises(pb.PBError) as e:
         pb.pb_rhs_charges(ctx, m, cuda(xq[:0]), cuda(q[:0]), P, "direct_int")
+    assert e.value.code == -1
+    with pytest.raises(pb.PBError) as e:  # the charge sums take PB_F64 or PB_F32_ACCURATE only
+        pb.pb_rhs_charges(ctx, m, cuda(xq), cuda(q), P, "direct_int", prec=pb.PB_F32)
     assert e.value.code == -1
