@@ -263,20 +263,6 @@ __device__ __forceinline__ double exp_nonpos(double x) {
     return x < -700.0 ? 0.0 : __longlong_as_double(bits);
 }
 
-// 1/sqrt(r2) in FP64 for r2 in the normal FP32 range: the FP32 hardware
-// estimate (relative error below 2^-22) and two Newton steps for
-// f(y) = y^-2 - r2, y <- y + y (1 - r2 y^2) / 2, each squaring the relative
-// error (2^-44, then rounding level): about 2 ulp, in 8 FP64 operations.
-__device__ __forceinline__ double rsqrt_nr(double x) {
-    float yf;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(yf) : "f"(__double2float_rn(x)));
-    double y = (double)yf;
-    double e = __fma_rn(-(x * y), y, 1.0);
-    y = __fma_rn(0.5 * y, e, y);
-    e = __fma_rn(-(x * y), y, 1.0);
-    return __fma_rn(0.5 * y, e, y);
-}
-
 // Accumulators: SL[9], SY[9], KL[9], KY[9], sum w G_L, sum w G_Y (38); with
 // the reversed pair also KTL[9], KTY[9] (56): the double-layer kernel with the
 // normal of the first triangle, which is the K block of the reversed pair.
@@ -289,7 +275,7 @@ __device__ __forceinline__ void accum_point(double* acc, double w, const double*
                                             const double* ly, double kappa) {
     const double d0 = x[0] - y[0], d1 = x[1] - y[1], d2 = x[2] - y[2];
     const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
-    const double rinv = rsqrt_nr(r2);
+    const double rinv = rsqrt(r2);
     const double r = r2 * rinv;
     const double gl = rinv * 0.07957747154594767;  // 1 / (4 pi r)
     const double ek = exp_nonpos(-kappa * r);
@@ -338,7 +324,7 @@ template <bool SYM>
 __device__ __forceinline__ void adj_kernels(const double* d, const TriFrame& A, const TriFrame& B, double kappa,
                                             double* g) {
     const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-    const double rinv = rsqrt_nr(r2);
+    const double rinv = rsqrt(r2);
     const double r = r2 * rinv;
     const double gl = rinv * 0.07957747154594767;  // 1 / (4 pi r)
     const double ek = exp_nonpos(-kappa * r);
@@ -419,7 +405,7 @@ __device__ __forceinline__ void accum_coin_frame(double* mom, const SSTable& tab
 #pragma unroll
     for (int k = 0; k < 3; ++k) d[k] = __fma_rn(dt, A.e2[k], ds * A.e1[k]);
     const double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-    const double rinv = rsqrt_nr(r2);
+    const double rinv = rsqrt(r2);
     const double gl = rinv * 0.07957747154594767;  // 1 / (4 pi r)
     const double gy = exp_nonpos(-kappa * (r2 * rinv)) * gl;
     double m[9];
@@ -628,7 +614,7 @@ __device__ __forceinline__ void accum_v(double* acc, double w, const double* x, 
                                         const double* ly, double kappa) {
     const double d0 = x[0] - y[0], d1 = x[1] - y[1], d2 = x[2] - y[2];
     const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
-    const double rinv = rsqrt_nr(r2);
+    const double rinv = rsqrt(r2);
     const double gl = rinv * 0.07957747154594767;  // 1 / (4 pi r)
     const double gy = exp_nonpos(-kappa * (r2 * rinv)) * gl;
     for (int a = 0; a < 3; ++a) {
@@ -747,7 +733,7 @@ __device__ __forceinline__ void band_pass(double* acc, const double (&pa)[3][3],
             const double d0 = x[0] - ys[(3 * j) * BAND_THREADS], d1 = x[1] - ys[(3 * j + 1) * BAND_THREADS],
                          d2 = x[2] - ys[(3 * j + 2) * BAND_THREADS];
             const double r2 = d0 * d0 + d1 * d1 + d2 * d2;
-            const double rinv = rsqrt_nr(r2);
+            const double rinv = rsqrt(r2);
             const double r = r2 * rinv;
             const double gl = rinv * 0.07957747154594767;  // 1 / (4 pi r)
             const double ek = exp_nonpos(-kappa * r);

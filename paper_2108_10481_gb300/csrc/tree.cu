@@ -27,8 +27,8 @@
 
 namespace pb {
 
-constexpr int TREE_MAXN = 8;
-constexpr int TREE_MAX_SPLITS = 8;  // CTAs sharing one leaf's interaction lists       // largest Chebyshev order + 1
+constexpr int TREE_MAXN = 8;        // largest Chebyshev order + 1
+constexpr int TREE_MAX_SPLITS = 8;  // CTAs sharing one leaf's interaction lists
 
 // ---------------------------------------------------------------- host tree
 struct HostNode {
@@ -44,6 +44,7 @@ struct PbTree {
     int64_t nleaf = 0, nslot = 0;
     int32_t* perm = nullptr;      // tree index -> point index
     int32_t* leaf_rng = nullptr;  // 2 per leaf
+    int32_t* leaf_order = nullptr;// leaves by decreasing interaction count (launch order)
     int32_t* far_ptr = nullptr;   // nleaf + 1
     int32_t* far_idx = nullptr;   // proxy slots
     int32_t* near_ptr = nullptr;  // nleaf + 1
@@ -206,6 +207,17 @@ static int build_tree(pb_mesh* m, int order, double theta, PbTree** out) {
         far_ptr.push_back((int32_t)far_idx.size());
         near_ptr.push_back((int32_t)(near_rng.size() / 2));
     }
+    // launch order: the leaves with the most interactions first, so that the CTAs the scheduler
+    // hands out last are the short ones (longest-first list scheduling)
+    std::vector<int64_t> cost(leaves.size(), 0);
+    for (size_t l = 0; l < leaves.size(); ++l) {
+        int64_t c = (int64_t)(far_ptr[l + 1] - far_ptr[l]) * nprox;
+        for (int32_t k = near_ptr[l]; k < near_ptr[l + 1]; ++k) c += near_rng[2 * k + 1] - near_rng[2 * k];
+        cost[l] = c * (leaf_rng[2 * l + 1] - leaf_rng[2 * l]);
+    }
+    std::vector<int32_t> leaf_order(leaves.size());
+    std::iota(leaf_order.begin(), leaf_order.end(), 0);
+    std::stable_sort(leaf_order.begin(), leaf_order.end(), [&](int32_t a, int32_t b) { return cost[a] > cost[b]; });
     // the slots whose proxies are read: those in a far list, and (for the transfer) every slot
     // below one of them; parents have lower slot numbers than their children
     std::vector<char> needed(nslot, 0);
@@ -228,8 +240,8 @@ static int build_tree(pb_mesh* m, int order, double theta, PbTree** out) {
     t->n_far = (int64_t)far_idx.size();
     t->n_near = (int64_t)(near_rng.size() / 2);
     // one device allocation for all arrays
-    const size_t ints = perm.size() + leaf_rng.size() + far_ptr.size() + far_idx.size() + near_ptr.size() +
-                        near_rng.size() + slot_rng.size() + slot_kids.size() + slot_order.size();
+    const size_t ints = perm.size() + leaf_rng.size() + leaf_order.size() + far_ptr.size() + far_idx.size() +
+                        near_ptr.size() + near_rng.size() + slot_rng.size() + slot_kids.size() + slot_order.size();
     const size_t bytes = sizeof(int32_t) * (ints + 8) + sizeof(float) * (slot_box.size() + 4);
     int rc = dev_alloc(&t->block, bytes);
     if (rc != PB_OK) {
@@ -245,6 +257,7 @@ static int build_tree(pb_mesh* m, int order, double theta, PbTree** out) {
     };
     t->perm = put(perm);
     t->leaf_rng = put(leaf_rng);
+    t->leaf_order = put(leaf_order);
     t->far_ptr = put(far_ptr);
     t->far_idx = put(far_idx);
     t->near_ptr = put(near_ptr);
@@ -267,7 +280,8 @@ static int build_tree(pb_mesh* m, int order, double theta, PbTree** out) {
 
 // ------------------------------------------------------------- device side
 // Source records in tree order: position (FP32, relative to the mesh centre),
-// s = w v, p = w u n, c = w curl u (the direct kernel's densities).
+// s = w v, p = w u n, c = w curl u (the direct kernel's densities), 0, 0; each
+// value stored twice (TREE_REC floats).
 __global__ void k_tree_sources(int64_t np, int Q, Rule rule, const int32_t* __restrict__ perm,
                                const int32_t* __restrict__ tris, const double* __restrict__ tgeo,
                                const double* __restrict__ pts64, const float* __restrict__ pts32,
@@ -286,15 +300,17 @@ __global__ void k_tree_sources(int64_t np, int Q, Rule rule, const int32_t* __re
     const double w = pts64[4 * pt + 3] * 0.07957747154594767;  // weight / (4 pi)
     const double uq = rule.l[q][0] * ua[0] + rule.l[q][1] * ua[1] + rule.l[q][2] * ua[2];
     const double vq = rule.l[q][0] * va[0] + rule.l[q][1] * va[1] + rule.l[q][2] * va[2];
-    float* r = rec + TREE_REC * i;
-    r[0] = pts32[4 * pt];
-    r[1] = pts32[4 * pt + 1];
-    r[2] = pts32[4 * pt + 2];
-    r[3] = (float)(w * vq);
-    for (int k = 0; k < 3; ++k) r[4 + k] = (float)(w * uq * g[k]);
+    float val[TREE_VALS];
+    val[0] = pts32[4 * pt];
+    val[1] = pts32[4 * pt + 1];
+    val[2] = pts32[4 * pt + 2];
+    val[3] = (float)(w * vq);
+    for (int k = 0; k < 3; ++k) val[4 + k] = (float)(w * uq * g[k]);
     for (int k = 0; k < 3; ++k)
-        r[7 + k] = (float)(w * inv2a * (ua[0] * g[4 + k] + ua[1] * g[7 + k] + ua[2] * g[10 + k]));
-    r[10] = r[11] = 0.f;
+        val[7 + k] = (float)(w * inv2a * (ua[0] * g[4 + k] + ua[1] * g[7 + k] + ua[2] * g[10 + k]));
+    val[10] = val[11] = 0.f;
+    float4* r = reinterpret_cast<float4*>(rec + TREE_REC * i);
+    for (int k = 0; k < TREE_VALS / 2; ++k) r[k] = make_float4(val[2 * k], val[2 * k], val[2 * k + 1], val[2 * k + 1]);
 }
 
 // Chebyshev points (second kind) of order n-1 on [-1, 1]
@@ -327,7 +343,7 @@ __device__ __forceinline__ void lagrange_n(float t, const float* tn, const float
 // the slot's interpolation (exact, the basis polynomials having the same
 // degree), any other child through its points. Sources are staged 128 at a
 // time with their 1-D basis values.
-// Proxy record: z (3), S, Q, C (3), N (3), 0.
+// Proxy record: z (3), S, Q, C (3), N (3), 0; each value stored twice.
 constexpr int PROXY_THREADS = 128;
 
 template <int N>
@@ -390,7 +406,8 @@ k_proxy_charges(const int32_t* __restrict__ slots, const int32_t* __restrict__ s
                 for (int a = 0; a < N; ++a) T[d][a][a2] = l[a];
             }
             const float* cp = prox + (int64_t)ks * NP * TREE_REC;
-            for (int k = threadIdx.x; k < NP * 8; k += PROXY_THREADS) buf0[k] = cp[(k >> 3) * TREE_REC + 3 + (k & 7)];
+            for (int k = threadIdx.x; k < NP * 8; k += PROXY_THREADS)
+                buf0[k] = cp[(k >> 3) * TREE_REC + 2 * (3 + (k & 7))];
             __syncthreads();
             for (int k = threadIdx.x; k < NP * 8; k += PROXY_THREADS) {  // x pass
                 const int c = k & 7, idx = k >> 3, a = idx / N2, rest = idx - a * N2;
@@ -434,12 +451,12 @@ k_proxy_charges(const int32_t* __restrict__ slots, const int32_t* __restrict__ s
                 const float* r = rec + TREE_REC * (int64_t)i;
 #pragma unroll
                 for (int d = 0; d < 3; ++d) {
-                    lagrange_n<N>((r[d] - mid[d]) * ihalf[d], tn, iden, my + N * d, my + N * (3 + d));
+                    lagrange_n<N>((r[2 * d] - mid[d]) * ihalf[d], tn, iden, my + N * d, my + N * (3 + d));
 #pragma unroll
                     for (int a = 0; a < N; ++a) my[N * (3 + d) + a] *= ihalf[d];  // d/dy = d/dt / half
                 }
 #pragma unroll
-                for (int c = 0; c < 7; ++c) my[6 * N + c] = r[3 + c];
+                for (int c = 0; c < 7; ++c) my[6 * N + c] = r[2 * (3 + c)];
             }
             __syncthreads();
             const int m = min(PROXY_THREADS, e - c0);
@@ -467,24 +484,30 @@ k_proxy_charges(const int32_t* __restrict__ slots, const int32_t* __restrict__ s
     for (int r = 0; r < PER; ++r) {
         const int k = threadIdx.x + r * PROXY_THREADS;
         if (k >= NP) break;
-        float* o = prox + ((int64_t)slot * NP + k) * TREE_REC;
-        o[0] = mid[0] + half[0] * tn[ka[r]];
-        o[1] = mid[1] + half[1] * tn[kb[r]];
-        o[2] = mid[2] + half[2] * tn[kc[r]];
+        float val[TREE_VALS];
+        val[0] = mid[0] + half[0] * tn[ka[r]];
+        val[1] = mid[1] + half[1] * tn[kb[r]];
+        val[2] = mid[2] + half[2] * tn[kc[r]];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) o[3 + c] = acc[r][c];
-        o[11] = 0.f;
+        for (int c = 0; c < 8; ++c) val[3 + c] = acc[r][c];
+        val[11] = 0.f;
+        float4* o = reinterpret_cast<float4*>(prox + ((int64_t)slot * NP + k) * TREE_REC);
+#pragma unroll
+        for (int c = 0; c < TREE_VALS / 2; ++c)
+            o[c] = make_float4(val[2 * c], val[2 * c], val[2 * c + 1], val[2 * c + 1]);
     }
 }
 
 // Packed pairs of FP32 values (f32x2 instructions: two targets per thread).
-// The treecode's own launch: one CTA per leaf of targets and split
-// (blockIdx.y), TREE_LEAF threads in two groups (tree_leaf_body with NQ = 2).
+// The treecode's own launch: one CTA per leaf of targets and split, TREE_LEAF
+// threads in two groups (tree_leaf_body with NQ = 2); the linear block index
+// walks the leaves longest first, a leaf's splits side by side.
 template <int MODE>
-__global__ void __launch_bounds__(TREE_LEAF) k_tree_eval(TreeJob job) {
+__global__ void __launch_bounds__(TREE_LEAF, 7) k_tree_eval(TreeJob job) {
     __shared__ __align__(16) float tile[2 * TREE_EVAL_TILE * TREE_REC];
     static_assert((MODE == 0 ? 2 : 10) * TREE_LEAF <= 2 * TREE_EVAL_TILE * TREE_REC, "reduction buffer");
-    tree_leaf_body<MODE, 2>(job, blockIdx.x, blockIdx.y, tile);
+    const int sp = (int)(blockIdx.x % (unsigned)job.nsplit);
+    tree_leaf_body<MODE, 2>(job, job.leaf_order[blockIdx.x / (unsigned)job.nsplit], sp, tile);
 }
 
 // y-part of the far field by the treecode: per-target partial sums in the
@@ -539,6 +562,7 @@ int tree_prepare(const pb_mesh* mc, const FarPlan& fp, const double* x, bool nee
     J.nsplit = S;
     J.perm = t->perm;
     J.leaf_rng = t->leaf_rng;
+    J.leaf_order = t->leaf_order;
     J.far_ptr = t->far_ptr;
     J.far_idx = t->far_idx;
     J.near_ptr = t->near_ptr;
@@ -558,7 +582,7 @@ int tree_far(const pb_mesh* m, const FarPlan& fp, const double* x, bool need_u, 
     TreeJob job;
     PB_TRY(tree_prepare(m, fp, x, need_u, need_v, &job, s));
     const PbTree* t = m->tree;
-    const dim3 grid((unsigned)t->nleaf, (unsigned)job.nsplit);
+    const unsigned grid = (unsigned)(t->nleaf * job.nsplit);
     Timer tm(m->ctx, PB_KERNEL_TREE32, s, (double)(t->direct_pairs + t->proxy_pairs), fp.mode == 0 ? 25.0 : 36.0);
     if (fp.mode == 0) k_tree_eval<0><<<grid, TREE_LEAF, 0, s>>>(job);
     else k_tree_eval<1><<<grid, TREE_LEAF, 0, s>>>(job);

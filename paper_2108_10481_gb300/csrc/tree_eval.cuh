@@ -7,7 +7,9 @@
 namespace pb {
 
 constexpr int TREE_LEAF = 128;     // targets per leaf
-constexpr int TREE_REC = 12;       // floats per tree source / proxy record
+constexpr int TREE_VALS = 12;      // values per tree source / proxy record
+constexpr int TREE_REC = 24;       // floats per record: every value twice, so that one shared-memory
+                                   // load gives both halves of a packed f32x2 operand
 constexpr int TREE_EVAL_TILE = 128;  // sources staged per round
 
 struct TreeCoef {
@@ -57,6 +59,7 @@ struct TreeJob {
     int nsplit;                 // slices of partial sums (the leaves' lists are cut into nsplit shares)
     const int32_t* perm;        // tree index -> point index
     const int32_t* leaf_rng;    // 2 per leaf
+    const int32_t* leaf_order;  // leaves by decreasing interaction count
     const int32_t* far_ptr;     // per leaf: its proxied clusters
     const int32_t* far_idx;
     const int32_t* near_ptr;    // per leaf: its directly summed source ranges
@@ -141,13 +144,13 @@ __device__ __forceinline__ void tree_leaf_body(const TreeJob& T, int leaf, int s
     float2 X0 = t_splat(0.f), X1 = X0, X2 = X0;
     if (live0) {
         X0.x = rec[TREE_REC * (int64_t)ti0];
-        X1.x = rec[TREE_REC * (int64_t)ti0 + 1];
-        X2.x = rec[TREE_REC * (int64_t)ti0 + 2];
+        X1.x = rec[TREE_REC * (int64_t)ti0 + 2];
+        X2.x = rec[TREE_REC * (int64_t)ti0 + 4];
     }
     if (live1) {
         X0.y = rec[TREE_REC * (int64_t)ti1];
-        X1.y = rec[TREE_REC * (int64_t)ti1 + 1];
-        X2.y = rec[TREE_REC * (int64_t)ti1 + 2];
+        X1.y = rec[TREE_REC * (int64_t)ti1 + 2];
+        X2.y = rec[TREE_REC * (int64_t)ti1 + 4];
     }
     const TreeCoef& cf = T.cf;
     const float2 c00 = t_splat(cf.k[0][0]), c01 = t_splat(cf.k[0][1]), c02 = t_splat(cf.k[0][2]),
@@ -181,15 +184,17 @@ __device__ __forceinline__ void tree_leaf_body(const TreeJob& T, int leaf, int s
         if (any && far) {
 #pragma unroll 2
             for (int j = grp; j < cnt; j += NQ) {
-                const float* z = cur + TREE_REC * j;
-                const float2 d0 = t_sub2(X0, t_splat(z[0])), d1 = t_sub2(X1, t_splat(z[1])),
-                             d2 = t_sub2(X2, t_splat(z[2]));
+                // the record's values, each as a splatted pair
+                const float4* z4 = reinterpret_cast<const float4*>(cur + TREE_REC * j);
+                const float4 a = z4[0], b = z4[1], c = z4[2];
+                const float2 d0 = t_sub2(X0, make_float2(a.x, a.y)), d1 = t_sub2(X1, make_float2(a.z, a.w)),
+                             d2 = t_sub2(X2, make_float2(b.x, b.y));
                 const float2 r2 = t_fma2(d0, d0, t_fma2(d1, d1, t_mul2(d2, d2)));
                 const float2 rinv = make_float2(t_rsqrt(r2.x), t_rsqrt(r2.y));
                 const float2 rr = t_mul2(r2, rinv);
                 const float2 arg = t_mul2(rr, mk2);
                 const float2 e = make_float2(t_ex2(arg.x), t_ex2(arg.y));
-                const float2 gs = t_mul2(rinv, t_splat(z[3])), gq = t_mul2(rinv, t_splat(z[4]));
+                const float2 gs = t_mul2(rinv, make_float2(b.z, b.w)), gq = t_mul2(rinv, make_float2(c.x, c.y));
                 acc[0] = t_fma2(t_fma2(c01, e, c00), gs, acc[0]);
                 acc[0] = t_fma2(t_fma2(c03, e, c02), gq, acc[0]);
                 if (MODE == 0) {
@@ -201,22 +206,26 @@ __device__ __forceinline__ void tree_leaf_body(const TreeJob& T, int leaf, int s
                     acc[1] = t_fma2(ts, d0, acc[1]);
                     acc[2] = t_fma2(ts, d1, acc[2]);
                     acc[3] = t_fma2(ts, d2, acc[3]);
+                    const float4 dd = z4[3], ee = z4[4], ff = z4[5];
                     const float2 gc = t_mul2(t_fma2(c11, e, c10), rinv);
-                    acc[4] = t_fma2(gc, t_splat(z[5]), acc[4]);
-                    acc[5] = t_fma2(gc, t_splat(z[6]), acc[5]);
-                    acc[6] = t_fma2(gc, t_splat(z[7]), acc[6]);
+                    acc[4] = t_fma2(gc, make_float2(c.z, c.w), acc[4]);
+                    acc[5] = t_fma2(gc, make_float2(dd.x, dd.y), acc[5]);
+                    acc[6] = t_fma2(gc, make_float2(dd.z, dd.w), acc[6]);
                     const float2 gb = t_mul2(e, rinv);
-                    acc[7] = t_fma2(gb, t_splat(z[8]), acc[7]);
-                    acc[8] = t_fma2(gb, t_splat(z[9]), acc[8]);
-                    acc[9] = t_fma2(gb, t_splat(z[10]), acc[9]);
+                    acc[7] = t_fma2(gb, make_float2(ee.x, ee.y), acc[7]);
+                    acc[8] = t_fma2(gb, make_float2(ee.z, ee.w), acc[8]);
+                    acc[9] = t_fma2(gb, make_float2(ff.x, ff.y), acc[9]);
                 }
             }
         } else if (any) {
 #pragma unroll 2
             for (int j = grp; j < cnt; j += NQ) {
-                const float* y = cur + TREE_REC * j;
-                const float2 d0 = t_sub2(X0, t_splat(y[0])), d1 = t_sub2(X1, t_splat(y[1])),
-                             d2 = t_sub2(X2, t_splat(y[2]));
+                const float4* y4 = reinterpret_cast<const float4*>(cur + TREE_REC * j);
+                const float4 a = y4[0], b = y4[1], c = y4[2], dd = y4[3];
+                const float2 y0 = make_float2(a.x, a.y), y1 = make_float2(a.z, a.w), y2 = make_float2(b.x, b.y),
+                             y3 = make_float2(b.z, b.w), y4v = make_float2(c.x, c.y), y5 = make_float2(c.z, c.w),
+                             y6 = make_float2(dd.x, dd.y);
+                const float2 d0 = t_sub2(X0, y0), d1 = t_sub2(X1, y1), d2 = t_sub2(X2, y2);
                 const float2 r2 = t_fma2(d0, d0, t_fma2(d1, d1, t_mul2(d2, d2)));
                 const float2 rinv = make_float2(r2.x > 0.f ? t_rsqrt(r2.x) : 0.f, r2.y > 0.f ? t_rsqrt(r2.y) : 0.f);
                 const float2 rr = t_mul2(r2, rinv);
@@ -224,26 +233,27 @@ __device__ __forceinline__ void tree_leaf_body(const TreeJob& T, int leaf, int s
                 const float2 e = make_float2(t_ex2(arg.x), t_ex2(arg.y));
                 const float2 ek = t_fma2(e, t_mul2(rr, kap), e);
                 const float2 rinv3 = t_mul2(t_mul2(rinv, rinv), rinv);
-                const float2 dp = t_fma2(d0, t_splat(y[4]), t_fma2(d1, t_splat(y[5]), t_mul2(d2, t_splat(y[6]))));
-                const float2 rs = t_mul2(rinv, t_splat(y[3])), r3dp = t_mul2(rinv3, dp);
+                const float2 dp = t_fma2(d0, y4v, t_fma2(d1, y5, t_mul2(d2, y6)));
+                const float2 rs = t_mul2(rinv, y3), r3dp = t_mul2(rinv3, dp);
                 acc[0] = t_fma2(t_fma2(c01, e, c00), rs, acc[0]);
                 acc[0] = t_fma2(t_fma2(c03, ek, c02), r3dp, acc[0]);
                 if (MODE == 0) {
                     acc[1] = t_fma2(t_fma2(c11, e, c10), rs, acc[1]);
                     acc[1] = t_fma2(t_fma2(c13, ek, c12), r3dp, acc[1]);
                 } else {
-                    const float2 ts = t_mul2(t_fma2(c13, ek, c12), t_mul2(rinv3, t_splat(y[3])));
+                    const float4 ee = y4[4];
+                    const float2 ts = t_mul2(t_fma2(c13, ek, c12), t_mul2(rinv3, y3));
                     acc[1] = t_fma2(ts, d0, acc[1]);
                     acc[2] = t_fma2(ts, d1, acc[2]);
                     acc[3] = t_fma2(ts, d2, acc[3]);
                     const float2 gc = t_mul2(t_fma2(c11, e, c10), rinv);
-                    acc[4] = t_fma2(gc, t_splat(y[7]), acc[4]);
-                    acc[5] = t_fma2(gc, t_splat(y[8]), acc[5]);
-                    acc[6] = t_fma2(gc, t_splat(y[9]), acc[6]);
+                    acc[4] = t_fma2(gc, make_float2(dd.z, dd.w), acc[4]);
+                    acc[5] = t_fma2(gc, make_float2(ee.x, ee.y), acc[5]);
+                    acc[6] = t_fma2(gc, make_float2(ee.z, ee.w), acc[6]);
                     const float2 gb = t_mul2(e, rinv);
-                    acc[7] = t_fma2(gb, t_splat(y[4]), acc[7]);
-                    acc[8] = t_fma2(gb, t_splat(y[5]), acc[8]);
-                    acc[9] = t_fma2(gb, t_splat(y[6]), acc[9]);
+                    acc[7] = t_fma2(gb, y4v, acc[7]);
+                    acc[8] = t_fma2(gb, y5, acc[8]);
+                    acc[9] = t_fma2(gb, y6, acc[9]);
                 }
             }
         }
