@@ -130,12 +130,27 @@ __device__ __forceinline__ bool share_vertex_dev(const int32_t* a, const int32_t
 struct BandGrid {
     const double* C;      // nt x 3 centroids
     const double* R;      // nt radii
+    const float4* CR32;   // nt: centroid relative to the box centre, radius, in FP32 (the prefilter)
+    float slack;          // absolute margin of the prefilter: 4 x 2^-23 x the largest centred coordinate
     const int32_t* cstart;  // ncell + 1
     const int32_t* ctri;    // triangles by cell
     const int32_t* tcell;   // cell of each triangle
     int64_t dim[3];
     double eta;
 };
+
+// FP32 prefilter of the band test: true only where the FP64 test (band_hit)
+// is certain to fail. Rounding the centred coordinates to FP32 moves each
+// centroid difference by at most 2 x 2^-24 x the largest centred coordinate,
+// and the FP32 operations change the distance and the limit by a few units of
+// 2^-24 relative; the test demands a distance above 1.001 limits plus more
+// than twice that absolute error (the slack), far outside either.
+__device__ __forceinline__ bool band_far32(const float4& a, const float4& b, float eta, float slack) {
+    const float d0 = a.x - b.x, d1 = a.y - b.y, d2 = a.z - b.z;
+    const float q = fmaf(d0, d0, fmaf(d1, d1, d2 * d2));
+    const float lim = fmaf(1.001f * eta, a.w + b.w, slack);
+    return q > lim * lim;
+}
 
 // One warp per triangle, lanes over the candidates of the 27 cells around its
 // cell. Pass 0 counts the band partners of each triangle; pass 1 writes them
@@ -151,6 +166,8 @@ __global__ void k_band_search(int64_t nt, const int32_t* __restrict__ tris, Band
     const int64_t c = g.tcell[t];
     const int64_t c0 = c % g.dim[0], c1 = (c / g.dim[0]) % g.dim[1], c2 = c / (g.dim[0] * g.dim[1]);
     const int32_t* ft = tris + 3 * t;
+    const float4 ct = g.CR32[t];
+    const float eta32 = (float)g.eta;
     int n = 0;  // hits so far (the same in every lane)
     const int64_t base = pass ? ptr[t] : 0;
     for (int64_t z = max((int64_t)0, c2 - 1); z <= min(g.dim[2] - 1, c2 + 1); ++z)
@@ -164,8 +181,8 @@ __global__ void k_band_search(int64_t nt, const int32_t* __restrict__ tris, Band
                     bool hit = false;
                     if (k < k1) {
                         s = g.ctri[k];
-                        hit = s != (int32_t)t && band_hit(g.C, g.R, t, s, g.eta) &&
-                              !share_vertex_dev(ft, tris + 3 * (int64_t)s);
+                        hit = s != (int32_t)t && !band_far32(ct, g.CR32[s], eta32, g.slack) &&
+                              band_hit(g.C, g.R, t, s, g.eta) && !share_vertex_dev(ft, tris + 3 * (int64_t)s);
                     }
                     const unsigned m = __ballot_sync(0xffffffffu, hit);
                     if (pass && hit) bt[base + n + __popc(m & ((1u << lane) - 1u))] = s;
@@ -217,9 +234,13 @@ __global__ void k_scan(int64_t n, const int32_t* __restrict__ cnt, int32_t* __re
 
 // ---- near pattern on the device: row i holds every vertex of every triangle
 // paired (adjacent or band) with a triangle at i. One warp per row inserts the
-// candidates into a shared-memory hash set of PAT_HASH slots (a power of two,
-// sized from the largest candidate count of any row), compacts it, and (pass 1)
-// writes the columns in increasing order (each one's rank among the row's values).
+// candidates into a shared-memory hash set of PAT_HASH slots (a power of two),
+// compacts it, and (pass 1) writes the columns in increasing order (each one's
+// rank among the row's values). The candidates repeat each column many times
+// (every triangle pair that reaches it), so pass 0 starts from a small set and
+// reports in *ovf a row that did not fit (the host then retries with a larger
+// set, up to twice the largest candidate count); pass 1 is sized from the
+// largest column count that pass 0 found.
 
 // candidates of each row (with repetitions): an upper bound of its columns
 __global__ void k_row_candidates(int64_t nv, const int32_t* __restrict__ v2t_ptr, const int32_t* __restrict__ v2t,
@@ -241,7 +262,7 @@ __global__ void k_row_pattern(int64_t nv, int pass, int PAT_HASH, int PAT_WARPS,
                               const int32_t* __restrict__ adj_ptr, const int4* __restrict__ pairs,
                               const int32_t* __restrict__ band_ptr, const int32_t* __restrict__ band_s,
                               int32_t* __restrict__ cnt, int* __restrict__ maxrow, const int32_t* __restrict__ row_ptr,
-                              int32_t* __restrict__ col, int* __restrict__ status) {
+                              int32_t* __restrict__ col, int* __restrict__ ovf, int* __restrict__ status) {
     extern __shared__ int32_t psm[];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t i = (int64_t)blockIdx.x * PAT_WARPS + w;
@@ -269,6 +290,7 @@ __global__ void k_row_pattern(int64_t nv, int pass, int PAT_HASH, int PAT_WARPS,
             }
             full |= probe == PAT_HASH;
         }
+        if (__any_sync(0xffffffffu, full)) break;  // the set is too small for this row
     }
     __syncwarp();
     int n = 0;
@@ -283,7 +305,7 @@ __global__ void k_row_pattern(int64_t nv, int pass, int PAT_HASH, int PAT_WARPS,
     }
     full = __any_sync(0xffffffffu, full) || n > PAT_HASH / 2;
     if (full) {
-        if (lane == 0) atomicExch(status, PB_EINVAL);
+        if (lane == 0) atomicExch(pass == 0 ? ovf : status, PB_EINVAL);
         return;
     }
     if (pass == 0) {
@@ -685,11 +707,24 @@ static int load(pb_ctx* ctx, const double* verts_in, int64_t nv, const int32_t* 
             std::vector<int32_t> fill(cstart.begin(), cstart.end() - 1);
             for (int64_t t = 0; t < nt; ++t) ctri[fill[tcell[t]]++] = (int32_t)t;
         }
-        // scratch on the device: C, R, grid, counts, total
-        const size_t sb = sizeof(double) * 4 * nt + sizeof(int32_t) * (ncell + 1 + 3 * nt) + 64;
+        // the prefilter's FP32 copies, centred on the box
+        std::vector<float4> CR32(nt);
+        double cmax = 0.0;
+        for (int64_t t = 0; t < nt; ++t) {
+            double c[3];
+            for (int k = 0; k < 3; ++k) {
+                c[k] = C[3 * t + k] - 0.5 * (lo[k] + hi[k]);
+                cmax = std::max(cmax, std::fabs(c[k]));
+            }
+            CR32[t] = make_float4((float)c[0], (float)c[1], (float)c[2], (float)R[t]);
+        }
+        const float slack = (float)(4.0 * std::ldexp(std::max(cmax, rmax), -23));
+        // scratch on the device: C, R, the FP32 copies, grid, counts, total
+        const size_t sb = sizeof(float4) * nt + sizeof(double) * 4 * nt + sizeof(int32_t) * (ncell + 1 + 3 * nt) + 64;
         char* scratch = nullptr;
         PB_TRY(dev_alloc((void**)&scratch, sb));
-        double* dC = (double*)scratch;
+        float4* dCR = (float4*)scratch;
+        double* dC = (double*)(dCR + nt);
         double* dR = dC + 3 * nt;
         int64_t* dtotal = (int64_t*)(dR + nt);
         int32_t* dcs = (int32_t*)(dtotal + 1);
@@ -699,7 +734,8 @@ static int load(pb_ctx* ctx, const double* verts_in, int64_t nv, const int32_t* 
         int rc = PB_OK;
         int64_t total = 0;
         do {
-            if (cudaMemcpy(dC, C.data(), sizeof(double) * 3 * nt, cudaMemcpyHostToDevice) != cudaSuccess ||
+            if (cudaMemcpy(dCR, CR32.data(), sizeof(float4) * nt, cudaMemcpyHostToDevice) != cudaSuccess ||
+                cudaMemcpy(dC, C.data(), sizeof(double) * 3 * nt, cudaMemcpyHostToDevice) != cudaSuccess ||
                 cudaMemcpy(dR, R.data(), sizeof(double) * nt, cudaMemcpyHostToDevice) != cudaSuccess ||
                 cudaMemcpy(dcs, cstart.data(), sizeof(int32_t) * (ncell + 1), cudaMemcpyHostToDevice) != cudaSuccess ||
                 cudaMemcpy(dct, ctri.data(), sizeof(int32_t) * nt, cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -707,7 +743,7 @@ static int load(pb_ctx* ctx, const double* verts_in, int64_t nv, const int32_t* 
                 rc = set_error(PB_ECUDA, "band search upload failed");
                 break;
             }
-            BandGrid g = {dC, dR, dcs, dct, dtc, {dim[0], dim[1], dim[2]}, eta};
+            BandGrid g = {dC, dR, dCR, slack, dcs, dct, dtc, {dim[0], dim[1], dim[2]}, eta};
             const unsigned nb = (unsigned)((nt * 32 + 127) / 128);  // a warp per triangle
             rc = dev_alloc((void**)&m->band_ptr, sizeof(int32_t) * (nt + 1));
             if (rc != PB_OK) break;
@@ -757,6 +793,7 @@ static int load(pb_ctx* ctx, const double* verts_in, int64_t nv, const int32_t* 
         int64_t* dtot = (int64_t*)(cntv + nv + (nv & 1));
         int* dmax = (int*)(dtot + 1);
         int* dcand = dmax + 1;
+        int* dovf = dmax + 2;
         int rc = PB_OK;
         int64_t nnz = 0;
         int hmax = 0, st = 0, maxc = 0;
@@ -772,27 +809,48 @@ static int load(pb_ctx* ctx, const double* verts_in, int64_t nv, const int32_t* 
                 rc = set_error(PB_ECUDA, "near pattern failed");
                 break;
             }
-            // hash slots: a power of two at least twice the candidates (at most 32768), warps per
-            // block so that a block stays within 160 KB of shared memory
-            PAT_HASH = 64;
-            while (PAT_HASH < 2 * maxc && PAT_HASH < 32768) PAT_HASH *= 2;
-            const size_t per_warp = sizeof(int32_t) * (size_t)(PAT_HASH + PAT_HASH / 2);
-            PAT_WARPS = (int)std::max<size_t>(1, std::min<size_t>(8, (160u << 10) / per_warp));
-            psmem = per_warp * PAT_WARPS;
-            pb_blocks = (unsigned)((nv + PAT_WARPS - 1) / PAT_WARPS);
-            // the largest allowed (227 KB; psmem is at most 6 x 32768 x 4 B = 192 KB), whatever
-            // psmem is: another host thread may load a mesh at the same time, and a smaller
-            // limit set by it must not stand when this launch runs
+            // hash slots: a power of two; pass 0 from 512 (or twice the candidates, if fewer) up to
+            // twice the candidates (at most 32768), warps per block so that a block stays within
+            // 160 KB of shared memory. The dynamic shared-memory limit is the largest allowed
+            // (227 KB; a block takes at most 6 x 32768 x 4 B = 192 KB), whatever the launch
+            // takes: another host thread may load a mesh at the same time, and a smaller limit
+            // set by it must not stand when this launch runs.
             if (cudaFuncSetAttribute(k_row_pattern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 << 10) !=
                 cudaSuccess) {
-                rc = set_error(PB_ECUDA, "near pattern: shared memory of %zu bytes refused", psmem);
+                rc = set_error(PB_ECUDA, "near pattern: shared memory refused");
                 break;
             }
-            k_row_pattern<<<pb_blocks, 32 * PAT_WARPS, psmem>>>(nv, 0, PAT_HASH, PAT_WARPS, m->v2t_ptr, m->v2t,
-                                                                 m->tris, m->adj_ptr, m->pairs, bp, m->band_s, cntv,
-                                                                 dmax, nullptr, nullptr, m->status);
+            int hash_cap = 64;
+            while (hash_cap < 2 * maxc && hash_cap < 32768) hash_cap *= 2;
+            auto shape = [&](int slots) {
+                PAT_HASH = slots;
+                const size_t per_warp = sizeof(int32_t) * (size_t)(PAT_HASH + PAT_HASH / 2);
+                PAT_WARPS = (int)std::max<size_t>(1, std::min<size_t>(8, (160u << 10) / per_warp));
+                psmem = per_warp * PAT_WARPS;
+                pb_blocks = (unsigned)((nv + PAT_WARPS - 1) / PAT_WARPS);
+            };
+            int ovf = 0;
+            for (int slots = std::min(512, hash_cap);; slots = std::min(4 * slots, hash_cap)) {
+                shape(slots);
+                if (cudaMemset(dmax, 0, 3 * sizeof(int)) != cudaSuccess) { rc = set_error(PB_ECUDA, "pattern"); break; }
+                k_row_pattern<<<pb_blocks, 32 * PAT_WARPS, psmem>>>(nv, 0, PAT_HASH, PAT_WARPS, m->v2t_ptr, m->v2t,
+                                                                     m->tris, m->adj_ptr, m->pairs, bp, m->band_s,
+                                                                     cntv, dmax, nullptr, nullptr, dovf, m->status);
+                ::pb::count_launch();
+                if (cudaMemcpy(&ovf, dovf, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
+                    rc = set_error(PB_ECUDA, "near pattern failed");
+                    break;
+                }
+                if (!ovf || slots >= hash_cap) break;
+            }
+            if (rc != PB_OK) break;
+            if (ovf) {
+                rc = set_error(PB_EINVAL, "near pattern: a row has more than %d columns (distance band too wide)",
+                               PAT_HASH / 2);
+                break;
+            }
             k_scan<<<1, 1024>>>(nv, cntv, m->row_ptr, dtot);
-            ::pb::count_launch(2);
+            ::pb::count_launch();
             if (cudaMemcpy(&nnz, dtot, sizeof(int64_t), cudaMemcpyDeviceToHost) != cudaSuccess ||
                 cudaMemcpy(&hmax, dmax, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess ||
                 cudaMemcpy(&st, m->status, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) {
@@ -811,9 +869,13 @@ static int load(pb_ctx* ctx, const double* verts_in, int64_t nv, const int32_t* 
             m->nnz = nnz;
             m->max_row = hmax;
             if ((rc = dev_alloc((void**)&m->col, sizeof(int32_t) * (nnz + 1))) != PB_OK) break;
+            // every row has at most hmax columns: a set of twice that many slots holds any of them
+            int slots1 = 64;
+            while (slots1 < 2 * hmax && slots1 < 32768) slots1 *= 2;
+            shape(std::min(slots1, PAT_HASH));
             k_row_pattern<<<pb_blocks, 32 * PAT_WARPS, psmem>>>(nv, 1, PAT_HASH, PAT_WARPS, m->v2t_ptr, m->v2t,
                                                                  m->tris, m->adj_ptr, m->pairs, bp, m->band_s, nullptr,
-                                                                 nullptr, m->row_ptr, m->col, m->status);
+                                                                 nullptr, m->row_ptr, m->col, dovf, m->status);
             ::pb::count_launch();
         } while (false);
         cudaFree(cntv);
