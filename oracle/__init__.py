@@ -10,9 +10,9 @@ itself (closed forms, invariants, brute force, library special cases); see
 tests/test_oracle_*.py. Functions without such a pin say "parity unpinned".
 """
 from .oracle import (CASES, FORMS, KCAL_PER_PAPER_UNIT, Operators, Physics, Plan, assemble,
-                     assemble_rows, gmres, interior_traces, pair_blocks, preconditioner,
+                     assemble_rows, band_pair_count, gmres, interior_traces, pair_blocks, preconditioner,
                      reaction_potential, solve, source_projections, system)
 
 __all__ = ["CASES", "FORMS", "KCAL_PER_PAPER_UNIT", "Operators", "Physics", "Plan", "assemble",
-           "assemble_rows", "gmres", "interior_traces", "pair_blocks", "preconditioner",
+           "assemble_rows", "band_pair_count", "gmres", "interior_traces", "pair_blocks", "preconditioner",
            "reaction_potential", "solve", "source_projections", "system"]

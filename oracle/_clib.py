@@ -42,6 +42,8 @@ def lib():
             L.oracle_assemble_rows.argtypes = [P, I64, P, I64, P, I64, I, P, P, P, P, P, D, D, I, P, P, I] + [P] * 7
             L.oracle_rhs.argtypes = [P, I64, P, I64, I, P, P, P, P, I64, D, P, P]
             L.oracle_reaction_potential.argtypes = [P, I64, P, I64, I, P, P, P, P, P, I64, P]
+            L.oracle_band_pair_count.argtypes = [P, P, I64, D, I]
+            L.oracle_band_pair_count.restype = I64
             for f in (L.oracle_pair_blocks, L.oracle_assemble_dense, L.oracle_assemble_rows,
                       L.oracle_rhs, L.oracle_reaction_potential):
                 f.restype = ctypes.c_int

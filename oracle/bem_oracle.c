@@ -514,6 +514,34 @@ int oracle_reaction_potential(const double* verts, int64_t nv, const int32_t* tr
     return 0;
 }
 
+/* Number of ordered triangle pairs (ti, tj), ti != tj, that share no vertex and
+ * lie in the distance band of eta (in_band): the pairs on which a banded plan
+ * uses the band rule instead of the far rule. A plain loop over all pairs. */
+int64_t oracle_band_pair_count(const double* verts, const int32_t* tris, int64_t nt, double eta, int nthreads) {
+    int64_t count = 0;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#endif
+#pragma omp parallel for schedule(dynamic, 64) reduction(+ : count)
+    for (int64_t ti = 0; ti < nt; ++ti) {
+        tri_geom t;
+        make_geom(verts, tris + 3 * ti, &t);
+        for (int64_t tj = 0; tj < nt; ++tj) {
+            if (tj == ti) continue;
+            const int32_t* A = tris + 3 * ti;
+            const int32_t* B = tris + 3 * tj;
+            int shared = 0;
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) shared |= A[a] == B[b];
+            if (shared) continue;
+            tri_geom s;
+            make_geom(verts, B, &s);
+            count += in_band(&t, &s, eta);
+        }
+    }
+    return count;
+}
+
 /* Exposed for unit tests of the singular maps: integral over [0,1]^4 of the
  * region Jacobian times s_x^a t_x^b s_y^c t_y^d, summed over the regions of
  * one kind (0 = coincident, 1 = edge, 2 = vertex). For correct maps this is

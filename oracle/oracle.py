@@ -168,6 +168,14 @@ def assemble_rows(verts, tris, rows, kappa, plan=Plan(), nthreads=0):
     return dict(zip(["VL", "KL", "DL", "VY", "KY", "DY", "M"], mats))
 
 
+def band_pair_count(verts, tris, band_eta, nthreads=0):
+    """Ordered triangle pairs that share no vertex and whose centroids are
+    closer than band_eta times the sum of their radii (largest centroid-vertex
+    distance): the pairs a banded plan integrates with its band rule."""
+    v, t = _mesh_arrays(verts, tris)
+    return int(_clib.lib().oracle_band_pair_count(_ptr(v), _ptr(t), t.shape[0], float(band_eta), int(nthreads)))
+
+
 def source_projections(verts, tris, xq, q, eps_int, plan=Plan()):
     """(b_D, b_N): the charge potential and its normal derivative tested
     against the P1 basis (paper, source projections phi_D, phi_N)."""

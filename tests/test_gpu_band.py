@@ -162,6 +162,24 @@ def test_near_kernels_are_profiled(pb, ctx):
     del nf
 
 
+@pytest.mark.parametrize("name,eta", [("uv", 2.5), ("ico3", 3.0), ("protein500", 3.0)])
+def test_band_search_finds_the_oracle_pairs(pb, ctx, name, eta):
+    """The device band search (FP32 prefilter, then the exact FP64 test) lists
+    as many pairs as the oracle's loop over all pairs selects: the banded mesh
+    holds that many pairs more than the plain one."""
+    if name == "protein500":
+        from synth import protein_like_500
+        v, t, _, _, _ = protein_like_500()
+    else:
+        v, t, _, _ = mesh_case(name)
+    mb = pb.pb_mesh_load(ctx, v, t, far_q=3, n_ss=4, band_eta=eta, band_q=6)
+    m0 = pb.pb_mesh_load(ctx, v, t, far_q=3, n_ss=4, band_eta=0.0, band_q=6)
+    n_gpu = mb.info()["n_pairs"] - m0.info()["n_pairs"]
+    n_orc = oracle.band_pair_count(v, t, eta)
+    print(f"{name} eta {eta}: band pairs GPU {n_gpu} oracle {n_orc}")
+    assert n_gpu == n_orc > 0
+
+
 def test_band_plan_errors(pb, ctx):
     v, t, _, _ = mesh_case("ico2")
     for bad in [dict(far_q=6, band_eta=2.0, band_q=6), dict(far_q=3, band_eta=-1.0), dict(far_q=3, band_eta=2.0,

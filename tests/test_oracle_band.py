@@ -7,7 +7,8 @@ closer pairs take the finer band rule. Pins:
   is the coarse plan, bit for bit;
 - classification: the banded matrices equal the coarse matrices plus, for every
   pair the criterion selects (found here by brute force over all pairs), the
-  difference of its fine and coarse blocks;
+  difference of its fine and coarse blocks; the oracle's count of band pairs
+  (which the GPU tests hold the device search to) is the brute-force count;
 - convergence: Delta G of the banded plan approaches the reference plan's as
   the band widens (the coarse rule's error falls with distance).
 """
@@ -75,6 +76,24 @@ def test_band_blocks_are_the_fine_rule_on_selected_pairs(ellipsoid, eta):
         assert np.array_equal(O.pair_blocks(v, t, i, j, KAPPA, plan_b), O.pair_blocks(v, t, i, j, KAPPA, O.Plan(6, 4)))
     for a, b in zip(banded, expect):
         assert np.abs(a - b).max() <= 1e-13 * np.abs(b).max()
+
+
+@pytest.mark.parametrize("eta", [0.0, 1.0, 2.5, 4.0, 1e6])
+def test_band_pair_count_is_the_brute_force_count(ellipsoid, eta):
+    """The oracle's band-pair count (a C loop over all pairs) against the
+    brute-force list above; the widest band holds every pair sharing no
+    vertex, counted here from the vertex incidences."""
+    v, t = ellipsoid
+    n = oracle.band_pair_count(v, t, eta)
+    assert n == len(_band_pairs(v, t, eta))
+    if eta == 0.0:
+        assert n == 0
+    if eta == 1e6:
+        nt = len(t)
+        inc = np.zeros((nt, len(v)), dtype=np.int64)
+        inc[np.repeat(np.arange(nt), 3), t.ravel()] = 1
+        sharing = int(((inc @ inc.T) > 0).sum())  # ordered pairs with a common vertex, (t, t) included
+        assert n == nt * nt - sharing
 
 
 def test_band_delta_G_approaches_the_reference_plan():
