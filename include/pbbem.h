@@ -392,8 +392,10 @@ typedef struct {
  * wave-filling split count x0.5, x1 and x2) and keep the fastest of each
  * variant in ctx for meshes of this size (same power-of-two bucket of
  * quadrature points). Later applications, solves and the server use it. out
- * may be NULL. PB_F32 applications of meshes that take the treecode do not
- * use the pair kernel, so their timings are all alike there. */
+ * may be NULL. The treecode is off while the candidates are timed (the choice
+ * is the direct pair kernel's: PB_F32 applications of meshes that take the
+ * treecode use it only when the treecode is switched off); the context must
+ * not be in use by another host thread meanwhile. */
 int pb_autotune(pb_ctx* ctx, const pb_mesh* mesh, const pb_near* near, const pb_params* prm, int form,
                 pb_tune_result* out, void* stream);
 /* Quadrature plan for a molecule: solve it (host arrays, like

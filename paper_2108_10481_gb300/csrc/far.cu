@@ -1525,6 +1525,10 @@ extern "C" int pb_autotune(pb_ctx* ctx, const pb_mesh* m, const pb_near* nf, con
     cudaEventCreate(&e0);
     cudaEventCreate(&e1);
     int rc = PB_OK;
+    // the pair kernel is what is timed: the treecode, which would otherwise take the fast
+    // variant's applications of large meshes, is off meanwhile
+    const int tree_was = ctx->tree_enable;
+    ctx->tree_enable = 0;
     for (int acc = 0; acc < 2 && rc == PB_OK; ++acc) {
         const int prec = acc ? PB_F32_ACCURATE : PB_F32;
         TuneEntry& slot = ctx->tune[fp.mode ? 1 : 0][acc][bucket];
@@ -1537,6 +1541,7 @@ extern "C" int pb_autotune(pb_ctx* ctx, const pb_mesh* m, const pb_near* nf, con
                 slot.kernel = k;
                 slot.shape = kc.second;
                 slot.split_scale = sc;
+                const uint64_t gen0 = m->ws_gen;
                 cudaEventRecord(e0, s);
                 rc = apply_blockop(m, nf, B, prec, xy, xy + n2, s);  // warm-up and workspace growth
                 if (rc != PB_OK) break;
@@ -1544,13 +1549,17 @@ extern "C" int pb_autotune(pb_ctx* ctx, const pb_mesh* m, const pb_near* nf, con
                 cudaEventSynchronize(e1);
                 float ms_total = 0.0f;
                 cudaEventElapsedTime(&ms_total, e0, e1);
-                const int reps = ms_total > 50.0f ? 1 : 3;  // long launches: one timed run each
-                cudaEventRecord(e0, s);
-                for (int r = 0; r < reps && rc == PB_OK; ++r) rc = apply_blockop(m, nf, B, prec, xy, xy + n2, s);
-                cudaEventRecord(e1, s);
-                cudaEventSynchronize(e1);
-                cudaEventElapsedTime(&ms_total, e0, e1);
-                const double ms = ms_total / reps;
+                // long launches: one timed run each, or none when the warm-up grew no workspace
+                // (its time is then a clean measurement)
+                const int reps = ms_total > 50.0f ? (m->ws_gen == gen0 ? 0 : 1) : 3;
+                if (reps > 0) {
+                    cudaEventRecord(e0, s);
+                    for (int r = 0; r < reps && rc == PB_OK; ++r) rc = apply_blockop(m, nf, B, prec, xy, xy + n2, s);
+                    cudaEventRecord(e1, s);
+                    cudaEventSynchronize(e1);
+                    cudaEventElapsedTime(&ms_total, e0, e1);
+                }
+                const double ms = ms_total / std::max(1, reps);
                 if (k == 2 && kc.second == 0 && sc == 1.0) dflt = ms;
                 if (ms < best) {
                     best = ms;
@@ -1572,6 +1581,7 @@ extern "C" int pb_autotune(pb_ctx* ctx, const pb_mesh* m, const pb_near* nf, con
             o.default_ms = dflt;
         }
     }
+    ctx->tree_enable = tree_was;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     cudaFree(xy);
