@@ -486,7 +486,9 @@ __device__ __forceinline__ void warp_allsum(double* v, int lane, double* buf) {
 
 // Six 3x3 blocks (V_L, K_L, D_L, V_Y, K_Y, D_Y) of the pair (tau, sigma), or with
 // rev = true of the reversed pair (sigma, tau): every block transposed and the
-// double layer taken from the KT accumulators.
+// double layer taken from the KT accumulators. Layout: out[6 (3a + b) + k] for
+// corner a of the test triangle, corner b of the trial one and operator k, so
+// that the six values one row-assembly lane reads are 48 contiguous bytes.
 __device__ void expand_blocks(const double* acc, const TriFrame& A, const TriFrame& B, const double* tgeoA,
                               const double* tgeoB, double kappa, bool rev, double* out) {
     double nn = A.n[0] * B.n[0] + A.n[1] * B.n[1] + A.n[2] * B.n[2];
@@ -499,12 +501,13 @@ __device__ void expand_blocks(const double* acc, const TriFrame& A, const TriFra
             double cc = f * (ea[0] * eb[0] + ea[1] * eb[1] + ea[2] * eb[2]);
             const int ab = 3 * a + b;
             const int o = rev ? 3 * b + a : ab;
-            out[0 * 9 + o] = acc[ab];
-            out[1 * 9 + o] = acc[kL + ab];
-            out[2 * 9 + o] = cc * acc[36];
-            out[3 * 9 + o] = acc[9 + ab];
-            out[4 * 9 + o] = acc[kY + ab];
-            out[5 * 9 + o] = cc * acc[37] + kappa * kappa * nn * acc[9 + ab];
+            double* e = out + 6 * o;
+            e[0] = acc[ab];
+            e[1] = acc[kL + ab];
+            e[2] = cc * acc[36];
+            e[3] = acc[9 + ab];
+            e[4] = acc[kY + ab];
+            e[5] = cc * acc[37] + kappa * kappa * nn * acc[9 + ab];
         }
 }
 
@@ -639,12 +642,13 @@ __device__ void expand_coin(const double* acc, const TriFrame& A, const double* 
             const double cc = f * (ea[0] * eb[0] + ea[1] * eb[1] + ea[2] * eb[2]);
             const int ab = 3 * a + b, ba = 3 * b + a;
             const double vl = acc[ab] + acc[ba], vy = acc[9 + ab] + acc[9 + ba];
-            out[0 * 9 + ab] = vl;
-            out[1 * 9 + ab] = 0.0;
-            out[2 * 9 + ab] = cc * (2.0 * acc[18]);
-            out[3 * 9 + ab] = vy;
-            out[4 * 9 + ab] = 0.0;
-            out[5 * 9 + ab] = cc * (2.0 * acc[19]) + kappa * kappa * nn * vy;
+            double* e = out + 6 * ab;  // the layout of expand_blocks
+            e[0] = vl;
+            e[1] = 0.0;
+            e[2] = cc * (2.0 * acc[18]);
+            e[3] = vy;
+            e[4] = 0.0;
+            e[5] = cc * (2.0 * acc[19]) + kappa * kappa * nn * vy;
         }
 }
 
@@ -904,10 +908,15 @@ __global__ void k_near_rows(int64_t nv, int64_t nnz, int maxrow, int warps, cons
                     const int4 pr = pairs[pp];
                     const int32_t j = tris[3 * (int64_t)pr.y + b];
                     spos[lane] = row_lower_bound(scol, n, j);
-                    for (int o = 0; o < 6; ++o) {
-                        const double sv = ss[54 * pp + 9 * o + ab];
-                        my[o] = sv - far[54 * pp + 9 * o + ab];
-                        my[6 + o] = sv;
+                    const double2* s2 = reinterpret_cast<const double2*>(ss + 54 * pp + 6 * ab);
+                    const double2* f2 = reinterpret_cast<const double2*>(far + 54 * pp + 6 * ab);
+#pragma unroll
+                    for (int h = 0; h < 3; ++h) {
+                        const double2 sv = s2[h], fv = f2[h];
+                        my[2 * h] = sv.x - fv.x;
+                        my[2 * h + 1] = sv.y - fv.y;
+                        my[6 + 2 * h] = sv.x;
+                        my[7 + 2 * h] = sv.y;
                     }
                     my[12] = pr.z == 0 ? tgeo[16 * (int64_t)pr.x + 3] / 12.0 * ((ab % 4 == 0) ? 2.0 : 1.0) : 0.0;
                 } else {
@@ -915,10 +924,14 @@ __global__ void k_near_rows(int64_t nv, int64_t nnz, int maxrow, int warps, cons
                     const int64_t pp = n_adj + q;
                     const int32_t j = tris[3 * (int64_t)band_s[q] + b];
                     spos[lane] = row_lower_bound(scol, n, j);
-                    for (int o = 0; o < 6; ++o) {
-                        my[o] = ss[54 * pp + 9 * o + ab];
-                        my[6 + o] = 0.0;  // band pairs never touch the diagonal
+                    const double2* s2 = reinterpret_cast<const double2*>(ss + 54 * pp + 6 * ab);
+#pragma unroll
+                    for (int h = 0; h < 3; ++h) {
+                        const double2 sv = s2[h];
+                        my[2 * h] = sv.x;
+                        my[2 * h + 1] = sv.y;
                     }
+                    for (int o = 0; o < 6; ++o) my[6 + o] = 0.0;  // band pairs never touch the diagonal
                     my[12] = 0.0;
                 }
             }
