@@ -674,7 +674,7 @@ __global__ void __launch_bounds__(TPB2) k_pair32x2_queue(const PairJob* __restri
         const PairItem it0 = items[item];
         if (it0.kind == 1) {
             if (!ACC) {
-                static_assert(ST2 * TS2 * REC2 >= 2 * TREE_EVAL_TILE * TREE_REC &&
+                static_assert(ST2 * TS2 * REC2 >= TREE_EVAL_TILE * (2 * TREE_REC + TREE_DUP) &&
                               ST2 * TS2 * REC2 >= 3 * (MODE == 0 ? 2 : 10) * TREE_LEAF, "tree scratch");
                 static_assert(TPB2 == 4 * (TREE_LEAF / 2), "tree groups");
                 tree_leaf_body<MODE, 4>(tjobs[it0.job], it0.tb, it0.split, &sh[0][0]);

@@ -280,8 +280,7 @@ static int build_tree(pb_mesh* m, int order, double theta, PbTree** out) {
 
 // ------------------------------------------------------------- device side
 // Source records in tree order: position (FP32, relative to the mesh centre),
-// s = w v, p = w u n, c = w curl u (the direct kernel's densities), 0, 0; each
-// value stored twice (TREE_REC floats).
+// s = w v, p = w u n, c = w curl u (the direct kernel's densities), 0, 0.
 __global__ void k_tree_sources(int64_t np, int Q, Rule rule, const int32_t* __restrict__ perm,
                                const int32_t* __restrict__ tris, const double* __restrict__ tgeo,
                                const double* __restrict__ pts64, const float* __restrict__ pts32,
@@ -300,7 +299,7 @@ __global__ void k_tree_sources(int64_t np, int Q, Rule rule, const int32_t* __re
     const double w = pts64[4 * pt + 3] * 0.07957747154594767;  // weight / (4 pi)
     const double uq = rule.l[q][0] * ua[0] + rule.l[q][1] * ua[1] + rule.l[q][2] * ua[2];
     const double vq = rule.l[q][0] * va[0] + rule.l[q][1] * va[1] + rule.l[q][2] * va[2];
-    float val[TREE_VALS];
+    float val[TREE_REC];
     val[0] = pts32[4 * pt];
     val[1] = pts32[4 * pt + 1];
     val[2] = pts32[4 * pt + 2];
@@ -310,7 +309,7 @@ __global__ void k_tree_sources(int64_t np, int Q, Rule rule, const int32_t* __re
         val[7 + k] = (float)(w * inv2a * (ua[0] * g[4 + k] + ua[1] * g[7 + k] + ua[2] * g[10 + k]));
     val[10] = val[11] = 0.f;
     float4* r = reinterpret_cast<float4*>(rec + TREE_REC * i);
-    for (int k = 0; k < TREE_VALS / 2; ++k) r[k] = make_float4(val[2 * k], val[2 * k], val[2 * k + 1], val[2 * k + 1]);
+    for (int k = 0; k < TREE_REC / 4; ++k) r[k] = make_float4(val[4 * k], val[4 * k + 1], val[4 * k + 2], val[4 * k + 3]);
 }
 
 // Chebyshev points (second kind) of order n-1 on [-1, 1]
@@ -343,7 +342,7 @@ __device__ __forceinline__ void lagrange_n(float t, const float* tn, const float
 // the slot's interpolation (exact, the basis polynomials having the same
 // degree), any other child through its points. Sources are staged 128 at a
 // time with their 1-D basis values.
-// Proxy record: z (3), S, Q, C (3), N (3), 0; each value stored twice.
+// Proxy record: z (3), S, Q, C (3), N (3), 0.
 constexpr int PROXY_THREADS = 128;
 
 template <int N>
@@ -406,8 +405,7 @@ k_proxy_charges(const int32_t* __restrict__ slots, const int32_t* __restrict__ s
                 for (int a = 0; a < N; ++a) T[d][a][a2] = l[a];
             }
             const float* cp = prox + (int64_t)ks * NP * TREE_REC;
-            for (int k = threadIdx.x; k < NP * 8; k += PROXY_THREADS)
-                buf0[k] = cp[(k >> 3) * TREE_REC + 2 * (3 + (k & 7))];
+            for (int k = threadIdx.x; k < NP * 8; k += PROXY_THREADS) buf0[k] = cp[(k >> 3) * TREE_REC + 3 + (k & 7)];
             __syncthreads();
             for (int k = threadIdx.x; k < NP * 8; k += PROXY_THREADS) {  // x pass
                 const int c = k & 7, idx = k >> 3, a = idx / N2, rest = idx - a * N2;
@@ -451,12 +449,12 @@ k_proxy_charges(const int32_t* __restrict__ slots, const int32_t* __restrict__ s
                 const float* r = rec + TREE_REC * (int64_t)i;
 #pragma unroll
                 for (int d = 0; d < 3; ++d) {
-                    lagrange_n<N>((r[2 * d] - mid[d]) * ihalf[d], tn, iden, my + N * d, my + N * (3 + d));
+                    lagrange_n<N>((r[d] - mid[d]) * ihalf[d], tn, iden, my + N * d, my + N * (3 + d));
 #pragma unroll
                     for (int a = 0; a < N; ++a) my[N * (3 + d) + a] *= ihalf[d];  // d/dy = d/dt / half
                 }
 #pragma unroll
-                for (int c = 0; c < 7; ++c) my[6 * N + c] = r[2 * (3 + c)];
+                for (int c = 0; c < 7; ++c) my[6 * N + c] = r[3 + c];
             }
             __syncthreads();
             const int m = min(PROXY_THREADS, e - c0);
@@ -484,17 +482,13 @@ k_proxy_charges(const int32_t* __restrict__ slots, const int32_t* __restrict__ s
     for (int r = 0; r < PER; ++r) {
         const int k = threadIdx.x + r * PROXY_THREADS;
         if (k >= NP) break;
-        float val[TREE_VALS];
-        val[0] = mid[0] + half[0] * tn[ka[r]];
-        val[1] = mid[1] + half[1] * tn[kb[r]];
-        val[2] = mid[2] + half[2] * tn[kc[r]];
+        float* o = prox + ((int64_t)slot * NP + k) * TREE_REC;
+        o[0] = mid[0] + half[0] * tn[ka[r]];
+        o[1] = mid[1] + half[1] * tn[kb[r]];
+        o[2] = mid[2] + half[2] * tn[kc[r]];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) val[3 + c] = acc[r][c];
-        val[11] = 0.f;
-        float4* o = reinterpret_cast<float4*>(prox + ((int64_t)slot * NP + k) * TREE_REC);
-#pragma unroll
-        for (int c = 0; c < TREE_VALS / 2; ++c)
-            o[c] = make_float4(val[2 * c], val[2 * c], val[2 * c + 1], val[2 * c + 1]);
+        for (int c = 0; c < 8; ++c) o[3 + c] = acc[r][c];
+        o[11] = 0.f;
     }
 }
 
@@ -504,8 +498,8 @@ k_proxy_charges(const int32_t* __restrict__ slots, const int32_t* __restrict__ s
 // walks the leaves longest first, a leaf's splits side by side.
 template <int MODE>
 __global__ void __launch_bounds__(TREE_LEAF, 7) k_tree_eval(TreeJob job) {
-    __shared__ __align__(16) float tile[2 * TREE_EVAL_TILE * TREE_REC];
-    static_assert((MODE == 0 ? 2 : 10) * TREE_LEAF <= 2 * TREE_EVAL_TILE * TREE_REC, "reduction buffer");
+    __shared__ __align__(16) float tile[TREE_EVAL_TILE * (2 * TREE_REC + TREE_DUP)];
+    static_assert((MODE == 0 ? 2 : 10) * TREE_LEAF <= TREE_EVAL_TILE * (2 * TREE_REC + TREE_DUP), "reduction buffer");
     const int sp = (int)(blockIdx.x % (unsigned)job.nsplit);
     tree_leaf_body<MODE, 2>(job, job.leaf_order[blockIdx.x / (unsigned)job.nsplit], sp, tile);
 }

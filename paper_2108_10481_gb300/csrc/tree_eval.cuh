@@ -7,9 +7,9 @@
 namespace pb {
 
 constexpr int TREE_LEAF = 128;     // targets per leaf
-constexpr int TREE_VALS = 12;      // values per tree source / proxy record
-constexpr int TREE_REC = 24;       // floats per record: every value twice, so that one shared-memory
-                                   // load gives both halves of a packed f32x2 operand
+constexpr int TREE_REC = 12;       // floats per tree source / proxy record in global memory
+constexpr int TREE_DUP = 24;       // floats per record as summed from shared memory: every value twice,
+                                   // so that one load gives both halves of a packed f32x2 operand
 constexpr int TREE_EVAL_TILE = 128;  // sources staged per round
 
 struct TreeCoef {
@@ -119,10 +119,12 @@ struct TreeTiles {
 // (kernel G with the interpolated charges). Near: the other sources directly,
 // with the direct pair kernel's arithmetic (identical points skipped). Tiles
 // are staged in two buffers by asynchronous copies, the next one in flight
-// while the current one is summed. `tile` holds at least
-// 2 x TREE_EVAL_TILE x TREE_REC floats and (NQ - 1) x NACC x TREE_LEAF floats.
-// Every thread of the group calls it (it synchronises the CTA) and returns
-// with no copy in flight.
+// while the current one is summed; before it is summed a tile is copied once
+// more inside shared memory with every value twice (TREE_DUP floats per
+// record), which keeps the records in global memory (and L2) at 48 bytes.
+// `tile` holds at least TREE_EVAL_TILE x (2 TREE_REC + TREE_DUP) floats and
+// (NQ - 1) x NACC x TREE_LEAF floats. Every thread of the group calls it (it
+// synchronises the CTA) and returns with no copy in flight.
 template <int MODE, int NQ>
 __device__ __forceinline__ void tree_leaf_body(const TreeJob& T, int leaf, int sp, float* tile) {
     constexpr int NACC = MODE == 0 ? 2 : 10;
@@ -144,13 +146,13 @@ __device__ __forceinline__ void tree_leaf_body(const TreeJob& T, int leaf, int s
     float2 X0 = t_splat(0.f), X1 = X0, X2 = X0;
     if (live0) {
         X0.x = rec[TREE_REC * (int64_t)ti0];
-        X1.x = rec[TREE_REC * (int64_t)ti0 + 2];
-        X2.x = rec[TREE_REC * (int64_t)ti0 + 4];
+        X1.x = rec[TREE_REC * (int64_t)ti0 + 1];
+        X2.x = rec[TREE_REC * (int64_t)ti0 + 2];
     }
     if (live1) {
         X0.y = rec[TREE_REC * (int64_t)ti1];
-        X1.y = rec[TREE_REC * (int64_t)ti1 + 2];
-        X2.y = rec[TREE_REC * (int64_t)ti1 + 4];
+        X1.y = rec[TREE_REC * (int64_t)ti1 + 1];
+        X2.y = rec[TREE_REC * (int64_t)ti1 + 2];
     }
     const TreeCoef& cf = T.cf;
     const float2 c00 = t_splat(cf.k[0][0]), c01 = t_splat(cf.k[0][1]), c02 = t_splat(cf.k[0][2]),
@@ -179,13 +181,24 @@ __device__ __forceinline__ void tree_leaf_body(const TreeJob& T, int leaf, int s
         }
         cp_async_commit();
         cp_async_wait<1>();  // this thread's copies of the current tile have landed
-        __syncthreads();     // and every thread's
-        const float* cur = tile + buf * TILE * TREE_REC;
+        __syncthreads();     // and every thread's; the duplicated tile's last readers are done
+        float* dup = tile + 2 * TILE * TREE_REC;
+        {
+            const float4* raw = reinterpret_cast<const float4*>(tile + buf * TILE * TREE_REC);
+            float4* d4 = reinterpret_cast<float4*>(dup);
+            for (int k = threadIdx.x; k < cnt * TREE_REC / 4; k += NTH) {
+                const float4 v = raw[k];
+                d4[2 * k] = make_float4(v.x, v.x, v.y, v.y);
+                d4[2 * k + 1] = make_float4(v.z, v.z, v.w, v.w);
+            }
+        }
+        __syncthreads();
+        const float* cur = dup;
         if (any && far) {
 #pragma unroll 2
             for (int j = grp; j < cnt; j += NQ) {
                 // the record's values, each as a splatted pair
-                const float4* z4 = reinterpret_cast<const float4*>(cur + TREE_REC * j);
+                const float4* z4 = reinterpret_cast<const float4*>(cur + TREE_DUP * j);
                 const float4 a = z4[0], b = z4[1], c = z4[2];
                 const float2 d0 = t_sub2(X0, make_float2(a.x, a.y)), d1 = t_sub2(X1, make_float2(a.z, a.w)),
                              d2 = t_sub2(X2, make_float2(b.x, b.y));
@@ -220,7 +233,7 @@ __device__ __forceinline__ void tree_leaf_body(const TreeJob& T, int leaf, int s
         } else if (any) {
 #pragma unroll 2
             for (int j = grp; j < cnt; j += NQ) {
-                const float4* y4 = reinterpret_cast<const float4*>(cur + TREE_REC * j);
+                const float4* y4 = reinterpret_cast<const float4*>(cur + TREE_DUP * j);
                 const float4 a = y4[0], b = y4[1], c = y4[2], dd = y4[3];
                 const float2 y0 = make_float2(a.x, a.y), y1 = make_float2(a.z, a.w), y2 = make_float2(b.x, b.y),
                              y3 = make_float2(b.z, b.w), y4v = make_float2(c.x, c.y), y5 = make_float2(c.z, c.w),
@@ -257,7 +270,6 @@ __device__ __forceinline__ void tree_leaf_body(const TreeJob& T, int leaf, int s
                 }
             }
         }
-        __syncthreads();  // every thread is done with this buffer before it is refilled
         have = have_next;
         cnt = cnt_next;
         far = far_next;
