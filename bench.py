@@ -38,15 +38,13 @@ FP32_LANES_PER_SM = 128  # FP32 pipe operations per SM per clock
 FP64_FLOPS_PER_SM = 4    # FP64 flops per SM per clock (two FMA lanes): 152 x 4 x 2.07 GHz = 1.26 TFLOP/s
 HBM_FALLBACK_GBS = 6800.0  # the profiling recipe's fallback copy bandwidth, used only without MEASURED_PEAKS.json
 L2_FLUSH_BYTES = 256 << 20
-# DRAM bytes per launch of the packed FP32 pair kernel in its V/K + D/T mode, from one ncu capture at 122,880
-# points (dram__bytes_read.sum + dram__bytes_write.sum; profiles/pair32x2_vkdt_multi_charge_sphere.md). Valid only
-# for that kernel as captured; any other dominant kernel reports null.
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of kernel families from ncu captures of
+# the same workload (profiles/memory_kernels_protein5000.md and the other summaries there); a family whose kernel
+# changed since its capture, or that has none, reports null.
 NCU_TRAFFIC = {  # (kernel family, formulation or "any", far-rule points, band) -> dram read + write per launch
-    ("pair32", "juffer", 122880, 0.0): 17.72e6,
-    ("near_adj", "any", 61440, 3.0): 172.08e6,
-    ("near_coin", "any", 61440, 3.0): 6.95e6,
-    ("near_band", "any", 61440, 3.0): 690.51e6,
-    ("tree32", "juffer", 61440, 3.0): 7.47e6,
+    # 5,000-atom molecule (667,788 far-rule points, band of 3 radii), ncu dram__bytes_{read,write}.sum
+    ("spmv", "juffer", 667788, 3.0): 337.5e6,
+    ("cheb", "juffer", 667788, 3.0): 16.04e6,
 }
 
 
