@@ -117,12 +117,15 @@ static int free_req(ServeReq* r) {
 
 // Device bytes a request holds while resident (upper estimates of the
 // adjacency sizes: 16 adjacent pairs per triangle, 25 near nonzeros per vertex;
-// a distance band of eta radii adds about 12 eta^2 pairs per triangle and
-// 7 eta^2 nonzeros per vertex).
+// a distance band of eta radii adds about 18 eta^2 ordered pairs per triangle
+// and 15 eta^2 nonzeros per vertex: the synthetic molecules have about 145
+// band pairs per triangle and 147 nonzeros per vertex at 3 radii). The near
+// build's per-pair blocks (432 bytes per listed pair) are the largest
+// transient: about 14 GB on the 5,000-atom molecule.
 static size_t footprint(pb_ctx* ctx, int64_t nv, int64_t nt, const pb_quad_plan& plan, int mmax, int64_t nq) {
     const int Q = plan.far_q;
-    const double eta = plan.band_eta, band = 12.0 * eta * eta * nt;
-    const double np = (double)Q * nt, nadj = 16.0 * nt, npairs = nadj + band, nnz = (25.0 + 7.0 * eta * eta) * nv;
+    const double eta = plan.band_eta, band = 18.0 * eta * eta * nt;
+    const double np = (double)Q * nt, nadj = 16.0 * nt, npairs = nadj + band, nnz = (25.0 + 15.0 * eta * eta) * nv;
     const double npref = eta > 0.0 ? 6.0 * nt : 0.0;
     double mesh = 24 * nv + 12 * nt + 128 * nt + 64 * np + 32 * npref + 8 * (nv + 1) + 12 * nt + 16 * npairs +
                   12 * nnz + 4 * nv + 4 * (nnz + 1) + 36 * npairs;
