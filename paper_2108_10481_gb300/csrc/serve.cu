@@ -374,7 +374,7 @@ static int tick(pb_server* srv) {
                 r->phase = PH_ENERGY;
                 continue;
             }
-            r->inner_tol = r->mixed ? std::min(0.5, std::max(r->opts.inner_tol, INNER_AIM * tol / r->rel)) : tol;
+            r->inner_tol = r->mixed ? std::min(INNER_CAP, std::max(r->opts.inner_tol, INNER_AIM * tol / r->rel)) : tol;
             PB_TRY(gm_begin(r->G, r->w, srv->res_dev + 4 * r->slot, rs_of(r)));
             if (r->mixed) PB_CUDA(cudaMemsetAsync(r->dd, 0, sizeof(double) * 2 * r->m->nv, rs_of(r)));
             r->j = 0;

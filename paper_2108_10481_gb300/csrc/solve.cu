@@ -799,7 +799,7 @@ static int solve_one(const pb_mesh* m, const pb_near* nf, const pb_solve_opts* o
                 // the outer residual no longer falls: its own accuracy is reached
                 if (outer >= 2 && rel > 0.5 * prev) break;
                 PB_CUDA(cudaMemsetAsync(dd, 0, sizeof(double) * n2, s));
-                double inner = std::min(0.5, std::max(o->inner_tol, INNER_AIM * o->tol / rel));
+                double inner = std::min(INNER_CAP, std::max(o->inner_tol, INNER_AIM * o->tol / rel));
                 rc = gmres(S, G, PB_F32, rr, dd, true, inner, 0.0, o->max_it, &it, &res, &beta);
                 total_it += it;
                 if (rc != PB_OK) break;
