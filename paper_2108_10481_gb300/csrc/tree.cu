@@ -73,7 +73,10 @@ static int build_tree(pb_mesh* m, int order, double theta, PbTree** out) {
     std::vector<HostNode> nodes;
     nodes.reserve(2 * np / TREE_LEAF + 16);
     const int n = order + 1, nprox = n * n * n;
-    // recursive median split on the longest axis (explicit stack)
+    // recursive split on the longest axis (explicit stack), near the median but with a multiple of
+    // TREE_LEAF points on the left: every leaf then holds TREE_LEAF points but at most one per
+    // path, and the evaluation's f32x2 lanes (a thread's targets i and i + TREE_LEAF / 2) are full
+    // (median splits leave 81 points per leaf on average on the 5,000-atom molecule)
     struct Job { int32_t b, e, node; };
     nodes.push_back(HostNode{});
     std::vector<Job> stack{{0, (int32_t)np, 0}};
@@ -98,7 +101,8 @@ static int build_tree(pb_mesh* m, int order, double theta, PbTree** out) {
             int ax = 0;
             for (int k = 1; k < 3; ++k)
                 if (nd.hi[k] - nd.lo[k] > nd.hi[ax] - nd.lo[ax]) ax = k;
-            const int32_t mid = j.b + (j.e - j.b) / 2;
+            const int32_t n_here = j.e - j.b, half = n_here / 2;
+            const int32_t mid = j.b + std::min(n_here - 1, (half + TREE_LEAF - 1) / TREE_LEAF * TREE_LEAF);
             std::nth_element(perm.begin() + j.b, perm.begin() + mid, perm.begin() + j.e,
                              [&](int32_t a, int32_t c) { return P[4 * a + ax] < P[4 * c + ax]; });
             nd.c0 = (int32_t)nodes.size();
