@@ -581,7 +581,13 @@ int tree_far(const pb_mesh* m, const FarPlan& fp, const double* x, bool need_u, 
     PB_TRY(tree_prepare(m, fp, x, need_u, need_v, &job, s));
     const PbTree* t = m->tree;
     const unsigned grid = (unsigned)(t->nleaf * job.nsplit);
-    Timer tm(m->ctx, PB_KERNEL_TREE32, s, (double)(t->direct_pairs + t->proxy_pairs), fp.mode == 0 ? 25.0 : 36.0);
+    // FP32 operations per interaction as the evaluation does them (f32x2 lanes counted singly; the two
+    // MUFU operations, rsqrt and ex2, not counted): a direct pair 24 (V/K rows) or 35 (V/K + D/T
+    // rows), a proxy 12 or 29 (its charges come combined with the kernel coefficients)
+    const double ops_near = fp.mode == 0 ? 24.0 : 35.0, ops_far = fp.mode == 0 ? 12.0 : 29.0;
+    const double inter = (double)(t->direct_pairs + t->proxy_pairs);
+    const double ops = ((double)t->direct_pairs * ops_near + (double)t->proxy_pairs * ops_far) / std::max(1.0, inter);
+    Timer tm(m->ctx, PB_KERNEL_TREE32, s, inter, ops);
     if (fp.mode == 0) k_tree_eval<0><<<grid, TREE_LEAF, 0, s>>>(job);
     else k_tree_eval<1><<<grid, TREE_LEAF, 0, s>>>(job);
     ::pb::count_launch();
