@@ -45,6 +45,11 @@ NCU_TRAFFIC = {  # (kernel family, formulation or "any", far-rule points, band) 
     # 5,000-atom molecule (667,788 far-rule points, band of 3 radii), ncu dram__bytes_{read,write}.sum
     ("spmv", "juffer", 667788, 3.0): 337.5e6,
     ("cheb", "juffer", 667788, 3.0): 16.04e6,
+    ("tree32", "juffer", 667788, 3.0): 246.8e6,
+    ("pair32acc", "juffer", 667788, 3.0): 496.5e6,
+    ("near_adj", "any", 667788, 3.0): 1372.1e6,  # mean of the edge-pair and vertex-pair launches
+    ("near_band", "any", 667788, 3.0): 15203.8e6,
+    ("near_coin", "any", 667788, 3.0): 233.9e6,
 }
 
 
