@@ -61,6 +61,9 @@ def test_tree_application_accuracy(pb, sphere, form):
     assert errs[6] < 1e-4
     assert errs[6] < errs[3]
     assert info["direct_pairs"] + info["proxy_pairs"] < npts * npts
+    # every split leaves a multiple of 128 points on the left: the leaves are full but one per path,
+    # ceil(points / 128) of them
+    assert info["leaves"] == -(-npts // 128)
 
 
 def test_tree_mixed_solve_reaches_direct_solution(pb, sphere):
