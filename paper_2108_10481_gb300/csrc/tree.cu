@@ -2,8 +2,9 @@
 // of the direct pair sum for large meshes, where the paper uses a fast
 // multipole method (ExaFMM, expansion order 3).
 //
-// The quadrature points are sorted into a kd-tree (longest-axis median
-// splits, leaves of at most LEAF points). For a leaf of targets and a cluster
+// The quadrature points are sorted into a kd-tree (longest-axis splits near
+// the median, with a multiple of TREE_LEAF points on the left, so that the
+// leaves hold TREE_LEAF points but one per path). For a leaf of targets and a cluster
 // that is well separated (radius sum below theta times the centre distance),
 // the cluster's sources are replaced by proxy sources on an n x n x n tensor
 // grid of Chebyshev points of its bounding box: the y-dependence of every
@@ -15,7 +16,9 @@
 // both kernels at once (the interpolation is kernel independent). Clusters
 // with fewer points than proxies, and all other pairs, are summed directly
 // with the same arithmetic as the direct FP32 pair kernel (identical points
-// skipped). The result approximates the direct far sum; the mixed-precision
+// skipped; the direct and proxy arithmetic is the same formula with the
+// charges that only meet constant coefficients combined with them once per
+// staged record). The result approximates the direct far sum; the mixed-precision
 // solver uses it only for its inner iterations and keeps the exact sums for
 // the outer residual.
 #include <algorithm>
