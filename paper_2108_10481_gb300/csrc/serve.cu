@@ -368,13 +368,18 @@ static int tick(pb_server* srv) {
             if (r->outer == 0) r->bnorm = beta;
             r->prev_rel = r->rel;
             r->rel = r->bnorm > 0.0 ? beta / r->bnorm : 0.0;
-            bool stall = r->mixed && r->outer >= 2 && r->rel > 0.5 * r->prev_rel;
+            // r->inner_tol still holds the last sweep's inner tolerance
+            const double next =
+                r->mixed && r->rel > 0.0
+                    ? refine_inner_tol(r->outer, r->rel, r->prev_rel, r->inner_tol, tol, r->opts.inner_tol)
+                    : tol;
+            const bool stall = r->mixed && next < 0.0;
             if (beta == 0.0 || (r->mixed && (r->rel <= tol || stall)) || (!r->mixed && r->outer > 0)) {
                 if (r->rel > tol) r->status = PB_ENOCONV;
                 r->phase = PH_ENERGY;
                 continue;
             }
-            r->inner_tol = r->mixed ? std::min(INNER_CAP, std::max(r->opts.inner_tol, INNER_AIM * tol / r->rel)) : tol;
+            r->inner_tol = next;
             PB_TRY(gm_begin(r->G, r->w, srv->res_dev + 4 * r->slot, rs_of(r)));
             if (r->mixed) PB_CUDA(cudaMemsetAsync(r->dd, 0, sizeof(double) * 2 * r->m->nv, rs_of(r)));
             r->j = 0;

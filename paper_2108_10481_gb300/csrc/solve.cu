@@ -772,7 +772,7 @@ static int solve_one(const pb_mesh* m, const pb_near* nf, const pb_solve_opts* o
         rc = dev_alloc((void**)&rr, sizeof(double) * 2 * n2);
         if (rc == PB_OK) {
             double* dd = rr + n2;
-            double bnorm = 0.0;
+            double bnorm = 0.0, inner_last = 1.0;
             for (outer = 0; outer < std::max(1, o->max_outer) && rc == PB_OK; ++outer) {
                 int it = 0;
                 double res = 0.0, beta = 0.0;
@@ -796,10 +796,10 @@ static int solve_one(const pb_mesh* m, const pb_near* nf, const pb_solve_opts* o
                 rel = bnorm > 0.0 ? beta / bnorm : 0.0;
                 tr.note("outer_rel", rel);
                 if (rel <= o->tol) break;
-                // the outer residual no longer falls: its own accuracy is reached
-                if (outer >= 2 && rel > 0.5 * prev) break;
+                const double inner = refine_inner_tol(outer, rel, prev, inner_last, o->tol, o->inner_tol);
+                if (inner < 0.0) break;  // the outer residual no longer falls: its own accuracy is reached
+                inner_last = inner;
                 PB_CUDA(cudaMemsetAsync(dd, 0, sizeof(double) * n2, s));
-                double inner = std::min(INNER_CAP, std::max(o->inner_tol, INNER_AIM * o->tol / rel));
                 rc = gmres(S, G, PB_F32, rr, dd, true, inner, 0.0, o->max_it, &it, &res, &beta);
                 total_it += it;
                 if (rc != PB_OK) break;

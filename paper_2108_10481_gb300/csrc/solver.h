@@ -3,6 +3,8 @@
 
 #include "internal.h"
 
+#include <algorithm>
+
 namespace pb {
 
 // Mixed-precision refinement: an inner solve asks for
@@ -17,6 +19,24 @@ namespace pb {
 // last sweep land above the tolerance on the 500-atom molecule (one sweep more).
 constexpr double INNER_AIM = 1.0;
 constexpr double INNER_CAP = 0.1;
+constexpr double INNER_RETRY = 1e-3;
+
+// Inner tolerance of the next refinement sweep after `sweeps` sweeps whose
+// outer residuals were prev and then rel, the last sweep having asked its
+// inner solve for inner_last; negative when the refinement should stop
+// because the outer residual no longer falls (less than a halving) although
+// the last inner solve asked for a reduction of INNER_RETRY or better (the
+// residual's own accuracy is reached). A sweep that stalled on a looser inner
+// solve (a Calderon preconditioner's FP32 operator, say, can make a sweep
+// contract by less than the inner solve did) is followed by one that asks for
+// INNER_RETRY.
+inline double refine_inner_tol(int sweeps, double rel, double prev, double inner_last, double tol,
+                               double inner_min) {
+    const double inner = std::min(INNER_CAP, std::max(inner_min, INNER_AIM * tol / rel));
+    if (sweeps < 2 || rel <= 0.5 * prev) return inner;
+    if (inner_last <= std::max(INNER_RETRY, inner_min)) return -1.0;
+    return std::max(inner_min, std::min(inner, INNER_RETRY));
+}
 
 struct Solver {
     const pb_mesh* m;
