@@ -136,8 +136,8 @@ typedef struct {
     int max_it;        /* GMRES iterations (per refinement sweep for PB_MIXED) */
     int restart;       /* 0 = unrestarted (basis of max_it vectors) */
     int precision;     /* PB_F64 or PB_MIXED */
-    double inner_tol;  /* PB_MIXED: relative tolerance of each inner solve */
-    int max_outer;     /* PB_MIXED: refinement sweeps */
+    double inner_tol;  /* PB_MIXED: smallest relative tolerance an inner solve asks for */
+    int max_outer;     /* PB_MIXED: refinement sweeps at most */
     double alpha;      /* PB_CFIE_INT / PB_CFIE_EXT coefficients */
     double beta;
     double pc_a;       /* scaled-mass constants; 0 = the paper's choice */
@@ -254,7 +254,16 @@ int pb_rhs_charges(pb_ctx* ctx, const pb_mesh* mesh, const double* xq, const dou
 /* Solve P^-1 A x = P^-1 rhs (paper, "Preconditioning": left preconditioning,
  * GMRES) from x = 0. opts NULL = {tol 1e-6, max_it 500, unrestarted, PB_F64}.
  * rhs and x are device arrays of 2*N_v. On PB_ENOCONV x holds the best
- * iterate and info (optional) is filled. */
+ * iterate and info (optional) is filled.
+ * PB_MIXED: each sweep computes the residual r = rhs - A x with PB_F32_ACCURATE
+ * applications and its preconditioned norm, stops once that is at most tol
+ * relative to the right-hand side's, and otherwise solves A d = r with PB_F32
+ * applications to min(0.1, max(inner_tol, tol / rel)) of the current relative
+ * residual rel and adds d to x. After a sweep (from the second on) that did
+ * not halve the residual the next one asks for 1e-3; a sweep that asked for 1e-3 (or inner_tol, if
+ * larger) and still did not halve it ends the solve (PB_ENOCONV if above tol):
+ * the split-coordinate residual's own accuracy, about 2e-8 relative on the
+ * molecules, is then reached. */
 int pb_solve(pb_ctx* ctx, const pb_mesh* mesh, const pb_near* near, const pb_params* prm, int form,
              int precond, const pb_solve_opts* opts, const double* rhs, double* x,
              pb_solve_info* info, void* stream);
