@@ -1535,8 +1535,9 @@ extern "C" int pb_autotune(pb_ctx* ctx, const pb_mesh* m, const pb_near* nf, con
         const TuneEntry saved = slot;
         double best = 1e300, dflt = 0.0;
         TuneEntry best_e;
-        for (const auto& kc : cands)
+        for (size_t ci = 0; ci < cands.size() && rc == PB_OK; ++ci)
             for (double sc : scales) {
+                const auto& kc = cands[ci];
                 const int k = kc.first;
                 slot.kernel = k;
                 slot.shape = kc.second;
